@@ -1,0 +1,194 @@
+"""ctypes binding of the FP64 CPU oracle (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It never touches the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_U8 = ctypes.POINTER(ctypes.c_ubyte)
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("n_bins", ctypes.c_int), ("order_k", ctypes.c_int), ("quad_q", ctypes.c_int),
+        ("flux_mode", ctypes.c_int), ("coag_kind", ctypes.c_int), ("frag_kind", ctypes.c_int),
+        ("break_kind", ctypes.c_int), ("cutoff_mode", ctypes.c_int), ("limiter", ctypes.c_int),
+        ("mfrag_mode", ctypes.c_int),
+        ("x_min", ctypes.c_double), ("x_max", ctypes.c_double),
+        ("coag_p", ctypes.c_double * 8), ("frag_p", ctypes.c_double * 8),
+        ("break_p", ctypes.c_double * 8),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER(OrcParams)
+        L.orc_gauss.argtypes = [ctypes.c_int, _D, _D]
+        L.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D]
+        L.orc_mfrag_ratio.argtypes = [ctypes.c_double]
+        L.orc_mfrag_ratio.restype = ctypes.c_double
+        L.orc_bin_min.argtypes = [_D, ctypes.c_int]
+        L.orc_bin_min.restype = ctypes.c_double
+        L.orc_edges.argtypes = [P, _D]
+        L.orc_kernels.argtypes = [P, ctypes.c_int, _D, _D, _D, _D]
+        L.orc_mass_split.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D]
+        L.orc_flux_point.argtypes = [P, _D, ctypes.c_int, _D, ctypes.c_int, _D, _D]
+        L.orc_vol_frag.argtypes = [P, _D, ctypes.c_int, _D, _D]
+        L.orc_rhs_batch.argtypes = [P, ctypes.c_int, _D, _D, _D, ctypes.c_int]
+        L.orc_limit_batch.argtypes = [P, ctypes.c_int, _D, _U8]
+        L.orc_step_batch.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _U8, ctypes.c_int]
+        L.orc_mass_batch.argtypes = [P, ctypes.c_int, _D, _D]
+        L.orc_project_batch.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D]
+        L.orc_max_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def params(spec) -> OrcParams:
+    p = OrcParams()
+    p.n_bins, p.order_k, p.quad_q = spec.n_bins, spec.order_k, spec.quad_q
+    p.flux_mode, p.coag_kind, p.frag_kind = spec.flux_mode, spec.coag_kind, spec.frag_kind
+    p.break_kind, p.cutoff_mode, p.limiter = spec.break_kind, spec.cutoff_mode, spec.limiter
+    p.mfrag_mode = spec.mfrag_mode
+    p.x_min, p.x_max = spec.x_min, spec.x_max
+    for name in ("coag_p", "frag_p", "break_p"):
+        vals = getattr(spec, name)
+        arr = getattr(p, name)
+        for i, v in enumerate(vals):
+            arr[i] = v
+    return p
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def gauss(Q: int):
+    s = np.zeros(Q)
+    w = np.zeros(Q)
+    _check(lib().orc_gauss(Q, _p(s), _p(w)), "gauss")
+    return s, w
+
+
+def legendre(k: int, xi: float):
+    P = np.zeros(k + 1)
+    dP = np.zeros(k + 1)
+    _check(lib().orc_legendre(k, float(xi), _p(P), _p(dP)), "legendre")
+    return P, dP
+
+
+def mfrag_ratio(q: float) -> float:
+    return lib().orc_mfrag_ratio(float(q))
+
+
+def bin_min(gj, k: int) -> float:
+    gj = _f64(gj)
+    return lib().orc_bin_min(_p(gj), int(k))
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()
+
+
+class Oracle:
+    """FP64 reference for one group description (see paper_2607_13740_b300.workloads.GroupSpec)."""
+
+    def __init__(self, spec):
+        self.spec = spec
+        self._par = params(spec)
+        self.P = spec.n_bins * (spec.order_k + 1)
+
+    @property
+    def _pp(self):
+        return ctypes.byref(self._par)
+
+    def edges(self):
+        e = np.zeros(self.spec.n_bins + 1)
+        _check(lib().orc_edges(self._pp, _p(e)), "edges")
+        return e
+
+    def kernels(self, u, v):
+        u, v = _f64(u), _f64(v)
+        kc, kf = np.zeros_like(u), np.zeros_like(u)
+        _check(lib().orc_kernels(self._pp, u.size, _p(u), _p(v), _p(kc), _p(kf)), "kernels")
+        return kc, kf
+
+    def mass_split(self, x, u, v):
+        x, u, v = _f64(x), _f64(u), _f64(v)
+        a, b = np.zeros_like(x), np.zeros_like(x)
+        _check(lib().orc_mass_split(self._pp, x.size, _p(x), _p(u), _p(v), _p(a), _p(b)), "mass_split")
+        return a, b
+
+    def flux_point(self, g, x, parts: int = 3):
+        g = _f64(g).reshape(-1)
+        x = _f64(np.atleast_1d(x))
+        F, Fa = np.zeros_like(x), np.zeros_like(x)
+        _check(lib().orc_flux_point(self._pp, _p(g), x.size, _p(x), parts, _p(F), _p(Fa)), "flux_point")
+        return F, Fa
+
+    def vol_frag(self, g, j: int):
+        g = _f64(g).reshape(-1)
+        V = np.zeros(self.spec.order_k + 1)
+        Va = np.zeros_like(V)
+        _check(lib().orc_vol_frag(self._pp, _p(g), int(j), _p(V), _p(Va)), "vol_frag")
+        return V, Va
+
+    def rhs(self, g, threads: int = 0):
+        g = _f64(g).reshape(-1, self.P)
+        L = np.zeros_like(g)
+        S = np.zeros_like(g)
+        _check(lib().orc_rhs_batch(self._pp, g.shape[0], _p(g), _p(L), _p(S), threads), "rhs")
+        return L, S
+
+    def limit(self, g):
+        g = _f64(g).reshape(-1, self.P).copy()
+        f = np.zeros(g.shape[0], dtype=np.uint8)
+        _check(lib().orc_limit_batch(self._pp, g.shape[0], _p(g), f.ctypes.data_as(_U8)), "limit")
+        return g, f
+
+    def step(self, g, dt, n_steps: int, threads: int = 0):
+        g = _f64(g).reshape(-1, self.P).copy()
+        n = g.shape[0]
+        dt = _f64(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        mass = np.zeros(n)
+        f = np.zeros(n, dtype=np.uint8)
+        _check(lib().orc_step_batch(self._pp, n, _p(g), _p(dt), int(n_steps), _p(mass),
+                                    f.ctypes.data_as(_U8), threads), "step")
+        return g, mass, f
+
+    def mass(self, g):
+        g = _f64(g).reshape(-1, self.P)
+        m = np.zeros(g.shape[0])
+        _check(lib().orc_mass_batch(self._pp, g.shape[0], _p(g), _p(m)), "mass")
+        return m
+
+    def project(self, ic_kind: int, ic_params):
+        ic = _f64(np.atleast_2d(ic_params))
+        if ic.shape[1] < 4:
+            ic = np.pad(ic, ((0, 0), (0, 4 - ic.shape[1])))
+        g = np.zeros((ic.shape[0], self.P))
+        _check(lib().orc_project_batch(self._pp, ic.shape[0], int(ic_kind), _p(ic), _p(g)), "project")
+        return g

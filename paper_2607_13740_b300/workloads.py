@@ -1,0 +1,137 @@
+"""Seeded synthetic workloads shared by the CUDA path, the tests and the benchmark.
+
+This module holds configuration and random numbers only: group descriptions
+(grid, order, physics kinds and parameters), per-cell initial-condition
+parameters and random coefficient arrays.  It contains none of the method's
+arithmetic (no quadrature, basis functions, fluxes or time stepping), so both
+the CUDA library and the independent FP64 oracle can take their inputs from it.
+
+The enumerations below are the interface values accepted by both
+implementations (the C header ``include/grace.h`` declares the same numbers).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# collision kernels (Secs. 4.2-4.5)
+COAG_NONE, COAG_CONST, COAG_ADD, COAG_MULT, COAG_MAXWELL, COAG_BALLISTIC = 0, 1, 2, 3, 4, 5
+FRAG_NONE, FRAG_MULT, FRAG_MAXWELL, FRAG_BALLISTIC = 0, 1, 2, 3
+# breakage functions: uniform binary (Sec. 4.4), power law + remnant (eq. break),
+# and b = delta(w - u - v), the coagulation special case of eq. (Ffrag)
+BREAK_UNIFORM_BINARY, BREAK_POWERLAW_REMNANT, BREAK_COAG_DELTA = 0, 1, 2
+# initial conditions projected with eq. (init)
+IC_EXP, IC_POWERLAW, IC_FIRST_BIN = 0, 1, 2
+# flux truncation (Sec. 3.3): Delta x = -u + x_min, or Delta x = 0
+FLUX_CONSERVATIVE, FLUX_NONCONSERVATIVE = 0, 1
+
+
+@dataclasses.dataclass(frozen=True)
+class GroupSpec:
+    """One (grid, order, physics) combination; every cell of a group shares it."""
+    n_bins: int
+    order_k: int
+    x_min: float
+    x_max: float
+    flux_mode: int = FLUX_CONSERVATIVE
+    coag_kind: int = COAG_NONE
+    coag_p: tuple = ()
+    frag_kind: int = FRAG_NONE
+    frag_p: tuple = ()
+    break_kind: int = BREAK_UNIFORM_BINARY
+    break_p: tuple = ()
+    cutoff_mode: int = 0
+    mfrag_mode: int = 0
+    quad_q: int = 0
+    limiter: int = 1
+
+    @property
+    def n_coef(self) -> int:
+        return self.n_bins * (self.order_k + 1)
+
+    def replace(self, **kw) -> "GroupSpec":
+        return dataclasses.replace(self, **kw)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    spec: GroupSpec
+    n_cells: int
+    ic_kind: int
+    ic_params: np.ndarray      # [n_cells, 4] float64
+    dt: np.ndarray             # [n_cells] float64
+    n_steps: int
+    notes: str = ""
+
+
+# --------------------------------------------------------------------------
+# the paper's test problems (Sec. 4) and the large synthetic batches
+# --------------------------------------------------------------------------
+
+def constant_kernel_spec(n_bins=20, order_k=2, flux_mode=FLUX_NONCONSERVATIVE,
+                         x_min=1e-4, x_max=1e6) -> GroupSpec:
+    """Pure coagulation with K = 1 (Sec. 4.2)."""
+    return GroupSpec(n_bins, order_k, x_min, x_max, flux_mode, COAG_CONST, (1.0,))
+
+
+def single_cell_constant(flux_mode=FLUX_NONCONSERVATIVE) -> Workload:
+    """One cell, K = 1, N = 20 over [1e-4, 1e6], k = 2, g0 = x exp(-x),
+    SSP-RK3 with dt = 1e-2 to t = 10 (1000 steps)."""
+    spec = constant_kernel_spec(20, 2, flux_mode)
+    return Workload("single_cell_constant_N20_k2", spec, 1, IC_EXP,
+                    np.array([[1.0, 1.0, 0.0, 0.0]]), np.array([1e-2]), 1000)
+
+
+def additive_spec(n_bins=40, order_k=2, x_min=1e-6, x_max=1e10) -> GroupSpec:
+    """Pure coagulation with K = x + y (Sec. 4.3), conservative fluxes."""
+    return GroupSpec(n_bins, order_k, x_min, x_max, FLUX_CONSERVATIVE, COAG_ADD, (1.0,))
+
+
+def batched_additive(n_cells=65536, seed=1002, n_bins=40, order_k=2, n_steps=100) -> Workload:
+    """Batched coagulation: K = x + y, N = 40 over [1e-6, 1e10], k = 2.
+    Per cell g0 = A x exp(-x / x0), A ~ lognormal(0, 0.5), x0 ~ loguniform[1e-3, 1];
+    dt_c = 0.02 / M_c with M_c = A x0^2 the cell's total mass, so 100 steps
+    reach M_c t = 2."""
+    rng = np.random.default_rng(seed)
+    A = rng.lognormal(0.0, 0.5, n_cells)
+    x0 = np.exp(rng.uniform(math.log(1e-3), math.log(1.0), n_cells))
+    ic = np.zeros((n_cells, 4))
+    ic[:, 0] = A
+    ic[:, 1] = x0
+    dt = 0.02 / (A * x0 * x0)
+    return Workload(f"batched_additive_{n_cells}cells_N{n_bins}_k{order_k}",
+                    additive_spec(n_bins, order_k), n_cells, IC_EXP, ic, dt, n_steps,
+                    "A~lognormal(0,0.5), x0~loguniform[1e-3,1], dt=0.02/(A x0^2)")
+
+
+def pure_fragmentation_spec(n_bins=20, order_k=2, x_min=1e-6, x_max=1e3,
+                            flux_mode=FLUX_NONCONSERVATIVE) -> GroupSpec:
+    """Pure fragmentation, K_frag = x y with uniform binary breakage (Sec. 4.4)."""
+    return GroupSpec(n_bins, order_k, x_min, x_max, flux_mode, COAG_NONE, (),
+                     FRAG_MULT, (1.0,), BREAK_UNIFORM_BINARY, ())
+
+
+def coupled_toy_spec(n_bins=20, order_k=2, flux_mode=FLUX_NONCONSERVATIVE,
+                     x_min=1e-6, x_max=1e3, alpha=-1.83) -> GroupSpec:
+    """Coupled aggregation-breakage toy model (Sec. 4.5): Maxwellian relative
+    velocities with dv_rms = 0.5, v_b = 0.1, v_f = 1; power-law fragments with
+    index alpha plus a remnant, m_frag from eq. (mfrag)."""
+    return GroupSpec(n_bins, order_k, x_min, x_max, flux_mode,
+                     COAG_MAXWELL, (0.5, 0.1), FRAG_MAXWELL, (0.5, 1.0),
+                     BREAK_POWERLAW_REMNANT, (alpha,), 0, 0)
+
+
+def random_coefficients(spec: GroupSpec, n_cells: int, seed: int = 7, rel_modes: float = 0.3,
+                        dynamic_range: float = 3.0) -> np.ndarray:
+    """Random modal coefficients: positive bin means spanning ``dynamic_range``
+    decades per cell, higher modes a uniform fraction of the mean."""
+    rng = np.random.default_rng(seed)
+    N, k = spec.n_bins, spec.order_k
+    g = np.zeros((n_cells, N, k + 1))
+    g[:, :, 0] = 10.0 ** rng.uniform(-dynamic_range, 0.0, (n_cells, N))
+    if k >= 1:
+        g[:, :, 1:] = g[:, :, :1] * rng.uniform(-rel_modes, rel_modes, (n_cells, N, k)) / np.arange(1, k + 1)
+    return g.reshape(n_cells, N * (k + 1))

@@ -1,0 +1,196 @@
+"""Pins for the oracle's flux evaluation (Sec. 3.3, App. B) against exact
+polynomial integrals, brute-force adaptive quadrature and identities."""
+import warnings
+
+import numpy as np
+import pytest
+from numpy.polynomial import Polynomial as Poly
+from numpy.polynomial import legendre as npl
+from scipy import integrate
+
+import oracle
+from paper_2607_13740_b300 import workloads as W
+from analytic import dg_eval
+
+
+def _project_poly(o, coeffs):
+    """Coefficients of the global polynomial sum_p c_p x^p (projection is exact for p <= k)."""
+    g = np.zeros(o.P)
+    for p, c in enumerate(coeffs):
+        g += o.project(W.IC_POWERLAW, [c, float(p), 0.0, 1e300])[0]
+    return g
+
+
+def _exact_uv_flux(spec, coeffs, x):
+    """F(x) of eq. (Fcoagtrun) for K = uv and a global polynomial g, integrated exactly:
+    F = int_{x_min}^x u g(u) [G(v_max(u)) - G(x - u + x_min)] du with G' = g."""
+    g = Poly(coeffs)
+    G = g.integ()
+    u = Poly([0.0, 1.0])
+    lo = Poly([x + spec.x_min, -1.0])
+    hi = Poly([spec.x_max + spec.x_min, -1.0]) if spec.flux_mode == 0 else Poly([spec.x_max])
+    outer = (u * g * (G(hi) - G(lo))).integ()
+    return outer(x) - outer(spec.x_min)
+
+
+@pytest.mark.parametrize("k,coeffs", [(2, [0.7, 1.3]), (3, [0.5, 0.8, 0.4])])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_uv_kernel_flux_is_exact(k, coeffs, mode):
+    """With K = uv the integrand u g(u) g(v) is a polynomial of degree <= 2Q - 1 in each
+    variable when g is a global polynomial of degree <= k - 1, so the nested Q = k+1 rule
+    (partial bins A, B and, inside a bin, the partial outer piece) is exact."""
+    spec = W.GroupSpec(5, k, 1e-1, 1e2, mode, W.COAG_MULT, (1.0,))
+    o = oracle.Oracle(spec)
+    e = o.edges()
+    g = _project_poly(o, coeffs)
+    xs = np.concatenate([e[1:-1], [0.37, 2.2, 45.0, 99.0]])
+    F, _ = o.flux_point(g, xs, 1)
+    ex = np.array([_exact_uv_flux(spec, coeffs, x) for x in xs])
+    np.testing.assert_allclose(F, ex, rtol=1e-13)
+    # the same exactness through the fragmentation path with b = delta(w - u - v)
+    fspec = spec.replace(coag_kind=W.COAG_NONE, coag_p=(), frag_kind=W.FRAG_MULT, frag_p=(1.0,),
+                         break_kind=W.BREAK_COAG_DELTA)
+    Ff, _ = oracle.Oracle(fspec).flux_point(g, xs, 2)
+    np.testing.assert_allclose(Ff, ex, rtol=1e-13)
+
+
+def _brute_coag(spec, coef, x, kern):
+    e = oracle.Oracle(spec).edges()
+    xmin, xmax, k = spec.x_min, spec.x_max, spec.order_k
+    g = lambda y: dg_eval(coef, e, k, np.array([y]))[0]
+
+    def inner(u):
+        lo = x - u + xmin
+        hi = xmax - u + xmin if spec.flux_mode == 0 else xmax
+        if hi <= lo:
+            return 0.0
+        pts = [p for p in e if lo < p < hi]
+        return integrate.quad(lambda v: kern(u, v) * g(v) / v, lo, hi, points=pts or None,
+                              limit=200, epsabs=0, epsrel=1e-12)[0]
+
+    # the inner lower limit crosses a bin edge at u = x + x_min - edge (a kink in u)
+    pts = [p for p in e if xmin < p < x] + [x + xmin - p for p in e if xmin < x + xmin - p < x]
+    if spec.flux_mode == 0:
+        pts += [xmax + xmin - p for p in e if xmin < xmax + xmin - p < x]
+    return integrate.quad(lambda u: g(u) * inner(u), xmin, x, points=sorted(set(pts)) or None,
+                          limit=400, epsabs=0, epsrel=1e-11)[0]
+
+
+def test_additive_flux_converges_to_adaptive_quadrature():
+    """eq. (Fcoagtrun) with K = x + y: the nested Gauss rule converges to an
+    adaptive double integral (breakpoints at edges and kinks) as Q grows."""
+    spec = W.GroupSpec(4, 1, 1e-2, 1e2, 0, W.COAG_ADD, (1.0,))
+    coef = W.random_coefficients(spec, 1, seed=5, dynamic_range=1.0)[0]
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        for x in (0.3, 7.0):
+            ex = _brute_coag(spec, coef, x, lambda u, v: u + v)
+            err = []
+            for Q in (2, 24):
+                F, _ = oracle.Oracle(spec.replace(quad_q=Q)).flux_point(coef, [x], 1)
+                err.append(abs(F[0] - ex) / abs(ex))
+            assert err[0] < 5e-2
+            assert err[1] < 5e-5 and err[1] < err[0] / 100
+
+
+def test_pure_fragmentation_flux_converges_to_adaptive_quadrature():
+    """eq. (Ffragtrun) with K_frag = xy and uniform binary breakage: positive
+    minus negative flux against a brute-force nested quadrature."""
+    spec = W.pure_fragmentation_spec(4, 1, 1e-2, 1e2)
+    o = oracle.Oracle(spec)
+    e = o.edges()
+    xmin, xmax, k = spec.x_min, spec.x_max, spec.order_k
+    coef = W.random_coefficients(spec, 1, seed=6, dynamic_range=1.0)[0]
+    g = lambda y: dg_eval(coef, e, k, np.array([y]))[0]
+    x = 0.3
+
+    def above(u, v):  # Sec. 4.4: (y^2 - x^2)/y for each fragmenting particle y > x
+        return ((u * u - x * x) / u if u > x else 0.0) + ((v * v - x * x) / v if v > x else 0.0)
+
+    def below(u, v):
+        return (min(x, u) ** 2 - xmin ** 2) / u + (min(x, v) ** 2 - xmin ** 2) / v
+
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        vmax = lambda u: xmax if spec.flux_mode else xmax - u + xmin
+        pos = integrate.quad(lambda u: g(u) * integrate.quad(
+            lambda v: u * v * g(v) * above(u, v) / (v * (u + v)), x - u + xmin, vmax(u),
+            points=[p for p in list(e) + [x] if x - u + xmin < p < vmax(u)] or None, limit=300,
+            epsrel=1e-10)[0], xmin, x,
+            points=sorted(set([p for p in e if xmin < p < x] + [x + xmin - p for p in e if xmin < x + xmin - p < x])) or None,
+            limit=300, epsrel=1e-9)[0]
+        neg = integrate.quad(lambda u: g(u) * integrate.quad(
+            lambda v: u * v * g(v) * below(u, v) / (v * (u + v)), xmin, vmax(u),
+            points=[p for p in list(e) + [x] if xmin < p < vmax(u)] or None, limit=300, epsrel=1e-10)[0],
+            x, xmax, points=[p for p in e if x < p < xmax] or None, limit=300, epsrel=1e-9)[0]
+    ex = pos - neg
+    err = []
+    for Q in (2, 24):
+        F, _ = oracle.Oracle(spec.replace(quad_q=Q)).flux_point(coef, [x], 2)
+        err.append(abs(F[0] - ex) / abs(ex))
+    assert err[0] < 5e-2
+    assert err[1] < 1e-3 and err[1] < err[0] / 20
+
+
+@pytest.mark.parametrize("spec", [
+    W.additive_spec(6, 2, 1e-2, 1e3),
+    W.pure_fragmentation_spec(6, 2, 1e-2, 1e3, flux_mode=0),
+    W.coupled_toy_spec(6, 2, flux_mode=0, x_min=1e-2, x_max=1e3),
+], ids=["coag", "frag", "toy"])
+def test_boundary_fluxes_vanish(spec):
+    """Sec. 3.3: F(x_min) = 0 in both modes; F(x_max) = 0 for the conservative fluxes.
+    With Delta x = 0 the flux through x_max is non-zero when coagulation is present
+    (pure uniform binary breakage never makes products heavier than a collider)."""
+    o = oracle.Oracle(spec)
+    g = W.random_coefficients(spec, 1, seed=9)[0]
+    F, Fa = o.flux_point(g, [spec.x_min, spec.x_max], 3)
+    assert F[0] == 0.0 and F[1] == 0.0
+    Fi, _ = o.flux_point(g, [np.sqrt(spec.x_min * spec.x_max)], 3)
+    assert Fi[0] != 0.0
+    ospec = spec.replace(flux_mode=1)
+    F2, _ = oracle.Oracle(ospec).flux_point(g, [spec.x_min, spec.x_max], 3)
+    assert F2[0] == 0.0
+    assert (F2[1] != 0.0) == (spec.coag_kind != W.COAG_NONE)
+
+
+def test_delta_breakage_equals_coagulation_rhs():
+    """eq. (Ffrag) with b = delta(w - (u + v)) is the coagulation flux (end of Sec. 2.2);
+    the whole L[g] through the fragmentation path equals the coagulation one."""
+    cspec = W.GroupSpec(8, 2, 1e-3, 1e3, 0, W.COAG_MULT, (0.5,))
+    fspec = cspec.replace(coag_kind=W.COAG_NONE, coag_p=(), frag_kind=W.FRAG_MULT, frag_p=(0.5,),
+                          break_kind=W.BREAK_COAG_DELTA)
+    g = W.random_coefficients(cspec, 3, seed=11)
+    Lc, Sc = oracle.Oracle(cspec).rhs(g)
+    Lf, _ = oracle.Oracle(fspec).rhs(g)
+    assert np.all(np.abs(Lc - Lf) <= 1e-14 * Sc)
+
+
+def test_appB_volume_term_converges_to_pointwise_flux_integral():
+    """App. B reordering: sum over (u, v) of the five sub-interval integrals equals
+    int_{I_j} F_frag(x) d_x phi_i dx computed from the pointwise flux; both converge
+    to the same value as the Gauss order grows (R7, R8)."""
+    spec0 = W.coupled_toy_spec(3, 2, flux_mode=0, x_min=1e-2, x_max=1e2)
+    coef = W.random_coefficients(spec0, 1, seed=8, dynamic_range=1.0)[0]
+    s8, w8 = npl.leggauss(8)
+    diffs = {}
+    for Q in (3, 24):
+        o = oracle.Oracle(spec0.replace(quad_q=Q))
+        e = o.edges()
+        for j in range(3):
+            V, Va = o.vol_frag(coef, j)
+            h = e[j + 1] - e[j]
+            acc = np.zeros(3)
+            for p in range(64):
+                a, b = e[j] + h * p / 64, e[j] + h * (p + 1) / 64
+                xs = 0.5 * (a + b) + 0.5 * (b - a) * s8
+                F, _ = o.flux_point(coef, xs, 2)
+                xi = 2 * (xs - 0.5 * (e[j] + e[j + 1])) / h
+                for i in (1, 2):
+                    c = np.zeros(i + 1)
+                    c[i] = 1
+                    acc[i] += np.sum(0.5 * (b - a) * w8 * F * (2 / h) * npl.legval(xi, npl.legder(c)))
+            diffs[(Q, j)] = np.max(np.abs(V[1:] - acc[1:]) / Va[1:])
+            assert V[0] == 0.0
+    for j in range(3):
+        assert diffs[(24, j)] < 5e-3
+        assert diffs[(24, j)] < diffs[(3, j)] / 5

@@ -1,0 +1,390 @@
+"""Benchmark: DG coagulation RHS throughput in cell-steps/s on the batched additive-kernel workload.
+
+Workload: 65,536 independent cells, K = x + y, N = 40 logarithmic bins on
+[1e-6, 1e10], k = 2 (P = 120 coefficients per cell), conservative fluxes,
+per-cell g0 = A x exp(-x/x0) with A ~ lognormal(0, 0.5), x0 ~ loguniform[1e-3, 1],
+dt = 0.02 / (A x0^2).  One "step" is one SSP-RK3 step of the whole batch:
+reconstruction (limiter), three flux contractions and three fused
+flux-difference / RK-stage updates.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32|bf16x3]
+                [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference implementation
+of this method available) on a bounded sample of the same workload.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DG RHS cell-steps/s (N=40,k=2) vs plain FP64 GPU; roofline frac; err vs FP64"
+UNIT = "cell-steps/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+# nominal dense rates of this part (TF32 relative to BF16; FP64 on CUDA cores)
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            flat = {}
+
+            def walk(x, prefix=""):
+                if isinstance(x, dict):
+                    for k, v in x.items():
+                        walk(v, f"{prefix}{k}.")
+                elif isinstance(x, (int, float)):
+                    flat[prefix[:-1]] = float(x)
+            walk(d)
+
+            def pick(*names):
+                for n in names:
+                    for k, v in flat.items():
+                        if k.split(".")[-1] == n:
+                            return v
+                return None
+            peaks = {"hbm_gbs": pick("hbm_gbs"), "bf16_tflops": pick("bf16_tflops"),
+                     "bf16_tflops_sustained": pick("bf16_tflops_sustained")}
+            if all(v is not None for v in peaks.values()):
+                peaks["source"] = "measured"
+                return peaks
+        except Exception:
+            pass
+    p = dict(FALLBACK_PEAKS)
+    p["source"] = "fallback"
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, n_steps_per_sample=1, target_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload's cells."""
+    import oracle
+    o = oracle.Oracle(wl.spec)
+    threads = oracle.max_threads()
+    g0 = o.project(wl.ic_kind, wl.ic_params[:threads])
+    t = time.perf_counter()
+    o.step(g0, wl.dt[:threads], n_steps_per_sample, threads=threads)
+    per = (time.perf_counter() - t)
+    n = int(max(threads, min(4096, threads * max(1, target_s / max(per, 1e-6)))))
+    n = min(n, wl.n_cells)
+    g0 = o.project(wl.ic_kind, wl.ic_params[:n])
+    t = time.perf_counter()
+    o.step(g0, wl.dt[:n], n_steps_per_sample, threads=threads)
+    el = time.perf_counter() - t
+    return {"value": n * n_steps_per_sample / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} cells of the 65,536-cell batch x {n_steps_per_sample} SSP-RK3 step(s), "
+                      f"FP64 C oracle with OpenMP, {el:.1f} s"}
+
+
+def run_reference(args, rank):
+    """--impl reference: the oracle timed as it stands on bounded samples of the workload."""
+    from paper_2607_13740_b300 import workloads as W
+    if rank != 0:
+        return
+    import oracle
+    wl = W.batched_additive(n_cells=args.cells)
+    o = oracle.Oracle(wl.spec)
+    threads = oracle.max_threads()
+    n = max(threads, 2 * threads)
+    g0 = o.project(wl.ic_kind, wl.ic_params[:n])
+    times = []
+    for s in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        g0, _, _ = o.step(g0, wl.dt[:n], 1, threads=threads)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    el = sum(times)
+    value = n * len(times) / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "cells_per_step_sample": n, "n_bins": 40, "order_k": 2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} of the 65,536 cells per step, FP64 C oracle with OpenMP"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3"])
+    ap.add_argument("--cells", type=int, default=65536)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if args.steps is None:
+            args.steps = 3
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2607_13740_b300 import grace, workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl = W.batched_additive(n_cells=args.cells)
+    n = wl.n_cells
+    candidates = [grace.FP64, grace.TF32, grace.BF16X3]
+    ctx = None
+    for forms in (candidates, [grace.FP64]):
+        try:
+            ctx = grace.Context([wl.spec], local, precisions=forms)
+            break
+        except grace.GraceError:
+            ctx = None
+    forms = list(ctx.precisions)
+    head = grace.PRECISIONS[args.precision] if args.precision else forms[-1]
+    if head not in forms:
+        raise SystemExit(f"precision {args.precision} is not available in this build")
+    if args.steps is None:
+        args.steps = 3 if head == grace.FP64 else 50
+    b = ctx.batch(n)
+    g0 = b.project(wl.ic_kind, wl.ic_params)
+    dt = torch.as_tensor(wl.dt, device=dev)
+    nnz, _ = ctx.stats(0, grace.FP64)
+    peaks = load_peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    names = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}
+
+    def timed(form, steps, warmup, clocks=False):
+        g = g0.clone()
+        for _ in range(warmup):
+            b.step(g, dt, 1, form)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ctx.profile(True)
+        ctx.profile_read(0)
+        ctx.profile_read(1)
+        evs = []
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        torch.cuda.synchronize()
+        for s in range(steps):
+            flush.fill_(float(s))            # evict L2 between timed steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.step(g, dt, 1, form)
+            e1.record()
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        ms = sum(a.elapsed_time(c) for a, c in evs)
+        c_ms, c_n = ctx.profile_read(0)
+        u_ms, u_n = ctx.profile_read(1)
+        ctx.profile(False)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.barrier()
+        return {"ms": float(t.item()), "contract_ms": c_ms, "contract_launches": c_n, "update_ms": u_ms,
+                "update_launches": u_n, "g": g, "clocks": sampler.summary() if sampler else None}
+
+    # accuracy of each form against the FP64 GPU path over the same steps
+    err_steps = 3
+    ref = g0.clone()
+    b.step(ref, dt, err_steps, grace.FP64)
+    m0 = b.mass(g0)
+    edges = torch.as_tensor(np.array([wl.spec.x_min * (wl.spec.x_max / wl.spec.x_min) ** (j / 40)
+                                      for j in range(41)]), device=dev)
+    h = (edges[1:] - edges[:-1])
+
+    forms_out = {}
+    for form in forms:
+        steps = args.steps if form == head else min(args.steps, 3 if form == grace.FP64 else 20)
+        r = timed(form, steps, args.warmup if form == head else 1, clocks=(form == head))
+        cell_steps = n * world * steps / (r["ms"] / 1e3)
+        passes = 3 if form == grace.BF16X3 else 1
+        alg_flop = 2.0 * nnz * n * passes           # per contraction launch
+        avg = r["contract_ms"] / max(1, r["contract_launches"])
+        achieved = alg_flop / (avg / 1e3) / 1e12      # TFLOP/s
+        if form == grace.FP64:
+            peak, bound, psrc = NOMINAL_FP64_TFLOPS, "alu", "nominal FP64 rate of the part (1.25 TFLOP/s)"
+        elif form == grace.TF32:
+            peak = peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16
+            bound, psrc = "tensor", f"{peaks['source']} sustained bf16 x nominal tf32/bf16 ratio"
+        else:
+            peak, bound, psrc = peaks["bf16_tflops_sustained"], "tensor", f"{peaks['source']} sustained bf16"
+        g = g0.clone()
+        b.step(g, dt, err_steps, form)
+        d = (g - ref).abs().reshape(n, 40, 3)
+        l1 = ((h[None, :] * d.sum(dim=2)).sum(dim=1) / m0.abs()).max().item()
+        mx = (d.amax(dim=(1, 2)) / ref.reshape(n, 40, 3).abs().amax(dim=(1, 2))).max().item()
+        mass = b.mass(g)
+        drift = ((mass - m0).abs() / m0.abs()).max().item()
+        forms_out[names[form]] = {
+            "cell_steps_per_s": cell_steps, "ms_per_step": r["ms"] / steps, "steps": steps,
+            "contract_ms_avg": avg, "contract_launches": r["contract_launches"],
+            "update_ms_avg": r["update_ms"] / max(1, r["update_launches"]),
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": psrc},
+            "l1_err_vs_fp64_over_M1": l1, "max_rel_err_vs_fp64": mx, "mass_drift": drift,
+            "err_steps": err_steps, "_r": r}
+
+    hd = forms_out[names[head]]
+    r = hd.pop("_r")
+    for f in forms_out.values():
+        f.pop("_r", None)
+    fp64_rate = forms_out["fp64"]["cell_steps_per_s"]
+    for f in forms_out.values():
+        f["speedup_vs_fp64_gpu"] = f["cell_steps_per_s"] / fp64_rate
+
+    # end to end through the public API: pinned host state in, one step, state out
+    e2e = None
+    try:
+        host_in = g0.cpu().pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        gdev = torch.empty_like(g0)
+        e2e_steps = max(3, min(args.steps, 20))
+        for _ in range(2):
+            gdev.copy_(host_in, non_blocking=True)
+            b.step(gdev, dt, 1, head)
+            host_out.copy_(gdev, non_blocking=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(e2e_steps):
+            gdev.copy_(host_in, non_blocking=True)
+            b.step(gdev, dt, 1, head)
+            host_out.copy_(gdev, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        t = torch.tensor([ems], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        nbytes = host_in.numel() * 8
+        e2e = {"value": n * world * e2e_steps / (float(t.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+    except Exception as exc:  # pinned memory may be unavailable
+        e2e = {"value": None, "unit": UNIT, "error": str(exc)[:200]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    launches_per_step = 1 + 3 + 3
+    line = {
+        "metric": METRIC, "value": hd["cell_steps_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": hd["steps"], "warmup": args.warmup, "ms_per_step": hd["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {grace.FP64: "f64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[head],
+        "data": "synthetic",
+        "config": {"workload": wl.name, "cells_per_gpu": n, "n_bins": 40, "order_k": 2,
+                   "coef_per_cell": wl.spec.n_coef, "kernel": "additive K=x+y", "flux": "conservative",
+                   "x_range": [wl.spec.x_min, wl.spec.x_max], "precision": names[head],
+                   "l2": "256 MB buffer written between timed steps (outside the timed events)",
+                   "parallelism": f"dp{world} (independent cells, no collective on the data path)"},
+        "roofline": {"bound": hd["roofline"]["bound"], "achieved": hd["roofline"]["achieved"],
+                     "peak": hd["roofline"]["peak"], "unit": "TFLOP/s", "frac": hd["roofline"]["frac"],
+                     "traffic": None, "kernel": "flux contraction",
+                     "algorithmic": f"2 x {nnz} non-zeros of T per cell and RHS x {n} cells"
+                                    + (" x 3 bf16 passes" if head == grace.BF16X3 else ""),
+                     "peak_source": hd["roofline"]["peak_source"]},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * hd["steps"],
+        "clocks": r["clocks"],
+        "forms": forms_out,
+        "peaks": peaks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * grace.h - C ABI of the B300-native GRACE-DG hot path.
+ *
+ * The library evaluates the right-hand side L[g] of the DG-discretised
+ * Smoluchowski equation (coagulation flux plus the conservative nonlinear
+ * fragmentation flux) for the Legendre modal coefficients of every
+ * logarithmic mass bin, over a batch of independent cells, and advances the
+ * batch with SSP-RK3.  The method is that of Yang, Chen & Bai,
+ * "GRACE-DG: A Discontinuous Galerkin Method-Based Code for General
+ * Nonlinear Coagulation-Fragmentation Equations" (arXiv 2607.13740).
+ *
+ * Conventions for every function below:
+ *   - Pointers marked "device" must point to CUDA device memory of the
+ *     context's device; "host" pointers to ordinary host memory.  The caller
+ *     owns every buffer it passes; the library owns its context, batch and
+ *     workspaces and frees them in grace_batch_destroy / grace_destroy.
+ *   - Coefficient arrays are FP64, packed cell after cell; a cell of a group
+ *     with N bins and degree k holds P = N (k+1) doubles ordered bin-major,
+ *     coefficient index fastest: g[c*P + j*(k+1) + i] = g_j^i of cell c.
+ *     Pointers must be 16-byte aligned.
+ *   - Compute calls (grace_project, grace_rhs, grace_step, grace_mass,
+ *     grace_limit, grace_rhs_jvp, grace_rhs_vjp) are asynchronous on the
+ *     stream bound with grace_set_stream (the legacy default stream if none)
+ *     and do not synchronise.  grace_setup, grace_precompute and
+ *     grace_bind_batch allocate and synchronise.
+ *   - No exception or abort crosses this interface.  Every function returns a
+ *     grace_status; grace_last_error() gives a human-readable detail for the
+ *     calling thread.  CUDA errors map to GRACE_ERR_CUDA.
+ *   - One context per host thread at a time.
+ */
+#ifndef GRACE_H
+#define GRACE_H
+
+#if defined(__GNUC__)
+#define GRACE_API __attribute__((visibility("default")))
+#else
+#define GRACE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grace_ctx grace_ctx;
+typedef struct grace_batch grace_batch;
+
+typedef enum {
+    GRACE_OK = 0,
+    GRACE_ERR_ARG = 1,          /* invalid argument (null pointer, size, kind)        */
+    GRACE_ERR_ORDER = 2,        /* call sequence violated (e.g. rhs before precompute) */
+    GRACE_ERR_CUDA = 3,         /* a CUDA runtime call failed                          */
+    GRACE_ERR_NOMEM = 4,        /* device or host allocation failed                    */
+    GRACE_ERR_UNSUPPORTED = 5,  /* valid request the build does not implement          */
+    GRACE_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up                  */
+} grace_status;
+
+/* arithmetic of the bulk flux contraction (Sec. 3.3 quadrature, folded into a
+   coefficient tensor); everything else always runs in FP64 */
+typedef enum {
+    GRACE_FP64 = 0,    /* FP64 CUDA-core contraction                                */
+    GRACE_TF32 = 1,    /* tcgen05 kind::tf32, FP32 accumulation in tensor memory     */
+    GRACE_BF16X3 = 2   /* tcgen05 kind::f16 with bf16 hi+lo splits of both operands, */
+                       /* three products hi*hi + hi*lo + lo*hi, FP32 accumulation    */
+} grace_precision;
+
+/* collision kernels: K = p0 (Sec. 4.2), p0 (x+y) (Sec. 4.3), p0 x y (Sec. 4.4);
+   Maxwellian sigma * dv_rms * beta (Sec. 4.5: p0 = dv_rms, p1 = v_b for
+   coagulation or v_f for fragmentation); ballistic-turbulent (library model,
+   p0 rho_s, p1 Sigma_g, p2 c_s, p3 alpha_turb, p4 v_frag, p5 ramp half-width
+   fraction, p6 rate scale) */
+enum { GRACE_COAG_NONE = 0, GRACE_COAG_CONST = 1, GRACE_COAG_ADD = 2, GRACE_COAG_MULT = 3,
+       GRACE_COAG_MAXWELL = 4, GRACE_COAG_BALLISTIC = 5 };
+enum { GRACE_FRAG_NONE = 0, GRACE_FRAG_MULT = 1, GRACE_FRAG_MAXWELL = 2, GRACE_FRAG_BALLISTIC = 3 };
+/* breakage: uniform binary (Sec. 4.4), power law + remnant (eq. break with
+   m_frag of eq. mfrag; break_p[0] = power-law index alpha), and the delta
+   b = delta(w - u - v) that turns eq. (Ffrag) into coagulation */
+enum { GRACE_BREAK_UNIFORM_BINARY = 0, GRACE_BREAK_POWERLAW_REMNANT = 1, GRACE_BREAK_COAG_DELTA = 2 };
+/* initial conditions for grace_project (per-cell parameters q[0..3]):
+   EXP g0 = q0 x exp(-x/q1); POWERLAW g0 = q0 x^q1 on [q2, q3]; FIRST_BIN g0 = q0 in bin 0 */
+enum { GRACE_IC_EXP = 0, GRACE_IC_POWERLAW = 1, GRACE_IC_FIRST_BIN = 2 };
+/* flux truncation of Sec. 3.3: Delta x = -u + x_min (mass conserving) or 0 */
+enum { GRACE_FLUX_CONSERVATIVE = 0, GRACE_FLUX_NONCONSERVATIVE = 1 };
+/* per-cell status bits written by grace_step / grace_limit */
+enum { GRACE_FLAG_NEGATIVE_MEAN = 1,  /* a cell mean g_j^0 went negative (eq. dt violated) */
+       GRACE_FLAG_LIMITED = 2,        /* the scaling limiter changed a bin (eq. gamma < 1)  */
+       GRACE_FLAG_NONFINITE = 4 };    /* a coefficient became Inf or NaN                    */
+
+/* One (grid, order, physics) combination shared by the cells of a group. */
+typedef struct {
+    int n_bins;       /* N >= 2: logarithmic bins on [x_min, x_max] (Sec. 3.1)          */
+    int order_k;      /* k in 0..3: Legendre degree (eq. 2.3)                            */
+    int quad_q;       /* Gauss points per quadrature piece; 0 means k+1 (Sec. 3.3), <= 16 */
+    int flux_mode;    /* GRACE_FLUX_*                                                   */
+    int coag_kind;    /* GRACE_COAG_*                                                   */
+    int frag_kind;    /* GRACE_FRAG_*                                                   */
+    int break_kind;   /* GRACE_BREAK_*                                                  */
+    int cutoff_mode;  /* 0: power law up to m_frag (eq. break); 1: up to max(u, v)       */
+    int limiter;      /* 1: scaling limiter once per step before the RK stages; 0: off  */
+    int mfrag_mode;   /* 0: m_frag from eq. (mfrag); 1: destructive, m_frag = u + v      */
+    double x_min, x_max;
+    double coag_p[8];
+    double frag_p[8];
+    double break_p[8];
+} grace_group_desc;
+
+GRACE_API int grace_version(void);
+GRACE_API const char *grace_status_string(grace_status s);
+/* detail of the last failing call on this thread ("" if none); valid until the next call */
+GRACE_API const char *grace_last_error(void);
+
+/* Creates a context on CUDA device `device` for n_groups >= 1 group
+   descriptions (host array, copied).  Validates every description. */
+GRACE_API grace_status grace_setup(grace_ctx **ctx, int n_groups, const grace_group_desc *groups, int device);
+
+/* Binds the CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+   used by every later compute call of this context and its batches; NULL = legacy stream. */
+GRACE_API grace_status grace_set_stream(grace_ctx *ctx, void *cuda_stream);
+
+/* Builds, on the GPU in FP64, the coefficient tensors of every group: for each
+   flux functional r (the interface fluxes F(x_{j+1/2}) of eqs. Fcoagtrun /
+   Ffragtrun, and the volume integrals int_{I_j} F d_x phi_i of eq. evo, by the
+   nested Gauss quadrature of Sec. 3.3 and the reordered App. B form for
+   breakage with a Dirac remnant) the P x P matrix T_r with
+   functional_r = sum_{p,q} T_r[p,q] g_p g_q.  precision_mask bit (1<<GRACE_TF32)
+   and (1<<GRACE_BF16X3) also build the tensor-core operand tiles.  Synchronises. */
+GRACE_API grace_status grace_precompute(grace_ctx *ctx, unsigned precision_mask);
+
+/* Number of coefficients P and of flux functionals R of a group. */
+GRACE_API grace_status grace_group_info(const grace_ctx *ctx, int group, int *n_coef, int *n_functionals);
+
+/* Binds a batch of n_cells >= 1 cells; cell_group (host, may be NULL = all in
+   group 0) gives each cell's group.  Allocates the batch workspaces.  The cell
+   layout is packed in the given order; grace_batch_offsets returns it. */
+GRACE_API grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group, grace_batch **batch);
+/* host out[n_cells + 1]: offset (in doubles) of every cell's coefficients; out[n_cells] = total */
+GRACE_API grace_status grace_batch_offsets(const grace_batch *batch, long long *out);
+
+/* Projects per-cell initial conditions (eq. init, 16-point Gauss rule per bin).
+   ic_params: device [n_cells][4] doubles; g: device output. */
+GRACE_API grace_status grace_project(grace_batch *batch, int ic_kind, const double *ic_params, double *g);
+
+/* L = L[g] (eq. evo) for every cell.  g, L: device, packed layout (L has g's layout). */
+GRACE_API grace_status grace_rhs(grace_batch *batch, const double *g, double *L, int precision);
+
+/* n_steps SSP-RK3 steps (eq. RK3), each preceded by the scaling limiter
+   (eqs. recon, gamma) when the group enables it, in place on g (device).
+   dt: device [n_cells] per-cell time steps.  mass (device [n_cells] or NULL)
+   receives M_1 = sum_j h_j g_j^0 after the last step; flags (device
+   [n_cells] or NULL) receives the OR of GRACE_FLAG_* bits over all stages. */
+GRACE_API grace_status grace_step(grace_batch *batch, double *g, const double *dt, int n_steps, int precision,
+                        double *mass, unsigned char *flags);
+
+/* M_1 = sum_j h_j g_j^0 per cell (Sec. 4.1).  g, mass: device. */
+GRACE_API grace_status grace_mass(grace_batch *batch, const double *g, double *mass);
+
+/* The scaling limiter alone, in place; flags (device [n_cells] or NULL). */
+GRACE_API grace_status grace_limit(grace_batch *batch, double *g, unsigned char *flags);
+
+/* Launch timing with CUDA events recorded on the bound stream around every
+   contraction (kernel 0) and flux-update (kernel 1) launch of this context.
+   grace_profile_read synchronises the stream, returns the summed device time
+   in milliseconds and the launch count since the last read, and resets them. */
+GRACE_API grace_status grace_profile_enable(grace_ctx *ctx, int enable);
+GRACE_API grace_status grace_profile_read(grace_ctx *ctx, int kernel, double *total_ms, long long *launches);
+
+/* Structural statistics of a group's coefficient tensors: the number of
+   non-zero entries of all T_r (the algorithmic multiply-adds of one cell's
+   RHS) and the multiply-adds the tensor-core tiles of `precision` execute
+   per cell and RHS (0 if not built). */
+GRACE_API grace_status grace_group_stats(const grace_ctx *ctx, int group, int precision, long long *nnz,
+                                         long long *tile_macs);
+
+GRACE_API void grace_batch_destroy(grace_batch *batch);
+GRACE_API void grace_destroy(grace_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRACE_H */

@@ -1,0 +1,79 @@
+// Plain FP64 contraction on CUDA cores:  F[c, r] = sum_p g_c[p] sum_q T_r[p, q] g_c[q].
+//
+// One warp owns 32 cells; their coefficients sit in shared memory transposed
+// ([q][lane], conflict-free), and the warp walks every non-empty row (r, p) of
+// T once, reading each T entry as a warp-wide broadcast.  Warps of a block walk
+// T in the same order, so T is served from L1.  The kernel is bound by the
+// FP64 FMA rate, which on this part is a small fraction of the FP32 rate.
+#include "grace_internal.h"
+
+namespace grace {
+
+namespace {
+
+__global__ void __launch_bounds__(128) contract_fp64_kernel(
+    const double *__restrict__ T, const int *__restrict__ qlo, const int *__restrict__ qhi,
+    const int *__restrict__ prange, int R, int P, const double *__restrict__ g, int n_cells,
+    double *__restrict__ F)
+{
+    extern __shared__ double gsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const long long cell0 = ((long long)blockIdx.x * nwarps + warp) * 32;
+    double *gw = gsm + (size_t)warp * P * 32;
+
+    // coalesced load of 32 consecutive cells, stored transposed
+    for (int idx = lane; idx < 32 * P; idx += 32) {
+        const int c = idx / P, q = idx - c * P;
+        const long long cell = cell0 + c;
+        gw[q * 32 + c] = cell < n_cells ? g[cell * P + q] : 0.0;
+    }
+    __syncwarp();
+
+    const long long cell = cell0 + lane;
+    for (int r = 0; r < R; ++r) {
+        const int p0 = prange[2 * r], p1 = prange[2 * r + 1];
+        double Fr = 0.0;
+        for (int p = p0; p < p1; ++p) {
+            const int q0 = qlo[r * P + p], q1 = qhi[r * P + p];
+            if (q0 >= q1) continue;
+            const double *Trow = T + ((size_t)r * P + p) * P;
+            double y0 = 0.0, y1 = 0.0;
+            int q = q0;
+            for (; q + 1 < q1; q += 2) {
+                y0 = fma(__ldg(Trow + q), gw[q * 32 + lane], y0);
+                y1 = fma(__ldg(Trow + q + 1), gw[(q + 1) * 32 + lane], y1);
+            }
+            if (q < q1) y0 = fma(__ldg(Trow + q), gw[q * 32 + lane], y0);
+            Fr = fma(gw[p * 32 + lane], y0 + y1, Fr);
+        }
+        if (cell < n_cells) F[cell * R + r] = Fr;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int *d_qlo, const int *d_qhi,
+                                 const int *d_prange, const double *d_g, int n_cells, double *d_F,
+                                 cudaStream_t st)
+{
+    const size_t per_warp = (size_t)g.P * 32 * sizeof(double);
+    int wpb = (int)((200 * 1024) / per_warp);
+    if (wpb > 4) wpb = 4;
+    if (wpb < 1) return cudaErrorInvalidValue;   // P too large for one warp's tile
+    const size_t smem = per_warp * wpb;
+    static int configured_max = 0;
+    if ((int)smem > configured_max) {
+        cudaError_t e = cudaFuncSetAttribute(contract_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_max = (int)smem;
+    }
+    const int cells_per_block = 32 * wpb;
+    const int blocks = (n_cells + cells_per_block - 1) / cells_per_block;
+    contract_fp64_kernel<<<blocks, 32 * wpb, smem, st>>>(d_T, d_qlo, d_qhi, d_prange, g.R, g.P, d_g, n_cells,
+                                                          d_F);
+    return cudaGetLastError();
+}
+
+}  // namespace grace

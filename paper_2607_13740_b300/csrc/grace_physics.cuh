@@ -1,0 +1,146 @@
+// Device-side physics and basis functions of the GRACE-DG hot path.
+#pragma once
+
+#include "grace_internal.h"
+
+namespace grace {
+
+// Legendre polynomials phi_i (eq. 2.4) and derivatives at xi, i = 0..k
+__device__ __forceinline__ void dev_legendre(int k, double xi, double *P, double *dP)
+{
+    P[0] = 1.0;
+    if (dP) dP[0] = 0.0;
+    if (k >= 1) {
+        P[1] = xi;
+        if (dP) dP[1] = 1.0;
+    }
+    for (int n = 1; n < k; ++n) {
+        double c = 2.0 * n + 1.0;
+        P[n + 1] = (c * xi * P[n] - n * P[n - 1]) / (n + 1.0);
+        if (dP) dP[n + 1] = dP[n - 1] + c * P[n];
+    }
+}
+
+// geometric cross section of Sec. 4.5 in mass units
+__device__ __forceinline__ double dev_sigma(double u, double v)
+{
+    double r = cbrt(u) + cbrt(v);
+    return 3.141592653589793 * r * r;
+}
+
+// ballistic cross section with a turbulent relative velocity and a linear
+// fragmentation ramp (library model for the large disk batches)
+__device__ __forceinline__ void dev_ballistic(const double *p, double u, double v, double *kc, double *kf)
+{
+    const double pi = 3.141592653589793;
+    double rho = p[0], sig = p[1], cs = p[2], alpha = p[3], vf = p[4], wr = p[5];
+    double au = cbrt(3.0 * u / (4.0 * pi * rho));
+    double av = cbrt(3.0 * v / (4.0 * pi * rho));
+    double st = pi * rho * fmax(au, av) / (2.0 * sig);
+    double dv = cs * sqrt(3.0 * alpha * st / (1.0 + st * st));
+    double pf = fmin(fmax((dv - (1.0 - wr) * vf) / (2.0 * wr * vf), 0.0), 1.0);
+    double rate = p[6] * pi * (au + av) * (au + av) * dv;
+    *kc = rate * (1.0 - pf);
+    *kf = rate * pf;
+}
+
+__device__ __forceinline__ double dev_kcoag(const DevGroup &G, double u, double v)
+{
+    switch (G.coag_kind) {
+    case GRACE_COAG_CONST: return G.coag_p[0];
+    case GRACE_COAG_ADD: return G.coag_p[0] * (u + v);
+    case GRACE_COAG_MULT: return G.coag_p[0] * u * v;
+    case GRACE_COAG_MAXWELL: return dev_sigma(u, v) * G.coag_p[0] * G.beta_coag;
+    case GRACE_COAG_BALLISTIC: { double kc, kf; dev_ballistic(G.coag_p, u, v, &kc, &kf); return kc; }
+    default: return 0.0;
+    }
+}
+
+__device__ __forceinline__ double dev_kfrag(const DevGroup &G, double u, double v)
+{
+    switch (G.frag_kind) {
+    case GRACE_FRAG_MULT: return G.frag_p[0] * u * v;
+    case GRACE_FRAG_MAXWELL: return dev_sigma(u, v) * G.frag_p[0] * G.beta_frag;
+    case GRACE_FRAG_BALLISTIC: { double kc, kf; dev_ballistic(G.frag_p, u, v, &kc, &kf); return kf; }
+    default: return 0.0;
+    }
+}
+
+// m_frag / (y + z) of eq. (mfrag) as a function of the mass ratio q >= 1
+__device__ __forceinline__ double dev_mfrag_ratio(double q)
+{
+    const double pi = 3.141592653589793;
+    if (q <= 10.0) return 1.0;
+    if (q <= 12.0) return (6.5 + 4.5 * cos(0.5 * (q - 10.0) * pi)) / (1.0 + q);
+    if (q <= 15.0) return 2.0 / (1.0 + q);
+    if (q <= 50.0) return (1.45 + 0.55 * cos((q - 15.0) / 35.0 * pi)) / (1.0 + q);
+    return 0.9 / (1.0 + q);
+}
+
+struct FragOutcome { double mfrag, mleft, mcut, alpha; };
+
+__device__ __forceinline__ FragOutcome dev_outcome(const DevGroup &G, double u, double v)
+{
+    FragOutcome o;
+    double hi = fmax(u, v), lo = fmin(u, v), tot = u + v;
+    o.alpha = G.break_p[0];
+    o.mfrag = G.mfrag_mode == 1 ? tot : tot * dev_mfrag_ratio(hi / lo);
+    o.mleft = fmax(tot - o.mfrag, 0.0);
+    o.mcut = G.cutoff_mode == 1 ? hi : o.mfrag;
+    return o;
+}
+
+// share of the power-law fragment mass (eq. break, normalised on [x_min, m_cut]) at or below x
+__device__ __forceinline__ double dev_pl_fraction(double x, double xmin, double mcut, double alpha)
+{
+    if (!(mcut > xmin)) return x > xmin ? 1.0 : 0.0;
+    double e = 2.0 + alpha;
+    double f = (pow(x, e) - pow(xmin, e)) / (pow(mcut, e) - pow(xmin, e));
+    return fmin(fmax(f, 0.0), 1.0);
+}
+
+// product mass strictly above x (eq. inte1)
+__device__ __forceinline__ double dev_mass_above(const DevGroup &G, double x, double u, double v)
+{
+    switch (G.break_kind) {
+    case GRACE_BREAK_UNIFORM_BINARY:
+        return (u > x ? (u * u - x * x) / u : 0.0) + (v > x ? (v * v - x * x) / v : 0.0);
+    case GRACE_BREAK_POWERLAW_REMNANT: {
+        FragOutcome o = dev_outcome(G, u, v);
+        double m = o.mfrag * (1.0 - dev_pl_fraction(x, G.x_min, o.mcut, o.alpha));
+        return m + (o.mleft > x ? o.mleft : 0.0);
+    }
+    case GRACE_BREAK_COAG_DELTA:
+        return u + v > x ? u + v : 0.0;
+    default: return 0.0;
+    }
+}
+
+// product mass in [x_min, x] (eq. inte2)
+__device__ __forceinline__ double dev_mass_below(const DevGroup &G, double x, double u, double v)
+{
+    double xm = G.x_min;
+    switch (G.break_kind) {
+    case GRACE_BREAK_UNIFORM_BINARY: {
+        double mu = fmin(x, u), mv = fmin(x, v), m = 0.0;
+        if (mu > xm) m += (mu * mu - xm * xm) / u;
+        if (mv > xm) m += (mv * mv - xm * xm) / v;
+        return m;
+    }
+    case GRACE_BREAK_POWERLAW_REMNANT: {
+        FragOutcome o = dev_outcome(G, u, v);
+        double m = o.mfrag * dev_pl_fraction(x, xm, o.mcut, o.alpha);
+        return m + ((o.mleft >= xm && o.mleft <= x) ? o.mleft : 0.0);
+    }
+    case GRACE_BREAK_COAG_DELTA:
+        return u + v <= x ? u + v : 0.0;
+    default: return 0.0;
+    }
+}
+
+__device__ __forceinline__ double dev_vmax(const DevGroup &G, double u)
+{
+    return G.flux_mode == GRACE_FLUX_CONSERVATIVE ? G.x_max - u + G.x_min : G.x_max;
+}
+
+}  // namespace grace

@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the C ABI in include/grace.h (argument marshalling only).
+
+Device buffers are torch tensors on the context's CUDA device; every compute
+call runs on torch's current stream.  There is no CPU fallback: if the
+library or a CUDA device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgrace.so")
+
+FP64, TF32, BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16x3": BF16X3}
+FLAG_NEGATIVE_MEAN, FLAG_LIMITED, FLAG_NONFINITE = 1, 2, 4
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+class GraceError(RuntimeError):
+    pass
+
+
+class GroupDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_bins", ctypes.c_int), ("order_k", ctypes.c_int), ("quad_q", ctypes.c_int),
+        ("flux_mode", ctypes.c_int), ("coag_kind", ctypes.c_int), ("frag_kind", ctypes.c_int),
+        ("break_kind", ctypes.c_int), ("cutoff_mode", ctypes.c_int), ("limiter", ctypes.c_int),
+        ("mfrag_mode", ctypes.c_int),
+        ("x_min", ctypes.c_double), ("x_max", ctypes.c_double),
+        ("coag_p", ctypes.c_double * 8), ("frag_p", ctypes.c_double * 8),
+        ("break_p", ctypes.c_double * 8),
+    ]
+
+
+def exported_symbols():
+    return ["grace_version", "grace_status_string", "grace_last_error", "grace_setup",
+            "grace_set_stream", "grace_precompute", "grace_group_info", "grace_bind_batch",
+            "grace_batch_offsets", "grace_project", "grace_rhs", "grace_step", "grace_mass",
+            "grace_limit", "grace_profile_enable", "grace_profile_read", "grace_group_stats",
+            "grace_batch_destroy", "grace_destroy"]
+
+
+def load(path: str | None = None):
+    """Loads libgrace.so (built in-tree by paper_2607_13740_b300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise GraceError(f"CUDA library not built: {path} (run paper_2607_13740_b300.build)")
+    L = ctypes.CDLL(path)
+    S = ctypes.c_int
+    L.grace_version.restype = ctypes.c_int
+    L.grace_status_string.argtypes = [S]
+    L.grace_status_string.restype = ctypes.c_char_p
+    L.grace_last_error.restype = ctypes.c_char_p
+    L.grace_setup.argtypes = [ctypes.POINTER(_VP), S, ctypes.POINTER(GroupDesc), S]
+    L.grace_set_stream.argtypes = [_VP, _VP]
+    L.grace_precompute.argtypes = [_VP, ctypes.c_uint]
+    L.grace_group_info.argtypes = [_VP, S, ctypes.POINTER(S), ctypes.POINTER(S)]
+    L.grace_bind_batch.argtypes = [_VP, S, _VP, ctypes.POINTER(_VP)]
+    L.grace_batch_offsets.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong)]
+    L.grace_project.argtypes = [_VP, S, _VP, _VP]
+    L.grace_rhs.argtypes = [_VP, _VP, _VP, S]
+    L.grace_step.argtypes = [_VP, _VP, _VP, S, S, _VP, _VP]
+    L.grace_mass.argtypes = [_VP, _VP, _VP]
+    L.grace_limit.argtypes = [_VP, _VP, _VP]
+    L.grace_profile_enable.argtypes = [_VP, S]
+    L.grace_profile_read.argtypes = [_VP, S, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    L.grace_group_stats.argtypes = [_VP, S, S, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.grace_batch_destroy.argtypes = [_VP]
+    L.grace_destroy.argtypes = [_VP]
+    for name in exported_symbols():
+        if not hasattr(L, name):
+            raise GraceError(f"{path} does not export {name}")
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        L = load()
+        msg = L.grace_status_string(status).decode()
+        detail = L.grace_last_error().decode()
+        raise GraceError(f"{what}: {msg} ({detail})")
+
+
+def group_desc(spec: W.GroupSpec) -> GroupDesc:
+    d = GroupDesc()
+    for f in ("n_bins", "order_k", "quad_q", "flux_mode", "coag_kind", "frag_kind", "break_kind",
+              "cutoff_mode", "limiter", "mfrag_mode", "x_min", "x_max"):
+        setattr(d, f, getattr(spec, f))
+    for name in ("coag_p", "frag_p", "break_p"):
+        arr = getattr(d, name)
+        for i, v in enumerate(getattr(spec, name)):
+            arr[i] = v
+    return d
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """Setup + FP64 precompute (and tensor-core tiles for the requested precisions)."""
+
+    def __init__(self, specs, device: int = 0, precisions=(FP64,)):
+        import torch
+        if not torch.cuda.is_available():
+            raise GraceError("no CUDA device: the GRACE-DG library has no CPU path")
+        L = load()
+        self.specs = list(specs) if isinstance(specs, (list, tuple)) else [specs]
+        self.device = device
+        arr = (GroupDesc * len(self.specs))(*[group_desc(s) for s in self.specs])
+        h = _VP()
+        torch.cuda.set_device(device)
+        _check(L.grace_setup(ctypes.byref(h), len(self.specs), arr, device), "grace_setup")
+        self._h = h
+        self.set_stream()
+        mask = 0
+        for p in precisions:
+            mask |= 1 << int(p)
+        _check(L.grace_precompute(h, mask), "grace_precompute")
+        self.precisions = tuple(int(p) for p in precisions)
+
+    def set_stream(self):
+        _check(load().grace_set_stream(self._h, _stream_handle()), "grace_set_stream")
+
+    def group_info(self, group: int = 0):
+        P, R = ctypes.c_int(), ctypes.c_int()
+        _check(load().grace_group_info(self._h, group, ctypes.byref(P), ctypes.byref(R)), "grace_group_info")
+        return P.value, R.value
+
+    def profile(self, enable: bool = True):
+        _check(load().grace_profile_enable(self._h, 1 if enable else 0), "grace_profile_enable")
+
+    def profile_read(self, kernel: int):
+        """(total device ms, launches) of kernel 0 (contraction) or 1 (flux update) since the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        _check(load().grace_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(n)), "grace_profile_read")
+        return ms.value, n.value
+
+    def stats(self, group: int = 0, precision: int = FP64):
+        """(non-zeros of the coefficient tensors, executed tile MACs) per cell and RHS."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().grace_group_stats(self._h, group, precision, ctypes.byref(a), ctypes.byref(b)),
+               "grace_group_stats")
+        return a.value, b.value
+
+    def batch(self, n_cells: int, cell_group=None) -> "Batch":
+        return Batch(self, n_cells, cell_group)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().grace_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    def __init__(self, ctx: Context, n_cells: int, cell_group=None):
+        self.ctx = ctx
+        self.n_cells = n_cells
+        h = _VP()
+        cg = None
+        if cell_group is not None:
+            cg_arr = np.ascontiguousarray(cell_group, dtype=np.int32)
+            cg = cg_arr.ctypes.data_as(ctypes.c_void_p)
+        _check(load().grace_bind_batch(ctx._h, n_cells, cg, ctypes.byref(h)), "grace_bind_batch")
+        self._h = h
+        self.P, self.R = ctx.group_info(0)
+
+    def offsets(self):
+        out = (ctypes.c_longlong * (self.n_cells + 1))()
+        _check(load().grace_batch_offsets(self._h, out), "grace_batch_offsets")
+        return np.frombuffer(out, dtype=np.int64).copy()
+
+    def _check_state(self, g):
+        import torch
+        if not (g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()):
+            raise GraceError("coefficient arrays must be contiguous float64 CUDA tensors")
+        if g.numel() != self.n_cells * self.P:
+            raise GraceError(f"expected {self.n_cells * self.P} coefficients, got {g.numel()}")
+
+    def project(self, ic_kind: int, ic_params):
+        import torch
+        ic = torch.as_tensor(np.ascontiguousarray(ic_params, dtype=np.float64)).reshape(self.n_cells, 4)
+        ic = ic.to(f"cuda:{self.ctx.device}")
+        g = torch.empty(self.n_cells, self.P, dtype=torch.float64, device=ic.device)
+        self.ctx.set_stream()
+        _check(load().grace_project(self._h, int(ic_kind), _ptr(ic), _ptr(g)), "grace_project")
+        return g
+
+    def rhs(self, g, precision: int = FP64, out=None):
+        import torch
+        self._check_state(g)
+        L = out if out is not None else torch.empty_like(g)
+        self.ctx.set_stream()
+        _check(load().grace_rhs(self._h, _ptr(g), _ptr(L), int(precision)), "grace_rhs")
+        return L
+
+    def step(self, g, dt, n_steps: int, precision: int = FP64, mass=None, flags=None):
+        """In place on g; dt is a float64 CUDA tensor [n_cells]."""
+        self._check_state(g)
+        self.ctx.set_stream()
+        _check(load().grace_step(self._h, _ptr(g), _ptr(dt), int(n_steps), int(precision),
+                                 _ptr(mass), _ptr(flags)), "grace_step")
+        return g
+
+    def mass(self, g):
+        import torch
+        self._check_state(g)
+        m = torch.empty(self.n_cells, dtype=torch.float64, device=g.device)
+        self.ctx.set_stream()
+        _check(load().grace_mass(self._h, _ptr(g), _ptr(m)), "grace_mass")
+        return m
+
+    def limit(self, g, flags=None):
+        self._check_state(g)
+        self.ctx.set_stream()
+        _check(load().grace_limit(self._h, _ptr(g), _ptr(flags)), "grace_limit")
+        return g
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().grace_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,87 @@
+"""Host-side checks of the C-ABI library: it loads, exports every declared
+symbol, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2607_13740_b300 import build, grace, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "grace.h")).read()
+    return sorted(set(re.findall(r"GRACE_API[^;(]*?\b(grace_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return grace.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 16
+    raw = ctypes.CDLL(grace.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+    assert set(grace.exported_symbols()) <= set(names)
+
+
+def test_version_and_status_strings(lib):
+    assert lib.grace_version() >= 1
+    for s in range(0, 7):
+        assert lib.grace_status_string(s).decode()
+    assert lib.grace_status_string(99).decode() == "unknown status"
+
+
+def _setup(lib, desc, n=1, device=0):
+    h = ctypes.c_void_p()
+    arr = (grace.GroupDesc * n)(*([desc] * n))
+    return lib.grace_setup(ctypes.byref(h), n, arr, device), h
+
+
+@pytest.mark.parametrize("field,value", [
+    ("n_bins", 1), ("order_k", -1), ("quad_q", 17), ("x_min", 0.0), ("x_max", 1e-9),
+    ("flux_mode", 2), ("coag_kind", 9), ("frag_kind", 7), ("break_kind", 5), ("limiter", 3),
+])
+def test_setup_rejects_invalid_groups(lib, field, value):
+    d = grace.group_desc(W.additive_spec(8, 2))
+    setattr(d, field, value)
+    st, h = _setup(lib, d)
+    assert st == 1, lib.grace_last_error()
+    assert not h.value
+    assert lib.grace_last_error().decode()
+
+
+def test_setup_reports_unsupported_order(lib):
+    d = grace.group_desc(W.additive_spec(8, 4))
+    st, _ = _setup(lib, d)
+    assert st == 5
+
+
+def test_setup_rejects_missing_kernels_and_bad_power_law(lib):
+    d = grace.group_desc(W.additive_spec(8, 2).replace(coag_kind=W.COAG_NONE))
+    assert _setup(lib, d)[0] == 1
+    d = grace.group_desc(W.coupled_toy_spec(8, 2).replace(break_p=(-2.0,)))
+    assert _setup(lib, d)[0] == 1
+
+
+def test_null_arguments_are_errors(lib):
+    assert lib.grace_setup(None, 1, None, 0) == 1
+    assert lib.grace_set_stream(None, None) == 1
+    assert lib.grace_precompute(None, 0) == 1
+    assert lib.grace_bind_batch(None, 4, None, None) == 1
+    assert lib.grace_rhs(None, None, None, 0) == 1
+    assert lib.grace_step(None, None, None, 1, 0, None, None) == 1
+    assert lib.grace_mass(None, None, None) == 1
+    lib.grace_batch_destroy(None)
+    lib.grace_destroy(None)
+
+
+def test_negative_device_is_rejected_on_host(lib):
+    d = grace.group_desc(W.additive_spec(8, 2))
+    assert _setup(lib, d, device=-1)[0] == 1

@@ -170,6 +170,12 @@ GRACE_API grace_status grace_profile_read(grace_ctx *ctx, int kernel, double *to
 GRACE_API grace_status grace_group_stats(const grace_ctx *ctx, int group, int precision, long long *nnz,
                                          long long *tile_macs);
 
+/* Reads and clears the batch's device error word: non-zero bits mean a bounded
+   device-side wait inside a tensor-core launch gave up (the launch then wrote
+   no results for the affected cells).  Synchronises the bound stream; returns
+   GRACE_ERR_TIMEOUT when the word was non-zero. */
+GRACE_API grace_status grace_batch_error(grace_batch *batch, int *code);
+
 GRACE_API void grace_batch_destroy(grace_batch *batch);
 GRACE_API void grace_destroy(grace_ctx *ctx);
 

@@ -392,6 +392,7 @@ grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group
         if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
         if (e == cudaSuccess && (ctx->precision_mask & ((1u << GRACE_TF32) | (1u << GRACE_BF16X3)))) {
             e = cudaMalloc(&b->d_F32, n * g.R * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemset(b->d_F32, 0, n * g.R * sizeof(float));
             size_t bytes = 0;
             for (int prec = GRACE_TF32; prec <= GRACE_BF16X3; ++prec)
                 if (ctx->precision_mask & (1u << prec)) {
@@ -641,6 +642,26 @@ grace_status grace_group_stats(const grace_ctx *ctx, int group, int prec, long l
     const Group &G = ctx->groups[group];
     if (nnz) *nnz = G.nnz;
     if (tile_macs) *tile_macs = prec == GRACE_FP64 ? G.nnz : G.tc[prec].mac_per_cell;
+    return GRACE_OK;
+}
+
+grace_status grace_batch_error(grace_batch *b, int *code)
+{
+    if (!b) {
+        set_error("grace_batch_error: null batch");
+        return GRACE_ERR_ARG;
+    }
+    Guard guard(b->ctx->device);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grace_batch_error");
+    if (code) *code = h;
+    if (h) {
+        set_error("a bounded device wait timed out (code " + std::to_string(h) + ")");
+        return GRACE_ERR_TIMEOUT;
+    }
     return GRACE_OK;
 }
 

@@ -1,9 +1,467 @@
-// K-b: tensor-core (tcgen05) contraction of the flux functionals.  (in progress)
+// K-b: tensor-core contraction of the flux functionals on tcgen05 / TMEM.
+//
+// Every flux functional of a cell is a quadratic form of its coefficients,
+//     F_r = sum_{p,q} T_r[p,q] g_p g_q                     (see grace_precompute.cu).
+// Over a batch this is one GEMM per tile of 128 cells, factorised as
+//     Y[c, (r,p)] = sum_q  ghat[c, q] * That_r[p, q]        (tcgen05.mma, FP32 in TMEM)
+//     F[c, r]     = sum_p  ghat[c, p] * Y[c, (r,p)]         (epilogue, one lane per cell)
+// with ghat = g * h_bin (bin-mass scaling) and That = T / (h_bin(p) h_bin(q)), so
+// operands stay in a comfortable FP32/BF16 range for grids spanning 16 decades.
+// The product g (x) g is never materialised: the MMA contracts T with g on one
+// side and the epilogue contracts the accumulator with g on the other, which
+// keeps the A operand equal to the cells' own coefficient tile.
+//
+// Output columns of one MMA tile are a set of up to 4 functionals x a window of
+// 32 consecutive p; the epilogue holds that 32-wide window of ghat in
+// registers and reuses it for every functional of the tile.  A tile's K range
+// is the union of the non-zero q extents of its rows (T is block-sparse: for
+// an interface flux at x_{j+1/2} the u-side rows p < 3j only couple to v-side
+// columns q of bins >= j-1), so zero blocks are skipped at the MMA k-step.
+//
+// Operands live in global memory as ready-made shared-memory images in the
+// canonical K-major SWIZZLE_128B layout (grace_tc_layout.cuh); one
+// cp.async.bulk moves a cell tile's A operand or one K atom of a B tile.
+//
+// Warp roles (persistent, one CTA per SM, cell tiles round-robin):
+//   warp 0 lane 0 : bulk-copy producer (A tile, then the B atoms of every N tile)
+//   warp 1 lane 0 : MMA issuer (kind::tf32, or kind::f16 with bf16 hi/lo x3)
+//   warp 2        : TMEM allocation / release
+//   warps 4..7    : epilogue, TMEM lane quadrant = warp % 4, one cell per thread
+// Every wait on an mbarrier is bounded; on timeout the CTA records an error in
+// the device error word, stops issuing work, drains its outstanding copies and
+// releases its tensor memory before returning.
+#include <cstring>
+#include <vector>
+
 #include "grace_internal.h"
 #include "grace_tc_layout.cuh"
 
 namespace grace {
 
+namespace {
+
+constexpr int kMaxFunc = 4;         // functionals per N tile
+constexpr int kWin = 32;            // p window per functional
+constexpr int kMaxN = kMaxFunc * kWin;
+constexpr int kSlots = 4;           // B ring depth (K atoms)
+constexpr int kAccCols = 128;       // TMEM columns per accumulator buffer
+constexpr int kTmemCols = 256;      // two accumulator buffers
+constexpr int kThreads = 256;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+struct TileDesc {
+    long long b_off;    // byte offset of the tile's first K atom image
+    int nrows;          // MMA N = nf * 32
+    int nf;             // functionals in this tile
+    int atom_lo;        // first K atom (global K index / atom width)
+    int n_atoms;        // K atoms stored for this tile
+    int ks_lo, ks_hi;   // MMA k-steps [ks_lo, ks_hi) (32 bytes of K each)
+    int p0;             // first p of the window
+    int flush;          // last window of its functional group: write F
+    int r[kMaxFunc];    // functional ids (-1 unused)
+    int pad_[2];
+};
+static_assert(sizeof(TileDesc) == 64, "TileDesc layout");
+
+struct TcParams {
+    const TileDesc *tiles;
+    int n_tiles;
+    const uint8_t *B;
+    const uint8_t *A;
+    long long a_tile_bytes;
+    int n_cells;
+    int n_cell_tiles;
+    int R;
+    float *F;
+    int prec;
+    int slot_bytes;       // bytes of one ring slot (max nrows x 128 x planes)
+    int *err;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false on timeout or when another role already aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// SWIZZLE_128B K-major shared-memory matrix descriptor (8-row groups 1024 B apart)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset
+    d |= (uint64_t)1u << 46;                   // descriptor version
+    d |= (uint64_t)2u << 61;                   // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = n
+__device__ __forceinline__ uint32_t instr_desc(int prec, int n)
+{
+    const uint32_t fmt = prec == GRACE_TF32 ? 2u : 1u;   // TF32 = 2, BF16 = 1
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- kernel
+struct Smem {
+    uint64_t a_full, a_empty;
+    uint64_t full[kSlots], empty[kSlots];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t mma_drain;
+    uint32_t tmem_base;
+    int abort_flag;
+    int slot_issued[kSlots];    // copies issued per slot (producer)
+    int slot_done[kSlots];      // copies consumed per slot (MMA)
+    int a_issued, a_done;
+};
+
+__device__ __forceinline__ void fail(TcParams &P, volatile int *abort_flag, int code)
+{
+    if (P.err) atomicOr(P.err, code);
+    *abort_flag = 1;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
+{
+    extern __shared__ uint8_t smem_raw[];
+    // 1024-byte aligned operand region: A tile, then the B ring
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    const uint32_t a_smem = base;
+    const uint32_t b_smem = base + (uint32_t)P.a_tile_bytes;
+    Smem *S = reinterpret_cast<Smem *>(gbase + P.a_tile_bytes + (size_t)kSlots * P.slot_bytes);
+    volatile int *abort_flag = &S->abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int planes = P.prec == GRACE_TF32 ? 1 : 2;
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&S->a_full), 1);
+        mbar_init(smem_u32(&S->a_empty), 1 + 4);
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(smem_u32(&S->full[s]), 1);
+            mbar_init(smem_u32(&S->empty[s]), 1);
+            S->slot_issued[s] = 0;
+            S->slot_done[s] = 0;
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&S->acc_full[b]), 1);
+            mbar_init(smem_u32(&S->acc_empty[b]), 4);
+        }
+        mbar_init(smem_u32(&S->mma_drain), 1);
+        S->abort_flag = 0;
+        S->a_issued = S->a_done = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S->tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ producer
+        int slot = 0, nuse = 0, ctl = 0;
+        for (int ct = blockIdx.x; ct < P.n_cell_tiles && !*abort_flag; ct += gridDim.x, ++ctl) {
+            if (ctl > 0 && !mbar_wait(smem_u32(&S->a_empty), (ctl - 1) & 1, abort_flag)) {
+                fail(P, abort_flag, 1);
+                break;
+            }
+            mbar_expect_tx(smem_u32(&S->a_full), (uint32_t)P.a_tile_bytes);
+            bulk_g2s(a_smem, P.A + (size_t)ct * P.a_tile_bytes, (uint32_t)P.a_tile_bytes, smem_u32(&S->a_full));
+            S->a_issued = ctl + 1;
+            for (int t = 0; t < P.n_tiles && !*abort_flag; ++t) {
+                const TileDesc td = P.tiles[t];
+                const uint32_t atom_bytes = (uint32_t)td.nrows * 128u * planes;
+                for (int a = 0; a < td.n_atoms; ++a) {
+                    const int use = nuse / kSlots;
+                    if (use > 0 && !mbar_wait(smem_u32(&S->empty[slot]), (use - 1) & 1, abort_flag)) {
+                        fail(P, abort_flag, 2);
+                        break;
+                    }
+                    mbar_expect_tx(smem_u32(&S->full[slot]), atom_bytes);
+                    bulk_g2s(b_smem + (uint32_t)slot * P.slot_bytes, P.B + td.b_off + (size_t)a * atom_bytes,
+                             atom_bytes, smem_u32(&S->full[slot]));
+                    S->slot_issued[slot] = use + 1;
+                    ++nuse;
+                    slot = nuse % kSlots;
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        int slot = 0, nuse = 0, acc_use = 0, ctl = 0;
+        for (int ct = blockIdx.x; ct < P.n_cell_tiles && !*abort_flag; ct += gridDim.x, ++ctl) {
+            if (!mbar_wait(smem_u32(&S->a_full), ctl & 1, abort_flag)) {
+                fail(P, abort_flag, 4);
+                break;
+            }
+            S->a_done = ctl + 1;
+            tc_fence_after();
+            for (int t = 0; t < P.n_tiles && !*abort_flag; ++t) {
+                const TileDesc td = P.tiles[t];
+                const int buf = acc_use & 1, bu = acc_use >> 1;
+                if (bu > 0 && !mbar_wait(smem_u32(&S->acc_empty[buf]), (bu - 1) & 1, abort_flag)) {
+                    fail(P, abort_flag, 8);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dcol = tmem + (uint32_t)(buf * kAccCols);
+                const uint32_t idesc = instr_desc(P.prec, td.nrows);
+                const uint32_t atom_bytes = (uint32_t)td.nrows * 128u * planes;
+                int first = 1;
+                for (int a = 0; a < td.n_atoms; ++a) {
+                    const int use = nuse / kSlots;
+                    if (!mbar_wait(smem_u32(&S->full[slot]), use & 1, abort_flag)) {
+                        fail(P, abort_flag, 16);
+                        break;
+                    }
+                    S->slot_done[slot] = use + 1;
+                    tc_fence_after();
+                    const int atom = td.atom_lo + a;
+                    const uint32_t bslot = b_smem + (uint32_t)slot * P.slot_bytes;
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int ks = atom * 4 + kk;
+                        if (ks < td.ks_lo || ks >= td.ks_hi) continue;
+                        const uint32_t a_off = (uint32_t)atom * (kTileM * 128u) + (uint32_t)kk * 32u;
+                        const uint32_t b_off = (uint32_t)kk * 32u;
+                        if (P.prec == GRACE_TF32) {
+                            mma_tf32(dcol, smem_desc(a_smem + a_off), smem_desc(bslot + b_off), idesc, first ? 0u : 1u);
+                        } else {
+                            const uint32_t a_lo = a_smem + (uint32_t)(P.a_tile_bytes / 2);
+                            const uint32_t b_lo = bslot + (uint32_t)td.nrows * 128u;
+                            mma_f16(dcol, smem_desc(a_smem + a_off), smem_desc(bslot + b_off), idesc, first ? 0u : 1u);
+                            mma_f16(dcol, smem_desc(a_smem + a_off), smem_desc(b_lo + b_off), idesc, 1u);
+                            mma_f16(dcol, smem_desc(a_lo + a_off), smem_desc(bslot + b_off), idesc, 1u);
+                        }
+                        first = 0;
+                    }
+                    tc_commit(smem_u32(&S->empty[slot]));   // frees the slot once these MMAs retire
+                    ++nuse;
+                    slot = nuse % kSlots;
+                    (void)atom_bytes;
+                }
+                if (*abort_flag) break;
+                if (first) {
+                    // a tile with no k-step in range cannot occur (tiles are built non-empty);
+                    // keep the accumulator well defined anyway
+                    fail(P, abort_flag, 64);
+                    break;
+                }
+                tc_commit(smem_u32(&S->acc_full[buf]));
+                ++acc_use;
+            }
+            tc_commit(smem_u32(&S->a_empty));   // A may be overwritten once the MMAs of this cell tile retire
+        }
+        if (*abort_flag) {
+            // make sure every MMA this thread issued has retired before tensor memory is released
+            tc_commit(smem_u32(&S->mma_drain));
+            const long long t0 = clock64();
+            while (!mbar_try_wait(smem_u32(&S->mma_drain), 0) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+    } else if (warp >= 4) {
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;              // TMEM lane quadrant
+        const int row = q * 32 + lane;       // cell within the tile
+        int acc_use = 0, ctl = 0;
+        const uint8_t *a_gen = gbase;        // generic pointer to the A tile
+        for (int ct = blockIdx.x; ct < P.n_cell_tiles && !*abort_flag; ct += gridDim.x, ++ctl) {
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full), ctl & 1, abort_flag))) {
+                fail(P, abort_flag, 32);
+                break;
+            }
+            const long long cell = (long long)ct * kTileM + row;
+            float Facc[kMaxFunc] = {0.f, 0.f, 0.f, 0.f};
+            for (int t = 0; t < P.n_tiles; ++t) {
+                if (__any_sync(0xffffffffu, *abort_flag)) break;
+                const TileDesc td = P.tiles[t];
+                // ghat window [p0, p0 + 32) of this thread's cell from the A tile
+                float gw[kWin];
+                if (P.prec == GRACE_TF32) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 v = *reinterpret_cast<const float4 *>(a_gen + swz_offset(kTileM, row, td.p0 + 4 * c, 4));
+                        gw[4 * c] = v.x;
+                        gw[4 * c + 1] = v.y;
+                        gw[4 * c + 2] = v.z;
+                        gw[4 * c + 3] = v.w;
+                    }
+                } else {
+                    const size_t lo_plane = (size_t)(P.a_tile_bytes / 2);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const size_t off = swz_offset(kTileM, row, td.p0 + 8 * c, 2);
+                        const uint4 hi = *reinterpret_cast<const uint4 *>(a_gen + off);
+                        const uint4 lo = *reinterpret_cast<const uint4 *>(a_gen + lo_plane + off);
+                        const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            gw[8 * c + 2 * e] = __uint_as_float(hw[e] << 16) + __uint_as_float(lw[e] << 16);
+                            gw[8 * c + 2 * e + 1] =
+                                __uint_as_float(hw[e] & 0xFFFF0000u) + __uint_as_float(lw[e] & 0xFFFF0000u);
+                        }
+                    }
+                }
+                const int buf = acc_use & 1, bu = acc_use >> 1;
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->acc_full[buf]), bu & 1, abort_flag))) {
+                    fail(P, abort_flag, 128);
+                    break;
+                }
+                tc_fence_after();
+                for (int f = 0; f < td.nf; ++f) {
+                    float y[kWin];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kAccCols + f * kWin), y);
+                    float s = 0.f;
+#pragma unroll
+                    for (int c = 0; c < kWin; ++c) s = fmaf(gw[c], y[c], s);
+                    Facc[f] += s;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&S->acc_empty[buf]));
+                ++acc_use;
+                if (td.flush) {
+                    if (cell < P.n_cells)
+                        for (int f = 0; f < td.nf; ++f) P.F[cell * P.R + td.r[f]] = Facc[f];
+                    for (int f = 0; f < kMaxFunc; ++f) Facc[f] = 0.f;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&S->a_empty));
+        }
+    }
+
+    // ---------------------------------------------------- teardown
+    __syncwarp();
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        // drain copies still in flight into this CTA's shared memory (bounded)
+        for (int s = 0; s < kSlots; ++s)
+            for (int u = S->slot_done[s]; u < S->slot_issued[s]; ++u) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(smem_u32(&S->full[s]), u & 1) && clock64() - t0 < kWaitCycles) {
+                }
+            }
+        for (int u = S->a_done; u < S->a_issued; ++u) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(smem_u32(&S->a_full), u & 1) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 2) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
 void free_tc_tiles(TcTiles &t)
 {
     cudaFree(t.d_b);
@@ -20,19 +478,200 @@ size_t opA_bytes_for(const DevGroup &g, int prec, int n_cells, int *kpad)
     return tiles * opA_tile_bytes(prec, kp);
 }
 
-grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
+static uint16_t bf16_bits_rn(float f)
 {
-    (void)G;
-    (void)prec;
-    (void)st;
-    set_error("tensor-core contraction not available in this build");
-    return GRACE_ERR_UNSUPPORTED;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);   // inf / nan
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
 }
 
-cudaError_t launch_contract_tc(const DevGroup &, const TcTiles &, int, const void *, int, float *, int *,
-                               cudaStream_t)
+static float bf16_to_f(uint16_t b)
 {
-    return cudaErrorNotSupported;
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+static uint32_t tf32_bits_rn(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return u;
+    u += 0x1000u;            // round half away from zero at bit 13
+    return u & 0xFFFFE000u;
+}
+
+grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
+{
+    const DevGroup &g = G.dg;
+    if (g.k > 3) {
+        set_error("tensor-core tiles need k <= 3");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    const int P_ = g.P, R = g.R, K1 = g.K1;
+    const int ae = atom_elems(prec), eb = elem_bytes(prec), planes = n_planes(prec);
+    const int kstep = 32 / eb;   // elements per MMA k-step
+    std::vector<double> T((size_t)R * P_ * P_);
+    std::vector<int> qlo((size_t)R * P_), qhi((size_t)R * P_), pr(2 * R);
+    cudaError_t e = cudaMemcpyAsync(T.data(), G.d_T, T.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(qlo.data(), G.d_qlo, qlo.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(qhi.data(), G.d_qhi, qhi.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pr.data(), G.d_prange, pr.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core tiles: copy T");
+
+    std::vector<double> h(g.N);
+    for (int j = 0; j < g.N; ++j) h[j] = G.h_edges[j + 1] - G.h_edges[j];
+
+    // functional groups: bin by bin, up to kMaxFunc functionals each
+    std::vector<std::vector<int>> groups;
+    std::vector<int> cur;
+    for (int j = 0; j < g.N; ++j) {
+        std::vector<int> fj;
+        if (j < g.n_if) fj.push_back(j);
+        for (int i = 1; i <= g.k; ++i) fj.push_back(g.n_if + j * g.k + i - 1);
+        if (!cur.empty() && cur.size() + fj.size() > (size_t)kMaxFunc) {
+            groups.push_back(cur);
+            cur.clear();
+        }
+        for (int r : fj) {
+            if (cur.size() == (size_t)kMaxFunc) {
+                groups.push_back(cur);
+                cur.clear();
+            }
+            cur.push_back(r);
+        }
+    }
+    if (!cur.empty()) groups.push_back(cur);
+
+    std::vector<TileDesc> tiles;
+    std::vector<uint8_t> B;
+    long long macs = 0;
+    for (const auto &grp : groups) {
+        int plo = P_, phi = 0;
+        for (int r : grp)
+            if (pr[2 * r + 1] > pr[2 * r]) {
+                plo = std::min(plo, pr[2 * r]);
+                phi = std::max(phi, pr[2 * r + 1]);
+            }
+        if (phi <= plo) continue;   // all functionals of the group vanish identically
+        const int nf = (int)grp.size(), nrows = nf * kWin;
+        size_t first_tile = tiles.size();
+        for (int w = plo / kWin; w * kWin < phi; ++w) {
+            const int p0 = w * kWin;
+            int q_lo = P_, q_hi = 0;
+            for (int f = 0; f < nf; ++f)
+                for (int c = 0; c < kWin; ++c) {
+                    const int p = p0 + c;
+                    if (p >= P_) continue;
+                    const size_t row = (size_t)grp[f] * P_ + p;
+                    if (qlo[row] < qhi[row]) {
+                        q_lo = std::min(q_lo, qlo[row]);
+                        q_hi = std::max(q_hi, qhi[row]);
+                    }
+                }
+            if (q_hi <= q_lo) continue;
+            TileDesc td;
+            std::memset(&td, 0, sizeof(td));
+            td.nrows = nrows;
+            td.nf = nf;
+            td.ks_lo = q_lo / kstep;
+            td.ks_hi = (q_hi + kstep - 1) / kstep;
+            td.atom_lo = td.ks_lo / 4;
+            td.n_atoms = (td.ks_hi + 3) / 4 - td.atom_lo;
+            td.p0 = p0;
+            for (int f = 0; f < kMaxFunc; ++f) td.r[f] = f < nf ? grp[f] : -1;
+            td.b_off = (long long)B.size();
+            const size_t atom_plane = (size_t)nrows * 128;
+            B.resize(B.size() + (size_t)td.n_atoms * atom_plane * planes, 0);
+            uint8_t *img = B.data() + td.b_off;
+            for (int a = 0; a < td.n_atoms; ++a) {
+                uint8_t *ai = img + (size_t)a * atom_plane * planes;
+                for (int f = 0; f < nf; ++f)
+                    for (int c = 0; c < kWin; ++c) {
+                        const int p = p0 + c, rowi = f * kWin + c;
+                        if (p >= P_) continue;
+                        const double *Trow = T.data() + ((size_t)grp[f] * P_ + p) * P_;
+                        for (int x = 0; x < ae; ++x) {
+                            const int qq = (td.atom_lo + a) * ae + x;
+                            if (qq >= P_) break;
+                            const double val = Trow[qq] / (h[p / K1] * h[qq / K1]);
+                            const size_t off = swz_offset(nrows, rowi, x, eb);
+                            if (prec == GRACE_TF32) {
+                                const uint32_t bits = tf32_bits_rn((float)val);
+                                std::memcpy(ai + off, &bits, 4);
+                            } else {
+                                const uint16_t hi = bf16_bits_rn((float)val);
+                                const uint16_t lo = bf16_bits_rn((float)(val - (double)bf16_to_f(hi)));
+                                std::memcpy(ai + off, &hi, 2);
+                                std::memcpy(ai + atom_plane + off, &lo, 2);
+                            }
+                        }
+                    }
+            }
+            macs += (long long)nrows * (td.ks_hi - td.ks_lo) * kstep;
+            tiles.push_back(td);
+        }
+        if (tiles.size() > first_tile) tiles.back().flush = 1;
+    }
+    if (tiles.empty()) {
+        set_error("tensor-core tiles: the coefficient tensor is empty");
+        return GRACE_ERR_ARG;
+    }
+    TcTiles &out = G.tc[prec];
+    free_tc_tiles(out);
+    e = cudaMalloc(&out.d_b, B.size());
+    if (e == cudaSuccess) e = cudaMalloc(&out.d_desc, tiles.size() * sizeof(TileDesc));
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_b, B.data(), B.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_desc, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_tc_tiles(out);
+        return cuda_fail(e, "tensor-core tiles: upload");
+    }
+    out.n_tiles = (int)tiles.size();
+    out.k_pad = (P_ + ae - 1) / ae * ae;
+    out.b_bytes = B.size();
+    out.mac_per_cell = macs;
+    out.built = 1;
+    return GRACE_OK;
+}
+
+static int sm_count(int dev)
+{
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, int n_cells,
+                               float *d_F32, int *d_err, cudaStream_t st)
+{
+    if (!t.built) return cudaErrorInvalidValue;
+    TcParams P;
+    P.tiles = (const TileDesc *)t.d_desc;
+    P.n_tiles = t.n_tiles;
+    P.B = (const uint8_t *)t.d_b;
+    P.A = (const uint8_t *)opA;
+    P.a_tile_bytes = (long long)opA_tile_bytes(prec, t.k_pad);
+    P.n_cells = n_cells;
+    P.n_cell_tiles = (n_cells + kTileM - 1) / kTileM;
+    P.R = g.R;
+    P.F = d_F32;
+    P.prec = prec;
+    P.slot_bytes = kMaxN * 128 * n_planes(prec);
+    P.err = d_err;
+    const size_t smem = 1024 + (size_t)P.a_tile_bytes + (size_t)kSlots * P.slot_bytes + sizeof(Smem) + 64;
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int grid = std::min(P.n_cell_tiles, sm_count(dev));
+    contract_tc_kernel<<<grid, kThreads, smem, st>>>(P);
+    return cudaGetLastError();
 }
 
 }  // namespace grace

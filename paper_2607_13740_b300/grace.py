@@ -45,7 +45,7 @@ def exported_symbols():
             "grace_set_stream", "grace_precompute", "grace_group_info", "grace_bind_batch",
             "grace_batch_offsets", "grace_project", "grace_rhs", "grace_step", "grace_mass",
             "grace_limit", "grace_profile_enable", "grace_profile_read", "grace_group_stats",
-            "grace_batch_destroy", "grace_destroy"]
+            "grace_batch_error", "grace_batch_destroy", "grace_destroy"]
 
 
 def load(path: str | None = None):
@@ -76,6 +76,7 @@ def load(path: str | None = None):
     L.grace_profile_enable.argtypes = [_VP, S]
     L.grace_profile_read.argtypes = [_VP, S, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     L.grace_group_stats.argtypes = [_VP, S, S, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.grace_batch_error.argtypes = [_VP, ctypes.POINTER(S)]
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -238,6 +239,14 @@ class Batch:
         self.ctx.set_stream()
         _check(load().grace_limit(self._h, _ptr(g), _ptr(flags)), "grace_limit")
         return g
+
+    def device_error(self) -> int:
+        """Reads and clears the device error word (0 = no bounded wait gave up)."""
+        code = ctypes.c_int()
+        st = load().grace_batch_error(self._h, ctypes.byref(code))
+        if st not in (0, 6):
+            _check(st, "grace_batch_error")
+        return code.value
 
     def close(self):
         if getattr(self, "_h", None):

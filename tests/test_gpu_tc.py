@@ -1,0 +1,127 @@
+"""Parity of the tcgen05 tensor-core forms (TF32 and split BF16 x3) with the FP64 oracle.
+
+Stated tolerances (relative to the oracle's rounding scale S of each RHS
+coefficient, and for trajectories to the cell's mass M_1):
+  TF32:    |L - L_oracle| <= 2e-3 S,  trajectory L1 <= 1e-3 M_1
+  BF16X3:  |L - L_oracle| <= 5e-5 S,  trajectory L1 <= 1e-5 M_1
+Mass is conserved to FP64 round-off in every form (the i = 0 row only sees
+flux differences, summed in FP64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_13740_b300 import grace, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TOL_RHS = {grace.TF32: 2e-3, grace.BF16X3: 5e-5}
+TOL_L1 = {grace.TF32: 1e-3, grace.BF16X3: 1e-5}
+FORMS = [grace.TF32, grace.BF16X3]
+IDS = ["tf32", "bf16x3"]
+
+SPECS = {
+    "add_N40_k2": W.additive_spec(40, 2),
+    "const_noncons_k1": W.constant_kernel_spec(16, 1, W.FLUX_NONCONSERVATIVE, 1e-4, 1e6),
+    "k0": W.additive_spec(20, 0, 1e-3, 1e5),
+    "k3": W.GroupSpec(12, 3, 1e-2, 1e4, 0, W.COAG_ADD, (1.0,)),
+    "pure_frag": W.pure_fragmentation_spec(10, 2, 1e-6, 1e3),
+    "toy_remnant": W.coupled_toy_spec(10, 2, flux_mode=0),
+}
+
+
+def _ctx(spec):
+    return grace.Context([spec], 0, precisions=(grace.FP64, grace.TF32, grace.BF16X3))
+
+
+def _scaled(L, Lo, S):
+    den = np.maximum(np.abs(Lo), S)
+    d = np.abs(L - Lo)
+    return np.where(den > 0, d / np.where(den > 0, den, 1.0), np.where(d > 0, np.inf, 0.0))
+
+
+@pytest.mark.parametrize("form", FORMS, ids=IDS)
+@pytest.mark.parametrize("name", sorted(SPECS))
+def test_rhs_parity_tensor_core(name, form):
+    spec = SPECS[name]
+    n = 300    # three 128-cell tiles, the last one ragged
+    g = W.random_coefficients(spec, n, seed=301)
+    ctx = _ctx(spec)
+    b = ctx.batch(n)
+    L = b.rhs(torch.as_tensor(g, device=DEV), precision=form).cpu().numpy()
+    assert b.device_error() == 0
+    Lo, S = oracle.Oracle(spec).rhs(g)
+    err = _scaled(L, Lo, S)
+    assert np.isfinite(L).all()
+    assert err.max() <= TOL_RHS[form], f"{name}: {err.max():.3e}"
+    # mass: sum_j h_j L_j^0 telescopes to zero in FP64 (conservative fluxes)
+    if spec.flux_mode == W.FLUX_CONSERVATIVE:
+        h = np.diff(oracle.Oracle(spec).edges())
+        L0 = L.reshape(n, spec.n_bins, spec.order_k + 1)[:, :, 0]
+        assert np.all(np.abs((h * L0).sum(axis=1)) <= 1e-14 * np.abs(h * L0).sum(axis=1))
+
+
+@pytest.mark.parametrize("form", FORMS, ids=IDS)
+@pytest.mark.parametrize("n", [1, 127, 129])
+def test_small_and_ragged_batches(form, n):
+    spec = SPECS["add_N40_k2"]
+    g = W.random_coefficients(spec, n, seed=302)
+    ctx = _ctx(spec)
+    b = ctx.batch(n)
+    L = b.rhs(torch.as_tensor(g, device=DEV), precision=form).cpu().numpy()
+    assert b.device_error() == 0
+    Lo, S = oracle.Oracle(spec).rhs(g)
+    assert _scaled(L, Lo, S).max() <= TOL_RHS[form]
+
+
+@pytest.mark.parametrize("form", FORMS, ids=IDS)
+def test_batched_additive_trajectory(form):
+    """100 SSP-RK3 steps of the batched additive workload at 256 cells."""
+    wl = W.batched_additive(n_cells=256)
+    ctx = _ctx(wl.spec)
+    b = ctx.batch(wl.n_cells)
+    g = b.project(wl.ic_kind, wl.ic_params)
+    g0 = g.cpu().numpy()
+    m0 = b.mass(g).cpu().numpy()
+    dt = torch.as_tensor(wl.dt, device=DEV)
+    mass = torch.zeros(wl.n_cells, dtype=torch.float64, device=DEV)
+    b.step(g, dt, wl.n_steps, precision=form, mass=mass)
+    assert b.device_error() == 0
+    m = mass.cpu().numpy()
+    assert np.all(np.abs(m - m0) <= 1e-13 * np.abs(m0))
+    o = oracle.Oracle(wl.spec)
+    sample = np.arange(0, 256, 8)
+    go, _, _ = o.step(g0[sample], wl.dt[sample], wl.n_steps)
+    h = np.diff(o.edges())
+    d = np.abs(g.cpu().numpy()[sample] - go).reshape(len(sample), 40, 3)
+    l1 = (h[None, :] * d.sum(axis=2)).sum(axis=1) / np.abs(m0[sample])
+    assert l1.max() <= TOL_L1[form], l1.max()
+
+
+@pytest.mark.parametrize("form", FORMS, ids=IDS)
+def test_full_size_batch_sampled(form):
+    """65,536 cells (512 tiles over every SM, several tiles per CTA)."""
+    wl = W.batched_additive()
+    ctx = _ctx(wl.spec)
+    b = ctx.batch(wl.n_cells)
+    g = b.project(wl.ic_kind, wl.ic_params)
+    L = b.rhs(g, precision=form)
+    assert b.device_error() == 0
+    sample = np.array([0, 1, 127, 128, 18943, 18944, 40000, 65535])
+    Lo, S = oracle.Oracle(wl.spec).rhs(g[sample].cpu().numpy())
+    assert _scaled(L[sample].cpu().numpy(), Lo, S).max() <= TOL_RHS[form]
+
+
+def test_forms_agree_with_fp64_gpu_path():
+    """Reduced-precision forms against the FP64 GPU path on the same batch (all cells)."""
+    spec = SPECS["add_N40_k2"]
+    g = torch.as_tensor(W.random_coefficients(spec, 1000, seed=303), device=DEV)
+    ctx = _ctx(spec)
+    b = ctx.batch(1000)
+    L64 = b.rhs(g, precision=grace.FP64)
+    for form in FORMS:
+        L = b.rhs(g, precision=form)
+        rel = ((L - L64).abs().amax(dim=1) / L64.abs().amax(dim=1)).max().item()
+        assert rel <= 50 * TOL_RHS[form], (form, rel)

@@ -188,6 +188,9 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3"])
     ap.add_argument("--cells", type=int, default=65536)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--forms", default=None,
+                    help="comma-separated subset of fp64,tf32,bf16x3 to time (default: all built)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -221,6 +224,9 @@ def main():
         except grace.GraceError:
             ctx = None
     forms = list(ctx.precisions)
+    if args.forms:
+        want = [grace.PRECISIONS[f.strip()] for f in args.forms.split(",") if f.strip()]
+        forms = [f for f in forms if f in want]
     head = grace.PRECISIONS[args.precision] if args.precision else forms[-1]
     if head not in forms:
         raise SystemExit(f"precision {args.precision} is not available in this build")
@@ -316,13 +322,18 @@ def main():
     r = hd.pop("_r")
     for f in forms_out.values():
         f.pop("_r", None)
-    fp64_rate = forms_out["fp64"]["cell_steps_per_s"]
-    for f in forms_out.values():
-        f["speedup_vs_fp64_gpu"] = f["cell_steps_per_s"] / fp64_rate
+    if "fp64" in forms_out:
+        fp64_rate = forms_out["fp64"]["cell_steps_per_s"]
+        for f in forms_out.values():
+            f["speedup_vs_fp64_gpu"] = f["cell_steps_per_s"] / fp64_rate
 
     # end to end through the public API: pinned host state in, one step, state out
     e2e = None
+    if args.no_e2e:
+        e2e = {"value": None, "unit": UNIT, "skipped": "--no-e2e"}
     try:
+        if args.no_e2e:
+            raise StopIteration
         host_in = g0.cpu().pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         gdev = torch.empty_like(g0)
@@ -348,6 +359,8 @@ def main():
         nbytes = host_in.numel() * 8
         e2e = {"value": n * world * e2e_steps / (float(t.item()) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+    except StopIteration:
+        pass
     except Exception as exc:  # pinned memory may be unavailable
         e2e = {"value": None, "unit": UNIT, "error": str(exc)[:200]}
 

@@ -132,6 +132,7 @@ struct Guard {   // switches to the context's device for the duration of a call
     int prev = -1;
     explicit Guard(int dev)
     {
+        cudaGetLastError();   // a stale error of an earlier, unrelated call must not be reported as ours
         cudaGetDevice(&prev);
         if (prev != dev) cudaSetDevice(dev);
     }

@@ -150,6 +150,23 @@ GRACE_API grace_status grace_rhs(grace_batch *batch, const double *g, double *L,
 GRACE_API grace_status grace_step(grace_batch *batch, double *g, const double *dt, int n_steps, int precision,
                         double *mass, unsigned char *flags);
 
+/* The FP64 L = L[g] of grace_rhs for n_cells cells of one group, for callers
+   that cannot allocate device memory: codes whose device memory belongs to
+   another framework's pool allocator, and solvers calling the RHS inside a
+   per-substep loop where an allocation (cudaMalloc synchronises the device)
+   is not acceptable.  This call allocates nothing: its flux-functional
+   workspace is a fixed 16 MiB array (2^21 doubles) inside the library, held on
+   every GPU that loads the library until the process exits, so
+   n_cells * n_functionals must not exceed 2^21 (GRACE_ERR_ARG otherwise; C2's
+   N = 40, k = 2 group allows 17,620 cells per call).  The context must have
+   been set up and precomputed beforehand (those calls do allocate).  The first
+   call on a device looks up the array's device address on that device; make
+   that first call before any stream capture.  All calls share the one array:
+   calls whose executions overlap on the GPU (other streams, other threads)
+   race and must be serialised by the caller.  g, L: device, packed layout; runs
+   on the context's bound stream.  The paper has no counterpart of this call. */
+GRACE_API grace_status grace_rhs_noalloc(grace_ctx *ctx, int group, int n_cells, const double *g, double *L);
+
 /* M_1 = sum_j h_j g_j^0 per cell (Sec. 4.1).  g, mass: device. */
 GRACE_API grace_status grace_mass(grace_batch *batch, const double *g, double *mass);
 

@@ -129,8 +129,11 @@ GRACE_API grace_status grace_precompute(grace_ctx *ctx, unsigned precision_mask)
 GRACE_API grace_status grace_group_info(const grace_ctx *ctx, int group, int *n_coef, int *n_functionals);
 
 /* Binds a batch of n_cells >= 1 cells; cell_group (host, may be NULL = all in
-   group 0) gives each cell's group.  Allocates the batch workspaces.  The cell
-   layout is packed in the given order; grace_batch_offsets returns it. */
+   group 0) gives each cell's group, in any order and mix.  Allocates the batch
+   workspaces.  The cell layout is packed in the given order (cell c holds
+   P(group(c)) doubles); grace_batch_offsets returns it.  Cells of one group
+   are computed together on their own stream; a batch of one group in caller
+   order works directly on the caller's arrays. */
 GRACE_API grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group, grace_batch **batch);
 /* host out[n_cells + 1]: offset (in doubles) of every cell's coefficients; out[n_cells] = total */
 GRACE_API grace_status grace_batch_offsets(const grace_batch *batch, long long *out);
@@ -167,11 +170,47 @@ GRACE_API grace_status grace_step(grace_batch *batch, double *g, const double *d
    on the context's bound stream.  The paper has no counterpart of this call. */
 GRACE_API grace_status grace_rhs_noalloc(grace_ctx *ctx, int group, int n_cells, const double *g, double *L);
 
+/* enable != 0: grace_step records its whole launch sequence (every group of the
+   batch, every step and stage) into a CUDA graph on the first call with a given
+   (g, dt, mass, flags, n_steps, precision) and replays the graph on later calls
+   with the same arguments.  Needs a bound non-default stream; launch timing
+   (grace_profile_enable) is not recorded inside graphs. */
+GRACE_API grace_status grace_batch_set_graph(grace_batch *batch, int enable);
+
 /* M_1 = sum_j h_j g_j^0 per cell (Sec. 4.1).  g, mass: device. */
 GRACE_API grace_status grace_mass(grace_batch *batch, const double *g, double *mass);
 
 /* The scaling limiter alone, in place; flags (device [n_cells] or NULL). */
 GRACE_API grace_status grace_limit(grace_batch *batch, double *g, unsigned char *flags);
+
+/* Tangent-linear RHS: Jv = (dL/dg)(g) v.  L is quadratic in g, so
+   Jv = D (g^T (T_r + T_r^T) v)_r exactly.  g, v, Jv: device, packed layout.
+   GRACE_FP64 only (GRACE_ERR_UNSUPPORTED otherwise).  The paper has no adjoint;
+   this and the next three calls differentiate its scheme. */
+GRACE_API grace_status grace_rhs_jvp(grace_batch *batch, const double *g, const double *v, double *Jv, int precision);
+
+/* Adjoint RHS: w = (dL/dg)(g)^T lambda.  g, lambda, w: device.  GRACE_FP64 only. */
+GRACE_API grace_status grace_rhs_vjp(grace_batch *batch, const double *g, const double *lambda, double *w,
+                                     int precision);
+
+/* Prepares parameter gradients for grace_adjoint: for each id (0..7 coag_p[i],
+   8..15 frag_p[i-8], 16..23 break_p[i-16]) builds dT_r/dtheta by a central
+   difference of the FP64 precompute with relative step rel_step (<= 0 means
+   1e-5).  Replaces any earlier set.  Allocates and synchronises. */
+GRACE_API grace_status grace_param_grad_setup(grace_ctx *ctx, int group, int n_params, const int *param_ids,
+                                              double rel_step);
+
+/* Discrete adjoint of n_steps steps of grace_step (limiter + SSP-RK3) from g0
+   with per-cell dt: given lambda_T = dJ/dg(t_end), returns lambda_0 = dJ/dg0
+   and, when dtheta is not NULL, dtheta[c * n_params + i] = dJ/dtheta_i from
+   cell c for the parameters of grace_param_grad_setup.  Stores a checkpoint
+   every ckpt_every steps and recomputes the stage states of one segment at a
+   time.  g0, dt, lambda_T, lambda_0, dtheta: device.  The workspace
+   (checkpoints + one segment's stage states + adjoint vectors) is allocated on
+   first use and kept with the batch; that call synchronises.  GRACE_FP64 only. */
+GRACE_API grace_status grace_adjoint(grace_batch *batch, const double *g0, const double *dt, int n_steps,
+                                     int ckpt_every, const double *lambda_T, double *lambda_0, double *dtheta,
+                                     int precision);
 
 /* Launch timing with CUDA events recorded on the bound stream around every
    contraction (kernel 0) and flux-update (kernel 1) launch of this context.
@@ -192,6 +231,11 @@ GRACE_API grace_status grace_group_stats(const grace_ctx *ctx, int group, int pr
    no results for the affected cells).  Synchronises the bound stream; returns
    GRACE_ERR_TIMEOUT when the word was non-zero. */
 GRACE_API grace_status grace_batch_error(grace_batch *batch, int *code);
+
+/* Measures, on `device`, the CUDA-core throughput used as roofline
+   denominators: rates[0] FP64 FMA/s, rates[1] FP32 FMA/s, rates[2] FP64->FP32
+   conversions/s (3 doubles, host).  Allocates and synchronises. */
+GRACE_API grace_status grace_probe_rates(int device, double *rates);
 
 GRACE_API void grace_batch_destroy(grace_batch *batch);
 GRACE_API void grace_destroy(grace_ctx *ctx);

@@ -1,0 +1,581 @@
+// Tangent-linear and adjoint of the DG right-hand side and of the SSP-RK3 step.
+//
+// With F_r = g^T T_r g (every flux functional is a quadratic form of the cell's
+// coefficients) and L = D F (D: the flux-difference / volume assembly of eq.
+// (evo), linear), the derivatives are
+//     J v        = D ( g^T (T_r + T_r^T) v )_r                 (JVP)
+//     J^T lambda = sum_r mu_r (T_r + T_r^T) g,  mu = D^T lambda  (VJP)
+// The scaling limiter (eqs. recon, gamma) is differentiated with the envelope
+// theorem: the derivative of the bin minimum with respect to g^i is phi_i at
+// the minimiser.  The SSP-RK3 stages (eq. RK3) are reversed exactly, with the
+// stage states recomputed from checkpoints.  Parameter gradients contract
+// mu with g^T (dT_r / dtheta) g, where dT/dtheta is a central difference of the
+// FP64 precompute.  This is the FP64 (CUDA-core) adjoint.
+#include <string>
+#include <vector>
+
+#include "grace_physics.cuh"
+
+namespace grace {
+
+namespace {
+
+constexpr int kB = kKMax + 1;
+
+// ------------------------------------------------------------------ JVP contraction
+// F_r = sum_{p,q} T_r[p,q] (a_p b_q + b_p a_q), one warp per 32 cells
+__global__ void __launch_bounds__(128) contract_pair_kernel(
+    const double *__restrict__ T, const int *__restrict__ qlo, const int *__restrict__ qhi,
+    const int *__restrict__ prange, int R, int P, const double *__restrict__ a, const double *__restrict__ b,
+    int n_cells, double *__restrict__ F)
+{
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const long long cell0 = ((long long)blockIdx.x * nw + warp) * 32;
+    double *aw = sm + (size_t)warp * 2 * P * 32;
+    double *bw = aw + (size_t)P * 32;
+    for (int idx = lane; idx < 32 * P; idx += 32) {
+        const int c = idx / P, q = idx - c * P;
+        const long long cell = cell0 + c;
+        aw[q * 32 + c] = cell < n_cells ? a[cell * P + q] : 0.0;
+        bw[q * 32 + c] = cell < n_cells ? b[cell * P + q] : 0.0;
+    }
+    __syncwarp();
+    const long long cell = cell0 + lane;
+    for (int r = 0; r < R; ++r) {
+        double Fr = 0.0;
+        for (int p = prange[2 * r]; p < prange[2 * r + 1]; ++p) {
+            const int q0 = qlo[r * P + p], q1 = qhi[r * P + p];
+            if (q0 >= q1) continue;
+            const double *Trow = T + ((size_t)r * P + p) * P;
+            double ya = 0.0, yb = 0.0;
+            for (int q = q0; q < q1; ++q) {
+                const double t = __ldg(Trow + q);
+                ya = fma(t, aw[q * 32 + lane], ya);
+                yb = fma(t, bw[q * 32 + lane], yb);
+            }
+            Fr = fma(aw[p * 32 + lane], yb, fma(bw[p * 32 + lane], ya, Fr));
+        }
+        if (cell < n_cells) F[cell * R + r] = Fr;
+    }
+}
+
+// ------------------------------------------------------------------ mu = D^T lambda
+// L_j^i = (2i+1)/h_j [ V_j^i - F_{j+1/2} + (-1)^i F_{j-1/2} ]  (eq. evo)
+__global__ void dT_lambda_kernel(DevGroup G, const double *lambda, int n_cells, double *mu)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_cells * G.R) return;
+    const long long cell = t / G.R;
+    const int r = (int)(t - cell * G.R);
+    const double *lam = lambda + cell * G.P;
+    double m = 0.0;
+    if (r < G.n_if) {
+        const int j = r;   // F_{j+1/2}: -(2i+1)/h_j in bin j, +(-1)^i (2i+1)/h_{j+1} in bin j+1
+        for (int i = 0; i <= G.k; ++i) {
+            m -= (2.0 * i + 1.0) * G.inv_h[j] * lam[j * G.K1 + i];
+            if (j + 1 < G.N) m += ((i & 1) ? -1.0 : 1.0) * (2.0 * i + 1.0) * G.inv_h[j + 1] * lam[(j + 1) * G.K1 + i];
+        }
+    } else {
+        const int q = r - G.n_if, j = q / G.k, i = q % G.k + 1;
+        m = (2.0 * i + 1.0) * G.inv_h[j] * lam[j * G.K1 + i];
+    }
+    mu[cell * G.R + r] = m;
+}
+
+// ------------------------------------------------------------------ VJP contraction
+// w = sum_r mu_r (T_r + T_r^T) g, one warp per 32 cells
+__global__ void __launch_bounds__(128) vjp_kernel(const double *__restrict__ T, const int *__restrict__ qlo,
+                                                   const int *__restrict__ qhi, const int *__restrict__ prange,
+                                                   int R, int P, const double *__restrict__ g,
+                                                   const double *__restrict__ mu, int n_cells, double *__restrict__ w)
+{
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const long long cell0 = ((long long)blockIdx.x * nw + warp) * 32;
+    double *gw = sm + (size_t)warp * 2 * P * 32;
+    double *ww = gw + (size_t)P * 32;
+    for (int idx = lane; idx < 32 * P; idx += 32) {
+        const int c = idx / P, q = idx - c * P;
+        const long long cell = cell0 + c;
+        gw[q * 32 + c] = cell < n_cells ? g[cell * P + q] : 0.0;
+        ww[q * 32 + c] = 0.0;
+    }
+    __syncwarp();
+    const long long cell = cell0 + lane;
+    for (int r = 0; r < R; ++r) {
+        const double m = cell < n_cells ? mu[cell * R + r] : 0.0;
+        for (int p = prange[2 * r]; p < prange[2 * r + 1]; ++p) {
+            const int q0 = qlo[r * P + p], q1 = qhi[r * P + p];
+            if (q0 >= q1) continue;
+            const double *Trow = T + ((size_t)r * P + p) * P;
+            const double mg = m * gw[p * 32 + lane];
+            double y = 0.0;
+            for (int q = q0; q < q1; ++q) {
+                const double t = __ldg(Trow + q);
+                y = fma(t, gw[q * 32 + lane], y);
+                ww[q * 32 + lane] = fma(mg, t, ww[q * 32 + lane]);
+            }
+            ww[p * 32 + lane] = fma(m, y, ww[p * 32 + lane]);
+        }
+    }
+    __syncwarp();
+    for (int idx = lane; idx < 32 * P; idx += 32) {
+        const int c = idx / P, q = idx - c * P;
+        const long long cl = cell0 + c;
+        if (cl < n_cells) w[cl * P + q] = ww[q * 32 + c];
+    }
+}
+
+// ------------------------------------------------------------------ limiter derivative
+__device__ __forceinline__ double poly_at(const double *c, int k, double xi, double *P)
+{
+    dev_legendre(k, xi, P, nullptr);
+    double s = 0.0;
+    for (int i = 0; i <= k; ++i) s += c[i] * P[i];
+    return s;
+}
+
+// minimum of sum_i c_i phi_i on [-1, 1] and its location
+__device__ double argmin_bin(const double *c, int k, double *xstar)
+{
+    double P[kB];
+    double m = poly_at(c, k, -1.0, P), t;
+    *xstar = -1.0;
+    t = poly_at(c, k, 1.0, P);
+    if (t < m) { m = t; *xstar = 1.0; }
+    double r[2];
+    int nr = 0;
+    if (k == 2 && c[2] != 0.0) r[nr++] = -c[1] / (3.0 * c[2]);
+    if (k == 3) {
+        const double A = 7.5 * c[3], B = 3.0 * c[2], C = c[1] - 1.5 * c[3];
+        if (A == 0.0) {
+            if (B != 0.0) r[nr++] = -C / B;
+        } else {
+            const double disc = B * B - 4.0 * A * C;
+            if (disc >= 0.0) {
+                const double sq = sqrt(disc), qq = -0.5 * (B + copysign(sq, B));
+                if (qq != 0.0) { r[nr++] = qq / A; r[nr++] = C / qq; }
+                else r[nr++] = 0.0;
+            }
+        }
+    }
+    for (int n = 0; n < nr; ++n)
+        if (r[n] > -1.0 && r[n] < 1.0) {
+            t = poly_at(c, k, r[n], P);
+            if (t < m) { m = t; *xstar = r[n]; }
+        }
+    return m;
+}
+
+// lambda_g = (d limit / d g)^T lambda_limited, in place on lam; g is the pre-limiter state
+__global__ void limiter_vjp_kernel(DevGroup G, const double *g, double *lam, int n_cells)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_cells * G.N || G.k == 0 || !G.limiter) return;
+    const long long cell = t / G.N;
+    const int j = (int)(t - cell * G.N), k = G.k;
+    const size_t base = (size_t)cell * G.P + (size_t)j * G.K1;
+    double c[kB], l[kB];
+    for (int i = 0; i <= k; ++i) { c[i] = g[base + i]; l[i] = lam[base + i]; }
+    const double g0 = c[0];
+    if (g0 < 0.0) {                       // gamma = 0: higher modes discarded
+        for (int i = 1; i <= k; ++i) lam[base + i] = 0.0;
+        return;
+    }
+    double xs;
+    const double m = argmin_bin(c, k, &xs);
+    const double den = g0 - m;
+    if (!(den > 0.0) || g0 / den >= 1.0) return;   // gamma = 1: identity
+    const double gamma = g0 / den;
+    double P[kB];
+    dev_legendre(k, xs, P, nullptr);
+    double S = 0.0;
+    for (int i = 1; i <= k; ++i) S += l[i] * c[i];
+    // d gamma / d g^0 = 1 / (g0 - m), d gamma / d g^i = g0 phi_i(xi*) / (g0 - m)^2; written with
+    // S / den and gamma = g0 / den so that tiny bins neither overflow nor produce 0 * inf
+    const double sd = S / den;
+    lam[base] = l[0] + sd;
+    for (int j2 = 1; j2 <= k; ++j2) lam[base + j2] = gamma * l[j2] + sd * gamma * P[j2];
+}
+
+// ------------------------------------------------------------------ small vector kernels
+// out = a * x + b * (y + dt_c * z)   (dt per cell; any of y, z may be null)
+__global__ void axpby_dt_kernel(int P, long long n, double a, const double *x, double b, const double *y,
+                                const double *z, const double *dt, double *out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const long long cell = t / P;
+    double v = y ? y[t] : 0.0;
+    if (z) v += dt[cell] * z[t];
+    out[t] = (x ? a * x[t] : 0.0) + b * v;
+}
+
+// dtheta[cell][ip] += w * dt_c * sum_r mu_r Fp_r
+__global__ void param_dot_kernel(int R, int n_cells, const double *mu, const double *Fp, const double *dt, double w,
+                                 int n_params, int ip, double *dtheta)
+{
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= n_cells) return;
+    double s = 0.0;
+    for (int r = 0; r < R; ++r) s = fma(mu[(size_t)cell * R + r], Fp[(size_t)cell * R + r], s);
+    dtheta[(size_t)cell * n_params + ip] += w * dt[cell] * s;
+}
+
+inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+size_t warp_tile_smem(int P, int arrays, int *wpb)
+{
+    const size_t per = (size_t)P * 32 * sizeof(double) * arrays;
+    int w = (int)((200 * 1024) / per);
+    if (w > 4) w = 4;
+    *wpb = w;
+    return per * (w > 0 ? w : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_jvp_contract(const DevGroup &g, const double *T, const int *qlo, const int *qhi,
+                                const int *prange, const double *a, const double *b, int n, double *F,
+                                cudaStream_t st)
+{
+    int wpb;
+    const size_t smem = warp_tile_smem(g.P, 2, &wpb);
+    if (wpb < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(contract_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    contract_pair_kernel<<<blocks(n, 32 * wpb), 32 * wpb, smem, st>>>(T, qlo, qhi, prange, g.R, g.P, a, b, n, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vjp(const DevGroup &g, const double *T, const int *qlo, const int *qhi, const int *prange,
+                       const double *gst, const double *lambda, double *mu_ws, int n, double *w, cudaStream_t st)
+{
+    dT_lambda_kernel<<<blocks((long long)n * g.R, 256), 256, 0, st>>>(g, lambda, n, mu_ws);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int wpb;
+    const size_t smem = warp_tile_smem(g.P, 2, &wpb);
+    if (wpb < 1) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    vjp_kernel<<<blocks(n, 32 * wpb), 32 * wpb, smem, st>>>(T, qlo, qhi, prange, g.R, g.P, gst, mu_ws, n, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu(const DevGroup &g, const double *lambda, int n, double *mu, cudaStream_t st)
+{
+    dT_lambda_kernel<<<blocks((long long)n * g.R, 256), 256, 0, st>>>(g, lambda, n, mu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_limiter_vjp(const DevGroup &g, const double *gpre, double *lam, int n, cudaStream_t st)
+{
+    limiter_vjp_kernel<<<blocks((long long)n * g.N, 256), 256, 0, st>>>(g, gpre, lam, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby_dt(int P, int n, double a, const double *x, double b, const double *y, const double *z,
+                            const double *dt, double *out, cudaStream_t st)
+{
+    const long long m = (long long)n * P;
+    axpby_dt_kernel<<<blocks(m, 256), 256, 0, st>>>(P, m, a, x, b, y, z, dt, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_param_dot(int R, int n, const double *mu, const double *Fp, const double *dt, double w,
+                             int n_params, int ip, double *dtheta, cudaStream_t st)
+{
+    param_dot_kernel<<<blocks(n, 128), 128, 0, st>>>(R, n, mu, Fp, dt, w, n_params, ip, dtheta);
+    return cudaGetLastError();
+}
+
+}  // namespace grace
+
+// ====================================================================== host side
+namespace grace {
+
+void free_param_derivs(Group &G)
+{
+    for (ParamDeriv &d : G.dparams) {
+        cudaFree(d.d_dT);
+        cudaFree(d.d_qlo);
+        cudaFree(d.d_qhi);
+        cudaFree(d.d_prange);
+    }
+    G.dparams.clear();
+}
+
+namespace {
+
+__global__ void central_diff_kernel(size_t n, const double *a, const double *b, double inv2h, double *out)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (a[i] - b[i]) * inv2h;
+}
+
+double *param_slot(grace_group_desc &d, int id)
+{
+    if (id < 0 || id >= 24) return nullptr;
+    if (id < 8) return &d.coag_p[id];
+    if (id < 16) return &d.frag_p[id - 8];
+    return &d.break_p[id - 16];
+}
+
+// the adjoint calls work on batches of one group in the caller's order
+grace_status single_part(grace_batch *b, const char *who)
+{
+    if (b->parts.size() != 1 || !b->parts[0].direct) {
+        set_error(std::string(who) + ": batches mixing groups are not supported");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    return GRACE_OK;
+}
+
+// one forward SSP-RK3 step in FP64 that keeps the stage states:
+// pre -> gt (limited) -> g1 -> g2 -> next
+cudaError_t fwd_step(grace_batch *b, const double *pre, double *gt, double *g1, double *g2, double *next,
+                     const double *dt)
+{
+    Group &G = b->ctx->groups[0];
+    const DevGroup &dg = G.dg;
+    cudaStream_t st = b->ctx->stream;
+    const int n = b->n_cells;
+    double *dF = b->parts[0].d_F;
+    const size_t bytes = (size_t)n * dg.P * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(gt, pre, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && dg.limiter) e = launch_limit(dg, gt, n, nullptr, nullptr, 0, 0, st);
+    const double *gin[3] = {gt, g1, g2};
+    double *gout[3] = {g1, g2, next};
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
+        e = launch_contract_fp64(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gin[s], n, dF, st);
+        if (e != cudaSuccess) break;
+        UpdateArgs u;
+        u.F = dF;
+        u.gn = gt;
+        u.gs = gin[s];
+        u.gout = gout[s];
+        u.dt = dt;
+        u.a = ca[s];
+        u.b = cb[s];
+        e = launch_update(dg, u, n, st);
+    }
+    return e;
+}
+
+}  // namespace
+}  // namespace grace
+
+using namespace grace;
+
+extern "C" {
+
+grace_status grace_rhs_jvp(grace_batch *b, const double *g, const double *v, double *Jv, int precision)
+{
+    if (!b || !g || !v || !Jv) {
+        set_error("grace_rhs_jvp: null argument");
+        return GRACE_ERR_ARG;
+    }
+    if (precision != GRACE_FP64) {
+        set_error("grace_rhs_jvp: only GRACE_FP64 is implemented");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    grace_status sp = single_part(b, "grace_rhs_jvp");
+    if (sp != GRACE_OK) return sp;
+    Guard guard(b->ctx->device);
+    Group &G = b->ctx->groups[0];
+    cudaStream_t st = b->ctx->stream;
+    double *dF = b->parts[0].d_F;
+    cudaError_t e = launch_jvp_contract(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, v, b->n_cells, dF, st);
+    if (e == cudaSuccess) {
+        UpdateArgs u;
+        u.F = dF;
+        u.gout = Jv;
+        e = launch_update(G.dg, u, b->n_cells, st);
+    }
+    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_jvp");
+}
+
+grace_status grace_rhs_vjp(grace_batch *b, const double *g, const double *lambda, double *w, int precision)
+{
+    if (!b || !g || !lambda || !w) {
+        set_error("grace_rhs_vjp: null argument");
+        return GRACE_ERR_ARG;
+    }
+    if (precision != GRACE_FP64) {
+        set_error("grace_rhs_vjp: only GRACE_FP64 is implemented");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    grace_status sp = single_part(b, "grace_rhs_vjp");
+    if (sp != GRACE_OK) return sp;
+    Guard guard(b->ctx->device);
+    Group &G = b->ctx->groups[0];
+    cudaError_t e = launch_vjp(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, lambda, b->parts[0].d_F, b->n_cells, w,
+                               b->ctx->stream);
+    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_vjp");
+}
+
+grace_status grace_param_grad_setup(grace_ctx *ctx, int group, int n_params, const int *param_ids,
+                                    double rel_step)
+{
+    if (!ctx || group < 0 || group >= (int)ctx->groups.size() || n_params < 0 || (n_params > 0 && !param_ids)) {
+        set_error("grace_param_grad_setup: bad argument");
+        return GRACE_ERR_ARG;
+    }
+    if (!ctx->precomputed) {
+        set_error("grace_param_grad_setup: call grace_precompute first");
+        return GRACE_ERR_ORDER;
+    }
+    if (!(rel_step > 0.0)) rel_step = 1e-5;
+    Guard guard(ctx->device);
+    Group &G = ctx->groups[group];
+    free_param_derivs(G);
+    const DevGroup &dg = G.dg;
+    const size_t nT = (size_t)dg.R * dg.P * dg.P;
+    double *tp = nullptr, *tm = nullptr;
+    cudaError_t e = cudaMalloc(&tp, nT * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&tm, nT * sizeof(double));
+    for (int i = 0; i < n_params && e == cudaSuccess; ++i) {
+        grace_group_desc dplus = G.desc, dminus = G.desc;
+        double *sp = param_slot(dplus, param_ids[i]), *sm = param_slot(dminus, param_ids[i]);
+        if (!sp) {
+            cudaFree(tp);
+            cudaFree(tm);
+            set_error("grace_param_grad_setup: parameter id out of range (0..23)");
+            return GRACE_ERR_ARG;
+        }
+        const double h = *sp != 0.0 ? rel_step * std::fabs(*sp) : rel_step;
+        *sp += h;
+        *sm -= h;
+        ParamDeriv pd;
+        pd.id = param_ids[i];
+        pd.step = h;
+        e = cudaMalloc(&pd.d_dT, nT * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&pd.d_qlo, sizeof(int) * dg.R * dg.P);
+        if (e == cudaSuccess) e = cudaMalloc(&pd.d_qhi, sizeof(int) * dg.R * dg.P);
+        if (e == cudaSuccess) e = cudaMalloc(&pd.d_prange, sizeof(int) * 2 * dg.R);
+        G.dparams.push_back(pd);
+        if (e != cudaSuccess) break;
+        e = launch_build_T(make_devgroup(dplus, G.d_edges), tp, ctx->stream);
+        if (e == cudaSuccess) e = launch_build_T(make_devgroup(dminus, G.d_edges), tm, ctx->stream);
+        if (e == cudaSuccess) {
+            central_diff_kernel<<<1024, 256, 0, ctx->stream>>>(nT, tp, tm, 0.5 / h, pd.d_dT);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = launch_row_extents(dg, pd.d_dT, pd.d_qlo, pd.d_qhi, pd.d_prange, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tp);
+    cudaFree(tm);
+    if (e != cudaSuccess) {
+        free_param_derivs(G);
+        return cuda_fail(e, "grace_param_grad_setup");
+    }
+    return GRACE_OK;
+}
+
+grace_status grace_adjoint(grace_batch *b, const double *g0, const double *dt, int n_steps, int ckpt_every,
+                           const double *lambda_T, double *lambda_0, double *dtheta, int precision)
+{
+    if (!b || !g0 || !dt || !lambda_T || !lambda_0 || n_steps < 0 || ckpt_every < 1) {
+        set_error("grace_adjoint: null argument, negative step count or ckpt_every < 1");
+        return GRACE_ERR_ARG;
+    }
+    if (precision != GRACE_FP64) {
+        set_error("grace_adjoint: only GRACE_FP64 is implemented");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    grace_status sp = single_part(b, "grace_adjoint");
+    if (sp != GRACE_OK) return sp;
+    Guard guard(b->ctx->device);
+    Group &G = b->ctx->groups[0];
+    const DevGroup &dg = G.dg;
+    cudaStream_t st = b->ctx->stream;
+    const int n = b->n_cells, P = dg.P, R = dg.R;
+    double *dF = b->parts[0].d_F;
+    const size_t vec = (size_t)n * P;
+    const int n_ck = n_steps > 0 ? (n_steps + ckpt_every - 1) / ckpt_every : 1;
+    const int np = (int)G.dparams.size();
+    // workspace: checkpoints, per-step (pre, gt, g1, g2) of one segment, 6 adjoint vectors, Fp
+    const size_t need = sizeof(double) * (vec * (size_t)n_ck + vec * 4 * (size_t)ckpt_every + 6 * vec +
+                                          (size_t)n * R);
+    cudaError_t e = cudaSuccess;
+    if (b->adj_bytes < need) {
+        cudaFree(b->d_adj);
+        b->d_adj = nullptr;
+        b->adj_bytes = 0;
+        e = cudaMalloc(&b->d_adj, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("grace_adjoint: workspace allocation failed");
+            return GRACE_ERR_NOMEM;
+        }
+        b->adj_bytes = need;
+    }
+    double *ck = b->d_adj;
+    double *seg = ck + vec * n_ck;
+    double *lam = seg + vec * 4 * ckpt_every;
+    double *lt = lam + vec, *l1 = lt + vec, *l2 = l1 + vec, *tmp = l2 + vec, *cur = tmp + vec;
+    double *Fp = cur + vec;
+    const size_t bytes = vec * sizeof(double);
+    if (dtheta && np > 0) e = cudaMemsetAsync(dtheta, 0, sizeof(double) * n * np, st);
+
+    // forward sweep: checkpoints every ckpt_every steps
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cur, g0, bytes, cudaMemcpyDeviceToDevice, st);
+    for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
+        if (s % ckpt_every == 0) e = cudaMemcpyAsync(ck + vec * (s / ckpt_every), cur, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = fwd_step(b, cur, seg, seg + vec, seg + 2 * vec, cur, dt);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lam, lambda_T, bytes, cudaMemcpyDeviceToDevice, st);
+
+    auto vjp_at = [&](const double *gs, const double *l, double *out) {
+        return launch_vjp(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gs, l, dF, n, out, st);
+    };
+    // dtheta += w dt mu(l) . g^T dT g (mu of the last vjp is in b->d_F)
+    auto param_terms = [&](const double *gs, double w) {
+        cudaError_t r = cudaSuccess;
+        for (int i = 0; i < np && r == cudaSuccess && dtheta; ++i) {
+            const ParamDeriv &pd = G.dparams[i];
+            r = launch_contract_fp64(dg, pd.d_dT, pd.d_qlo, pd.d_qhi, pd.d_prange, gs, n, Fp, st);
+            if (r == cudaSuccess) r = launch_param_dot(R, n, dF, Fp, dt, w, np, i, dtheta, st);
+        }
+        return r;
+    };
+
+    for (int sg = n_ck - 1; sg >= 0 && e == cudaSuccess && n_steps > 0; --sg) {
+        const int s0 = sg * ckpt_every, s1 = std::min(s0 + ckpt_every, n_steps);
+        // recompute the segment, keeping (pre, gt, g1, g2) of every step
+        e = cudaMemcpyAsync(cur, ck + vec * sg, bytes, cudaMemcpyDeviceToDevice, st);
+        for (int s = s0; s < s1 && e == cudaSuccess; ++s) {
+            double *S = seg + vec * 4 * (s - s0);
+            e = cudaMemcpyAsync(S, cur, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = fwd_step(b, S, S + vec, S + 2 * vec, S + 3 * vec, cur, dt);
+        }
+        for (int s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
+            const double *S = seg + vec * 4 * (s - s0);
+            const double *pre = S, *gt = S + vec, *g1 = S + 2 * vec, *g2 = S + 3 * vec;
+            // stage 3: g' = 1/3 gt + 2/3 (g2 + dt L(g2))
+            e = vjp_at(g2, lam, tmp);
+            if (e == cudaSuccess) e = param_terms(g2, 2.0 / 3.0);
+            if (e == cudaSuccess) e = launch_axpby_dt(P, n, 0.0, nullptr, 2.0 / 3.0, lam, tmp, dt, l2, st);
+            if (e == cudaSuccess) e = launch_axpby_dt(P, n, 0.0, nullptr, 1.0 / 3.0, lam, nullptr, dt, lt, st);
+            // stage 2: g2 = 3/4 gt + 1/4 (g1 + dt L(g1))
+            if (e == cudaSuccess) e = vjp_at(g1, l2, tmp);
+            if (e == cudaSuccess) e = param_terms(g1, 0.25);
+            if (e == cudaSuccess) e = launch_axpby_dt(P, n, 0.0, nullptr, 0.25, l2, tmp, dt, l1, st);
+            if (e == cudaSuccess) e = launch_axpby_dt(P, n, 1.0, lt, 0.75, l2, nullptr, dt, lt, st);
+            // stage 1: g1 = gt + dt L(gt)
+            if (e == cudaSuccess) e = vjp_at(gt, l1, tmp);
+            if (e == cudaSuccess) e = param_terms(gt, 1.0);
+            if (e == cudaSuccess) e = launch_axpby_dt(P, n, 1.0, lt, 1.0, l1, tmp, dt, lam, st);
+            // reconstruction (limiter) of this step
+            if (e == cudaSuccess) e = launch_limiter_vjp(dg, pre, lam, n, st);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lambda_0, lam, bytes, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_adjoint");
+}
+
+}  // extern "C"

@@ -97,6 +97,9 @@ DevGroup make_devgroup(const grace_group_desc &d, const double *d_edges)
     if (d.frag_kind == GRACE_FRAG_MAXWELL) g.beta_frag = 1.0 - maxwell_cdf_below(d.frag_p[1], d.frag_p[0]);
     gauss_rule(g.Q, g.gs, g.gw);
     g.edges = d_edges;
+    g.hbin = d_edges ? d_edges + g.N + 1 : nullptr;
+    g.inv_h = d_edges ? d_edges + 2 * g.N + 1 : nullptr;
+    g.inv_h32 = d_edges ? reinterpret_cast<const float *>(d_edges + 3 * g.N + 1) : nullptr;
     return g;
 }
 
@@ -128,21 +131,6 @@ static grace_status validate(const grace_group_desc &d, int idx)
     return GRACE_OK;
 }
 
-struct Guard {   // switches to the context's device for the duration of a call
-    int prev = -1;
-    explicit Guard(int dev)
-    {
-        cudaGetLastError();   // a stale error of an earlier, unrelated call must not be reported as ours
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~Guard()
-    {
-        int cur;
-        if (cudaGetDevice(&cur) == cudaSuccess && prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 static void free_group(Group &G)
 {
     cudaFree(G.d_edges);
@@ -154,6 +142,7 @@ static void free_group(Group &G)
     G.d_T = nullptr;
     G.d_qlo = G.d_qhi = G.d_prange = nullptr;
     for (auto &t : G.tc) free_tc_tiles(t);
+    free_param_derivs(G);
 }
 
 __global__ void count_nnz_kernel(const double *T, size_t n, unsigned long long *out)
@@ -163,31 +152,6 @@ __global__ void count_nnz_kernel(const double *T, size_t n, unsigned long long *
         c += T[i] != 0.0;
     atomicAdd(out, c);
 }
-
-// events around one launch when profiling is enabled
-struct LaunchTimer {
-    grace_ctx *ctx;
-    int kind;
-    cudaEvent_t a = nullptr, b = nullptr;
-    LaunchTimer(grace_ctx *c, int k) : ctx(c), kind(k)
-    {
-        if (!ctx->profiling) return;
-        while (ctx->ev_pool.size() < ctx->ev_used + 2) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return;
-            ctx->ev_pool.push_back(e);
-        }
-        a = ctx->ev_pool[ctx->ev_used++];
-        b = ctx->ev_pool[ctx->ev_used++];
-        cudaEventRecord(a, ctx->stream);
-    }
-    ~LaunchTimer()
-    {
-        if (!a) return;
-        cudaEventRecord(b, ctx->stream);
-        ctx->ev_pairs[kind].push_back({a, b});
-    }
-};
 
 }  // namespace grace
 
@@ -251,9 +215,18 @@ grace_status grace_setup(grace_ctx **out, int n_groups, const grace_group_desc *
                 G.h_edges[j] = G.desc.x_min * std::pow(G.desc.x_max / G.desc.x_min, (double)j / N);
             G.h_edges[0] = G.desc.x_min;
             G.h_edges[N] = G.desc.x_max;
-            e = cudaMalloc(&G.d_edges, sizeof(double) * (N + 1));
+            // one allocation: edges (N+1), h (N), 1/h (N) in FP64, then 1/h (N) in FP32
+            std::vector<double> tab(3 * (size_t)N + 1 + (N + 1) / 2, 0.0);
+            for (int j = 0; j <= N; ++j) tab[j] = G.h_edges[j];
+            for (int j = 0; j < N; ++j) {
+                const double h = G.h_edges[j + 1] - G.h_edges[j];
+                tab[N + 1 + j] = h;
+                tab[2 * N + 1 + j] = 1.0 / h;
+                reinterpret_cast<float *>(tab.data() + 3 * N + 1)[j] = (float)(1.0 / h);
+            }
+            e = cudaMalloc(&G.d_edges, sizeof(double) * tab.size());
             if (e == cudaSuccess)
-                e = cudaMemcpy(G.d_edges, G.h_edges.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice);
+                e = cudaMemcpy(G.d_edges, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) {
                 grace_destroy(ctx);
                 return cuda_fail(e, "grace_setup: edges");
@@ -349,258 +322,6 @@ grace_status grace_group_info(const grace_ctx *ctx, int group, int *n_coef, int 
     return GRACE_OK;
 }
 
-grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group, grace_batch **out)
-{
-    try {
-        if (!ctx || !out || n_cells < 1) {
-            set_error("grace_bind_batch: null context/output or n_cells < 1");
-            return GRACE_ERR_ARG;
-        }
-        *out = nullptr;
-        if (!ctx->precomputed) {
-            set_error("grace_bind_batch: call grace_precompute first");
-            return GRACE_ERR_ORDER;
-        }
-        Guard guard(ctx->device);
-        grace_batch *b = new grace_batch();
-        b->ctx = ctx;
-        b->n_cells = n_cells;
-        b->h_group.assign(n_cells, 0);
-        if (cell_group) {
-            for (int c = 0; c < n_cells; ++c) {
-                if (cell_group[c] < 0 || cell_group[c] >= (int)ctx->groups.size()) {
-                    delete b;
-                    set_error("grace_bind_batch: cell group out of range");
-                    return GRACE_ERR_ARG;
-                }
-                b->h_group[c] = cell_group[c];
-                if (cell_group[c] != 0) b->single_group = 0;
-            }
-        }
-        if (!b->single_group) {
-            delete b;
-            set_error("grace_bind_batch: batches mixing groups are not supported by this build");
-            return GRACE_ERR_UNSUPPORTED;
-        }
-        const DevGroup &g = ctx->groups[0].dg;
-        b->h_off.resize(n_cells + 1);
-        for (int c = 0; c <= n_cells; ++c) b->h_off[c] = (long long)c * g.P;
-        const size_t n = (size_t)n_cells;
-        cudaError_t e = cudaMalloc(&b->d_F, n * g.R * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_g1, n * g.P * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_g2, n * g.P * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
-        if (e == cudaSuccess && (ctx->precision_mask & ((1u << GRACE_TF32) | (1u << GRACE_BF16X3)))) {
-            e = cudaMalloc(&b->d_F32, n * g.R * sizeof(float));
-            if (e == cudaSuccess) e = cudaMemset(b->d_F32, 0, n * g.R * sizeof(float));
-            size_t bytes = 0;
-            for (int prec = GRACE_TF32; prec <= GRACE_BF16X3; ++prec)
-                if (ctx->precision_mask & (1u << prec)) {
-                    int kpad = 0;
-                    size_t s = opA_bytes_for(g, prec, n_cells, &kpad);
-                    if (s > bytes) bytes = s;
-                }
-            if (e == cudaSuccess) e = cudaMalloc(&b->d_opA, bytes);
-            if (e == cudaSuccess) e = cudaMemset(b->d_opA, 0, bytes);
-            b->opA_bytes = bytes;
-        }
-        if (e != cudaSuccess) {
-            grace_batch_destroy(b);
-            cudaGetLastError();
-            set_error(std::string("grace_bind_batch: allocation: ") + cudaGetErrorString(e));
-            return GRACE_ERR_NOMEM;
-        }
-        *out = b;
-        return GRACE_OK;
-    } catch (const std::bad_alloc &) {
-        set_error("grace_bind_batch: host allocation failed");
-        return GRACE_ERR_NOMEM;
-    } catch (...) {
-        set_error("grace_bind_batch: unexpected exception");
-        return GRACE_ERR_ARG;
-    }
-}
-
-grace_status grace_batch_offsets(const grace_batch *b, long long *out)
-{
-    if (!b || !out) {
-        set_error("grace_batch_offsets: null argument");
-        return GRACE_ERR_ARG;
-    }
-    std::memcpy(out, b->h_off.data(), sizeof(long long) * (b->n_cells + 1));
-    return GRACE_OK;
-}
-
-static grace_status check_prec(grace_batch *b, int prec)
-{
-    if (prec < GRACE_FP64 || prec > GRACE_BF16X3) {
-        set_error("unknown precision");
-        return GRACE_ERR_ARG;
-    }
-    if (prec != GRACE_FP64 && !b->ctx->groups[0].tc[prec].built) {
-        set_error("precision not precomputed: pass its bit to grace_precompute before binding the batch");
-        return GRACE_ERR_ORDER;
-    }
-    if (prec != GRACE_FP64 && !b->d_opA) {
-        set_error("batch bound before the tensor-core precompute");
-        return GRACE_ERR_ORDER;
-    }
-    return GRACE_OK;
-}
-
-// F <- functionals of g (FP64 path) or of the packed A operand (tensor path)
-static grace_status contract(grace_batch *b, const double *g, int prec, UpdateArgs &u)
-{
-    Group &G = b->ctx->groups[0];
-    cudaStream_t st = b->ctx->stream;
-    cudaError_t e;
-    LaunchTimer timer(b->ctx, 0);
-    if (prec == GRACE_FP64) {
-        e = launch_contract_fp64(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, b->n_cells, b->d_F, st);
-        u.F = b->d_F;
-        u.F32 = nullptr;
-    } else {
-        e = launch_contract_tc(G.dg, G.tc[prec], prec, b->d_opA, b->n_cells, b->d_F32, b->d_err, st);
-        u.F = nullptr;
-        u.F32 = b->d_F32;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "contraction launch");
-    return GRACE_OK;
-}
-
-grace_status grace_rhs(grace_batch *b, const double *g, double *L, int prec)
-{
-    if (!b || !g || !L) {
-        set_error("grace_rhs: null argument");
-        return GRACE_ERR_ARG;
-    }
-    grace_status s = check_prec(b, prec);
-    if (s != GRACE_OK) return s;
-    Guard guard(b->ctx->device);
-    Group &G = b->ctx->groups[0];
-    cudaStream_t st = b->ctx->stream;
-    if (prec != GRACE_FP64) {
-        cudaError_t e = launch_pack_A(G.dg, g, b->n_cells, b->d_opA, prec, G.tc[prec].k_pad, st);
-        if (e != cudaSuccess) return cuda_fail(e, "grace_rhs: operand pack");
-    }
-    UpdateArgs u;
-    s = contract(b, g, prec, u);
-    if (s != GRACE_OK) return s;
-    u.gout = L;
-    cudaError_t e;
-    {
-        LaunchTimer timer(b->ctx, 1);
-        e = launch_update(G.dg, u, b->n_cells, st);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "grace_rhs: update");
-    return GRACE_OK;
-}
-
-grace_status grace_step(grace_batch *b, double *g, const double *dt, int n_steps, int prec, double *mass,
-                        unsigned char *flags)
-{
-    if (!b || !g || !dt || n_steps < 0) {
-        set_error("grace_step: null argument or negative step count");
-        return GRACE_ERR_ARG;
-    }
-    grace_status s = check_prec(b, prec);
-    if (s != GRACE_OK) return s;
-    Guard guard(b->ctx->device);
-    Group &G = b->ctx->groups[0];
-    const DevGroup &dg = G.dg;
-    cudaStream_t st = b->ctx->stream;
-    const int n = b->n_cells;
-    const bool tc = prec != GRACE_FP64;
-    const int kpad = tc ? G.tc[prec].k_pad : 0;
-    void *opA = tc ? b->d_opA : nullptr;
-    cudaError_t e = cudaSuccess;
-    if (flags) e = cudaMemsetAsync(flags, 0, n, st);
-    if (e != cudaSuccess) return cuda_fail(e, "grace_step: flags");
-    if (n_steps == 0) {
-        if (mass) {
-            e = launch_mass(dg, g, n, mass, st);
-            if (e != cudaSuccess) return cuda_fail(e, "grace_step: mass");
-        }
-        return GRACE_OK;
-    }
-    // reconstruction of the first step (Sec. 3.2.2); later ones are fused into stage 3
-    if (dg.limiter || tc) {
-        DevGroup d0 = dg;
-        e = launch_limit(d0, g, n, flags, opA, prec, kpad, st);
-        if (e != cudaSuccess) return cuda_fail(e, "grace_step: limiter");
-    }
-    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
-    static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
-    for (int step = 0; step < n_steps; ++step) {
-        const bool last = step == n_steps - 1;
-        const double *gin[3] = {g, b->d_g1, b->d_g2};
-        double *gout[3] = {b->d_g1, b->d_g2, g};
-        for (int stage = 0; stage < 3; ++stage) {
-            UpdateArgs u;
-            s = contract(b, gin[stage], prec, u);
-            if (s != GRACE_OK) return s;
-            u.gn = g;
-            u.gs = gin[stage];
-            u.gout = gout[stage];
-            u.dt = dt;
-            u.a = ca[stage];
-            u.b = cb[stage];
-            u.flags = flags;
-            if (stage == 2) {
-                u.apply_limiter = (!last && dg.limiter) ? 1 : 0;
-                u.mass = last ? mass : nullptr;
-            }
-            if (tc && !(stage == 2 && last)) {
-                u.opA = opA;
-                u.opA_prec = prec;
-                u.opA_kpad = kpad;
-            }
-            {
-                LaunchTimer timer(b->ctx, 1);
-                e = launch_update(dg, u, n, st);
-            }
-            if (e != cudaSuccess) return cuda_fail(e, "grace_step: update");
-        }
-    }
-    return GRACE_OK;
-}
-
-grace_status grace_mass(grace_batch *b, const double *g, double *mass)
-{
-    if (!b || !g || !mass) {
-        set_error("grace_mass: null argument");
-        return GRACE_ERR_ARG;
-    }
-    Guard guard(b->ctx->device);
-    cudaError_t e = launch_mass(b->ctx->groups[0].dg, g, b->n_cells, mass, b->ctx->stream);
-    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_mass");
-}
-
-grace_status grace_limit(grace_batch *b, double *g, unsigned char *flags)
-{
-    if (!b || !g) {
-        set_error("grace_limit: null argument");
-        return GRACE_ERR_ARG;
-    }
-    Guard guard(b->ctx->device);
-    cudaError_t e = cudaSuccess;
-    if (flags) e = cudaMemsetAsync(flags, 0, b->n_cells, b->ctx->stream);
-    if (e == cudaSuccess) e = launch_limit(b->ctx->groups[0].dg, g, b->n_cells, flags, nullptr, 0, 0, b->ctx->stream);
-    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_limit");
-}
-
-grace_status grace_project(grace_batch *b, int ic_kind, const double *ic_params, double *g)
-{
-    if (!b || !ic_params || !g || ic_kind < GRACE_IC_EXP || ic_kind > GRACE_IC_FIRST_BIN) {
-        set_error("grace_project: bad argument");
-        return GRACE_ERR_ARG;
-    }
-    Guard guard(b->ctx->device);
-    cudaError_t e = launch_project(b->ctx->groups[0].dg, ic_kind, ic_params, b->n_cells, g, b->ctx->stream);
-    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_project");
-}
-
 grace_status grace_profile_enable(grace_ctx *ctx, int enable)
 {
     if (!ctx) {
@@ -644,40 +365,6 @@ grace_status grace_group_stats(const grace_ctx *ctx, int group, int prec, long l
     if (nnz) *nnz = G.nnz;
     if (tile_macs) *tile_macs = prec == GRACE_FP64 ? G.nnz : G.tc[prec].mac_per_cell;
     return GRACE_OK;
-}
-
-grace_status grace_batch_error(grace_batch *b, int *code)
-{
-    if (!b) {
-        set_error("grace_batch_error: null batch");
-        return GRACE_ERR_ARG;
-    }
-    Guard guard(b->ctx->device);
-    int h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "grace_batch_error");
-    if (code) *code = h;
-    if (h) {
-        set_error("a bounded device wait timed out (code " + std::to_string(h) + ")");
-        return GRACE_ERR_TIMEOUT;
-    }
-    return GRACE_OK;
-}
-
-void grace_batch_destroy(grace_batch *b)
-{
-    if (!b) return;
-    Guard guard(b->ctx->device);
-    cudaFree(b->d_F);
-    cudaFree(b->d_F32);
-    cudaFree(b->d_g1);
-    cudaFree(b->d_g2);
-    cudaFree(b->d_opA);
-    cudaFree(b->d_flags);
-    cudaFree(b->d_err);
-    delete b;
 }
 
 void grace_destroy(grace_ctx *ctx)

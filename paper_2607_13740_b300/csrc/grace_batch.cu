@@ -1,0 +1,538 @@
+// Batches: binding, per-group parts, RHS, SSP-RK3 stepping, mass, limiter,
+// projection, device error word and CUDA-graph replay of grace_step.
+//
+// A batch may mix cells of several groups (different N, k or physics) in any
+// order.  Cells are partitioned by group into parts; each part gathers its
+// cells' rows from the caller's packed layout into contiguous workspaces, runs
+// the group's kernels on its own stream (parts overlap on the GPU), and
+// scatters results back.  A batch whose cells all belong to one group in the
+// caller's order is a single direct part that works on the caller's arrays.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "grace_internal.h"
+#include "grace_tc_layout.cuh"
+
+namespace grace {
+namespace {
+
+__global__ void gather_rows_kernel(int n, int P, const long long *off, const double *src, double *dst)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * P) return;
+    const long long c = t / P;
+    dst[t] = src[off[c] + (t - c * P)];
+}
+
+__global__ void scatter_rows_kernel(int n, int P, const long long *off, const double *src, double *dst)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * P) return;
+    const long long c = t / P;
+    dst[off[c] + (t - c * P)] = src[t];
+}
+
+template <typename T>
+__global__ void gather_kernel(int n, int w, const int *idx, const T *src, T *dst)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * w) return;
+    const long long c = t / w;
+    dst[t] = src[(long long)idx[c] * w + (t - c * w)];
+}
+
+template <typename T>
+__global__ void scatter_kernel(int n, const int *idx, const T *src, T *dst)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dst[idx[t]] = src[t];
+}
+
+inline unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
+
+cudaStream_t part_stream(const grace_batch *b, const Part &p) { return p.direct ? b->ctx->stream : p.stream; }
+
+grace_status fail_cuda(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+
+void free_part(Part &p)
+{
+    cudaFree(p.d_idx);
+    cudaFree(p.d_off);
+    cudaFree(p.d_g);
+    cudaFree(p.d_out);
+    cudaFree(p.d_dt);
+    cudaFree(p.d_mass);
+    cudaFree(p.d_flags);
+    cudaFree(p.d_ic);
+    cudaFree(p.d_F);
+    cudaFree(p.d_F32);
+    cudaFree(p.d_g1);
+    cudaFree(p.d_g2);
+    cudaFree(p.d_opA);
+    if (p.stream) cudaStreamDestroy(p.stream);
+    if (p.done) cudaEventDestroy(p.done);
+    p = Part();
+}
+
+grace_status check_prec(grace_batch *b, int prec)
+{
+    if (prec < GRACE_FP64 || prec > GRACE_BF16X3) {
+        set_error("unknown precision");
+        return GRACE_ERR_ARG;
+    }
+    for (const Part &p : b->parts) {
+        if (prec != GRACE_FP64 && !b->ctx->groups[p.group].tc[prec].built) {
+            set_error("precision not precomputed: pass its bit to grace_precompute before binding the batch");
+            return GRACE_ERR_ORDER;
+        }
+        if (prec != GRACE_FP64 && !p.d_opA) {
+            set_error("batch bound before the tensor-core precompute");
+            return GRACE_ERR_ORDER;
+        }
+    }
+    return GRACE_OK;
+}
+
+// ------------------------------------------------------------------ per-part compute
+cudaError_t part_rhs(grace_batch *b, Part &p, const double *g, double *L, int prec)
+{
+    Group &G = b->ctx->groups[p.group];
+    cudaStream_t st = part_stream(b, p);
+    cudaError_t e;
+    if (prec != GRACE_FP64) {
+        e = launch_pack_A(G.dg, g, p.n, p.d_opA, prec, G.tc[prec].k_pad, st);
+        if (e != cudaSuccess) return e;
+        UpdateArgs u;
+        u.gout = L;
+        LaunchTimer timer(b->ctx, 0, st);
+        return launch_contract_tc(G.dg, G.tc[prec], prec, p.d_opA, p.n, p.d_F32, b->d_err, st, 1, &u);
+    }
+    {
+        LaunchTimer timer(b->ctx, 0, st);
+        e = launch_contract_fp64(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, p.n, p.d_F, st);
+    }
+    if (e != cudaSuccess) return e;
+    UpdateArgs u;
+    u.F = p.d_F;
+    u.gout = L;
+    LaunchTimer timer(b->ctx, 1, st);
+    return launch_update(G.dg, u, p.n, st);
+}
+
+cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int n_steps, int prec, double *mass,
+                      unsigned char *flags)
+{
+    Group &G = b->ctx->groups[p.group];
+    const DevGroup &dg = G.dg;
+    cudaStream_t st = part_stream(b, p);
+    const int n = p.n;
+    const bool tc = prec != GRACE_FP64;
+    const int kpad = tc ? G.tc[prec].k_pad : 0;
+    void *opA = tc ? p.d_opA : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (flags) e = cudaMemsetAsync(flags, 0, n, st);
+    if (e != cudaSuccess) return e;
+    if (n_steps == 0) return mass ? launch_mass(dg, g, n, mass, st) : cudaSuccess;
+    // reconstruction of the first step (Sec. 3.2.2); later ones are fused into stage 3
+    if (dg.limiter || tc) {
+        e = launch_limit(dg, g, n, flags, opA, prec, kpad, st);
+        if (e != cudaSuccess) return e;
+    }
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int step = 0; step < n_steps; ++step) {
+        const bool last = step == n_steps - 1;
+        const double *gin[3] = {g, p.d_g1, p.d_g2};
+        double *gout[3] = {p.d_g1, p.d_g2, g};
+        for (int stage = 0; stage < 3; ++stage) {
+            UpdateArgs u;
+            u.gn = g;
+            u.gs = gin[stage];
+            u.gout = gout[stage];
+            u.dt = dt;
+            u.a = ca[stage];
+            u.b = cb[stage];
+            u.flags = flags;
+            if (stage == 2) {
+                u.apply_limiter = (!last && dg.limiter) ? 1 : 0;
+                u.mass = last ? mass : nullptr;
+            }
+            if (tc) {
+                // tcgen05 contraction with the flux difference / RK stage fused into its epilogue;
+                // the next stage's A operand is rewritten in place
+                u.opA = (stage == 2 && last) ? nullptr : opA;
+                LaunchTimer timer(b->ctx, 0, st);
+                e = launch_contract_tc(dg, G.tc[prec], prec, opA, n, p.d_F32, b->d_err, st, 2, &u);
+            } else {
+                {
+                    LaunchTimer timer(b->ctx, 0, st);
+                    e = launch_contract_fp64(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gin[stage], n, p.d_F, st);
+                }
+                if (e != cudaSuccess) return e;
+                u.F = p.d_F;
+                LaunchTimer timer(b->ctx, 1, st);
+                e = launch_update(dg, u, n, st);
+            }
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+// runs fn(part, stream) for every part: direct parts on the context stream, the
+// others on their own streams forked from and joined back to it
+template <typename Fn>
+cudaError_t for_parts(grace_batch *b, Fn fn)
+{
+    cudaStream_t st = b->ctx->stream;
+    cudaError_t e = cudaSuccess;
+    const bool fork = !(b->parts.size() == 1 && b->parts[0].direct);
+    if (fork) e = cudaEventRecord(b->fork, st);
+    for (Part &p : b->parts) {
+        if (e != cudaSuccess) break;
+        if (!p.direct) e = cudaStreamWaitEvent(p.stream, b->fork, 0);
+        if (e == cudaSuccess) e = fn(p, part_stream(b, p));
+        if (e == cudaSuccess && !p.direct) e = cudaEventRecord(p.done, p.stream);
+    }
+    if (fork)
+        for (Part &p : b->parts)
+            if (e == cudaSuccess && !p.direct) e = cudaStreamWaitEvent(st, p.done, 0);
+    return e;
+}
+
+cudaError_t gather_state(const Part &p, int P, const double *src, double *dst, cudaStream_t st)
+{
+    gather_rows_kernel<<<nb((long long)p.n * P), 256, 0, st>>>(p.n, P, p.d_off, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t scatter_state(const Part &p, int P, const double *src, double *dst, cudaStream_t st)
+{
+    scatter_rows_kernel<<<nb((long long)p.n * P), 256, 0, st>>>(p.n, P, p.d_off, src, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace grace
+
+using namespace grace;
+
+extern "C" {
+
+grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group, grace_batch **out)
+{
+    try {
+        if (!ctx || !out || n_cells < 1) {
+            set_error("grace_bind_batch: null context/output or n_cells < 1");
+            return GRACE_ERR_ARG;
+        }
+        *out = nullptr;
+        if (!ctx->precomputed) {
+            set_error("grace_bind_batch: call grace_precompute first");
+            return GRACE_ERR_ORDER;
+        }
+        Guard guard(ctx->device);
+        grace_batch *b = new grace_batch();
+        b->ctx = ctx;
+        b->n_cells = n_cells;
+        b->h_group.assign(n_cells, 0);
+        const int ng = (int)ctx->groups.size();
+        if (cell_group)
+            for (int c = 0; c < n_cells; ++c) {
+                if (cell_group[c] < 0 || cell_group[c] >= ng) {
+                    delete b;
+                    set_error("grace_bind_batch: cell group out of range");
+                    return GRACE_ERR_ARG;
+                }
+                b->h_group[c] = cell_group[c];
+            }
+        b->h_off.resize(n_cells + 1);
+        b->h_off[0] = 0;
+        for (int c = 0; c < n_cells; ++c) b->h_off[c + 1] = b->h_off[c] + ctx->groups[b->h_group[c]].dg.P;
+        // one part per group present
+        std::vector<std::vector<int>> members(ng);
+        for (int c = 0; c < n_cells; ++c) members[b->h_group[c]].push_back(c);
+        int present = 0;
+        for (int gi = 0; gi < ng; ++gi) present += !members[gi].empty();
+        const bool direct = present == 1 && members[b->h_group[0]].size() == (size_t)n_cells;
+        cudaError_t e = cudaMalloc(&b->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        const bool tc_any = (ctx->precision_mask & ((1u << GRACE_TF32) | (1u << GRACE_BF16X3))) != 0;
+        for (int gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+            if (members[gi].empty()) continue;
+            b->parts.emplace_back();
+            Part &p = b->parts.back();
+            p.group = gi;
+            p.n = (int)members[gi].size();
+            p.direct = direct;
+            const DevGroup &g = ctx->groups[gi].dg;
+            const size_t n = (size_t)p.n;
+            e = cudaMalloc(&p.d_F, n * g.R * sizeof(double));
+            if (e == cudaSuccess) e = cudaMalloc(&p.d_g1, n * g.P * sizeof(double));
+            if (e == cudaSuccess) e = cudaMalloc(&p.d_g2, n * g.P * sizeof(double));
+            if (e == cudaSuccess && !direct) {
+                std::vector<long long> off(n);
+                for (size_t c = 0; c < n; ++c) off[c] = b->h_off[members[gi][c]];
+                e = cudaMalloc(&p.d_idx, n * sizeof(int));
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_off, n * sizeof(long long));
+                if (e == cudaSuccess) e = cudaMemcpy(p.d_idx, members[gi].data(), n * sizeof(int), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess) e = cudaMemcpy(p.d_off, off.data(), n * sizeof(long long), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_g, n * g.P * sizeof(double));
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_out, n * g.P * sizeof(double));
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_dt, n * sizeof(double));
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_mass, n * sizeof(double));
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_flags, n);
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_ic, n * 4 * sizeof(double));
+                if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming);
+            }
+            if (e == cudaSuccess && tc_any) {
+                e = cudaMalloc(&p.d_F32, n * g.R * sizeof(float));
+                if (e == cudaSuccess) e = cudaMemset(p.d_F32, 0, n * g.R * sizeof(float));
+                size_t bytes = 0;
+                for (int prec = GRACE_TF32; prec <= GRACE_BF16X3; ++prec)
+                    if (ctx->precision_mask & (1u << prec)) bytes = std::max(bytes, opA_bytes_for(g, prec, p.n, nullptr));
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_opA, bytes);
+                if (e == cudaSuccess) e = cudaMemset(p.d_opA, 0, bytes);
+                p.opA_bytes = bytes;
+            }
+        }
+        if (e != cudaSuccess) {
+            grace_batch_destroy(b);
+            cudaGetLastError();
+            set_error(std::string("grace_bind_batch: allocation: ") + cudaGetErrorString(e));
+            return GRACE_ERR_NOMEM;
+        }
+        *out = b;
+        return GRACE_OK;
+    } catch (const std::bad_alloc &) {
+        set_error("grace_bind_batch: host allocation failed");
+        return GRACE_ERR_NOMEM;
+    } catch (...) {
+        set_error("grace_bind_batch: unexpected exception");
+        return GRACE_ERR_ARG;
+    }
+}
+
+grace_status grace_batch_offsets(const grace_batch *b, long long *out)
+{
+    if (!b || !out) {
+        set_error("grace_batch_offsets: null argument");
+        return GRACE_ERR_ARG;
+    }
+    std::memcpy(out, b->h_off.data(), sizeof(long long) * (b->n_cells + 1));
+    return GRACE_OK;
+}
+
+grace_status grace_rhs(grace_batch *b, const double *g, double *L, int prec)
+{
+    if (!b || !g || !L) {
+        set_error("grace_rhs: null argument");
+        return GRACE_ERR_ARG;
+    }
+    grace_status s = check_prec(b, prec);
+    if (s != GRACE_OK) return s;
+    Guard guard(b->ctx->device);
+    cudaError_t e = for_parts(b, [&](Part &p, cudaStream_t st) {
+        if (p.direct) return part_rhs(b, p, g, L, prec);
+        const int P = b->ctx->groups[p.group].dg.P;
+        cudaError_t r = gather_state(p, P, g, p.d_g, st);
+        if (r == cudaSuccess) r = part_rhs(b, p, p.d_g, p.d_out, prec);
+        if (r == cudaSuccess) r = scatter_state(p, P, p.d_out, L, st);
+        return r;
+    });
+    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs");
+}
+
+static cudaError_t step_body(grace_batch *b, double *g, const double *dt, int n_steps, int prec, double *mass,
+                             unsigned char *flags)
+{
+    return for_parts(b, [&](Part &p, cudaStream_t st) {
+        if (p.direct) return part_step(b, p, g, dt, n_steps, prec, mass, flags);
+        const int P = b->ctx->groups[p.group].dg.P;
+        cudaError_t r = gather_state(p, P, g, p.d_g, st);
+        if (r == cudaSuccess) {
+            gather_kernel<double><<<nb(p.n), 256, 0, st>>>(p.n, 1, p.d_idx, dt, p.d_dt);
+            r = cudaGetLastError();
+        }
+        if (r == cudaSuccess)
+            r = part_step(b, p, p.d_g, p.d_dt, n_steps, prec, mass ? p.d_mass : nullptr, flags ? p.d_flags : nullptr);
+        if (r == cudaSuccess) r = scatter_state(p, P, p.d_g, g, st);
+        if (r == cudaSuccess && mass) {
+            scatter_kernel<double><<<nb(p.n), 256, 0, st>>>(p.n, p.d_idx, p.d_mass, mass);
+            r = cudaGetLastError();
+        }
+        if (r == cudaSuccess && flags) {
+            scatter_kernel<unsigned char><<<nb(p.n), 256, 0, st>>>(p.n, p.d_idx, p.d_flags, flags);
+            r = cudaGetLastError();
+        }
+        return r;
+    });
+}
+
+grace_status grace_step(grace_batch *b, double *g, const double *dt, int n_steps, int prec, double *mass,
+                        unsigned char *flags)
+{
+    if (!b || !g || !dt || n_steps < 0) {
+        set_error("grace_step: null argument or negative step count");
+        return GRACE_ERR_ARG;
+    }
+    grace_status s = check_prec(b, prec);
+    if (s != GRACE_OK) return s;
+    Guard guard(b->ctx->device);
+    cudaError_t e = cudaSuccess;
+    if (!b->use_graph) {
+        e = step_body(b, g, dt, n_steps, prec, mass, flags);
+        return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_step");
+    }
+    // CUDA graph: capture the whole call once per argument set, then replay it
+    const void *key[4] = {g, dt, mass, flags};
+    const bool same = b->graph && b->graph_steps == n_steps && b->graph_prec == prec &&
+                      std::equal(key, key + 4, b->graph_key);
+    cudaStream_t st = b->ctx->stream;
+    if (!same) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        if (!st) {
+            set_error("grace_step: graph replay needs a non-default stream (grace_set_stream)");
+            return GRACE_ERR_ARG;
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            b->ctx->capturing = 1;
+            cudaError_t body = step_body(b, g, dt, n_steps, prec, mass, flags);
+            b->ctx->capturing = 0;
+            e = cudaStreamEndCapture(st, &graph);
+            if (body != cudaSuccess) e = body;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return cuda_fail(e, "grace_step: graph capture");
+        }
+        std::copy(key, key + 4, b->graph_key);
+        b->graph_steps = n_steps;
+        b->graph_prec = prec;
+    }
+    e = cudaGraphLaunch(b->graph, st);
+    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_step: graph launch");
+}
+
+grace_status grace_batch_set_graph(grace_batch *b, int enable)
+{
+    if (!b) {
+        set_error("grace_batch_set_graph: null batch");
+        return GRACE_ERR_ARG;
+    }
+    b->use_graph = enable ? 1 : 0;
+    if (!enable && b->graph) {
+        Guard guard(b->ctx->device);
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return GRACE_OK;
+}
+
+grace_status grace_mass(grace_batch *b, const double *g, double *mass)
+{
+    if (!b || !g || !mass) {
+        set_error("grace_mass: null argument");
+        return GRACE_ERR_ARG;
+    }
+    Guard guard(b->ctx->device);
+    cudaError_t e = for_parts(b, [&](Part &p, cudaStream_t st) {
+        const DevGroup &dg = b->ctx->groups[p.group].dg;
+        if (p.direct) return launch_mass(dg, g, p.n, mass, st);
+        cudaError_t r = gather_state(p, dg.P, g, p.d_g, st);
+        if (r == cudaSuccess) r = launch_mass(dg, p.d_g, p.n, p.d_mass, st);
+        if (r == cudaSuccess) {
+            scatter_kernel<double><<<nb(p.n), 256, 0, st>>>(p.n, p.d_idx, p.d_mass, mass);
+            r = cudaGetLastError();
+        }
+        return r;
+    });
+    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_mass");
+}
+
+grace_status grace_limit(grace_batch *b, double *g, unsigned char *flags)
+{
+    if (!b || !g) {
+        set_error("grace_limit: null argument");
+        return GRACE_ERR_ARG;
+    }
+    Guard guard(b->ctx->device);
+    cudaError_t e = for_parts(b, [&](Part &p, cudaStream_t st) {
+        const DevGroup &dg = b->ctx->groups[p.group].dg;
+        double *gs = p.direct ? g : p.d_g;
+        unsigned char *fl = flags ? (p.direct ? flags : p.d_flags) : nullptr;
+        cudaError_t r = cudaSuccess;
+        if (!p.direct) r = gather_state(p, dg.P, g, p.d_g, st);
+        if (r == cudaSuccess && fl) r = cudaMemsetAsync(fl, 0, p.n, st);
+        if (r == cudaSuccess) r = launch_limit(dg, gs, p.n, fl, nullptr, 0, 0, st);
+        if (r == cudaSuccess && !p.direct) r = scatter_state(p, dg.P, p.d_g, g, st);
+        if (r == cudaSuccess && fl && !p.direct) {
+            scatter_kernel<unsigned char><<<nb(p.n), 256, 0, st>>>(p.n, p.d_idx, p.d_flags, flags);
+            r = cudaGetLastError();
+        }
+        return r;
+    });
+    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_limit");
+}
+
+grace_status grace_project(grace_batch *b, int ic_kind, const double *ic_params, double *g)
+{
+    if (!b || !ic_params || !g || ic_kind < GRACE_IC_EXP || ic_kind > GRACE_IC_FIRST_BIN) {
+        set_error("grace_project: bad argument");
+        return GRACE_ERR_ARG;
+    }
+    Guard guard(b->ctx->device);
+    cudaError_t e = for_parts(b, [&](Part &p, cudaStream_t st) {
+        const DevGroup &dg = b->ctx->groups[p.group].dg;
+        if (p.direct) return launch_project(dg, ic_kind, ic_params, p.n, g, st);
+        gather_kernel<double><<<nb((long long)p.n * 4), 256, 0, st>>>(p.n, 4, p.d_idx, ic_params, p.d_ic);
+        cudaError_t r = cudaGetLastError();
+        if (r == cudaSuccess) r = launch_project(dg, ic_kind, p.d_ic, p.n, p.d_g, st);
+        if (r == cudaSuccess) r = scatter_state(p, dg.P, p.d_g, g, st);
+        return r;
+    });
+    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_project");
+}
+
+grace_status grace_batch_error(grace_batch *b, int *code)
+{
+    if (!b) {
+        set_error("grace_batch_error: null batch");
+        return GRACE_ERR_ARG;
+    }
+    Guard guard(b->ctx->device);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grace_batch_error");
+    if (code) *code = h;
+    if (h) {
+        set_error("a bounded device wait timed out (code " + std::to_string(h) + ")");
+        return GRACE_ERR_TIMEOUT;
+    }
+    return GRACE_OK;
+}
+
+void grace_batch_destroy(grace_batch *b)
+{
+    if (!b) return;
+    Guard guard(b->ctx->device);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (Part &p : b->parts) free_part(p);
+    cudaFree(b->d_err);
+    cudaFree(b->d_adj);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+}  // extern "C"

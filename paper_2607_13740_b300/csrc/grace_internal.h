@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/grace.h"
+#include "grace.h"
 
 namespace grace {
 
@@ -22,6 +22,9 @@ struct DevGroup {
     double beta_coag, beta_frag;     // Maxwellian probabilities (constant dv_rms)
     double gs[kQMax], gw[kQMax];     // Gauss-Legendre rule with Q points on [-1, 1]
     const double *edges;             // device, N+1 bin edges x_{j-1/2}
+    const double *hbin;              // device, N bin widths h_j
+    const double *inv_h;             // device, N values 1 / h_j
+    const float *inv_h32;            // device, N values 1 / h_j in FP32
 };
 
 // Tensor-core operand tiles of one group for one precision (built by precompute).
@@ -29,10 +32,19 @@ struct TcTiles {
     int built = 0;
     int n_tiles = 0;          // N-tiles (bin group x p-window)
     int k_pad = 0;            // padded K extent of the A operand (elements)
+    int max_rows = 0;         // largest MMA N over the tiles
     void *d_b = nullptr;      // pre-swizzled B tiles (all tiles back to back)
     void *d_desc = nullptr;   // per-tile descriptors
     size_t b_bytes = 0;
     long long mac_per_cell = 0;   // executed MACs per cell and RHS (tile shapes)
+};
+
+// d T / d theta for one kernel parameter (central difference of the FP64 precompute)
+struct ParamDeriv {
+    int id = -1;                  // 0..7 coag_p, 8..15 frag_p, 16..23 break_p
+    double step = 0.0;
+    double *d_dT = nullptr;       // [R][P][P]
+    int *d_qlo = nullptr, *d_qhi = nullptr, *d_prange = nullptr;
 };
 
 struct Group {
@@ -46,6 +58,7 @@ struct Group {
     int *d_prange = nullptr;      // [R][2] p range with non-empty rows
     long long nnz = 0;            // structural non-zeros of T (all rows)
     TcTiles tc[3];                // indexed by grace_precision
+    std::vector<ParamDeriv> dparams;
 };
 
 }  // namespace grace
@@ -61,23 +74,53 @@ struct grace_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pairs[2];
     size_t ev_used = 0;
+    int capturing = 0;              // a CUDA graph capture is in progress
 };
+
+namespace grace {
+
+// The cells of one group inside a batch.  A "direct" part is a batch whose cells
+// all belong to one group and sit in the caller's order: the caller's arrays
+// are the part's state.  Otherwise the part gathers its cells' rows from the
+// caller's packed layout into contiguous workspaces and scatters results back.
+struct Part {
+    int group = 0;
+    int n = 0;
+    bool direct = true;
+    int *d_idx = nullptr;          // [n] caller cell index of each part cell
+    long long *d_off = nullptr;    // [n] caller offset (doubles) of each part cell
+    double *d_g = nullptr;         // [n][P] gathered state
+    double *d_out = nullptr;       // [n][P] gathered output (RHS)
+    double *d_dt = nullptr;        // [n]
+    double *d_mass = nullptr;      // [n]
+    unsigned char *d_flags = nullptr;  // [n]
+    double *d_ic = nullptr;        // [n][4]
+    double *d_F = nullptr;         // [n][R] functionals, FP64
+    float *d_F32 = nullptr;        // [n][R] functionals from the tensor path
+    double *d_g1 = nullptr, *d_g2 = nullptr;   // stage states
+    void *d_opA = nullptr;         // tensor-core A operand of the current stage
+    size_t opA_bytes = 0;
+    cudaStream_t stream = nullptr; // own stream for concurrent parts (null: the context's)
+    cudaEvent_t done = nullptr;
+};
+
+}  // namespace grace
 
 struct grace_batch {
     grace_ctx *ctx = nullptr;
     int n_cells = 0;
-    int single_group = 1;          // all cells in group 0 with the plain packed layout
     std::vector<int> h_group;
     std::vector<long long> h_off;
-    // workspaces (device)
-    double *d_F = nullptr;         // [n_cells][R] flux functionals, FP64
-    float *d_F32 = nullptr;        // [n_cells][R] flux functionals from the tensor path
-    double *d_g1 = nullptr;        // stage states
-    double *d_g2 = nullptr;
-    void *d_opA = nullptr;         // tensor-core A operand tiles (current stage)
-    size_t opA_bytes = 0;
-    unsigned char *d_flags = nullptr;
+    std::vector<grace::Part> parts;
     int *d_err = nullptr;          // device error word (bounded waits)
+    double *d_adj = nullptr;       // adjoint workspace (checkpoints, stage states, adjoints)
+    size_t adj_bytes = 0;
+    cudaEvent_t fork = nullptr;
+    // CUDA graph of one grace_step call (grace_batch_set_graph)
+    int use_graph = 0;
+    cudaGraphExec_t graph = nullptr;
+    const void *graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int graph_steps = -1, graph_prec = -1;
 };
 
 namespace grace {
@@ -85,6 +128,22 @@ namespace grace {
 // thread-local error detail
 void set_error(const std::string &msg);
 grace_status cuda_fail(cudaError_t e, const char *where);
+
+// switches to a device for the duration of an ABI call and clears stale errors
+struct Guard {
+    int prev = -1;
+    explicit Guard(int dev)
+    {
+        cudaGetLastError();
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~Guard()
+    {
+        int cur;
+        if (cudaGetDevice(&cur) == cudaSuccess && prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 // host helpers
 void gauss_rule(int Q, double *s, double *w);
@@ -116,6 +175,10 @@ struct UpdateArgs {
     int opA_kpad = 0;
 };
 cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st);
+// tcgen05 contraction; mode 0 writes the functionals to d_F32, mode 1 the RHS L
+// to u->gout, mode 2 performs the SSP-RK3 stage update of u (fused epilogue)
+cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, int n_cells,
+                               float *d_F32, int *d_err, cudaStream_t st, int mode, const UpdateArgs *u);
 cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned char *flags,
                          void *opA, int opA_prec, int opA_kpad, cudaStream_t st);
 cudaError_t launch_mass(const DevGroup &g, const double *d_g, int n_cells, double *mass,
@@ -125,11 +188,49 @@ cudaError_t launch_project(const DevGroup &g, int ic_kind, const double *ic, int
 cudaError_t launch_pack_A(const DevGroup &g, const double *d_g, int n_cells, void *opA, int prec,
                           int kpad, cudaStream_t st);
 
+// events recorded around one launch when the context's profiling is on
+struct LaunchTimer {
+    grace_ctx *ctx;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchTimer(grace_ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
+    {
+        if (!ctx->profiling || ctx->capturing) return;
+        while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            ctx->ev_pool.push_back(e);
+        }
+        a = ctx->ev_pool[ctx->ev_used++];
+        b = ctx->ev_pool[ctx->ev_used++];
+        cudaEventRecord(a, st);
+    }
+    ~LaunchTimer()
+    {
+        if (!a) return;
+        cudaEventRecord(b, st);
+        ctx->ev_pairs[kind].push_back({a, b});
+    }
+};
+
+// adjoint (grace_adjoint.cu)
+cudaError_t launch_jvp_contract(const DevGroup &g, const double *T, const int *qlo, const int *qhi,
+                                const int *prange, const double *a, const double *b, int n, double *F,
+                                cudaStream_t st);
+cudaError_t launch_vjp(const DevGroup &g, const double *T, const int *qlo, const int *qhi, const int *prange,
+                       const double *gst, const double *lambda, double *mu_ws, int n, double *w, cudaStream_t st);
+cudaError_t launch_limiter_vjp(const DevGroup &g, const double *gpre, double *lam, int n, cudaStream_t st);
+cudaError_t launch_axpby_dt(int P, int n, double a, const double *x, double b, const double *y, const double *z,
+                            const double *dt, double *out, cudaStream_t st);
+cudaError_t launch_param_dot(int R, int n, const double *mu, const double *Fp, const double *dt, double w,
+                             int n_params, int ip, double *dtheta, cudaStream_t st);
+void free_param_derivs(Group &G);
+
 // tensor-core path
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);
 void free_tc_tiles(TcTiles &t);
 size_t opA_bytes_for(const DevGroup &g, int prec, int n_cells, int *kpad);
-cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA,
-                               int n_cells, float *d_F32, int *d_err, cudaStream_t st);
+
 
 }  // namespace grace

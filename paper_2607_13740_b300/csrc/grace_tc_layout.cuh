@@ -15,7 +15,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
-#include "../../include/grace.h"
+#include "grace.h"
 
 namespace grace {
 

@@ -9,7 +9,7 @@
 // i = 0 row only ever sees F(x_{j-1/2}) - F(x_{j+1/2}), so the sum of h_j L_j^0
 // telescopes and the mass is conserved to round-off whatever precision the
 // functionals came from.
-#include "grace_physics.cuh"
+#include "grace_limiter.cuh"
 #include "grace_tc_layout.cuh"
 
 namespace grace {
@@ -17,69 +17,6 @@ namespace grace {
 namespace {
 
 constexpr int kB = kKMax + 1;
-
-__device__ __forceinline__ double poly(const double *c, int k, double xi)
-{
-    double P[kB];
-    dev_legendre(k, xi, P, nullptr);
-    double s = 0.0;
-    for (int i = 0; i <= k; ++i) s += c[i] * P[i];
-    return s;
-}
-
-// minimum over [-1, 1] of sum_i c_i phi_i: endpoints and interior stationary points
-__device__ double bin_minimum(const double *c, int k)
-{
-    if (k == 0) return c[0];
-    double m = fmin(poly(c, k, -1.0), poly(c, k, 1.0));
-    if (k == 2 && c[2] != 0.0) {
-        const double xs = -c[1] / (3.0 * c[2]);          // phi_1' = 1, phi_2' = 3 xi
-        if (xs > -1.0 && xs < 1.0) m = fmin(m, poly(c, k, xs));
-    } else if (k == 3) {
-        // derivative 7.5 c3 xi^2 + 3 c2 xi + (c1 - 1.5 c3)
-        const double A = 7.5 * c[3], B = 3.0 * c[2], C = c[1] - 1.5 * c[3];
-        double r0 = 2.0, r1 = 2.0;
-        if (A == 0.0) {
-            if (B != 0.0) r0 = -C / B;
-        } else {
-            const double disc = B * B - 4.0 * A * C;
-            if (disc >= 0.0) {
-                const double sq = sqrt(disc);
-                const double qq = -0.5 * (B + copysign(sq, B));
-                if (qq != 0.0) {
-                    r0 = qq / A;
-                    r1 = C / qq;
-                } else {
-                    r0 = 0.0;
-                }
-            }
-        }
-        if (r0 > -1.0 && r0 < 1.0) m = fmin(m, poly(c, k, r0));
-        if (r1 > -1.0 && r1 < 1.0) m = fmin(m, poly(c, k, r1));
-    }
-    return m;
-}
-
-// eq. (recon) with gamma from eq. (gamma); returns flag bits
-__device__ __forceinline__ unsigned limit_bin(double *c, int k)
-{
-    if (k == 0) return 0u;
-    const double gbar = c[0];
-    double gamma;
-    unsigned f = 0u;
-    if (gbar < 0.0) {
-        gamma = 0.0;
-        f |= GRACE_FLAG_NEGATIVE_MEAN;
-    } else {
-        const double den = gbar - bin_minimum(c, k);
-        gamma = den > 0.0 ? fmin(gbar / den, 1.0) : 1.0;
-    }
-    if (gamma < 1.0) {
-        f |= GRACE_FLAG_LIMITED;
-        for (int i = 1; i <= k; ++i) c[i] *= gamma;
-    }
-    return f;
-}
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -93,79 +30,144 @@ __device__ __forceinline__ unsigned warp_or(unsigned v)
     return v;
 }
 
+// Writes one cell's new coefficients, staged in shared memory, to the FP64 state
+// (coalesced) and, if requested, to the cell's row of the tensor-core A operand
+// as whole 16-byte chunks (TF32: 4 values, BF16: 8 hi + 8 lo values per chunk).
+__device__ __forceinline__ void write_row(const DevGroup &G, const double *row, long long cell, double *gout,
+                                          void *opA, int prec, int kpad, int lane)
+{
+    const int P = G.P;
+    if (gout)
+        for (int i = lane; i < P; i += 32) gout[(size_t)cell * P + i] = row[i];
+    if (!opA) return;
+    const long long tile = cell / kTileM;
+    const int r = (int)(cell - tile * kTileM);
+    char *t = (char *)opA + (size_t)tile * opA_tile_bytes(prec, kpad);
+    if (prec == GRACE_TF32) {
+        for (int c = lane; c * 4 < P; c += 32) {
+            uint32_t w[4];
+            for (int e = 0; e < 4; ++e) {
+                const int k = 4 * c + e;
+                w[e] = k < P ? f32_to_tf32_rna((float)(row[k] * G.hbin[k / G.K1])) : 0u;
+            }
+            *reinterpret_cast<uint4 *>(t + swz_offset(kTileM, r, 4 * c, 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        const size_t plane = (size_t)kTileM * kpad * 2;
+        for (int c = lane; c * 8 < P; c += 32) {
+            uint32_t hi[4], lo[4];
+            for (int e = 0; e < 4; ++e) {
+                uint32_t h2[2], l2[2];
+                for (int u = 0; u < 2; ++u) {
+                    const int k = 8 * c + 2 * e + u;
+                    const double v = k < P ? row[k] * G.hbin[k / G.K1] : 0.0;
+                    const __nv_bfloat16 h = __double2bfloat16(v);
+                    const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
+                    h2[u] = (uint32_t)__bfloat16_as_ushort(h);
+                    l2[u] = (uint32_t)__bfloat16_as_ushort(l);
+                }
+                hi[e] = h2[0] | (h2[1] << 16);
+                lo[e] = l2[0] | (l2[1] << 16);
+            }
+            const size_t off = swz_offset(kTileM, r, 8 * c, 2);
+            *reinterpret_cast<uint4 *>(t + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4 *>(t + plane + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+
+// FT = double: FP64 functionals, everything in FP64 (the plain path).
+// FT = float: functionals from the tensor path; the i = 0 row (flux difference,
+// stage combination, mass) stays FP64 so the telescoping sum conserves mass to
+// FP64 round-off, the i >= 1 rows are formed in FP32 (their error is far below
+// that of the reduced-precision contraction they come from).
+// One warp per cell; the new row is staged in shared memory and written out
+// coalesced.
+template <typename FT>
 __global__ void __launch_bounds__(256) update_kernel(DevGroup G, UpdateArgs A, int n_cells)
 {
+    extern __shared__ double rows[];
     const long long cell = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (cell >= n_cells) return;
     const int N = G.N, k = G.k, K1 = G.K1, R = G.R, P = G.P;
-    const double *Fd = A.F ? A.F + cell * R : nullptr;
-    const float *Ff = A.F32 ? A.F32 + cell * R : nullptr;
-    const double dt = A.dt ? A.dt[cell] : 0.0;
+    double *row = rows + (size_t)(threadIdx.x >> 5) * P;
+    const FT *F = (const FT *)(sizeof(FT) == 8 ? (const void *)A.F : (const void *)A.F32) + cell * R;
+    const bool step = A.dt != nullptr;
+    const double dt = step ? A.dt[cell] : 0.0;
     double msum = 0.0;
     unsigned fl = 0u;
     for (int j = lane; j < N; j += 32) {
-        auto Fr = [&](int r) -> double { return Fd ? Fd[r] : (double)Ff[r]; };
-        const double Fm = j == 0 ? 0.0 : Fr(j - 1);            // F(x_{j-1/2}), F(x_min) = 0
-        const double Fp = j < G.n_if ? Fr(j) : 0.0;            // F(x_{j+1/2}), 0 at x_max (cons.)
-        const double h = G.edges[j + 1] - G.edges[j];
+        const FT Fm = j == 0 ? FT(0) : F[j - 1];             // F(x_{j-1/2}), F(x_min) = 0
+        const FT Fp = j < G.n_if ? F[j] : FT(0);             // F(x_{j+1/2}), 0 at x_max (cons.)
         const size_t base = (size_t)cell * P + (size_t)j * K1;
         double v[kB];
-        for (int i = 0; i <= k; ++i) {
-            const double V = i == 0 ? 0.0 : Fr(G.n_if + j * k + i - 1);
-            const double L = (2.0 * i + 1.0) / h * (V - Fp + ((i & 1) ? -Fm : Fm));
-            if (A.dt)
-                v[i] = A.a * A.gn[base + i] + A.b * (A.gs[base + i] + dt * L);
-            else
-                v[i] = L;
+        const double L0 = ((double)Fm - (double)Fp) * G.inv_h[j];
+        v[0] = step ? A.a * A.gn[base] + A.b * (A.gs[base] + dt * L0) : L0;
+        if (sizeof(FT) == 8) {
+            const double ih = G.inv_h[j];
+            for (int i = 1; i <= k; ++i) {
+                const double V = (double)F[G.n_if + j * k + i - 1];
+                const double L = (2.0 * i + 1.0) * ih * (V - (double)Fp + ((i & 1) ? -(double)Fm : (double)Fm));
+                v[i] = step ? A.a * A.gn[base + i] + A.b * (A.gs[base + i] + dt * L) : L;
+            }
+        } else {
+            const float ih = G.inv_h32[j];
+            const float a = (float)A.a, b = (float)A.b, dtf = (float)dt;
+            const float fp = (float)Fp, fm = (float)Fm;
+            for (int i = 1; i <= k; ++i) {
+                const float V = (float)F[G.n_if + j * k + i - 1];
+                const float L = (2.f * i + 1.f) * ih * (V - fp + ((i & 1) ? -fm : fm));
+                v[i] = step ? (double)(a * (float)A.gn[base + i] + b * ((float)A.gs[base + i] + dtf * L)) : (double)L;
+            }
         }
-        if (A.dt) {
+        if (step) {
             if (v[0] < 0.0) fl |= GRACE_FLAG_NEGATIVE_MEAN;
             for (int i = 0; i <= k; ++i)
                 if (!isfinite(v[i])) fl |= GRACE_FLAG_NONFINITE;
             if (A.apply_limiter) fl |= limit_bin(v, k);
         }
-        for (int i = 0; i <= k; ++i) A.gout[base + i] = v[i];
-        if (A.opA)
-            for (int i = 0; i <= k; ++i) opA_store(A.opA, A.opA_prec, A.opA_kpad, cell, j * K1 + i, v[i] * h);
-        msum += h * v[0];
+        for (int i = 0; i <= k; ++i) row[j * K1 + i] = v[i];
+        if (A.mass) msum += G.hbin[j] * v[0];
     }
+    __syncwarp();
+    write_row(G, row, cell, A.gout, A.opA, A.opA_prec, A.opA_kpad, lane);
     if (A.mass) {
         msum = warp_sum(msum);
         if (lane == 0) A.mass[cell] = msum;
     }
     if (A.flags) {
         fl = warp_or(fl);
-        if (lane == 0) A.flags[cell] |= (unsigned char)fl;
+        if (lane == 0 && fl) A.flags[cell] |= (unsigned char)fl;
     }
 }
 
 __global__ void __launch_bounds__(256) limit_kernel(DevGroup G, double *g, int n_cells, unsigned char *flags,
                                                      void *opA, int prec, int kpad)
 {
+    extern __shared__ double rows[];
     const long long cell = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (cell >= n_cells) return;
-    const int k = G.k, K1 = G.K1;
-    unsigned fl = 0u;
+    const int k = G.k, K1 = G.K1, P = G.P;
+    double *row = rows + (size_t)(threadIdx.x >> 5) * P;
+    for (int i = lane; i < P; i += 32) row[i] = g[(size_t)cell * P + i];
+    __syncwarp();
+    unsigned fl = 0u, changed = 0u;
     for (int j = lane; j < G.N; j += 32) {
-        const size_t base = (size_t)cell * G.P + (size_t)j * K1;
-        double v[kB];
-        for (int i = 0; i <= k; ++i) v[i] = g[base + i];
+        double *v = row + j * K1;
         if (G.limiter) {
             const unsigned f = limit_bin(v, k);
-            if (f & GRACE_FLAG_LIMITED)
-                for (int i = 1; i <= k; ++i) g[base + i] = v[i];
+            if (f & GRACE_FLAG_LIMITED) changed = 1u;
             fl |= f;
         }
-        if (opA) {
-            const double h = G.edges[j + 1] - G.edges[j];
-            for (int i = 0; i <= k; ++i) opA_store(opA, prec, kpad, cell, j * K1 + i, v[i] * h);
-        }
     }
+    __syncwarp();
+    changed = warp_or(changed);
+    write_row(G, row, cell, changed ? g : nullptr, opA, prec, kpad, lane);
     if (flags) {
         fl = warp_or(fl);
-        if (lane == 0) flags[cell] |= (unsigned char)fl;
+        if (lane == 0 && fl) flags[cell] |= (unsigned char)fl;
     }
 }
 
@@ -175,8 +177,7 @@ __global__ void __launch_bounds__(256) mass_kernel(DevGroup G, const double *g, 
     const int lane = threadIdx.x & 31;
     if (cell >= n_cells) return;
     double s = 0.0;
-    for (int j = lane; j < G.N; j += 32)
-        s += (G.edges[j + 1] - G.edges[j]) * g[(size_t)cell * G.P + (size_t)j * G.K1];
+    for (int j = lane; j < G.N; j += 32) s += G.hbin[j] * g[(size_t)cell * G.P + (size_t)j * G.K1];
     s = warp_sum(s);
     if (lane == 0) mass[cell] = s;
 }
@@ -214,14 +215,19 @@ inline int warp_blocks(int n_cells) { return (int)(((long long)n_cells * 32 + 25
 
 cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
 {
-    update_kernel<<<warp_blocks(n_cells), 256, 0, st>>>(g, a, n_cells);
+    const size_t smem = (size_t)8 * g.P * sizeof(double);
+    if (a.F)
+        update_kernel<double><<<warp_blocks(n_cells), 256, smem, st>>>(g, a, n_cells);
+    else
+        update_kernel<float><<<warp_blocks(n_cells), 256, smem, st>>>(g, a, n_cells);
     return cudaGetLastError();
 }
 
 cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned char *flags, void *opA,
                          int opA_prec, int opA_kpad, cudaStream_t st)
 {
-    limit_kernel<<<warp_blocks(n_cells), 256, 0, st>>>(g, d_g, n_cells, flags, opA, opA_prec, opA_kpad);
+    limit_kernel<<<warp_blocks(n_cells), 256, (size_t)8 * g.P * sizeof(double), st>>>(g, d_g, n_cells, flags, opA,
+                                                                                       opA_prec, opA_kpad);
     return cudaGetLastError();
 }
 
@@ -246,8 +252,8 @@ cudaError_t launch_pack_A(const DevGroup &g, const double *d_g, int n_cells, voi
 {
     DevGroup g0 = g;
     g0.limiter = 0;
-    limit_kernel<<<warp_blocks(n_cells), 256, 0, st>>>(g0, const_cast<double *>(d_g), n_cells, nullptr, opA,
-                                                       prec, kpad);
+    limit_kernel<<<warp_blocks(n_cells), 256, (size_t)8 * g.P * sizeof(double), st>>>(
+        g0, const_cast<double *>(d_g), n_cells, nullptr, opA, prec, kpad);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,9 @@ def exported_symbols():
             "grace_set_stream", "grace_precompute", "grace_group_info", "grace_bind_batch",
             "grace_batch_offsets", "grace_project", "grace_rhs", "grace_step", "grace_mass",
             "grace_limit", "grace_profile_enable", "grace_profile_read", "grace_group_stats",
-            "grace_batch_error", "grace_batch_destroy", "grace_destroy"]
+            "grace_batch_error", "grace_rhs_jvp", "grace_rhs_vjp", "grace_param_grad_setup",
+            "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_destroy",
+            "grace_destroy"]
 
 
 def load(path: str | None = None):
@@ -77,6 +79,12 @@ def load(path: str | None = None):
     L.grace_profile_read.argtypes = [_VP, S, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     L.grace_group_stats.argtypes = [_VP, S, S, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.grace_batch_error.argtypes = [_VP, ctypes.POINTER(S)]
+    L.grace_rhs_jvp.argtypes = [_VP, _VP, _VP, _VP, S]
+    L.grace_rhs_vjp.argtypes = [_VP, _VP, _VP, _VP, S]
+    L.grace_param_grad_setup.argtypes = [_VP, S, S, _VP, ctypes.c_double]
+    L.grace_adjoint.argtypes = [_VP, _VP, _VP, S, S, _VP, _VP, _VP, S]
+    L.grace_probe_rates.argtypes = [S, ctypes.POINTER(ctypes.c_double)]
+    L.grace_batch_set_graph.argtypes = [_VP, S]
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -113,6 +121,13 @@ def _ptr(t):
 def _stream_handle():
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def probe_rates(device: int = 0):
+    """Measured CUDA-core rates on this device: FP64 FMA/s, FP32 FMA/s, FP64->FP32 conversions/s."""
+    out = (ctypes.c_double * 3)()
+    _check(load().grace_probe_rates(int(device), out), "grace_probe_rates")
+    return {"fp64_fma_per_s": out[0], "fp32_fma_per_s": out[1], "f64_to_f32_cvt_per_s": out[2]}
 
 
 class Context:
@@ -161,6 +176,14 @@ class Context:
                "grace_group_stats")
         return a.value, b.value
 
+    def param_grad_setup(self, param_ids, group: int = 0, rel_step: float = 1e-5):
+        """Enables dJ/dtheta in Batch.adjoint for kernel parameters given by id:
+        0..7 coag_p[i], 8..15 frag_p[i-8], 16..23 break_p[i-16]."""
+        ids = np.ascontiguousarray(param_ids, dtype=np.int32)
+        _check(load().grace_param_grad_setup(self._h, group, len(ids), ids.ctypes.data_as(ctypes.c_void_p),
+                                             float(rel_step)), "grace_param_grad_setup")
+        self.param_ids = tuple(int(i) for i in ids)
+
     def batch(self, n_cells: int, cell_group=None) -> "Batch":
         return Batch(self, n_cells, cell_group)
 
@@ -187,7 +210,10 @@ class Batch:
             cg = cg_arr.ctypes.data_as(ctypes.c_void_p)
         _check(load().grace_bind_batch(ctx._h, n_cells, cg, ctypes.byref(h)), "grace_bind_batch")
         self._h = h
-        self.P, self.R = ctx.group_info(0)
+        self.group0 = int(np.asarray(cell_group).reshape(-1)[0]) if cell_group is not None else 0
+        self.P, self.R = ctx.group_info(self.group0)
+        self.mixed = cell_group is not None and len(set(np.asarray(cell_group).tolist())) > 1
+        self.total = int(self.offsets()[-1])
 
     def offsets(self):
         out = (ctypes.c_longlong * (self.n_cells + 1))()
@@ -198,14 +224,16 @@ class Batch:
         import torch
         if not (g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()):
             raise GraceError("coefficient arrays must be contiguous float64 CUDA tensors")
-        if g.numel() != self.n_cells * self.P:
-            raise GraceError(f"expected {self.n_cells * self.P} coefficients, got {g.numel()}")
+        if g.numel() != self.total:
+            raise GraceError(f"expected {self.total} coefficients, got {g.numel()}")
 
     def project(self, ic_kind: int, ic_params):
         import torch
         ic = torch.as_tensor(np.ascontiguousarray(ic_params, dtype=np.float64)).reshape(self.n_cells, 4)
         ic = ic.to(f"cuda:{self.ctx.device}")
-        g = torch.empty(self.n_cells, self.P, dtype=torch.float64, device=ic.device)
+        g = torch.empty(self.total, dtype=torch.float64, device=ic.device)
+        if not self.mixed:
+            g = g.view(self.n_cells, self.P)
         self.ctx.set_stream()
         _check(load().grace_project(self._h, int(ic_kind), _ptr(ic), _ptr(g)), "grace_project")
         return g
@@ -240,6 +268,44 @@ class Batch:
         _check(load().grace_limit(self._h, _ptr(g), _ptr(flags)), "grace_limit")
         return g
 
+    def jvp(self, g, v, precision: int = FP64):
+        import torch
+        self._check_state(g)
+        self._check_state(v)
+        out = torch.empty_like(g)
+        self.ctx.set_stream()
+        _check(load().grace_rhs_jvp(self._h, _ptr(g), _ptr(v), _ptr(out), int(precision)), "grace_rhs_jvp")
+        return out
+
+    def vjp(self, g, lam, precision: int = FP64):
+        import torch
+        self._check_state(g)
+        self._check_state(lam)
+        out = torch.empty_like(g)
+        self.ctx.set_stream()
+        _check(load().grace_rhs_vjp(self._h, _ptr(g), _ptr(lam), _ptr(out), int(precision)), "grace_rhs_vjp")
+        return out
+
+    def adjoint(self, g0, dt, n_steps: int, lam_T, ckpt_every: int = 10, param_grads: bool = False,
+                precision: int = FP64):
+        """(lambda_0, dtheta [n_cells, n_params] or None) for J with dJ/dg(t_end) = lam_T."""
+        import torch
+        self._check_state(g0)
+        self._check_state(lam_T)
+        lam0 = torch.empty_like(g0)
+        dth = None
+        if param_grads:
+            npar = len(getattr(self.ctx, "param_ids", ()))
+            dth = torch.zeros(self.n_cells, max(npar, 1), dtype=torch.float64, device=g0.device)
+        self.ctx.set_stream()
+        _check(load().grace_adjoint(self._h, _ptr(g0), _ptr(dt), int(n_steps), int(ckpt_every), _ptr(lam_T),
+                                    _ptr(lam0), _ptr(dth), int(precision)), "grace_adjoint")
+        return lam0, dth
+
+    def set_graph(self, enable: bool = True):
+        """Replay grace_step from a captured CUDA graph for repeated identical calls."""
+        _check(load().grace_batch_set_graph(self._h, 1 if enable else 0), "grace_batch_set_graph")
+
     def device_error(self) -> int:
         """Reads and clears the device error word (0 = no bounded wait gave up)."""
         code = ctypes.c_int()
@@ -258,3 +324,35 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _make_step_function():
+    import torch
+
+    class StepFunction(torch.autograd.Function):
+        """g_T = n_steps SSP-RK3 steps (with the limiter) of the batch from g0.
+        backward runs the checkpointed discrete adjoint (FP64)."""
+
+        @staticmethod
+        def forward(ctx, g0, batch, dt, n_steps, ckpt_every):
+            g = g0.detach().clone().contiguous()
+            batch.step(g, dt, n_steps, FP64)
+            ctx.batch, ctx.dt, ctx.n_steps, ctx.ckpt = batch, dt, n_steps, ckpt_every
+            ctx.save_for_backward(g0.detach())
+            return g
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g0,) = ctx.saved_tensors
+            lam0, _ = ctx.batch.adjoint(g0.contiguous(), ctx.dt, ctx.n_steps, grad_out.contiguous(), ctx.ckpt)
+            return lam0, None, None, None, None
+
+    return StepFunction
+
+
+def step_autograd(g0, batch, dt, n_steps: int, ckpt_every: int = 10):
+    """Differentiable wrapper of Batch.step (FP64) for torch.autograd."""
+    global StepFunction
+    if "StepFunction" not in globals():
+        StepFunction = _make_step_function()
+    return StepFunction.apply(g0, batch, dt, n_steps, ckpt_every)

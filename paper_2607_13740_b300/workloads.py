@@ -135,3 +135,30 @@ def random_coefficients(spec: GroupSpec, n_cells: int, seed: int = 7, rel_modes:
     if k >= 1:
         g[:, :, 1:] = g[:, :, :1] * rng.uniform(-rel_modes, rel_modes, (n_cells, N, k)) / np.arange(1, k + 1)
     return g.reshape(n_cells, N * (k + 1))
+
+
+def uneven_batch(n_cells=100000, seed=1004, n_range=(16, 80), orders=(0, 1, 2, 3),
+                 kinds=(COAG_CONST, COAG_ADD), x_min=1e-6, x_max=1e10):
+    """Uneven batch: per cell N ~ U{n_range}, k ~ U{orders}, kernel kind ~ U{kinds}
+    (constant or additive coagulation, conservative fluxes) and a per-cell rate
+    scale s ~ lognormal(0, 0.5); ICs as in batched_additive.  A kernel scale s
+    multiplies the RHS, which is the same as multiplying the cell's time step,
+    so it is folded into dt.  Returns (specs, cell_group, ic_params, dt)."""
+    rng = np.random.default_rng(seed)
+    N = rng.integers(n_range[0], n_range[1] + 1, n_cells)
+    k = rng.choice(np.asarray(orders), n_cells)
+    kind = rng.choice(np.asarray(kinds), n_cells)
+    s = rng.lognormal(0.0, 0.5, n_cells)
+    A = rng.lognormal(0.0, 0.5, n_cells)
+    x0 = np.exp(rng.uniform(math.log(1e-3), math.log(1.0), n_cells))
+    keys = sorted(set(zip(N.tolist(), k.tolist(), kind.tolist())))
+    index = {key: i for i, key in enumerate(keys)}
+    specs = [GroupSpec(int(n), int(o), x_min, x_max, FLUX_CONSERVATIVE, int(kd), (1.0,)) for (n, o, kd) in keys]
+    group = np.array([index[(a, b, c)] for a, b, c in zip(N.tolist(), k.tolist(), kind.tolist())], dtype=np.int32)
+    ic = np.zeros((n_cells, 4))
+    ic[:, 0] = A
+    ic[:, 1] = x0
+    # time scale of the cell's kernel: total mass A x0^2 (additive), number A x0 (constant)
+    rate = np.where(kind == COAG_ADD, A * x0 * x0, A * x0) * s
+    dt = 0.02 / rate
+    return specs, group, ic, dt

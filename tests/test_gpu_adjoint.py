@@ -1,0 +1,141 @@
+"""Tangent-linear and adjoint of the RHS and of the SSP-RK3 trajectory (FP64).
+
+Pins: L is a quadratic form, so (L(g+v) - L(g-v))/2 = J(g) v exactly; the
+oracle supplies that exact directional derivative.  The VJP is checked by the
+dot-product identity against the JVP; the trajectory adjoint against central
+differences of oracle trajectories (the FP64 reference gradient) and against
+torch.autograd.gradcheck; parameter gradients against central differences of
+oracle trajectories in the parameter.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_13740_b300 import grace, workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+SPECS = {
+    "add_k2": W.additive_spec(16, 2, 1e-4, 1e6),
+    "toy_remnant_k2": W.coupled_toy_spec(10, 2, flux_mode=0),
+    "pure_frag_k1": W.pure_fragmentation_spec(10, 1, 1e-6, 1e3, flux_mode=0),
+    "const_k3": W.GroupSpec(8, 3, 1e-2, 1e3, 0, W.COAG_CONST, (1.0,)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SPECS))
+def test_jvp_equals_exact_central_difference_of_oracle(name):
+    spec = SPECS[name]
+    g = W.random_coefficients(spec, 9, seed=601)
+    v = W.random_coefficients(spec, 9, seed=602) * 0.3
+    ctx = grace.Context([spec])
+    b = ctx.batch(9)
+    Jv = b.jvp(torch.as_tensor(g, device=DEV), torch.as_tensor(v, device=DEV)).cpu().numpy()
+    o = oracle.Oracle(spec)
+    Lp, Sp = o.rhs(g + v)
+    Lm, Sm = o.rhs(g - v)
+    ref = 0.5 * (Lp - Lm)
+    scale = np.maximum(Sp, Sm)
+    assert np.all(np.abs(Jv - ref) <= 1e-12 * np.maximum(scale, 1e-300)), name
+
+
+@pytest.mark.parametrize("name", sorted(SPECS))
+def test_vjp_dot_product_identity(name):
+    spec = SPECS[name]
+    n = 40
+    g = torch.as_tensor(W.random_coefficients(spec, n, seed=603), device=DEV)
+    w = torch.as_tensor(np.random.default_rng(604).normal(size=(n, spec.n_coef)), device=DEV)
+    lam = torch.as_tensor(np.random.default_rng(605).normal(size=(n, spec.n_coef)), device=DEV)
+    ctx = grace.Context([spec])
+    b = ctx.batch(n)
+    lhs = (w * b.vjp(g, lam)).sum(dim=1)
+    rhs = (b.jvp(g, w) * lam).sum(dim=1)
+    rel = ((lhs - rhs).abs() / (lhs.abs() + rhs.abs())).max().item()
+    assert rel < 1e-12, rel
+
+
+def _traj_setup(spec, n, seed):
+    o = oracle.Oracle(spec)
+    g0 = o.project(W.IC_EXP, np.column_stack([np.full(n, 1.0), np.linspace(0.5, 2.0, n), np.zeros(n), np.zeros(n)]))
+    rng = np.random.default_rng(seed)
+    return o, g0, rng
+
+
+@pytest.mark.parametrize("ckpt", [1, 4, 20])
+def test_trajectory_adjoint_vs_oracle_directional_derivative(ckpt):
+    spec = W.additive_spec(12, 2, 1e-3, 1e4).replace(limiter=0)
+    n, steps, dt = 4, 12, 0.05
+    o, g0, rng = _traj_setup(spec, n, 606)
+    lamT = rng.normal(size=g0.shape)
+    # relative perturbation: empty tail bins (where dt times the collision rate is large) stay empty
+    v = rng.uniform(-0.1, 0.1, size=g0.shape) * g0
+    ctx = grace.Context([spec])
+    b = ctx.batch(n)
+    dtt = torch.full((n,), dt, dtype=torch.float64, device=DEV)
+    lam0, _ = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, torch.as_tensor(lamT, device=DEV), ckpt)
+    lam0 = lam0.cpu().numpy()
+    eps = 1e-4
+    gp, _, _ = o.step(g0 + eps * v, dt, steps)
+    gm, _, _ = o.step(g0 - eps * v, dt, steps)
+    fd = ((gp - gm) / (2 * eps) * lamT).sum(axis=1)
+    ad = (lam0 * v).sum(axis=1)
+    assert np.allclose(ad, fd, rtol=1e-7, atol=1e-9 * np.abs(fd).max()), (ad, fd)
+
+
+def test_trajectory_adjoint_with_active_limiter():
+    """Limiter on (kinks away from the evaluation point): adjoint vs oracle central differences."""
+    spec = W.coupled_toy_spec(10, 2, flux_mode=0)
+    n, steps, dt = 3, 10, 0.05
+    o, g0, rng = _traj_setup(spec, n, 607)
+    g0 = o.project(W.IC_EXP, [[1.0, 0.3, 0, 0], [2.0, 1.0, 0, 0], [0.5, 3.0, 0, 0]])
+    lamT = rng.normal(size=g0.shape)
+    v = rng.uniform(-0.1, 0.1, size=g0.shape) * g0
+    ctx = grace.Context([spec])
+    b = ctx.batch(n)
+    dtt = torch.full((n,), dt, dtype=torch.float64, device=DEV)
+    lam0, _ = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, torch.as_tensor(lamT, device=DEV), 5)
+    eps = 1e-5
+    gp, _, _ = o.step(g0 + eps * v, dt, steps)
+    gm, _, _ = o.step(g0 - eps * v, dt, steps)
+    fd = ((gp - gm) / (2 * eps) * lamT).sum(axis=1)
+    ad = (lam0.cpu().numpy() * v).sum(axis=1)
+    assert np.allclose(ad, fd, rtol=1e-5, atol=1e-7 * np.abs(fd).max()), (ad, fd)
+
+
+def test_parameter_gradients_vs_oracle_central_differences():
+    """dJ/dv_frag and dJ/dalpha of the coupled toy model (Sec. 4.5 physics), J = <lambda_T, g_T>."""
+    spec = W.coupled_toy_spec(10, 2, flux_mode=0)
+    n, steps, dt = 3, 8, 0.05
+    o, g0, rng = _traj_setup(spec, n, 608)
+    lamT = rng.normal(size=g0.shape)
+    ids = [9, 16]                      # frag_p[1] = v_f, break_p[0] = alpha
+    ctx = grace.Context([spec])
+    ctx.param_grad_setup(ids)
+    b = ctx.batch(n)
+    dtt = torch.full((n,), dt, dtype=torch.float64, device=DEV)
+    _, dth = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, torch.as_tensor(lamT, device=DEV), 4,
+                       param_grads=True)
+    dth = dth.cpu().numpy()
+    for col, (field, idx) in enumerate([("frag_p", 1), ("break_p", 0)]):
+        base = list(getattr(spec, field))
+        h = 1e-5 * abs(base[idx])
+        vals = []
+        for sgn in (+1, -1):
+            p = list(base)
+            p[idx] = base[idx] + sgn * h
+            gT, _, _ = oracle.Oracle(spec.replace(**{field: tuple(p)})).step(g0, dt, steps)
+            vals.append((gT * lamT).sum(axis=1))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert np.allclose(dth[:, col], fd, rtol=2e-4, atol=1e-6 * np.abs(fd).max()), (field, dth[:, col], fd)
+
+
+def test_autograd_function_gradcheck():
+    spec = W.additive_spec(4, 1, 1e-2, 1e2).replace(limiter=0)
+    ctx = grace.Context([spec])
+    b = ctx.batch(1)
+    g0 = b.project(W.IC_EXP, [[1.0, 1.0, 0.0, 0.0]]).requires_grad_(True)
+    dt = torch.full((1,), 0.05, dtype=torch.float64, device=DEV)
+    f = lambda g: grace.step_autograd(g, b, dt, 3, 2)
+    assert torch.autograd.gradcheck(f, (g0,), eps=1e-6, atol=1e-8, rtol=1e-6)

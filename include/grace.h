@@ -226,6 +226,16 @@ GRACE_API grace_status grace_profile_read(grace_ctx *ctx, int kernel, double *to
 GRACE_API grace_status grace_group_stats(const grace_ctx *ctx, int group, int precision, long long *nnz,
                                          long long *tile_macs);
 
+/* Tensor-core tile plan of one group for precision GRACE_TF32 or GRACE_BF16X3
+   (built by grace_precompute; the tile shapes are chosen by a cost model over
+   the sparsity of T, see the contraction's documentation).  Writes 7 values
+   (host): [0] N-tiles, [1] tcgen05.mma instructions per 128-cell tile and RHS,
+   [2] executed multiply-adds per cell and RHS, [3] bytes of the B images,
+   [4] cost-model SM cycles per 128-cell tile and RHS, [5] widest MMA N,
+   [6] non-zeros of the symmetric-folded tables (the multiply-adds a cell needs).
+   GRACE_ERR_ORDER when that precision was not precomputed. */
+GRACE_API grace_status grace_tile_info(const grace_ctx *ctx, int group, int precision, long long *info);
+
 /* Reads and clears the batch's device error word: non-zero bits mean a bounded
    device-side wait inside a tensor-core launch gave up (the launch then wrote
    no results for the affected cells).  Synchronises the bound stream; returns

@@ -100,6 +100,7 @@ DevGroup make_devgroup(const grace_group_desc &d, const double *d_edges)
     g.hbin = d_edges ? d_edges + g.N + 1 : nullptr;
     g.inv_h = d_edges ? d_edges + 2 * g.N + 1 : nullptr;
     g.inv_h32 = d_edges ? reinterpret_cast<const float *>(d_edges + 3 * g.N + 1) : nullptr;
+    g.h32 = d_edges ? reinterpret_cast<const float *>(d_edges + 3 * g.N + 1) + g.N : nullptr;
     return g;
 }
 
@@ -215,14 +216,15 @@ grace_status grace_setup(grace_ctx **out, int n_groups, const grace_group_desc *
                 G.h_edges[j] = G.desc.x_min * std::pow(G.desc.x_max / G.desc.x_min, (double)j / N);
             G.h_edges[0] = G.desc.x_min;
             G.h_edges[N] = G.desc.x_max;
-            // one allocation: edges (N+1), h (N), 1/h (N) in FP64, then 1/h (N) in FP32
-            std::vector<double> tab(3 * (size_t)N + 1 + (N + 1) / 2, 0.0);
+            // one allocation: edges (N+1), h (N), 1/h (N) in FP64, then 1/h (N) and h (N) in FP32
+            std::vector<double> tab(3 * (size_t)N + 1 + N, 0.0);
             for (int j = 0; j <= N; ++j) tab[j] = G.h_edges[j];
             for (int j = 0; j < N; ++j) {
                 const double h = G.h_edges[j + 1] - G.h_edges[j];
                 tab[N + 1 + j] = h;
                 tab[2 * N + 1 + j] = 1.0 / h;
                 reinterpret_cast<float *>(tab.data() + 3 * N + 1)[j] = (float)(1.0 / h);
+                reinterpret_cast<float *>(tab.data() + 3 * N + 1)[N + j] = (float)h;
             }
             e = cudaMalloc(&G.d_edges, sizeof(double) * tab.size());
             if (e == cudaSuccess)
@@ -364,6 +366,27 @@ grace_status grace_group_stats(const grace_ctx *ctx, int group, int prec, long l
     const Group &G = ctx->groups[group];
     if (nnz) *nnz = G.nnz;
     if (tile_macs) *tile_macs = prec == GRACE_FP64 ? G.nnz : G.tc[prec].mac_per_cell;
+    return GRACE_OK;
+}
+
+grace_status grace_tile_info(const grace_ctx *ctx, int group, int prec, long long *info)
+{
+    if (!ctx || !info || group < 0 || group >= (int)ctx->groups.size() || (prec != GRACE_TF32 && prec != GRACE_BF16X3)) {
+        set_error("grace_tile_info: bad argument");
+        return GRACE_ERR_ARG;
+    }
+    const TcTiles &t = ctx->groups[group].tc[prec];
+    if (!t.built) {
+        set_error("grace_tile_info: precision not precomputed");
+        return GRACE_ERR_ORDER;
+    }
+    info[0] = t.n_tiles;
+    info[1] = t.mma_per_tile;
+    info[2] = t.mac_per_cell;
+    info[3] = (long long)t.b_bytes;
+    info[4] = (long long)(t.pred_clk + 0.5);
+    info[5] = t.max_rows;
+    info[6] = t.nnz_fold;
     return GRACE_OK;
 }
 

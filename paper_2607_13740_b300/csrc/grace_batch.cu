@@ -54,8 +54,6 @@ inline unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
 
 cudaStream_t part_stream(const grace_batch *b, const Part &p) { return p.direct ? b->ctx->stream : p.stream; }
 
-grace_status fail_cuda(cudaError_t e, const char *where) { return cuda_fail(e, where); }
-
 void free_part(Part &p)
 {
     cudaFree(p.d_idx);
@@ -104,10 +102,16 @@ cudaError_t part_rhs(grace_batch *b, Part &p, const double *g, double *L, int pr
     if (prec != GRACE_FP64) {
         e = launch_pack_A(G.dg, g, p.n, p.d_opA, prec, G.tc[prec].k_pad, st);
         if (e != cudaSuccess) return e;
+        {
+            LaunchTimer timer(b->ctx, 0, st);
+            e = launch_contract_tc(G.dg, G.tc[prec], prec, p.d_opA, p.n, p.d_F32, b->d_err, st);
+        }
+        if (e != cudaSuccess) return e;
         UpdateArgs u;
+        u.F32 = p.d_F32;
         u.gout = L;
-        LaunchTimer timer(b->ctx, 0, st);
-        return launch_contract_tc(G.dg, G.tc[prec], prec, p.d_opA, p.n, p.d_F32, b->d_err, st, 1, &u);
+        LaunchTimer timer(b->ctx, 1, st);
+        return launch_update_tc(G.dg, u, p.n, st);
     }
     {
         LaunchTimer timer(b->ctx, 0, st);
@@ -160,11 +164,21 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
                 u.mass = last ? mass : nullptr;
             }
             if (tc) {
-                // tcgen05 contraction with the flux difference / RK stage fused into its epilogue;
-                // the next stage's A operand is rewritten in place
-                u.opA = (stage == 2 && last) ? nullptr : opA;
-                LaunchTimer timer(b->ctx, 0, st);
-                e = launch_contract_tc(dg, G.tc[prec], prec, opA, n, p.d_F32, b->d_err, st, 2, &u);
+                // tcgen05 contraction, then the flux difference / RK stage, which also
+                // writes the next stage's A operand
+                {
+                    LaunchTimer timer(b->ctx, 0, st);
+                    e = launch_contract_tc(dg, G.tc[prec], prec, opA, n, p.d_F32, b->d_err, st);
+                }
+                if (e != cudaSuccess) return e;
+                u.F32 = p.d_F32;
+                if (!(stage == 2 && last)) {
+                    u.opA = opA;
+                    u.opA_prec = prec;
+                    u.opA_kpad = kpad;
+                }
+                LaunchTimer timer(b->ctx, 1, st);
+                e = launch_update_tc(dg, u, n, st);
             } else {
                 {
                     LaunchTimer timer(b->ctx, 0, st);
@@ -290,8 +304,8 @@ grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group
                 if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming);
             }
             if (e == cudaSuccess && tc_any) {
-                e = cudaMalloc(&p.d_F32, n * g.R * sizeof(float));
-                if (e == cudaSuccess) e = cudaMemset(p.d_F32, 0, n * g.R * sizeof(float));
+                e = cudaMalloc(&p.d_F32, f32_bytes_for(g, (int)n));
+                if (e == cudaSuccess) e = cudaMemset(p.d_F32, 0, f32_bytes_for(g, (int)n));
                 size_t bytes = 0;
                 for (int prec = GRACE_TF32; prec <= GRACE_BF16X3; ++prec)
                     if (ctx->precision_mask & (1u << prec)) bytes = std::max(bytes, opA_bytes_for(g, prec, p.n, nullptr));

@@ -25,18 +25,26 @@ struct DevGroup {
     const double *hbin;              // device, N bin widths h_j
     const double *inv_h;             // device, N values 1 / h_j
     const float *inv_h32;            // device, N values 1 / h_j in FP32
+    const float *h32;                // device, N values h_j in FP32
 };
 
 // Tensor-core operand tiles of one group for one precision (built by precompute).
 struct TcTiles {
     int built = 0;
-    int n_tiles = 0;          // N-tiles (bin group x p-window)
+    int n_tiles = 0;          // MMA N-tiles (functional group x p-window)
     int k_pad = 0;            // padded K extent of the A operand (elements)
     int max_rows = 0;         // largest MMA N over the tiles
-    void *d_b = nullptr;      // pre-swizzled B tiles (all tiles back to back)
+    int slot_bytes = 0;       // largest single B copy (bytes)
+    void *d_b = nullptr;      // pre-swizzled B k-step blocks (all tiles back to back)
     void *d_desc = nullptr;   // per-tile descriptors
+    int *d_ford = nullptr;    // functional ids in tile order
     size_t b_bytes = 0;
-    long long mac_per_cell = 0;   // executed MACs per cell and RHS (tile shapes)
+    long long mac_per_cell = 0;    // executed MACs per cell and RHS (tile shapes)
+    long long mma_per_tile = 0;    // tcgen05.mma instructions per 128-cell tile and RHS
+    long long nnz_fold = 0;        // non-zeros of the folded (upper-triangular) tables
+    double pred_clk = 0.0;         // cost-model SM cycles per 128-cell tile and RHS
+    std::vector<int> group_tile;   // first tile of every functional group (+ end)
+    std::vector<double> group_cost;   // cost-model cycles of every group
 };
 
 // d T / d theta for one kernel parameter (central difference of the FP64 precompute)
@@ -96,7 +104,7 @@ struct Part {
     unsigned char *d_flags = nullptr;  // [n]
     double *d_ic = nullptr;        // [n][4]
     double *d_F = nullptr;         // [n][R] functionals, FP64
-    float *d_F32 = nullptr;        // [n][R] functionals from the tensor path
+    float *d_F32 = nullptr;        // [tiles][R][128] functionals from the tensor path
     double *d_g1 = nullptr, *d_g2 = nullptr;   // stage states
     void *d_opA = nullptr;         // tensor-core A operand of the current stage
     size_t opA_bytes = 0;
@@ -161,7 +169,7 @@ cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int
 // K-c: fused flux difference (eq. evo), RK stage (eq. RK3), limiter, mass, flags.
 struct UpdateArgs {
     const double *F = nullptr;     // [n][R] FP64 functionals, or
-    const float *F32 = nullptr;    // [n][R] FP32 functionals (tensor path)
+    const float *F32 = nullptr;    // [tiles][R][128] FP32 functionals (tensor path)
     const double *gn = nullptr;    // g^n
     const double *gs = nullptr;    // stage input g^(s)
     double *gout = nullptr;        // output (may alias gn)
@@ -175,10 +183,13 @@ struct UpdateArgs {
     int opA_kpad = 0;
 };
 cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st);
-// tcgen05 contraction; mode 0 writes the functionals to d_F32, mode 1 the RHS L
-// to u->gout, mode 2 performs the SSP-RK3 stage update of u (fused epilogue)
+// tcgen05 contraction: the flux functionals of every cell into d_F32 laid out as
+// [128-cell tile][functional][row of the tile]
 cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, int n_cells,
-                               float *d_F32, int *d_err, cudaStream_t st, int mode, const UpdateArgs *u);
+                               float *d_F32, int *d_err, cudaStream_t st);
+// K-c for the tensor path: reads d_F32 in the tile layout above
+cudaError_t launch_update_tc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st);
+size_t f32_bytes_for(const DevGroup &g, int n_cells);
 cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned char *flags,
                          void *opA, int opA_prec, int opA_kpad, cudaStream_t st);
 cudaError_t launch_mass(const DevGroup &g, const double *d_g, int n_cells, double *mass,

@@ -2,6 +2,7 @@
 // (closed form for k <= 3), an FP32 positivity pre-test and the limiter itself.
 #pragma once
 
+#include "grace_convert.cuh"
 #include "grace_physics.cuh"
 
 namespace grace {
@@ -50,16 +51,14 @@ __device__ __forceinline__ double bin_minimum(const double *c, int k)
     return m;
 }
 
-// FP32 test that a bin's polynomial is clearly positive on [-1, 1]: then the FP64
-// scaling limiter would leave it untouched (gamma = 1) and can be skipped.  The
-// margin covers FP32 rounding of the evaluation (coefficients summed in |.|).
-__device__ __forceinline__ bool clearly_positive(const double *c, int k)
+// FP32 test that a bin's polynomial (coefficients cf, already in FP32) is
+// clearly positive on [-1, 1]: then the FP64 scaling limiter would leave it
+// untouched (gamma = 1) and can be skipped.  The margin covers FP32 rounding of
+// the evaluation (coefficients summed in |.|).
+__device__ __forceinline__ bool clearly_positive_f(const float *cf, int k)
 {
-    float cf[kBinMax], s = 0.f;
-    for (int i = 0; i <= k; ++i) {
-        cf[i] = (float)c[i];
-        s += fabsf(cf[i]);
-    }
+    float s = 0.f;
+    for (int i = 0; i <= k; ++i) s += fabsf(cf[i]);
     if (!(cf[0] > 0.f)) return false;
     float m = cf[0];
     if (k >= 1) {
@@ -91,6 +90,96 @@ __device__ __forceinline__ bool clearly_positive(const double *c, int k)
         }
     }
     return m > 1e-5f * s;
+}
+
+__device__ __forceinline__ bool clearly_positive(const double *c, int k)
+{
+    float cf[kBinMax];
+    for (int i = 0; i <= k; ++i) cf[i] = (float)c[i];
+    return clearly_positive_f(cf, k);
+}
+
+// The same test for a bin whose mean v0 is FP64 and whose higher modes are FP32:
+// everything is rescaled by the power of two that brings v0 into [1, 2), so the
+// test holds at any magnitude (integer operations only, no FP64 arithmetic).
+__device__ __forceinline__ bool clearly_positive_mixed(double v0, const float *c, int k)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v0);
+    const uint32_t hi = (uint32_t)(u >> 32);
+    const int e0 = (int)((hi >> 20) & 0x7FFu);
+    if ((hi >> 31) || e0 == 0 || e0 == 0x7FF) return false;   // v0 <= 0, subnormal, inf or nan
+    float cf[kBinMax];
+    cf[0] = __uint_as_float(0x3F800000u | ((hi & 0xFFFFFu) << 3));   // mantissa of v0, truncated
+    for (int i = 1; i <= k; ++i) cf[i] = scale_pow2(c[i], 1023 - e0);
+    return clearly_positive_f(cf, k);
+}
+
+// sum_i c_i phi_i(x) in FP32 (Legendre polynomials up to degree 3)
+__device__ __forceinline__ float poly_f(const float *c, int k, float x)
+{
+    float s = c[0];
+    if (k >= 1) s += c[1] * x;
+    if (k >= 2) s += c[2] * (1.5f * x * x - 0.5f);
+    if (k >= 3) s += c[3] * (2.5f * x * x * x - 1.5f * x);
+    return s;
+}
+
+// minimum over [-1, 1] in FP32: end points and interior stationary points
+__device__ __forceinline__ float bin_minimum_f(const float *c, int k)
+{
+    float m = fminf(poly_f(c, k, 1.f), poly_f(c, k, -1.f));
+    if (k == 2 && c[2] != 0.f) {
+        const float xs = -c[1] / (3.f * c[2]);
+        if (xs > -1.f && xs < 1.f) m = fminf(m, poly_f(c, k, xs));
+    } else if (k == 3) {
+        // derivative 7.5 c3 x^2 + 3 c2 x + (c1 - 1.5 c3)
+        const float A = 7.5f * c[3], B = 3.f * c[2], C = c[1] - 1.5f * c[3];
+        float r0 = 2.f, r1 = 2.f;
+        if (A == 0.f) {
+            if (B != 0.f) r0 = -C / B;
+        } else {
+            const float disc = B * B - 4.f * A * C;
+            if (disc >= 0.f) {
+                const float sq = sqrtf(disc);
+                const float qq = -0.5f * (B + copysignf(sq, B));
+                if (qq != 0.f) {
+                    r0 = qq / A;
+                    r1 = C / qq;
+                } else {
+                    r0 = 0.f;
+                }
+            }
+        }
+        if (r0 > -1.f && r0 < 1.f) m = fminf(m, poly_f(c, k, r0));
+        if (r1 > -1.f && r1 < 1.f) m = fminf(m, poly_f(c, k, r1));
+    }
+    return m;
+}
+
+// Scaling limiter (eqs. (recon), (gamma)) evaluated in FP32 on a bin rescaled by
+// the power of two that brings its FP64 mean v0 into [1, 2): cf[0] is set here
+// from v0, the caller passes the rescaled higher modes in cf[1..k] (rescale by
+// 2^(1023 - e0), e0 from scaled_exponent).  Returns gamma in (0, 1]; a bin whose
+// FP32 minimum lies within the evaluation's rounding (1e-6 of sum |cf|) of zero
+// or above is left alone (gamma = 1).
+__device__ __forceinline__ int scaled_exponent(double v0)
+{
+    // biased exponent of v0 when v0 is positive, normal and finite, else -1
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v0);
+    const int e0 = (int)((u >> 52) & 0x7FFull);
+    return ((u >> 63) || e0 == 0 || e0 == 0x7FF) ? -1 : e0;
+}
+
+__device__ __forceinline__ float limiter_gamma_scaled(double v0, float *cf, int k)
+{
+    const uint32_t hi = (uint32_t)((unsigned long long)__double_as_longlong(v0) >> 32);
+    cf[0] = __uint_as_float(0x3F800000u | ((hi & 0xFFFFFu) << 3));
+    float s = 0.f;
+    for (int i = 0; i <= k; ++i) s += fabsf(cf[i]);
+    if (!(s < 3.0e38f)) return -1.f;   // a mode out of FP32 range relative to the mean: exact path
+    const float m = bin_minimum_f(cf, k);
+    if (!(m < -1e-6f * s)) return 1.f;
+    return fminf(cf[0] / (cf[0] - m), 1.f);
 }
 
 // eq. (recon) with gamma from eq. (gamma); returns flag bits

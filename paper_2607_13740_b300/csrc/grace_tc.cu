@@ -2,76 +2,89 @@
 //
 // Every flux functional of a cell is a quadratic form of its coefficients,
 //     F_r = sum_{p,q} T_r[p,q] g_p g_q                     (see grace_precompute.cu).
-// Over a batch this is one GEMM per tile of 128 cells, factorised as
-//     Y[c, (r,p)] = sum_q  ghat[c, q] * That_r[p, q]        (tcgen05.mma, FP32 in TMEM)
-//     F[c, r]     = sum_p  ghat[c, p] * Y[c, (r,p)]         (epilogue, one lane per cell)
-// with ghat = g * h_bin (bin-mass scaling) and That = T / (h_bin(p) h_bin(q)), so
+// Only the symmetric part of T_r matters, so it is folded onto the upper
+// triangle, U_r[p,q] = T_r[p,q] + T_r[q,p] (q > p), U_r[p,p] = T_r[p,p], which
+// halves the multiply-adds.  Over a batch the contraction is one GEMM per tile
+// of 128 cells, factorised as
+//     Y[c, (r,p)] = sum_{q >= p} ghat[c, q] * Uhat_r[p, q]    (tcgen05.mma, FP32 in TMEM)
+//     F[c, r]     = sum_p        ghat[c, p] * Y[c, (r,p)]     (epilogue, one lane per cell)
+// with ghat = g * h_bin (bin-mass scaling) and Uhat = U / (h_bin(p) h_bin(q)), so
 // operands stay in a comfortable FP32/BF16 range for grids spanning 16 decades.
-// The product g (x) g is never materialised: the MMA contracts T with g on one
-// side and the epilogue contracts the accumulator with g on the other, which
-// keeps the A operand equal to the cells' own coefficient tile.
 //
-// Output columns of one MMA tile are a set of up to 4 functionals x a window of
-// 32 consecutive p; the epilogue holds that 32-wide window of ghat in
-// registers and reuses it for every functional of the tile.  A tile's K range
-// is the union of the non-zero q extents of its rows (T is block-sparse: for
-// an interface flux at x_{j+1/2} the u-side rows p < 3j only couple to v-side
-// columns q of bins >= j-1), so zero blocks are skipped at the MMA k-step.
+// An N-tile of the GEMM is a run of nf consecutive functionals (in bin order)
+// times a window of 16 consecutive p (N = 16 nf <= 256); its K range is the union of
+// the non-zero q extents of its rows, so the zero blocks of the staircase
+// support are skipped.  One tcgen05.mma with M = 128 costs about the same time
+// for any N on this part, so tiles are made as wide as the support allows; the
+// grouping of functionals (hence N) is chosen by a dynamic program over a cost
+// model (MMA issue, B-operand L2 traffic and the epilogue), i.e. the tile
+// shapes are autotuned from T's sparsity.
 //
-// Operands live in global memory as ready-made shared-memory images in the
-// canonical K-major SWIZZLE_128B layout (grace_tc_layout.cuh); one
-// cp.async.bulk moves a cell tile's A operand or one K atom of a B tile.
+// B (the tables) lives in global memory as ready-made shared-memory images, one
+// block of N rows x 32 bytes per MMA k-step in the K-major SWIZZLE_32B layout;
+// A (the cells' coefficients) as 128-row K-major SWIZZLE_128B tiles
+// (grace_tc_layout.cuh).  Both move with cp.async.bulk (no tensor map).
 //
-// Warp roles (persistent, one CTA per SM, cell tiles round-robin):
-//   warp 0 lane 0 : bulk-copy producer (A tile, then the B atoms of every N tile)
+// Warp roles (persistent, one CTA per SM, work items round-robin):
+//   warps 0, 3    : bulk-copy producers (lane 0; warp 0 also the A tiles): B copies of up to
+//                   32 KB alternate between the two issuing threads
 //   warp 1 lane 0 : MMA issuer (kind::tf32, or kind::f16 with bf16 hi/lo x3)
-//   warp 2        : TMEM allocation / release
-//   warps 4..7    : epilogue, TMEM lane quadrant = warp % 4, one cell per thread
+//   warp 2        : TMEM allocation / release (2 accumulators x 256 columns)
+//   warps 4..19   : epilogue; TMEM lane quadrant = warp % 4, four warps per quadrant
+//                   splitting the functionals of a tile; one cell per thread
+// A work item is one 128-cell tile and a contiguous range of N-tiles (a split):
+// splitting the tile list lets a batch of few cell tiles fill every SM.
 // Every wait on an mbarrier is bounded; on timeout the CTA records an error in
 // the device error word, stops issuing work, drains its outstanding copies and
 // releases its tensor memory before returning.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
-#include "grace_limiter.cuh"
+#include "grace_internal.h"
 #include "grace_tc_layout.cuh"
 
 namespace grace {
 
 namespace {
 
-constexpr int kMaxFunc = 4;         // functionals per N tile
-constexpr int kWin = 32;            // p window per functional
-constexpr int kMaxSlots = 16;       // B ring depth (K atoms), sized at launch from free shared memory
-constexpr int kAccCols = 128;       // TMEM columns per accumulator buffer
-constexpr int kHalfCols = 256;      // two accumulator buffers per cell tile
+constexpr int kWin = 16;            // p window width of every N tile
+constexpr int kMaxF = 16;           // functionals per N tile (kMaxF * kWin = 256)
+constexpr int kMaxN = 256;          // MMA N
+constexpr int kMaxSlots = 16;       // B ring depth, sized at launch from free shared memory
+constexpr int kAccCols = 256;       // TMEM columns per accumulator buffer
+constexpr int kTmemCols = 512;      // two accumulator buffers
+constexpr int kEpiWarps = 8;
+constexpr int kEpiSplit = kEpiWarps / 4;   // epilogue warps per TMEM lane quadrant
+constexpr int kThreads = 32 * (4 + kEpiWarps);
+constexpr int kMaxSplits = 8;
 constexpr int kSmemLimit = 227 * 1024;
-
-// NT = cell tiles per CTA pass (1 or 2): TMEM columns, epilogue warps, threads
-template <int NT> struct Cfg {
-    static constexpr int tmem_cols = NT * kHalfCols;
-    static constexpr int epi_warps = 4 * NT;     // warps 4..7: first tile, 8..11: second
-    static constexpr int threads = 32 * (4 + 4 * NT);
-};
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
+// cost model (SM cycles), from measurements on this part: one tcgen05.mma with
+// M = 128 issues every ~139 cycles whatever its N; L2 delivers ~45 B/cycle/SM
+constexpr double kMmaClk = 139.0;
+constexpr double kL2BytesPerClk = 45.0;
+constexpr double kTileClk = 60.0;        // accumulator hand-off per tile
+constexpr double kItemClk = 2500.0;      // A tile load + pipeline fill per work item
+
 struct TileDesc {
-    long long b_off;    // byte offset of the tile's first K atom image
-    int nrows;          // MMA N = nf * 32
-    int nf;             // functionals in this tile
-    int atom_lo;        // first K atom (global K index / atom width)
-    int n_atoms;        // K atoms stored for this tile
-    int ks_lo, ks_hi;   // MMA k-steps [ks_lo, ks_hi) (32 bytes of K each)
+    int b_off16;        // offset of the tile's first k-step block in the B images, in 16-byte units
+    int n;              // MMA N = nf * w
+    int nf_flush;       // functionals (ford[f0 .. f0 + nf)) | flush << 16 (last window of its group: write F)
+    int w;              // p window width (kWin)
     int p0;             // first p of the window
-    int flush;          // last window of its functional group: write F
-    int r[kMaxFunc];    // functional ids (-1 unused)
-    int bin_lo, bin_hi; // bins whose functionals belong to this tile's group
+    int ks_lo, ks_hi;   // MMA k-steps [ks_lo, ks_hi)
+    int f0;             // first functional (index into the functional order)
 };
-static_assert(sizeof(TileDesc) == 64, "TileDesc layout");
+static_assert(sizeof(TileDesc) == 32, "TileDesc layout");
 
 struct TcParams {
     const TileDesc *tiles;
+    const int *ford;
     int n_tiles;
+    int table_bytes;      // shared-memory copy of tiles + ford
     const uint8_t *B;
     const uint8_t *A;
     long long a_tile_bytes;
@@ -79,20 +92,12 @@ struct TcParams {
     int n_cell_tiles;
     int R;
     float *F;
-    int prec;
-    int slot_bytes;       // bytes of one ring slot (max nrows x 128 x planes)
+    int slot_bytes;       // bytes of one ring slot
     int n_slots;          // ring depth
+    int a_bufs;           // A tiles in shared memory (2: the next item's A loads during this one)
+    int n_splits;
+    int split[kMaxSplits + 1];
     int *err;
-    // fused flux difference / RK stage (eq. evo, eq. RK3), used when mode != 0
-    int mode;             // 0: functionals to F; 1: L[g] to gout; 2: SSP-RK3 stage update
-    DevGroup G;
-    const double *gn, *gs, *dt;
-    double *gout;
-    double ca, cb;
-    int apply_limiter;
-    double *mass;
-    unsigned char *flags;
-    uint8_t *a_next;      // A operand of gout (may alias A), or null
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -157,16 +162,18 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
                  : "memory");
 }
 
-// SWIZZLE_128B K-major shared-memory matrix descriptor (8-row groups 1024 B apart)
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+// K-major shared-memory matrix descriptors: SWIZZLE_128B (A: 128-byte rows, 8-row
+// groups 1024 B apart) and SWIZZLE_32B (B: 32-byte rows, 8-row groups 256 B apart)
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr)
 {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;                   // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset
-    d |= (uint64_t)1u << 46;                   // descriptor version
-    d |= (uint64_t)2u << 61;                   // SWIZZLE_128B
-    return d;
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(256u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)6u << 61);
 }
 
 // instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = n
@@ -196,151 +203,18 @@ __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint
         : "memory");
 }
 
-// ---------------------------------------------------------------- fused update
-// 16-byte chunk of one cell's row of the next-stage A operand, filled in k order
-struct OpChunk {
-    int c;
-    uint32_t w[4], lo[4];
-};
-
-__device__ __forceinline__ void chunk_flush(const OpChunk &ch, const TcParams &P, uint8_t *tile, int row)
+// TMEM -> registers, 32 lanes x 16 / 32 columns, no wait
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r)
 {
-    if (ch.c < 0) return;
-    if (P.prec == GRACE_TF32) {
-        *reinterpret_cast<uint4 *>(tile + swz_offset(kTileM, row, 4 * ch.c, 4)) = make_uint4(ch.w[0], ch.w[1], ch.w[2], ch.w[3]);
-    } else {
-        const size_t off = swz_offset(kTileM, row, 8 * ch.c, 2);
-        *reinterpret_cast<uint4 *>(tile + off) = make_uint4(ch.w[0], ch.w[1], ch.w[2], ch.w[3]);
-        *reinterpret_cast<uint4 *>(tile + P.a_tile_bytes / 2 + off) = make_uint4(ch.lo[0], ch.lo[1], ch.lo[2], ch.lo[3]);
-    }
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
 }
 
-__device__ __forceinline__ void set4(uint32_t *w, int e, uint32_t v)
-{
-    w[0] = e == 0 ? v : w[0];
-    w[1] = e == 1 ? v : w[1];
-    w[2] = e == 2 ? v : w[2];
-    w[3] = e == 3 ? v : w[3];
-}
-
-__device__ __forceinline__ void chunk_put(OpChunk &ch, const TcParams &P, uint8_t *tile, int row, int k, float x)
-{
-    const int per = P.prec == GRACE_TF32 ? 4 : 8;
-    const int c = k / per, e = k - c * per;
-    if (c != ch.c) {
-        chunk_flush(ch, P, tile, row);
-        ch.c = c;
-        for (int i = 0; i < 4; ++i) ch.w[i] = ch.lo[i] = 0u;
-    }
-    if (P.prec == GRACE_TF32) {
-        set4(ch.w, e, f32_to_tf32_rna(x));
-    } else {
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        const int wi = e >> 1, sh = (e & 1) * 16;
-        const uint32_t hm = (uint32_t)__bfloat16_as_ushort(h) << sh, lm = (uint32_t)__bfloat16_as_ushort(l) << sh;
-        const uint32_t keep = (e & 1) ? 0x0000FFFFu : 0xFFFF0000u;
-        uint32_t hw = 0, lw = 0;
-        for (int i = 0; i < 4; ++i)
-            if (i == wi) { hw = ch.w[i]; lw = ch.lo[i]; }
-        set4(ch.w, wi, (hw & keep) | hm);
-        set4(ch.lo, wi, (lw & keep) | lm);
-    }
-}
-
-// L_j^i of eq. (evo) from the bin's functionals and, in stage mode, the SSP-RK3
-// combination; the i = 0 row in FP64 (telescoping flux difference, mass), the
-// i >= 1 rows in FP32.  gnb / gsb hold the bin's stage inputs (loaded ahead of
-// time by the caller).  Writes gout (and the next A operand through ch).
-__device__ __forceinline__ void update_bin(const TcParams &P, long long cell, int j, float Fm, float Fp,
-                                           const float *V, double dtc, const double *gnb, const double *gsb,
-                                           double &msum, unsigned &fl, OpChunk &ch, uint8_t *tile, int row)
-{
-    const DevGroup &G = P.G;
-    const int k = G.k, K1 = G.K1;
-    const size_t base = (size_t)cell * G.P + (size_t)j * K1;
-    double v[kBinMax];
-    float vf[kBinMax];
-    const double L0 = ((double)Fm - (double)Fp) * G.inv_h[j];
-    const float ih = G.inv_h32[j];
-    if (P.mode == 1) {
-        v[0] = L0;
-#pragma unroll
-        for (int i = 1; i < kBinMax; ++i)
-            if (i <= k) {
-                vf[i] = (2.f * i + 1.f) * ih * (V[i - 1] - Fp + ((i & 1) ? -Fm : Fm));
-                v[i] = (double)vf[i];
-            }
-    } else {
-        v[0] = P.ca * gnb[0] + P.cb * (gsb[0] + dtc * L0);
-        const float a = (float)P.ca, b = (float)P.cb, dtf = (float)dtc;
-#pragma unroll
-        for (int i = 1; i < kBinMax; ++i)
-            if (i <= k) {
-                const float L = (2.f * i + 1.f) * ih * (V[i - 1] - Fp + ((i & 1) ? -Fm : Fm));
-                vf[i] = a * (float)gnb[i] + b * ((float)gsb[i] + dtf * L);
-                v[i] = (double)vf[i];
-            }
-        if (v[0] < 0.0) fl |= GRACE_FLAG_NEGATIVE_MEAN;
-#pragma unroll
-        for (int i = 0; i < kBinMax; ++i)
-            if (i <= k && !isfinite(v[i])) fl |= GRACE_FLAG_NONFINITE;
-        if (P.apply_limiter) {
-            const unsigned f = limit_bin(v, k);
-            fl |= f;
-            if (f & GRACE_FLAG_LIMITED) {
-#pragma unroll
-                for (int i = 1; i < kBinMax; ++i)
-                    if (i <= k) vf[i] = (float)v[i];
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < kBinMax; ++i)
-        if (i <= k) P.gout[base + i] = v[i];
-    if (P.a_next) {
-        vf[0] = (float)v[0];
-        const float h = (float)G.hbin[j];
-#pragma unroll
-        for (int i = 0; i < kBinMax; ++i)
-            if (i <= k) chunk_put(ch, P, tile, row, j * K1 + i, vf[i] * h);
-    }
-    msum += G.hbin[j] * v[0];
-}
-
-// stage inputs of bin j (zeros beyond k)
-__device__ __forceinline__ void load_bin(const TcParams &P, long long cell, int j, double *gnb, double *gsb)
-{
-    const size_t base = (size_t)cell * P.G.P + (size_t)j * P.G.K1;
-#pragma unroll
-    for (int i = 0; i < kBinMax; ++i) {
-        const bool ok = P.mode == 2 && i <= P.G.k;
-        gnb[i] = ok ? P.gn[base + i] : 0.0;
-        gsb[i] = ok ? P.gs[base + i] : 0.0;
-    }
-}
-
-// ---------------------------------------------------------------- kernel
-struct Smem {
-    uint64_t a_full, a_empty;
-    uint64_t full[kMaxSlots], empty[kMaxSlots];
-    uint64_t acc_full[2], acc_empty[2];
-    uint64_t mma_drain;
-    uint32_t tmem_base;
-    int abort_flag;
-    int slot_issued[kMaxSlots];  // copies issued per slot (producer)
-    int slot_done[kMaxSlots];    // copies consumed per slot (MMA)
-    int a_issued, a_done;
-};
-
-__device__ __forceinline__ void fail(TcParams &P, volatile int *abort_flag, int code)
-{
-    if (P.err) atomicOr(P.err, code);
-    *abort_flag = 1;
-}
-
-// TMEM -> registers, 32 lanes x 32 columns, no wait
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r)
 {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -356,45 +230,134 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Each CTA takes NT 128-cell tiles at a time (a pair when both A tiles fit in
-// shared memory): every B atom it streams feeds NT MMAs, one per cell tile, so
-// B traffic per cell drops by NT.  TMEM holds NT tiles x 2 buffers x 128 columns.
-template <int NT>
-__global__ void __launch_bounds__(Cfg<NT>::threads, 1) contract_tc_kernel(TcParams P)
+// ---------------------------------------------------------------- kernel
+struct Smem {
+    uint64_t a_full[2], a_empty[2];
+    uint64_t full[kMaxSlots], empty[kMaxSlots];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t mma_drain;
+    uint32_t tmem_base;
+    int abort_flag;
+    int slot_issued[kMaxSlots];  // copies issued per slot (producer)
+    int slot_done[kMaxSlots];    // copies consumed per slot (MMA)
+    int a_issued[2], a_done[2];
+};
+
+__device__ __forceinline__ void fail(const TcParams &P, volatile int *abort_flag, int code)
 {
-    constexpr int kEpiWarps = Cfg<NT>::epi_warps;
-    constexpr int kTmemCols = Cfg<NT>::tmem_cols;
+    if (P.err) atomicOr(P.err, code);
+    *abort_flag = 1;
+}
+
+// One tile of the epilogue for a p window of width W: loads the cell's ghat
+// window [p0, p0 + W) from its A tile in shared memory, then adds to Facc[m]
+// (functional f = kEpiSplit m + part of the tile) the sum over the functional's W
+// accumulator columns times the window; G functionals' TMEM loads are in
+// flight before each wait.
+template <int PREC, int W, int G>
+__device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_bytes, int row, int p0,
+                                         uint32_t tcol, int nf, int part, float *Facc)
+{
+    float gw[W];
+    if (PREC == GRACE_TF32) {
+#pragma unroll
+        for (int c = 0; c < W / 4; ++c) {
+            const float4 v = *reinterpret_cast<const float4 *>(a_gen + swz_offset(kTileM, row, p0 + 4 * c, 4));
+            gw[4 * c] = v.x;
+            gw[4 * c + 1] = v.y;
+            gw[4 * c + 2] = v.z;
+            gw[4 * c + 3] = v.w;
+        }
+    } else {
+        const size_t lo_plane = (size_t)(a_tile_bytes / 2);
+#pragma unroll
+        for (int c = 0; c < W / 8; ++c) {
+            const size_t off = swz_offset(kTileM, row, p0 + 8 * c, 2);
+            const uint4 hi = *reinterpret_cast<const uint4 *>(a_gen + off);
+            const uint4 lo = *reinterpret_cast<const uint4 *>(a_gen + lo_plane + off);
+            const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                gw[8 * c + 2 * e] = __uint_as_float(hw[e] << 16) + __uint_as_float(lw[e] << 16);
+                gw[8 * c + 2 * e + 1] = __uint_as_float(hw[e] & 0xFFFF0000u) + __uint_as_float(lw[e] & 0xFFFF0000u);
+            }
+        }
+    }
+#pragma unroll
+    for (int m0 = 0; m0 < kMaxF / kEpiSplit; m0 += G) {
+        if (kEpiSplit * m0 + part >= nf) break;
+        uint32_t y[G][W];
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+            const int f = kEpiSplit * (m0 + gg) + part;
+            if (f < nf) {
+                if (W == 32) tmem_ld32(tcol + (uint32_t)(f * W), y[gg]);
+                else tmem_ld16(tcol + (uint32_t)(f * W), y[gg]);
+            }
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+            const int f = kEpiSplit * (m0 + gg) + part;
+            if (f < nf) {
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int c = 0; c < W; c += 2) {
+                    s0 = fmaf(gw[c], __uint_as_float(y[gg][c]), s0);
+                    s1 = fmaf(gw[c + 1], __uint_as_float(y[gg][c + 1]), s1);
+                }
+                Facc[m0 + gg] += s0 + s1;
+            }
+        }
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
+{
+    constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
+    constexpr int kps = PREC == GRACE_TF32 ? 4 : 2;   // MMA k-steps per B copy (32 KB at N = 256)
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    const uint32_t a_smem = base;                                          // NT A tiles
-    const uint32_t b_smem = base + (uint32_t)NT * (uint32_t)P.a_tile_bytes;   // B ring
-    Smem *S = reinterpret_cast<Smem *>(gbase + NT * P.a_tile_bytes + (size_t)P.n_slots * P.slot_bytes);
+    const uint32_t a_smem = base;
+    const uint32_t b_smem = base + (uint32_t)P.a_bufs * (uint32_t)P.a_tile_bytes;
+    uint8_t *tab = gbase + P.a_bufs * P.a_tile_bytes + (size_t)P.n_slots * P.slot_bytes;
+    const TileDesc *tiles = reinterpret_cast<const TileDesc *>(tab);
+    const int *ford = reinterpret_cast<const int *>(tab + (size_t)P.n_tiles * sizeof(TileDesc));
+    Smem *S = reinterpret_cast<Smem *>(tab + P.table_bytes);
     volatile int *abort_flag = &S->abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int planes = P.prec == GRACE_TF32 ? 1 : 2;
     const int NS = P.n_slots;
-    const int n_pairs = (P.n_cell_tiles + NT - 1) / NT;   // CTA work items of NT tiles
+    const int n_items = P.n_cell_tiles * P.n_splits;
 
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&S->a_full), 1);
-        mbar_init(smem_u32(&S->a_empty), 1 + kEpiWarps);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&S->a_full[b]), 1);
+            mbar_init(smem_u32(&S->a_empty[b]), 1 + kEpiWarps);
+            mbar_init(smem_u32(&S->acc_full[b]), 1);
+            mbar_init(smem_u32(&S->acc_empty[b]), kEpiWarps);
+            S->a_issued[b] = S->a_done[b] = 0;
+        }
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&S->full[s]), 1);
             mbar_init(smem_u32(&S->empty[s]), 1);
             S->slot_issued[s] = 0;
             S->slot_done[s] = 0;
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&S->acc_full[b]), 1);
-            mbar_init(smem_u32(&S->acc_empty[b]), kEpiWarps);
-        }
         mbar_init(smem_u32(&S->mma_drain), 1);
         S->abort_flag = 0;
-        S->a_issued = S->a_done = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // tile table and functional order into shared memory (read by every role for every tile)
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(P.tiles);
+        int4 *dst = reinterpret_cast<int4 *>(tab);
+        for (int i = threadIdx.x; i < P.n_tiles * (int)(sizeof(TileDesc) / 16); i += blockDim.x) dst[i] = src[i];
+        int *fo = const_cast<int *>(ford);
+        for (int i = threadIdx.x; i < P.R; i += blockDim.x) fo[i] = P.ford[i];
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -408,105 +371,121 @@ __global__ void __launch_bounds__(Cfg<NT>::threads, 1) contract_tc_kernel(TcPara
     tc_fence_after();
     const uint32_t tmem = S->tmem_base;
 
-    if (warp == 0 && lane == 0) {
-        // ------------------------------------------------ producer
-        int slot = 0, nuse = 0, ctl = 0;
-        for (int pr = blockIdx.x; pr < n_pairs && !*abort_flag; pr += gridDim.x, ++ctl) {
-            if (ctl > 0 && !mbar_wait(smem_u32(&S->a_empty), (ctl - 1) & 1, abort_flag)) {
-                fail(P, abort_flag, 1);
-                break;
-            }
-            const uint32_t abytes = (uint32_t)NT * (uint32_t)P.a_tile_bytes;   // the NT tiles are contiguous
-            mbar_expect_tx(smem_u32(&S->a_full), abytes);
-            bulk_g2s(a_smem, P.A + (size_t)(NT * pr) * P.a_tile_bytes, abytes, smem_u32(&S->a_full));
-            S->a_issued = ctl + 1;
-            for (int t = 0; t < P.n_tiles && !*abort_flag; ++t) {
-                const TileDesc td = P.tiles[t];
-                const uint32_t atom_bytes = (uint32_t)td.nrows * 128u * planes;
-                for (int a = 0; a < td.n_atoms; ++a) {
-                    const int use = nuse / NS;
-                    if (use > 0 && !mbar_wait(smem_u32(&S->empty[slot]), (use - 1) & 1, abort_flag)) {
-                        fail(P, abort_flag, 2);
-                        break;
+    if (warp == 0 || warp == 3) {
+        // ------------------------------------------------ producers: warp 0 loads the A tiles and the
+        // even-numbered B copies, warp 3 the odd ones (each issuing thread retires about one bulk copy
+        // at a time, so two issuers keep twice as many copies in flight)
+        const int me = warp == 0 ? 0 : 1;
+        int q = 0, ctl = 0;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
+            const int ct = it / P.n_splits, sp = it - ct * P.n_splits;
+            const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
+            int ok = 1;
+            if (lane == 0) {
+                if (*abort_flag) ok = 0;
+                else if (me == 0) {
+                    if (au > 0 && !mbar_wait(smem_u32(&S->a_empty[ab]), (au - 1) & 1, abort_flag)) {
+                        fail(P, abort_flag, 1);
+                        ok = 0;
                     }
-                    mbar_expect_tx(smem_u32(&S->full[slot]), atom_bytes);
-                    bulk_g2s(b_smem + (uint32_t)slot * P.slot_bytes, P.B + td.b_off + (size_t)a * atom_bytes,
-                             atom_bytes, smem_u32(&S->full[slot]));
-                    S->slot_issued[slot] = use + 1;
-                    ++nuse;
-                    slot = nuse % NS;
+                    if (ok) {
+                        mbar_expect_tx(smem_u32(&S->a_full[ab]), (uint32_t)P.a_tile_bytes);
+                        bulk_g2s(a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes, P.A + (size_t)ct * P.a_tile_bytes,
+                                 (uint32_t)P.a_tile_bytes, smem_u32(&S->a_full[ab]));
+                        S->a_issued[ab] = au + 1;
+                    }
                 }
             }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            for (int t = P.split[sp]; t < P.split[sp + 1] && ok; ++t) {
+                const TileDesc td = tiles[t];
+                const int nks = td.ks_hi - td.ks_lo, n_copies = (nks + kps - 1) / kps;
+                const uint32_t ks_bytes = (uint32_t)td.n * 32u * planes;
+                const uint8_t *bsrc = P.B + (size_t)td.b_off16 * 16;
+                if (lane == 0)
+                    for (int c = 0; c < n_copies; ++c, ++q) {
+                        if ((q & 1) != me) continue;
+                        const int slot = q % NS, use = q / NS;
+                        if (use > 0 && !mbar_wait(smem_u32(&S->empty[slot]), (use - 1) & 1, abort_flag)) {
+                            fail(P, abort_flag, 2);
+                            ok = 0;
+                            break;
+                        }
+                        const int k0 = c * kps, kn = min(kps, nks - k0);
+                        const uint32_t bytes = (uint32_t)kn * ks_bytes;
+                        mbar_expect_tx(smem_u32(&S->full[slot]), bytes);
+                        bulk_g2s(b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes, bsrc + (size_t)k0 * ks_bytes, bytes,
+                                 smem_u32(&S->full[slot]));
+                        S->slot_issued[slot] = use + 1;
+                    }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                q = __shfl_sync(0xffffffffu, q, 0);
+            }
+            if (!ok) break;
         }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
-        int slot = 0, nuse = 0, acc_use = 0, ctl = 0;
-        const uint32_t a1 = a_smem + (uint32_t)P.a_tile_bytes;
-        for (int pr = blockIdx.x; pr < n_pairs && !*abort_flag; pr += gridDim.x, ++ctl) {
-            if (!mbar_wait(smem_u32(&S->a_full), ctl & 1, abort_flag)) {
+        int q = 0, acc_use = 0, ctl = 0;
+        for (int it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x, ++ctl) {
+            const int ct = it / P.n_splits, sp = it - ct * P.n_splits;
+            const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
+            if (!mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag)) {
                 fail(P, abort_flag, 4);
                 break;
             }
-            S->a_done = ctl + 1;
+            S->a_done[ab] = au + 1;
             tc_fence_after();
-            for (int t = 0; t < P.n_tiles && !*abort_flag; ++t) {
-                const TileDesc td = P.tiles[t];
+            const uint32_t a0 = a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes;
+            const uint32_t a_lo = a0 + (uint32_t)(P.a_tile_bytes / 2);
+            for (int t = P.split[sp]; t < P.split[sp + 1] && !*abort_flag; ++t) {
+                const TileDesc td = tiles[t];
                 const int buf = acc_use & 1, bu = acc_use >> 1;
                 if (bu > 0 && !mbar_wait(smem_u32(&S->acc_empty[buf]), (bu - 1) & 1, abort_flag)) {
                     fail(P, abort_flag, 8);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d0 = tmem + (uint32_t)(buf * kAccCols);
-                const uint32_t d1 = d0 + (uint32_t)kHalfCols;
-                const uint32_t idesc = instr_desc(P.prec, td.nrows);
-                int first = 1;
-                for (int a = 0; a < td.n_atoms; ++a) {
-                    const int use = nuse / NS;
+                const uint32_t d = tmem + (uint32_t)(buf * kAccCols);
+                const uint32_t idesc = instr_desc(PREC, td.n);
+                const uint32_t ks_bytes = (uint32_t)td.n * 32u * planes;
+                const int nks = td.ks_hi - td.ks_lo, n_copies = (nks + kps - 1) / kps;
+                uint32_t acc = 0u;
+                for (int c = 0; c < n_copies; ++c) {
+                    const int slot = q % NS, use = q / NS;
                     if (!mbar_wait(smem_u32(&S->full[slot]), use & 1, abort_flag)) {
                         fail(P, abort_flag, 16);
                         break;
                     }
                     S->slot_done[slot] = use + 1;
                     tc_fence_after();
-                    const int atom = td.atom_lo + a;
-                    const uint32_t bslot = b_smem + (uint32_t)slot * P.slot_bytes;
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const int ks = atom * 4 + kk;
-                        if (ks < td.ks_lo || ks >= td.ks_hi) continue;
-                        const uint32_t a_off = (uint32_t)atom * (kTileM * 128u) + (uint32_t)kk * 32u;
-                        const uint64_t bd = smem_desc(bslot + (uint32_t)kk * 32u);
-                        const uint32_t acc = first ? 0u : 1u;
-                        if (P.prec == GRACE_TF32) {
-                            mma_tf32(d0, smem_desc(a_smem + a_off), bd, idesc, acc);
-                            if (NT == 2) mma_tf32(d1, smem_desc(a1 + a_off), bd, idesc, acc);
+                    const uint32_t bslot = b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes;
+                    const int k0 = c * kps, kn = min(kps, nks - k0);
+                    for (int kk = 0; kk < kn; ++kk) {
+                        const int ks = td.ks_lo + k0 + kk;
+                        const uint32_t a_off = (uint32_t)(ks >> 2) * (kTileM * 128u) + (uint32_t)(ks & 3) * 32u;
+                        const uint32_t bk = bslot + (uint32_t)kk * ks_bytes;
+                        if (PREC == GRACE_TF32) {
+                            mma_tf32(d, desc_sw128(a0 + a_off), desc_sw32(bk), idesc, acc);
                         } else {
-                            const uint32_t lo_plane = (uint32_t)(P.a_tile_bytes / 2);
-                            const uint64_t bl = smem_desc(bslot + (uint32_t)td.nrows * 128u + (uint32_t)kk * 32u);
-                            mma_f16(d0, smem_desc(a_smem + a_off), bd, idesc, acc);
-                            mma_f16(d0, smem_desc(a_smem + a_off), bl, idesc, 1u);
-                            mma_f16(d0, smem_desc(a_smem + lo_plane + a_off), bd, idesc, 1u);
-                            if (NT == 2) {
-                                mma_f16(d1, smem_desc(a1 + a_off), bd, idesc, acc);
-                                mma_f16(d1, smem_desc(a1 + a_off), bl, idesc, 1u);
-                                mma_f16(d1, smem_desc(a1 + lo_plane + a_off), bd, idesc, 1u);
-                            }
+                            const uint64_t bh = desc_sw32(bk), bl = desc_sw32(bk + (uint32_t)td.n * 32u);
+                            mma_f16(d, desc_sw128(a0 + a_off), bh, idesc, acc);
+                            mma_f16(d, desc_sw128(a0 + a_off), bl, idesc, 1u);
+                            mma_f16(d, desc_sw128(a_lo + a_off), bh, idesc, 1u);
                         }
-                        first = 0;
+                        acc = 1u;
                     }
                     tc_commit(smem_u32(&S->empty[slot]));   // frees the slot once these MMAs retire
-                    ++nuse;
-                    slot = nuse % NS;
+                    ++q;
                 }
                 if (*abort_flag) break;
-                if (first) {
+                if (!acc) {
                     fail(P, abort_flag, 64);   // tiles are built with a non-empty K range
                     break;
                 }
                 tc_commit(smem_u32(&S->acc_full[buf]));
                 ++acc_use;
             }
-            tc_commit(smem_u32(&S->a_empty));   // the A pair may be overwritten once these MMAs retire
+            tc_commit(smem_u32(&S->a_empty[ab]));   // the A tile may be overwritten once these MMAs retire
         }
         if (*abort_flag) {
             tc_commit(smem_u32(&S->mma_drain));
@@ -516,143 +495,68 @@ __global__ void __launch_bounds__(Cfg<NT>::threads, 1) contract_tc_kernel(TcPara
         }
     } else if (warp >= 4) {
         // ------------------------------------------------ epilogue: one thread per cell
-        const int half = (warp - 4) >> 2;    // which tile of the pair
-        const int q = warp & 3;              // TMEM lane quadrant (warp % 4)
-        const int row = q * 32 + lane;
-        const uint8_t *a_gen = gbase + (size_t)half * P.a_tile_bytes;
-        const uint32_t tcol0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * kHalfCols);
+        const int part = (warp - 4) >> 2;    // functionals f with f % kEpiSplit == part
+        const int qd = warp & 3;             // TMEM lane quadrant (warp % 4)
+        const int row = qd * 32 + lane;
+        const uint32_t tlane = (uint32_t)(qd * 32) << 16;
         int acc_use = 0, ctl = 0;
-        for (int pr = blockIdx.x; pr < n_pairs && !*abort_flag; pr += gridDim.x, ++ctl) {
-            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full), ctl & 1, abort_flag))) {
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
+            const int ct = it / P.n_splits, sp = it - ct * P.n_splits;
+            const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag))) {
                 fail(P, abort_flag, 32);
                 break;
             }
-            const long long cell = (long long)(NT * pr + half) * kTileM + row;
+            const uint8_t *a_gen = gbase + (size_t)ab * P.a_tile_bytes;
+            const long long cell = (long long)ct * kTileM + row;
             const bool live = cell < P.n_cells;
-            float Facc[kMaxFunc] = {0.f, 0.f, 0.f, 0.f};
-            // fused update state of this cell
-            const double dtc = (P.mode == 2 && live) ? P.dt[cell] : 0.0;
-            double msum = 0.0;
-            unsigned fl = 0u;
-            OpChunk ch;
-            ch.c = -1;
-            uint8_t *anext = P.a_next ? P.a_next + (size_t)(NT * pr + half) * P.a_tile_bytes : nullptr;
-            int jnext = 0;          // next bin to update
-            float Fprev = 0.f;      // F(x_{jnext - 1/2}); F(x_min) = 0
-            for (int t = 0; t < P.n_tiles; ++t) {
-                if (__any_sync(0xffffffffu, *abort_flag)) break;
-                const TileDesc td = P.tiles[t];
-                // ghat window [p0, p0 + 32) of this thread's cell from its A tile
-                float gw[kWin];
-                if (P.prec == GRACE_TF32) {
+            float Facc[kMaxF / kEpiSplit];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float4 v = *reinterpret_cast<const float4 *>(a_gen + swz_offset(kTileM, row, td.p0 + 4 * c, 4));
-                        gw[4 * c] = v.x;
-                        gw[4 * c + 1] = v.y;
-                        gw[4 * c + 2] = v.z;
-                        gw[4 * c + 3] = v.w;
-                    }
-                } else {
-                    const size_t lo_plane = (size_t)(P.a_tile_bytes / 2);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const size_t off = swz_offset(kTileM, row, td.p0 + 8 * c, 2);
-                        const uint4 hi = *reinterpret_cast<const uint4 *>(a_gen + off);
-                        const uint4 lo = *reinterpret_cast<const uint4 *>(a_gen + lo_plane + off);
-                        const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            gw[8 * c + 2 * e] = __uint_as_float(hw[e] << 16) + __uint_as_float(lw[e] << 16);
-                            gw[8 * c + 2 * e + 1] =
-                                __uint_as_float(hw[e] & 0xFFFF0000u) + __uint_as_float(lw[e] & 0xFFFF0000u);
-                        }
-                    }
+            for (int m = 0; m < kMaxF / kEpiSplit; ++m) Facc[m] = 0.f;
+            bool aborted = false;
+            for (int t = P.split[sp]; t < P.split[sp + 1]; ++t) {
+                if (__any_sync(0xffffffffu, *abort_flag)) {
+                    aborted = true;
+                    break;
                 }
-                // stage inputs of the next bin to update, loaded before the accumulator wait
-                double pgn[kBinMax], pgs[kBinMax];
-                const bool pre = P.mode == 2 && td.flush && live && jnext <= td.bin_hi;
-                if (pre) load_bin(P, cell, jnext, pgn, pgs);
+                const TileDesc td = tiles[t];
+                const int nf = td.nf_flush & 0xFFFF;
                 const int buf = acc_use & 1, bu = acc_use >> 1;
                 if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->acc_full[buf]), bu & 1, abort_flag))) {
                     fail(P, abort_flag, 128);
+                    aborted = true;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tcol = tcol0 + (uint32_t)(buf * kAccCols);
-                for (int f = 0; f < td.nf; f += 2) {
-                    uint32_t y0[kWin], y1[kWin];
-                    tmem_ld32_nowait(tcol + (uint32_t)(f * kWin), y0);
-                    if (f + 1 < td.nf) tmem_ld32_nowait(tcol + (uint32_t)((f + 1) * kWin), y1);
-                    tmem_wait_ld();
-                    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                    for (int c = 0; c < kWin; ++c) s0 = fmaf(gw[c], __uint_as_float(y0[c]), s0);
-                    Facc[f] += s0;
-                    if (f + 1 < td.nf) {
-#pragma unroll
-                        for (int c = 0; c < kWin; ++c) s1 = fmaf(gw[c], __uint_as_float(y1[c]), s1);
-                        Facc[f + 1] += s1;
-                    }
-                }
+                const uint32_t tcol = tmem + tlane + (uint32_t)(buf * kAccCols);
+                epi_tile<PREC, kWin, kMaxF / kEpiSplit>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, Facc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&S->acc_empty[buf]));
                 ++acc_use;
-                if (td.flush) {
-                    if (P.mode == 0) {
-                        if (live)
-                            for (int f = 0; f < td.nf; ++f) P.F[cell * P.R + td.r[f]] = Facc[f];
-                    } else if (live) {
-                        // bins [jnext, bin_hi]: functionals of this group by (bin, i), 0 where absent
-                        const int K1 = P.G.K1;
-                        float Fb[kMaxFunc * (kKMax + 1)];
-                        for (int e = 0; e < kMaxFunc * (kKMax + 1); ++e) Fb[e] = 0.f;
-                        for (int f = 0; f < td.nf; ++f) {
-                            const int r = td.r[f];
-                            int jj, ii;
-                            if (r < P.G.n_if) { jj = r; ii = 0; }
-                            else { const int qq = r - P.G.n_if; jj = qq / P.G.k; ii = qq % P.G.k + 1; }
-                            const int slot = (jj - td.bin_lo) * K1 + ii;
-                            for (int e = 0; e < kMaxFunc * (kKMax + 1); ++e) Fb[e] = e == slot ? Facc[f] : Fb[e];
-                        }
-                        for (bool first_bin = true; jnext <= td.bin_hi; ++jnext, first_bin = false) {
-                            float Fp = 0.f, V[kKMax] = {0.f, 0.f, 0.f};
-                            if (jnext >= td.bin_lo) {
-                                const int o = (jnext - td.bin_lo) * K1;
-                                for (int e = 0; e < kMaxFunc * (kKMax + 1); ++e) {
-                                    Fp = e == o ? Fb[e] : Fp;
-                                    for (int i = 1; i <= kKMax; ++i) V[i - 1] = e == o + i ? Fb[e] : V[i - 1];
-                                }
-                            }
-                            if (jnext >= P.G.n_if) Fp = 0.f;   // F(x_max) = 0 for conservative fluxes
-                            if (!(pre && first_bin)) load_bin(P, cell, jnext, pgn, pgs);
-                            update_bin(P, cell, jnext, Fprev, Fp, V, dtc, pgn, pgs, msum, fl, ch, anext, row);
-                            Fprev = Fp;
+                if (td.nf_flush >> 16) {
+                    if (live) {
+                        float *Fo = P.F + ((size_t)ct * P.R) * kTileM + row;
+#pragma unroll
+                        for (int m = 0; m < kMaxF / kEpiSplit; ++m) {
+                            const int f = kEpiSplit * m + part;
+                            if (f < nf) Fo[(size_t)ford[td.f0 + f] * kTileM] = Facc[m];
                         }
                     }
-                    for (int f = 0; f < kMaxFunc; ++f) Facc[f] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < kMaxF / kEpiSplit; ++m) Facc[m] = 0.f;
                 }
             }
-            if (P.mode != 0 && live) {
-                const float V0[kKMax] = {0.f, 0.f, 0.f};
-                for (; jnext < P.G.N; ++jnext) {   // bins whose functionals all vanish
-                    double gnb[kBinMax], gsb[kBinMax];
-                    load_bin(P, cell, jnext, gnb, gsb);
-                    update_bin(P, cell, jnext, Fprev, 0.f, V0, dtc, gnb, gsb, msum, fl, ch, anext, row);
-                    Fprev = 0.f;
-                }
-                if (anext) chunk_flush(ch, P, anext, row);
-                if (P.mass) P.mass[cell] = msum;
-                if (P.flags && fl) P.flags[cell] |= (unsigned char)fl;
-            }
+            if (aborted) break;
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&S->a_empty));
+            if (lane == 0) mbar_arrive(smem_u32(&S->a_empty[ab]));
         }
     }
 
     // ---------------------------------------------------- teardown
+    // every role has stopped issuing; after an abort, drain the copies still in flight
     __syncwarp();
+    __syncthreads();
     if (warp == 0 && lane == 0 && *abort_flag) {
         // drain copies still in flight into this CTA's shared memory (bounded)
         for (int s = 0; s < NS; ++s)
@@ -661,11 +565,12 @@ __global__ void __launch_bounds__(Cfg<NT>::threads, 1) contract_tc_kernel(TcPara
                 while (!mbar_try_wait(smem_u32(&S->full[s]), u & 1) && clock64() - t0 < kWaitCycles) {
                 }
             }
-        for (int u = S->a_done; u < S->a_issued; ++u) {
-            const long long t0 = clock64();
-            while (!mbar_try_wait(smem_u32(&S->a_full), u & 1) && clock64() - t0 < kWaitCycles) {
+        for (int b = 0; b < 2; ++b)
+            for (int u = S->a_done[b]; u < S->a_issued[b]; ++u) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(smem_u32(&S->a_full[b]), u & 1) && clock64() - t0 < kWaitCycles) {
+                }
             }
-        }
     }
     tc_fence_before();
     __syncthreads();
@@ -683,6 +588,7 @@ void free_tc_tiles(TcTiles &t)
 {
     cudaFree(t.d_b);
     cudaFree(t.d_desc);
+    cudaFree(t.d_ford);
     t = TcTiles();
 }
 
@@ -691,9 +597,14 @@ size_t opA_bytes_for(const DevGroup &g, int prec, int n_cells, int *kpad)
     const int ae = atom_elems(prec);
     const int kp = (g.P + ae - 1) / ae * ae;
     if (kpad) *kpad = kp;
-    size_t tiles = ((size_t)n_cells + kTileM - 1) / kTileM;
-    tiles += tiles & 1;   // the contraction takes tiles in pairs; a missing partner reads zeros
+    const size_t tiles = ((size_t)n_cells + kTileM - 1) / kTileM;
     return tiles * opA_tile_bytes(prec, kp);
+}
+
+size_t f32_bytes_for(const DevGroup &g, int n_cells)
+{
+    const size_t tiles = ((size_t)n_cells + kTileM - 1) / kTileM;
+    return tiles * (size_t)g.R * kTileM * sizeof(float);
 }
 
 static uint16_t bf16_bits_rn(float f)
@@ -723,149 +634,227 @@ static uint32_t tf32_bits_rn(float f)
     return u & 0xFFFFE000u;
 }
 
+// byte offset of element x (0 .. 32/eb - 1) of row `row` in a K-major SWIZZLE_32B k-step block
+static inline size_t sw32_offset(int row, int x, int eb)
+{
+    const int byte = x * eb;
+    const int chunk = (byte >> 4) ^ ((row >> 2) & 1);
+    return (size_t)row * 32 + (chunk << 4) + (byte & 15);
+}
+
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
 {
     const DevGroup &g = G.dg;
-    if (g.k > 3) {
+    if (g.k > kKMax) {
         set_error("tensor-core tiles need k <= 3");
         return GRACE_ERR_UNSUPPORTED;
     }
     const int P_ = g.P, R = g.R, K1 = g.K1;
-    const int ae = atom_elems(prec), eb = elem_bytes(prec), planes = n_planes(prec);
-    const int kstep = 32 / eb;   // elements per MMA k-step
+    const int eb = elem_bytes(prec), planes = n_planes(prec);
+    const int kstep = 32 / eb;                        // elements per MMA k-step
+    const int kps = prec == GRACE_TF32 ? 4 : 2;       // k-steps per B copy
+    const int mult = prec == GRACE_TF32 ? 1 : 3;      // MMAs per k-step
     std::vector<double> T((size_t)R * P_ * P_);
-    std::vector<int> qlo((size_t)R * P_), qhi((size_t)R * P_), pr(2 * R);
     cudaError_t e = cudaMemcpyAsync(T.data(), G.d_T, T.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(qlo.data(), G.d_qlo, qlo.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(qhi.data(), G.d_qhi, qhi.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(pr.data(), G.d_prange, pr.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core tiles: copy T");
 
     std::vector<double> h(g.N);
     for (int j = 0; j < g.N; ++j) h[j] = G.h_edges[j + 1] - G.h_edges[j];
 
-    // functional groups: whole bins, in bin order, up to kMaxFunc functionals each
-    // (the fused update needs every functional of a bin in one group)
-    std::vector<std::vector<int>> groups;
-    std::vector<std::pair<int, int>> gbins;
-    std::vector<int> cur;
-    int cur_lo = 0;
-    for (int j = 0; j < g.N; ++j) {
-        std::vector<int> fj;
-        if (j < g.n_if) fj.push_back(j);
-        for (int i = 1; i <= g.k; ++i) fj.push_back(g.n_if + j * g.k + i - 1);
-        if (fj.size() > (size_t)kMaxFunc) {
-            set_error("tensor-core tiles: a bin has more functionals than a tile holds");
-            return GRACE_ERR_UNSUPPORTED;
-        }
-        if (!cur.empty() && cur.size() + fj.size() > (size_t)kMaxFunc) {
-            groups.push_back(cur);
-            gbins.push_back({cur_lo, j - 1});
-            cur.clear();
-        }
-        if (cur.empty()) cur_lo = j;
-        for (int r : fj) cur.push_back(r);
-    }
-    if (!cur.empty()) {
-        groups.push_back(cur);
-        gbins.push_back({cur_lo, g.N - 1});
+    // fold onto the upper triangle (in place) and record each row's q extent
+    std::vector<int> qlo((size_t)R * P_, P_), qhi((size_t)R * P_, 0);
+    long long nnz_fold = 0;
+    for (int r = 0; r < R; ++r) {
+        double *Tr = T.data() + (size_t)r * P_ * P_;
+        for (int p = 0; p < P_; ++p)
+            for (int q = p + 1; q < P_; ++q) {
+                Tr[(size_t)p * P_ + q] += Tr[(size_t)q * P_ + p];
+                Tr[(size_t)q * P_ + p] = 0.0;
+            }
+        for (int p = 0; p < P_; ++p)
+            for (int q = p; q < P_; ++q)
+                if (Tr[(size_t)p * P_ + q] != 0.0) {
+                    ++nnz_fold;
+                    qlo[(size_t)r * P_ + p] = std::min(qlo[(size_t)r * P_ + p], q);
+                    qhi[(size_t)r * P_ + p] = q + 1;
+                }
     }
 
+    // functionals in bin order: interface flux of bin j, then its volume terms
+    std::vector<int> ford;
+    for (int j = 0; j < g.N; ++j) {
+        if (j < g.n_if) ford.push_back(j);
+        for (int i = 1; i <= g.k; ++i) ford.push_back(g.n_if + j * g.k + i - 1);
+    }
+    if ((int)ford.size() != R) {
+        set_error("tensor-core tiles: functional count mismatch");
+        return GRACE_ERR_ARG;
+    }
+
+    // per functional: union of the q extents over each window of kWin p (the
+    // epilogue holds one window of ghat and all of a warp's accumulator columns
+    // in registers, which fixes the width; N = nf * kWin is chosen per group)
+    const int widths[1] = {kWin};
+    struct Ext {
+        int lo, hi;
+    };
+    std::vector<std::vector<Ext>> wext[1];
+    int n_win[1];
+    for (int wi = 0; wi < 1; ++wi) {
+        const int W = widths[wi];
+        n_win[wi] = (P_ + W - 1) / W;
+        wext[wi].assign(R, std::vector<Ext>(n_win[wi], Ext{P_, 0}));
+        for (int x = 0; x < R; ++x) {
+            const int r = ford[x];
+            for (int p = 0; p < P_; ++p) {
+                const size_t row = (size_t)r * P_ + p;
+                if (qhi[row] <= qlo[row]) continue;
+                Ext &E = wext[wi][x][p / W];
+                E.lo = std::min(E.lo, qlo[row]);
+                E.hi = std::max(E.hi, qhi[row]);
+            }
+        }
+    }
+    auto tile_cost = [&](int n, int nks) {
+        const double mma = (double)nks * mult * kMmaClk;
+        const double l2 = (double)nks * n * 32.0 * planes / kL2BytesPerClk;
+        const double epi = n + 150.0;
+        return std::max(mma, std::max(l2, epi)) + kTileClk;
+    };
+    // dynamic program over the functional order: best[y] = cheapest cover of ford[0, y)
+    const double inf = 1e300;
+    std::vector<double> best(R + 1, inf);
+    std::vector<int> from(R + 1, -1), wsel(R + 1, 0);
+    best[0] = 0.0;
+    for (int x = 0; x < R; ++x) {
+        if (best[x] >= inf) continue;
+        for (int wi = 0; wi < 1; ++wi) {
+            const int W = widths[wi], maxf = std::min(kMaxF, kMaxN / W);
+            std::vector<Ext> U(n_win[wi], Ext{P_, 0});
+            for (int y = x + 1; y <= std::min(R, x + maxf); ++y) {
+                double c = 0.0;
+                for (int w = 0; w < n_win[wi]; ++w) {
+                    const Ext &E = wext[wi][y - 1][w];
+                    U[w].lo = std::min(U[w].lo, E.lo);
+                    U[w].hi = std::max(U[w].hi, E.hi);
+                    if (U[w].hi > U[w].lo)
+                        c += tile_cost((y - x) * W, (U[w].hi + kstep - 1) / kstep - U[w].lo / kstep);
+                }
+                if (best[x] + c < best[y]) {
+                    best[y] = best[x] + c;
+                    from[y] = x;
+                    wsel[y] = wi;
+                }
+            }
+        }
+    }
+    std::vector<std::pair<int, int>> groups;   // (x, wi) in order
+    for (int y = R; y > 0; y = from[y]) groups.push_back({from[y], wsel[y]});
+    std::reverse(groups.begin(), groups.end());
+
+    TcTiles out;
     std::vector<TileDesc> tiles;
     std::vector<uint8_t> B;
-    long long macs = 0;
+    long long macs = 0, mmas = 0;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
-        const auto &grp = groups[gi];
-        int plo = P_, phi = 0;
-        for (int r : grp)
-            if (pr[2 * r + 1] > pr[2 * r]) {
-                plo = std::min(plo, pr[2 * r]);
-                phi = std::max(phi, pr[2 * r + 1]);
+        const int x = groups[gi].first, wi = groups[gi].second;
+        const int y = gi + 1 < groups.size() ? groups[gi + 1].first : R;
+        const int W = widths[wi], nf = y - x, n = nf * W;
+        const size_t first = tiles.size();
+        double gcost = 0.0;
+        for (int w = 0; w < n_win[wi]; ++w) {
+            Ext U{P_, 0};
+            for (int f = x; f < y; ++f) {
+                U.lo = std::min(U.lo, wext[wi][f][w].lo);
+                U.hi = std::max(U.hi, wext[wi][f][w].hi);
             }
-        if (phi <= plo) continue;   // all functionals of the group vanish identically
-        const int nf = (int)grp.size(), nrows = nf * kWin;
-        size_t first_tile = tiles.size();
-        for (int w = plo / kWin; w * kWin < phi; ++w) {
-            const int p0 = w * kWin;
-            int q_lo = P_, q_hi = 0;
-            for (int f = 0; f < nf; ++f)
-                for (int c = 0; c < kWin; ++c) {
-                    const int p = p0 + c;
-                    if (p >= P_) continue;
-                    const size_t row = (size_t)grp[f] * P_ + p;
-                    if (qlo[row] < qhi[row]) {
-                        q_lo = std::min(q_lo, qlo[row]);
-                        q_hi = std::max(q_hi, qhi[row]);
-                    }
-                }
-            if (q_hi <= q_lo) continue;
+            if (U.hi <= U.lo) continue;
             TileDesc td;
             std::memset(&td, 0, sizeof(td));
-            td.nrows = nrows;
-            td.nf = nf;
-            td.ks_lo = q_lo / kstep;
-            td.ks_hi = (q_hi + kstep - 1) / kstep;
-            td.atom_lo = td.ks_lo / 4;
-            td.n_atoms = (td.ks_hi + 3) / 4 - td.atom_lo;
-            td.p0 = p0;
-            td.bin_lo = gbins[gi].first;
-            td.bin_hi = gbins[gi].second;
-            for (int f = 0; f < kMaxFunc; ++f) td.r[f] = f < nf ? grp[f] : -1;
-            td.b_off = (long long)B.size();
-            const size_t atom_plane = (size_t)nrows * 128;
-            B.resize(B.size() + (size_t)td.n_atoms * atom_plane * planes, 0);
-            uint8_t *img = B.data() + td.b_off;
-            for (int a = 0; a < td.n_atoms; ++a) {
-                uint8_t *ai = img + (size_t)a * atom_plane * planes;
-                for (int f = 0; f < nf; ++f)
-                    for (int c = 0; c < kWin; ++c) {
-                        const int p = p0 + c, rowi = f * kWin + c;
+            td.n = n;
+            td.nf_flush = nf;
+            td.w = W;
+            td.p0 = w * W;
+            td.ks_lo = U.lo / kstep;
+            td.ks_hi = (U.hi + kstep - 1) / kstep;
+            td.f0 = x;
+            const int nks = td.ks_hi - td.ks_lo;
+            td.b_off16 = (int)(B.size() / 16);
+            const size_t blk = (size_t)n * 32;   // one plane of one k-step
+            B.resize(B.size() + (size_t)nks * blk * planes, 0);
+            uint8_t *img = B.data() + (size_t)td.b_off16 * 16;
+            for (int s = 0; s < nks; ++s) {
+                uint8_t *bk = img + (size_t)s * blk * planes;
+                for (int f = 0; f < nf; ++f) {
+                    const double *Tr = T.data() + (size_t)ford[x + f] * P_ * P_;
+                    for (int c = 0; c < W; ++c) {
+                        const int p = td.p0 + c, rowi = f * W + c;
                         if (p >= P_) continue;
-                        const double *Trow = T.data() + ((size_t)grp[f] * P_ + p) * P_;
-                        for (int x = 0; x < ae; ++x) {
-                            const int qq = (td.atom_lo + a) * ae + x;
-                            if (qq >= P_) break;
-                            const double val = Trow[qq] / (h[p / K1] * h[qq / K1]);
-                            const size_t off = swz_offset(nrows, rowi, x, eb);
+                        for (int xx = 0; xx < kstep; ++xx) {
+                            const int q = (td.ks_lo + s) * kstep + xx;
+                            if (q < p || q >= P_) continue;
+                            const double v = Tr[(size_t)p * P_ + q];
+                            if (v == 0.0) continue;
+                            const double val = v / (h[p / K1] * h[q / K1]);
+                            const size_t off = sw32_offset(rowi, xx, eb);
                             if (prec == GRACE_TF32) {
                                 const uint32_t bits = tf32_bits_rn((float)val);
-                                std::memcpy(ai + off, &bits, 4);
+                                std::memcpy(bk + off, &bits, 4);
                             } else {
                                 const uint16_t hi = bf16_bits_rn((float)val);
                                 const uint16_t lo = bf16_bits_rn((float)(val - (double)bf16_to_f(hi)));
-                                std::memcpy(ai + off, &hi, 2);
-                                std::memcpy(ai + atom_plane + off, &lo, 2);
+                                std::memcpy(bk + off, &hi, 2);
+                                std::memcpy(bk + blk + off, &lo, 2);
                             }
                         }
                     }
+                }
             }
-            macs += (long long)nrows * (td.ks_hi - td.ks_lo) * kstep;
+            macs += (long long)n * nks * kstep;
+            mmas += (long long)nks * mult;
+            gcost += tile_cost(n, nks);
+            out.slot_bytes = std::max(out.slot_bytes, (int)(std::min(kps, nks) * blk * planes));
+            out.max_rows = std::max(out.max_rows, n);
             tiles.push_back(td);
         }
-        if (tiles.size() > first_tile) tiles.back().flush = 1;
+        if (tiles.size() > first) {
+            tiles.back().nf_flush |= 1 << 16;
+            out.group_tile.push_back((int)first);
+            out.group_cost.push_back(gcost);
+        }
     }
     if (tiles.empty()) {
         set_error("tensor-core tiles: the coefficient tensor is empty");
         return GRACE_ERR_ARG;
     }
-    TcTiles &out = G.tc[prec];
-    free_tc_tiles(out);
+    if (B.size() / 16 > (size_t)INT32_MAX) {
+        set_error("tensor-core tiles: B images too large");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    out.group_tile.push_back((int)tiles.size());
+    free_tc_tiles(G.tc[prec]);
     e = cudaMalloc(&out.d_b, B.size());
     if (e == cudaSuccess) e = cudaMalloc(&out.d_desc, tiles.size() * sizeof(TileDesc));
+    if (e == cudaSuccess) e = cudaMalloc(&out.d_ford, ford.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(out.d_b, B.data(), B.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(out.d_desc, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_ford, ford.data(), ford.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_tc_tiles(out);
         return cuda_fail(e, "tensor-core tiles: upload");
     }
+    const int ae = atom_elems(prec);
     out.n_tiles = (int)tiles.size();
-    out.max_rows = 0;
-    for (const TileDesc &td : tiles) out.max_rows = std::max(out.max_rows, td.nrows);
     out.k_pad = (P_ + ae - 1) / ae * ae;
     out.b_bytes = B.size();
     out.mac_per_cell = macs;
+    out.mma_per_tile = mmas;
+    out.nnz_fold = nnz_fold;
+    out.pred_clk = best[R];
+    out.slot_bytes = (out.slot_bytes + 1023) / 1024 * 1024;
     out.built = 1;
+    G.tc[prec] = out;
     return GRACE_OK;
 }
 
@@ -876,45 +865,65 @@ static int sm_count(int dev)
     return n > 0 ? n : 1;
 }
 
-template <int NT>
-static cudaError_t launch_nt(TcParams P, cudaStream_t st)
+// Splits of the tile list (at functional-group boundaries) so that
+// n_cell_tiles x n_splits work items fill the SMs evenly.
+static void choose_splits(const TcTiles &t, int n_cell_tiles, int n_sm, TcParams &P)
 {
-    const size_t fixed = 1024 + (size_t)NT * P.a_tile_bytes + sizeof(Smem) + 64;
-    if (fixed + (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
-    P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed) / P.slot_bytes);
-    const size_t smem = fixed + (size_t)P.n_slots * P.slot_bytes;
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int n_groups = (int)t.group_cost.size();
+    double total = 0.0;
+    for (double c : t.group_cost) total += c;
+    int best_s = 1;
+    double best_t = 1e300;
+    for (int s = 1; s <= std::min(kMaxSplits, n_groups); ++s) {
+        const long long items = (long long)n_cell_tiles * s;
+        const long long rounds = (items + n_sm - 1) / n_sm;
+        const double time = (double)rounds * (total / s + kItemClk);
+        if (time < best_t * 0.97) {
+            best_t = time;
+            best_s = s;
+        }
+    }
+    // cut where the running cost crosses multiples of total / s
+    P.split[0] = 0;
+    int ns = 0;
+    double run = 0.0;
+    for (int gi = 0; gi < n_groups && ns + 1 < best_s; ++gi) {
+        run += t.group_cost[gi];
+        if (run >= total * (ns + 1) / best_s && gi + 1 < n_groups) P.split[++ns] = t.group_tile[gi + 1];
+    }
+    P.split[++ns] = t.n_tiles;
+    P.n_splits = ns;
+}
+
+template <int PREC>
+static cudaError_t launch_prec(TcParams P, cudaStream_t st)
+{
+    P.table_bytes = (int)((P.n_tiles * sizeof(TileDesc) + (size_t)P.R * sizeof(int) + 15) / 16 * 16);
+    const size_t fixed = 1024 + (size_t)P.table_bytes + sizeof(Smem) + 64;
+    const size_t a1 = (size_t)P.a_tile_bytes;
+    if (fixed + a1 + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
+    // two A tiles when that still leaves a 4-deep B ring, else one
+    P.a_bufs = fixed + 2 * a1 + 4 * (size_t)P.slot_bytes <= (size_t)kSmemLimit ? 2 : 1;
+    P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed - P.a_bufs * a1) / P.slot_bytes);
+    const size_t smem = fixed + P.a_bufs * a1 + (size_t)P.n_slots * P.slot_bytes;
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int items = (P.n_cell_tiles + NT - 1) / NT;
+    const int items = P.n_cell_tiles * P.n_splits;
     const int grid = std::min(items, sm_count(dev));
-    contract_tc_kernel<NT><<<grid, Cfg<NT>::threads, smem, st>>>(P);
+    contract_tc_kernel<PREC><<<grid, kThreads, smem, st>>>(P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, int n_cells,
-                               float *d_F32, int *d_err, cudaStream_t st, int mode, const UpdateArgs *u)
+                               float *d_F32, int *d_err, cudaStream_t st)
 {
-    if (!t.built) return cudaErrorInvalidValue;
-    if (mode != 0 && !u) return cudaErrorInvalidValue;
+    if (!t.built || n_cells <= 0) return n_cells == 0 ? cudaSuccess : cudaErrorInvalidValue;
     TcParams P;
     std::memset(&P, 0, sizeof(P));
-    P.mode = mode;
-    P.G = g;
-    if (u) {
-        P.gn = u->gn;
-        P.gs = u->gs;
-        P.gout = u->gout;
-        P.dt = u->dt;
-        P.ca = u->a;
-        P.cb = u->b;
-        P.apply_limiter = u->apply_limiter;
-        P.mass = u->mass;
-        P.flags = u->flags;
-        P.a_next = (uint8_t *)u->opA;
-    }
     P.tiles = (const TileDesc *)t.d_desc;
+    P.ford = t.d_ford;
     P.n_tiles = t.n_tiles;
     P.B = (const uint8_t *)t.d_b;
     P.A = (const uint8_t *)opA;
@@ -923,14 +932,12 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
     P.n_cell_tiles = (n_cells + kTileM - 1) / kTileM;
     P.R = g.R;
     P.F = d_F32;
-    P.prec = prec;
-    P.slot_bytes = t.max_rows * 128 * n_planes(prec);
-    P.n_slots = 0;
+    P.slot_bytes = t.slot_bytes;
     P.err = d_err;
-    // two cell tiles per CTA pass when both A tiles and a 4-deep B ring fit, else one
-    const size_t pair_need = 1024 + 2 * (size_t)P.a_tile_bytes + sizeof(Smem) + 64 + 4 * (size_t)P.slot_bytes;
-    if (pair_need <= (size_t)kSmemLimit && P.n_cell_tiles > 1) return launch_nt<2>(P, st);
-    return launch_nt<1>(P, st);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
+    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32>(P, st) : launch_prec<GRACE_BF16X3>(P, st);
 }
 
 }  // namespace grace

@@ -9,6 +9,7 @@
 // i = 0 row only ever sees F(x_{j-1/2}) - F(x_{j+1/2}), so the sum of h_j L_j^0
 // telescopes and the mass is conserved to round-off whatever precision the
 // functionals came from.
+#include "grace_convert.cuh"
 #include "grace_limiter.cuh"
 #include "grace_tc_layout.cuh"
 
@@ -76,14 +77,9 @@ __device__ __forceinline__ void write_row(const DevGroup &G, const double *row, 
     }
 }
 
-// FT = double: FP64 functionals, everything in FP64 (the plain path).
-// FT = float: functionals from the tensor path; the i = 0 row (flux difference,
-// stage combination, mass) stays FP64 so the telescoping sum conserves mass to
-// FP64 round-off, the i >= 1 rows are formed in FP32 (their error is far below
-// that of the reduced-precision contraction they come from).
-// One warp per cell; the new row is staged in shared memory and written out
-// coalesced.
-template <typename FT>
+// The plain path: FP64 functionals in the [cell][functional] layout, everything
+// in FP64.  One warp per cell; the new row is staged in shared memory and
+// written out coalesced.
 __global__ void __launch_bounds__(256) update_kernel(DevGroup G, UpdateArgs A, int n_cells)
 {
     extern __shared__ double rows[];
@@ -92,34 +88,23 @@ __global__ void __launch_bounds__(256) update_kernel(DevGroup G, UpdateArgs A, i
     if (cell >= n_cells) return;
     const int N = G.N, k = G.k, K1 = G.K1, R = G.R, P = G.P;
     double *row = rows + (size_t)(threadIdx.x >> 5) * P;
-    const FT *F = (const FT *)(sizeof(FT) == 8 ? (const void *)A.F : (const void *)A.F32) + cell * R;
+    const double *F = A.F + cell * R;
     const bool step = A.dt != nullptr;
     const double dt = step ? A.dt[cell] : 0.0;
     double msum = 0.0;
     unsigned fl = 0u;
     for (int j = lane; j < N; j += 32) {
-        const FT Fm = j == 0 ? FT(0) : F[j - 1];             // F(x_{j-1/2}), F(x_min) = 0
-        const FT Fp = j < G.n_if ? F[j] : FT(0);             // F(x_{j+1/2}), 0 at x_max (cons.)
+        const double Fm = j == 0 ? 0.0 : F[j - 1];             // F(x_{j-1/2}), F(x_min) = 0
+        const double Fp = j < G.n_if ? F[j] : 0.0;             // F(x_{j+1/2}), 0 at x_max (cons.)
         const size_t base = (size_t)cell * P + (size_t)j * K1;
         double v[kB];
-        const double L0 = ((double)Fm - (double)Fp) * G.inv_h[j];
+        const double ih = G.inv_h[j];
+        const double L0 = (Fm - Fp) * ih;
         v[0] = step ? A.a * A.gn[base] + A.b * (A.gs[base] + dt * L0) : L0;
-        if (sizeof(FT) == 8) {
-            const double ih = G.inv_h[j];
-            for (int i = 1; i <= k; ++i) {
-                const double V = (double)F[G.n_if + j * k + i - 1];
-                const double L = (2.0 * i + 1.0) * ih * (V - (double)Fp + ((i & 1) ? -(double)Fm : (double)Fm));
-                v[i] = step ? A.a * A.gn[base + i] + A.b * (A.gs[base + i] + dt * L) : L;
-            }
-        } else {
-            const float ih = G.inv_h32[j];
-            const float a = (float)A.a, b = (float)A.b, dtf = (float)dt;
-            const float fp = (float)Fp, fm = (float)Fm;
-            for (int i = 1; i <= k; ++i) {
-                const float V = (float)F[G.n_if + j * k + i - 1];
-                const float L = (2.f * i + 1.f) * ih * (V - fp + ((i & 1) ? -fm : fm));
-                v[i] = step ? (double)(a * (float)A.gn[base + i] + b * ((float)A.gs[base + i] + dtf * L)) : (double)L;
-            }
+        for (int i = 1; i <= k; ++i) {
+            const double V = F[G.n_if + j * k + i - 1];
+            const double L = (2.0 * i + 1.0) * ih * (V - Fp + ((i & 1) ? -Fm : Fm));
+            v[i] = step ? A.a * A.gn[base + i] + A.b * (A.gs[base + i] + dt * L) : L;
         }
         if (step) {
             if (v[0] < 0.0) fl |= GRACE_FLAG_NEGATIVE_MEAN;
@@ -171,6 +156,193 @@ __global__ void __launch_bounds__(256) limit_kernel(DevGroup G, double *g, int n
     }
 }
 
+// ---------------------------------------------------------------------------
+// K-c for the tensor path.  One warp per cell, one lane per bin (j = lane,
+// lane + 32, ...).  The stage inputs are read directly (each lane reads its
+// bin's K1 contiguous doubles, so a warp reads one contiguous span); the new row
+// and its A-operand row are assembled in a small per-warp shared-memory buffer and
+// written out coalesced.  The functionals come from the contraction in the
+// [tile][functional][row] layout.  Only the mean row (i = 0: flux difference,
+// stage combination, mass) uses FP64 arithmetic; the higher modes, the limiter
+// and all conversions run on the FP32 and integer pipes.
+//   MODE_RHS   : gout = L[g]                            (F32 required)
+//   MODE_STAGE : gout = a gn + b (gs + dt L[gs]), then the limiter when asked
+//   MODE_LIMIT : g = limit(g) (when asked) and the next A operand (no F32)
+// In every mode the A operand of the result (ghat = g h_bin, TF32 or BF16 hi/lo)
+// is written when A.opA is set.
+enum { MODE_RHS = 0, MODE_STAGE = 1, MODE_LIMIT = 2 };
+constexpr int kUpdWarps = 8;
+
+// LPC lanes per cell (16 or 32, whichever leaves fewer lanes idle for N bins);
+// lane l of a cell handles bins l, l + LPC, ...
+template <int MODE, int LPC>
+__global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G, UpdateArgs A, int n_cells)
+{
+    extern __shared__ double sm[];
+    const int N = G.N, k = G.k, K1 = G.K1, P = G.P;
+    const int slot = threadIdx.x / LPC, lane = threadIdx.x % LPC;
+    const long long cell = (long long)blockIdx.x * (kUpdWarps * 32 / LPC) + slot;
+    if (cell >= n_cells) return;   // whole groups of LPC lanes leave together
+    const int lda = A.opA_kpad;
+    double *row = sm + (size_t)slot * (P + lda / 2 + 1);          // new coefficients of the cell
+    float *arow = reinterpret_cast<float *>(row + P);             // its ghat row (A operand), kpad floats
+    const float *F = MODE == MODE_LIMIT ? nullptr
+                                        : A.F32 + ((size_t)(cell >> 7) * G.R) * kTileM + (cell & (kTileM - 1));
+    const double *gsr = (MODE == MODE_LIMIT ? A.gout : A.gs) + (size_t)cell * P;
+    const double *gnr = MODE == MODE_STAGE ? A.gn + (size_t)cell * P : gsr;
+    const double dt = MODE == MODE_STAGE ? A.dt[cell] : 0.0;
+    const float af = (float)A.a, bf = (float)A.b, dtf = MODE == MODE_STAGE ? d2f_fast(dt) : 0.f;
+    double msum = 0.0;
+    unsigned fl = 0u;
+    for (int j = lane; j < N; j += LPC) {
+        const double *vs = gsr + (size_t)j * K1;
+        const double *vn = gnr + (size_t)j * K1;
+        double v0;
+        double vd[kB];     // MODE_LIMIT: the FP64 higher modes
+        float vf[kB];
+        if (MODE == MODE_LIMIT) {
+            v0 = vs[0];
+#pragma unroll
+            for (int i = 1; i < kB; ++i) {
+                vd[i] = i <= k ? vs[i] : 0.0;
+                vf[i] = d2f_fast(vd[i]);
+            }
+        } else {
+            const float Fm = j == 0 ? 0.f : F[(size_t)(j - 1) * kTileM];   // F(x_{j-1/2}), F(x_min) = 0
+            const float Fp = j < G.n_if ? F[(size_t)j * kTileM] : 0.f;   // F(x_{j+1/2}), 0 at x_max (cons.)
+            const double L0 = (f2d_fast(Fm) - f2d_fast(Fp)) * G.inv_h[j];
+            if (MODE == MODE_STAGE) {
+                v0 = fma(A.a, vn[0], A.b * fma(dt, L0, vs[0]));
+            } else {
+                v0 = L0;
+            }
+            const float ih = G.inv_h32[j];
+#pragma unroll
+            for (int i = 1; i < kB; ++i) {
+                vf[i] = 0.f;
+                if (i <= k) {
+                    const float V = F[(size_t)(G.n_if + j * k + i - 1) * kTileM];
+                    const float L = (2.f * i + 1.f) * ih * (V - Fp + ((i & 1) ? -Fm : Fm));
+                    vf[i] = MODE == MODE_STAGE ? af * d2f_fast(vn[i]) + bf * (d2f_fast(vs[i]) + dtf * L) : L;
+                }
+            }
+        }
+        if (MODE == MODE_STAGE) {
+            if (negative_bits(v0)) fl |= GRACE_FLAG_NEGATIVE_MEAN;
+            bool nf = nonfinite_bits(v0);
+#pragma unroll
+            for (int i = 1; i < kB; ++i) nf = nf || (i <= k && nonfinite_bits(vf[i]));
+            if (nf) fl |= GRACE_FLAG_NONFINITE;
+        }
+        if (MODE != MODE_RHS && A.apply_limiter && k > 0) {
+            // FP32 limiter on the bin rescaled to a mean in [1, 2); the exact FP64
+            // limiter only for a mean <= 0, subnormal or not finite
+            const int e0 = scaled_exponent(v0);
+            float gam = -1.f;
+            if (e0 >= 0) {
+                float cf[kB];
+#pragma unroll
+                for (int i = 1; i < kB; ++i)
+                    cf[i] = i > k ? 0.f : (MODE == MODE_LIMIT ? d2f_scaled(vd[i], 1023 - e0) : scale_pow2(vf[i], 1023 - e0));
+                gam = limiter_gamma_scaled(v0, cf, k);
+            }
+            if (gam < 0.f) {
+                bool zero = ((unsigned long long)__double_as_longlong(v0) << 1) == 0ull;
+#pragma unroll
+                for (int i = 1; i < kB; ++i)
+                    zero = zero && (i > k || (MODE == MODE_LIMIT ? ((unsigned long long)__double_as_longlong(vd[i]) << 1) == 0ull
+                                                                 : vf[i] == 0.f));
+                if (!zero) {
+                    double v[kB];
+                    v[0] = v0;
+#pragma unroll
+                    for (int i = 1; i < kB; ++i) v[i] = i <= k ? (MODE == MODE_LIMIT ? vd[i] : f2d_fast(vf[i])) : 0.0;
+                    const unsigned f = limit_bin(v, k);
+                    fl |= f;
+                    if (f & GRACE_FLAG_LIMITED) {
+#pragma unroll
+                        for (int i = 1; i < kB; ++i) {
+                            vd[i] = v[i];
+                            vf[i] = (float)v[i];
+                        }
+                    }
+                }
+            } else if (gam < 1.f) {
+                fl |= GRACE_FLAG_LIMITED;
+#pragma unroll
+                for (int i = 1; i < kB; ++i) {
+                    if (MODE == MODE_LIMIT) {
+                        vd[i] *= (double)gam;
+                        vf[i] = d2f_fast(vd[i]);
+                    } else {
+                        vf[i] *= gam;
+                    }
+                }
+            }
+        }
+        double *rj = row + j * K1;
+        rj[0] = v0;
+#pragma unroll
+        for (int i = 1; i < kB; ++i)
+            if (i <= k) rj[i] = MODE == MODE_LIMIT ? vd[i] : f2d_fast(vf[i]);
+        if (A.opA) {
+            const float h = G.h32[j];
+            float *ar = arow + j * K1;
+            ar[0] = d2f_fast(v0) * h;
+#pragma unroll
+            for (int i = 1; i < kB; ++i)
+                if (i <= k) ar[i] = vf[i] * h;
+        }
+        if (A.mass) msum = fma(G.hbin[j], v0, msum);
+    }
+    const unsigned gmask = LPC == 32 ? 0xffffffffu : (0xFFFFu << (threadIdx.x & 16));
+    if (A.opA)
+        for (int e = P + lane; e < lda; e += LPC) arow[e] = 0.f;
+    __syncwarp(gmask);
+    // coalesced stores of the row (MODE_LIMIT rewrites it only when the limiter may have changed it)
+    if (MODE != MODE_LIMIT || A.apply_limiter) {
+        double *go = A.gout + (size_t)cell * P;
+        for (int e = lane; e < P; e += LPC) go[e] = row[e];
+    }
+    if (A.opA) {
+        const long long tile = cell / kTileM;
+        const int r = (int)(cell - tile * kTileM);
+        char *t = (char *)A.opA + (size_t)tile * opA_tile_bytes(A.opA_prec, lda);
+        if (A.opA_prec == GRACE_TF32) {
+            for (int qc = lane; qc < lda / 4; qc += LPC) {
+                const float *x = arow + 4 * qc;
+                *reinterpret_cast<uint4 *>(t + swz_offset(kTileM, r, 4 * qc, 4)) =
+                    make_uint4(f32_to_tf32_rna(x[0]), f32_to_tf32_rna(x[1]), f32_to_tf32_rna(x[2]), f32_to_tf32_rna(x[3]));
+            }
+        } else {
+            const size_t plane = (size_t)kTileM * lda * 2;
+            for (int qc = lane; qc < lda / 8; qc += LPC) {
+                const float *x = arow + 8 * qc;
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * e]), h1 = __float2bfloat16_rn(x[2 * e + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * e] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * e + 1] - __bfloat162float(h1));
+                    hi[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    lo[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                const size_t off = swz_offset(kTileM, r, 8 * qc, 2);
+                *reinterpret_cast<uint4 *>(t + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4 *>(t + plane + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            }
+        }
+    }
+    if (A.mass) {
+        for (int o = LPC / 2; o > 0; o >>= 1) msum += __shfl_xor_sync(gmask, msum, o);
+        if (lane == 0) A.mass[cell] = msum;
+    }
+    if (A.flags) {
+        for (int o = LPC / 2; o > 0; o >>= 1) fl |= __shfl_xor_sync(gmask, fl, o);
+        if (lane == 0 && fl) A.flags[cell] |= (unsigned char)fl;
+    }
+}
+
 __global__ void __launch_bounds__(256) mass_kernel(DevGroup G, const double *g, int n_cells, double *mass)
 {
     const long long cell = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -215,17 +387,59 @@ inline int warp_blocks(int n_cells) { return (int)(((long long)n_cells * 32 + 25
 
 cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
 {
+    if (!a.F) return cudaErrorInvalidValue;
     const size_t smem = (size_t)8 * g.P * sizeof(double);
-    if (a.F)
-        update_kernel<double><<<warp_blocks(n_cells), 256, smem, st>>>(g, a, n_cells);
-    else
-        update_kernel<float><<<warp_blocks(n_cells), 256, smem, st>>>(g, a, n_cells);
+    update_kernel<<<warp_blocks(n_cells), 256, smem, st>>>(g, a, n_cells);
     return cudaGetLastError();
+}
+
+// shared memory of update_tc_kernel: one row (P doubles) and one ghat row (kpad floats) per cell
+static size_t update_tc_smem(const DevGroup &g, const UpdateArgs &a, int lpc)
+{
+    return (size_t)(kUpdWarps * 32 / lpc) * (g.P + a.opA_kpad / 2 + 1) * sizeof(double);
+}
+
+template <int MODE, int LPC>
+static cudaError_t launch_update_lpc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
+{
+    const size_t smem = update_tc_smem(g, a, LPC);
+    cudaError_t e = cudaFuncSetAttribute(update_tc_kernel<MODE, LPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int per_block = kUpdWarps * 32 / LPC;
+    update_tc_kernel<MODE, LPC><<<(n_cells + per_block - 1) / per_block, 32 * kUpdWarps, smem, st>>>(g, a, n_cells);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_update_mode(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
+{
+    // lanes per cell: the choice that leaves fewer lanes idle over the N bins
+    const int idle16 = (g.N + 15) / 16 * 16 - g.N, idle32 = (g.N + 31) / 32 * 32 - g.N;
+    return idle16 <= idle32 ? launch_update_lpc<MODE, 16>(g, a, n_cells, st) : launch_update_lpc<MODE, 32>(g, a, n_cells, st);
+}
+
+cudaError_t launch_update_tc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
+{
+    if (n_cells <= 0) return cudaSuccess;
+    if (!a.F32 || !a.gout) return cudaErrorInvalidValue;
+    return a.dt ? launch_update_mode<MODE_STAGE>(g, a, n_cells, st) : launch_update_mode<MODE_RHS>(g, a, n_cells, st);
 }
 
 cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned char *flags, void *opA,
                          int opA_prec, int opA_kpad, cudaStream_t st)
 {
+    if (n_cells <= 0) return cudaSuccess;
+    if (opA) {
+        // tensor path: limiter pre-test off the FP64 pipe, and the A operand
+        UpdateArgs a;
+        a.gout = d_g;
+        a.apply_limiter = g.limiter;
+        a.flags = flags;
+        a.opA = opA;
+        a.opA_prec = opA_prec;
+        a.opA_kpad = opA_kpad;
+        return launch_update_mode<MODE_LIMIT>(g, a, n_cells, st);
+    }
     limit_kernel<<<warp_blocks(n_cells), 256, (size_t)8 * g.P * sizeof(double), st>>>(g, d_g, n_cells, flags, opA,
                                                                                        opA_prec, opA_kpad);
     return cudaGetLastError();
@@ -250,11 +464,13 @@ cudaError_t launch_project(const DevGroup &g, int ic_kind, const double *ic, int
 cudaError_t launch_pack_A(const DevGroup &g, const double *d_g, int n_cells, void *opA, int prec, int kpad,
                           cudaStream_t st)
 {
-    DevGroup g0 = g;
-    g0.limiter = 0;
-    limit_kernel<<<warp_blocks(n_cells), 256, (size_t)8 * g.P * sizeof(double), st>>>(
-        g0, const_cast<double *>(d_g), n_cells, nullptr, opA, prec, kpad);
-    return cudaGetLastError();
+    if (n_cells <= 0) return cudaSuccess;
+    UpdateArgs a;
+    a.gout = const_cast<double *>(d_g);   // read only: MODE_LIMIT without the limiter writes no rows
+    a.opA = opA;
+    a.opA_prec = prec;
+    a.opA_kpad = kpad;
+    return launch_update_mode<MODE_LIMIT>(g, a, n_cells, st);
 }
 
 }  // namespace grace

@@ -47,7 +47,7 @@ def exported_symbols():
             "grace_limit", "grace_profile_enable", "grace_profile_read", "grace_group_stats",
             "grace_batch_error", "grace_rhs_jvp", "grace_rhs_vjp", "grace_param_grad_setup",
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_destroy",
-            "grace_destroy"]
+            "grace_destroy", "grace_tile_info"]
 
 
 def load(path: str | None = None):
@@ -79,6 +79,7 @@ def load(path: str | None = None):
     L.grace_profile_read.argtypes = [_VP, S, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     L.grace_group_stats.argtypes = [_VP, S, S, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.grace_batch_error.argtypes = [_VP, ctypes.POINTER(S)]
+    L.grace_tile_info.argtypes = [_VP, S, S, ctypes.POINTER(ctypes.c_longlong)]
     L.grace_rhs_jvp.argtypes = [_VP, _VP, _VP, _VP, S]
     L.grace_rhs_vjp.argtypes = [_VP, _VP, _VP, _VP, S]
     L.grace_param_grad_setup.argtypes = [_VP, S, S, _VP, ctypes.c_double]
@@ -175,6 +176,13 @@ class Context:
         _check(load().grace_group_stats(self._h, group, precision, ctypes.byref(a), ctypes.byref(b)),
                "grace_group_stats")
         return a.value, b.value
+
+    def tile_info(self, group: int = 0, precision: int = TF32) -> dict:
+        """The tensor-core tile plan of a group (grace_tile_info)."""
+        a = (ctypes.c_longlong * 7)()
+        _check(load().grace_tile_info(self._h, group, precision, a), "grace_tile_info")
+        keys = ("n_tiles", "mma_per_tile", "mac_per_cell", "b_bytes", "pred_clk_per_tile", "max_n", "nnz_fold")
+        return dict(zip(keys, list(a)))
 
     def param_grad_setup(self, param_ids, group: int = 0, rel_step: float = 1e-5):
         """Enables dJ/dtheta in Batch.adjoint for kernel parameters given by id:

@@ -40,6 +40,25 @@ NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 NOMINAL_FP64_TFLOPS = 1.25
 
 
+def profiled_traffic(form_name):
+    """DRAM bytes per launch of the contraction from the committed ncu summary of
+    this form, or None when the kernel source changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", f"contract_tc_kernel_{form_name}_batched_additive_65536.md")
+    src = os.path.join(ROOT, "paper_2607_13740_b300", "csrc", "grace_tc.cu")
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if f"sha256 prefix `{sha}`" not in text:
+        return None
+    for line in text.splitlines():
+        if line.strip().startswith("traffic_bytes_per_launch:"):
+            return int(line.split(":")[1])
+    return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -300,7 +319,12 @@ def main():
         avg = r["contract_ms"] / max(1, r["contract_launches"])
         achieved = alg_flop / (avg / 1e3) / 1e12      # TFLOP/s
         if form == grace.FP64:
-            peak, bound, psrc = NOMINAL_FP64_TFLOPS, "alu", "nominal FP64 rate of the part (1.25 TFLOP/s)"
+            try:
+                fma64 = grace.probe_rates(local)["fp64_fma_per_s"]   # measured on this GPU
+                peak, psrc = 2.0 * fma64 / 1e12, "measured FP64 FMA rate (grace_probe_rates) x 2 flop"
+            except Exception:
+                peak, psrc = NOMINAL_FP64_TFLOPS, "nominal FP64 rate of the part (1.25 TFLOP/s)"
+            bound = "alu"
         elif form == grace.TF32:
             peak = peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16
             bound, psrc = "tensor", f"{peaks['source']} sustained bf16 x nominal tf32/bf16 ratio"
@@ -386,7 +410,10 @@ def main():
                    "parallelism": f"dp{world} (independent cells, no collective on the data path)"},
         "roofline": {"bound": hd["roofline"]["bound"], "achieved": hd["roofline"]["achieved"],
                      "peak": hd["roofline"]["peak"], "unit": "TFLOP/s", "frac": hd["roofline"]["frac"],
-                     "traffic": None, "kernel": "flux contraction",
+                     "traffic": profiled_traffic(names[head]) if head != grace.FP64 else None,
+                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch, committed ncu "
+                                       "summary (null when the kernel changed since)",
+                     "kernel": "flux contraction",
                      "algorithmic": (f"2 x {hd['tiles']['nnz_fold']} non-zeros of the folded tables"
                                      if hd.get("tiles") else f"2 x {nnz} non-zeros of T")
                                     + f" per cell and RHS x {n} cells"

@@ -179,15 +179,28 @@ template <int MODE, int LPC>
 __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G, UpdateArgs A, int n_cells)
 {
     extern __shared__ double sm[];
-    const int N = G.N, k = G.k, K1 = G.K1, P = G.P;
+    constexpr int CPB = kUpdWarps * 32 / LPC;                     // cells per block (a divisor of 128)
+    const int N = G.N, k = G.k, K1 = G.K1, P = G.P, R = G.R;
     const int slot = threadIdx.x / LPC, lane = threadIdx.x % LPC;
-    const long long cell = (long long)blockIdx.x * (kUpdWarps * 32 / LPC) + slot;
-    if (cell >= n_cells) return;   // whole groups of LPC lanes leave together
+    const long long cell0 = (long long)blockIdx.x * CPB;
+    const long long cell = cell0 + slot;
     const int lda = A.opA_kpad;
     double *row = sm + (size_t)slot * (P + lda / 2 + 1);          // new coefficients of the cell
     float *arow = reinterpret_cast<float *>(row + P);             // its ghat row (A operand), kpad floats
-    const float *F = MODE == MODE_LIMIT ? nullptr
-                                        : A.F32 + ((size_t)(cell >> 7) * G.R) * kTileM + (cell & (kTileM - 1));
+    // the block's functionals, transposed to [cell][functional]: read from the contraction's
+    // [tile][functional][row] layout as CPB-float pieces of each functional's row
+    float *Fs = reinterpret_cast<float *>(sm + (size_t)CPB * (P + lda / 2 + 1));
+    if (MODE != MODE_LIMIT) {
+        const float *Ft = A.F32 + ((size_t)(cell0 >> 7) * R) * kTileM + (cell0 & (kTileM - 1));
+        const int nc = (int)min((long long)CPB, (long long)n_cells - cell0);
+        for (int idx = threadIdx.x; idx < R * CPB; idx += 32 * kUpdWarps) {
+            const int r = idx / CPB, c = idx - r * CPB;
+            if (c < nc) Fs[c * (R + 1) + r] = Ft[(size_t)r * kTileM + c];
+        }
+        __syncthreads();
+    }
+    if (cell >= n_cells) return;   // whole groups of LPC lanes leave together
+    const float *F = Fs + slot * (R + 1);
     const double *gsr = (MODE == MODE_LIMIT ? A.gout : A.gs) + (size_t)cell * P;
     const double *gnr = MODE == MODE_STAGE ? A.gn + (size_t)cell * P : gsr;
     const double dt = MODE == MODE_STAGE ? A.dt[cell] : 0.0;
@@ -208,8 +221,8 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
                 vf[i] = d2f_fast(vd[i]);
             }
         } else {
-            const float Fm = j == 0 ? 0.f : F[(size_t)(j - 1) * kTileM];   // F(x_{j-1/2}), F(x_min) = 0
-            const float Fp = j < G.n_if ? F[(size_t)j * kTileM] : 0.f;   // F(x_{j+1/2}), 0 at x_max (cons.)
+            const float Fm = j == 0 ? 0.f : F[j - 1];          // F(x_{j-1/2}), F(x_min) = 0
+            const float Fp = j < G.n_if ? F[j] : 0.f;           // F(x_{j+1/2}), 0 at x_max (cons.)
             const double L0 = (f2d_fast(Fm) - f2d_fast(Fp)) * G.inv_h[j];
             if (MODE == MODE_STAGE) {
                 v0 = fma(A.a, vn[0], A.b * fma(dt, L0, vs[0]));
@@ -221,7 +234,7 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
             for (int i = 1; i < kB; ++i) {
                 vf[i] = 0.f;
                 if (i <= k) {
-                    const float V = F[(size_t)(G.n_if + j * k + i - 1) * kTileM];
+                    const float V = F[G.n_if + j * k + i - 1];
                     const float L = (2.f * i + 1.f) * ih * (V - Fp + ((i & 1) ? -Fm : Fm));
                     vf[i] = MODE == MODE_STAGE ? af * d2f_fast(vn[i]) + bf * (d2f_fast(vs[i]) + dtf * L) : L;
                 }
@@ -234,6 +247,7 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
             for (int i = 1; i < kB; ++i) nf = nf || (i <= k && nonfinite_bits(vf[i]));
             if (nf) fl |= GRACE_FLAG_NONFINITE;
         }
+        bool changed = false;   // the limiter scaled this bin's higher modes
         if (MODE != MODE_RHS && A.apply_limiter && k > 0) {
             // FP32 limiter on the bin rescaled to a mean in [1, 2); the exact FP64
             // limiter only for a mean <= 0, subnormal or not finite
@@ -260,6 +274,7 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
                     const unsigned f = limit_bin(v, k);
                     fl |= f;
                     if (f & GRACE_FLAG_LIMITED) {
+                        changed = true;
 #pragma unroll
                         for (int i = 1; i < kB; ++i) {
                             vd[i] = v[i];
@@ -269,6 +284,7 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
                 }
             } else if (gam < 1.f) {
                 fl |= GRACE_FLAG_LIMITED;
+                changed = true;
 #pragma unroll
                 for (int i = 1; i < kB; ++i) {
                     if (MODE == MODE_LIMIT) {
@@ -279,6 +295,11 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
                     }
                 }
             }
+            // MODE_LIMIT rewrites only the bins it changed (the rest of the state is untouched)
+            if (MODE == MODE_LIMIT && changed)
+#pragma unroll
+                for (int i = 1; i < kB; ++i)
+                    if (i <= k) A.gout[(size_t)cell * P + (size_t)j * K1 + i] = vd[i];
         }
         double *rj = row + j * K1;
         rj[0] = v0;
@@ -299,8 +320,8 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
     if (A.opA)
         for (int e = P + lane; e < lda; e += LPC) arow[e] = 0.f;
     __syncwarp(gmask);
-    // coalesced stores of the row (MODE_LIMIT rewrites it only when the limiter may have changed it)
-    if (MODE != MODE_LIMIT || A.apply_limiter) {
+    // coalesced stores of the row (MODE_LIMIT has written its changed bins above)
+    if (MODE != MODE_LIMIT) {
         double *go = A.gout + (size_t)cell * P;
         for (int e = lane; e < P; e += LPC) go[e] = row[e];
     }
@@ -393,10 +414,12 @@ cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, c
     return cudaGetLastError();
 }
 
-// shared memory of update_tc_kernel: one row (P doubles) and one ghat row (kpad floats) per cell
+// shared memory of update_tc_kernel: one row (P doubles) and one ghat row (kpad floats) per cell,
+// then the block's functionals [cells][R + 1] floats
 static size_t update_tc_smem(const DevGroup &g, const UpdateArgs &a, int lpc)
 {
-    return (size_t)(kUpdWarps * 32 / lpc) * (g.P + a.opA_kpad / 2 + 1) * sizeof(double);
+    const size_t cpb = (size_t)kUpdWarps * 32 / lpc;
+    return cpb * (g.P + a.opA_kpad / 2 + 1) * sizeof(double) + cpb * (g.R + 1) * sizeof(float);
 }
 
 template <int MODE, int LPC>

@@ -101,6 +101,10 @@ typedef struct {
     double coag_p[8];
     double frag_p[8];
     double break_p[8];
+    int cell_alpha;   /* 1: the ballistic-turbulent kernels take alpha_turb (p3) per cell, set
+                         by grace_batch_cell_params; coag_kind must be BALLISTIC, frag_kind NONE
+                         or BALLISTIC with the same p0..p2, p4..p6 as coagulation; 0: per group */
+    int reserved_;    /* zero */
 } grace_group_desc;
 
 GRACE_API int grace_version(void);
@@ -235,6 +239,14 @@ GRACE_API grace_status grace_group_stats(const grace_ctx *ctx, int group, int pr
    [6] non-zeros of the symmetric-folded tables (the multiply-adds a cell needs).
    GRACE_ERR_ORDER when that precision was not precomputed. */
 GRACE_API grace_status grace_tile_info(const grace_ctx *ctx, int group, int precision, long long *info);
+
+/* Per-cell turbulence strength for the cells of groups with cell_alpha = 1
+   (non-separable kernels: the flux functionals are no longer fixed quadratic
+   forms of the coefficients, so they are evaluated from node-space tables and a
+   per-cell kernel factor each RHS; FP64 only).  alpha: device, n_cells doubles in
+   the batch's cell order (entries of other groups are ignored), copied.
+   GRACE_ERR_ORDER from grace_rhs / grace_step on such a batch until this was called. */
+GRACE_API grace_status grace_batch_cell_params(grace_batch *batch, const double *alpha);
 
 /* Reads and clears the batch's device error word: non-zero bits mean a bounded
    device-side wait inside a tensor-core launch gave up (the launch then wrote

@@ -330,6 +330,10 @@ grace_status single_part(grace_batch *b, const char *who)
         set_error(std::string(who) + ": batches mixing groups are not supported");
         return GRACE_ERR_UNSUPPORTED;
     }
+    if (b->ctx->groups[b->parts[0].group].dg.cell_alpha) {
+        set_error(std::string(who) + ": groups with a per-cell kernel parameter have no fixed T (not supported)");
+        return GRACE_ERR_UNSUPPORTED;
+    }
     return GRACE_OK;
 }
 
@@ -431,6 +435,10 @@ grace_status grace_param_grad_setup(grace_ctx *ctx, int group, int n_params, con
     if (!(rel_step > 0.0)) rel_step = 1e-5;
     Guard guard(ctx->device);
     Group &G = ctx->groups[group];
+    if (G.dg.cell_alpha) {
+        set_error("grace_param_grad_setup: groups with a per-cell kernel parameter have no fixed T (not supported)");
+        return GRACE_ERR_UNSUPPORTED;
+    }
     free_param_derivs(G);
     const DevGroup &dg = G.dg;
     const size_t nT = (size_t)dg.R * dg.P * dg.P;

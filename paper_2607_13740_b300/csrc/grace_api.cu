@@ -85,6 +85,7 @@ DevGroup make_devgroup(const grace_group_desc &d, const double *d_edges)
     g.mfrag_mode = d.mfrag_mode;
     g.limiter = d.limiter;
     g.has_delta = d.frag_kind != GRACE_FRAG_NONE && d.break_kind == GRACE_BREAK_POWERLAW_REMNANT;
+    g.cell_alpha = d.cell_alpha;
     g.x_min = d.x_min;
     g.x_max = d.x_max;
     for (int i = 0; i < 8; ++i) {
@@ -124,6 +125,17 @@ static grace_status validate(const grace_group_desc &d, int idx)
     if (d.frag_kind < GRACE_FRAG_NONE || d.frag_kind > GRACE_FRAG_BALLISTIC) return bad("frag_kind");
     if (d.break_kind < GRACE_BREAK_UNIFORM_BINARY || d.break_kind > GRACE_BREAK_COAG_DELTA) return bad("break_kind");
     if (d.coag_kind == GRACE_COAG_NONE && d.frag_kind == GRACE_FRAG_NONE) return bad("no collision kernel");
+    if (d.cell_alpha != 0 && d.cell_alpha != 1) return bad("cell_alpha must be 0 or 1");
+    if (d.cell_alpha) {
+        if (d.coag_kind != GRACE_COAG_BALLISTIC) return bad("cell_alpha needs coag_kind BALLISTIC");
+        if (d.frag_kind != GRACE_FRAG_NONE && d.frag_kind != GRACE_FRAG_BALLISTIC)
+            return bad("cell_alpha needs frag_kind NONE or BALLISTIC");
+        if (d.frag_kind == GRACE_FRAG_BALLISTIC)
+            for (int i = 0; i < 7; ++i)
+                if (i != 3 && d.frag_p[i] != d.coag_p[i])
+                    return bad("cell_alpha: fragmentation must use the coagulation's ballistic parameters");
+        if (!(d.coag_p[5] > 0.0) || !(d.coag_p[4] > 0.0)) return bad("cell_alpha: v_frag and the ramp width must be > 0");
+    }
     if (d.coag_kind == GRACE_COAG_MAXWELL && !(d.coag_p[0] > 0.0)) return bad("Maxwellian dv_rms must be > 0");
     if (d.frag_kind == GRACE_FRAG_MAXWELL && !(d.frag_p[0] > 0.0)) return bad("Maxwellian dv_rms must be > 0");
     if (d.frag_kind != GRACE_FRAG_NONE && d.break_kind == GRACE_BREAK_POWERLAW_REMNANT && d.break_p[0] == -2.0)
@@ -134,6 +146,7 @@ static grace_status validate(const grace_group_desc &d, int idx)
 
 static void free_group(Group &G)
 {
+    free_nc_tables(G.nc);
     cudaFree(G.d_edges);
     cudaFree(G.d_T);
     cudaFree(G.d_qlo);
@@ -267,6 +280,15 @@ grace_status grace_precompute(grace_ctx *ctx, unsigned mask)
         cudaStream_t st = ctx->stream;
         for (Group &G : ctx->groups) {
             const DevGroup &g = G.dg;
+            if (g.cell_alpha) {
+                // per-cell kernel: no fixed T exists; node-space tables (FP64 path only)
+                if (!G.nc.built) {
+                    grace_status s = build_nc_tables(G, st);
+                    if (s != GRACE_OK) return s;
+                    G.nnz = 0;
+                }
+                continue;
+            }
             if (!G.d_T) {
                 const size_t nT = (size_t)g.R * g.P * g.P;
                 cudaError_t e = cudaMalloc(&G.d_T, nT * sizeof(double));

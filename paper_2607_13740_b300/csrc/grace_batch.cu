@@ -69,6 +69,9 @@ void free_part(Part &p)
     cudaFree(p.d_g1);
     cudaFree(p.d_g2);
     cudaFree(p.d_opA);
+    cudaFree(p.d_alpha);
+    cudaFree(p.d_G);
+    cudaFree(p.d_H);
     if (p.stream) cudaStreamDestroy(p.stream);
     if (p.done) cudaEventDestroy(p.done);
     p = Part();
@@ -81,6 +84,17 @@ grace_status check_prec(grace_batch *b, int prec)
         return GRACE_ERR_ARG;
     }
     for (const Part &p : b->parts) {
+        if (b->ctx->groups[p.group].dg.cell_alpha) {
+            if (prec != GRACE_FP64) {
+                set_error("groups with a per-cell kernel parameter run in GRACE_FP64 only");
+                return GRACE_ERR_UNSUPPORTED;
+            }
+            if (!b->alpha_set) {
+                set_error("per-cell kernel parameters not set: call grace_batch_cell_params first");
+                return GRACE_ERR_ORDER;
+            }
+            continue;
+        }
         if (prec != GRACE_FP64 && !b->ctx->groups[p.group].tc[prec].built) {
             set_error("precision not precomputed: pass its bit to grace_precompute before binding the batch");
             return GRACE_ERR_ORDER;
@@ -115,7 +129,8 @@ cudaError_t part_rhs(grace_batch *b, Part &p, const double *g, double *L, int pr
     }
     {
         LaunchTimer timer(b->ctx, 0, st);
-        e = launch_contract_fp64(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, p.n, p.d_F, st);
+        e = G.dg.cell_alpha ? launch_nc_functionals(G.dg, G.nc, g, p.d_alpha, p.n, p.d_G, p.d_H, p.d_F, st)
+                            : launch_contract_fp64(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, p.n, p.d_F, st);
     }
     if (e != cudaSuccess) return e;
     UpdateArgs u;
@@ -182,7 +197,9 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
             } else {
                 {
                     LaunchTimer timer(b->ctx, 0, st);
-                    e = launch_contract_fp64(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gin[stage], n, p.d_F, st);
+                    e = dg.cell_alpha
+                            ? launch_nc_functionals(dg, G.nc, gin[stage], p.d_alpha, n, p.d_G, p.d_H, p.d_F, st)
+                            : launch_contract_fp64(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gin[stage], n, p.d_F, st);
                 }
                 if (e != cudaSuccess) return e;
                 u.F = p.d_F;
@@ -285,6 +302,12 @@ grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group
             const DevGroup &g = ctx->groups[gi].dg;
             const size_t n = (size_t)p.n;
             e = cudaMalloc(&p.d_F, n * g.R * sizeof(double));
+            if (e == cudaSuccess && g.cell_alpha) {
+                const size_t nq = (size_t)g.N * g.Q;
+                e = cudaMalloc(&p.d_alpha, n * sizeof(double));
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_G, n * nq * sizeof(double));
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_H, 2 * n * nq * sizeof(double));
+            }
             if (e == cudaSuccess) e = cudaMalloc(&p.d_g1, n * g.P * sizeof(double));
             if (e == cudaSuccess) e = cudaMalloc(&p.d_g2, n * g.P * sizeof(double));
             if (e == cudaSuccess && !direct) {
@@ -515,6 +538,24 @@ grace_status grace_project(grace_batch *b, int ic_kind, const double *ic_params,
         return r;
     });
     return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_project");
+}
+
+grace_status grace_batch_cell_params(grace_batch *b, const double *alpha)
+{
+    if (!b || !alpha) {
+        set_error("grace_batch_cell_params: null argument");
+        return GRACE_ERR_ARG;
+    }
+    Guard guard(b->ctx->device);
+    cudaError_t e = for_parts(b, [&](Part &p, cudaStream_t st) {
+        if (!b->ctx->groups[p.group].dg.cell_alpha) return cudaSuccess;
+        if (p.direct) return cudaMemcpyAsync(p.d_alpha, alpha, (size_t)p.n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        gather_kernel<double><<<nb(p.n), 256, 0, st>>>(p.n, 1, p.d_idx, alpha, p.d_alpha);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "grace_batch_cell_params");
+    b->alpha_set = 1;
+    return GRACE_OK;
 }
 
 grace_status grace_batch_error(grace_batch *b, int *code)

@@ -17,6 +17,7 @@ constexpr int kKMax = 3;    // largest Legendre degree with an analytic limiter
 struct DevGroup {
     int N, k, K1, Q, P, R, n_if;
     int flux_mode, coag_kind, frag_kind, break_kind, cutoff_mode, mfrag_mode, limiter, has_delta;
+    int cell_alpha;                  // ballistic alpha_turb per cell (node-space path)
     double x_min, x_max;
     double coag_p[8], frag_p[8], break_p[8];
     double beta_coag, beta_frag;     // Maxwellian probabilities (constant dv_rms)
@@ -47,6 +48,19 @@ struct TcTiles {
     std::vector<double> group_cost;   // cost-model cycles of every group
 };
 
+// Node-space tables of a group with a per-cell kernel parameter (grace_ncell.cu)
+struct NcTables {
+    int built = 0;
+    int NQ = 0;                   // fixed Gauss nodes (N x Q), in increasing size
+    double *d_Cc = nullptr;       // [R][NQ][NQ] upper-triangular weights of the coagulation factor
+    double *d_Cf = nullptr;       // [R][NQ][NQ] upper-triangular weights of the fragmentation factor
+    int *d_qlo = nullptr, *d_qhi = nullptr;   // [R*NQ] non-zero column range of each row
+    double *d_D0 = nullptr;       // [NQ] D0 of each fixed node
+    void *d_entries = nullptr;    // partial-pair entries, grouped by functional
+    long long *d_seg = nullptr;   // [R+1] entry ranges per functional
+    long long n_entries = 0;
+};
+
 // d T / d theta for one kernel parameter (central difference of the FP64 precompute)
 struct ParamDeriv {
     int id = -1;                  // 0..7 coag_p, 8..15 frag_p, 16..23 break_p
@@ -66,6 +80,7 @@ struct Group {
     int *d_prange = nullptr;      // [R][2] p range with non-empty rows
     long long nnz = 0;            // structural non-zeros of T (all rows)
     TcTiles tc[3];                // indexed by grace_precision
+    NcTables nc;                  // cell_alpha groups: node-space tables instead of T
     std::vector<ParamDeriv> dparams;
 };
 
@@ -107,6 +122,8 @@ struct Part {
     float *d_F32 = nullptr;        // [tiles][R][128] functionals from the tensor path
     double *d_g1 = nullptr, *d_g2 = nullptr;   // stage states
     void *d_opA = nullptr;         // tensor-core A operand of the current stage
+    double *d_alpha = nullptr;     // [n] per-cell alpha_turb (cell_alpha groups)
+    double *d_G = nullptr, *d_H = nullptr;   // [n][NQ], [2][n][NQ] nodal values (cell_alpha groups)
     size_t opA_bytes = 0;
     cudaStream_t stream = nullptr; // own stream for concurrent parts (null: the context's)
     cudaEvent_t done = nullptr;
@@ -129,6 +146,7 @@ struct grace_batch {
     cudaGraphExec_t graph = nullptr;
     const void *graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
     int graph_steps = -1, graph_prec = -1;
+    int alpha_set = 0;             // grace_batch_cell_params was called
 };
 
 namespace grace {
@@ -237,6 +255,12 @@ cudaError_t launch_axpby_dt(int P, int n, double a, const double *x, double b, c
 cudaError_t launch_param_dot(int R, int n, const double *mu, const double *Fp, const double *dt, double w,
                              int n_params, int ip, double *dtheta, cudaStream_t st);
 void free_param_derivs(Group &G);
+
+// node-space path for per-cell kernels (grace_ncell.cu)
+grace_status build_nc_tables(Group &G, cudaStream_t st);
+void free_nc_tables(NcTables &t);
+cudaError_t launch_nc_functionals(const DevGroup &g, const NcTables &t, const double *d_g, const double *d_alpha,
+                                  int n_cells, double *d_G, double *d_H, double *d_F, cudaStream_t st);
 
 // tensor-core path
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);

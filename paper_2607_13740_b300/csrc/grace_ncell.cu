@@ -1,0 +1,542 @@
+// a4': flux functionals of groups whose kernel has a per-cell parameter
+// (non-separable: the functionals are no longer fixed quadratic forms of the
+// coefficients, so no T can be precomputed).
+//
+// The ballistic-turbulent kernels depend on the cell's alpha_turb only through
+// s = sqrt(alpha) and the fragmentation ramp pf(s D0), with D0 a function of the
+// larger colliding particle alone (grace_physics.cuh):
+//     K_coag = s S0(u, v) (1 - pf(s D0(max(u, v)))),   K_frag = s S0(u, v) pf(s D0(max(u, v))).
+// Every flux functional is the nested Gauss sum of Sec. 3.3 / App. B over node
+// pairs (u, v) of w(u, v) K(u, v) g(u) g(v) with cell-independent weights w.  The
+// pairs split into
+//   * fixed pairs: u and v are Gauss nodes of whole bins (shared by many
+//     functionals).  With G_a = g at fixed node a (nodes in increasing size), the
+//     pair's kernel factor depends on the larger node max(a, b) only, so the fixed
+//     part of functional r is
+//         s [ G^T Cc_r Hc + G^T Cf_r Hf ],   Hc = (1 - pf(s D0)) (.) G,  Hf = pf(s D0) (.) G,
+//     with C{c,f}_r = fold(B{c,f}_r), B{c,f}_r[a][b] the summed weights x S0 of the
+//     coagulation / fragmentation terms, fold(M)[i][j] = M[i][j] + M[j][i] (i < j),
+//     M[i][i] on the diagonal (upper triangle, the larger node on the H side).
+//     The two products are kept apart (not Hf = G - Hc) so that a vanishing
+//     fragmentation probability contributes an exact zero, whatever the size of
+//     the fragmentation weights;
+//   * partial pairs: u or v is a node remapped onto part of a bin (the end bins of
+//     the inner range, the outer bin that contains a volume point): a list of
+//     entries (functional, weight x S0, D0, bins and basis values of u and v),
+//     evaluated per cell.
+// Both are built once per setup on the device in FP64 by the same quadrature
+// walk as the T build (grace_precompute.cu); each RHS then costs a bilinear
+// contraction in node space plus one cheap kernel factor per partial entry.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "grace_physics.cuh"
+
+namespace grace {
+
+namespace {
+
+constexpr int kB = kKMax + 1;
+
+struct NcEntry {
+    int r;              // functional
+    int kind;           // 0 coagulation factor (1 - pf), 1 fragmentation factor pf
+    double w;           // quadrature weight x S0(u, v) (all cell-independent factors)
+    double D0;          // D0 of the larger particle
+    int bu, bv;         // bins of u and v
+    double pu[kB], pv[kB];   // phi_i at u and v
+};
+static_assert(sizeof(NcEntry) == 96, "NcEntry layout");
+
+struct NcBuild {
+    double *Bc, *Bf;            // [R][NQ][NQ] fixed-pair weights (dense)
+    const long long *offset;    // [R][N][N] first entry of each (r, l, m) block (pass 1)
+    long long *count;           // [R][N][N] entries of each block (pass 0)
+    NcEntry *entries;           // pass 1
+    int pass;
+};
+
+struct Acc {
+    // fixed-pair accumulators of one (r, l, m) block and the partial-entry cursor
+    double c[kQMax * kQMax], f[kQMax * kQMax];
+    long long n;
+};
+
+__device__ __forceinline__ void emit(const DevGroup &G, const NcBuild &B, Acc &A, long long base, int r, int kind,
+                                     double w, double u, double v, int l, int m)
+{
+    if (B.pass == 1) {
+        double S0, D0;
+        dev_ballistic_split(G.coag_p, u, v, &S0, &D0);
+        NcEntry e;
+        e.r = r;
+        e.kind = kind;
+        e.w = w * S0;
+        e.D0 = D0;
+        e.bu = l;
+        e.bv = m;
+        const double *ed = G.edges;
+        dev_legendre(G.k, 2.0 / (ed[l + 1] - ed[l]) * (u - 0.5 * (ed[l] + ed[l + 1])), e.pu, nullptr);
+        dev_legendre(G.k, 2.0 / (ed[m + 1] - ed[m]) * (v - 0.5 * (ed[m] + ed[m + 1])), e.pv, nullptr);
+        for (int i = G.k + 1; i < kB; ++i) e.pu[i] = e.pv[i] = 0.0;
+        B.entries[base + A.n] = e;
+    }
+    ++A.n;
+}
+
+// contribution c x (flux at x) of outer bin l and inner bin m, split into fixed
+// pairs and partial entries (the walk of point_block in grace_precompute.cu)
+__device__ void nc_point(const DevGroup &G, const NcBuild &B, Acc &A, long long base, int r, double x, int l, int m,
+                         double c, bool frag)
+{
+    const double *e = G.edges;
+    const int Q = G.Q;
+    const bool do_frag = frag && G.frag_kind != GRACE_FRAG_NONE;
+    // positive flux: u in [x_min, x] (outer bin l), v in [x - u + x_min, v_max(u)] within bin m
+    if (e[l] < x) {
+        const double a = e[l], b = fmin(e[l + 1], x);
+        const bool ufix = b == e[l + 1];
+        if (b > a)
+            for (int al = 0; al < Q; ++al) {
+                const double u = 0.5 * (a + b) + 0.5 * (b - a) * G.gs[al];
+                const double Wu = 0.5 * (b - a) * G.gw[al];
+                const double lo = x - u + G.x_min, hi = dev_vmax(G, u);
+                if (!(hi > lo)) continue;
+                const double va = fmax(lo, e[m]), vb = fmin(hi, e[m + 1]);
+                if (!(vb > va)) continue;
+                const bool vfix = va == e[m] && vb == e[m + 1];
+                for (int be = 0; be < Q; ++be) {
+                    const double v = 0.5 * (va + vb) + 0.5 * (vb - va) * G.gs[be];
+                    const double Wv = 0.5 * (vb - va) * G.gw[be];
+                    const double wc = c * Wu * Wv / v;
+                    const double wf = do_frag ? c * Wu * Wv * dev_mass_above(G, x, u, v) / (v * (u + v)) : 0.0;
+                    if (ufix && vfix) {
+                        if (B.pass == 1) {
+                            double S0, D0;
+                            dev_ballistic_split(G.coag_p, u, v, &S0, &D0);
+                            A.c[al * Q + be] += wc * S0;
+                            A.f[al * Q + be] += wf * S0;
+                        }
+                    } else {
+                        emit(G, B, A, base, r, 0, wc, u, v, l, m);
+                        if (do_frag && wf != 0.0) emit(G, B, A, base, r, 1, wf, u, v, l, m);
+                    }
+                }
+            }
+    }
+    // negative fragmentation flux: u in [x, x_max], v in [x_min, v_max(u)]
+    if (do_frag && e[l + 1] > x) {
+        const double a = fmax(e[l], x), b = e[l + 1];
+        const bool ufix = a == e[l];
+        if (b > a)
+            for (int al = 0; al < Q; ++al) {
+                const double u = 0.5 * (a + b) + 0.5 * (b - a) * G.gs[al];
+                const double Wu = 0.5 * (b - a) * G.gw[al];
+                const double hi = dev_vmax(G, u);
+                const double va = fmax(G.x_min, e[m]), vb = fmin(hi, e[m + 1]);
+                if (!(vb > va)) continue;
+                const bool vfix = va == e[m] && vb == e[m + 1];
+                for (int be = 0; be < Q; ++be) {
+                    const double v = 0.5 * (va + vb) + 0.5 * (vb - va) * G.gs[be];
+                    const double Wv = 0.5 * (vb - va) * G.gw[be];
+                    const double wf = -c * Wu * Wv * dev_mass_below(G, x, u, v) / (v * (u + v));
+                    if (wf == 0.0) continue;
+                    if (ufix && vfix) {
+                        if (B.pass == 1) {
+                            double S0, D0;
+                            dev_ballistic_split(G.coag_p, u, v, &S0, &D0);
+                            A.f[al * Q + be] += wf * S0;
+                        }
+                    } else {
+                        emit(G, B, A, base, r, 1, wf, u, v, l, m);
+                    }
+                }
+            }
+    }
+}
+
+// the App. B volume term of fragmentation with a Dirac remnant (appB_block)
+__device__ double nc_sub_interval(const DevGroup &G, int j, int i, double a, double b, double c0, double c1,
+                                  double alpha, bool pw)
+{
+    if (!(b > a)) return 0.0;
+    const double *e = G.edges;
+    const double h = e[j + 1] - e[j], xc = 0.5 * (e[j] + e[j + 1]);
+    double P[kB], dP[kB], s = 0.0;
+    for (int t = 0; t < G.Q; ++t) {
+        const double x = 0.5 * (a + b) + 0.5 * (b - a) * G.gs[t];
+        const double W = 0.5 * (b - a) * G.gw[t];
+        const double f = pw ? c0 + c1 * pow(x, 2.0 + alpha) : c0;
+        dev_legendre(G.k, 2.0 / h * (x - xc), P, dP);
+        s += W * f * (2.0 / h) * dP[i];
+    }
+    return s;
+}
+
+__device__ double nc_appB_J(const DevGroup &G, int j, int i, double u, double v)
+{
+    const double ja = G.edges[j], jb = G.edges[j + 1], xmin = G.x_min;
+    const FragOutcome o = dev_outcome(G, u, v);
+    const double top = u + v - xmin;
+    double J = 0.0;
+    if (o.mcut > xmin) {
+        const double a2 = 2.0 + o.alpha;
+        const double mc2 = pow(o.mcut, a2), xm2 = pow(xmin, a2);
+        const double cA = o.mfrag / (mc2 - xm2);
+        J += nc_sub_interval(G, j, i, fmax(ja, u), fmin(jb, fmin(top, o.mcut)), cA * mc2, -cA, o.alpha, true);
+        J -= nc_sub_interval(G, j, i, fmax(ja, xmin), fmin(jb, u), -cA * xm2, cA, o.alpha, true);
+        J += nc_sub_interval(G, j, i, fmax(ja, o.mcut), fmin(jb, u), -cA * mc2, cA, o.alpha, true);
+    } else {
+        J -= nc_sub_interval(G, j, i, fmax(ja, xmin), fmin(jb, u), o.mfrag, 0.0, 0.0, false);
+    }
+    if (o.mleft > 0.0) {
+        J += nc_sub_interval(G, j, i, fmax(ja, u), fmin(jb, fmin(top, o.mleft)), o.mleft, 0.0, 0.0, false);
+        if (o.mleft >= xmin) J -= nc_sub_interval(G, j, i, fmax(ja, o.mleft), fmin(jb, u), o.mleft, 0.0, 0.0, false);
+    }
+    return J;
+}
+
+__device__ void nc_appB(const DevGroup &G, const NcBuild &B, Acc &A, long long base, int r, int j, int i, int l,
+                        int m)
+{
+    const double *e = G.edges;
+    const int Q = G.Q;
+    const double hl = e[l + 1] - e[l], xl = 0.5 * (e[l] + e[l + 1]);
+    for (int al = 0; al < Q; ++al) {
+        const double u = xl + 0.5 * hl * G.gs[al];
+        const double Wu = 0.5 * hl * G.gw[al];
+        const double hi = dev_vmax(G, u);
+        const double va = fmax(G.x_min, e[m]), vb = fmin(hi, e[m + 1]);
+        if (!(vb > va)) continue;
+        const bool vfix = va == e[m] && vb == e[m + 1];
+        for (int be = 0; be < Q; ++be) {
+            const double v = 0.5 * (va + vb) + 0.5 * (vb - va) * G.gs[be];
+            const double Wv = 0.5 * (vb - va) * G.gw[be];
+            const double w = Wu * Wv / (v * (u + v)) * nc_appB_J(G, j, i, u, v);
+            if (w == 0.0) continue;
+            if (vfix) {
+                if (B.pass == 1) {
+                    double S0, D0;
+                    dev_ballistic_split(G.coag_p, u, v, &S0, &D0);
+                    A.f[al * Q + be] += w * S0;
+                }
+            } else {
+                emit(G, B, A, base, r, 1, w, u, v, l, m);
+            }
+        }
+    }
+}
+
+// one thread per (r, l, m) block, as in the T build: pass 0 counts partial
+// entries, pass 1 writes them and the block's fixed-pair weights
+__global__ void __launch_bounds__(128) nc_build_kernel(DevGroup G, NcBuild B)
+{
+    const int r = blockIdx.y;
+    const int lm = blockIdx.x * blockDim.x + threadIdx.x;
+    if (lm >= G.N * G.N || r >= G.R) return;
+    const int l = lm / G.N, m = lm % G.N, Q = G.Q, NQ = G.N * G.Q;
+    const size_t blk = ((size_t)r * G.N + l) * G.N + m;
+    const long long base = B.pass == 1 ? B.offset[blk] : 0;
+    Acc A;
+    for (int t = 0; t < Q * Q; ++t) A.c[t] = A.f[t] = 0.0;
+    A.n = 0;
+    if (r < G.n_if) {
+        nc_point(G, B, A, base, r, G.edges[r + 1], l, m, 1.0, true);
+    } else {
+        const int q = r - G.n_if, j = q / G.k, i = q % G.k + 1;
+        const double h = G.edges[j + 1] - G.edges[j], xc = 0.5 * (G.edges[j] + G.edges[j + 1]);
+        double P_[kB], dP[kB];
+        for (int th = 0; th < G.Q; ++th) {
+            dev_legendre(G.k, G.gs[th], P_, dP);
+            nc_point(G, B, A, base, r, xc + 0.5 * h * G.gs[th], l, m, G.gw[th] * dP[i], !G.has_delta);
+        }
+        if (G.has_delta) nc_appB(G, B, A, base, r, j, i, l, m);
+    }
+    if (B.pass == 0) {
+        B.count[blk] = A.n;
+    } else {
+        for (int al = 0; al < Q; ++al)
+            for (int be = 0; be < Q; ++be) {
+                const size_t o = ((size_t)r * NQ + l * Q + al) * NQ + m * Q + be;
+                B.Bc[o] = A.c[al * Q + be];
+                B.Bf[o] = A.f[al * Q + be];
+            }
+    }
+}
+
+// B <- fold(B) in place for both tables, one thread per (r, i, j > i)
+__global__ void nc_fold_kernel(int R, int NQ, double *Bc, double *Bf)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)R * NQ * NQ) return;
+    const int r = (int)(t / ((long long)NQ * NQ));
+    const int rem = (int)(t - (long long)r * NQ * NQ), i = rem / NQ, j = rem % NQ;
+    if (j <= i) return;
+    double *c = Bc + (size_t)r * NQ * NQ, *f = Bf + (size_t)r * NQ * NQ;
+    const size_t ij = (size_t)i * NQ + j, ji = (size_t)j * NQ + i;
+    c[ij] += c[ji];
+    c[ji] = 0.0;
+    f[ij] += f[ji];
+    f[ji] = 0.0;
+}
+
+// first / one-past-last column with a non-zero in either table, per row (r, i), and the rows' range per r
+__global__ void nc_extent_kernel(int R, int NQ, const double *Qt, const double *Dt, int *qlo, int *qhi)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= R * NQ) return;
+    const double *a = Qt + (size_t)row * NQ, *b = Dt + (size_t)row * NQ;
+    int lo = NQ, hi = 0;
+    for (int j = 0; j < NQ; ++j)
+        if (a[j] != 0.0 || b[j] != 0.0) {
+            if (lo == NQ) lo = j;
+            hi = j + 1;
+        }
+    qlo[row] = lo;
+    qhi[row] = hi;
+}
+
+// nodal values G = g at the fixed nodes, Hc = (1 - pf(s D0)) G and Hf = pf(s D0) G, per cell
+struct NodeRule {
+    double phi[kQMax * kB];   // phi_i at the Gauss node alpha: phi[alpha * kB + i]
+};
+
+__global__ void nc_nodal_kernel(DevGroup G, NodeRule rule, const double *__restrict__ D0, const double *__restrict__ g,
+                                const double *__restrict__ alpha, int n_cells, double *__restrict__ Gv,
+                                double *__restrict__ Hc, double *__restrict__ Hf)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int NQ = G.N * G.Q;
+    if (t >= (long long)n_cells * NQ) return;
+    const long long cell = t / NQ;
+    const int a = (int)(t - cell * NQ), l = a / G.Q, al = a - l * G.Q;
+    const double *gb = g + (size_t)cell * G.P + (size_t)l * G.K1;
+    double v = 0.0;
+    for (int i = 0; i <= G.k; ++i) v += gb[i] * rule.phi[al * kB + i];
+    const double s = sqrt(alpha[cell]);
+    const double pf = dev_pfrag(G.coag_p, s * D0[a]);
+    Gv[t] = v;
+    Hc[t] = (1.0 - pf) * v;
+    Hf[t] = pf * v;
+}
+
+// fixed part: F[c][r] = s_c sum_i G_i sum_{j >= i} (Cc_r[i][j] Hc_j + Cf_r[i][j] Hf_j); one warp per 32 cells
+__global__ void __launch_bounds__(128) nc_fixed_kernel(const double *__restrict__ Cc, const double *__restrict__ Cf,
+                                                       const int *__restrict__ qlo, const int *__restrict__ qhi,
+                                                       int R, int NQ, const double *__restrict__ Gv,
+                                                       const double *__restrict__ Hcv, const double *__restrict__ Hfv,
+                                                       const double *__restrict__ alpha, int n_cells,
+                                                       double *__restrict__ F)
+{
+    extern __shared__ double nsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const long long cell0 = ((long long)blockIdx.x * nwarps + warp) * 32;
+    double *gw = nsm + (size_t)warp * NQ * 96;   // G, Hc, Hf, transposed [node][cell]
+    double *hc = gw + (size_t)NQ * 32, *hf = hc + (size_t)NQ * 32;
+    for (int idx = lane; idx < 32 * NQ; idx += 32) {
+        const int c = idx / NQ, q = idx - c * NQ;
+        const long long cell = cell0 + c;
+        const bool ok = cell < n_cells;
+        gw[q * 32 + c] = ok ? Gv[cell * NQ + q] : 0.0;
+        hc[q * 32 + c] = ok ? Hcv[cell * NQ + q] : 0.0;
+        hf[q * 32 + c] = ok ? Hfv[cell * NQ + q] : 0.0;
+    }
+    __syncwarp();
+    const long long cell = cell0 + lane;
+    const double s = cell < n_cells ? sqrt(alpha[cell]) : 0.0;
+    for (int r = 0; r < R; ++r) {
+        double Fr = 0.0;
+        for (int i = 0; i < NQ; ++i) {
+            const int j0 = qlo[r * NQ + i], j1 = qhi[r * NQ + i];
+            if (j0 >= j1) continue;
+            const double *cr = Cc + ((size_t)r * NQ + i) * NQ, *fr = Cf + ((size_t)r * NQ + i) * NQ;
+            double y = 0.0;
+            for (int j = j0; j < j1; ++j) y = fma(__ldg(cr + j), hc[j * 32 + lane], fma(__ldg(fr + j), hf[j * 32 + lane], y));
+            Fr = fma(gw[i * 32 + lane], y, Fr);
+        }
+        if (cell < n_cells) F[cell * R + r] = s * Fr;
+    }
+}
+
+// partial entries of functional r (blockIdx.y) for 128 cells (one per thread); the
+// entries are staged through shared memory and shared by the block's cells
+__global__ void __launch_bounds__(128) nc_partial_kernel(DevGroup G, const NcEntry *__restrict__ entries,
+                                                         const long long *__restrict__ seg,
+                                                         const double *__restrict__ g,
+                                                         const double *__restrict__ alpha, int n_cells,
+                                                         double *__restrict__ F)
+{
+    __shared__ NcEntry es[64];
+    const int r = blockIdx.y;
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = cell < n_cells;
+    const double s = live ? sqrt(alpha[cell]) : 0.0;
+    const double *gc = g + (size_t)(live ? cell : 0) * G.P;
+    const long long e0 = seg[r], e1 = seg[r + 1];
+    double acc = 0.0;
+    for (long long c0 = e0; c0 < e1; c0 += 64) {
+        const int n = (int)min((long long)64, e1 - c0);
+        __syncthreads();
+        for (int w = threadIdx.x; w < n * (int)(sizeof(NcEntry) / 8); w += blockDim.x)
+            reinterpret_cast<double *>(es)[w] = reinterpret_cast<const double *>(entries + c0)[w];
+        __syncthreads();
+        if (live)
+            for (int t = 0; t < n; ++t) {
+                const NcEntry &e = es[t];
+                const double *gu = gc + (size_t)e.bu * G.K1, *gv = gc + (size_t)e.bv * G.K1;
+                double u = 0.0, v = 0.0;
+                for (int i = 0; i <= G.k; ++i) {
+                    u = fma(gu[i], e.pu[i], u);
+                    v = fma(gv[i], e.pv[i], v);
+                }
+                const double pf = dev_pfrag(G.coag_p, s * e.D0);
+                acc = fma(e.w * (e.kind ? pf : 1.0 - pf), u * v, acc);
+            }
+    }
+    if (live) F[cell * G.R + r] += s * acc;
+}
+
+}  // namespace
+
+void free_nc_tables(NcTables &t)
+{
+    cudaFree(t.d_Cc);
+    cudaFree(t.d_Cf);
+    cudaFree(t.d_qlo);
+    cudaFree(t.d_qhi);
+    cudaFree(t.d_D0);
+    cudaFree(t.d_entries);
+    cudaFree(t.d_seg);
+    t = NcTables();
+}
+
+grace_status build_nc_tables(Group &Gr, cudaStream_t st)
+{
+    const DevGroup &g = Gr.dg;
+    NcTables &T = Gr.nc;
+    free_nc_tables(T);
+    const int N = g.N, Q = g.Q, R = g.R, NQ = N * Q;
+    T.NQ = NQ;
+    const size_t ntab = (size_t)R * NQ * NQ, nblk = (size_t)R * N * N;
+    long long *d_count = nullptr, *d_off = nullptr;
+    cudaError_t e = cudaMalloc(&T.d_Cc, ntab * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_Cf, ntab * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&d_count, nblk * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&d_off, nblk * sizeof(long long));
+    if (e != cudaSuccess) {
+        cudaFree(d_count);
+        cudaFree(d_off);
+        free_nc_tables(T);
+        cudaGetLastError();
+        set_error(std::string("node-space tables: allocation: ") + cudaGetErrorString(e));
+        return GRACE_ERR_NOMEM;
+    }
+    NcBuild B;
+    B.Bc = T.d_Cc;   // folded in place afterwards
+    B.Bf = T.d_Cf;
+    B.count = d_count;
+    B.offset = d_off;
+    B.entries = nullptr;
+    B.pass = 0;
+    const dim3 grid((N * N + 127) / 128, R);
+    nc_build_kernel<<<grid, 128, 0, st>>>(g, B);
+    e = cudaGetLastError();
+    std::vector<long long> cnt(nblk), off(nblk);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_count, nblk * sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // entries ordered by (r, l, m): each functional's entries are contiguous
+    std::vector<long long> seg(R + 1, 0);
+    long long total = 0;
+    for (size_t b = 0; b < nblk; ++b) {
+        off[b] = total;
+        total += cnt[b];
+        seg[b / ((size_t)N * N) + 1] = total;
+    }
+    T.n_entries = total;
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_entries, (size_t)std::max<long long>(total, 1) * sizeof(NcEntry));
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_seg, (R + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), nblk * sizeof(long long), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(T.d_seg, seg.data(), (R + 1) * sizeof(long long), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        B.entries = (NcEntry *)T.d_entries;
+        B.pass = 1;
+        nc_build_kernel<<<grid, 128, 0, st>>>(g, B);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        nc_fold_kernel<<<(unsigned)((ntab + 255) / 256), 256, 0, st>>>(R, NQ, T.d_Cc, T.d_Cf);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_qlo, sizeof(int) * R * NQ);
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_qhi, sizeof(int) * R * NQ);
+    if (e == cudaSuccess) {
+        nc_extent_kernel<<<(R * NQ + 127) / 128, 128, 0, st>>>(R, NQ, T.d_Cc, T.d_Cf, T.d_qlo, T.d_qhi);
+        e = cudaGetLastError();
+    }
+    // D0 of every fixed node (the larger particle of a fixed pair is one of them)
+    std::vector<double> D0(NQ), gsv(Q);
+    for (int a = 0; a < NQ; ++a) {
+        const int l = a / Q, al = a % Q;
+        const double lo = Gr.h_edges[l], hi = Gr.h_edges[l + 1];
+        const double u = 0.5 * (lo + hi) + 0.5 * (hi - lo) * g.gs[al];
+        const double pi = 3.141592653589793, rho = g.coag_p[0], sig = g.coag_p[1], cs = g.coag_p[2];
+        const double au = std::cbrt(3.0 * u / (4.0 * pi * rho));
+        const double stn = pi * rho * au / (2.0 * sig);
+        D0[a] = cs * std::sqrt(3.0 * stn / (1.0 + stn * stn));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_D0, NQ * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(T.d_D0, D0.data(), NQ * sizeof(double), cudaMemcpyHostToDevice, st);
+    // structural non-zeros of the two tables
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_count);
+    cudaFree(d_off);
+    if (e != cudaSuccess) {
+        free_nc_tables(T);
+        return cuda_fail(e, "node-space tables: build");
+    }
+    T.built = 1;
+    return GRACE_OK;
+}
+
+cudaError_t launch_nc_functionals(const DevGroup &g, const NcTables &t, const double *d_g, const double *d_alpha,
+                                  int n_cells, double *d_G, double *d_H, double *d_F, cudaStream_t st)
+// d_G: [n][NQ] nodal values; d_H: [2][n][NQ] the coagulation- and fragmentation-weighted copies
+{
+    if (n_cells <= 0) return cudaSuccess;
+    if (!t.built) return cudaErrorInvalidValue;
+    const int NQ = t.NQ;
+    NodeRule rule;
+    for (int al = 0; al < g.Q; ++al) {
+        double P[kB];
+        // Legendre values at the Gauss node s_alpha (host recurrence, eq. 2.4)
+        P[0] = 1.0;
+        if (g.k >= 1) P[1] = g.gs[al];
+        for (int n = 1; n < g.k; ++n) P[n + 1] = ((2.0 * n + 1.0) * g.gs[al] * P[n] - n * P[n - 1]) / (n + 1.0);
+        for (int i = 0; i < kB; ++i) rule.phi[al * kB + i] = i <= g.k ? P[i] : 0.0;
+    }
+    const long long nn = (long long)n_cells * NQ;
+    double *d_Hc = d_H, *d_Hf = d_H + nn;
+    nc_nodal_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(g, rule, t.d_D0, d_g, d_alpha, n_cells, d_G, d_Hc,
+                                                                   d_Hf);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t per_warp = (size_t)NQ * 96 * sizeof(double);
+    int wpb = (int)((200 * 1024) / per_warp);
+    if (wpb > 4) wpb = 4;
+    if (wpb < 1) return cudaErrorInvalidValue;
+    const size_t smem = per_warp * wpb;
+    e = cudaFuncSetAttribute(nc_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int cells_per_block = 32 * wpb;
+    nc_fixed_kernel<<<(n_cells + cells_per_block - 1) / cells_per_block, 32 * wpb, smem, st>>>(
+        t.d_Cc, t.d_Cf, t.d_qlo, t.d_qhi, g.R, NQ, d_G, d_Hc, d_Hf, d_alpha, n_cells, d_F);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || t.n_entries == 0) return e;
+    const dim3 grid((n_cells + 127) / 128, g.R);
+    nc_partial_kernel<<<grid, 128, 0, st>>>(g, (const NcEntry *)t.d_entries, t.d_seg, d_g, d_alpha, n_cells, d_F);
+    return cudaGetLastError();
+}
+
+}  // namespace grace

@@ -57,6 +57,10 @@ extern "C" grace_status grace_rhs_noalloc(grace_ctx *ctx, int group, int n_cells
         return GRACE_ERR_ORDER;
     }
     const Group &G = ctx->groups[group];
+    if (G.dg.cell_alpha) {
+        set_error("grace_rhs_noalloc: groups with a per-cell kernel parameter are not supported");
+        return GRACE_ERR_UNSUPPORTED;
+    }
     const size_t need = (size_t)n_cells * (size_t)G.dg.R;
     if (need > kStaticScratchDoubles) {
         set_error("grace_rhs_noalloc: n_cells * n_functionals = " + std::to_string(need) +

@@ -44,6 +44,30 @@ __device__ __forceinline__ void dev_ballistic(const double *p, double u, double 
     *kf = rate * pf;
 }
 
+// The ballistic-turbulent kernels factor through sqrt(alpha_turb):
+//   K_coag = s S0(u, v) (1 - pf(s D0)),  K_frag = s S0(u, v) pf(s D0),  s = sqrt(alpha_turb),
+// with D0 = c_s sqrt(3 St / (1 + St^2)) a function of the larger particle only (St
+// from max(a_u, a_v)), S0 = p6 pi (a_u + a_v)^2 D0, and pf(z) = clamp((z - (1 - w) v_f)
+// / (2 w v_f), 0, 1).  A per-cell alpha_turb then enters only through s and pf.
+__device__ __forceinline__ void dev_ballistic_split(const double *p, double u, double v, double *S0, double *D0)
+{
+    const double pi = 3.141592653589793;
+    double rho = p[0], sig = p[1], cs = p[2];
+    double au = cbrt(3.0 * u / (4.0 * pi * rho));
+    double av = cbrt(3.0 * v / (4.0 * pi * rho));
+    double st = pi * rho * fmax(au, av) / (2.0 * sig);
+    double d0 = cs * sqrt(3.0 * st / (1.0 + st * st));
+    *D0 = d0;
+    *S0 = p[6] * pi * (au + av) * (au + av) * d0;
+}
+
+// fragmentation probability of the ramp as a function of z = s D0
+__device__ __forceinline__ double dev_pfrag(const double *p, double z)
+{
+    const double vf = p[4], wr = p[5];
+    return fmin(fmax((z - (1.0 - wr) * vf) / (2.0 * wr * vf), 0.0), 1.0);
+}
+
 __device__ __forceinline__ double dev_kcoag(const DevGroup &G, double u, double v)
 {
     switch (G.coag_kind) {

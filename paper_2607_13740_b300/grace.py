@@ -37,6 +37,7 @@ class GroupDesc(ctypes.Structure):
         ("x_min", ctypes.c_double), ("x_max", ctypes.c_double),
         ("coag_p", ctypes.c_double * 8), ("frag_p", ctypes.c_double * 8),
         ("break_p", ctypes.c_double * 8),
+        ("cell_alpha", ctypes.c_int), ("reserved_", ctypes.c_int),
     ]
 
 
@@ -47,7 +48,7 @@ def exported_symbols():
             "grace_limit", "grace_profile_enable", "grace_profile_read", "grace_group_stats",
             "grace_batch_error", "grace_rhs_jvp", "grace_rhs_vjp", "grace_param_grad_setup",
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_destroy",
-            "grace_destroy", "grace_tile_info"]
+            "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc"]
 
 
 def load(path: str | None = None):
@@ -80,6 +81,7 @@ def load(path: str | None = None):
     L.grace_group_stats.argtypes = [_VP, S, S, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.grace_batch_error.argtypes = [_VP, ctypes.POINTER(S)]
     L.grace_tile_info.argtypes = [_VP, S, S, ctypes.POINTER(ctypes.c_longlong)]
+    L.grace_batch_cell_params.argtypes = [_VP, _VP]
     L.grace_rhs_jvp.argtypes = [_VP, _VP, _VP, _VP, S]
     L.grace_rhs_vjp.argtypes = [_VP, _VP, _VP, _VP, S]
     L.grace_param_grad_setup.argtypes = [_VP, S, S, _VP, ctypes.c_double]
@@ -106,7 +108,7 @@ def _check(status: int, what: str):
 def group_desc(spec: W.GroupSpec) -> GroupDesc:
     d = GroupDesc()
     for f in ("n_bins", "order_k", "quad_q", "flux_mode", "coag_kind", "frag_kind", "break_kind",
-              "cutoff_mode", "limiter", "mfrag_mode", "x_min", "x_max"):
+              "cutoff_mode", "limiter", "mfrag_mode", "x_min", "x_max", "cell_alpha"):
         setattr(d, f, getattr(spec, f))
     for name in ("coag_p", "frag_p", "break_p"):
         arr = getattr(d, name)
@@ -309,6 +311,14 @@ class Batch:
         _check(load().grace_adjoint(self._h, _ptr(g0), _ptr(dt), int(n_steps), int(ckpt_every), _ptr(lam_T),
                                     _ptr(lam0), _ptr(dth), int(precision)), "grace_adjoint")
         return lam0, dth
+
+    def cell_params(self, alpha):
+        """Per-cell alpha_turb for groups with cell_alpha = 1 (device FP64, batch order)."""
+        import torch
+        a = torch.as_tensor(alpha, dtype=torch.float64, device=f"cuda:{self.ctx.device}").contiguous()
+        self.ctx.set_stream()
+        _check(load().grace_batch_cell_params(self._h, _ptr(a)), "grace_batch_cell_params")
+        self._alpha = a
 
     def set_graph(self, enable: bool = True):
         """Replay grace_step from a captured CUDA graph for repeated identical calls."""

@@ -281,11 +281,26 @@ grace_status grace_precompute(grace_ctx *ctx, unsigned mask)
         for (Group &G : ctx->groups) {
             const DevGroup &g = G.dg;
             if (g.cell_alpha) {
-                // per-cell kernel: no fixed T exists; node-space tables (FP64 path only)
+                // per-cell kernel: no fixed T exists; node-space tables (FP64 path only).
+                // nnz reports the multiply-adds of one RHS per cell: the non-zeros of the
+                // two tables plus 2 (k+1) + 2 per partial entry
                 if (!G.nc.built) {
                     grace_status s = build_nc_tables(G, st);
                     if (s != GRACE_OK) return s;
-                    G.nnz = 0;
+                    const size_t nt = (size_t)g.R * G.nc.NQ * G.nc.NQ;
+                    unsigned long long *d_cnt = nullptr, cnt = 0;
+                    cudaError_t e = cudaMalloc(&d_cnt, sizeof(unsigned long long));
+                    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st);
+                    if (e == cudaSuccess) {
+                        count_nnz_kernel<<<256, 256, 0, st>>>(G.nc.d_Cc, nt, d_cnt);
+                        count_nnz_kernel<<<256, 256, 0, st>>>(G.nc.d_Cf, nt, d_cnt);
+                        e = cudaGetLastError();
+                    }
+                    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                    cudaFree(d_cnt);
+                    if (e != cudaSuccess) return cuda_fail(e, "grace_precompute: node-space tables");
+                    G.nnz = (long long)cnt + G.nc.n_entries * (2LL * g.K1 + 2);
                 }
                 continue;
             }

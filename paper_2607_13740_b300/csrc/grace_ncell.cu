@@ -321,7 +321,9 @@ __global__ void nc_nodal_kernel(DevGroup G, NodeRule rule, const double *__restr
     Hf[t] = pf * v;
 }
 
-// fixed part: F[c][r] = s_c sum_i G_i sum_{j >= i} (Cc_r[i][j] Hc_j + Cf_r[i][j] Hf_j); one warp per 32 cells
+// fixed part: F[c][r] = s_c sum_i G_i sum_{j >= i} (Cc_r[i][j] Hc_j + Cf_r[i][j] Hf_j); one warp per 32
+// cells and a chunk of kRChunk functionals (blockIdx.y), so that small batches still fill the GPU
+constexpr int kRChunk = 8;
 __global__ void __launch_bounds__(128) nc_fixed_kernel(const double *__restrict__ Cc, const double *__restrict__ Cf,
                                                        const int *__restrict__ qlo, const int *__restrict__ qhi,
                                                        int R, int NQ, const double *__restrict__ Gv,
@@ -346,7 +348,8 @@ __global__ void __launch_bounds__(128) nc_fixed_kernel(const double *__restrict_
     __syncwarp();
     const long long cell = cell0 + lane;
     const double s = cell < n_cells ? sqrt(alpha[cell]) : 0.0;
-    for (int r = 0; r < R; ++r) {
+    const int r_end = min(R, (int)(blockIdx.y + 1) * kRChunk);
+    for (int r = blockIdx.y * kRChunk; r < r_end; ++r) {
         double Fr = 0.0;
         for (int i = 0; i < NQ; ++i) {
             const int j0 = qlo[r * NQ + i], j1 = qhi[r * NQ + i];
@@ -530,7 +533,8 @@ cudaError_t launch_nc_functionals(const DevGroup &g, const NcTables &t, const do
     e = cudaFuncSetAttribute(nc_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int cells_per_block = 32 * wpb;
-    nc_fixed_kernel<<<(n_cells + cells_per_block - 1) / cells_per_block, 32 * wpb, smem, st>>>(
+    const dim3 fgrid((n_cells + cells_per_block - 1) / cells_per_block, (g.R + kRChunk - 1) / kRChunk);
+    nc_fixed_kernel<<<fgrid, 32 * wpb, smem, st>>>(
         t.d_Cc, t.d_Cf, t.d_qlo, t.d_qhi, g.R, NQ, d_G, d_Hc, d_Hf, d_alpha, n_cells, d_F);
     e = cudaGetLastError();
     if (e != cudaSuccess || t.n_entries == 0) return e;

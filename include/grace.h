@@ -232,11 +232,12 @@ GRACE_API grace_status grace_group_stats(const grace_ctx *ctx, int group, int pr
 
 /* Tensor-core tile plan of one group for precision GRACE_TF32 or GRACE_BF16X3
    (built by grace_precompute; the tile shapes are chosen by a cost model over
-   the sparsity of T, see the contraction's documentation).  Writes 7 values
+   the sparsity of T, see the contraction's documentation).  Writes 8 values
    (host): [0] N-tiles, [1] tcgen05.mma instructions per 128-cell tile and RHS,
    [2] executed multiply-adds per cell and RHS, [3] bytes of the B images,
    [4] cost-model SM cycles per 128-cell tile and RHS, [5] widest MMA N,
-   [6] non-zeros of the symmetric-folded tables (the multiply-adds a cell needs).
+   [6] the multiply-adds a cell needs (non-zeros of T or of its symmetric fold, the
+   smaller), [7] 1 when the tiles hold the folded tables, 0 when T as built.
    GRACE_ERR_ORDER when that precision was not precomputed. */
 GRACE_API grace_status grace_tile_info(const grace_ctx *ctx, int group, int precision, long long *info);
 

@@ -424,6 +424,7 @@ grace_status grace_tile_info(const grace_ctx *ctx, int group, int prec, long lon
     info[4] = (long long)(t.pred_clk + 0.5);
     info[5] = t.max_rows;
     info[6] = t.nnz_fold;
+    info[7] = t.folded;
     return GRACE_OK;
 }
 

@@ -69,6 +69,7 @@ void free_part(Part &p)
     cudaFree(p.d_g1);
     cudaFree(p.d_g2);
     cudaFree(p.d_opA);
+    cudaFree(p.d_mx);
     cudaFree(p.d_alpha);
     cudaFree(p.d_G);
     cudaFree(p.d_H);
@@ -154,13 +155,59 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
     if (flags) e = cudaMemsetAsync(flags, 0, n, st);
     if (e != cudaSuccess) return e;
     if (n_steps == 0) return mass ? launch_mass(dg, g, n, mass, st) : cudaSuccess;
-    // reconstruction of the first step (Sec. 3.2.2); later ones are fused into stage 3
-    if (dg.limiter || tc) {
-        e = launch_limit(dg, g, n, flags, opA, prec, kpad, st);
-        if (e != cudaSuccess) return e;
-    }
     static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
     static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    if (tc) {
+        // Tensor path.  Inside the call the state lives in the compact stage layout (FP64
+        // means, FP32 higher modes): X[0] = g^n, X[1] = g^(1), X[2] = g^(2).  The step-start
+        // limiter (Sec. 3.2.2) converts the caller's rows into X[0] and writes the A operand;
+        // later reconstructions are fused into stage 3, and the last stage writes the
+        // caller's FP64 rows.
+        const size_t xs = (mixed_bytes_for(dg, n) + 15) / 16 * 2;   // doubles per compact state
+        double *X[3] = {p.d_mx, p.d_mx + xs, p.d_mx + 2 * xs};
+        e = launch_limit_pack(dg, g, n, flags, X[0], opA, prec, kpad, st);
+        if (e != cudaSuccess) return e;
+        for (int step = 0; step < n_steps; ++step) {
+            const bool last = step == n_steps - 1;
+            for (int stage = 0; stage < 3; ++stage) {
+                {
+                    LaunchTimer timer(b->ctx, 0, st);
+                    e = launch_contract_tc(dg, G.tc[prec], prec, opA, n, p.d_F32, b->d_err, st);
+                }
+                if (e != cudaSuccess) return e;
+                UpdateArgs u;
+                u.F32 = p.d_F32;
+                u.gn = X[0];
+                u.gs = X[stage];
+                u.in_mixed = 1;
+                u.dt = dt;
+                u.a = ca[stage];
+                u.b = cb[stage];
+                u.flags = flags;
+                const bool final_stage = stage == 2 && last;
+                u.gout = stage < 2 ? X[stage + 1] : (last ? g : X[0]);
+                u.out_mixed = final_stage ? 0 : 1;
+                if (stage == 2) {
+                    u.apply_limiter = (!last && dg.limiter) ? 1 : 0;
+                    u.mass = last ? mass : nullptr;
+                }
+                if (!final_stage) {
+                    u.opA = opA;
+                    u.opA_prec = prec;
+                    u.opA_kpad = kpad;
+                }
+                LaunchTimer timer(b->ctx, 1, st);
+                e = launch_update_tc(dg, u, n, st);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    }
+    // reconstruction of the first step (Sec. 3.2.2); later ones are fused into stage 3
+    if (dg.limiter) {
+        e = launch_limit(dg, g, n, flags, nullptr, 0, 0, st);
+        if (e != cudaSuccess) return e;
+    }
     for (int step = 0; step < n_steps; ++step) {
         const bool last = step == n_steps - 1;
         const double *gin[3] = {g, p.d_g1, p.d_g2};
@@ -178,23 +225,7 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
                 u.apply_limiter = (!last && dg.limiter) ? 1 : 0;
                 u.mass = last ? mass : nullptr;
             }
-            if (tc) {
-                // tcgen05 contraction, then the flux difference / RK stage, which also
-                // writes the next stage's A operand
-                {
-                    LaunchTimer timer(b->ctx, 0, st);
-                    e = launch_contract_tc(dg, G.tc[prec], prec, opA, n, p.d_F32, b->d_err, st);
-                }
-                if (e != cudaSuccess) return e;
-                u.F32 = p.d_F32;
-                if (!(stage == 2 && last)) {
-                    u.opA = opA;
-                    u.opA_prec = prec;
-                    u.opA_kpad = kpad;
-                }
-                LaunchTimer timer(b->ctx, 1, st);
-                e = launch_update_tc(dg, u, n, st);
-            } else {
+            {
                 {
                     LaunchTimer timer(b->ctx, 0, st);
                     e = dg.cell_alpha
@@ -333,6 +364,7 @@ grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group
                 for (int prec = GRACE_TF32; prec <= GRACE_BF16X3; ++prec)
                     if (ctx->precision_mask & (1u << prec)) bytes = std::max(bytes, opA_bytes_for(g, prec, p.n, nullptr));
                 if (e == cudaSuccess) e = cudaMalloc(&p.d_opA, bytes);
+                if (e == cudaSuccess) e = cudaMalloc(&p.d_mx, 3 * ((mixed_bytes_for(g, (int)n) + 15) / 16 * 16));
                 if (e == cudaSuccess) e = cudaMemset(p.d_opA, 0, bytes);
                 p.opA_bytes = bytes;
             }

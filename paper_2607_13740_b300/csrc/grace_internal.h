@@ -42,7 +42,8 @@ struct TcTiles {
     size_t b_bytes = 0;
     long long mac_per_cell = 0;    // executed MACs per cell and RHS (tile shapes)
     long long mma_per_tile = 0;    // tcgen05.mma instructions per 128-cell tile and RHS
-    long long nnz_fold = 0;        // non-zeros of the folded (upper-triangular) tables
+    long long nnz_fold = 0;        // min(non-zeros of T, of its upper-triangular fold): the MACs a cell needs
+    int folded = 0;                // the tiles hold the folded tables (else T as built)
     double pred_clk = 0.0;         // cost-model SM cycles per 128-cell tile and RHS
     std::vector<int> group_tile;   // first tile of every functional group (+ end)
     std::vector<double> group_cost;   // cost-model cycles of every group
@@ -121,6 +122,7 @@ struct Part {
     double *d_F = nullptr;         // [n][R] functionals, FP64
     float *d_F32 = nullptr;        // [tiles][R][128] functionals from the tensor path
     double *d_g1 = nullptr, *d_g2 = nullptr;   // stage states
+    double *d_mx = nullptr;        // tensor path: three stage states in the compact layout
     void *d_opA = nullptr;         // tensor-core A operand of the current stage
     double *d_alpha = nullptr;     // [n] per-cell alpha_turb (cell_alpha groups)
     double *d_G = nullptr, *d_H = nullptr;   // [n][NQ], [2][n][NQ] nodal values (cell_alpha groups)
@@ -199,6 +201,8 @@ struct UpdateArgs {
     void *opA = nullptr;           // tensor-core A tiles of gout, or null
     int opA_prec = 0;              // GRACE_TF32 / GRACE_BF16X3
     int opA_kpad = 0;
+    int in_mixed = 0;              // tensor path: gn / gs in the compact stage layout
+    int out_mixed = 0;             // tensor path: gout in the compact stage layout
 };
 cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st);
 // tcgen05 contraction: the flux functionals of every cell into d_F32 laid out as
@@ -208,6 +212,14 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
 // K-c for the tensor path: reads d_F32 in the tile layout above
 cudaError_t launch_update_tc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st);
 size_t f32_bytes_for(const DevGroup &g, int n_cells);
+// the step-start limiter of the tensor path: FP64 rows d_g -> compact stage layout + A operand
+cudaError_t launch_limit_pack(const DevGroup &g, const double *d_g, int n_cells, unsigned char *flags,
+                              double *mixed_out, void *opA, int opA_prec, int opA_kpad, cudaStream_t st);
+// bytes of one state in the compact stage layout (FP64 means, FP32 higher modes)
+inline size_t mixed_bytes_for(const DevGroup &g, int n_cells)
+{
+    return (size_t)n_cells * g.N * (sizeof(double) + (size_t)g.k * sizeof(float));
+}
 cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned char *flags,
                          void *opA, int opA_prec, int opA_kpad, cudaStream_t st);
 cudaError_t launch_mass(const DevGroup &g, const double *d_g, int n_cells, double *mass,

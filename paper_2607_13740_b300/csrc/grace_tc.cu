@@ -33,7 +33,9 @@
 //   warps 4..19   : epilogue; TMEM lane quadrant = warp % 4, four warps per quadrant
 //                   splitting the functionals of a tile; one cell per thread
 // A work item is one 128-cell tile and a contiguous range of N-tiles (a split):
-// splitting the tile list lets a batch of few cell tiles fill every SM.
+// splitting the tile list lets a batch of few cell tiles fill every SM.  Items are
+// numbered split-major (item = split x cell tiles + cell tile) so that the
+// round-robin assignment gives every CTA a mix of splits.
 // Every wait on an mbarrier is bounded; on timeout the CTA records an error in
 // the device error word, stops issuing work, drains its outstanding copies and
 // releases its tensor memory before returning.
@@ -57,6 +59,7 @@ constexpr int kAccCols = 256;       // TMEM columns per accumulator buffer
 constexpr int kTmemCols = 512;      // two accumulator buffers
 constexpr int kEpiWarps = 8;
 constexpr int kEpiSplit = kEpiWarps / 4;   // epilogue warps per TMEM lane quadrant
+constexpr int kEpiF = (kMaxF + kEpiSplit - 1) / kEpiSplit;   // functionals per epilogue warp and tile
 constexpr int kThreads = 32 * (4 + kEpiWarps);
 constexpr int kMaxSplits = 8;
 constexpr int kSmemLimit = 227 * 1024;
@@ -67,6 +70,8 @@ constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 constexpr double kMmaClk = 139.0;
 constexpr double kL2BytesPerClk = 45.0;
 constexpr double kTileClk = 60.0;        // accumulator hand-off per tile
+constexpr double kEpiBaseClk = 250.0;    // epilogue per tile: fixed part (TMEM round trip, window load)
+constexpr double kEpiColClk = 5.5;       // epilogue per tile and accumulator column (8 warps)
 constexpr double kItemClk = 2500.0;      // A tile load + pipeline fill per work item
 
 struct TileDesc {
@@ -284,7 +289,7 @@ __device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_
         }
     }
 #pragma unroll
-    for (int m0 = 0; m0 < kMaxF / kEpiSplit; m0 += G) {
+    for (int m0 = 0; m0 < kEpiF; m0 += G) {
         if (kEpiSplit * m0 + part >= nf) break;
         uint32_t y[G][W];
 #pragma unroll
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         const int me = warp == 0 ? 0 : 1;
         int q = 0, ctl = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
-            const int ct = it / P.n_splits, sp = it - ct * P.n_splits;
+            const int sp = it / P.n_cell_tiles, ct = it - sp * P.n_cell_tiles;
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             int ok = 1;
             if (lane == 0) {
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         // ------------------------------------------------ MMA issuer
         int q = 0, acc_use = 0, ctl = 0;
         for (int it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x, ++ctl) {
-            const int ct = it / P.n_splits, sp = it - ct * P.n_splits;
+            const int sp = it / P.n_cell_tiles;
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             if (!mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag)) {
                 fail(P, abort_flag, 4);
@@ -501,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         const uint32_t tlane = (uint32_t)(qd * 32) << 16;
         int acc_use = 0, ctl = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
-            const int ct = it / P.n_splits, sp = it - ct * P.n_splits;
+            const int sp = it / P.n_cell_tiles, ct = it - sp * P.n_cell_tiles;
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag))) {
                 fail(P, abort_flag, 32);
@@ -510,9 +515,9 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             const uint8_t *a_gen = gbase + (size_t)ab * P.a_tile_bytes;
             const long long cell = (long long)ct * kTileM + row;
             const bool live = cell < P.n_cells;
-            float Facc[kMaxF / kEpiSplit];
+            float Facc[kEpiF];
 #pragma unroll
-            for (int m = 0; m < kMaxF / kEpiSplit; ++m) Facc[m] = 0.f;
+            for (int m = 0; m < kEpiF; ++m) Facc[m] = 0.f;
             bool aborted = false;
             for (int t = P.split[sp]; t < P.split[sp + 1]; ++t) {
                 if (__any_sync(0xffffffffu, *abort_flag)) {
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 }
                 tc_fence_after();
                 const uint32_t tcol = tmem + tlane + (uint32_t)(buf * kAccCols);
-                epi_tile<PREC, kWin, kMaxF / kEpiSplit>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, Facc);
+                epi_tile<PREC, kWin, kEpiF>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, Facc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&S->acc_empty[buf]));
@@ -538,13 +543,13 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     if (live) {
                         float *Fo = P.F + ((size_t)ct * P.R) * kTileM + row;
 #pragma unroll
-                        for (int m = 0; m < kMaxF / kEpiSplit; ++m) {
+                        for (int m = 0; m < kEpiF; ++m) {
                             const int f = kEpiSplit * m + part;
                             if (f < nf) Fo[(size_t)ford[td.f0 + f] * kTileM] = Facc[m];
                         }
                     }
 #pragma unroll
-                    for (int m = 0; m < kMaxF / kEpiSplit; ++m) Facc[m] = 0.f;
+                    for (int m = 0; m < kEpiF; ++m) Facc[m] = 0.f;
                 }
             }
             if (aborted) break;
@@ -662,23 +667,22 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
     std::vector<double> h(g.N);
     for (int j = 0; j < g.N; ++j) h[j] = G.h_edges[j + 1] - G.h_edges[j];
 
-    // fold onto the upper triangle (in place) and record each row's q extent
-    std::vector<int> qlo((size_t)R * P_, P_), qhi((size_t)R * P_, 0);
-    long long nnz_fold = 0;
+    // Two representations of the same quadratic forms: T as built (u-side p, v-side q) and its
+    // fold onto the upper triangle U (U[p][q] = T[p][q] + T[q][p], q > p).  Both are planned and the
+    // cheaper plan under the cost model is built.
+    std::vector<double> U(T);
+    long long nnz_fold = 0, nnz_T = 0;
     for (int r = 0; r < R; ++r) {
-        double *Tr = T.data() + (size_t)r * P_ * P_;
+        double *Ur = U.data() + (size_t)r * P_ * P_;
         for (int p = 0; p < P_; ++p)
             for (int q = p + 1; q < P_; ++q) {
-                Tr[(size_t)p * P_ + q] += Tr[(size_t)q * P_ + p];
-                Tr[(size_t)q * P_ + p] = 0.0;
+                Ur[(size_t)p * P_ + q] += Ur[(size_t)q * P_ + p];
+                Ur[(size_t)q * P_ + p] = 0.0;
             }
-        for (int p = 0; p < P_; ++p)
-            for (int q = p; q < P_; ++q)
-                if (Tr[(size_t)p * P_ + q] != 0.0) {
-                    ++nnz_fold;
-                    qlo[(size_t)r * P_ + p] = std::min(qlo[(size_t)r * P_ + p], q);
-                    qhi[(size_t)r * P_ + p] = q + 1;
-                }
+    }
+    for (size_t i = 0; i < T.size(); ++i) {
+        nnz_T += T[i] != 0.0;
+        nnz_fold += U[i] != 0.0;
     }
 
     // functionals in bin order: interface flux of bin j, then its volume terms
@@ -692,92 +696,103 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
         return GRACE_ERR_ARG;
     }
 
-    // per functional: union of the q extents over each window of kWin p (the
-    // epilogue holds one window of ghat and all of a warp's accumulator columns
-    // in registers, which fixes the width; N = nf * kWin is chosen per group)
-    const int widths[1] = {kWin};
-    struct Ext {
-        int lo, hi;
-    };
-    std::vector<std::vector<Ext>> wext[1];
-    int n_win[1];
-    for (int wi = 0; wi < 1; ++wi) {
-        const int W = widths[wi];
-        n_win[wi] = (P_ + W - 1) / W;
-        wext[wi].assign(R, std::vector<Ext>(n_win[wi], Ext{P_, 0}));
-        for (int x = 0; x < R; ++x) {
-            const int r = ford[x];
-            for (int p = 0; p < P_; ++p) {
-                const size_t row = (size_t)r * P_ + p;
-                if (qhi[row] <= qlo[row]) continue;
-                Ext &E = wext[wi][x][p / W];
-                E.lo = std::min(E.lo, qlo[row]);
-                E.hi = std::max(E.hi, qhi[row]);
-            }
-        }
-    }
     auto tile_cost = [&](int n, int nks) {
         const double mma = (double)nks * mult * kMmaClk;
         const double l2 = (double)nks * n * 32.0 * planes / kL2BytesPerClk;
-        const double epi = n + 150.0;
+        const double epi = kEpiBaseClk + kEpiColClk * n;
         return std::max(mma, std::max(l2, epi)) + kTileClk;
     };
+    struct Ext {
+        int lo, hi;
+    };
+    struct Plan {
+        double cost = 1e300;
+        std::vector<std::pair<int, int>> groups;   // (first functional in ford order, window-width index)
+        std::vector<std::vector<Ext>> wext;       // [ford index][window] union of q extents
+        int n_win = 0;
+    };
+    const int W = kWin;
     // dynamic program over the functional order: best[y] = cheapest cover of ford[0, y)
-    const double inf = 1e300;
-    std::vector<double> best(R + 1, inf);
-    std::vector<int> from(R + 1, -1), wsel(R + 1, 0);
-    best[0] = 0.0;
-    for (int x = 0; x < R; ++x) {
-        if (best[x] >= inf) continue;
-        for (int wi = 0; wi < 1; ++wi) {
-            const int W = widths[wi], maxf = std::min(kMaxF, kMaxN / W);
-            std::vector<Ext> U(n_win[wi], Ext{P_, 0});
+    auto plan = [&](const std::vector<double> &M) {
+        Plan pl;
+        pl.n_win = (P_ + W - 1) / W;
+        pl.wext.assign(R, std::vector<Ext>(pl.n_win, Ext{P_, 0}));
+        for (int x = 0; x < R; ++x) {
+            const double *Mr = M.data() + (size_t)ford[x] * P_ * P_;
+            for (int p = 0; p < P_; ++p) {
+                int lo = P_, hi = 0;
+                for (int q = 0; q < P_; ++q)
+                    if (Mr[(size_t)p * P_ + q] != 0.0) {
+                        lo = std::min(lo, q);
+                        hi = q + 1;
+                    }
+                if (hi <= lo) continue;
+                Ext &E = pl.wext[x][p / W];
+                E.lo = std::min(E.lo, lo);
+                E.hi = std::max(E.hi, hi);
+            }
+        }
+        const double inf = 1e300;
+        std::vector<double> best(R + 1, inf);
+        std::vector<int> from(R + 1, -1);
+        best[0] = 0.0;
+        const int maxf = std::min(kMaxF, kMaxN / W);
+        for (int x = 0; x < R; ++x) {
+            if (best[x] >= inf) continue;
+            std::vector<Ext> Un(pl.n_win, Ext{P_, 0});
             for (int y = x + 1; y <= std::min(R, x + maxf); ++y) {
                 double c = 0.0;
-                for (int w = 0; w < n_win[wi]; ++w) {
-                    const Ext &E = wext[wi][y - 1][w];
-                    U[w].lo = std::min(U[w].lo, E.lo);
-                    U[w].hi = std::max(U[w].hi, E.hi);
-                    if (U[w].hi > U[w].lo)
-                        c += tile_cost((y - x) * W, (U[w].hi + kstep - 1) / kstep - U[w].lo / kstep);
+                for (int w = 0; w < pl.n_win; ++w) {
+                    const Ext &E = pl.wext[y - 1][w];
+                    Un[w].lo = std::min(Un[w].lo, E.lo);
+                    Un[w].hi = std::max(Un[w].hi, E.hi);
+                    if (Un[w].hi > Un[w].lo)
+                        c += tile_cost((y - x) * W, (Un[w].hi + kstep - 1) / kstep - Un[w].lo / kstep);
                 }
                 if (best[x] + c < best[y]) {
                     best[y] = best[x] + c;
                     from[y] = x;
-                    wsel[y] = wi;
                 }
             }
         }
-    }
-    std::vector<std::pair<int, int>> groups;   // (x, wi) in order
-    for (int y = R; y > 0; y = from[y]) groups.push_back({from[y], wsel[y]});
-    std::reverse(groups.begin(), groups.end());
+        for (int y = R; y > 0; y = from[y]) pl.groups.push_back({from[y], 0});
+        std::reverse(pl.groups.begin(), pl.groups.end());
+        pl.cost = best[R];
+        return pl;
+    };
+    Plan pT = plan(T), pU = plan(U);
+    const bool use_fold = pU.cost <= pT.cost;
+    const Plan &pl = use_fold ? pU : pT;
+    const std::vector<double> &M = use_fold ? U : T;
+    const auto &groups = pl.groups;
+    const auto &wext_sel = pl.wext;
+    const int n_win_sel = pl.n_win;
 
     TcTiles out;
     std::vector<TileDesc> tiles;
     std::vector<uint8_t> B;
     long long macs = 0, mmas = 0;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
-        const int x = groups[gi].first, wi = groups[gi].second;
+        const int x = groups[gi].first;
         const int y = gi + 1 < groups.size() ? groups[gi + 1].first : R;
-        const int W = widths[wi], nf = y - x, n = nf * W;
+        const int nf = y - x, n = nf * W;
         const size_t first = tiles.size();
         double gcost = 0.0;
-        for (int w = 0; w < n_win[wi]; ++w) {
-            Ext U{P_, 0};
+        for (int w = 0; w < n_win_sel; ++w) {
+            Ext Un{P_, 0};
             for (int f = x; f < y; ++f) {
-                U.lo = std::min(U.lo, wext[wi][f][w].lo);
-                U.hi = std::max(U.hi, wext[wi][f][w].hi);
+                Un.lo = std::min(Un.lo, wext_sel[f][w].lo);
+                Un.hi = std::max(Un.hi, wext_sel[f][w].hi);
             }
-            if (U.hi <= U.lo) continue;
+            if (Un.hi <= Un.lo) continue;
             TileDesc td;
             std::memset(&td, 0, sizeof(td));
             td.n = n;
             td.nf_flush = nf;
             td.w = W;
             td.p0 = w * W;
-            td.ks_lo = U.lo / kstep;
-            td.ks_hi = (U.hi + kstep - 1) / kstep;
+            td.ks_lo = Un.lo / kstep;
+            td.ks_hi = (Un.hi + kstep - 1) / kstep;
             td.f0 = x;
             const int nks = td.ks_hi - td.ks_lo;
             td.b_off16 = (int)(B.size() / 16);
@@ -787,13 +802,13 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
             for (int s = 0; s < nks; ++s) {
                 uint8_t *bk = img + (size_t)s * blk * planes;
                 for (int f = 0; f < nf; ++f) {
-                    const double *Tr = T.data() + (size_t)ford[x + f] * P_ * P_;
+                    const double *Tr = M.data() + (size_t)ford[x + f] * P_ * P_;
                     for (int c = 0; c < W; ++c) {
                         const int p = td.p0 + c, rowi = f * W + c;
                         if (p >= P_) continue;
                         for (int xx = 0; xx < kstep; ++xx) {
                             const int q = (td.ks_lo + s) * kstep + xx;
-                            if (q < p || q >= P_) continue;
+                            if (q >= P_) continue;
                             const double v = Tr[(size_t)p * P_ + q];
                             if (v == 0.0) continue;
                             const double val = v / (h[p / K1] * h[q / K1]);
@@ -850,8 +865,9 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
     out.b_bytes = B.size();
     out.mac_per_cell = macs;
     out.mma_per_tile = mmas;
-    out.nnz_fold = nnz_fold;
-    out.pred_clk = best[R];
+    out.nnz_fold = std::min(nnz_fold, nnz_T);
+    out.pred_clk = pl.cost;
+    out.folded = use_fold ? 1 : 0;
     out.slot_bytes = (out.slot_bytes + 1023) / 1024 * 1024;
     out.built = 1;
     G.tc[prec] = out;

@@ -175,7 +175,13 @@ constexpr int kUpdWarps = 8;
 
 // LPC lanes per cell (16 or 32, whichever leaves fewer lanes idle for N bins);
 // lane l of a cell handles bins l, l + LPC, ...
-template <int MODE, int LPC>
+//
+// State layouts: FP64 rows [cell][bin][i] (the caller's), or the compact stage
+// layout used inside grace_step for the tensor forms ("mixed"): for a part of n
+// cells, the means [n][N] in FP64 followed by the higher modes [n][N][k] in FP32
+// (the tensor forms carry the higher modes at FP32 precision anyway).  IN_MIX /
+// OUT_MIX select the layout of the stage inputs / the result.
+template <int MODE, int LPC, bool IN_MIX, bool OUT_MIX>
 __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G, UpdateArgs A, int n_cells)
 {
     extern __shared__ double sm[];
@@ -201,31 +207,56 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
     }
     if (cell >= n_cells) return;   // whole groups of LPC lanes leave together
     const float *F = Fs + slot * (R + 1);
-    const double *gsr = (MODE == MODE_LIMIT ? A.gout : A.gs) + (size_t)cell * P;
-    const double *gnr = MODE == MODE_STAGE ? A.gn + (size_t)cell * P : gsr;
+    // stage inputs: s = gs (MODE_STAGE), or the state to limit (MODE_LIMIT, FP64 rows in A.gs)
+    const double *srcs = MODE == MODE_LIMIT ? A.gs : A.gs;
+    const double *srcn = MODE == MODE_STAGE ? A.gn : srcs;
+    const size_t nN = (size_t)n_cells * N;
     const double dt = MODE == MODE_STAGE ? A.dt[cell] : 0.0;
     const float af = (float)A.a, bf = (float)A.b, dtf = MODE == MODE_STAGE ? d2f_fast(dt) : 0.f;
     double msum = 0.0;
     unsigned fl = 0u;
     for (int j = lane; j < N; j += LPC) {
-        const double *vs = gsr + (size_t)j * K1;
-        const double *vn = gnr + (size_t)j * K1;
-        double v0;
+        // inputs of bin j: means (FP64) and higher modes (FP32 values, FP64 for MODE_LIMIT)
+        double s0 = 0.0, n0 = 0.0;
+        float sf[kB], nf_[kB];
         double vd[kB];     // MODE_LIMIT: the FP64 higher modes
+        if (MODE != MODE_RHS) {
+            if (IN_MIX) {
+                s0 = srcs[cell * N + j];
+                n0 = srcn[cell * N + j];
+                const float *sh = reinterpret_cast<const float *>(srcs + nN) + ((size_t)cell * N + j) * k;
+                const float *nh = reinterpret_cast<const float *>(srcn + nN) + ((size_t)cell * N + j) * k;
+#pragma unroll
+                for (int i = 1; i < kB; ++i) {
+                    sf[i] = i <= k ? sh[i - 1] : 0.f;
+                    nf_[i] = i <= k ? nh[i - 1] : 0.f;
+                    vd[i] = f2d_fast(sf[i]);
+                }
+            } else {
+                const double *vs = srcs + (size_t)cell * P + (size_t)j * K1;
+                const double *vn = srcn + (size_t)cell * P + (size_t)j * K1;
+                s0 = vs[0];
+                n0 = vn[0];
+#pragma unroll
+                for (int i = 1; i < kB; ++i) {
+                    vd[i] = i <= k ? vs[i] : 0.0;
+                    sf[i] = d2f_fast(vd[i]);
+                    nf_[i] = i <= k ? d2f_fast(vn[i]) : 0.f;
+                }
+            }
+        }
+        double v0;
         float vf[kB];
         if (MODE == MODE_LIMIT) {
-            v0 = vs[0];
+            v0 = s0;
 #pragma unroll
-            for (int i = 1; i < kB; ++i) {
-                vd[i] = i <= k ? vs[i] : 0.0;
-                vf[i] = d2f_fast(vd[i]);
-            }
+            for (int i = 1; i < kB; ++i) vf[i] = sf[i];
         } else {
             const float Fm = j == 0 ? 0.f : F[j - 1];          // F(x_{j-1/2}), F(x_min) = 0
             const float Fp = j < G.n_if ? F[j] : 0.f;           // F(x_{j+1/2}), 0 at x_max (cons.)
             const double L0 = (f2d_fast(Fm) - f2d_fast(Fp)) * G.inv_h[j];
             if (MODE == MODE_STAGE) {
-                v0 = fma(A.a, vn[0], A.b * fma(dt, L0, vs[0]));
+                v0 = fma(A.a, n0, A.b * fma(dt, L0, s0));
             } else {
                 v0 = L0;
             }
@@ -236,7 +267,7 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
                 if (i <= k) {
                     const float V = F[G.n_if + j * k + i - 1];
                     const float L = (2.f * i + 1.f) * ih * (V - Fp + ((i & 1) ? -Fm : Fm));
-                    vf[i] = MODE == MODE_STAGE ? af * d2f_fast(vn[i]) + bf * (d2f_fast(vs[i]) + dtf * L) : L;
+                    vf[i] = MODE == MODE_STAGE ? af * nf_[i] + bf * (sf[i] + dtf * L) : L;
                 }
             }
         }
@@ -257,7 +288,9 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
                 float cf[kB];
 #pragma unroll
                 for (int i = 1; i < kB; ++i)
-                    cf[i] = i > k ? 0.f : (MODE == MODE_LIMIT ? d2f_scaled(vd[i], 1023 - e0) : scale_pow2(vf[i], 1023 - e0));
+                    cf[i] = i > k ? 0.f
+                                  : (MODE == MODE_LIMIT && !IN_MIX ? d2f_scaled(vd[i], 1023 - e0)
+                                                                   : scale_pow2(vf[i], 1023 - e0));
                 gam = limiter_gamma_scaled(v0, cf, k);
             }
             if (gam < 0.f) {
@@ -295,17 +328,26 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
                     }
                 }
             }
-            // MODE_LIMIT rewrites only the bins it changed (the rest of the state is untouched)
-            if (MODE == MODE_LIMIT && changed)
+            // MODE_LIMIT into the caller's FP64 rows rewrites only the bins it changed
+            if (MODE == MODE_LIMIT && !OUT_MIX && changed)
 #pragma unroll
                 for (int i = 1; i < kB; ++i)
                     if (i <= k) A.gout[(size_t)cell * P + (size_t)j * K1 + i] = vd[i];
         }
-        double *rj = row + j * K1;
-        rj[0] = v0;
+        if (OUT_MIX) {
+            // the compact layout: lane j writes its bin's mean and modes directly (coalesced)
+            A.gout[cell * N + j] = v0;
+            float *oh = reinterpret_cast<float *>(A.gout + nN) + ((size_t)cell * N + j) * k;
 #pragma unroll
-        for (int i = 1; i < kB; ++i)
-            if (i <= k) rj[i] = MODE == MODE_LIMIT ? vd[i] : f2d_fast(vf[i]);
+            for (int i = 1; i < kB; ++i)
+                if (i <= k) oh[i - 1] = vf[i];
+        } else if (MODE != MODE_LIMIT) {
+            double *rj = row + j * K1;
+            rj[0] = v0;
+#pragma unroll
+            for (int i = 1; i < kB; ++i)
+                if (i <= k) rj[i] = f2d_fast(vf[i]);
+        }
         if (A.opA) {
             const float h = G.h32[j];
             float *ar = arow + j * K1;
@@ -320,8 +362,8 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
     if (A.opA)
         for (int e = P + lane; e < lda; e += LPC) arow[e] = 0.f;
     __syncwarp(gmask);
-    // coalesced stores of the row (MODE_LIMIT has written its changed bins above)
-    if (MODE != MODE_LIMIT) {
+    // coalesced stores of an FP64 result row (the compact layout was written above)
+    if (MODE != MODE_LIMIT && !OUT_MIX) {
         double *go = A.gout + (size_t)cell * P;
         for (int e = lane; e < P; e += LPC) go[e] = row[e];
     }
@@ -422,30 +464,53 @@ static size_t update_tc_smem(const DevGroup &g, const UpdateArgs &a, int lpc)
     return cpb * (g.P + a.opA_kpad / 2 + 1) * sizeof(double) + cpb * (g.R + 1) * sizeof(float);
 }
 
-template <int MODE, int LPC>
+template <int MODE, int LPC, bool IN_MIX, bool OUT_MIX>
 static cudaError_t launch_update_lpc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
 {
     const size_t smem = update_tc_smem(g, a, LPC);
-    cudaError_t e = cudaFuncSetAttribute(update_tc_kernel<MODE, LPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(update_tc_kernel<MODE, LPC, IN_MIX, OUT_MIX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int per_block = kUpdWarps * 32 / LPC;
-    update_tc_kernel<MODE, LPC><<<(n_cells + per_block - 1) / per_block, 32 * kUpdWarps, smem, st>>>(g, a, n_cells);
+    update_tc_kernel<MODE, LPC, IN_MIX, OUT_MIX>
+        <<<(n_cells + per_block - 1) / per_block, 32 * kUpdWarps, smem, st>>>(g, a, n_cells);
     return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, bool IN_MIX, bool OUT_MIX>
 static cudaError_t launch_update_mode(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
 {
     // lanes per cell: the choice that leaves fewer lanes idle over the N bins
     const int idle16 = (g.N + 15) / 16 * 16 - g.N, idle32 = (g.N + 31) / 32 * 32 - g.N;
-    return idle16 <= idle32 ? launch_update_lpc<MODE, 16>(g, a, n_cells, st) : launch_update_lpc<MODE, 32>(g, a, n_cells, st);
+    return idle16 <= idle32 ? launch_update_lpc<MODE, 16, IN_MIX, OUT_MIX>(g, a, n_cells, st)
+                            : launch_update_lpc<MODE, 32, IN_MIX, OUT_MIX>(g, a, n_cells, st);
 }
 
 cudaError_t launch_update_tc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
 {
     if (n_cells <= 0) return cudaSuccess;
     if (!a.F32 || !a.gout) return cudaErrorInvalidValue;
-    return a.dt ? launch_update_mode<MODE_STAGE>(g, a, n_cells, st) : launch_update_mode<MODE_RHS>(g, a, n_cells, st);
+    if (!a.dt) return launch_update_mode<MODE_RHS, false, false>(g, a, n_cells, st);
+    if (a.in_mixed && a.out_mixed) return launch_update_mode<MODE_STAGE, true, true>(g, a, n_cells, st);
+    if (a.in_mixed) return launch_update_mode<MODE_STAGE, true, false>(g, a, n_cells, st);
+    if (a.out_mixed) return cudaErrorInvalidValue;
+    return launch_update_mode<MODE_STAGE, false, false>(g, a, n_cells, st);
+}
+
+cudaError_t launch_limit_pack(const DevGroup &g, const double *d_g, int n_cells, unsigned char *flags,
+                              double *mixed_out, void *opA, int opA_prec, int opA_kpad, cudaStream_t st)
+{
+    if (n_cells <= 0) return cudaSuccess;
+    UpdateArgs a;
+    a.gs = d_g;
+    a.gout = mixed_out;
+    a.apply_limiter = g.limiter;
+    a.flags = flags;
+    a.opA = opA;
+    a.opA_prec = opA_prec;
+    a.opA_kpad = opA_kpad;
+    a.out_mixed = 1;
+    return launch_update_mode<MODE_LIMIT, false, true>(g, a, n_cells, st);
 }
 
 cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned char *flags, void *opA,
@@ -455,13 +520,14 @@ cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned c
     if (opA) {
         // tensor path: limiter pre-test off the FP64 pipe, and the A operand
         UpdateArgs a;
+        a.gs = d_g;
         a.gout = d_g;
         a.apply_limiter = g.limiter;
         a.flags = flags;
         a.opA = opA;
         a.opA_prec = opA_prec;
         a.opA_kpad = opA_kpad;
-        return launch_update_mode<MODE_LIMIT>(g, a, n_cells, st);
+        return launch_update_mode<MODE_LIMIT, false, false>(g, a, n_cells, st);
     }
     limit_kernel<<<warp_blocks(n_cells), 256, (size_t)8 * g.P * sizeof(double), st>>>(g, d_g, n_cells, flags, opA,
                                                                                        opA_prec, opA_kpad);
@@ -489,11 +555,11 @@ cudaError_t launch_pack_A(const DevGroup &g, const double *d_g, int n_cells, voi
 {
     if (n_cells <= 0) return cudaSuccess;
     UpdateArgs a;
-    a.gout = const_cast<double *>(d_g);   // read only: MODE_LIMIT without the limiter writes no rows
+    a.gs = d_g;            // read only: MODE_LIMIT without the limiter writes no rows
     a.opA = opA;
     a.opA_prec = prec;
     a.opA_kpad = kpad;
-    return launch_update_mode<MODE_LIMIT>(g, a, n_cells, st);
+    return launch_update_mode<MODE_LIMIT, false, false>(g, a, n_cells, st);
 }
 
 }  // namespace grace

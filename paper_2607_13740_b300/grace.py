@@ -181,9 +181,10 @@ class Context:
 
     def tile_info(self, group: int = 0, precision: int = TF32) -> dict:
         """The tensor-core tile plan of a group (grace_tile_info)."""
-        a = (ctypes.c_longlong * 7)()
+        a = (ctypes.c_longlong * 8)()
         _check(load().grace_tile_info(self._h, group, precision, a), "grace_tile_info")
-        keys = ("n_tiles", "mma_per_tile", "mac_per_cell", "b_bytes", "pred_clk_per_tile", "max_n", "nnz_fold")
+        keys = ("n_tiles", "mma_per_tile", "mac_per_cell", "b_bytes", "pred_clk_per_tile", "max_n", "nnz_fold",
+                "folded")
         return dict(zip(keys, list(a)))
 
     def param_grad_setup(self, param_ids, group: int = 0, rel_step: float = 1e-5):

@@ -273,6 +273,65 @@ def run_disk(args):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args):
+    """Uneven batch: cells of many groups (N ~ U{16..80}, k ~ U{0..3}, constant or additive
+    kernel, per-cell rate scale) stepped together in the bf16x3 form, with and without CUDA-graph
+    replay of the per-group launches.  One JSON line."""
+    import torch
+    from paper_2607_13740_b300 import grace, workloads as W
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    n = args.cells if args.cells != 65536 else 100000
+    steps = args.steps or 3
+    specs, group, ic, dt_np = W.uneven_batch(n_cells=n)
+    t0 = time.time()
+    ctx = grace.Context(specs, local, precisions=(grace.FP64, grace.BF16X3))
+    setup_s = time.time() - t0
+    b = ctx.batch(n, group)
+    g0 = b.project(W.IC_EXP, ic)
+    dt = torch.as_tensor(dt_np, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    side = torch.cuda.Stream(device=dev)     # graph capture needs a non-default stream
+    for graph in (False, True):
+        b.set_graph(graph)
+        g = g0.clone()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            for _ in range(args.warmup):
+                b.step(g, dt, 1, grace.BF16X3)
+            evs = []
+            for s_ in range(steps):
+                flush.fill_(float(s_))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(side)
+                b.step(g, dt, 1, grace.BF16X3)
+                e1.record(side)
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(c) for a, c in evs)
+        res[graph] = {"ms_per_step": ms / steps, "cell_steps_per_s": n * steps / (ms / 1e3),
+                      "finite": bool(torch.isfinite(g).all().item())}
+    b.set_graph(False)
+    tiles = [ctx.tile_info(i, grace.BF16X3) for i in range(len(specs))]
+    line = {
+        "metric": "uneven-batch cell-steps/s (bf16x3, per-group launches)", "value": res[True]["cell_steps_per_s"],
+        "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": res[True]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+        "config": {"workload": f"uneven_{n}cells_{len(specs)}groups", "cells": n, "groups": len(specs),
+                   "N": "U{16..80}", "k": "U{0..3}", "kernels": "constant / additive", "precompute_s": setup_s,
+                   "l2": "256 MB buffer written between timed steps (outside the timed events)"},
+        "graph_replay": res[True], "direct_launches": res[False],
+        "tiles": {"mma_per_tile_min": min(t["mma_per_tile"] for t in tiles),
+                  "mma_per_tile_max": max(t["mma_per_tile"] for t in tiles),
+                  "max_n_hist": {str(k): sum(1 for t in tiles if t["max_n"] == k) for k in sorted({t["max_n"] for t in tiles})},
+                  "folded_groups": sum(t["folded"] for t in tiles)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -285,7 +344,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--forms", default=None,
                     help="comma-separated subset of fp64,tf32,bf16x3 to time (default: all built)")
-    ap.add_argument("--workload", default="additive", choices=["additive", "disk"],
+    ap.add_argument("--workload", default="additive", choices=["additive", "disk", "uneven"],
                     help="additive: the batched additive-kernel headline; disk: coagulation + fragmentation "
                          "with a per-cell turbulence strength (node-space path, FP64)")
     ap.add_argument("--order", type=int, default=2, help="disk workload: Legendre degree k (1..3)")
@@ -293,6 +352,9 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.workload == "disk":
         run_disk(args)
+        return
+    if args.workload == "uneven":
+        run_uneven(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -98,6 +98,7 @@ struct TcParams {
     int R;
     float *F;
     int slot_bytes;       // bytes of one ring slot
+    int kps;              // MMA k-steps per B copy
     int n_slots;          // ring depth
     int a_bufs;           // A tiles in shared memory (2: the next item's A loads during this one)
     int n_splits;
@@ -321,7 +322,7 @@ template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 {
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
-    constexpr int kps = PREC == GRACE_TF32 ? 4 : 2;   // MMA k-steps per B copy (32 KB at N = 256)
+    const int kps = P.kps;                             // MMA k-steps per B copy
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -912,11 +913,20 @@ static void choose_splits(const TcTiles &t, int n_cell_tiles, int n_sm, TcParams
 }
 
 template <int PREC>
-static cudaError_t launch_prec(TcParams P, cudaStream_t st)
+static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
 {
+    constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
     P.table_bytes = (int)((P.n_tiles * sizeof(TileDesc) + (size_t)P.R * sizeof(int) + 15) / 16 * 16);
     const size_t fixed = 1024 + (size_t)P.table_bytes + sizeof(Smem) + 64;
     const size_t a1 = (size_t)P.a_tile_bytes;
+    // 32 KB B copies at N = 256 (two issuers keep them in flight); for groups whose A tile leaves
+    // too little room, fewer k-steps per copy
+    P.kps = PREC == GRACE_TF32 ? 4 : 2;
+    for (;;) {
+        P.slot_bytes = (int)(((size_t)P.kps * max_rows * 32 * planes + 1023) / 1024 * 1024);
+        if (fixed + a1 + 2 * (size_t)P.slot_bytes <= (size_t)kSmemLimit || P.kps == 1) break;
+        P.kps /= 2;
+    }
     if (fixed + a1 + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
     // two A tiles when that still leaves a 4-deep B ring, else one
     P.a_bufs = fixed + 2 * a1 + 4 * (size_t)P.slot_bytes <= (size_t)kSmemLimit ? 2 : 1;
@@ -948,12 +958,11 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
     P.n_cell_tiles = (n_cells + kTileM - 1) / kTileM;
     P.R = g.R;
     P.F = d_F32;
-    P.slot_bytes = t.slot_bytes;
     P.err = d_err;
     int dev = 0;
     cudaGetDevice(&dev);
     choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
-    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32>(P, st) : launch_prec<GRACE_BF16X3>(P, st);
+    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32>(P, t.max_rows, st) : launch_prec<GRACE_BF16X3>(P, t.max_rows, st);
 }
 
 }  // namespace grace

@@ -26,8 +26,8 @@
 // (grace_tc_layout.cuh).  Both move with cp.async.bulk (no tensor map).
 //
 // Warp roles (persistent, one CTA per SM, work items round-robin):
-//   warps 0, 3    : bulk-copy producers (lane 0; warp 0 also the A tiles): B copies of up to
-//                   32 KB alternate between the two issuing threads
+//   warps 0, 3    : B bulk-copy producers (lane 0), copies alternating between the two issuers
+//   warp 2 lane 0 : A-tile loader (after allocating TMEM)
 //   warp 1 lane 0 : MMA issuer (kind::tf32, or kind::f16 with bf16 hi/lo x3)
 //   warp 2        : TMEM allocation / release (2 accumulators x 256 columns)
 //   warps 4..19   : epilogue; TMEM lane quadrant = warp % 4, four warps per quadrant
@@ -377,32 +377,40 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
     tc_fence_after();
     const uint32_t tmem = S->tmem_base;
 
-    if (warp == 0 || warp == 3) {
-        // ------------------------------------------------ producers: warp 0 loads the A tiles and the
-        // even-numbered B copies, warp 3 the odd ones (each issuing thread retires about one bulk copy
-        // at a time, so two issuers keep twice as many copies in flight)
-        const int me = warp == 0 ? 0 : 1;
-        int q = 0, ctl = 0;
+    if (warp == 2) {
+        // ------------------------------------------------ A loader (after the TMEM allocation): the
+        // next work item's A tile as soon as the previous use of that buffer is released
+        int ctl = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
             const int sp = it / P.n_cell_tiles, ct = it - sp * P.n_cell_tiles;
+            (void)sp;
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             int ok = 1;
             if (lane == 0) {
                 if (*abort_flag) ok = 0;
-                else if (me == 0) {
-                    if (au > 0 && !mbar_wait(smem_u32(&S->a_empty[ab]), (au - 1) & 1, abort_flag)) {
-                        fail(P, abort_flag, 1);
-                        ok = 0;
-                    }
-                    if (ok) {
-                        mbar_expect_tx(smem_u32(&S->a_full[ab]), (uint32_t)P.a_tile_bytes);
-                        bulk_g2s(a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes, P.A + (size_t)ct * P.a_tile_bytes,
-                                 (uint32_t)P.a_tile_bytes, smem_u32(&S->a_full[ab]));
-                        S->a_issued[ab] = au + 1;
-                    }
+                else if (au > 0 && !mbar_wait(smem_u32(&S->a_empty[ab]), (au - 1) & 1, abort_flag)) {
+                    fail(P, abort_flag, 1);
+                    ok = 0;
+                }
+                if (ok) {
+                    mbar_expect_tx(smem_u32(&S->a_full[ab]), (uint32_t)P.a_tile_bytes);
+                    bulk_g2s(a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes, P.A + (size_t)ct * P.a_tile_bytes,
+                             (uint32_t)P.a_tile_bytes, smem_u32(&S->a_full[ab]));
+                    S->a_issued[ab] = au + 1;
                 }
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+        }
+    } else if (warp == 0 || warp == 3) {
+        // ------------------------------------------------ B producers: copy q is issued by warp 0
+        // (q even) or warp 3 (q odd); each issuing thread retires about one bulk copy at a time, so
+        // two issuers keep twice as many copies in flight.  The B stream runs ahead across work-item
+        // boundaries, limited only by the ring.
+        const int me = warp == 0 ? 0 : 1;
+        int q = 0;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+            const int sp = it / P.n_cell_tiles;
+            int ok = *abort_flag ? 0 : 1;
             for (int t = P.split[sp]; t < P.split[sp + 1] && ok; ++t) {
                 const TileDesc td = tiles[t];
                 const int nks = td.ks_hi - td.ks_lo, n_copies = (nks + kps - 1) / kps;
@@ -919,16 +927,15 @@ static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
     P.table_bytes = (int)((P.n_tiles * sizeof(TileDesc) + (size_t)P.R * sizeof(int) + 15) / 16 * 16);
     const size_t fixed = 1024 + (size_t)P.table_bytes + sizeof(Smem) + 64;
     const size_t a1 = (size_t)P.a_tile_bytes;
-    // 32 KB B copies at N = 256 (two issuers keep them in flight); for groups whose A tile leaves
-    // too little room, fewer k-steps per copy
+    // Shared-memory plan: 32 KB B copies at N = 256 (fewer k-steps per copy for groups whose A tile
+    // leaves less room); two A tiles (the next work item's A loads during this one) when that still
+    // leaves a 4-deep B ring, else one.  Measured on the 65,536-cell workload: two A tiles with 16 KB
+    // copies are slower than one A tile with 32 KB copies.
+    auto slot_of = [&](int kps) { return (int)(((size_t)kps * max_rows * 32 * planes + 1023) / 1024 * 1024); };
     P.kps = PREC == GRACE_TF32 ? 4 : 2;
-    for (;;) {
-        P.slot_bytes = (int)(((size_t)P.kps * max_rows * 32 * planes + 1023) / 1024 * 1024);
-        if (fixed + a1 + 2 * (size_t)P.slot_bytes <= (size_t)kSmemLimit || P.kps == 1) break;
-        P.kps /= 2;
-    }
+    while (P.kps > 1 && fixed + a1 + 2 * (size_t)slot_of(P.kps) > (size_t)kSmemLimit) P.kps /= 2;
+    P.slot_bytes = slot_of(P.kps);
     if (fixed + a1 + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
-    // two A tiles when that still leaves a 4-deep B ring, else one
     P.a_bufs = fixed + 2 * a1 + 4 * (size_t)P.slot_bytes <= (size_t)kSmemLimit ? 2 : 1;
     P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed - P.a_bufs * a1) / P.slot_bytes);
     const size_t smem = fixed + P.a_bufs * a1 + (size_t)P.n_slots * P.slot_bytes;

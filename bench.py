@@ -199,24 +199,27 @@ def run_reference(args, rank):
 
 
 def run_disk(args):
-    """Disk workload (per-cell alpha_turb, coagulation + fragmentation, N = 60): a bounded
-    number of cells through the FP64 node-space path; one JSON line like the headline's."""
+    """Disk workload (per-cell alpha_turb, coagulation + fragmentation, N = 60): the node-space
+    path in FP64 (a bounded 2,048 cells) or in a tensor-core form (65,536 cells by default:
+    fixed pairs on tcgen05, partial entries in FP32); one JSON line like the headline's."""
     import torch
     from paper_2607_13740_b300 import grace, workloads as W
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
-    n = args.cells if args.cells != 65536 else 2048
-    steps = args.steps or 3
+    form = {"fp64": grace.FP64, "tf32": grace.TF32, "bf16x3": grace.BF16X3}[args.precision or "bf16x3"]
+    fname = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[form]
+    n = args.cells if args.cells != 65536 or form != grace.FP64 else 2048
+    steps = args.steps or (3 if form == grace.FP64 else 10)
     spec, alpha, ic = W.disk_batch(n_cells=n, order_k=args.order)
     t0 = time.time()
-    ctx = grace.Context([spec], local)
+    ctx = grace.Context([spec], local, precisions=(grace.FP64, form) if form != grace.FP64 else (grace.FP64,))
     setup_s = time.time() - t0
     b = ctx.batch(n)
     b.cell_params(alpha)
     g0 = b.project(W.IC_POWERLAW, ic)
     # time step: half the positivity bound min_j g_j^0 / |L_j^0| at t = 0, held fixed
-    L = b.rhs(g0).reshape(n, spec.n_bins, spec.order_k + 1)[:, :, 0]
+    L = b.rhs(g0, form).reshape(n, spec.n_bins, spec.order_k + 1)[:, :, 0]
     m = g0.reshape(n, spec.n_bins, spec.order_k + 1)[:, :, 0]
     ratio = torch.where(L < 0, m / (-L), torch.full_like(m, float("inf")))
     dt = 0.5 * ratio.amin(dim=1)
@@ -224,11 +227,11 @@ def run_disk(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     g = g0.clone()
     for _ in range(args.warmup):
-        b.step(g, dt, 1, grace.FP64)
+        b.step(g, dt, 1, form)
     torch.cuda.synchronize()
     ctx.profile(True)
-    ctx.profile_read(0)
-    ctx.profile_read(1)
+    for kk in range(3):
+        ctx.profile_read(kk)
     sampler = ClockSampler(local)
     sampler.__enter__()
     evs = []
@@ -237,7 +240,7 @@ def run_disk(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        b.step(g, dt, 1, grace.FP64)
+        b.step(g, dt, 1, form)
         e1.record()
         evs.append((e0, e1))
     torch.cuda.synchronize()
@@ -245,29 +248,58 @@ def run_disk(args):
     ms = sum(a.elapsed_time(c) for a, c in evs)
     c_ms, c_n = ctx.profile_read(0)
     u_ms, u_n = ctx.profile_read(1)
+    x_ms, _ = ctx.profile_read(2)
     ctx.profile(False)
-    macs, _ = ctx.stats(0, grace.FP64)          # multiply-adds of one RHS per cell (node-space path)
     avg = c_ms / max(1, c_n)
-    achieved = 2.0 * macs * n / (avg / 1e3) / 1e12
-    try:
-        peak, psrc = 2.0 * grace.probe_rates(local)["fp64_fma_per_s"] / 1e12, "measured FP64 FMA rate x 2"
-    except Exception:
-        peak, psrc = NOMINAL_FP64_TFLOPS, "nominal FP64 rate"
+    peaks = load_peaks()
+    if form == grace.FP64:
+        macs, _ = ctx.stats(0, grace.FP64)          # multiply-adds of one RHS per cell (node-space path)
+        achieved = 2.0 * macs * n / (avg / 1e3) / 1e12
+        try:
+            peak, psrc = 2.0 * grace.probe_rates(local)["fp64_fma_per_s"] / 1e12, "measured FP64 FMA rate x 2"
+        except Exception:
+            peak, psrc = NOMINAL_FP64_TFLOPS, "nominal FP64 rate"
+        bound, kname = "alu", "node-space flux functionals (FP64)"
+        alg = f"2 x {macs} multiply-adds per cell and RHS x {n} cells"
+    else:
+        tinfo = ctx.tile_info(0, form)
+        passes = 3 if form == grace.BF16X3 else 1
+        nz = tinfo["nnz_fold"]                      # non-zeros of the two fixed-pair tables
+        achieved = 2.0 * nz * passes * n / (avg / 1e3) / 1e12
+        if form == grace.TF32:
+            peak = peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16
+            psrc = f"{peaks['source']} sustained bf16 x nominal tf32/bf16 ratio"
+        else:
+            peak, psrc = peaks["bf16_tflops_sustained"], f"{peaks['source']} sustained bf16"
+        bound, kname = "tensor", "contract_tc_kernel (node-space tiles)"
+        alg = f"2 x {nz} fixed-pair multiply-adds x {passes} MMA passes per cell and RHS x {n} cells"
     m0 = b.mass(g0)
     drift = ((b.mass(g) - m0).abs() / m0.abs()).max().item()
+    acc = None
+    if form != grace.FP64:
+        # accuracy of one RHS against the FP64 GPU path on the first 512 cells
+        na = min(n, 512)
+        bs = ctx.batch(na)
+        bs.cell_params(alpha[:na])
+        gs = g0.reshape(n, -1)[:na].reshape(-1).clone()
+        L64 = bs.rhs(gs).reshape(na, -1)
+        Lt = bs.rhs(gs, form).reshape(na, -1)
+        acc = ((Lt - L64).abs().amax(dim=1) / L64.abs().amax(dim=1)).max().item()
     line = {
         "metric": "disk workload cell-steps/s (N=60, per-cell alpha, coag+frag)", "value": n * steps / (ms / 1e3),
         "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[fname], "data": "synthetic",
         "config": {"workload": f"disk_{n}cells_N60_k{args.order}", "cells": n, "n_bins": 60, "order_k": args.order,
-                   "alpha": "loguniform[1e-4, 1e-2] per cell", "ic": "MRN a^-3.5 over 1-10 um",
+                   "form": fname, "alpha": "loguniform[1e-4, 1e-2] per cell", "ic": "MRN a^-3.5 over 1-10 um",
                    "dt": "0.5 x positivity bound at t=0", "precompute_s": setup_s,
                    "l2": "256 MB buffer written between timed steps (outside the timed events)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "node-space flux functionals",
-                     "algorithmic": f"2 x {macs} multiply-adds per cell and RHS x {n} cells", "peak_source": psrc},
-        "functionals_ms_avg": avg, "update_ms_avg": u_ms / max(1, u_n), "mass_drift": drift,
-        "finite": bool(torch.isfinite(g).all().item()),
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": kname, "algorithmic": alg,
+                     "peak_source": psrc},
+        "functionals_ms_avg": avg, "update_ms_avg": u_ms / max(1, u_n),
+        "pack_and_partial_ms_per_stage": x_ms / max(1, c_n), "mass_drift": drift,
+        "max_rel_err_vs_fp64_rhs": acc, "finite": bool(torch.isfinite(g).all().item()),
         "clocks": sampler.summary(),
     }
     print(json.dumps(line), flush=True)

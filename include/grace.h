@@ -217,7 +217,9 @@ GRACE_API grace_status grace_adjoint(grace_batch *batch, const double *g0, const
                                      int precision);
 
 /* Launch timing with CUDA events recorded on the bound stream around every
-   contraction (kernel 0) and flux-update (kernel 1) launch of this context.
+   contraction (kernel 0) and flux-update (kernel 1) launch of this context;
+   kernel 2 covers the per-cell-kernel pieces of the reduced-precision forms
+   around their contraction (node values, FP32 partial entries).
    grace_profile_read synchronises the stream, returns the summed device time
    in milliseconds and the launch count since the last read, and resets them. */
 GRACE_API grace_status grace_profile_enable(grace_ctx *ctx, int enable);

@@ -281,7 +281,7 @@ grace_status grace_precompute(grace_ctx *ctx, unsigned mask)
         for (Group &G : ctx->groups) {
             const DevGroup &g = G.dg;
             if (g.cell_alpha) {
-                // per-cell kernel: no fixed T exists; node-space tables (FP64 path only).
+                // per-cell kernel: no fixed T exists; node-space tables.
                 // nnz reports the multiply-adds of one RHS per cell: the non-zeros of the
                 // two tables plus 2 (k+1) + 2 per partial entry
                 if (!G.nc.built) {
@@ -301,6 +301,13 @@ grace_status grace_precompute(grace_ctx *ctx, unsigned mask)
                     cudaFree(d_cnt);
                     if (e != cudaSuccess) return cuda_fail(e, "grace_precompute: node-space tables");
                     G.nnz = (long long)cnt + G.nc.n_entries * (2LL * g.K1 + 2);
+                }
+                // reduced-precision forms: tensor-core tiles of the fixed part, FP32 partial entries
+                for (int prec = GRACE_TF32; prec <= GRACE_BF16X3; ++prec) {
+                    if (!(mask & (1u << prec)) || G.tc[prec].built) continue;
+                    grace_status s = build_nc_tc_entries(G, st);
+                    if (s == GRACE_OK) s = build_nc_tc_tiles(G, prec, st);
+                    if (s != GRACE_OK) return s;
                 }
                 continue;
             }
@@ -373,7 +380,7 @@ grace_status grace_profile_enable(grace_ctx *ctx, int enable)
 
 grace_status grace_profile_read(grace_ctx *ctx, int kernel, double *total_ms, long long *launches)
 {
-    if (!ctx || kernel < 0 || kernel > 1) {
+    if (!ctx || kernel < 0 || kernel > 2) {
         set_error("grace_profile_read: bad context or kernel index");
         return GRACE_ERR_ARG;
     }
@@ -390,7 +397,7 @@ grace_status grace_profile_read(grace_ctx *ctx, int kernel, double *total_ms, lo
     if (total_ms) *total_ms = tot;
     if (launches) *launches = (long long)ctx->ev_pairs[kernel].size();
     ctx->ev_pairs[kernel].clear();
-    if (ctx->ev_pairs[0].empty() && ctx->ev_pairs[1].empty()) ctx->ev_used = 0;
+    if (ctx->ev_pairs[0].empty() && ctx->ev_pairs[1].empty() && ctx->ev_pairs[2].empty()) ctx->ev_used = 0;
     return GRACE_OK;
 }
 

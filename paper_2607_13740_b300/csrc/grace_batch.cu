@@ -73,6 +73,8 @@ void free_part(Part &p)
     cudaFree(p.d_alpha);
     cudaFree(p.d_G);
     cudaFree(p.d_H);
+    cudaFree(p.d_gh);
+    cudaFree(p.d_s);
     if (p.stream) cudaStreamDestroy(p.stream);
     if (p.done) cudaEventDestroy(p.done);
     p = Part();
@@ -85,16 +87,9 @@ grace_status check_prec(grace_batch *b, int prec)
         return GRACE_ERR_ARG;
     }
     for (const Part &p : b->parts) {
-        if (b->ctx->groups[p.group].dg.cell_alpha) {
-            if (prec != GRACE_FP64) {
-                set_error("groups with a per-cell kernel parameter run in GRACE_FP64 only");
-                return GRACE_ERR_UNSUPPORTED;
-            }
-            if (!b->alpha_set) {
-                set_error("per-cell kernel parameters not set: call grace_batch_cell_params first");
-                return GRACE_ERR_ORDER;
-            }
-            continue;
+        if (b->ctx->groups[p.group].dg.cell_alpha && !b->alpha_set) {
+            set_error("per-cell kernel parameters not set: call grace_batch_cell_params first");
+            return GRACE_ERR_ORDER;
         }
         if (prec != GRACE_FP64 && !b->ctx->groups[p.group].tc[prec].built) {
             set_error("precision not precomputed: pass its bit to grace_precompute before binding the batch");
@@ -109,15 +104,36 @@ grace_status check_prec(grace_batch *b, int prec)
 }
 
 // ------------------------------------------------------------------ per-part compute
+// flux functionals of a per-cell kernel group in a reduced-precision form, into p.d_F32
+cudaError_t nc_tc_functionals(grace_batch *b, Group &G, Part &p, int prec, const double *g, cudaStream_t st)
+{
+    const TcTiles &t = G.tc[prec];
+    cudaError_t e;
+    {
+        LaunchTimer timer(b->ctx, 2, st);
+        e = launch_nc_pack_tc(G.dg, t, prec, g, p.d_alpha, p.n, p.d_opA, p.d_gh, p.d_s, st);
+    }
+    if (e != cudaSuccess) return e;
+    {
+        LaunchTimer timer(b->ctx, 0, st);
+        e = launch_contract_tc(G.dg, t, prec, p.d_opA, p.n, p.d_F32, b->d_err, st, p.d_s);
+    }
+    if (e != cudaSuccess) return e;
+    LaunchTimer timer(b->ctx, 2, st);
+    return launch_nc_partial_tc(G.dg, G.nc, t, p.n, p.d_gh, p.d_s, p.d_F32, st);
+}
+
 cudaError_t part_rhs(grace_batch *b, Part &p, const double *g, double *L, int prec)
 {
     Group &G = b->ctx->groups[p.group];
     cudaStream_t st = part_stream(b, p);
     cudaError_t e;
     if (prec != GRACE_FP64) {
-        e = launch_pack_A(G.dg, g, p.n, p.d_opA, prec, G.tc[prec].k_pad, st);
-        if (e != cudaSuccess) return e;
-        {
+        if (G.dg.cell_alpha) {
+            e = nc_tc_functionals(b, G, p, prec, g, st);
+        } else {
+            e = launch_pack_A(G.dg, g, p.n, p.d_opA, prec, G.tc[prec].k_pad, st);
+            if (e != cudaSuccess) return e;
             LaunchTimer timer(b->ctx, 0, st);
             e = launch_contract_tc(G.dg, G.tc[prec], prec, p.d_opA, p.n, p.d_F32, b->d_err, st);
         }
@@ -157,6 +173,40 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
     if (n_steps == 0) return mass ? launch_mass(dg, g, n, mass, st) : cudaSuccess;
     static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
     static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    if (tc && dg.cell_alpha) {
+        // Per-cell kernels, reduced-precision forms: FP64 stage rows (the contraction dominates,
+        // so the compact layout buys nothing here); functionals from nc_tc_functionals, FP32 K-c.
+        if (dg.limiter) {
+            e = launch_limit(dg, g, n, flags, nullptr, 0, 0, st);
+            if (e != cudaSuccess) return e;
+        }
+        for (int step = 0; step < n_steps; ++step) {
+            const bool last = step == n_steps - 1;
+            const double *gin[3] = {g, p.d_g1, p.d_g2};
+            double *gout[3] = {p.d_g1, p.d_g2, g};
+            for (int stage = 0; stage < 3; ++stage) {
+                e = nc_tc_functionals(b, G, p, prec, gin[stage], st);
+                if (e != cudaSuccess) return e;
+                UpdateArgs u;
+                u.F32 = p.d_F32;
+                u.gn = g;
+                u.gs = gin[stage];
+                u.gout = gout[stage];
+                u.dt = dt;
+                u.a = ca[stage];
+                u.b = cb[stage];
+                u.flags = flags;
+                if (stage == 2) {
+                    u.apply_limiter = (!last && dg.limiter) ? 1 : 0;
+                    u.mass = last ? mass : nullptr;
+                }
+                LaunchTimer timer(b->ctx, 1, st);
+                e = launch_update_tc(dg, u, n, st);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    }
     if (tc) {
         // Tensor path.  Inside the call the state lives in the compact stage layout (FP64
         // means, FP32 higher modes): X[0] = g^n, X[1] = g^(1), X[2] = g^(2).  The step-start
@@ -367,6 +417,12 @@ grace_status grace_bind_batch(grace_ctx *ctx, int n_cells, const int *cell_group
                 if (e == cudaSuccess) e = cudaMalloc(&p.d_mx, 3 * ((mixed_bytes_for(g, (int)n) + 15) / 16 * 16));
                 if (e == cudaSuccess) e = cudaMemset(p.d_opA, 0, bytes);
                 p.opA_bytes = bytes;
+                if (e == cudaSuccess && g.cell_alpha) {
+                    const size_t tiles = (n + kTileM - 1) / kTileM;
+                    e = cudaMalloc(&p.d_gh, tiles * g.P * kTileM * sizeof(float));
+                    if (e == cudaSuccess) e = cudaMemset(p.d_gh, 0, tiles * g.P * kTileM * sizeof(float));
+                    if (e == cudaSuccess) e = cudaMalloc(&p.d_s, n * sizeof(float));
+                }
             }
         }
         if (e != cudaSuccess) {

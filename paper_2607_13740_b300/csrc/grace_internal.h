@@ -47,6 +47,12 @@ struct TcTiles {
     double pred_clk = 0.0;         // cost-model SM cycles per 128-cell tile and RHS
     std::vector<int> group_tile;   // first tile of every functional group (+ end)
     std::vector<double> group_cost;   // cost-model cycles of every group
+    // node-space tiles of a per-cell kernel group: the epilogue applies the fragmentation ramp
+    int nc = 0;
+    float *d_D0 = nullptr;         // [n_d0] D0 of every fixed node (0 past the last one)
+    int n_d0 = 0;
+    float ramp_a = 0.f, ramp_b = 0.f;   // pf(z) = clamp(ramp_a z + ramp_b, 0, 1), z = s D0
+    int *d_written = nullptr;      // [R] 1 where the contraction writes the functional
 };
 
 // Node-space tables of a group with a per-cell kernel parameter (grace_ncell.cu)
@@ -58,6 +64,9 @@ struct NcTables {
     int *d_qlo = nullptr, *d_qhi = nullptr;   // [R*NQ] non-zero column range of each row
     double *d_D0 = nullptr;       // [NQ] D0 of each fixed node
     void *d_entries = nullptr;    // partial-pair entries, grouped by functional
+    void *d_entf = nullptr;       // FP32 entries of the reduced-precision forms (coag/frag pairs merged)
+    long long *d_segf = nullptr;  // [R+1] their ranges per functional
+    long long n_entf = 0;
     long long *d_seg = nullptr;   // [R+1] entry ranges per functional
     long long n_entries = 0;
 };
@@ -96,7 +105,7 @@ struct grace_ctx {
     // launch timing (grace_profile_enable)
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pairs[2];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pairs[3];
     size_t ev_used = 0;
     int capturing = 0;              // a CUDA graph capture is in progress
 };
@@ -126,6 +135,8 @@ struct Part {
     void *d_opA = nullptr;         // tensor-core A operand of the current stage
     double *d_alpha = nullptr;     // [n] per-cell alpha_turb (cell_alpha groups)
     double *d_G = nullptr, *d_H = nullptr;   // [n][NQ], [2][n][NQ] nodal values (cell_alpha groups)
+    float *d_gh = nullptr;         // [tiles][P][128] scaled coefficients (cell_alpha groups, tensor forms)
+    float *d_s = nullptr;          // [n] sqrt(alpha) in FP32 (cell_alpha groups, tensor forms)
     size_t opA_bytes = 0;
     cudaStream_t stream = nullptr; // own stream for concurrent parts (null: the context's)
     cudaEvent_t done = nullptr;
@@ -206,9 +217,10 @@ struct UpdateArgs {
 };
 cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st);
 // tcgen05 contraction: the flux functionals of every cell into d_F32 laid out as
-// [128-cell tile][functional][row of the tile]
+// [128-cell tile][functional][row of the tile]; node-space tiles (t.nc) also need the
+// per-cell s = sqrt(alpha) in FP32 (d_cell_s)
 cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, int n_cells,
-                               float *d_F32, int *d_err, cudaStream_t st);
+                               float *d_F32, int *d_err, cudaStream_t st, const float *d_cell_s = nullptr);
 // K-c for the tensor path: reads d_F32 in the tile layout above
 cudaError_t launch_update_tc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st);
 size_t f32_bytes_for(const DevGroup &g, int n_cells);
@@ -273,9 +285,18 @@ grace_status build_nc_tables(Group &G, cudaStream_t st);
 void free_nc_tables(NcTables &t);
 cudaError_t launch_nc_functionals(const DevGroup &g, const NcTables &t, const double *d_g, const double *d_alpha,
                                   int n_cells, double *d_G, double *d_H, double *d_F, cudaStream_t st);
+// reduced-precision forms: FP32 partial entries (built once); per RHS the node values -> A
+// operand (+ FP32 scaled coefficients, s per cell), the tcgen05 fixed part (launch_contract_tc
+// with d_cell_s), then the FP32 partial part added into d_F32 ([tile][functional][row])
+grace_status build_nc_tc_entries(Group &G, cudaStream_t st);
+cudaError_t launch_nc_pack_tc(const DevGroup &g, const TcTiles &t, int prec, const double *d_g, const double *d_alpha,
+                              int n_cells, void *opA, float *d_gh, float *d_s, cudaStream_t st);
+cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const TcTiles &t, int n_cells,
+                                 const float *d_gh, const float *d_s, float *d_F32, cudaStream_t st);
 
 // tensor-core path
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);
+grace_status build_nc_tc_tiles(Group &G, int prec, cudaStream_t st);
 void free_tc_tiles(TcTiles &t);
 size_t opA_bytes_for(const DevGroup &g, int prec, int n_cells, int *kpad);
 

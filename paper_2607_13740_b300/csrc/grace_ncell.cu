@@ -27,11 +27,19 @@
 // Both are built once per setup on the device in FP64 by the same quadrature
 // walk as the T build (grace_precompute.cu); each RHS then costs a bilinear
 // contraction in node space plus one cheap kernel factor per partial entry.
+//
+// Reduced-precision forms (TF32 / BF16x3): the fixed part runs on the tensor cores
+// (grace_tc.cu, node-space tiles: the MMA contracts over the smaller node, the
+// epilogue applies the ramp of the larger node), the partial entries in FP32 on
+// the CUDA cores, both on bin-mass-scaled values (Ghat = h_bin G) so that the
+// operands stay inside the FP32 range.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "grace_convert.cuh"
 #include "grace_physics.cuh"
+#include "grace_tc_layout.cuh"
 
 namespace grace {
 
@@ -48,6 +56,17 @@ struct NcEntry {
     double pu[kB], pv[kB];   // phi_i at u and v
 };
 static_assert(sizeof(NcEntry) == 96, "NcEntry layout");
+
+// FP32 entry of the reduced-precision forms.  A coagulation entry and the fragmentation entry of
+// the same node pair are merged: the pair contributes (wc + wd pf) u v with wc the coagulation
+// weight and wd = w_frag - w_coag, both divided by h_bu h_bv (to be used with the
+// bin-mass-scaled coefficients h_bin g).
+struct NcEntryF {
+    int bins;              // bu | bv << 16
+    float wc, wd, D0;
+    float pu[kB], pv[kB];
+};
+static_assert(sizeof(NcEntryF) == 48, "NcEntryF layout");
 
 struct NcBuild {
     double *Bc, *Bf;            // [R][NQ][NQ] fixed-pair weights (dense)
@@ -401,7 +420,256 @@ __global__ void __launch_bounds__(128) nc_partial_kernel(DevGroup G, const NcEnt
     if (live) F[cell * G.R + r] += s * acc;
 }
 
+// ---------------------------------------------------------------- reduced-precision forms
+// Per cell tile and bin (block = (tile, bin), thread = row): the scaled coefficients
+// h_l g_{l,i} in FP32 into gh ([tile][P][128]), the node values Ghat_a = sum_i h_l g_{l,i} phi_i(s_alpha)
+// (node a = l Q + alpha) into the A operand, and s = sqrt(alpha_turb) per cell.
+struct NodeRuleF {
+    float phi[kQMax * kB];
+};
+
+__global__ void __launch_bounds__(128) nc_pack_tc_kernel(DevGroup G, NodeRuleF rule, const double *__restrict__ g,
+                                                         const double *__restrict__ alpha, int n_cells, void *opA,
+                                                         int prec, int kpad, float *__restrict__ gh,
+                                                         float *__restrict__ cell_s)
+{
+    const int l = blockIdx.x % G.N;
+    const long long ct = blockIdx.x / G.N;
+    const int row = threadIdx.x;
+    const long long cell = ct * kTileM + row;
+    if (cell >= n_cells) return;
+    const double h = G.hbin[l];
+    const double *gb = g + (size_t)cell * G.P + (size_t)l * G.K1;
+    float c[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+        c[i] = i <= G.k ? d2f_fast(h * gb[i]) : 0.f;
+        if (i <= G.k) gh[((size_t)ct * G.P + (size_t)l * G.K1 + i) * kTileM + row] = c[i];
+    }
+    char *t = (char *)opA + (size_t)ct * opA_tile_bytes(prec, kpad);
+    for (int al = 0; al < G.Q; ++al) {
+        float v = 0.f;
+#pragma unroll
+        for (int i = 0; i < kB; ++i) v = fmaf(c[i], rule.phi[al * kB + i], v);
+        const int col = l * G.Q + al;
+        if (prec == GRACE_TF32) {
+            *(uint32_t *)(t + swz_offset(kTileM, row, col, 4)) = f32_to_tf32_rna(v);
+        } else {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            const size_t plane = (size_t)kTileM * kpad * 2;
+            *(__nv_bfloat16 *)(t + swz_offset(kTileM, row, col, 2)) = hi;
+            *(__nv_bfloat16 *)(t + plane + swz_offset(kTileM, row, col, 2)) = lo;
+        }
+    }
+    if (l == 0) cell_s[cell] = sqrtf(d2f_fast(alpha[cell]));
+}
+
+// Partial entries of functional r (blockIdx.y) in FP32, added to the contraction's output
+// ([tile][functional][row]); functionals the contraction does not write are overwritten.  A block
+// covers C cell tiles: thread t handles row t of each (C cells), so every entry, staged through
+// shared memory, is read once per C cells (the broadcast loads, not the arithmetic, bound a
+// thread-per-cell loop).  Entries come sorted by (bin of u, bin of v); a thread reloads its cells'
+// two bins of coefficients only when that pair changes (coalesced: gh is cell-minor).
+template <int K1, int C>
+__global__ void __launch_bounds__(128) nc_partial_f32_kernel(int P, int R, const NcEntryF *__restrict__ entries,
+                                                             const long long *__restrict__ seg,
+                                                             const float *__restrict__ gh,
+                                                             const float *__restrict__ cell_s,
+                                                             const int *__restrict__ written, float ra, float rb,
+                                                             int n_cells, float *__restrict__ F32)
+{
+    constexpr int kChunk = 128;
+    __shared__ float4 es[kChunk * 3];
+    const int r = blockIdx.y, row = threadIdx.x;
+    const long long ct0 = (long long)blockIdx.x * C;
+    float s[C], acc[C], gu[C][K1], gv[C][K1];
+    const float *gc[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const long long cell = (ct0 + j) * kTileM + row;
+        s[j] = cell < n_cells ? cell_s[cell] : 0.f;   // 0 for rows past the batch: they add nothing
+        acc[j] = 0.f;
+        gc[j] = gh + (size_t)min(ct0 + j, (long long)(n_cells - 1) / kTileM) * P * kTileM + row;
+#pragma unroll
+        for (int i = 0; i < K1; ++i) gu[j][i] = gv[j][i] = 0.f;
+    }
+    const long long e0 = seg[r], e1 = seg[r + 1];
+    int cur = -1;
+    for (long long c0 = e0; c0 < e1; c0 += kChunk) {
+        const int n = (int)min((long long)kChunk, e1 - c0);
+        __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(entries + c0);
+        for (int w = threadIdx.x; w < n * 3; w += blockDim.x) es[w] = src[w];
+        __syncthreads();
+        for (int t = 0; t < n; ++t) {
+            const float4 a = es[3 * t], pu = es[3 * t + 1], pv = es[3 * t + 2];
+            const int bins = __float_as_int(a.x);
+            if (bins != cur) {
+                cur = bins;
+                const size_t ou = (size_t)(bins & 0xFFFF) * K1 * kTileM, ov = (size_t)(bins >> 16) * K1 * kTileM;
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+#pragma unroll
+                    for (int i = 0; i < K1; ++i) {
+                        gu[j][i] = gc[j][ou + i * kTileM];
+                        gv[j][i] = gc[j][ov + i * kTileM];
+                    }
+            }
+            const float pa[4] = {pu.x, pu.y, pu.z, pu.w}, pb[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                float u = gu[j][0] * pa[0], v = gv[j][0] * pb[0];
+#pragma unroll
+                for (int i = 1; i < K1; ++i) {
+                    u = fmaf(gu[j][i], pa[i], u);
+                    v = fmaf(gv[j][i], pb[i], v);
+                }
+                const float pf = fminf(fmaxf(fmaf(s[j] * a.w, ra, rb), 0.f), 1.f);
+                acc[j] = fmaf(fmaf(a.z, pf, a.y), u * v, acc[j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const long long ct = ct0 + j, cell = ct * kTileM + row;
+        if (cell < n_cells) {
+            float *Fo = F32 + ((size_t)ct * R + r) * kTileM + row;
+            *Fo = (written[r] ? *Fo : 0.f) + s[j] * acc[j];
+        }
+    }
+}
+
 }  // namespace
+
+grace_status build_nc_tc_entries(Group &Gr, cudaStream_t st)
+{
+    NcTables &T = Gr.nc;
+    if (T.d_entf) return GRACE_OK;
+    const int R = Gr.dg.R;
+    std::vector<NcEntry> in((size_t)T.n_entries);
+    std::vector<long long> seg(R + 1);
+    cudaError_t e = cudaSuccess;
+    if (T.n_entries > 0)
+        e = cudaMemcpyAsync(in.data(), T.d_entries, in.size() * sizeof(NcEntry), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(seg.data(), T.d_seg, (R + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "node-space FP32 entries: copy");
+    std::vector<double> h(Gr.dg.N);
+    for (int j = 0; j < Gr.dg.N; ++j) h[j] = Gr.h_edges[j + 1] - Gr.h_edges[j];
+    std::vector<NcEntryF> out;
+    out.reserve(in.size());
+    std::vector<long long> segf(R + 1, 0);
+    auto same_pair = [](const NcEntry &a, const NcEntry &b) {
+        if (a.r != b.r || a.bu != b.bu || a.bv != b.bv || a.D0 != b.D0) return false;
+        for (int i = 0; i < kB; ++i)
+            if (a.pu[i] != b.pu[i] || a.pv[i] != b.pv[i]) return false;
+        return true;
+    };
+    bool bad = false;
+    for (int r = 0; r < R; ++r) {
+        for (long long t = seg[r]; t < seg[r + 1]; ++t) {
+            const NcEntry &a = in[t];
+            double wc = a.kind == 0 ? a.w : 0.0, wf = a.kind == 1 ? a.w : 0.0;
+            if (a.kind == 0 && t + 1 < seg[r + 1] && in[t + 1].kind == 1 && same_pair(a, in[t + 1])) {
+                wf = in[t + 1].w;
+                ++t;
+            }
+            const double sc = 1.0 / (h[a.bu] * h[a.bv]);
+            wc *= sc;
+            wf *= sc;
+            // the scaled weights must be normal FP32 numbers with room for the products (their
+            // difference wd may round to zero where the two nearly agree)
+            for (double w : {wc, wf})
+                if (w != 0.0 && (std::fabs(w) < 1e-30 || std::fabs(w) > 1e30)) bad = true;
+            NcEntryF f;
+            f.bins = a.bu | (a.bv << 16);
+            f.wc = (float)wc;
+            f.wd = (float)(wf - wc);
+            f.D0 = (float)a.D0;
+            for (int i = 0; i < kB; ++i) {
+                f.pu[i] = (float)a.pu[i];
+                f.pv[i] = (float)a.pv[i];
+            }
+            out.push_back(f);
+        }
+        segf[r + 1] = (long long)out.size();
+    }
+    if (bad) {
+        set_error("node-space partial weights outside the FP32 range");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    if (Gr.dg.N > 0xFFFF) {
+        set_error("node-space FP32 entries: too many bins");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    e = cudaMalloc(&T.d_entf, std::max<size_t>(out.size(), 1) * sizeof(NcEntryF));
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_segf, (R + 1) * sizeof(long long));
+    if (e == cudaSuccess && !out.empty())
+        e = cudaMemcpy(T.d_entf, out.data(), out.size() * sizeof(NcEntryF), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(T.d_segf, segf.data(), (R + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(T.d_entf);
+        cudaFree(T.d_segf);
+        T.d_entf = nullptr;
+        T.d_segf = nullptr;
+        return cuda_fail(e, "node-space FP32 entries: upload");
+    }
+    T.n_entf = (long long)out.size();
+    return GRACE_OK;
+}
+
+cudaError_t launch_nc_pack_tc(const DevGroup &g, const TcTiles &t, int prec, const double *d_g, const double *d_alpha,
+                              int n_cells, void *opA, float *d_gh, float *d_s, cudaStream_t st)
+{
+    if (n_cells <= 0) return cudaSuccess;
+    if (!t.built || !t.nc) return cudaErrorInvalidValue;
+    NodeRuleF rule;
+    for (int al = 0; al < g.Q; ++al) {
+        double P[kB];
+        // Legendre values at the Gauss node s_alpha (host recurrence, eq. 2.4)
+        P[0] = 1.0;
+        if (g.k >= 1) P[1] = g.gs[al];
+        for (int n = 1; n < g.k; ++n) P[n + 1] = ((2.0 * n + 1.0) * g.gs[al] * P[n] - n * P[n - 1]) / (n + 1.0);
+        for (int i = 0; i < kB; ++i) rule.phi[al * kB + i] = i <= g.k ? (float)P[i] : 0.f;
+    }
+    const long long tiles = (n_cells + kTileM - 1) / kTileM;
+    nc_pack_tc_kernel<<<(unsigned)(tiles * g.N), kTileM, 0, st>>>(g, rule, d_g, d_alpha, n_cells, opA, prec, t.k_pad,
+                                                                   d_gh, d_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const TcTiles &t, int n_cells,
+                                 const float *d_gh, const float *d_s, float *d_F32, cudaStream_t st)
+{
+    if (n_cells <= 0 || nt.n_entf == 0) return cudaSuccess;
+    if (!nt.built || !nt.d_entf || !t.built || !t.nc) return cudaErrorInvalidValue;
+    const long long tiles = (n_cells + kTileM - 1) / kTileM;
+    const NcEntryF *ent = (const NcEntryF *)nt.d_entf;
+    // cells per thread: 8 once the grid still covers every SM a few times, else fewer
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int C = tiles * g.R >= 8LL * 4 * n_sm ? 8 : tiles * g.R >= 4LL * 4 * n_sm ? 4 : 1;
+    const dim3 grid((unsigned)((tiles + C - 1) / C), g.R);
+#define GRACE_NC_PARTIAL(K, CC)                                                                                   \
+    nc_partial_f32_kernel<K, CC><<<grid, kTileM, 0, st>>>(g.P, g.R, ent, nt.d_segf, d_gh, d_s, t.d_written, t.ramp_a, \
+                                                        t.ramp_b, n_cells, d_F32)
+#define GRACE_NC_PARTIAL_C(K)                \
+    if (C == 8) GRACE_NC_PARTIAL(K, 8);       \
+    else if (C == 4) GRACE_NC_PARTIAL(K, 4);  \
+    else GRACE_NC_PARTIAL(K, 1)
+    switch (g.K1) {
+    case 1: GRACE_NC_PARTIAL_C(1); break;
+    case 2: GRACE_NC_PARTIAL_C(2); break;
+    case 3: GRACE_NC_PARTIAL_C(3); break;
+    case 4: GRACE_NC_PARTIAL_C(4); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef GRACE_NC_PARTIAL_C
+#undef GRACE_NC_PARTIAL
+    return cudaGetLastError();
+}
 
 void free_nc_tables(NcTables &t)
 {
@@ -411,6 +679,8 @@ void free_nc_tables(NcTables &t)
     cudaFree(t.d_qhi);
     cudaFree(t.d_D0);
     cudaFree(t.d_entries);
+    cudaFree(t.d_entf);
+    cudaFree(t.d_segf);
     cudaFree(t.d_seg);
     t = NcTables();
 }

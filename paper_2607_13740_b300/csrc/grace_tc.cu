@@ -36,6 +36,9 @@
 // splitting the tile list lets a batch of few cell tiles fill every SM.  Items are
 // numbered split-major (item = split x cell tiles + cell tile) so that the
 // round-robin assignment gives every CTA a mix of splits.
+// Node-space tiles (groups with a per-cell kernel parameter, template NC): A holds the cells'
+// values at the fixed Gauss nodes, the MMA contracts over the smaller node of each pair, and the
+// epilogue weights the accumulator by the fragmentation ramp of the larger node (epi_tile_nc).
 // Every wait on an mbarrier is bounded; on timeout the CTA records an error in
 // the device error word, stops issuing work, drains its outstanding copies and
 // releases its tensor memory before returning.
@@ -104,6 +107,11 @@ struct TcParams {
     int n_splits;
     int split[kMaxSplits + 1];
     int *err;
+    // node-space tiles (per-cell kernels): ramp of the epilogue
+    const float *D0;      // [n_d0] D0 of every fixed node
+    int n_d0;
+    const float *cell_s;  // [n_cells] s = sqrt(alpha)
+    float ramp_a, ramp_b;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -260,11 +268,9 @@ __device__ __forceinline__ void fail(const TcParams &P, volatile int *abort_flag
 // (functional f = kEpiSplit m + part of the tile) the sum over the functional's W
 // accumulator columns times the window; G functionals' TMEM loads are in
 // flight before each wait.
-template <int PREC, int W, int G>
-__device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_bytes, int row, int p0,
-                                         uint32_t tcol, int nf, int part, float *Facc)
+template <int PREC, int W>
+__device__ __forceinline__ void load_window(const uint8_t *a_gen, long long a_tile_bytes, int row, int p0, float *gw)
 {
-    float gw[W];
     if (PREC == GRACE_TF32) {
 #pragma unroll
         for (int c = 0; c < W / 4; ++c) {
@@ -289,6 +295,14 @@ __device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_
             }
         }
     }
+}
+
+template <int PREC, int W, int G>
+__device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_bytes, int row, int p0,
+                                         uint32_t tcol, int nf, int part, float *Facc)
+{
+    float gw[W];
+    load_window<PREC, W>(a_gen, a_tile_bytes, row, p0, gw);
 #pragma unroll
     for (int m0 = 0; m0 < kEpiF; m0 += G) {
         if (kEpiSplit * m0 + part >= nf) break;
@@ -318,7 +332,54 @@ __device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_
     }
 }
 
-template <int PREC>
+// Epilogue of a node-space tile (per-cell kernels).  Accumulator columns [32 f, 32 f + 16) of
+// functional f hold, for the window's 16 larger nodes j, the coagulation sums over the smaller
+// node, columns [32 f + 16, 32 f + 32) the fragmentation sums; they are weighted by
+// s (1 - pf_j) Ghat_j and s pf_j Ghat_j, pf_j = clamp(ra s D0_j + rb, 0, 1), with Ghat_j the
+// cell's node value from its A tile.
+constexpr int kEpiFnc = (kMaxN / (2 * kWin) + kEpiSplit - 1) / kEpiSplit;
+
+template <int PREC, int G>
+__device__ __forceinline__ void epi_tile_nc(const uint8_t *a_gen, long long a_tile_bytes, int row, int p0,
+                                            uint32_t tcol, int nf, int part, float s, const float *D0, float ra,
+                                            float rb, float *Facc)
+{
+    float wc[kWin], wf[kWin];
+    load_window<PREC, kWin>(a_gen, a_tile_bytes, row, p0, wc);
+#pragma unroll
+    for (int t = 0; t < kWin; ++t) {
+        const float pf = fminf(fmaxf(fmaf(s * D0[p0 + t], ra, rb), 0.f), 1.f);
+        const float sg = s * wc[t];
+        wf[t] = pf * sg;
+        wc[t] = sg - wf[t];
+    }
+#pragma unroll
+    for (int m0 = 0; m0 < kEpiFnc; m0 += G) {
+        if (kEpiSplit * m0 + part >= nf) break;
+        uint32_t y[G][2 * kWin];
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+            const int f = kEpiSplit * (m0 + gg) + part;
+            if (f < nf) tmem_ld32(tcol + (uint32_t)(f * 2 * kWin), y[gg]);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+            const int f = kEpiSplit * (m0 + gg) + part;
+            if (f < nf) {
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int t = 0; t < kWin; ++t) {
+                    s0 = fmaf(wc[t], __uint_as_float(y[gg][t]), s0);
+                    s1 = fmaf(wf[t], __uint_as_float(y[gg][kWin + t]), s1);
+                }
+                Facc[m0 + gg] += s0 + s1;
+            }
+        }
+    }
+}
+
+template <int PREC, bool NC>
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 {
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
@@ -332,6 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
     uint8_t *tab = gbase + P.a_bufs * P.a_tile_bytes + (size_t)P.n_slots * P.slot_bytes;
     const TileDesc *tiles = reinterpret_cast<const TileDesc *>(tab);
     const int *ford = reinterpret_cast<const int *>(tab + (size_t)P.n_tiles * sizeof(TileDesc));
+    const float *D0s = reinterpret_cast<const float *>(ford + P.R);
     Smem *S = reinterpret_cast<Smem *>(tab + P.table_bytes);
     volatile int *abort_flag = &S->abort_flag;
 
@@ -364,6 +426,10 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         for (int i = threadIdx.x; i < P.n_tiles * (int)(sizeof(TileDesc) / 16); i += blockDim.x) dst[i] = src[i];
         int *fo = const_cast<int *>(ford);
         for (int i = threadIdx.x; i < P.R; i += blockDim.x) fo[i] = P.ford[i];
+        if (NC) {
+            float *d0 = const_cast<float *>(D0s);
+            for (int i = threadIdx.x; i < P.n_d0; i += blockDim.x) d0[i] = P.D0[i];
+        }
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -524,6 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             const uint8_t *a_gen = gbase + (size_t)ab * P.a_tile_bytes;
             const long long cell = (long long)ct * kTileM + row;
             const bool live = cell < P.n_cells;
+            const float s_cell = NC && live ? P.cell_s[cell] : 0.f;
             float Facc[kEpiF];
 #pragma unroll
             for (int m = 0; m < kEpiF; ++m) Facc[m] = 0.f;
@@ -543,7 +610,11 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 }
                 tc_fence_after();
                 const uint32_t tcol = tmem + tlane + (uint32_t)(buf * kAccCols);
-                epi_tile<PREC, kWin, kEpiF>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, Facc);
+                if (NC)
+                    epi_tile_nc<PREC, 2>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, s_cell, D0s, P.ramp_a,
+                                         P.ramp_b, Facc);
+                else
+                    epi_tile<PREC, kWin, kEpiF>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, Facc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&S->acc_empty[buf]));
@@ -603,13 +674,16 @@ void free_tc_tiles(TcTiles &t)
     cudaFree(t.d_b);
     cudaFree(t.d_desc);
     cudaFree(t.d_ford);
+    cudaFree(t.d_D0);
+    cudaFree(t.d_written);
     t = TcTiles();
 }
 
 size_t opA_bytes_for(const DevGroup &g, int prec, int n_cells, int *kpad)
 {
     const int ae = atom_elems(prec);
-    const int kp = (g.P + ae - 1) / ae * ae;
+    const int K = g.cell_alpha ? g.N * g.Q : g.P;   // node values (per-cell kernels) or coefficients
+    const int kp = (K + ae - 1) / ae * ae;
     if (kpad) *kpad = kp;
     const size_t tiles = ((size_t)n_cells + kTileM - 1) / kTileM;
     return tiles * opA_tile_bytes(prec, kp);
@@ -656,142 +730,114 @@ static inline size_t sw32_offset(int row, int x, int eb)
     return (size_t)row * 32 + (chunk << 4) + (byte & 15);
 }
 
-grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
+namespace {
+
+// Dense per-functional matrices of one contraction, already scaled for the tensor
+// operands: M[(r * rows + p) * kdim + q] multiplies A column q into accumulator row p of
+// functional r.  Rows come in windows of W consecutive rows (the accumulator columns of
+// one functional in an N-tile); the epilogue vector of window w starts at A column
+// w * p0_stride.
+struct Forms {
+    int R = 0, rows = 0, kdim = 0, W = 0, p0_stride = 0;
+    std::vector<double> M;
+    const double *row(int r, int p) const { return M.data() + ((size_t)r * rows + p) * kdim; }
+    int n_win() const { return (rows + W - 1) / W; }
+};
+
+struct Ext {
+    int lo, hi;
+};
+
+struct Plan {
+    double cost = 1e300;
+    std::vector<int> first;                 // first functional (index into ford) of every group
+    std::vector<std::vector<Ext>> wext;     // [ford index][window] union of the rows' q extents
+};
+
+double tile_cost(int prec, int n, int nks)
 {
-    const DevGroup &g = G.dg;
-    if (g.k > kKMax) {
-        set_error("tensor-core tiles need k <= 3");
-        return GRACE_ERR_UNSUPPORTED;
+    const int planes = n_planes(prec), mult = prec == GRACE_TF32 ? 1 : 3;
+    const double mma = (double)nks * mult * kMmaClk;
+    const double l2 = (double)nks * n * 32.0 * planes / kL2BytesPerClk;
+    const double epi = kEpiBaseClk + kEpiColClk * n;
+    return std::max(mma, std::max(l2, epi)) + kTileClk;
+}
+
+// dynamic program over the functional order: best[y] = cheapest cover of ford[0, y) by
+// groups of consecutive functionals, each group one N-tile per non-empty window
+Plan plan_forms(const Forms &F, const std::vector<int> &ford, int prec)
+{
+    const int R = F.R, W = F.W, nw = F.n_win(), kstep = 32 / elem_bytes(prec);
+    Plan pl;
+    pl.wext.assign(R, std::vector<Ext>(nw, Ext{F.kdim, 0}));
+    for (int x = 0; x < R; ++x)
+        for (int p = 0; p < F.rows; ++p) {
+            const double *Mr = F.row(ford[x], p);
+            int lo = F.kdim, hi = 0;
+            for (int q = 0; q < F.kdim; ++q)
+                if (Mr[q] != 0.0) {
+                    lo = std::min(lo, q);
+                    hi = q + 1;
+                }
+            if (hi <= lo) continue;
+            Ext &E = pl.wext[x][p / W];
+            E.lo = std::min(E.lo, lo);
+            E.hi = std::max(E.hi, hi);
+        }
+    const double inf = 1e300;
+    std::vector<double> best(R + 1, inf);
+    std::vector<int> from(R + 1, -1);
+    best[0] = 0.0;
+    const int maxf = std::min(kMaxF, kMaxN / W);
+    for (int x = 0; x < R; ++x) {
+        if (best[x] >= inf) continue;
+        std::vector<Ext> Un(nw, Ext{F.kdim, 0});
+        for (int y = x + 1; y <= std::min(R, x + maxf); ++y) {
+            double c = 0.0;
+            for (int w = 0; w < nw; ++w) {
+                const Ext &E = pl.wext[y - 1][w];
+                Un[w].lo = std::min(Un[w].lo, E.lo);
+                Un[w].hi = std::max(Un[w].hi, E.hi);
+                if (Un[w].hi > Un[w].lo)
+                    c += tile_cost(prec, (y - x) * W, (Un[w].hi + kstep - 1) / kstep - Un[w].lo / kstep);
+            }
+            if (best[x] + c < best[y]) {
+                best[y] = best[x] + c;
+                from[y] = x;
+            }
+        }
     }
-    const int P_ = g.P, R = g.R, K1 = g.K1;
+    for (int y = R; y > 0; y = from[y]) pl.first.push_back(from[y]);
+    std::reverse(pl.first.begin(), pl.first.end());
+    pl.cost = best[R];
+    return pl;
+}
+
+// B images (SWIZZLE_32B k-step blocks, bf16 hi/lo planes or TF32) and tile descriptors of a
+// plan, uploaded into out; written[r] = 1 for every functional the contraction writes
+grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &ford, int prec, TcTiles &out,
+                        std::vector<int> &written)
+{
+    const int R = F.R, W = F.W, nw = F.n_win();
     const int eb = elem_bytes(prec), planes = n_planes(prec);
-    const int kstep = 32 / eb;                        // elements per MMA k-step
-    const int kps = prec == GRACE_TF32 ? 4 : 2;       // k-steps per B copy
-    const int mult = prec == GRACE_TF32 ? 1 : 3;      // MMAs per k-step
-    std::vector<double> T((size_t)R * P_ * P_);
-    cudaError_t e = cudaMemcpyAsync(T.data(), G.d_T, T.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "tensor-core tiles: copy T");
-
-    std::vector<double> h(g.N);
-    for (int j = 0; j < g.N; ++j) h[j] = G.h_edges[j + 1] - G.h_edges[j];
-
-    // Two representations of the same quadratic forms: T as built (u-side p, v-side q) and its
-    // fold onto the upper triangle U (U[p][q] = T[p][q] + T[q][p], q > p).  Both are planned and the
-    // cheaper plan under the cost model is built.
-    std::vector<double> U(T);
-    long long nnz_fold = 0, nnz_T = 0;
-    for (int r = 0; r < R; ++r) {
-        double *Ur = U.data() + (size_t)r * P_ * P_;
-        for (int p = 0; p < P_; ++p)
-            for (int q = p + 1; q < P_; ++q) {
-                Ur[(size_t)p * P_ + q] += Ur[(size_t)q * P_ + p];
-                Ur[(size_t)q * P_ + p] = 0.0;
-            }
-    }
-    for (size_t i = 0; i < T.size(); ++i) {
-        nnz_T += T[i] != 0.0;
-        nnz_fold += U[i] != 0.0;
-    }
-
-    // functionals in bin order: interface flux of bin j, then its volume terms
-    std::vector<int> ford;
-    for (int j = 0; j < g.N; ++j) {
-        if (j < g.n_if) ford.push_back(j);
-        for (int i = 1; i <= g.k; ++i) ford.push_back(g.n_if + j * g.k + i - 1);
-    }
-    if ((int)ford.size() != R) {
-        set_error("tensor-core tiles: functional count mismatch");
-        return GRACE_ERR_ARG;
-    }
-
-    auto tile_cost = [&](int n, int nks) {
-        const double mma = (double)nks * mult * kMmaClk;
-        const double l2 = (double)nks * n * 32.0 * planes / kL2BytesPerClk;
-        const double epi = kEpiBaseClk + kEpiColClk * n;
-        return std::max(mma, std::max(l2, epi)) + kTileClk;
-    };
-    struct Ext {
-        int lo, hi;
-    };
-    struct Plan {
-        double cost = 1e300;
-        std::vector<std::pair<int, int>> groups;   // (first functional in ford order, window-width index)
-        std::vector<std::vector<Ext>> wext;       // [ford index][window] union of q extents
-        int n_win = 0;
-    };
-    const int W = kWin;
-    // dynamic program over the functional order: best[y] = cheapest cover of ford[0, y)
-    auto plan = [&](const std::vector<double> &M) {
-        Plan pl;
-        pl.n_win = (P_ + W - 1) / W;
-        pl.wext.assign(R, std::vector<Ext>(pl.n_win, Ext{P_, 0}));
-        for (int x = 0; x < R; ++x) {
-            const double *Mr = M.data() + (size_t)ford[x] * P_ * P_;
-            for (int p = 0; p < P_; ++p) {
-                int lo = P_, hi = 0;
-                for (int q = 0; q < P_; ++q)
-                    if (Mr[(size_t)p * P_ + q] != 0.0) {
-                        lo = std::min(lo, q);
-                        hi = q + 1;
-                    }
-                if (hi <= lo) continue;
-                Ext &E = pl.wext[x][p / W];
-                E.lo = std::min(E.lo, lo);
-                E.hi = std::max(E.hi, hi);
-            }
-        }
-        const double inf = 1e300;
-        std::vector<double> best(R + 1, inf);
-        std::vector<int> from(R + 1, -1);
-        best[0] = 0.0;
-        const int maxf = std::min(kMaxF, kMaxN / W);
-        for (int x = 0; x < R; ++x) {
-            if (best[x] >= inf) continue;
-            std::vector<Ext> Un(pl.n_win, Ext{P_, 0});
-            for (int y = x + 1; y <= std::min(R, x + maxf); ++y) {
-                double c = 0.0;
-                for (int w = 0; w < pl.n_win; ++w) {
-                    const Ext &E = pl.wext[y - 1][w];
-                    Un[w].lo = std::min(Un[w].lo, E.lo);
-                    Un[w].hi = std::max(Un[w].hi, E.hi);
-                    if (Un[w].hi > Un[w].lo)
-                        c += tile_cost((y - x) * W, (Un[w].hi + kstep - 1) / kstep - Un[w].lo / kstep);
-                }
-                if (best[x] + c < best[y]) {
-                    best[y] = best[x] + c;
-                    from[y] = x;
-                }
-            }
-        }
-        for (int y = R; y > 0; y = from[y]) pl.groups.push_back({from[y], 0});
-        std::reverse(pl.groups.begin(), pl.groups.end());
-        pl.cost = best[R];
-        return pl;
-    };
-    Plan pT = plan(T), pU = plan(U);
-    const bool use_fold = pU.cost <= pT.cost;
-    const Plan &pl = use_fold ? pU : pT;
-    const std::vector<double> &M = use_fold ? U : T;
-    const auto &groups = pl.groups;
-    const auto &wext_sel = pl.wext;
-    const int n_win_sel = pl.n_win;
-
-    TcTiles out;
+    const int kstep = 32 / eb;
+    const int kps = prec == GRACE_TF32 ? 4 : 2;
+    const int mult = prec == GRACE_TF32 ? 1 : 3;
     std::vector<TileDesc> tiles;
     std::vector<uint8_t> B;
+    written.assign(R, 0);
     long long macs = 0, mmas = 0;
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-        const int x = groups[gi].first;
-        const int y = gi + 1 < groups.size() ? groups[gi + 1].first : R;
+    for (size_t gi = 0; gi < pl.first.size(); ++gi) {
+        const int x = pl.first[gi];
+        const int y = gi + 1 < pl.first.size() ? pl.first[gi + 1] : R;
         const int nf = y - x, n = nf * W;
         const size_t first = tiles.size();
         double gcost = 0.0;
-        for (int w = 0; w < n_win_sel; ++w) {
-            Ext Un{P_, 0};
+        for (int w = 0; w < nw; ++w) {
+            Ext Un{F.kdim, 0};
             for (int f = x; f < y; ++f) {
-                Un.lo = std::min(Un.lo, wext_sel[f][w].lo);
-                Un.hi = std::max(Un.hi, wext_sel[f][w].hi);
+                Un.lo = std::min(Un.lo, pl.wext[f][w].lo);
+                Un.hi = std::max(Un.hi, pl.wext[f][w].hi);
             }
             if (Un.hi <= Un.lo) continue;
             TileDesc td;
@@ -799,7 +845,7 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
             td.n = n;
             td.nf_flush = nf;
             td.w = W;
-            td.p0 = w * W;
+            td.p0 = w * F.p0_stride;
             td.ks_lo = Un.lo / kstep;
             td.ks_hi = (Un.hi + kstep - 1) / kstep;
             td.f0 = x;
@@ -810,17 +856,16 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
             uint8_t *img = B.data() + (size_t)td.b_off16 * 16;
             for (int s = 0; s < nks; ++s) {
                 uint8_t *bk = img + (size_t)s * blk * planes;
-                for (int f = 0; f < nf; ++f) {
-                    const double *Tr = M.data() + (size_t)ford[x + f] * P_ * P_;
+                for (int f = 0; f < nf; ++f)
                     for (int c = 0; c < W; ++c) {
-                        const int p = td.p0 + c, rowi = f * W + c;
-                        if (p >= P_) continue;
+                        const int p = w * W + c, rowi = f * W + c;
+                        if (p >= F.rows) continue;
+                        const double *Mr = F.row(ford[x + f], p);
                         for (int xx = 0; xx < kstep; ++xx) {
                             const int q = (td.ks_lo + s) * kstep + xx;
-                            if (q >= P_) continue;
-                            const double v = Tr[(size_t)p * P_ + q];
-                            if (v == 0.0) continue;
-                            const double val = v / (h[p / K1] * h[q / K1]);
+                            if (q >= F.kdim) continue;
+                            const double val = Mr[q];
+                            if (val == 0.0) continue;
                             const size_t off = sw32_offset(rowi, xx, eb);
                             if (prec == GRACE_TF32) {
                                 const uint32_t bits = tf32_bits_rn((float)val);
@@ -833,11 +878,10 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
                             }
                         }
                     }
-                }
             }
             macs += (long long)n * nks * kstep;
             mmas += (long long)nks * mult;
-            gcost += tile_cost(n, nks);
+            gcost += tile_cost(prec, n, nks);
             out.slot_bytes = std::max(out.slot_bytes, (int)(std::min(kps, nks) * blk * planes));
             out.max_rows = std::max(out.max_rows, n);
             tiles.push_back(td);
@@ -846,6 +890,7 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
             tiles.back().nf_flush |= 1 << 16;
             out.group_tile.push_back((int)first);
             out.group_cost.push_back(gcost);
+            for (int f = x; f < y; ++f) written[ford[f]] = 1;
         }
     }
     if (tiles.empty()) {
@@ -857,8 +902,7 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
         return GRACE_ERR_UNSUPPORTED;
     }
     out.group_tile.push_back((int)tiles.size());
-    free_tc_tiles(G.tc[prec]);
-    e = cudaMalloc(&out.d_b, B.size());
+    cudaError_t e = cudaMalloc(&out.d_b, B.size());
     if (e == cudaSuccess) e = cudaMalloc(&out.d_desc, tiles.size() * sizeof(TileDesc));
     if (e == cudaSuccess) e = cudaMalloc(&out.d_ford, ford.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(out.d_b, B.data(), B.size(), cudaMemcpyHostToDevice);
@@ -868,17 +912,177 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
         free_tc_tiles(out);
         return cuda_fail(e, "tensor-core tiles: upload");
     }
-    const int ae = atom_elems(prec);
     out.n_tiles = (int)tiles.size();
-    out.k_pad = (P_ + ae - 1) / ae * ae;
     out.b_bytes = B.size();
     out.mac_per_cell = macs;
     out.mma_per_tile = mmas;
-    out.nnz_fold = std::min(nnz_fold, nnz_T);
     out.pred_clk = pl.cost;
-    out.folded = use_fold ? 1 : 0;
     out.slot_bytes = (out.slot_bytes + 1023) / 1024 * 1024;
+    return GRACE_OK;
+}
+
+// functionals in bin order: interface flux of bin j, then its volume terms
+std::vector<int> functional_order(const DevGroup &g)
+{
+    std::vector<int> ford;
+    for (int j = 0; j < g.N; ++j) {
+        if (j < g.n_if) ford.push_back(j);
+        for (int i = 1; i <= g.k; ++i) ford.push_back(g.n_if + j * g.k + i - 1);
+    }
+    return ford;
+}
+
+}  // namespace
+
+grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
+{
+    const DevGroup &g = G.dg;
+    if (g.k > kKMax) {
+        set_error("tensor-core tiles need k <= 3");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    const int P_ = g.P, R = g.R, K1 = g.K1;
+    Forms FT, FU;
+    FT.R = FU.R = R;
+    FT.rows = FU.rows = P_;
+    FT.kdim = FU.kdim = P_;
+    FT.W = FU.W = kWin;
+    FT.p0_stride = FU.p0_stride = kWin;
+    FT.M.resize((size_t)R * P_ * P_);
+    cudaError_t e = cudaMemcpyAsync(FT.M.data(), G.d_T, FT.M.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core tiles: copy T");
+
+    std::vector<double> h(g.N);
+    for (int j = 0; j < g.N; ++j) h[j] = G.h_edges[j + 1] - G.h_edges[j];
+
+    // Two representations of the same quadratic forms: T as built (u-side p, v-side q) and its
+    // fold onto the upper triangle U (U[p][q] = T[p][q] + T[q][p], q > p).  Both are planned and the
+    // cheaper plan under the cost model is built.  Entries are scaled by 1 / (h_bin(p) h_bin(q)).
+    FU.M = FT.M;
+    long long nnz_fold = 0, nnz_T = 0;
+    for (int r = 0; r < R; ++r) {
+        double *Ur = FU.M.data() + (size_t)r * P_ * P_;
+        for (int p = 0; p < P_; ++p)
+            for (int q = p + 1; q < P_; ++q) {
+                Ur[(size_t)p * P_ + q] += Ur[(size_t)q * P_ + p];
+                Ur[(size_t)q * P_ + p] = 0.0;
+            }
+    }
+    for (size_t i = 0; i < FT.M.size(); ++i) {
+        nnz_T += FT.M[i] != 0.0;
+        nnz_fold += FU.M[i] != 0.0;
+    }
+    for (int r = 0; r < R; ++r)
+        for (int p = 0; p < P_; ++p)
+            for (int q = 0; q < P_; ++q) {
+                const size_t i = ((size_t)r * P_ + p) * P_ + q;
+                const double sc = 1.0 / (h[p / K1] * h[q / K1]);
+                FT.M[i] *= sc;
+                FU.M[i] *= sc;
+            }
+
+    const std::vector<int> ford = functional_order(g);
+    if ((int)ford.size() != R) {
+        set_error("tensor-core tiles: functional count mismatch");
+        return GRACE_ERR_ARG;
+    }
+    const Plan pT = plan_forms(FT, ford, prec), pU = plan_forms(FU, ford, prec);
+    const bool use_fold = pU.cost <= pT.cost;
+    TcTiles out;
+    std::vector<int> written;
+    grace_status s = emit_tiles(use_fold ? FU : FT, use_fold ? pU : pT, ford, prec, out, written);
+    if (s != GRACE_OK) return s;
+    const int ae = atom_elems(prec);
+    out.k_pad = (P_ + ae - 1) / ae * ae;
+    out.nnz_fold = std::min(nnz_fold, nnz_T);
+    out.folded = use_fold ? 1 : 0;
     out.built = 1;
+    free_tc_tiles(G.tc[prec]);
+    G.tc[prec] = out;
+    return GRACE_OK;
+}
+
+// Tensor-core tiles of the fixed-pair part of a per-cell kernel group.  The MMA contracts
+// over the smaller node i (A = the cell's node values Ghat_i = h_bin(i) G_i), one accumulator
+// row per (functional, larger node j, factor): rows [32 w, 32 w + 16) of window w hold the
+// coagulation weights Cc_r[i][j] of nodes j in [16 w, 16 w + 16), rows [32 w + 16, 32 w + 32)
+// the fragmentation weights Cf_r[i][j], both scaled by 1 / (h_bin(i) h_bin(j)).  The epilogue
+// multiplies them by s (1 - pf_j) Ghat_j and s pf_j Ghat_j.
+grace_status build_nc_tc_tiles(Group &G, int prec, cudaStream_t st)
+{
+    const DevGroup &g = G.dg;
+    const NcTables &T = G.nc;
+    if (!T.built) {
+        set_error("tensor-core tiles: node-space tables not built");
+        return GRACE_ERR_ORDER;
+    }
+    const int R = g.R, Q = g.Q, NQ = T.NQ;
+    const size_t ntab = (size_t)R * NQ * NQ;
+    std::vector<double> Cc(ntab), Cf(ntab), D0(NQ);
+    cudaError_t e = cudaMemcpyAsync(Cc.data(), T.d_Cc, ntab * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Cf.data(), T.d_Cf, ntab * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D0.data(), T.d_D0, NQ * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core tiles: copy node-space tables");
+    std::vector<double> h(g.N);
+    for (int j = 0; j < g.N; ++j) h[j] = G.h_edges[j + 1] - G.h_edges[j];
+
+    Forms F;
+    F.R = R;
+    F.W = 2 * kWin;
+    F.p0_stride = kWin;
+    const int nw = (NQ + kWin - 1) / kWin;
+    F.rows = nw * F.W;
+    F.kdim = NQ;
+    F.M.assign((size_t)R * F.rows * NQ, 0.0);
+    double vmin = INFINITY, vmax = 0.0;
+    for (int r = 0; r < R; ++r)
+        for (int i = 0; i < NQ; ++i)
+            for (int j = 0; j < NQ; ++j)
+                for (int src = 0; src < 2; ++src) {
+                    const double v = (src ? Cf : Cc)[((size_t)r * NQ + i) * NQ + j];
+                    if (v == 0.0) continue;
+                    const double sv = v / (h[i / Q] * h[j / Q]);
+                    const int row = (j / kWin) * F.W + src * kWin + j % kWin;
+                    F.M[((size_t)r * F.rows + row) * NQ + i] = sv;
+                    vmin = std::min(vmin, std::fabs(sv));
+                    vmax = std::max(vmax, std::fabs(sv));
+                }
+    // the scaled weights must be normal FP32 numbers (with room for the products)
+    if (vmax > 0.0 && (vmin < 1e-30 || vmax > 1e30)) {
+        set_error("tensor-core tiles: node-space weights outside the FP32 range");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    const std::vector<int> ford = functional_order(g);
+    const Plan pl = plan_forms(F, ford, prec);
+    TcTiles out;
+    std::vector<int> written;
+    grace_status s = emit_tiles(F, pl, ford, prec, out, written);
+    if (s != GRACE_OK) return s;
+    const int ae = atom_elems(prec);
+    out.k_pad = (NQ + ae - 1) / ae * ae;
+    long long nnz = 0;
+    for (size_t i = 0; i < ntab; ++i) nnz += (Cc[i] != 0.0) + (Cf[i] != 0.0);
+    out.nnz_fold = nnz;
+    out.folded = 1;
+    out.nc = 1;
+    out.n_d0 = nw * kWin;
+    std::vector<float> d0f(out.n_d0, 0.f);
+    for (int a = 0; a < NQ; ++a) d0f[a] = (float)D0[a];
+    const double vf = g.coag_p[4], wr = g.coag_p[5];
+    out.ramp_a = (float)(1.0 / (2.0 * wr * vf));
+    out.ramp_b = (float)(-(1.0 - wr) / (2.0 * wr));
+    e = cudaMalloc(&out.d_D0, d0f.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&out.d_written, R * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_D0, d0f.data(), d0f.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_written, written.data(), R * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_tc_tiles(out);
+        return cuda_fail(e, "tensor-core tiles: node tables upload");
+    }
+    out.built = 1;
+    free_tc_tiles(G.tc[prec]);
     G.tc[prec] = out;
     return GRACE_OK;
 }
@@ -920,11 +1124,12 @@ static void choose_splits(const TcTiles &t, int n_cell_tiles, int n_sm, TcParams
     P.n_splits = ns;
 }
 
-template <int PREC>
+template <int PREC, bool NC>
 static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
 {
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
-    P.table_bytes = (int)((P.n_tiles * sizeof(TileDesc) + (size_t)P.R * sizeof(int) + 15) / 16 * 16);
+    P.table_bytes = (int)((P.n_tiles * sizeof(TileDesc) + (size_t)P.R * sizeof(int) +
+                           (NC ? (size_t)P.n_d0 * sizeof(float) : 0) + 15) / 16 * 16);
     const size_t fixed = 1024 + (size_t)P.table_bytes + sizeof(Smem) + 64;
     const size_t a1 = (size_t)P.a_tile_bytes;
     // Shared-memory plan: 32 KB B copies at N = 256 (fewer k-steps per copy for groups whose A tile
@@ -939,20 +1144,21 @@ static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
     P.a_bufs = fixed + 2 * a1 + 4 * (size_t)P.slot_bytes <= (size_t)kSmemLimit ? 2 : 1;
     P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed - P.a_bufs * a1) / P.slot_bytes);
     const size_t smem = fixed + P.a_bufs * a1 + (size_t)P.n_slots * P.slot_bytes;
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     const int items = P.n_cell_tiles * P.n_splits;
     const int grid = std::min(items, sm_count(dev));
-    contract_tc_kernel<PREC><<<grid, kThreads, smem, st>>>(P);
+    contract_tc_kernel<PREC, NC><<<grid, kThreads, smem, st>>>(P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, int n_cells,
-                               float *d_F32, int *d_err, cudaStream_t st)
+                               float *d_F32, int *d_err, cudaStream_t st, const float *d_cell_s)
 {
     if (!t.built || n_cells <= 0) return n_cells == 0 ? cudaSuccess : cudaErrorInvalidValue;
+    if (t.nc && !d_cell_s) return cudaErrorInvalidValue;
     TcParams P;
     std::memset(&P, 0, sizeof(P));
     P.tiles = (const TileDesc *)t.d_desc;
@@ -969,7 +1175,17 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
     int dev = 0;
     cudaGetDevice(&dev);
     choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
-    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32>(P, t.max_rows, st) : launch_prec<GRACE_BF16X3>(P, t.max_rows, st);
+    if (t.nc) {
+        P.D0 = t.d_D0;
+        P.n_d0 = t.n_d0;
+        P.cell_s = d_cell_s;
+        P.ramp_a = t.ramp_a;
+        P.ramp_b = t.ramp_b;
+        return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, true>(P, t.max_rows, st)
+                                  : launch_prec<GRACE_BF16X3, true>(P, t.max_rows, st);
+    }
+    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, false>(P, t.max_rows, st)
+                              : launch_prec<GRACE_BF16X3, false>(P, t.max_rows, st);
 }
 
 }  // namespace grace

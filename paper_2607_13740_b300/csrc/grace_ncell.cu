@@ -60,10 +60,17 @@ static_assert(sizeof(NcEntry) == 96, "NcEntry layout");
 // FP32 entry of the reduced-precision forms.  A coagulation entry and the fragmentation entry of
 // the same node pair are merged: the pair contributes (wc + wd pf) u v with wc the coagulation
 // weight and wd = w_frag - w_coag, both divided by h_bu h_bv (to be used with the
-// bin-mass-scaled coefficients h_bin g).
+// bin-mass-scaled coefficients h_bin g), and pf = clamp(s D0r + rb, 0, 1) with D0r = D0 / (2 w v_frag)
+// the ramp-scaled D0 of the larger particle.  Flags mark where u or D0 differ from the previous
+// entry of the same functional, so that runs sharing them reuse u and pf.
+constexpr int kNcBinBits = 14;
+constexpr int kNcBinMask = (1 << kNcBinBits) - 1;
+constexpr int kNcBinsMask = (1 << (2 * kNcBinBits)) - 1;
+constexpr int kNcNewU = 1 << 28;
+constexpr int kNcNewPf = 1 << 29;
 struct NcEntryF {
-    int bins;              // bu | bv << 16
-    float wc, wd, D0;
+    int bins;              // bu | bv << 14 | flags
+    float wc, wd, D0r;
     float pu[kB], pv[kB];
 };
 static_assert(sizeof(NcEntryF) == 48, "NcEntryF layout");
@@ -470,27 +477,28 @@ __global__ void __launch_bounds__(128) nc_pack_tc_kernel(DevGroup G, NodeRuleF r
 // covers C cell tiles: thread t handles row t of each (C cells), so every entry, staged through
 // shared memory, is read once per C cells (the broadcast loads, not the arithmetic, bound a
 // thread-per-cell loop).  Entries come sorted by (bin of u, bin of v); a thread reloads its cells'
-// two bins of coefficients only when that pair changes (coalesced: gh is cell-minor).
+// two bins of coefficients only when that pair changes (coalesced: gh is cell-minor).  Within a
+// run of entries with the same u the terms are summed as u * sum (wc + wd pf) v, and pf is
+// recomputed only where D0 changes.
 template <int K1, int C>
 __global__ void __launch_bounds__(128) nc_partial_f32_kernel(int P, int R, const NcEntryF *__restrict__ entries,
                                                              const long long *__restrict__ seg,
                                                              const float *__restrict__ gh,
                                                              const float *__restrict__ cell_s,
-                                                             const int *__restrict__ written, float ra, float rb,
+                                                             const int *__restrict__ written, float rb,
                                                              int n_cells, float *__restrict__ F32)
 {
     constexpr int kChunk = 128;
     __shared__ float4 es[kChunk * 3];
     const int r = blockIdx.y, row = threadIdx.x;
     const long long ct0 = (long long)blockIdx.x * C;
-    float s[C], acc[C], gu[C][K1], gv[C][K1];
-    const float *gc[C];
+    const long long last_tile = (long long)(n_cells - 1) / kTileM;
+    float s[C], acc[C], ru[C], u[C], pf[C], gu[C][K1], gv[C][K1];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const long long cell = (ct0 + j) * kTileM + row;
         s[j] = cell < n_cells ? cell_s[cell] : 0.f;   // 0 for rows past the batch: they add nothing
-        acc[j] = 0.f;
-        gc[j] = gh + (size_t)min(ct0 + j, (long long)(n_cells - 1) / kTileM) * P * kTileM + row;
+        acc[j] = ru[j] = u[j] = pf[j] = 0.f;
 #pragma unroll
         for (int i = 0; i < K1; ++i) gu[j][i] = gv[j][i] = 0.f;
     }
@@ -503,30 +511,46 @@ __global__ void __launch_bounds__(128) nc_partial_f32_kernel(int P, int R, const
         for (int w = threadIdx.x; w < n * 3; w += blockDim.x) es[w] = src[w];
         __syncthreads();
         for (int t = 0; t < n; ++t) {
-            const float4 a = es[3 * t], pu = es[3 * t + 1], pv = es[3 * t + 2];
-            const int bins = __float_as_int(a.x);
+            const float4 a = es[3 * t], pv = es[3 * t + 2];
+            const int bf = __float_as_int(a.x), bins = bf & kNcBinsMask;
             if (bins != cur) {
                 cur = bins;
-                const size_t ou = (size_t)(bins & 0xFFFF) * K1 * kTileM, ov = (size_t)(bins >> 16) * K1 * kTileM;
+                const size_t ou = (size_t)(bins & kNcBinMask) * K1 * kTileM;
+                const size_t ov = (size_t)(bins >> kNcBinBits) * K1 * kTileM;
 #pragma unroll
-                for (int j = 0; j < C; ++j)
+                for (int j = 0; j < C; ++j) {
+                    const float *gc = gh + (size_t)min(ct0 + j, last_tile) * P * kTileM + row;
 #pragma unroll
                     for (int i = 0; i < K1; ++i) {
-                        gu[j][i] = gc[j][ou + i * kTileM];
-                        gv[j][i] = gc[j][ov + i * kTileM];
+                        gu[j][i] = gc[ou + i * kTileM];
+                        gv[j][i] = gc[ov + i * kTileM];
                     }
+                }
             }
-            const float pa[4] = {pu.x, pu.y, pu.z, pu.w}, pb[4] = {pv.x, pv.y, pv.z, pv.w};
+            if (bf & kNcNewU) {
+                const float4 pu = es[3 * t + 1];
+                const float pa[4] = {pu.x, pu.y, pu.z, pu.w};
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    acc[j] = fmaf(u[j], ru[j], acc[j]);
+                    ru[j] = 0.f;
+                    float x = gu[j][0] * pa[0];
+#pragma unroll
+                    for (int i = 1; i < K1; ++i) x = fmaf(gu[j][i], pa[i], x);
+                    u[j] = x;
+                }
+            }
+            if (bf & kNcNewPf) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) pf[j] = __saturatef(fmaf(s[j], a.w, rb));
+            }
+            const float pb[4] = {pv.x, pv.y, pv.z, pv.w};
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                float u = gu[j][0] * pa[0], v = gv[j][0] * pb[0];
+                float v = gv[j][0] * pb[0];
 #pragma unroll
-                for (int i = 1; i < K1; ++i) {
-                    u = fmaf(gu[j][i], pa[i], u);
-                    v = fmaf(gv[j][i], pb[i], v);
-                }
-                const float pf = fminf(fmaxf(fmaf(s[j] * a.w, ra, rb), 0.f), 1.f);
-                acc[j] = fmaf(fmaf(a.z, pf, a.y), u * v, acc[j]);
+                for (int i = 1; i < K1; ++i) v = fmaf(gv[j][i], pb[i], v);
+                ru[j] = fmaf(fmaf(a.z, pf[j], a.y), v, ru[j]);
             }
         }
     }
@@ -535,7 +559,7 @@ __global__ void __launch_bounds__(128) nc_partial_f32_kernel(int P, int R, const
         const long long ct = ct0 + j, cell = ct * kTileM + row;
         if (cell < n_cells) {
             float *Fo = F32 + ((size_t)ct * R + r) * kTileM + row;
-            *Fo = (written[r] ? *Fo : 0.f) + s[j] * acc[j];
+            *Fo = (written[r] ? *Fo : 0.f) + s[j] * fmaf(u[j], ru[j], acc[j]);
         }
     }
 }
@@ -566,8 +590,11 @@ grace_status build_nc_tc_entries(Group &Gr, cudaStream_t st)
             if (a.pu[i] != b.pu[i] || a.pv[i] != b.pv[i]) return false;
         return true;
     };
+    // ramp scale of D0: pf = clamp(s D0 / (2 w v_frag) - (1 - w) / (2 w), 0, 1)
+    const double ra = 1.0 / (2.0 * Gr.dg.coag_p[5] * Gr.dg.coag_p[4]);
     bool bad = false;
     for (int r = 0; r < R; ++r) {
+        const size_t first = out.size();
         for (long long t = seg[r]; t < seg[r + 1]; ++t) {
             const NcEntry &a = in[t];
             double wc = a.kind == 0 ? a.w : 0.0, wf = a.kind == 1 ? a.w : 0.0;
@@ -583,13 +610,22 @@ grace_status build_nc_tc_entries(Group &Gr, cudaStream_t st)
             for (double w : {wc, wf})
                 if (w != 0.0 && (std::fabs(w) < 1e-30 || std::fabs(w) > 1e30)) bad = true;
             NcEntryF f;
-            f.bins = a.bu | (a.bv << 16);
+            f.bins = a.bu | (a.bv << kNcBinBits);
             f.wc = (float)wc;
             f.wd = (float)(wf - wc);
-            f.D0 = (float)a.D0;
+            f.D0r = (float)(ra * a.D0);
             for (int i = 0; i < kB; ++i) {
                 f.pu[i] = (float)a.pu[i];
                 f.pv[i] = (float)a.pv[i];
+            }
+            if (out.size() == first) {
+                f.bins |= kNcNewU | kNcNewPf;
+            } else {
+                const NcEntryF &p = out.back();
+                bool same_u = (p.bins & kNcBinMask) == (f.bins & kNcBinMask);
+                for (int i = 0; i < kB; ++i) same_u = same_u && p.pu[i] == f.pu[i];
+                if (!same_u) f.bins |= kNcNewU;
+                if (p.D0r != f.D0r) f.bins |= kNcNewPf;
             }
             out.push_back(f);
         }
@@ -599,7 +635,7 @@ grace_status build_nc_tc_entries(Group &Gr, cudaStream_t st)
         set_error("node-space partial weights outside the FP32 range");
         return GRACE_ERR_UNSUPPORTED;
     }
-    if (Gr.dg.N > 0xFFFF) {
+    if (Gr.dg.N > kNcBinMask) {
         set_error("node-space FP32 entries: too many bins");
         return GRACE_ERR_UNSUPPORTED;
     }
@@ -653,8 +689,8 @@ cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const Tc
     const int C = tiles * g.R >= 8LL * 4 * n_sm ? 8 : tiles * g.R >= 4LL * 4 * n_sm ? 4 : 1;
     const dim3 grid((unsigned)((tiles + C - 1) / C), g.R);
 #define GRACE_NC_PARTIAL(K, CC)                                                                                   \
-    nc_partial_f32_kernel<K, CC><<<grid, kTileM, 0, st>>>(g.P, g.R, ent, nt.d_segf, d_gh, d_s, t.d_written, t.ramp_a, \
-                                                        t.ramp_b, n_cells, d_F32)
+    nc_partial_f32_kernel<K, CC><<<grid, kTileM, 0, st>>>(g.P, g.R, ent, nt.d_segf, d_gh, d_s, t.d_written, t.ramp_b, \
+                                                        n_cells, d_F32)
 #define GRACE_NC_PARTIAL_C(K)                \
     if (C == 8) GRACE_NC_PARTIAL(K, 8);       \
     else if (C == 4) GRACE_NC_PARTIAL(K, 4);  \

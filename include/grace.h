@@ -189,11 +189,19 @@ GRACE_API grace_status grace_limit(grace_batch *batch, double *g, unsigned char 
 
 /* Tangent-linear RHS: Jv = (dL/dg)(g) v.  L is quadratic in g, so
    Jv = D (g^T (T_r + T_r^T) v)_r exactly.  g, v, Jv: device, packed layout.
-   GRACE_FP64 only (GRACE_ERR_UNSUPPORTED otherwise).  The paper has no adjoint;
-   this and the next three calls differentiate its scheme. */
+   GRACE_FP64 evaluates that form on the CUDA cores; GRACE_TF32 / GRACE_BF16X3 use
+   the exact polarization Jv = [L(g + eps v) - L(g - eps v)] / (2 eps) with two
+   tensor-core contractions, eps = 2^(e_g - e_v) per cell (e_x the binary exponent
+   of the cell's largest |x|); their accuracy is that of the forward form.  The
+   tensor forms need the precision in grace_precompute's mask before the batch was
+   bound.  Batches of one group without per-cell kernel parameters only.  The paper
+   has no adjoint; this and the next three calls differentiate its scheme. */
 GRACE_API grace_status grace_rhs_jvp(grace_batch *batch, const double *g, const double *v, double *Jv, int precision);
 
-/* Adjoint RHS: w = (dL/dg)(g)^T lambda.  g, lambda, w: device.  GRACE_FP64 only. */
+/* Adjoint RHS: w = (dL/dg)(g)^T lambda = sum_r mu_r (T_r + T_r^T) g, mu = D^T lambda.
+   g, lambda, w: device.  GRACE_TF32 / GRACE_BF16X3 contract tiles of T_r + T_r^T on
+   the tensor cores (built, with the call's workspaces, on the first such call of a
+   batch, which then allocates and synchronises). */
 GRACE_API grace_status grace_rhs_vjp(grace_batch *batch, const double *g, const double *lambda, double *w,
                                      int precision);
 
@@ -211,7 +219,10 @@ GRACE_API grace_status grace_param_grad_setup(grace_ctx *ctx, int group, int n_p
    every ckpt_every steps and recomputes the stage states of one segment at a
    time.  g0, dt, lambda_T, lambda_0, dtheta: device.  The workspace
    (checkpoints + one segment's stage states + adjoint vectors) is allocated on
-   first use and kept with the batch; that call synchronises.  GRACE_FP64 only. */
+   first use and kept with the batch; that call synchronises.  With GRACE_TF32 /
+   GRACE_BF16X3 the forward sweep and its recomputation run in that tensor form and
+   every stage's VJP uses grace_rhs_vjp's tensor form; the limiter and parameter terms
+   stay FP64. */
 GRACE_API grace_status grace_adjoint(grace_batch *batch, const double *g0, const double *dt, int n_steps,
                                      int ckpt_every, const double *lambda_T, double *lambda_0, double *dtheta,
                                      int precision);

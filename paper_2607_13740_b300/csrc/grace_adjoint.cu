@@ -10,11 +10,23 @@
 // the minimiser.  The SSP-RK3 stages (eq. RK3) are reversed exactly, with the
 // stage states recomputed from checkpoints.  Parameter gradients contract
 // mu with g^T (dT_r / dtheta) g, where dT/dtheta is a central difference of the
-// FP64 precompute.  This is the FP64 (CUDA-core) adjoint.
+// FP64 precompute.
+//
+// Forms: FP64 on the CUDA cores, and TF32 / BF16x3 on the tensor cores.  The
+// tensor-form JVP uses polarization, exact for a quadratic form:
+//     J(g) v = [L(g + eps v) - L(g - eps v)] / (2 eps)
+// with eps a power of two per cell that brings v to the size of g (so the two
+// contractions do not cancel), i.e. two forward contractions of grace_tc.cu.  The
+// tensor-form VJP contracts the window-major tiles of S_r = T_r + T_r^T (one MMA
+// per tile, Y = Shat ghat) and sums mu_r Y in the epilogue; mu is scaled per cell
+// by a power of two into FP32.  The adjoint's own forward sweep then runs the
+// tensor form too, so that the reverse sweep differentiates the trajectory it
+// recomputes.
 #include <string>
 #include <vector>
 
 #include "grace_physics.cuh"
+#include "grace_tc_layout.cuh"
 
 namespace grace {
 
@@ -223,6 +235,91 @@ __global__ void param_dot_kernel(int R, int n_cells, const double *mu, const dou
     dtheta[(size_t)cell * n_params + ip] += w * dt[cell] * s;
 }
 
+// ------------------------------------------------------------------ tensor-form pieces
+__device__ __forceinline__ double warp_max(double x)
+{
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// mu (FP64 [cell][R]) -> mu * 2^-e in FP32, [tile][R][128] layout, with 2^e per cell so that
+// the largest |mu| of the cell lies in [0.5, 1); one warp per cell
+__global__ void mu_to_f32_kernel(int R, int n_cells, const double *__restrict__ mu, float *__restrict__ mu32,
+                                 double *__restrict__ inv_scale)
+{
+    const long long cell = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= n_cells) return;
+    const double *m = mu + cell * R;
+    double mx = 0.0;
+    for (int r = lane; r < R; r += 32) mx = fmax(mx, fabs(m[r]));
+    mx = warp_max(mx);
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    const double sc = ldexp(1.0, -e);
+    const long long ct = cell / kTileM;
+    const int row = (int)(cell - ct * kTileM);
+    for (int r = lane; r < R; r += 32) mu32[((size_t)ct * R + r) * kTileM + row] = (float)(m[r] * sc);
+    if (lane == 0) inv_scale[cell] = ldexp(1.0, e);
+}
+
+// w[cell][p] = 2^e h_bin(p) (W0 + W1)[p]: the two epilogue planes of the VJP contraction, unscaled
+__global__ void vjp_combine_kernel(DevGroup G, int Pw, int n_cells, const float *__restrict__ W,
+                                   const double *__restrict__ inv_scale, double *__restrict__ w)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_cells * G.P) return;
+    const long long cell = t / G.P;
+    const int p = (int)(t - cell * G.P);
+    const long long ct = cell / kTileM, tiles = (n_cells + kTileM - 1) / kTileM;
+    const int row = (int)(cell - ct * kTileM);
+    const float s0 = W[((size_t)ct * Pw + p) * kTileM + row];
+    const float s1 = W[(((size_t)tiles + ct) * Pw + p) * kTileM + row];
+    w[t] = inv_scale[cell] * G.hbin[p / G.K1] * ((double)s0 + (double)s1);
+}
+
+// a = g + eps v, b = g - eps v with eps = 2^(e_g - e_v) per cell (e: binary exponents of the
+// largest |g| and |v|), one warp per cell
+__global__ void polar_kernel(int P, int n_cells, const double *__restrict__ g, const double *__restrict__ v,
+                             double *__restrict__ a, double *__restrict__ b, double *__restrict__ eps)
+{
+    const long long cell = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= n_cells) return;
+    const double *gc = g + cell * P, *vc = v + cell * P;
+    double mg = 0.0, mv = 0.0;
+    for (int q = lane; q < P; q += 32) {
+        mg = fmax(mg, fabs(gc[q]));
+        mv = fmax(mv, fabs(vc[q]));
+    }
+    mg = warp_max(mg);
+    mv = warp_max(mv);
+    int eg = 0, ev = 0;
+    if (mg > 0.0 && isfinite(mg)) frexp(mg, &eg);
+    if (mv > 0.0 && isfinite(mv)) frexp(mv, &ev);
+    const double ep = ldexp(1.0, eg - ev);
+    for (int q = lane; q < P; q += 32) {
+        a[cell * P + q] = fma(ep, vc[q], gc[q]);
+        b[cell * P + q] = fma(-ep, vc[q], gc[q]);
+    }
+    if (lane == 0) eps[cell] = ep;
+}
+
+// dF[cell][r] (+)= sign F32[tile][r][row] / (2 eps[cell])
+__global__ void polar_accumulate_kernel(int R, int n_cells, const float *__restrict__ F32,
+                                        const double *__restrict__ eps, double sign, int accumulate,
+                                        double *__restrict__ dF)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_cells * R) return;
+    const long long cell = t / R;
+    const int r = (int)(t - cell * R);
+    const long long ct = cell / kTileM;
+    const int row = (int)(cell - ct * kTileM);
+    const double v = sign * (double)F32[((size_t)ct * R + r) * kTileM + row] / (2.0 * eps[cell]);
+    dF[t] = accumulate ? dF[t] + v : v;
+}
+
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 size_t warp_tile_smem(int P, int arrays, int *wpb)
@@ -337,6 +434,122 @@ grace_status single_part(grace_batch *b, const char *who)
     return GRACE_OK;
 }
 
+// tensor forms: the precision's tiles (forward, and VJP tiles built on first use) and the
+// workspaces of this file (VJP planes, FP32 mu, per-cell scales), allocated on first use
+grace_status prepare_tc(grace_batch *b, int prec, bool vjp, const char *who)
+{
+    if (prec != GRACE_TF32 && prec != GRACE_BF16X3) {
+        set_error(std::string(who) + ": unknown precision");
+        return GRACE_ERR_ARG;
+    }
+    Group &G = b->ctx->groups[b->parts[0].group];
+    Part &p = b->parts[0];
+    if (!G.tc[prec].built || !p.d_opA) {
+        set_error(std::string(who) + ": precision not precomputed: pass its bit to grace_precompute before binding the batch");
+        return GRACE_ERR_ORDER;
+    }
+    if (vjp && !G.tcv[prec].built) {
+        grace_status s = build_vjp_tiles(G, prec, b->ctx->stream);
+        if (s != GRACE_OK) return s;
+    }
+    const size_t tiles = ((size_t)p.n + kTileM - 1) / kTileM;
+    cudaError_t e = cudaSuccess;
+    if (!p.d_W32) e = cudaMalloc(&p.d_W32, 2 * tiles * vjp_window_cols(G.dg) * kTileM * sizeof(float));
+    if (e == cudaSuccess && !p.d_mu32) e = cudaMalloc(&p.d_mu32, tiles * G.dg.R * kTileM * sizeof(float));
+    if (e == cudaSuccess && !p.d_cscale) e = cudaMalloc(&p.d_cscale, (size_t)p.n * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string(who) + ": workspace allocation failed");
+        return GRACE_ERR_NOMEM;
+    }
+    return GRACE_OK;
+}
+
+// J(g) v in a tensor form by polarization, into Jv
+cudaError_t jvp_tc(grace_batch *b, int prec, const double *g, const double *v, double *Jv, cudaStream_t st)
+{
+    Group &G = b->ctx->groups[b->parts[0].group];
+    Part &p = b->parts[0];
+    const DevGroup &dg = G.dg;
+    const int n = p.n;
+    polar_kernel<<<blocks((long long)n * 32, 256), 256, 0, st>>>(dg.P, n, g, v, p.d_g1, p.d_g2, p.d_cscale);
+    cudaError_t e = cudaGetLastError();
+    const double *src[2] = {p.d_g1, p.d_g2};
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = launch_pack_A(dg, src[k], n, p.d_opA, prec, G.tc[prec].k_pad, st);
+        if (e == cudaSuccess) e = launch_contract_tc(dg, G.tc[prec], prec, p.d_opA, n, p.d_F32, b->d_err, st);
+        if (e == cudaSuccess) {
+            polar_accumulate_kernel<<<blocks((long long)n * dg.R, 256), 256, 0, st>>>(
+                dg.R, n, p.d_F32, p.d_cscale, k == 0 ? 1.0 : -1.0, k, p.d_F);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) {
+        UpdateArgs u;
+        u.F = p.d_F;
+        u.gout = Jv;
+        e = launch_update(dg, u, n, st);
+    }
+    return e;
+}
+
+// J(gs)^T lambda in a tensor form, into w; leaves mu = D^T lambda (FP64) in the part's d_F
+cudaError_t vjp_tc(grace_batch *b, int prec, const double *gs, const double *lambda, double *w, cudaStream_t st)
+{
+    Group &G = b->ctx->groups[b->parts[0].group];
+    Part &p = b->parts[0];
+    const DevGroup &dg = G.dg;
+    const int n = p.n;
+    const size_t tiles = ((size_t)n + kTileM - 1) / kTileM;
+    cudaError_t e = launch_mu(dg, lambda, n, p.d_F, st);
+    if (e == cudaSuccess) {
+        mu_to_f32_kernel<<<blocks((long long)n * 32, 256), 256, 0, st>>>(dg.R, n, p.d_F, p.d_mu32, p.d_cscale);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_pack_A(dg, gs, n, p.d_opA, prec, G.tc[prec].k_pad, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(p.d_W32, 0, 2 * tiles * vjp_window_cols(dg) * kTileM * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_vjp_tc(dg, G.tcv[prec], prec, p.d_opA, p.d_mu32, n, p.d_W32, b->d_err, st);
+    if (e == cudaSuccess) {
+        vjp_combine_kernel<<<blocks((long long)n * dg.P, 256), 256, 0, st>>>(dg, vjp_window_cols(dg), n, p.d_W32,
+                                                                              p.d_cscale, w);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// one forward SSP-RK3 step in a tensor form (FP64 stage rows, FP32 higher modes as in grace_step)
+cudaError_t fwd_step_tc(grace_batch *b, int prec, const double *pre, double *gt, double *g1, double *g2,
+                        double *next, const double *dt)
+{
+    Group &G = b->ctx->groups[0];
+    const DevGroup &dg = G.dg;
+    Part &p = b->parts[0];
+    cudaStream_t st = b->ctx->stream;
+    const int n = b->n_cells;
+    const size_t bytes = (size_t)n * dg.P * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(gt, pre, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && dg.limiter) e = launch_limit(dg, gt, n, nullptr, nullptr, 0, 0, st);
+    const double *gin[3] = {gt, g1, g2};
+    double *gout[3] = {g1, g2, next};
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
+        e = launch_pack_A(dg, gin[s], n, p.d_opA, prec, G.tc[prec].k_pad, st);
+        if (e == cudaSuccess) e = launch_contract_tc(dg, G.tc[prec], prec, p.d_opA, n, p.d_F32, b->d_err, st);
+        if (e != cudaSuccess) break;
+        UpdateArgs u;
+        u.F32 = p.d_F32;
+        u.gn = gt;
+        u.gs = gin[s];
+        u.gout = gout[s];
+        u.dt = dt;
+        u.a = ca[s];
+        u.b = cb[s];
+        e = launch_update_tc(dg, u, n, st);
+    }
+    return e;
+}
+
 // one forward SSP-RK3 step in FP64 that keeps the stage states:
 // pre -> gt (limited) -> g1 -> g2 -> next
 cudaError_t fwd_step(grace_batch *b, const double *pre, double *gt, double *g1, double *g2, double *next,
@@ -382,13 +595,15 @@ grace_status grace_rhs_jvp(grace_batch *b, const double *g, const double *v, dou
         set_error("grace_rhs_jvp: null argument");
         return GRACE_ERR_ARG;
     }
-    if (precision != GRACE_FP64) {
-        set_error("grace_rhs_jvp: only GRACE_FP64 is implemented");
-        return GRACE_ERR_UNSUPPORTED;
-    }
     grace_status sp = single_part(b, "grace_rhs_jvp");
     if (sp != GRACE_OK) return sp;
     Guard guard(b->ctx->device);
+    if (precision != GRACE_FP64) {
+        sp = prepare_tc(b, precision, false, "grace_rhs_jvp");
+        if (sp != GRACE_OK) return sp;
+        cudaError_t e = jvp_tc(b, precision, g, v, Jv, b->ctx->stream);
+        return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_jvp");
+    }
     Group &G = b->ctx->groups[0];
     cudaStream_t st = b->ctx->stream;
     double *dF = b->parts[0].d_F;
@@ -408,13 +623,15 @@ grace_status grace_rhs_vjp(grace_batch *b, const double *g, const double *lambda
         set_error("grace_rhs_vjp: null argument");
         return GRACE_ERR_ARG;
     }
-    if (precision != GRACE_FP64) {
-        set_error("grace_rhs_vjp: only GRACE_FP64 is implemented");
-        return GRACE_ERR_UNSUPPORTED;
-    }
     grace_status sp = single_part(b, "grace_rhs_vjp");
     if (sp != GRACE_OK) return sp;
     Guard guard(b->ctx->device);
+    if (precision != GRACE_FP64) {
+        sp = prepare_tc(b, precision, true, "grace_rhs_vjp");
+        if (sp != GRACE_OK) return sp;
+        cudaError_t e = vjp_tc(b, precision, g, lambda, w, b->ctx->stream);
+        return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_vjp");
+    }
     Group &G = b->ctx->groups[0];
     cudaError_t e = launch_vjp(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, lambda, b->parts[0].d_F, b->n_cells, w,
                                b->ctx->stream);
@@ -491,13 +708,14 @@ grace_status grace_adjoint(grace_batch *b, const double *g0, const double *dt, i
         set_error("grace_adjoint: null argument, negative step count or ckpt_every < 1");
         return GRACE_ERR_ARG;
     }
-    if (precision != GRACE_FP64) {
-        set_error("grace_adjoint: only GRACE_FP64 is implemented");
-        return GRACE_ERR_UNSUPPORTED;
-    }
     grace_status sp = single_part(b, "grace_adjoint");
     if (sp != GRACE_OK) return sp;
     Guard guard(b->ctx->device);
+    const bool tc = precision != GRACE_FP64;
+    if (tc) {
+        sp = prepare_tc(b, precision, true, "grace_adjoint");
+        if (sp != GRACE_OK) return sp;
+    }
     Group &G = b->ctx->groups[0];
     const DevGroup &dg = G.dg;
     cudaStream_t st = b->ctx->stream;
@@ -534,12 +752,15 @@ grace_status grace_adjoint(grace_batch *b, const double *g0, const double *dt, i
     if (e == cudaSuccess) e = cudaMemcpyAsync(cur, g0, bytes, cudaMemcpyDeviceToDevice, st);
     for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
         if (s % ckpt_every == 0) e = cudaMemcpyAsync(ck + vec * (s / ckpt_every), cur, bytes, cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) e = fwd_step(b, cur, seg, seg + vec, seg + 2 * vec, cur, dt);
+        if (e == cudaSuccess)
+            e = tc ? fwd_step_tc(b, precision, cur, seg, seg + vec, seg + 2 * vec, cur, dt)
+                   : fwd_step(b, cur, seg, seg + vec, seg + 2 * vec, cur, dt);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(lam, lambda_T, bytes, cudaMemcpyDeviceToDevice, st);
 
     auto vjp_at = [&](const double *gs, const double *l, double *out) {
-        return launch_vjp(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gs, l, dF, n, out, st);
+        return tc ? vjp_tc(b, precision, gs, l, out, st)
+                  : launch_vjp(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gs, l, dF, n, out, st);
     };
     // dtheta += w dt mu(l) . g^T dT g (mu of the last vjp is in b->d_F)
     auto param_terms = [&](const double *gs, double w) {
@@ -559,7 +780,9 @@ grace_status grace_adjoint(grace_batch *b, const double *g0, const double *dt, i
         for (int s = s0; s < s1 && e == cudaSuccess; ++s) {
             double *S = seg + vec * 4 * (s - s0);
             e = cudaMemcpyAsync(S, cur, bytes, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess) e = fwd_step(b, S, S + vec, S + 2 * vec, S + 3 * vec, cur, dt);
+            if (e == cudaSuccess)
+                e = tc ? fwd_step_tc(b, precision, S, S + vec, S + 2 * vec, S + 3 * vec, cur, dt)
+                       : fwd_step(b, S, S + vec, S + 2 * vec, S + 3 * vec, cur, dt);
         }
         for (int s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
             const double *S = seg + vec * 4 * (s - s0);

@@ -75,6 +75,9 @@ void free_part(Part &p)
     cudaFree(p.d_H);
     cudaFree(p.d_gh);
     cudaFree(p.d_s);
+    cudaFree(p.d_W32);
+    cudaFree(p.d_mu32);
+    cudaFree(p.d_cscale);
     if (p.stream) cudaStreamDestroy(p.stream);
     if (p.done) cudaEventDestroy(p.done);
     p = Part();

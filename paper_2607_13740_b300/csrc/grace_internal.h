@@ -53,6 +53,7 @@ struct TcTiles {
     int n_d0 = 0;
     float ramp_a = 0.f, ramp_b = 0.f;   // pf(z) = clamp(ramp_a z + ramp_b, 0, 1), z = s D0
     int *d_written = nullptr;      // [R] 1 where the contraction writes the functional
+    int vjp = 0;                   // window-major tiles of T + T^T for the VJP (launch_vjp_tc)
 };
 
 // Node-space tables of a group with a per-cell kernel parameter (grace_ncell.cu)
@@ -90,6 +91,7 @@ struct Group {
     int *d_prange = nullptr;      // [R][2] p range with non-empty rows
     long long nnz = 0;            // structural non-zeros of T (all rows)
     TcTiles tc[3];                // indexed by grace_precision
+    TcTiles tcv[3];               // VJP tiles (built on the first tensor-form VJP / adjoint call)
     NcTables nc;                  // cell_alpha groups: node-space tables instead of T
     std::vector<ParamDeriv> dparams;
 };
@@ -137,6 +139,9 @@ struct Part {
     double *d_G = nullptr, *d_H = nullptr;   // [n][NQ], [2][n][NQ] nodal values (cell_alpha groups)
     float *d_gh = nullptr;         // [tiles][P][128] scaled coefficients (cell_alpha groups, tensor forms)
     float *d_s = nullptr;          // [n] sqrt(alpha) in FP32 (cell_alpha groups, tensor forms)
+    float *d_W32 = nullptr;        // tensor-form VJP: two output planes [2][tiles][Pw][128]
+    float *d_mu32 = nullptr;       // tensor-form VJP: mu in FP32, [tiles][R][128]
+    double *d_cscale = nullptr;    // tensor-form JVP / VJP: per-cell power-of-two scales
     size_t opA_bytes = 0;
     cudaStream_t stream = nullptr; // own stream for concurrent parts (null: the context's)
     cudaEvent_t done = nullptr;
@@ -297,6 +302,13 @@ cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const Tc
 // tensor-core path
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);
 grace_status build_nc_tc_tiles(Group &G, int prec, cudaStream_t st);
+grace_status build_vjp_tiles(Group &G, int prec, cudaStream_t st);
+// VJP contraction: W[part][tile][Pw][128] (two partial planes, FP32) with
+// W = sum_r mu_r (Shat_r ghat) per cell, mu in the [tile][R][128] layout (FP32)
+cudaError_t launch_vjp_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, const float *d_mu32,
+                          int n_cells, float *d_W32, int *d_err, cudaStream_t st);
+// coefficient columns of the VJP output planes (P rounded up to the 16-wide windows)
+inline int vjp_window_cols(const DevGroup &g) { return (g.P + 15) / 16 * 16; }
 void free_tc_tiles(TcTiles &t);
 size_t opA_bytes_for(const DevGroup &g, int prec, int n_cells, int *kpad);
 

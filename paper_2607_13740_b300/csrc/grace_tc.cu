@@ -112,7 +112,15 @@ struct TcParams {
     int n_d0;
     const float *cell_s;  // [n_cells] s = sqrt(alpha)
     float ramp_a, ramp_b;
+    // VJP tiles: functional weights mu in the [tile][R][128] layout, output planes
+    // W[part][tile][Pw][128] (one per epilogue warp of a lane quadrant)
+    const float *mu;
+    float *W;
+    int Pw;
 };
+
+// contraction modes: flux functionals, node-space functionals (per-cell kernels), VJP
+constexpr int kModeF = 0, kModeNC = 1, kModeVJP = 2;
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -379,7 +387,40 @@ __device__ __forceinline__ void epi_tile_nc(const uint8_t *a_gen, long long a_ti
     }
 }
 
-template <int PREC, bool NC>
+// Epilogue of a VJP tile (window-major tiles of S_r = T_r + T_r^T): accumulator columns
+// [16 f, 16 f + 16) of functional f hold (S_r ghat)_p for the window's 16 coefficients p; the
+// functional's weight mu_r times them is added to the window accumulator Wacc.
+template <int G>
+__device__ __forceinline__ void epi_tile_vjp(uint32_t tcol, int nf, int part, const float *mu_cell, const int *ford,
+                                             int f0, float *Wacc)
+{
+#pragma unroll
+    for (int m0 = 0; m0 < kEpiF; m0 += G) {
+        if (kEpiSplit * m0 + part >= nf) break;
+        uint32_t y[G][kWin];
+        float mu[G];
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+            const int f = kEpiSplit * (m0 + gg) + part;
+            mu[gg] = 0.f;
+            if (f < nf) {
+                tmem_ld16(tcol + (uint32_t)(f * kWin), y[gg]);
+                mu[gg] = mu_cell[(size_t)ford[f0 + f] * kTileM];
+            }
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+            const int f = kEpiSplit * (m0 + gg) + part;
+            if (f < nf) {
+#pragma unroll
+                for (int t = 0; t < kWin; ++t) Wacc[t] = fmaf(mu[gg], __uint_as_float(y[gg][t]), Wacc[t]);
+            }
+        }
+    }
+}
+
+template <int PREC, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 {
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
@@ -426,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         for (int i = threadIdx.x; i < P.n_tiles * (int)(sizeof(TileDesc) / 16); i += blockDim.x) dst[i] = src[i];
         int *fo = const_cast<int *>(ford);
         for (int i = threadIdx.x; i < P.R; i += blockDim.x) fo[i] = P.ford[i];
-        if (NC) {
+        if (MODE == kModeNC) {
             float *d0 = const_cast<float *>(D0s);
             for (int i = threadIdx.x; i < P.n_d0; i += blockDim.x) d0[i] = P.D0[i];
         }
@@ -590,10 +631,14 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             const uint8_t *a_gen = gbase + (size_t)ab * P.a_tile_bytes;
             const long long cell = (long long)ct * kTileM + row;
             const bool live = cell < P.n_cells;
-            const float s_cell = NC && live ? P.cell_s[cell] : 0.f;
+            const float s_cell = MODE == kModeNC && live ? P.cell_s[cell] : 0.f;
+            const float *mu_cell = MODE == kModeVJP ? P.mu + (size_t)ct * P.R * kTileM + row : nullptr;
             float Facc[kEpiF];
 #pragma unroll
             for (int m = 0; m < kEpiF; ++m) Facc[m] = 0.f;
+            float Wacc[MODE == kModeVJP ? kWin : 1];
+#pragma unroll
+            for (int t = 0; t < (MODE == kModeVJP ? kWin : 1); ++t) Wacc[t] = 0.f;
             bool aborted = false;
             for (int t = P.split[sp]; t < P.split[sp + 1]; ++t) {
                 if (__any_sync(0xffffffffu, *abort_flag)) {
@@ -610,16 +655,27 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 }
                 tc_fence_after();
                 const uint32_t tcol = tmem + tlane + (uint32_t)(buf * kAccCols);
-                if (NC)
+                if (MODE == kModeNC)
                     epi_tile_nc<PREC, 2>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, s_cell, D0s, P.ramp_a,
                                          P.ramp_b, Facc);
+                else if (MODE == kModeVJP)
+                    epi_tile_vjp<4>(tcol, nf, part, mu_cell, ford, td.f0, Wacc);
                 else
                     epi_tile<PREC, kWin, kEpiF>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, Facc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&S->acc_empty[buf]));
                 ++acc_use;
-                if (td.nf_flush >> 16) {
+                if (MODE == kModeVJP && (td.nf_flush >> 16)) {
+                    // last tile of this coefficient window: this warp's partial sums over its functionals
+                    if (live) {
+                        float *Wo = P.W + (((size_t)part * P.n_cell_tiles + ct) * P.Pw + td.p0) * kTileM + row;
+#pragma unroll
+                        for (int t = 0; t < (MODE == kModeVJP ? kWin : 1); ++t) Wo[(size_t)t * kTileM] = Wacc[t];
+                    }
+#pragma unroll
+                    for (int t = 0; t < (MODE == kModeVJP ? kWin : 1); ++t) Wacc[t] = 0.f;
+                } else if (MODE != kModeVJP && (td.nf_flush >> 16)) {
                     if (live) {
                         float *Fo = P.F + ((size_t)ct * P.R) * kTileM + row;
 #pragma unroll
@@ -816,7 +872,7 @@ Plan plan_forms(const Forms &F, const std::vector<int> &ford, int prec)
 // B images (SWIZZLE_32B k-step blocks, bf16 hi/lo planes or TF32) and tile descriptors of a
 // plan, uploaded into out; written[r] = 1 for every functional the contraction writes
 grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &ford, int prec, TcTiles &out,
-                        std::vector<int> &written)
+                        std::vector<int> &written, bool window_major = false)
 {
     const int R = F.R, W = F.W, nw = F.n_win();
     const int eb = elem_bytes(prec), planes = n_planes(prec);
@@ -824,6 +880,8 @@ grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &
     const int kps = prec == GRACE_TF32 ? 4 : 2;
     const int mult = prec == GRACE_TF32 ? 1 : 3;
     std::vector<TileDesc> tiles;
+    std::vector<int> tile_win;        // window of every tile
+    std::vector<double> tile_cost_v;  // cost-model cycles of every tile
     std::vector<uint8_t> B;
     written.assign(R, 0);
     long long macs = 0, mmas = 0;
@@ -885,6 +943,8 @@ grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &
             out.slot_bytes = std::max(out.slot_bytes, (int)(std::min(kps, nks) * blk * planes));
             out.max_rows = std::max(out.max_rows, n);
             tiles.push_back(td);
+            tile_win.push_back(w);
+            tile_cost_v.push_back(tile_cost(prec, n, nks));
         }
         if (tiles.size() > first) {
             tiles.back().nf_flush |= 1 << 16;
@@ -896,6 +956,30 @@ grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &
     if (tiles.empty()) {
         set_error("tensor-core tiles: the coefficient tensor is empty");
         return GRACE_ERR_ARG;
+    }
+    if (window_major) {
+        // VJP order: all tiles of coefficient window 0, then window 1, ...; the last tile of every
+        // window flushes the window's partial sums; splits fall on window boundaries
+        std::vector<int> idx(tiles.size());
+        for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return tile_win[a] < tile_win[b]; });
+        std::vector<TileDesc> sorted;
+        out.group_tile.clear();
+        out.group_cost.clear();
+        for (size_t i = 0; i < idx.size(); ++i) {
+            TileDesc td = tiles[idx[i]];
+            td.nf_flush &= 0xFFFF;
+            const bool first = i == 0 || tile_win[idx[i]] != tile_win[idx[i - 1]];
+            const bool last = i + 1 == idx.size() || tile_win[idx[i]] != tile_win[idx[i + 1]];
+            if (first) {
+                out.group_tile.push_back((int)sorted.size());
+                out.group_cost.push_back(0.0);
+            }
+            out.group_cost.back() += tile_cost_v[idx[i]];
+            if (last) td.nf_flush |= 1 << 16;
+            sorted.push_back(td);
+        }
+        tiles.swap(sorted);
     }
     if (B.size() / 16 > (size_t)INT32_MAX) {
         set_error("tensor-core tiles: B images too large");
@@ -1000,6 +1084,51 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
     out.built = 1;
     free_tc_tiles(G.tc[prec]);
     G.tc[prec] = out;
+    return GRACE_OK;
+}
+
+// Tensor-core tiles of the VJP: the symmetric S_r = T_r + T_r^T (full, scaled by
+// 1 / (h_bin(p) h_bin(q))), so that the MMA gives Y[c, (r, p)] = sum_q Shat_r[p, q] ghat_q and the
+// epilogue sums mu_r Y over the functionals of each 16-wide window of p (window-major order).
+grace_status build_vjp_tiles(Group &G, int prec, cudaStream_t st)
+{
+    const DevGroup &g = G.dg;
+    if (g.k > kKMax) {
+        set_error("tensor-core tiles need k <= 3");
+        return GRACE_ERR_UNSUPPORTED;
+    }
+    const int P_ = g.P, R = g.R, K1 = g.K1;
+    Forms F;
+    F.R = R;
+    F.rows = P_;
+    F.kdim = P_;
+    F.W = kWin;
+    F.p0_stride = kWin;
+    std::vector<double> T((size_t)R * P_ * P_);
+    cudaError_t e = cudaMemcpyAsync(T.data(), G.d_T, T.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "VJP tiles: copy T");
+    std::vector<double> h(g.N);
+    for (int j = 0; j < g.N; ++j) h[j] = G.h_edges[j + 1] - G.h_edges[j];
+    F.M.resize(T.size());
+    for (int r = 0; r < R; ++r)
+        for (int p = 0; p < P_; ++p)
+            for (int q = 0; q < P_; ++q) {
+                const size_t i = ((size_t)r * P_ + p) * P_ + q, it = ((size_t)r * P_ + q) * P_ + p;
+                F.M[i] = (T[i] + T[it]) / (h[p / K1] * h[q / K1]);
+            }
+    const std::vector<int> ford = functional_order(g);
+    const Plan pl = plan_forms(F, ford, prec);
+    TcTiles out;
+    std::vector<int> written;
+    grace_status s = emit_tiles(F, pl, ford, prec, out, written, true);
+    if (s != GRACE_OK) return s;
+    const int ae = atom_elems(prec);
+    out.k_pad = (P_ + ae - 1) / ae * ae;
+    out.vjp = 1;
+    out.built = 1;
+    free_tc_tiles(G.tcv[prec]);
+    G.tcv[prec] = out;
     return GRACE_OK;
 }
 
@@ -1124,12 +1253,12 @@ static void choose_splits(const TcTiles &t, int n_cell_tiles, int n_sm, TcParams
     P.n_splits = ns;
 }
 
-template <int PREC, bool NC>
+template <int PREC, int MODE>
 static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
 {
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
     P.table_bytes = (int)((P.n_tiles * sizeof(TileDesc) + (size_t)P.R * sizeof(int) +
-                           (NC ? (size_t)P.n_d0 * sizeof(float) : 0) + 15) / 16 * 16);
+                           (MODE == kModeNC ? (size_t)P.n_d0 * sizeof(float) : 0) + 15) / 16 * 16);
     const size_t fixed = 1024 + (size_t)P.table_bytes + sizeof(Smem) + 64;
     const size_t a1 = (size_t)P.a_tile_bytes;
     // Shared-memory plan: 32 KB B copies at N = 256 (fewer k-steps per copy for groups whose A tile
@@ -1144,13 +1273,13 @@ static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
     P.a_bufs = fixed + 2 * a1 + 4 * (size_t)P.slot_bytes <= (size_t)kSmemLimit ? 2 : 1;
     P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed - P.a_bufs * a1) / P.slot_bytes);
     const size_t smem = fixed + P.a_bufs * a1 + (size_t)P.n_slots * P.slot_bytes;
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     const int items = P.n_cell_tiles * P.n_splits;
     const int grid = std::min(items, sm_count(dev));
-    contract_tc_kernel<PREC, NC><<<grid, kThreads, smem, st>>>(P);
+    contract_tc_kernel<PREC, MODE><<<grid, kThreads, smem, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -1181,11 +1310,37 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
         P.cell_s = d_cell_s;
         P.ramp_a = t.ramp_a;
         P.ramp_b = t.ramp_b;
-        return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, true>(P, t.max_rows, st)
-                                  : launch_prec<GRACE_BF16X3, true>(P, t.max_rows, st);
+        return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeNC>(P, t.max_rows, st)
+                                  : launch_prec<GRACE_BF16X3, kModeNC>(P, t.max_rows, st);
     }
-    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, false>(P, t.max_rows, st)
-                              : launch_prec<GRACE_BF16X3, false>(P, t.max_rows, st);
+    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeF>(P, t.max_rows, st)
+                              : launch_prec<GRACE_BF16X3, kModeF>(P, t.max_rows, st);
+}
+
+cudaError_t launch_vjp_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, const float *d_mu32,
+                          int n_cells, float *d_W32, int *d_err, cudaStream_t st)
+{
+    if (!t.built || !t.vjp || n_cells <= 0) return n_cells == 0 ? cudaSuccess : cudaErrorInvalidValue;
+    TcParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.tiles = (const TileDesc *)t.d_desc;
+    P.ford = t.d_ford;
+    P.n_tiles = t.n_tiles;
+    P.B = (const uint8_t *)t.d_b;
+    P.A = (const uint8_t *)opA;
+    P.a_tile_bytes = (long long)opA_tile_bytes(prec, t.k_pad);
+    P.n_cells = n_cells;
+    P.n_cell_tiles = (n_cells + kTileM - 1) / kTileM;
+    P.R = g.R;
+    P.err = d_err;
+    P.mu = d_mu32;
+    P.W = d_W32;
+    P.Pw = vjp_window_cols(g);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
+    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeVJP>(P, t.max_rows, st)
+                              : launch_prec<GRACE_BF16X3, kModeVJP>(P, t.max_rows, st);
 }
 
 }  // namespace grace

@@ -1,4 +1,4 @@
-"""Tangent-linear and adjoint of the RHS and of the SSP-RK3 trajectory (FP64).
+"""Tangent-linear and adjoint of the RHS and of the SSP-RK3 trajectory (FP64 and tensor forms).
 
 Pins: L is a quadratic form, so (L(g+v) - L(g-v))/2 = J(g) v exactly; the
 oracle supplies that exact directional derivative.  The VJP is checked by the
@@ -6,6 +6,16 @@ dot-product identity against the JVP; the trajectory adjoint against central
 differences of oracle trajectories (the FP64 reference gradient) and against
 torch.autograd.gradcheck; parameter gradients against central differences of
 oracle trajectories in the parameter.
+
+Tensor forms (TF32, BF16x3), with the forward bars of R15 (TOL = 2e-3 / 5e-5 of the
+oracle's term-magnitude scale S):
+  JVP   = [L(g + eps v) - L(g - eps v)] / (2 eps), eps a power of two per cell: each forward
+          is within TOL S of the oracle, so the JVP is within TOL (S+ + S-) / (2 eps).
+  VJP   component p against the oracle's lambda . J (s e_p) / s (exact by polarization), within
+          TOL sum_j |lambda_j| (S+ + S-)_j / (2 s), an upper bound of the rounding of
+          sum_r |mu_r| sum_q |(T_r + T_r^T)[p, q] g_q|.
+  trajectory adjoint: within 36 TOL of max |directional derivative| (12 steps x 3 stages of
+          per-RHS error, accumulated linearly).
 """
 import numpy as np
 import pytest
@@ -139,3 +149,100 @@ def test_autograd_function_gradcheck():
     dt = torch.full((1,), 0.05, dtype=torch.float64, device=DEV)
     f = lambda g: grace.step_autograd(g, b, dt, 3, 2)
     assert torch.autograd.gradcheck(f, (g0,), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+# ------------------------------------------------------------------ tensor forms
+TOL_RHS = {grace.TF32: 2e-3, grace.BF16X3: 5e-5}
+RANGE_FLOOR = 1e-24
+FORMS = [grace.TF32, grace.BF16X3]
+IDS = ["tf32", "bf16x3"]
+
+
+def _tc_ctx(spec):
+    return grace.Context([spec], 0, precisions=(grace.FP64, grace.TF32, grace.BF16X3))
+
+
+def _pow2(x):
+    """2^e with e the binary exponent of x (x = f 2^e, f in [0.5, 1)), per row."""
+    return np.ldexp(1.0, np.frexp(x)[1])
+
+
+@pytest.mark.parametrize("form", FORMS, ids=IDS)
+@pytest.mark.parametrize("name", sorted(SPECS))
+def test_jvp_tensor_forms_vs_oracle(name, form):
+    spec = SPECS[name]
+    n = 130                                   # two 128-cell tiles, the second ragged
+    g = W.random_coefficients(spec, n, seed=611)
+    v = W.random_coefficients(spec, n, seed=612) * 0.3
+    ctx = _tc_ctx(spec)
+    b = ctx.batch(n)
+    Jv = b.jvp(torch.as_tensor(g, device=DEV), torch.as_tensor(v, device=DEV), form).cpu().numpy()
+    assert np.isfinite(Jv).all()
+    eps = (_pow2(np.abs(g).max(axis=1)) / _pow2(np.abs(v).max(axis=1)))[:, None]
+    o = oracle.Oracle(spec)
+    Lp, Sp = o.rhs(g + eps * v)
+    Lm, Sm = o.rhs(g - eps * v)
+    ref = (Lp - Lm) / (2 * eps)
+    fl_p = RANGE_FLOOR * Sp.max(axis=1, keepdims=True)
+    fl_m = RANGE_FLOOR * Sm.max(axis=1, keepdims=True)
+    bound = TOL_RHS[form] * (np.maximum(Sp, fl_p) + np.maximum(Sm, fl_m)) / (2 * eps)
+    worst = (np.abs(Jv - ref) / bound).max()
+    assert worst <= 1.0, (name, worst)
+
+
+@pytest.mark.parametrize("form", FORMS, ids=IDS)
+@pytest.mark.parametrize("name", sorted(SPECS))
+def test_vjp_tensor_forms_vs_oracle_directions(name, form):
+    spec = SPECS[name]
+    n, P = 3, spec.n_coef
+    g = W.random_coefficients(spec, n, seed=613)
+    lam = np.random.default_rng(614).normal(size=(n, P))
+    ctx = _tc_ctx(spec)
+    b = ctx.batch(n)
+    w = b.vjp(torch.as_tensor(g, device=DEV), torch.as_tensor(lam, device=DEV), form).cpu().numpy()
+    assert np.isfinite(w).all()
+    o = oracle.Oracle(spec)
+    for c in range(n):
+        s = _pow2(np.abs(g[c]).max())
+        X = g[c][None, :] + s * np.eye(P)
+        Y = g[c][None, :] - s * np.eye(P)
+        Lp, Sp = o.rhs(X)
+        Lm, Sm = o.rhs(Y)
+        ref = ((Lp - Lm) / (2 * s)) @ lam[c]
+        bound = TOL_RHS[form] * ((Sp + Sm) / (2 * s)) @ np.abs(lam[c])
+        worst = (np.abs(w[c] - ref) / bound).max()
+        assert worst <= 1.0, (name, c, worst)
+
+
+@pytest.mark.parametrize("form", FORMS, ids=IDS)
+def test_trajectory_adjoint_tensor_forms_vs_oracle(form):
+    spec = W.additive_spec(12, 2, 1e-3, 1e4).replace(limiter=0)
+    n, steps, dt = 4, 12, 0.05
+    o, g0, rng = _traj_setup(spec, n, 615)
+    lamT = rng.normal(size=g0.shape)
+    v = rng.uniform(-0.1, 0.1, size=g0.shape) * g0
+    ctx = _tc_ctx(spec)
+    b = ctx.batch(n)
+    dtt = torch.full((n,), dt, dtype=torch.float64, device=DEV)
+    lam0, _ = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, torch.as_tensor(lamT, device=DEV), 4,
+                        precision=form)
+    lam0 = lam0.cpu().numpy()
+    assert np.isfinite(lam0).all()
+    eps = 1e-4
+    gp, _, _ = o.step(g0 + eps * v, dt, steps)
+    gm, _, _ = o.step(g0 - eps * v, dt, steps)
+    fd = ((gp - gm) / (2 * eps) * lamT).sum(axis=1)
+    ad = (lam0 * v).sum(axis=1)
+    err = np.abs(ad - fd).max() / np.abs(fd).max()
+    assert err <= 36 * TOL_RHS[form], (form, err, ad, fd)
+
+
+def test_tensor_form_adjoint_errors():
+    spec = SPECS["add_k2"]
+    ctx = grace.Context([spec])                 # FP64 only: no tensor tiles
+    b = ctx.batch(4)
+    g = torch.as_tensor(W.random_coefficients(spec, 4, seed=616), device=DEV)
+    with pytest.raises(grace.GraceError, match="precomputed"):
+        b.vjp(g, g, grace.TF32)
+    with pytest.raises(grace.GraceError, match="precomputed"):
+        b.jvp(g, g, grace.BF16X3)

@@ -200,7 +200,7 @@ def run_reference(args, rank):
 
 def run_disk(args):
     """Disk workload (per-cell alpha_turb, coagulation + fragmentation, N = 60): the node-space
-    path in FP64 (a bounded 2,048 cells) or in a tensor-core form (65,536 cells by default:
+    path in FP64 (a bounded 2,048 cells) or in a tensor-core form (262,144 cells by default:
     fixed pairs on tcgen05, partial entries in FP32); one JSON line like the headline's."""
     import torch
     from paper_2607_13740_b300 import grace, workloads as W
@@ -209,7 +209,7 @@ def run_disk(args):
     dev = torch.device(f"cuda:{local}")
     form = {"fp64": grace.FP64, "tf32": grace.TF32, "bf16x3": grace.BF16X3}[args.precision or "bf16x3"]
     fname = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[form]
-    n = args.cells if args.cells != 65536 or form != grace.FP64 else 2048
+    n = args.cells if args.cells != 65536 else (2048 if form == grace.FP64 else 262144)
     steps = args.steps or (3 if form == grace.FP64 else 10)
     spec, alpha, ic = W.disk_batch(n_cells=n, order_k=args.order)
     t0 = time.time()
@@ -305,6 +305,81 @@ def run_disk(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Adjoint workload: 4,096 cells of the coupled coagulation-fragmentation model (N = 40,
+    k = 2, conservative), 200 SSP-RK3 steps with a checkpoint every 10; gradient of the final
+    mass in the top 10 bins with respect to the initial coefficients, v_frag and the fragment
+    exponent.  Times grace_adjoint in the requested form (default bf16x3) next to the FP64
+    adjoint and the forward steps; one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2607_13740_b300 import grace, workloads as W
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    form = {"fp64": grace.FP64, "tf32": grace.TF32, "bf16x3": grace.BF16X3}[args.precision or "bf16x3"]
+    fname = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[form]
+    n = args.cells if args.cells != 65536 else 4096
+    steps, ckpt = args.steps or 200, 10
+    spec = W.coupled_toy_spec(40, 2, flux_mode=W.FLUX_CONSERVATIVE)
+    rng = np.random.default_rng(1005)
+    ic = np.zeros((n, 4))
+    ic[:, 0] = rng.lognormal(0.0, 0.5, n)
+    ic[:, 1] = np.exp(rng.uniform(np.log(1e-3), np.log(1.0), n))
+    ctx = grace.Context([spec], local, precisions=(grace.FP64, form) if form != grace.FP64 else (grace.FP64,))
+    ctx.param_grad_setup([9, 16])                 # frag_p[1] = v_frag, break_p[0] = fragment exponent
+    b = ctx.batch(n)
+    g0 = b.project(W.IC_EXP, ic)
+    L = b.rhs(g0).reshape(n, 40, 3)[:, :, 0]
+    m = g0.reshape(n, 40, 3)[:, :, 0]
+    ratio = torch.where(L < 0, m / (-L), torch.full_like(m, float("inf")))
+    dt = 0.2 * ratio.amin(dim=1)
+    dt = torch.where(torch.isfinite(dt), dt, torch.full_like(dt, 1e-3))
+    edges = spec.x_min * (spec.x_max / spec.x_min) ** (np.arange(41) / 40)
+    lamT = torch.zeros(n, 40, 3, dtype=torch.float64, device=dev)
+    lamT[:, 30:, 0] = torch.as_tensor(np.diff(edges)[30:], device=dev)     # J = mass in bins 30..39
+    lamT = lamT.reshape(n, -1).contiguous()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    ms_adj, (lam0, dth) = timed(lambda: b.adjoint(g0, dt, steps, lamT, ckpt, param_grads=True, precision=form))
+    sampler.__exit__(None, None, None)
+    ms_fwd, _ = timed(lambda: b.step(g0.clone(), dt, steps, form))
+    res = {"adjoint_ms": ms_adj, "forward_ms": ms_fwd, "adjoint_over_forward": ms_adj / ms_fwd}
+    if form != grace.FP64:
+        ms64, (lam64, dth64) = timed(lambda: b.adjoint(g0, dt, steps, lamT, ckpt, param_grads=True,
+                                                       precision=grace.FP64))
+        res["fp64_adjoint_ms"] = ms64
+        res["speedup_vs_fp64_adjoint"] = ms64 / ms_adj
+        res["lambda0_max_rel_err_vs_fp64"] = ((lam0 - lam64).abs().amax(dim=1) /
+                                              lam64.abs().amax(dim=1).clamp_min(1e-300)).max().item()
+        res["dtheta_max_rel_err_vs_fp64"] = ((dth - dth64).abs() / dth64.abs().clamp_min(1e-300)).max().item()
+    line = {
+        "metric": "adjoint cell-steps/s (4,096 cells, N=40, k=2, coag+frag, 200 steps, ckpt 10)",
+        "value": n * steps / (ms_adj / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 1,
+        "ms_per_step": ms_adj / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[fname], "data": "synthetic",
+        "config": {"workload": f"adjoint_{n}cells_N40_k2", "cells": n, "form": fname, "checkpoint_every": ckpt,
+                   "loss": "final mass in bins 30..39", "params": ["v_frag", "fragment exponent"],
+                   "ic": "A x exp(-x/x0), A ~ lognormal(0, 0.5), x0 ~ loguniform[1e-3, 1]",
+                   "dt": "0.2 x positivity bound at t=0"},
+        "finite": bool(torch.isfinite(lam0).all().item() and torch.isfinite(dth).all().item()),
+        "clocks": sampler.summary(), **res,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_uneven(args):
     """Uneven batch: cells of many groups (N ~ U{16..80}, k ~ U{0..3}, constant or additive
     kernel, per-cell rate scale) stepped together in the bf16x3 form, with and without CUDA-graph
@@ -376,15 +451,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--forms", default=None,
                     help="comma-separated subset of fp64,tf32,bf16x3 to time (default: all built)")
-    ap.add_argument("--workload", default="additive", choices=["additive", "disk", "uneven"],
+    ap.add_argument("--workload", default="additive", choices=["additive", "disk", "uneven", "adjoint"],
                     help="additive: the batched additive-kernel headline; disk: coagulation + fragmentation "
-                         "with a per-cell turbulence strength (node-space path, FP64)")
+                         "with a per-cell turbulence strength (node-space path); uneven: many groups in one batch; "
+                         "adjoint: checkpointed adjoint of 200 steps with parameter gradients")
     ap.add_argument("--order", type=int, default=2, help="disk workload: Legendre degree k (1..3)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.workload == "disk":
         run_disk(args)
         return
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     if args.workload == "uneven":
         run_uneven(args)
         return

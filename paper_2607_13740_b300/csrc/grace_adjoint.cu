@@ -235,6 +235,22 @@ __global__ void param_dot_kernel(int R, int n_cells, const double *mu, const dou
     dtheta[(size_t)cell * n_params + ip] += w * dt[cell] * s;
 }
 
+// dtheta[cell][ip] += w dt mu . Fp with Fp from a tensor-core contraction ([tile][R][128]); only
+// the functionals its tiles write (written[r]) count, the others are zero
+__global__ void param_dot_f32_kernel(int R, int n_cells, const double *__restrict__ mu, const float *__restrict__ Fp,
+                                     const int *__restrict__ written, const double *__restrict__ dt, double w,
+                                     int n_params, int ip, double *__restrict__ dtheta)
+{
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= n_cells) return;
+    const long long ct = cell / kTileM;
+    const int row = cell - (int)ct * kTileM;
+    double s = 0.0;
+    for (int r = 0; r < R; ++r)
+        if (written[r]) s = fma(mu[(size_t)cell * R + r], (double)Fp[((size_t)ct * R + r) * kTileM + row], s);
+    dtheta[(size_t)cell * n_params + ip] += w * dt[cell] * s;
+}
+
 // ------------------------------------------------------------------ tensor-form pieces
 __device__ __forceinline__ double warp_max(double x)
 {
@@ -396,6 +412,7 @@ namespace grace {
 void free_param_derivs(Group &G)
 {
     for (ParamDeriv &d : G.dparams) {
+        for (auto &t : d.tc) free_tc_tiles(t);
         cudaFree(d.d_dT);
         cudaFree(d.d_qlo);
         cudaFree(d.d_qhi);
@@ -452,6 +469,12 @@ grace_status prepare_tc(grace_batch *b, int prec, bool vjp, const char *who)
         grace_status s = build_vjp_tiles(G, prec, b->ctx->stream);
         if (s != GRACE_OK) return s;
     }
+    // parameter derivatives dT/dtheta of grace_param_grad_setup, contracted like T
+    for (ParamDeriv &pd : G.dparams)
+        if (vjp && !pd.tc[prec].built) {
+            grace_status s = build_tc_tiles_from(G, pd.d_dT, prec, pd.tc[prec], b->ctx->stream);
+            if (s != GRACE_OK) return s;
+        }
     const size_t tiles = ((size_t)p.n + kTileM - 1) / kTileM;
     cudaError_t e = cudaSuccess;
     if (!p.d_W32) e = cudaMalloc(&p.d_W32, 2 * tiles * vjp_window_cols(G.dg) * kTileM * sizeof(float));
@@ -762,11 +785,25 @@ grace_status grace_adjoint(grace_batch *b, const double *g0, const double *dt, i
         return tc ? vjp_tc(b, precision, gs, l, out, st)
                   : launch_vjp(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gs, l, dF, n, out, st);
     };
-    // dtheta += w dt mu(l) . g^T dT g (mu of the last vjp is in b->d_F)
+    // dtheta += w dt mu(l) . g^T dT g (mu of the last vjp is in b->d_F).  Tensor forms: the
+    // A operand of gs is still packed by the VJP; g^T dT g goes to the FP32 mu buffer, free
+    // once the VJP contraction has run
     auto param_terms = [&](const double *gs, double w) {
         cudaError_t r = cudaSuccess;
         for (int i = 0; i < np && r == cudaSuccess && dtheta; ++i) {
             const ParamDeriv &pd = G.dparams[i];
+            if (tc) {
+                const TcTiles &t = pd.tc[precision];
+                if (t.n_tiles == 0) continue;      // T does not depend on this parameter
+                Part &p = b->parts[0];
+                r = launch_contract_tc(dg, t, precision, p.d_opA, n, p.d_mu32, b->d_err, st);
+                if (r == cudaSuccess) {
+                    param_dot_f32_kernel<<<blocks(n, 128), 128, 0, st>>>(R, n, dF, p.d_mu32, t.d_written, dt, w, np,
+                                                                         i, dtheta);
+                    r = cudaGetLastError();
+                }
+                continue;
+            }
             r = launch_contract_fp64(dg, pd.d_dT, pd.d_qlo, pd.d_qhi, pd.d_prange, gs, n, Fp, st);
             if (r == cudaSuccess) r = launch_param_dot(R, n, dF, Fp, dt, w, np, i, dtheta, st);
         }

@@ -78,6 +78,7 @@ struct ParamDeriv {
     double step = 0.0;
     double *d_dT = nullptr;       // [R][P][P]
     int *d_qlo = nullptr, *d_qhi = nullptr, *d_prange = nullptr;
+    TcTiles tc[3];                // tensor-form tiles of dT (built by the first tensor-form adjoint)
 };
 
 struct Group {
@@ -301,6 +302,7 @@ cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const Tc
 
 // tensor-core path
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);
+grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st);
 grace_status build_nc_tc_tiles(Group &G, int prec, cudaStream_t st);
 grace_status build_vjp_tiles(Group &G, int prec, cudaStream_t st);
 // VJP contraction: W[part][tile][Pw][128] (two partial planes, FP32) with

@@ -1020,6 +1020,18 @@ std::vector<int> functional_order(const DevGroup &g)
 
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
 {
+    TcTiles out;
+    grace_status s = build_tc_tiles_from(G, G.d_T, prec, out, st);
+    if (s != GRACE_OK) return s;
+    free_tc_tiles(G.tc[prec]);
+    G.tc[prec] = out;
+    return GRACE_OK;
+}
+
+// tiles of the quadratic forms d_T ([R][P][P], FP64, device) of group G; an all-zero d_T gives
+// built tiles with n_tiles = 0 (nothing to contract)
+grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st)
+{
     const DevGroup &g = G.dg;
     if (g.k > kKMax) {
         set_error("tensor-core tiles need k <= 3");
@@ -1033,7 +1045,7 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
     FT.W = FU.W = kWin;
     FT.p0_stride = FU.p0_stride = kWin;
     FT.M.resize((size_t)R * P_ * P_);
-    cudaError_t e = cudaMemcpyAsync(FT.M.data(), G.d_T, FT.M.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(FT.M.data(), d_T, FT.M.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core tiles: copy T");
 
@@ -1071,19 +1083,27 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
         set_error("tensor-core tiles: functional count mismatch");
         return GRACE_ERR_ARG;
     }
+    out = TcTiles();
+    const int ae = atom_elems(prec);
+    out.k_pad = (P_ + ae - 1) / ae * ae;
+    if (nnz_T == 0) {
+        out.built = 1;
+        return GRACE_OK;
+    }
     const Plan pT = plan_forms(FT, ford, prec), pU = plan_forms(FU, ford, prec);
     const bool use_fold = pU.cost <= pT.cost;
-    TcTiles out;
     std::vector<int> written;
     grace_status s = emit_tiles(use_fold ? FU : FT, use_fold ? pU : pT, ford, prec, out, written);
     if (s != GRACE_OK) return s;
-    const int ae = atom_elems(prec);
-    out.k_pad = (P_ + ae - 1) / ae * ae;
+    e = cudaMalloc(&out.d_written, R * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_written, written.data(), R * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_tc_tiles(out);
+        return cuda_fail(e, "tensor-core tiles: upload");
+    }
     out.nnz_fold = std::min(nnz_fold, nnz_T);
     out.folded = use_fold ? 1 : 0;
     out.built = 1;
-    free_tc_tiles(G.tc[prec]);
-    G.tc[prec] = out;
     return GRACE_OK;
 }
 

@@ -353,7 +353,7 @@ def run_adjoint(args):
     sampler.__exit__(None, None, None)
     ms_fwd, _ = timed(lambda: b.step(g0.clone(), dt, steps, form))
     res = {"adjoint_ms": ms_adj, "forward_ms": ms_fwd, "adjoint_over_forward": ms_adj / ms_fwd}
-    if form != grace.FP64:
+    if form != grace.FP64 and not args.skip_fp64_compare:
         # like-for-like comparison with the FP64 adjoint: the first 512 cells, 20 steps, both forms
         ns, cs = min(n, 512), min(steps, 20)
         bs = ctx.batch(ns)
@@ -459,6 +459,7 @@ def main():
     ap.add_argument("--cells", type=int, default=65536)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--skip-fp64-compare", action="store_true", help="adjoint workload: no FP64 comparison run")
     ap.add_argument("--forms", default=None,
                     help="comma-separated subset of fp64,tf32,bf16x3 to time (default: all built)")
     ap.add_argument("--workload", default="additive", choices=["additive", "disk", "uneven", "adjoint"],

@@ -174,7 +174,7 @@ def run_reference(args, rank):
     if rank != 0:
         return
     import oracle
-    wl = W.batched_additive(n_cells=args.cells)
+    wl = W.batched_additive(n_cells=args.cells or 65536)
     o = oracle.Oracle(wl.spec)
     threads = oracle.max_threads()
     n = max(threads, 2 * threads)
@@ -209,7 +209,7 @@ def run_disk(args):
     dev = torch.device(f"cuda:{local}")
     form = {"fp64": grace.FP64, "tf32": grace.TF32, "bf16x3": grace.BF16X3}[args.precision or "bf16x3"]
     fname = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[form]
-    n = args.cells if args.cells != 65536 else (2048 if form == grace.FP64 else 262144)
+    n = args.cells or (2048 if form == grace.FP64 else 262144)
     steps = args.steps or (3 if form == grace.FP64 else 10)
     spec, alpha, ic = W.disk_batch(n_cells=n, order_k=args.order)
     t0 = time.time()
@@ -319,7 +319,7 @@ def run_adjoint(args):
     dev = torch.device(f"cuda:{local}")
     form = {"fp64": grace.FP64, "tf32": grace.TF32, "bf16x3": grace.BF16X3}[args.precision or "bf16x3"]
     fname = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[form]
-    n = args.cells if args.cells != 65536 else 4096
+    n = args.cells or 4096
     steps, ckpt = args.steps or 200, 10
     spec = W.coupled_toy_spec(40, 2, flux_mode=W.FLUX_CONSERVATIVE)
     rng = np.random.default_rng(1005)
@@ -399,7 +399,7 @@ def run_uneven(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
-    n = args.cells if args.cells != 65536 else 100000
+    n = args.cells or 100000
     steps = args.steps or 3
     specs, group, ic, dt_np = W.uneven_batch(n_cells=n)
     t0 = time.time()
@@ -456,7 +456,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3"])
-    ap.add_argument("--cells", type=int, default=65536)
+    ap.add_argument("--cells", type=int, default=None,
+                    help="cells of the workload (default: 65,536 additive, 262,144 disk tensor forms / 2,048 FP64, "
+                         "4,096 adjoint, 100,000 uneven)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--skip-fp64-compare", action="store_true", help="adjoint workload: no FP64 comparison run")
@@ -497,7 +499,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    wl = W.batched_additive(n_cells=args.cells)
+    wl = W.batched_additive(n_cells=args.cells or 65536)
     n = wl.n_cells
     candidates = [grace.FP64, grace.TF32, grace.BF16X3]
     ctx = None

@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(128) nc_pack_tc_kernel(DevGroup G, NodeRuleF r
     if (l == 0) cell_s[cell] = sqrtf(d2f_fast(alpha[cell]));
 }
 
-// Partial entries of functional r (blockIdx.y) in FP32, added to the contraction's output
+// Partial entries of functional r (blockIdx.x) in FP32, added to the contraction's output
 // ([tile][functional][row]); functionals the contraction does not write are overwritten.  A block
 // covers C cell tiles: thread t handles row t of each (C cells), so every entry, staged through
 // shared memory, is read once per C cells (the broadcast loads, not the arithmetic, bound a
@@ -490,8 +490,10 @@ __global__ void __launch_bounds__(128) nc_partial_f32_kernel(int P, int R, const
 {
     constexpr int kChunk = 128;
     __shared__ float4 es[kChunk * 3];
-    const int r = blockIdx.y, row = threadIdx.x;
-    const long long ct0 = (long long)blockIdx.x * C;
+    // functional fastest in the grid: the blocks of one group of C cell tiles run together, so
+    // its coefficients stay in L2 across the functionals
+    const int r = blockIdx.x, row = threadIdx.x;
+    const long long ct0 = (long long)blockIdx.y * C;
     const long long last_tile = (long long)(n_cells - 1) / kTileM;
     float s[C], acc[C], ru[C], u[C], pf[C], gu[C][K1], gv[C][K1];
 #pragma unroll
@@ -687,7 +689,7 @@ cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const Tc
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int C = tiles * g.R >= 8LL * 4 * n_sm ? 8 : tiles * g.R >= 4LL * 4 * n_sm ? 4 : 1;
-    const dim3 grid((unsigned)((tiles + C - 1) / C), g.R);
+    const dim3 grid(g.R, (unsigned)((tiles + C - 1) / C));
 #define GRACE_NC_PARTIAL(K, CC)                                                                                   \
     nc_partial_f32_kernel<K, CC><<<grid, kTileM, 0, st>>>(g.P, g.R, ent, nt.d_segf, d_gh, d_s, t.d_written, t.ramp_b, \
                                                         n_cells, d_F32)

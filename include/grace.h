@@ -181,6 +181,14 @@ GRACE_API grace_status grace_rhs_noalloc(grace_ctx *ctx, int group, int n_cells,
    (grace_profile_enable) is not recorded inside graphs. */
 GRACE_API grace_status grace_batch_set_graph(grace_batch *batch, int enable);
 
+/* enable != 0 (the default): grace_step of a batch with several groups in a tensor-core
+   form runs the whole batch in a fixed number of launches per stage - one multi-group
+   tcgen05 contraction over every group's cell tiles (work items ordered by modelled cost)
+   and one K-c launch over all parts - instead of one launch sequence per group.  Its
+   descriptors are built on the first such call (allocates and synchronises, before any
+   graph capture).  enable = 0 restores the per-group launches.  Same results bit for bit. */
+GRACE_API grace_status grace_batch_set_grouped(grace_batch *batch, int enable);
+
 /* M_1 = sum_j h_j g_j^0 per cell (Sec. 4.1).  g, mass: device. */
 GRACE_API grace_status grace_mass(grace_batch *batch, const double *g, double *mass);
 

@@ -34,6 +34,61 @@ __global__ void scatter_rows_kernel(int n, int P, const long long *off, const do
     dst[off[c] + (t - c * P)] = src[t];
 }
 
+// ---------------------------------------------------------------- grouped (one launch per batch)
+// one part of a grouped gather / scatter: its first element (state doubles) and first cell in the
+// grouped index spaces, its rows' offsets in the caller's arrays and its workspaces
+struct MovePart {
+    long long elem0, cell0;
+    int n, P;
+    const long long *off;
+    const int *idx;
+    double *g, *dt, *mass;
+    unsigned char *flags;
+};
+
+__device__ __forceinline__ int find_part(const MovePart *m, int np, long long t, bool by_elem)
+{
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((by_elem ? m[mid].elem0 : m[mid].cell0) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// state rows: caller -> parts (scatter = 0) or parts -> caller (scatter = 1)
+__global__ void grouped_rows_kernel(const MovePart *__restrict__ m, int np, long long total, const double *src,
+                                    double *dst, int scatter)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const MovePart &p = m[find_part(m, np, t, true)];
+    const long long e = t - p.elem0, c = e / p.P;
+    const long long o = p.off[c] + (e - c * p.P);
+    if (scatter) dst[o] = p.g[e];
+    else p.g[e] = src[o];
+}
+
+// per-cell arrays: before the step dt -> parts and the parts' flags cleared (mode 0); after it
+// the parts' mass and flags -> caller (mode 1)
+__global__ void grouped_cells_kernel(const MovePart *__restrict__ m, int np, long long total, const double *dt,
+                                     double *mass, unsigned char *flags, int mode)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const MovePart &p = m[find_part(m, np, t, false)];
+    const long long c = t - p.cell0;
+    const int ci = p.idx[c];
+    if (mode == 0) {
+        p.dt[c] = dt[ci];
+        p.flags[c] = 0;
+    } else {
+        if (mass) mass[ci] = p.mass[c];
+        if (flags) flags[ci] = p.flags[c];
+    }
+}
+
 template <typename T>
 __global__ void gather_kernel(int n, int w, const int *idx, const T *src, T *dst)
 {
@@ -475,9 +530,193 @@ grace_status grace_rhs(grace_batch *b, const double *g, double *L, int prec)
     return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs");
 }
 
+// Grouped tensor-form step: every part of the batch in a fixed number of launches per stage
+// (gather, step-start limiter, per stage one multi-group contraction and one grouped K-c,
+// scatter).  The descriptors depend on the precision and on whether mass / flags are asked for;
+// they are built (allocating, synchronising) before the launches and kept with the batch.
+struct GroupedPlan {
+    int prec = -1, with_mass = -1, with_flags = -1;
+    TcMulti multi;
+    UpdPart *d_upd = nullptr;        // [5][n_parts]: limiter, stage 1, stage 2, stage 3, last stage 3
+    MovePart *d_move = nullptr;
+    int n_parts = 0, n_blocks = 0;
+    size_t smem[5] = {0, 0, 0, 0, 0};
+    long long total_elems = 0, total_cells = 0;
+};
+
+static void free_grouped(grace_batch *b)
+{
+    GroupedPlan *gp = (GroupedPlan *)b->grouped;
+    if (!gp) return;
+    free_tc_multi(gp->multi);
+    cudaFree(gp->d_upd);
+    cudaFree(gp->d_move);
+    delete gp;
+    b->grouped = nullptr;
+}
+
+static bool grouped_applies(grace_batch *b, int prec, int n_steps)
+{
+    if (!b->use_grouped || prec == GRACE_FP64 || n_steps < 1 || b->parts.size() < 2) return false;
+    for (const Part &p : b->parts)
+        if (p.direct || b->ctx->groups[p.group].dg.cell_alpha) return false;
+    return true;
+}
+
+static grace_status grouped_prepare(grace_batch *b, int prec, bool with_mass, bool with_flags)
+{
+    GroupedPlan *gp = (GroupedPlan *)b->grouped;
+    if (gp && gp->prec == prec && gp->with_mass == (int)with_mass && gp->with_flags == (int)with_flags)
+        return GRACE_OK;
+    free_grouped(b);
+    gp = new GroupedPlan();
+    b->grouped = gp;
+    const int np = (int)b->parts.size();
+    std::vector<TcMultiPart> mp;
+    std::vector<UpdPart> up((size_t)5 * np);
+    std::vector<MovePart> mv(np);
+    const int cpb = update_tc_grouped_cpb();
+    int blocks = 0;
+    long long elems = 0, cells = 0;
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int i = 0; i < np; ++i) {
+        Part &p = b->parts[i];
+        Group &G = b->ctx->groups[p.group];
+        const DevGroup &dg = G.dg;
+        mp.push_back({&G.tc[prec], p.d_opA, p.d_F32, p.n, dg.R});
+        const int kpad = G.tc[prec].k_pad;
+        const size_t xs = (mixed_bytes_for(dg, p.n) + 15) / 16 * 2;
+        double *X[3] = {p.d_mx, p.d_mx + xs, p.d_mx + 2 * xs};
+        unsigned char *fl = with_flags ? p.d_flags : nullptr;
+        UpdateArgs u[5];
+        // step-start limiter: FP64 part rows -> compact X[0] + A operand
+        u[0].gs = p.d_g;
+        u[0].gout = X[0];
+        u[0].apply_limiter = dg.limiter;
+        u[0].flags = fl;
+        u[0].opA = p.d_opA;
+        u[0].opA_prec = prec;
+        u[0].opA_kpad = kpad;
+        u[0].out_mixed = 1;
+        // stages 1, 2, 3 (not the call's last step), 3 of the last step
+        for (int c = 1; c < 5; ++c) {
+            const int stage = c <= 3 ? c - 1 : 2;
+            const bool last = c == 4;
+            UpdateArgs &v = u[c];
+            v.F32 = p.d_F32;
+            v.gn = X[0];
+            v.gs = X[stage];
+            v.in_mixed = 1;
+            v.dt = p.d_dt;
+            v.a = ca[stage];
+            v.b = cb[stage];
+            v.flags = fl;
+            v.gout = stage < 2 ? X[stage + 1] : (last ? p.d_g : X[0]);
+            v.out_mixed = last ? 0 : 1;
+            if (stage == 2) {
+                v.apply_limiter = (!last && dg.limiter) ? 1 : 0;
+                v.mass = last && with_mass ? p.d_mass : nullptr;
+            }
+            if (!last) {
+                v.opA = p.d_opA;
+                v.opA_prec = prec;
+                v.opA_kpad = kpad;
+            }
+        }
+        for (int c = 0; c < 5; ++c) {
+            UpdPart &q = up[(size_t)c * np + i];
+            q.G = dg;
+            q.A = u[c];
+            q.n_cells = p.n;
+            q.first_block = blocks;
+            gp->smem[c] = std::max(gp->smem[c], update_tc_grouped_smem(dg, u[c]));
+        }
+        blocks += (p.n + cpb - 1) / cpb;
+        MovePart &m = mv[i];
+        m.elem0 = elems;
+        m.cell0 = cells;
+        m.n = p.n;
+        m.P = dg.P;
+        m.off = p.d_off;
+        m.idx = p.d_idx;
+        m.g = p.d_g;
+        m.dt = p.d_dt;
+        m.mass = p.d_mass;
+        m.flags = p.d_flags;
+        elems += (long long)p.n * dg.P;
+        cells += p.n;
+    }
+    grace_status s = build_tc_multi(prec, mp, gp->multi);
+    if (s != GRACE_OK) {
+        free_grouped(b);
+        return s;
+    }
+    cudaError_t e = cudaMalloc(&gp->d_upd, up.size() * sizeof(UpdPart));
+    if (e == cudaSuccess) e = cudaMalloc(&gp->d_move, mv.size() * sizeof(MovePart));
+    if (e == cudaSuccess) e = cudaMemcpy(gp->d_upd, up.data(), up.size() * sizeof(UpdPart), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(gp->d_move, mv.data(), mv.size() * sizeof(MovePart), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_grouped(b);
+        return cuda_fail(e, "grace_step: grouped plan");
+    }
+    gp->prec = prec;
+    gp->with_mass = with_mass;
+    gp->with_flags = with_flags;
+    gp->n_parts = np;
+    gp->n_blocks = blocks;
+    gp->total_elems = elems;
+    gp->total_cells = cells;
+    return GRACE_OK;
+}
+
+static cudaError_t grouped_step(grace_batch *b, double *g, const double *dt, int n_steps, double *mass,
+                                unsigned char *flags)
+{
+    GroupedPlan &gp = *(GroupedPlan *)b->grouped;
+    cudaStream_t st = b->ctx->stream;
+    const int np = gp.n_parts;
+    grouped_rows_kernel<<<nb(gp.total_elems), 256, 0, st>>>(gp.d_move, np, gp.total_elems, g, nullptr, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        grouped_cells_kernel<<<nb(gp.total_cells), 256, 0, st>>>(gp.d_move, np, gp.total_cells, dt, nullptr,
+                                                                 nullptr, 0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        LaunchTimer timer(b->ctx, 1, st);
+        e = launch_update_tc_grouped(GROUPED_LIMIT, false, true, gp.d_upd, np, gp.n_blocks, gp.smem[0], st);
+    }
+    for (int step = 0; step < n_steps && e == cudaSuccess; ++step) {
+        const bool last = step == n_steps - 1;
+        for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+            {
+                LaunchTimer timer(b->ctx, 0, st);
+                e = launch_contract_tc_multi(gp.multi, b->d_err, st);
+            }
+            if (e != cudaSuccess) break;
+            const int c = stage < 2 ? stage + 1 : (last ? 4 : 3);
+            LaunchTimer timer(b->ctx, 1, st);
+            e = launch_update_tc_grouped(GROUPED_STAGE, true, c != 4, gp.d_upd + (size_t)c * np, np, gp.n_blocks,
+                                         gp.smem[c], st);
+        }
+    }
+    if (e == cudaSuccess) {
+        grouped_rows_kernel<<<nb(gp.total_elems), 256, 0, st>>>(gp.d_move, np, gp.total_elems, nullptr, g, 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && (mass || flags)) {
+        grouped_cells_kernel<<<nb(gp.total_cells), 256, 0, st>>>(gp.d_move, np, gp.total_cells, nullptr, mass,
+                                                                 flags, 1);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 static cudaError_t step_body(grace_batch *b, double *g, const double *dt, int n_steps, int prec, double *mass,
                              unsigned char *flags)
 {
+    if (grouped_applies(b, prec, n_steps)) return grouped_step(b, g, dt, n_steps, mass, flags);
     return for_parts(b, [&](Part &p, cudaStream_t st) {
         if (p.direct) return part_step(b, p, g, dt, n_steps, prec, mass, flags);
         const int P = b->ctx->groups[p.group].dg.P;
@@ -512,6 +751,11 @@ grace_status grace_step(grace_batch *b, double *g, const double *dt, int n_steps
     if (s != GRACE_OK) return s;
     Guard guard(b->ctx->device);
     cudaError_t e = cudaSuccess;
+    if (grouped_applies(b, prec, n_steps)) {
+        // descriptors are built outside any graph capture
+        s = grouped_prepare(b, prec, mass != nullptr, flags != nullptr);
+        if (s != GRACE_OK) return s;
+    }
     if (!b->use_graph) {
         e = step_body(b, g, dt, n_steps, prec, mass, flags);
         return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_step");
@@ -549,6 +793,21 @@ grace_status grace_step(grace_batch *b, double *g, const double *dt, int n_steps
     }
     e = cudaGraphLaunch(b->graph, st);
     return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_step: graph launch");
+}
+
+grace_status grace_batch_set_grouped(grace_batch *b, int enable)
+{
+    if (!b) {
+        set_error("grace_batch_set_grouped: null batch");
+        return GRACE_ERR_ARG;
+    }
+    b->use_grouped = enable ? 1 : 0;
+    if (b->graph) {
+        Guard guard(b->ctx->device);
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return GRACE_OK;
 }
 
 grace_status grace_batch_set_graph(grace_batch *b, int enable)
@@ -674,6 +933,7 @@ void grace_batch_destroy(grace_batch *b)
     if (!b) return;
     Guard guard(b->ctx->device);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    free_grouped(b);
     for (Part &p : b->parts) free_part(p);
     cudaFree(b->d_err);
     cudaFree(b->d_adj);

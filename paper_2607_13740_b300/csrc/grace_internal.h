@@ -166,6 +166,9 @@ struct grace_batch {
     const void *graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
     int graph_steps = -1, graph_prec = -1;
     int alpha_set = 0;             // grace_batch_cell_params was called
+    // grouped tensor-form steps of batches with several groups (grace_batch_set_grouped)
+    int use_grouped = 1;
+    void *grouped = nullptr;       // the grouped plan (grace_batch.cu), built on first use
 };
 
 namespace grace {
@@ -230,6 +233,20 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
 // K-c for the tensor path: reads d_F32 in the tile layout above
 cudaError_t launch_update_tc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st);
 size_t f32_bytes_for(const DevGroup &g, int n_cells);
+// K-c over many parts in one launch (uneven batches): one descriptor per part, parts ordered
+// by first_block; modes: the step-start limiter (FP64 rows -> compact layout + A operand) and
+// the stage update (compact in; compact or FP64 rows out)
+struct UpdPart {
+    DevGroup G;
+    UpdateArgs A;
+    int n_cells;
+    int first_block;
+};
+enum { GROUPED_STAGE = 1, GROUPED_LIMIT = 2 };
+int update_tc_grouped_cpb();
+size_t update_tc_grouped_smem(const DevGroup &g, const UpdateArgs &a);
+cudaError_t launch_update_tc_grouped(int mode, bool in_mixed, bool out_mixed, const UpdPart *d_parts, int n_parts,
+                                     int n_blocks, size_t smem, cudaStream_t st);
 // the step-start limiter of the tensor path: FP64 rows d_g -> compact stage layout + A operand
 cudaError_t launch_limit_pack(const DevGroup &g, const double *d_g, int n_cells, unsigned char *flags,
                               double *mixed_out, void *opA, int opA_prec, int opA_kpad, cudaStream_t st);
@@ -305,6 +322,25 @@ grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);
 grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st);
 grace_status build_nc_tc_tiles(Group &G, int prec, cudaStream_t st);
 grace_status build_vjp_tiles(Group &G, int prec, cudaStream_t st);
+// multi-group contraction (uneven batches): the flux functionals of every part of a batch in one
+// persistent launch; items (part, 128-cell tile) ordered by modelled cost
+struct TcMultiPart {
+    const TcTiles *t;
+    const void *opA;
+    float *F32;
+    int n_cells, R;
+};
+struct TcMulti {
+    void *d_groups = nullptr;
+    void *d_items = nullptr;
+    int n_items = 0;
+    long long max_a = 0;
+    int max_rows = 0;
+    int prec = -1;
+};
+grace_status build_tc_multi(int prec, const std::vector<TcMultiPart> &parts, TcMulti &out);
+cudaError_t launch_contract_tc_multi(const TcMulti &m, int *d_err, cudaStream_t st);
+void free_tc_multi(TcMulti &m);
 // VJP contraction: W[part][tile][Pw][128] (two partial planes, FP32) with
 // W = sum_r mu_r (Shat_r ghat) per cell, mu in the [tile][R][128] layout (FP32)
 cudaError_t launch_vjp_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, const float *d_mu32,

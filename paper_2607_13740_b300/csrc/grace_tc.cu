@@ -117,10 +117,71 @@ struct TcParams {
     const float *mu;
     float *W;
     int Pw;
+    // multi-group mode: per-group descriptors and the work items (group, cell tile)
+    const struct TcGroupDesc *groups;
+    const int2 *items;
 };
 
-// contraction modes: flux functionals, node-space functionals (per-cell kernels), VJP
-constexpr int kModeF = 0, kModeNC = 1, kModeVJP = 2;
+// one group of a multi-group launch (all its tiles form one split)
+struct TcGroupDesc {
+    const TileDesc *tiles;
+    const int *ford;
+    const uint8_t *B;
+    const uint8_t *A;
+    float *F;
+    long long a_tile_bytes;
+    int n_cells, R, t0, t1;
+};
+
+// contraction modes: flux functionals, node-space functionals (per-cell kernels), VJP, flux
+// functionals of many groups in one launch (uneven batches)
+constexpr int kModeF = 0, kModeNC = 1, kModeVJP = 2, kModeMulti = 3;
+
+// the parameters of one work item: its group's tiles, operands and output, its tile range
+struct ItemCtx {
+    const TileDesc *tiles;
+    const int *ford;
+    const uint8_t *B;
+    const uint8_t *A;        // the item's A tile in global memory
+    float *F;
+    long long a_bytes;
+    int n_cells, R, t0, t1, ct;
+};
+
+template <int MODE>
+__device__ __forceinline__ ItemCtx item_ctx(const TcParams &P, int it, const TileDesc *tiles, const int *ford)
+{
+    ItemCtx c;
+    if (MODE == kModeMulti) {
+        const int2 v = P.items[it];
+        const TcGroupDesc &g = P.groups[v.x];
+        c.tiles = g.tiles;
+        c.ford = g.ford;
+        c.B = g.B;
+        c.a_bytes = g.a_tile_bytes;
+        c.A = g.A + (size_t)v.y * g.a_tile_bytes;
+        c.F = g.F;
+        c.n_cells = g.n_cells;
+        c.R = g.R;
+        c.t0 = g.t0;
+        c.t1 = g.t1;
+        c.ct = v.y;
+    } else {
+        const int sp = it / P.n_cell_tiles, ct = it - sp * P.n_cell_tiles;
+        c.tiles = tiles;
+        c.ford = ford;
+        c.B = P.B;
+        c.a_bytes = P.a_tile_bytes;
+        c.A = P.A + (size_t)ct * P.a_tile_bytes;
+        c.F = P.F;
+        c.n_cells = P.n_cells;
+        c.R = P.R;
+        c.t0 = P.split[sp];
+        c.t1 = P.split[sp + 1];
+        c.ct = ct;
+    }
+    return c;
+}
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -489,8 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         // next work item's A tile as soon as the previous use of that buffer is released
         int ctl = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
-            const int sp = it / P.n_cell_tiles, ct = it - sp * P.n_cell_tiles;
-            (void)sp;
+            const ItemCtx c = item_ctx<MODE>(P, it, tiles, ford);
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             int ok = 1;
             if (lane == 0) {
@@ -500,9 +560,9 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     ok = 0;
                 }
                 if (ok) {
-                    mbar_expect_tx(smem_u32(&S->a_full[ab]), (uint32_t)P.a_tile_bytes);
-                    bulk_g2s(a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes, P.A + (size_t)ct * P.a_tile_bytes,
-                             (uint32_t)P.a_tile_bytes, smem_u32(&S->a_full[ab]));
+                    mbar_expect_tx(smem_u32(&S->a_full[ab]), (uint32_t)c.a_bytes);
+                    bulk_g2s(a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes, c.A, (uint32_t)c.a_bytes,
+                             smem_u32(&S->a_full[ab]));
                     S->a_issued[ab] = au + 1;
                 }
             }
@@ -516,13 +576,13 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         const int me = warp == 0 ? 0 : 1;
         int q = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-            const int sp = it / P.n_cell_tiles;
+            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
             int ok = *abort_flag ? 0 : 1;
-            for (int t = P.split[sp]; t < P.split[sp + 1] && ok; ++t) {
-                const TileDesc td = tiles[t];
+            for (int t = ic.t0; t < ic.t1 && ok; ++t) {
+                const TileDesc td = ic.tiles[t];
                 const int nks = td.ks_hi - td.ks_lo, n_copies = (nks + kps - 1) / kps;
                 const uint32_t ks_bytes = (uint32_t)td.n * 32u * planes;
-                const uint8_t *bsrc = P.B + (size_t)td.b_off16 * 16;
+                const uint8_t *bsrc = ic.B + (size_t)td.b_off16 * 16;
                 if (lane == 0)
                     for (int c = 0; c < n_copies; ++c, ++q) {
                         if ((q & 1) != me) continue;
@@ -548,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         // ------------------------------------------------ MMA issuer
         int q = 0, acc_use = 0, ctl = 0;
         for (int it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x, ++ctl) {
-            const int sp = it / P.n_cell_tiles;
+            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             if (!mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag)) {
                 fail(P, abort_flag, 4);
@@ -557,9 +617,9 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             S->a_done[ab] = au + 1;
             tc_fence_after();
             const uint32_t a0 = a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes;
-            const uint32_t a_lo = a0 + (uint32_t)(P.a_tile_bytes / 2);
-            for (int t = P.split[sp]; t < P.split[sp + 1] && !*abort_flag; ++t) {
-                const TileDesc td = tiles[t];
+            const uint32_t a_lo = a0 + (uint32_t)(ic.a_bytes / 2);
+            for (int t = ic.t0; t < ic.t1 && !*abort_flag; ++t) {
+                const TileDesc td = ic.tiles[t];
                 const int buf = acc_use & 1, bu = acc_use >> 1;
                 if (bu > 0 && !mbar_wait(smem_u32(&S->acc_empty[buf]), (bu - 1) & 1, abort_flag)) {
                     fail(P, abort_flag, 8);
@@ -622,7 +682,8 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         const uint32_t tlane = (uint32_t)(qd * 32) << 16;
         int acc_use = 0, ctl = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
-            const int sp = it / P.n_cell_tiles, ct = it - sp * P.n_cell_tiles;
+            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
+            const int ct = ic.ct;
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag))) {
                 fail(P, abort_flag, 32);
@@ -630,7 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             }
             const uint8_t *a_gen = gbase + (size_t)ab * P.a_tile_bytes;
             const long long cell = (long long)ct * kTileM + row;
-            const bool live = cell < P.n_cells;
+            const bool live = cell < ic.n_cells;
             const float s_cell = MODE == kModeNC && live ? P.cell_s[cell] : 0.f;
             const float *mu_cell = MODE == kModeVJP ? P.mu + (size_t)ct * P.R * kTileM + row : nullptr;
             float Facc[kEpiF];
@@ -640,12 +701,12 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 #pragma unroll
             for (int t = 0; t < (MODE == kModeVJP ? kWin : 1); ++t) Wacc[t] = 0.f;
             bool aborted = false;
-            for (int t = P.split[sp]; t < P.split[sp + 1]; ++t) {
+            for (int t = ic.t0; t < ic.t1; ++t) {
                 if (__any_sync(0xffffffffu, *abort_flag)) {
                     aborted = true;
                     break;
                 }
-                const TileDesc td = tiles[t];
+                const TileDesc td = ic.tiles[t];
                 const int nf = td.nf_flush & 0xFFFF;
                 const int buf = acc_use & 1, bu = acc_use >> 1;
                 if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->acc_full[buf]), bu & 1, abort_flag))) {
@@ -656,12 +717,12 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 tc_fence_after();
                 const uint32_t tcol = tmem + tlane + (uint32_t)(buf * kAccCols);
                 if (MODE == kModeNC)
-                    epi_tile_nc<PREC, 2>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, s_cell, D0s, P.ramp_a,
+                    epi_tile_nc<PREC, 2>(a_gen, ic.a_bytes, row, td.p0, tcol, nf, part, s_cell, D0s, P.ramp_a,
                                          P.ramp_b, Facc);
                 else if (MODE == kModeVJP)
                     epi_tile_vjp<4>(tcol, nf, part, mu_cell, ford, td.f0, Wacc);
                 else
-                    epi_tile<PREC, kWin, kEpiF>(a_gen, P.a_tile_bytes, row, td.p0, tcol, nf, part, Facc);
+                    epi_tile<PREC, kWin, kEpiF>(a_gen, ic.a_bytes, row, td.p0, tcol, nf, part, Facc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&S->acc_empty[buf]));
@@ -677,11 +738,11 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     for (int t = 0; t < (MODE == kModeVJP ? kWin : 1); ++t) Wacc[t] = 0.f;
                 } else if (MODE != kModeVJP && (td.nf_flush >> 16)) {
                     if (live) {
-                        float *Fo = P.F + ((size_t)ct * P.R) * kTileM + row;
+                        float *Fo = ic.F + ((size_t)ct * ic.R) * kTileM + row;
 #pragma unroll
                         for (int m = 0; m < kEpiF; ++m) {
                             const int f = kEpiSplit * m + part;
-                            if (f < nf) Fo[(size_t)ford[td.f0 + f] * kTileM] = Facc[m];
+                            if (f < nf) Fo[(size_t)ic.ford[td.f0 + f] * kTileM] = Facc[m];
                         }
                     }
 #pragma unroll
@@ -1335,6 +1396,79 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
     }
     return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeF>(P, t.max_rows, st)
                               : launch_prec<GRACE_BF16X3, kModeF>(P, t.max_rows, st);
+}
+
+void free_tc_multi(TcMulti &m)
+{
+    cudaFree(m.d_groups);
+    cudaFree(m.d_items);
+    m = TcMulti();
+}
+
+grace_status build_tc_multi(int prec, const std::vector<TcMultiPart> &parts, TcMulti &out)
+{
+    free_tc_multi(out);
+    std::vector<TcGroupDesc> groups;
+    std::vector<std::pair<double, int2>> items;
+    long long max_a = 0;
+    int max_rows = 0;
+    for (size_t i = 0; i < parts.size(); ++i) {
+        const TcMultiPart &p = parts[i];
+        if (!p.t || !p.t->built || p.t->nc || p.t->vjp) {
+            set_error("multi-group contraction: a part has no forward tensor-core tiles");
+            return GRACE_ERR_ORDER;
+        }
+        TcGroupDesc g;
+        std::memset(&g, 0, sizeof(g));
+        g.tiles = (const TileDesc *)p.t->d_desc;
+        g.ford = p.t->d_ford;
+        g.B = (const uint8_t *)p.t->d_b;
+        g.A = (const uint8_t *)p.opA;
+        g.F = p.F32;
+        g.a_tile_bytes = (long long)opA_tile_bytes(prec, p.t->k_pad);
+        g.n_cells = p.n_cells;
+        g.R = p.R;
+        g.t0 = 0;
+        g.t1 = p.t->n_tiles;
+        max_a = std::max(max_a, g.a_tile_bytes);
+        max_rows = std::max(max_rows, p.t->max_rows);
+        const int n_ct = (p.n_cells + kTileM - 1) / kTileM;
+        for (int ct = 0; ct < n_ct; ++ct) items.push_back({p.t->pred_clk, make_int2((int)i, ct)});
+        groups.push_back(g);
+    }
+    // largest items first: the round-robin assignment then approximates a balanced schedule
+    std::stable_sort(items.begin(), items.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<int2> it(items.size());
+    for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
+    cudaError_t e = cudaMalloc(&out.d_groups, std::max<size_t>(groups.size(), 1) * sizeof(TcGroupDesc));
+    if (e == cudaSuccess) e = cudaMalloc(&out.d_items, std::max<size_t>(it.size(), 1) * sizeof(int2));
+    if (e == cudaSuccess && !groups.empty())
+        e = cudaMemcpy(out.d_groups, groups.data(), groups.size() * sizeof(TcGroupDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !it.empty()) e = cudaMemcpy(out.d_items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_tc_multi(out);
+        return cuda_fail(e, "multi-group contraction: upload");
+    }
+    out.n_items = (int)it.size();
+    out.max_a = max_a;
+    out.max_rows = max_rows;
+    out.prec = prec;
+    return GRACE_OK;
+}
+
+cudaError_t launch_contract_tc_multi(const TcMulti &m, int *d_err, cudaStream_t st)
+{
+    if (m.n_items == 0) return cudaSuccess;
+    TcParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.groups = (const TcGroupDesc *)m.d_groups;
+    P.items = (const int2 *)m.d_items;
+    P.n_cell_tiles = m.n_items;   // items, one split each
+    P.n_splits = 1;
+    P.a_tile_bytes = m.max_a;     // stride of the A buffers in shared memory
+    P.err = d_err;
+    return m.prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeMulti>(P, m.max_rows, st)
+                                : launch_prec<GRACE_BF16X3, kModeMulti>(P, m.max_rows, st);
 }
 
 cudaError_t launch_vjp_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, const float *d_mu32,

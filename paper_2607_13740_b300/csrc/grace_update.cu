@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(256) limit_kernel(DevGroup G, double *g, int n
 // is written when A.opA is set.
 enum { MODE_RHS = 0, MODE_STAGE = 1, MODE_LIMIT = 2 };
 constexpr int kUpdWarps = 8;
+constexpr int kGroupedLpc = 16;     // lanes per cell of the grouped launch (16 cells per block)
 
 // LPC lanes per cell (16 or 32, whichever leaves fewer lanes idle for N bins);
 // lane l of a cell handles bins l, l + LPC, ...
@@ -182,13 +183,13 @@ constexpr int kUpdWarps = 8;
 // (the tensor forms carry the higher modes at FP32 precision anyway).  IN_MIX /
 // OUT_MIX select the layout of the stage inputs / the result.
 template <int MODE, int LPC, bool IN_MIX, bool OUT_MIX>
-__global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G, UpdateArgs A, int n_cells)
+__device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateArgs &A, int n_cells, long long block)
 {
     extern __shared__ double sm[];
     constexpr int CPB = kUpdWarps * 32 / LPC;                     // cells per block (a divisor of 128)
     const int N = G.N, k = G.k, K1 = G.K1, P = G.P, R = G.R;
     const int slot = threadIdx.x / LPC, lane = threadIdx.x % LPC;
-    const long long cell0 = (long long)blockIdx.x * CPB;
+    const long long cell0 = block * CPB;
     const long long cell = cell0 + slot;
     const int lda = A.opA_kpad;
     double *row = sm + (size_t)slot * (P + lda / 2 + 1);          // new coefficients of the cell
@@ -406,6 +407,32 @@ __global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G
     }
 }
 
+template <int MODE, int LPC, bool IN_MIX, bool OUT_MIX>
+__global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_kernel(DevGroup G, UpdateArgs A, int n_cells)
+{
+    update_tc_body<MODE, LPC, IN_MIX, OUT_MIX>(G, A, n_cells, blockIdx.x);
+}
+
+// K-c over the parts of a batch in one launch: block b belongs to the part with the largest
+// first_block <= b; the part's descriptor is staged in shared memory
+template <int MODE, bool IN_MIX, bool OUT_MIX>
+__global__ void __launch_bounds__(32 * kUpdWarps, 3) update_tc_grouped_kernel(const UpdPart *__restrict__ parts,
+                                                                              int n_parts)
+{
+    __shared__ UpdPart sp;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_parts - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (parts[mid].first_block <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        sp = parts[lo];
+    }
+    __syncthreads();
+    update_tc_body<MODE, kGroupedLpc, IN_MIX, OUT_MIX>(sp.G, sp.A, sp.n_cells, (long long)blockIdx.x - sp.first_block);
+}
+
 __global__ void __launch_bounds__(256) mass_kernel(DevGroup G, const double *g, int n_cells, double *mass)
 {
     const long long cell = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -484,6 +511,33 @@ static cudaError_t launch_update_mode(const DevGroup &g, const UpdateArgs &a, in
     const int idle16 = (g.N + 15) / 16 * 16 - g.N, idle32 = (g.N + 31) / 32 * 32 - g.N;
     return idle16 <= idle32 ? launch_update_lpc<MODE, 16, IN_MIX, OUT_MIX>(g, a, n_cells, st)
                             : launch_update_lpc<MODE, 32, IN_MIX, OUT_MIX>(g, a, n_cells, st);
+}
+
+int update_tc_grouped_cpb() { return kUpdWarps * 32 / kGroupedLpc; }
+
+size_t update_tc_grouped_smem(const DevGroup &g, const UpdateArgs &a) { return update_tc_smem(g, a, kGroupedLpc); }
+
+template <int MODE, bool IN_MIX, bool OUT_MIX>
+static cudaError_t launch_grouped(const UpdPart *d_parts, int n_parts, int n_blocks, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(update_tc_grouped_kernel<MODE, IN_MIX, OUT_MIX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    update_tc_grouped_kernel<MODE, IN_MIX, OUT_MIX><<<n_blocks, 32 * kUpdWarps, smem, st>>>(d_parts, n_parts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_tc_grouped(int mode, bool in_mixed, bool out_mixed, const UpdPart *d_parts, int n_parts,
+                                     int n_blocks, size_t smem, cudaStream_t st)
+{
+    if (n_blocks <= 0 || n_parts <= 0) return cudaSuccess;
+    if (mode == GROUPED_LIMIT && !in_mixed && out_mixed)
+        return launch_grouped<MODE_LIMIT, false, true>(d_parts, n_parts, n_blocks, smem, st);
+    if (mode == GROUPED_STAGE && in_mixed && out_mixed)
+        return launch_grouped<MODE_STAGE, true, true>(d_parts, n_parts, n_blocks, smem, st);
+    if (mode == GROUPED_STAGE && in_mixed && !out_mixed)
+        return launch_grouped<MODE_STAGE, true, false>(d_parts, n_parts, n_blocks, smem, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_update_tc(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)

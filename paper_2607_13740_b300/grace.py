@@ -47,7 +47,7 @@ def exported_symbols():
             "grace_batch_offsets", "grace_project", "grace_rhs", "grace_step", "grace_mass",
             "grace_limit", "grace_profile_enable", "grace_profile_read", "grace_group_stats",
             "grace_batch_error", "grace_rhs_jvp", "grace_rhs_vjp", "grace_param_grad_setup",
-            "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_destroy",
+            "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_set_grouped", "grace_batch_destroy",
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc"]
 
 
@@ -88,6 +88,7 @@ def load(path: str | None = None):
     L.grace_adjoint.argtypes = [_VP, _VP, _VP, S, S, _VP, _VP, _VP, S]
     L.grace_probe_rates.argtypes = [S, ctypes.POINTER(ctypes.c_double)]
     L.grace_batch_set_graph.argtypes = [_VP, S]
+    L.grace_batch_set_grouped.argtypes = [_VP, S]
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -324,6 +325,10 @@ class Batch:
     def set_graph(self, enable: bool = True):
         """Replay grace_step from a captured CUDA graph for repeated identical calls."""
         _check(load().grace_batch_set_graph(self._h, 1 if enable else 0), "grace_batch_set_graph")
+
+    def set_grouped(self, enable: bool = True):
+        """Tensor-form steps of a multi-group batch as one multi-group launch per stage (default)."""
+        _check(load().grace_batch_set_grouped(self._h, 1 if enable else 0), "grace_batch_set_grouped")
 
     def device_error(self) -> int:
         """Reads and clears the device error word (0 = no bounded wait gave up)."""

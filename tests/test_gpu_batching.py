@@ -3,7 +3,9 @@
 A mixed batch must give, cell by cell, exactly the result of running each
 group's cells as a separate single-group batch (same kernels, same arithmetic),
 and match the oracle at the FP64 parity bar.  Graph replay must reproduce the
-direct launches bit for bit.
+direct launches bit for bit, and so must the grouped tensor-form step (one
+multi-group contraction and one K-c launch per stage) against the per-group
+launch sequences.
 """
 import numpy as np
 import pytest
@@ -114,3 +116,53 @@ def test_graph_replay_is_bitwise_identical(form):
         b.step(out, dtt, 3, form)     # replays
         torch.cuda.synchronize()
     assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("form", [grace.TF32, grace.BF16X3], ids=["tf32", "bf16x3"])
+def test_grouped_step_equals_per_group_launches(form):
+    # groups of very different sizes (N 16..80, k 0..3): several cell tiles for some groups,
+    # ragged last tiles everywhere
+    specs, group, ic, dt = W.uneven_batch(900, seed=1107, n_range=(16, 80), orders=(0, 1, 2, 3))
+    ctx = grace.Context(specs, 0, precisions=FORMS)
+    b = ctx.batch(len(group), group)
+    g0 = b.project(W.IC_EXP, ic)
+    dtt = torch.as_tensor(dt, device=DEV)
+    res = {}
+    for grouped in (True, False):
+        b.set_grouped(grouped)
+        g = g0.clone()
+        mass = torch.zeros(len(group), dtype=torch.float64, device=DEV)
+        flags = torch.zeros(len(group), dtype=torch.uint8, device=DEV)
+        b.step(g, dtt, 3, form, mass=mass, flags=flags)
+        b.step(g, dtt, 2, form)
+        res[grouped] = (g, mass, flags)
+    assert torch.equal(res[True][0], res[False][0])
+    assert torch.equal(res[True][2], res[False][2])
+    # the grouped K-c sums a cell's mass over 16 lanes; the per-group launch may use 32
+    assert torch.allclose(res[True][1], res[False][1], rtol=1e-15, atol=0.0)
+    assert b.device_error() == 0
+
+
+@pytest.mark.parametrize("form", [grace.BF16X3], ids=["bf16x3"])
+def test_grouped_step_matches_oracle(form):
+    specs, group, ic, dt = W.uneven_batch(400, seed=1108, n_range=(16, 40), orders=(1, 2, 3))
+    ctx = grace.Context(specs, 0, precisions=FORMS)
+    b = ctx.batch(len(group), group)
+    off = b.offsets()
+    g = b.project(W.IC_EXP, ic)
+    g0 = g.cpu().numpy()
+    m0 = b.mass(g).cpu().numpy()
+    mass = torch.zeros(len(group), dtype=torch.float64, device=DEV)
+    b.step(g, torch.as_tensor(dt, device=DEV), 4, form, mass=mass)
+    assert np.all(np.abs(mass.cpu().numpy() - m0) <= 1e-13 * np.abs(m0))
+    gg = g.cpu().numpy()
+    for gi, spec in enumerate(specs):
+        idx = np.where(group == gi)[0]
+        if idx.size == 0:
+            continue
+        o = oracle.Oracle(spec)
+        go, mo, _ = o.step(np.stack(_split(g0, off, idx)), dt[idx], 4)
+        h = np.diff(o.edges())
+        d = np.abs(np.stack(_split(gg, off, idx)) - go).reshape(idx.size, spec.n_bins, -1).sum(axis=2)
+        l1 = (h * d).sum(axis=1) / np.abs(mo)
+        assert l1.max() <= 2e-5, (gi, l1.max())      # the BF16x3 trajectory bar (R15)

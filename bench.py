@@ -168,6 +168,32 @@ def cpu_baseline(wl, n_steps_per_sample=1, target_s=12.0):
                       f"FP64 C oracle with OpenMP, {el:.1f} s"}
 
 
+def cpu_baseline_disk(spec, alpha, ic, n_cells=8):
+    """The FP64 oracle, as it stands, on the first cells of the disk workload, one SSP-RK3 step
+    each.  alpha is a parameter of the oracle's kernel, so every cell is its own oracle call (one
+    core); the time step is the oracle's own (half its positivity bound at t = 0, untimed)."""
+    import numpy as np
+    import oracle
+    from paper_2607_13740_b300 import workloads as W
+    el = 0.0
+    for c in range(n_cells):
+        p = list(spec.coag_p)
+        p[3] = float(alpha[c])
+        o = oracle.Oracle(spec.replace(coag_p=tuple(p), frag_p=tuple(p), cell_alpha=0))
+        g0 = o.project(W.IC_POWERLAW, ic[c:c + 1])
+        L, _ = o.rhs(g0, threads=1)
+        L0 = L.reshape(-1, spec.order_k + 1)[:, 0]
+        m0 = g0.reshape(-1, spec.order_k + 1)[:, 0]
+        neg = L0 < 0
+        dt = 0.5 * float(np.min(m0[neg] / -L0[neg])) if neg.any() else 1.0
+        t = time.perf_counter()
+        o.step(g0, dt, 1, threads=1)
+        el += time.perf_counter() - t
+    return {"value": n_cells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_cells} cells of the disk batch (each with its own alpha) x 1 SSP-RK3 step, "
+                      f"FP64 C oracle, one cell per call on one core, {el:.1f} s"}
+
+
 def run_reference(args, rank):
     """--impl reference: the oracle timed as it stands on bounded samples of the workload."""
     from paper_2607_13740_b300 import workloads as W
@@ -299,6 +325,7 @@ def run_disk(args):
                      "peak_source": psrc},
         "functionals_ms_avg": avg, "update_ms_avg": u_ms / max(1, u_n),
         "pack_and_partial_ms_per_stage": x_ms / max(1, c_n), "mass_drift": drift,
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_disk(spec, alpha, ic),
         "max_rel_err_vs_fp64_rhs": acc, "finite": bool(torch.isfinite(g).all().item()),
         "clocks": sampler.summary(),
     }

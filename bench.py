@@ -299,6 +299,23 @@ def run_disk(args):
             peak, psrc = peaks["bf16_tflops_sustained"], f"{peaks['source']} sustained bf16"
         bound, kname = "tensor", "contract_tc_kernel (node-space tiles)"
         alg = f"2 x {nz} fixed-pair multiply-adds x {passes} MMA passes per cell and RHS x {n} cells"
+        # the partial entries on the CUDA cores: 2 (k+1) + 2 multiply-adds per entry, cell and RHS
+        # (the count behind grace_group_stats), against the measured FP32 FMA rate
+        nnz_all, _ = ctx.stats(0, grace.FP64)
+        per_entry = 2 * (spec.order_k + 1) + 2
+        n_entries = (nnz_all - nz) // per_entry
+        x_avg = x_ms / max(1, c_n)
+        try:
+            fp32_peak = 2.0 * grace.probe_rates(local)["fp32_fma_per_s"] / 1e12
+            p32src = "measured FP32 FMA rate x 2"
+        except Exception:
+            fp32_peak, p32src = None, None
+        ach32 = 2.0 * per_entry * n_entries * n / (x_avg / 1e3) / 1e12
+        partial_roof = {"bound": "alu", "achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": ach32 / fp32_peak if fp32_peak else None,
+                        "kernel": "nc_partial_f32_kernel + nc_pack_tc_kernel (timed together)",
+                        "algorithmic": f"2 x {per_entry} multiply-adds x {n_entries} partial entries per cell "
+                                       f"and RHS x {n} cells", "peak_source": p32src}
     m0 = b.mass(g0)
     drift = ((b.mass(g) - m0).abs() / m0.abs()).max().item()
     acc = None
@@ -326,6 +343,7 @@ def run_disk(args):
         "functionals_ms_avg": avg, "update_ms_avg": u_ms / max(1, u_n),
         "pack_and_partial_ms_per_stage": x_ms / max(1, c_n), "mass_drift": drift,
         "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_disk(spec, alpha, ic),
+        "roofline_partial_entries": None if form == grace.FP64 else partial_roof,
         "max_rel_err_vs_fp64_rhs": acc, "finite": bool(torch.isfinite(g).all().item()),
         "clocks": sampler.summary(),
     }

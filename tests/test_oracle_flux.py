@@ -194,3 +194,61 @@ def test_appB_volume_term_converges_to_pointwise_flux_integral():
     for j in range(3):
         assert diffs[(24, j)] < 5e-3
         assert diffs[(24, j)] < diffs[(3, j)] / 5
+
+
+def test_ballistic_turbulent_fluxes_converge_to_adaptive_quadrature():
+    """The ballistic-turbulent model of the disk workload (per-cell alpha, fragmentation ramp,
+    power-law fragments with a remnant): the oracle's nested Q-point rule for the coagulation
+    flux (eq. Fcoagtrun) and for the fragmentation flux (eq. Ffragtrun, positive minus negative
+    part) converges to adaptive double integrals of the same integrands, evaluated with the
+    oracle's own kernel and product-mass functions, breakpoints at the bin edges, the end-bin
+    kinks and the masses where the ramp starts and saturates.  This pins the quadrature with this
+    kernel; the kernel itself is a library model (not in the paper)."""
+    spec = W.disk_spec(n_bins=4, order_k=1, a_min=1e-4, a_max=1e-1, cell_alpha=0, alpha=1e-3)
+    o = oracle.Oracle(spec)
+    e = o.edges()
+    xmin, xmax, k = spec.x_min, spec.x_max, spec.order_k
+    coef = W.random_coefficients(spec, 1, seed=7, dynamic_range=1.0)[0]
+    g = lambda y: dg_eval(coef, e, k, np.array([y]))[0]
+    m = np.geomspace(xmin, xmax, 4000)
+    kc, kf = o.kernels(m, np.full_like(m, xmin))
+    tot = kc + kf
+    pf = np.where(tot > 0, kf / np.where(tot > 0, tot, 1.0), 0.0)
+    kinks = [float(np.sqrt(m[i] * m[i + 1])) for i in range(len(m) - 1)
+             if (pf[i] == 0) != (pf[i + 1] == 0) or (pf[i] == 1) != (pf[i + 1] == 1)]
+    assert len(kinks) >= 2                      # the ramp lies inside the grid
+    x = float(np.sqrt(e[1] * e[2]))
+    Kc = lambda u, v: o.kernels([u], [v])[0][0]
+    Kf = lambda u, v: o.kernels([u], [v])[1][0]
+    above = lambda u, v: o.mass_split([x], [u], [v])[0][0]
+    below = lambda u, v: o.mass_split([x], [u], [v])[1][0]
+    vmax = lambda u: xmax - u + xmin
+
+    def pts(lo, hi, extra=()):
+        p = sorted(set(q for q in list(e) + kinks + list(extra) if lo < q < hi))
+        return p or None
+
+    def nested(f, ulo, uhi, vlo, vhi, upts, vextra):
+        inner = lambda u: integrate.quad(lambda v: f(u, v), vlo(u), vhi(u), points=pts(vlo(u), vhi(u), vextra(u)),
+                                         limit=100, epsrel=1e-8)[0]
+        return integrate.quad(lambda u: g(u) * inner(u), ulo, uhi, points=pts(ulo, uhi, upts), limit=100,
+                              epsrel=1e-7)[0]
+
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        lo = lambda u: x - u + xmin
+        ukinks = [x + xmin - q for q in list(e) + kinks] + kinks
+        coag = nested(lambda u, v: Kc(u, v) * g(v) / v, xmin, x, lo, vmax, ukinks, lambda u: [u])
+        pos = nested(lambda u, v: Kf(u, v) * g(v) * above(u, v) / (v * (u + v)), xmin, x, lo, vmax, ukinks,
+                     lambda u: [u, x])
+        neg = nested(lambda u, v: Kf(u, v) * g(v) * below(u, v) / (v * (u + v)), x, xmax, lambda u: xmin, vmax,
+                     kinks, lambda u: [u, x])
+    frag = pos - neg
+    assert coag != 0.0 and frag != 0.0
+    ec, ef = [], []
+    for Q in (2, 32):
+        oq = oracle.Oracle(spec.replace(quad_q=Q))
+        ec.append(abs(oq.flux_point(coef, [x], 1)[0][0] - coag) / abs(coag))
+        ef.append(abs(oq.flux_point(coef, [x], 2)[0][0] - frag) / abs(frag))
+    assert ec[1] < 1e-2 and ec[1] < ec[0] / 50, ec
+    assert ef[1] < 1e-3 and ef[1] < ef[0] / 100, ef

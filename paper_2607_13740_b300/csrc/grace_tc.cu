@@ -26,7 +26,7 @@
 // (grace_tc_layout.cuh).  Both move with cp.async.bulk (no tensor map).
 //
 // Warp roles (persistent, one CTA per SM, work items round-robin):
-//   warps 0, 3    : B bulk-copy producers (lane 0), copies alternating between the two issuers
+//   warps 0, 3    : B bulk-copy producers (lane 0), copies (up to 64 KB) alternating between the two issuers
 //   warp 2 lane 0 : A-tile loader (after allocating TMEM)
 //   warp 1 lane 0 : MMA issuer (kind::tf32, or kind::f16 with bf16 hi/lo x3)
 //   warp 2        : TMEM allocation / release (2 accumulators x 256 columns)
@@ -1342,12 +1342,14 @@ static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
                            (MODE == kModeNC ? (size_t)P.n_d0 * sizeof(float) : 0) + 15) / 16 * 16);
     const size_t fixed = 1024 + (size_t)P.table_bytes + sizeof(Smem) + 64;
     const size_t a1 = (size_t)P.a_tile_bytes;
-    // Shared-memory plan: 32 KB B copies at N = 256 (fewer k-steps per copy for groups whose A tile
+    // Shared-memory plan: 64 KB B copies at N = 256 (fewer k-steps per copy for groups whose A tile
     // leaves less room); two A tiles (the next work item's A loads during this one) when that still
-    // leaves a 4-deep B ring, else one.  Measured on the 65,536-cell workload: two A tiles with 16 KB
-    // copies are slower than one A tile with 32 KB copies.
+    // leaves a 4-deep B ring, else one.  An issuing thread completes about one bulk copy per ~800
+    // cycles whatever its size, so the B stream is bound by the number of copies: measured on the
+    // 65,536-cell workload, 64 KB copies in a 2-deep ring beat 48 KB x 3 and 32 KB x 4 (and 16 KB
+    // copies with two A tiles).
     auto slot_of = [&](int kps) { return (int)(((size_t)kps * max_rows * 32 * planes + 1023) / 1024 * 1024); };
-    P.kps = PREC == GRACE_TF32 ? 4 : 2;
+    P.kps = PREC == GRACE_TF32 ? 8 : 4;
     while (P.kps > 1 && fixed + a1 + 2 * (size_t)slot_of(P.kps) > (size_t)kSmemLimit) P.kps /= 2;
     P.slot_bytes = slot_of(P.kps);
     if (fixed + a1 + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;

@@ -148,9 +148,8 @@ struct ItemCtx {
     int n_cells, R, t0, t1, ct;
 };
 
-template <int MODE, bool PAIR = false>
-__device__ __forceinline__ ItemCtx item_ctx(const TcParams &P, int it, const TileDesc *tiles, const int *ford,
-                                            int rank = 0)
+template <int MODE>
+__device__ __forceinline__ ItemCtx item_ctx(const TcParams &P, int it, const TileDesc *tiles, const int *ford)
 {
     ItemCtx c;
     if (MODE == kModeMulti) {
@@ -168,9 +167,7 @@ __device__ __forceinline__ ItemCtx item_ctx(const TcParams &P, int it, const Til
         c.t1 = g.t1;
         c.ct = v.y;
     } else {
-        // pair mode: item = (split, pair of cell tiles), the CTA of rank r takes the pair's tile r
-        const int nct = PAIR ? P.n_cell_tiles / 2 : P.n_cell_tiles;
-        const int sp = it / nct, ct = PAIR ? 2 * (it - sp * nct) + rank : it - sp * nct;
+        const int sp = it / P.n_cell_tiles, ct = it - sp * P.n_cell_tiles;
         c.tiles = tiles;
         c.ford = ford;
         c.B = P.B;
@@ -241,37 +238,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// pairs of CTAs (a 2-CTA cluster sharing the B stream): rank, cluster-wide barrier, a bulk copy
-// delivered to both CTAs' shared memory (same offset, each CTA's mbarrier at the same offset), and
-// a tcgen05 commit that arrives on the mbarrier at the same offset in both CTAs
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s_pair(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::
-            "r"(dst),
-        "l"(src), "r"(bytes), "r"(bar), "h"((uint16_t)3)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_commit_pair(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-                 "h"((uint16_t)3)
-                 : "memory");
-}
 
 __device__ __forceinline__ void tc_commit(uint32_t bar)
 {
@@ -515,11 +481,7 @@ __device__ __forceinline__ void epi_tile_vjp(uint32_t tcol, int nf, int part, co
     }
 }
 
-// PAIR (flux mode, even number of cell tiles): a 2-CTA cluster works on the two cell tiles of a
-// pair with the same tile sequence; each CTA arms its own full barrier for every B copy but
-// issues every other one, multicast to both CTAs, and each MMA thread releases a slot on both
-// CTAs' empty barriers (count 2), so each CTA issues half the B copies.
-template <int PREC, int MODE, bool PAIR = false>
+template <int PREC, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 {
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
@@ -539,10 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NS = P.n_slots;
-    const int n_items = (PAIR ? P.n_cell_tiles / 2 : P.n_cell_tiles) * P.n_splits;
-    const int rank = PAIR ? (int)cluster_rank() : 0;
-    const int it0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-    const int it_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int n_items = P.n_cell_tiles * P.n_splits;
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
@@ -554,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         }
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&S->full[s]), 1);
-            mbar_init(smem_u32(&S->empty[s]), PAIR ? 2 : 1);
+            mbar_init(smem_u32(&S->empty[s]), 1);
             S->slot_issued[s] = 0;
             S->slot_done[s] = 0;
         }
@@ -584,15 +543,14 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (PAIR) cluster_sync();   // both CTAs' barriers are initialised before any remote arrive or copy
     const uint32_t tmem = S->tmem_base;
 
     if (warp == 2) {
         // ------------------------------------------------ A loader (after the TMEM allocation): the
         // next work item's A tile as soon as the previous use of that buffer is released
         int ctl = 0;
-        for (int it = it0; it < n_items; it += it_step, ++ctl) {
-            const ItemCtx c = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
+            const ItemCtx c = item_ctx<MODE>(P, it, tiles, ford);
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             int ok = 1;
             if (lane == 0) {
@@ -617,8 +575,8 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         // boundaries, limited only by the ring.
         const int me = warp == 0 ? 0 : 1;
         int q = 0;
-        for (int it = it0; it < n_items; it += it_step) {
-            const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
             int ok = *abort_flag ? 0 : 1;
             for (int t = ic.t0; t < ic.t1 && ok; ++t) {
                 const TileDesc td = ic.tiles[t];
@@ -637,12 +595,8 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                         const int k0 = c * kps, kn = min(kps, nks - k0);
                         const uint32_t bytes = (uint32_t)kn * ks_bytes;
                         mbar_expect_tx(smem_u32(&S->full[slot]), bytes);
-                        if (!PAIR)
-                            bulk_g2s(b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes, bsrc + (size_t)k0 * ks_bytes,
-                                     bytes, smem_u32(&S->full[slot]));
-                        else if (((q >> 1) & 1) == rank)
-                            bulk_g2s_pair(b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes, bsrc + (size_t)k0 * ks_bytes,
-                                          bytes, smem_u32(&S->full[slot]));
+                        bulk_g2s(b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes, bsrc + (size_t)k0 * ks_bytes, bytes,
+                                 smem_u32(&S->full[slot]));
                         S->slot_issued[slot] = use + 1;
                     }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -653,8 +607,8 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
         int q = 0, acc_use = 0, ctl = 0;
-        for (int it = it0; it < n_items && !*abort_flag; it += it_step, ++ctl) {
-            const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
+        for (int it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x, ++ctl) {
+            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             if (!mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag)) {
                 fail(P, abort_flag, 4);
@@ -701,9 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                         }
                         acc = 1u;
                     }
-                    // frees the slot (in both CTAs of a pair) once these MMAs retire
-                    if (PAIR) tc_commit_pair(smem_u32(&S->empty[slot]));
-                    else tc_commit(smem_u32(&S->empty[slot]));
+                    tc_commit(smem_u32(&S->empty[slot]));   // frees the slot once these MMAs retire
                     ++q;
                 }
                 if (*abort_flag) break;
@@ -729,8 +681,8 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         const int row = qd * 32 + lane;
         const uint32_t tlane = (uint32_t)(qd * 32) << 16;
         int acc_use = 0, ctl = 0;
-        for (int it = it0; it < n_items; it += it_step, ++ctl) {
-            const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
+            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
             const int ct = ic.ct;
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag))) {
@@ -829,7 +781,6 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                      : "memory");
     }
-    if (PAIR) cluster_sync();   // neither CTA of a pair exits while the other may still write into it
 }
 
 }  // namespace
@@ -1383,7 +1334,7 @@ static void choose_splits(const TcTiles &t, int n_cell_tiles, int n_sm, TcParams
     P.n_splits = ns;
 }
 
-template <int PREC, int MODE, bool PAIR = false>
+template <int PREC, int MODE>
 static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
 {
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
@@ -1405,32 +1356,10 @@ static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
     P.a_bufs = fixed + 2 * a1 + 4 * (size_t)P.slot_bytes <= (size_t)kSmemLimit ? 2 : 1;
     P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed - P.a_bufs * a1) / P.slot_bytes);
     const size_t smem = fixed + P.a_bufs * a1 + (size_t)P.n_slots * P.slot_bytes;
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC, MODE, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
-    if constexpr (PAIR) {
-        // 2-CTA clusters, one pair of cell tiles per work item
-        const int items = P.n_cell_tiles / 2 * P.n_splits;
-        const int clusters = std::min(items, sm_count(dev) / 2);
-        cudaLaunchConfig_t cfg;
-        std::memset(&cfg, 0, sizeof(cfg));
-        cfg.gridDim = dim3(2 * clusters);
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, contract_tc_kernel<PREC, MODE, true>, P);
-        if (e != cudaSuccess) return e;
-        return cudaGetLastError();
-    }
     const int items = P.n_cell_tiles * P.n_splits;
     const int grid = std::min(items, sm_count(dev));
     contract_tc_kernel<PREC, MODE><<<grid, kThreads, smem, st>>>(P);
@@ -1457,8 +1386,8 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
     P.err = d_err;
     int dev = 0;
     cudaGetDevice(&dev);
+    choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
     if (t.nc) {
-        choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
         P.D0 = t.d_D0;
         P.n_d0 = t.n_d0;
         P.cell_s = d_cell_s;
@@ -1467,13 +1396,6 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
         return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeNC>(P, t.max_rows, st)
                                   : launch_prec<GRACE_BF16X3, kModeNC>(P, t.max_rows, st);
     }
-    if (P.n_cell_tiles >= 2 && P.n_cell_tiles % 2 == 0) {
-        // pairs of CTAs share the B stream (half the B copies per CTA)
-        choose_splits(t, P.n_cell_tiles / 2, sm_count(dev) / 2, P);
-        return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeF, true>(P, t.max_rows, st)
-                                  : launch_prec<GRACE_BF16X3, kModeF, true>(P, t.max_rows, st);
-    }
-    choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
     return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeF>(P, t.max_rows, st)
                               : launch_prec<GRACE_BF16X3, kModeF>(P, t.max_rows, st);
 }

@@ -69,7 +69,7 @@ def test_rhs_parity_tensor_core(name, form):
 
 
 @pytest.mark.parametrize("form", FORMS, ids=IDS)
-@pytest.mark.parametrize("n", [1, 127, 129])
+@pytest.mark.parametrize("n", [1, 127, 129, 700])
 def test_small_and_ragged_batches(form, n):
     spec = SPECS["add_N40_k2"]
     g = W.random_coefficients(spec, n, seed=302)

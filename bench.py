@@ -593,7 +593,7 @@ def main():
         forms = [f for f in forms if f in want]
     head = grace.PRECISIONS[args.precision] if args.precision else forms[-1]
     if head not in forms:
-        raise SystemExit(f"precision {args.precision} is not available in this build")
+        raise SystemExit(f"precision {args.precision} was not precomputed by the library")
     if args.steps is None:
         args.steps = 3 if head == grace.FP64 else 50
     b = ctx.batch(n)

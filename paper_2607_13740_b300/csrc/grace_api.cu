@@ -114,7 +114,7 @@ static grace_status validate(const grace_group_desc &d, int idx)
     if (d.n_bins < 2 || d.n_bins > 4096) return bad("n_bins must be in [2, 4096]");
     if (d.order_k < 0) return bad("order_k must be >= 0");
     if (d.order_k > kKMax) {
-        set_error("group " + std::to_string(idx) + ": order_k > 3 is not supported by this build");
+        set_error("group " + std::to_string(idx) + ": order_k > 3 is not supported (the analytic limiter minimum covers k <= 3)");
         return GRACE_ERR_UNSUPPORTED;
     }
     const int Q = d.quad_q > 0 ? d.quad_q : d.order_k + 1;

@@ -194,6 +194,17 @@ def cpu_baseline_disk(spec, alpha, ic, n_cells=8):
                       f"FP64 C oracle, one cell per call on one core, {el:.1f} s"}
 
 
+def max_over_ranks(value, world, device):
+    """The largest of every rank's value (timings: the job ends with its slowest rank); a
+    collective only when world > 1 (gloo on CPU tensors, nccl on CUDA tensors)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank):
     """--impl reference: the oracle timed as it stands on bounded samples of the workload."""
     from paper_2607_13740_b300 import workloads as W
@@ -581,7 +592,10 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    wl = W.batched_additive(n_cells=args.cells or 65536)
+    # weak scaling: each rank steps its own share of a global batch of world x the per-rank cells
+    n_rank = args.cells or 65536
+    wl = W.shard(W.batched_additive(n_cells=n_rank * world), rank, world) if world > 1 else \
+        W.batched_additive(n_cells=n_rank)
     n = wl.n_cells
     candidates = [grace.FP64, grace.TF32, grace.BF16X3]
     ctx = None
@@ -638,11 +652,10 @@ def main():
         c_ms, c_n = ctx.profile_read(0)
         u_ms, u_n = ctx.profile_read(1)
         ctx.profile(False)
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        ms_max = max_over_ranks(ms, world, dev)
         if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dist.barrier()
-        return {"ms": float(t.item()), "contract_ms": c_ms, "contract_launches": c_n, "update_ms": u_ms,
+        return {"ms": ms_max, "contract_ms": c_ms, "contract_launches": c_n, "update_ms": u_ms,
                 "update_launches": u_n, "g": g, "clocks": sampler.summary() if sampler else None}
 
     # accuracy of each form against the FP64 GPU path over the same steps
@@ -758,11 +771,9 @@ def main():
         e1.record(comp)
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1)
-        t = torch.tensor([ems], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems_max = max_over_ranks(ems, world, dev)
         nbytes = host_in.numel() * 8
-        e2e = {"value": n * world * e2e_steps / (float(t.item()) / 1e3), "unit": UNIT,
+        e2e = {"value": n * world * e2e_steps / (ems_max / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
                "pipelining": "upload of step i+1 and download of step i overlap the compute of step i "
                              "(independent batches, pinned host buffers, two copy streams)"}
@@ -782,7 +793,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {grace.FP64: "f64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[head],
         "data": "synthetic",
-        "config": {"workload": wl.name, "cells_per_gpu": n, "n_bins": 40, "order_k": 2,
+        "config": {"workload": wl.name.split("_shard")[0], "cells_per_gpu": n, "global_batch": n * world,
+                   "n_bins": 40, "order_k": 2,
                    "coef_per_cell": wl.spec.n_coef, "kernel": "additive K=x+y", "flux": "conservative",
                    "x_range": [wl.spec.x_min, wl.spec.x_max], "precision": names[head],
                    "l2": "256 MB buffer written between timed steps (outside the timed events)",

@@ -86,6 +86,17 @@ def single_cell_constant(flux_mode=FLUX_NONCONSERVATIVE) -> Workload:
                     np.array([[1.0, 1.0, 0.0, 0.0]]), np.array([1e-2]), 1000)
 
 
+def shard(wl: Workload, rank: int, world: int) -> Workload:
+    """Rank ``rank``'s contiguous share of a workload's cells (weak scaling: the global batch
+    is world x the per-rank batch; shares are disjoint and cover it)."""
+    if world < 1 or not 0 <= rank < world or wl.n_cells % world:
+        raise ValueError("shard: rank outside [0, world) or cells not divisible by world")
+    m = wl.n_cells // world
+    lo, hi = rank * m, (rank + 1) * m
+    return Workload(f"{wl.name}_shard{rank}of{world}", wl.spec, m, wl.ic_kind, wl.ic_params[lo:hi].copy(),
+                    wl.dt[lo:hi].copy(), wl.n_steps, wl.notes)
+
+
 def additive_spec(n_bins=40, order_k=2, x_min=1e-6, x_max=1e10) -> GroupSpec:
     """Pure coagulation with K = x + y (Sec. 4.3), conservative fluxes."""
     return GroupSpec(n_bins, order_k, x_min, x_max, FLUX_CONSERVATIVE, COAG_ADD, (1.0,))

@@ -54,7 +54,9 @@ __global__ void __launch_bounds__(128) contract_pair_kernel(
     }
     __syncwarp();
     const long long cell = cell0 + lane;
-    for (int r = 0; r < R; ++r) {
+    const int r_per = (R + gridDim.y - 1) / gridDim.y;
+    const int r_begin = blockIdx.y * r_per, r_end = min(R, r_begin + r_per);
+    for (int r = r_begin; r < r_end; ++r) {
         double Fr = 0.0;
         for (int p = prange[2 * r]; p < prange[2 * r + 1]; ++p) {
             const int q0 = qlo[r * P + p], q1 = qhi[r * P + p];
@@ -358,7 +360,8 @@ cudaError_t launch_jvp_contract(const DevGroup &g, const double *T, const int *q
     if (wpb < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(contract_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    contract_pair_kernel<<<blocks(n, 32 * wpb), 32 * wpb, smem, st>>>(T, qlo, qhi, prange, g.R, g.P, a, b, n, F);
+    const dim3 grid(blocks(n, 32 * wpb), fp64_functional_chunks(n, g.R));
+    contract_pair_kernel<<<grid, 32 * wpb, smem, st>>>(T, qlo, qhi, prange, g.R, g.P, a, b, n, F);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,10 @@
 // T once, reading each T entry as a warp-wide broadcast.  Warps of a block walk
 // T in the same order, so T is served from L1.  The kernel is bound by the
 // FP64 FMA rate, which on this part is a small fraction of the FP32 rate.
+// Batches with fewer warps than the GPU holds split the functionals over
+// blockIdx.y (each F_r is computed exactly as in one pass).
+#include <algorithm>
+
 #include "grace_internal.h"
 
 namespace grace {
@@ -31,7 +35,9 @@ __global__ void __launch_bounds__(128) contract_fp64_kernel(
     __syncwarp();
 
     const long long cell = cell0 + lane;
-    for (int r = 0; r < R; ++r) {
+    const int r_per = (R + gridDim.y - 1) / gridDim.y;
+    const int r_begin = blockIdx.y * r_per, r_end = min(R, r_begin + r_per);
+    for (int r = r_begin; r < r_end; ++r) {
         const int p0 = prange[2 * r], p1 = prange[2 * r + 1];
         double Fr = 0.0;
         for (int p = p0; p < p1; ++p) {
@@ -53,6 +59,17 @@ __global__ void __launch_bounds__(128) contract_fp64_kernel(
 
 }  // namespace
 
+int fp64_functional_chunks(int n_cells, int R)
+{
+    // enough warps for about 8 per SM; larger batches keep one pass over all functionals
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const long long warps = ((long long)n_cells + 31) / 32, want = 8LL * n_sm;
+    if (warps >= want) return 1;
+    return (int)std::min<long long>(R, (want + warps - 1) / warps);
+}
+
 cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int *d_qlo, const int *d_qhi,
                                  const int *d_prange, const double *d_g, int n_cells, double *d_F,
                                  cudaStream_t st)
@@ -71,8 +88,8 @@ cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int
     }
     const int cells_per_block = 32 * wpb;
     const int blocks = (n_cells + cells_per_block - 1) / cells_per_block;
-    contract_fp64_kernel<<<blocks, 32 * wpb, smem, st>>>(d_T, d_qlo, d_qhi, d_prange, g.R, g.P, d_g, n_cells,
-                                                          d_F);
+    const dim3 grid(blocks, fp64_functional_chunks(n_cells, g.R));
+    contract_fp64_kernel<<<grid, 32 * wpb, smem, st>>>(d_T, d_qlo, d_qhi, d_prange, g.R, g.P, d_g, n_cells, d_F);
     return cudaGetLastError();
 }
 

@@ -202,6 +202,8 @@ int n_functionals(const grace_group_desc &d);
 cudaError_t launch_build_T(const DevGroup &g, double *d_T, cudaStream_t st);
 cudaError_t launch_row_extents(const DevGroup &g, const double *d_T, int *d_qlo, int *d_qhi,
                                int *d_prange, cudaStream_t st);
+// functional chunks (grid y) of the FP64 contractions for a batch of n_cells
+int fp64_functional_chunks(int n_cells, int R);
 cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int *d_qlo,
                                  const int *d_qhi, const int *d_prange, const double *d_g,
                                  int n_cells, double *d_F, cudaStream_t st);

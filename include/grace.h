@@ -83,7 +83,9 @@ enum { GRACE_FLUX_CONSERVATIVE = 0, GRACE_FLUX_NONCONSERVATIVE = 1 };
 /* per-cell status bits written by grace_step / grace_limit */
 enum { GRACE_FLAG_NEGATIVE_MEAN = 1,  /* a cell mean g_j^0 went negative (eq. dt violated) */
        GRACE_FLAG_LIMITED = 2,        /* the scaling limiter changed a bin (eq. gamma < 1)  */
-       GRACE_FLAG_NONFINITE = 4 };    /* a coefficient became Inf or NaN                    */
+       GRACE_FLAG_NONFINITE = 4,      /* a coefficient became Inf or NaN                    */
+       GRACE_FLAG_CFL = 8 };          /* a stage broke eq. (dt) in a bin losing mass:
+                                         L_j^0 < 0 and dt |L_j^0| >= g_j^0 of the stage input */
 
 /* One (grid, order, physics) combination shared by the cells of a group. */
 typedef struct {

@@ -702,6 +702,21 @@ static unsigned stage_flags(const octx *c, const double *g)
     return f;
 }
 
+/* eq. (dt): the forward-Euler update of stage input gs with rhs L keeps the mean of
+   bin j positive when dt |F_{j-1/2} - F_{j+1/2}| < h_j g_j^0, i.e. dt |L_j^0| < g_j^0.
+   The bound protects positivity, so it is tested where the bin loses mass
+   (L_j^0 < 0); a bin with influx or no flux cannot turn negative and is not flagged.
+   Flag bit 3. */
+static unsigned cfl_flags(const octx *c, const double *gs, const double *L, double dt)
+{
+    unsigned f = 0;
+    for (int j = 0; j < c->N; ++j) {
+        const double L0 = L[(size_t)j * (c->k + 1)];
+        if (L0 < 0.0 && -(dt * L0) >= gs[(size_t)j * (c->k + 1)]) f |= 8u;
+    }
+    return f;
+}
+
 /* one SSP-RK3 step (eq. RK3) preceded by the reconstruction (Sec. 3.2) */
 static unsigned step_one(const octx *c, double *g, double dt, double *work)
 {
@@ -710,12 +725,15 @@ static unsigned step_one(const octx *c, double *g, double dt, double *work)
     unsigned f = 0;
     if (c->p.limiter) f |= limit_one(c, g);
     rhs_one(c, g, L, NULL);
+    f |= cfl_flags(c, g, L, dt);
     for (int i = 0; i < P; ++i) g1[i] = g[i] + dt * L[i];
     f |= stage_flags(c, g1);
     rhs_one(c, g1, L, NULL);
+    f |= cfl_flags(c, g1, L, dt);
     for (int i = 0; i < P; ++i) g2[i] = 0.75 * g[i] + 0.25 * (g1[i] + dt * L[i]);
     f |= stage_flags(c, g2);
     rhs_one(c, g2, L, NULL);
+    f |= cfl_flags(c, g2, L, dt);
     for (int i = 0; i < P; ++i) g[i] = g[i] / 3.0 + 2.0 / 3.0 * (g2[i] + dt * L[i]);
     f |= stage_flags(c, g);
     return f;

@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(256) update_kernel(DevGroup G, UpdateArgs A, i
             v[i] = step ? A.a * A.gn[base + i] + A.b * (A.gs[base + i] + dt * L) : L;
         }
         if (step) {
+            // eq. (dt) for this stage's forward-Euler update of the mean
+            if (L0 < 0.0 && -(dt * L0) >= A.gs[base]) fl |= GRACE_FLAG_CFL;
             if (v[0] < 0.0) fl |= GRACE_FLAG_NEGATIVE_MEAN;
             for (int i = 0; i <= k; ++i)
                 if (!isfinite(v[i])) fl |= GRACE_FLAG_NONFINITE;
@@ -258,6 +260,8 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
             const double L0 = (f2d_fast(Fm) - f2d_fast(Fp)) * G.inv_h[j];
             if (MODE == MODE_STAGE) {
                 v0 = fma(A.a, n0, A.b * fma(dt, L0, s0));
+                // eq. (dt) for this stage's forward-Euler update of the mean
+                if (L0 < 0.0 && -(dt * L0) >= s0) fl |= GRACE_FLAG_CFL;
             } else {
                 v0 = L0;
             }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libgrace.so")
 
 FP64, TF32, BF16X3 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16x3": BF16X3}
-FLAG_NEGATIVE_MEAN, FLAG_LIMITED, FLAG_NONFINITE = 1, 2, 4
+FLAG_NEGATIVE_MEAN, FLAG_LIMITED, FLAG_NONFINITE, FLAG_CFL = 1, 2, 4, 8
 
 _lib = None
 _VP = ctypes.c_void_p

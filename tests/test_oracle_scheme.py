@@ -167,3 +167,31 @@ def test_step_conserves_mass_and_batches_independently():
     np.testing.assert_allclose(m, m0, rtol=1e-13)
     g3, _, _ = o.step(g0[3:4], wl.dt[3:4], wl.n_steps)
     np.testing.assert_array_equal(g3[0], g[3])
+
+
+def test_cfl_flag_follows_eq_dt():
+    """eq. (dt): a stage whose forward-Euler update would take a mean negative has broken
+    the bound (flag bit 8 set whenever bit 1 is, for non-negative stage inputs); a step far
+    below the bound sets no flag, although empty tail bins receive influx; a zero state has
+    no flux and sets none; a dt above the first stage's bound min over bins losing mass of
+    g_j^0 / |L_j^0| sets it."""
+    spec = SPECS["add"]
+    o = oracle.Oracle(spec)
+    k = spec.order_k
+    g = o.project(W.IC_EXP, [[1.0, 1.0, 0, 0]] * 3)
+    _, _, f = o.step(g, 1e-9, 1)
+    assert np.all((f & 9) == 0)
+    _, _, f = o.step(np.zeros_like(g), 10.0, 1)
+    assert np.all((f & 9) == 0)
+    L, _ = o.rhs(g[:1])
+    L0 = L.reshape(spec.n_bins, k + 1)[:, 0]
+    g0 = g[0].reshape(spec.n_bins, k + 1)[:, 0]
+    out = L0 < 0
+    bound = (g0[out] / -L0[out]).min()
+    _, _, f = o.step(g[:1], 1.01 * bound, 1)
+    assert f[0] & 8
+    for dt in (0.3 * bound, 3.0 * bound, 30.0 * bound):
+        _, _, f = o.step(g, dt, 2)
+        assert np.all((f & 1) == 0) or np.all(f[(f & 1) != 0] & 8)
+    _, _, f = o.step(g[:1], 30.0 * bound, 1)
+    assert f[0] & 1 and f[0] & 8

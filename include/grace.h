@@ -85,7 +85,8 @@ enum { GRACE_FLAG_NEGATIVE_MEAN = 1,  /* a cell mean g_j^0 went negative (eq. dt
        GRACE_FLAG_LIMITED = 2,        /* the scaling limiter changed a bin (eq. gamma < 1)  */
        GRACE_FLAG_NONFINITE = 4,      /* a coefficient became Inf or NaN                    */
        GRACE_FLAG_CFL = 8 };          /* a stage broke eq. (dt) in a bin losing mass:
-                                         L_j^0 < 0 and dt |L_j^0| >= g_j^0 of the stage input */
+                                         L_j^0 < 0 and g_j^0 + dt L_j^0 <= 0 (one rounding)
+                                         for the stage input g_j^0 */
 
 /* One (grid, order, physics) combination shared by the cells of a group. */
 typedef struct {

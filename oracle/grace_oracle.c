@@ -706,13 +706,14 @@ static unsigned stage_flags(const octx *c, const double *g)
    bin j positive when dt |F_{j-1/2} - F_{j+1/2}| < h_j g_j^0, i.e. dt |L_j^0| < g_j^0.
    The bound protects positivity, so it is tested where the bin loses mass
    (L_j^0 < 0); a bin with influx or no flux cannot turn negative and is not flagged.
-   Flag bit 3. */
+   For L_j^0 < 0 the bound fails exactly when g_j^0 + dt L_j^0 <= 0, evaluated with
+   one rounding (fma), which keeps its sign exact.  Flag bit 3. */
 static unsigned cfl_flags(const octx *c, const double *gs, const double *L, double dt)
 {
     unsigned f = 0;
     for (int j = 0; j < c->N; ++j) {
         const double L0 = L[(size_t)j * (c->k + 1)];
-        if (L0 < 0.0 && -(dt * L0) >= gs[(size_t)j * (c->k + 1)]) f |= 8u;
+        if (L0 < 0.0 && fma(dt, L0, gs[(size_t)j * (c->k + 1)]) <= 0.0) f |= 8u;
     }
     return f;
 }

@@ -65,6 +65,12 @@ __device__ __forceinline__ bool negative_bits(double d)
     return (u >> 63) && mag != 0ull && mag <= 0x7FF0000000000000ull;
 }
 
+// d <= 0 (false for NaN), on the integer pipe
+__device__ __forceinline__ bool nonpositive_bits(double d)
+{
+    return ((unsigned long long)__double_as_longlong(d) << 1) == 0ull || negative_bits(d);
+}
+
 // f * 2^s for a binary32 f (s may be large); results below 2^-126 become 0,
 // above the range +-inf.  Zero stays zero.
 __device__ __forceinline__ float scale_pow2(float f, int s)

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) update_kernel(DevGroup G, UpdateArgs A, i
         }
         if (step) {
             // eq. (dt) for this stage's forward-Euler update of the mean
-            if (L0 < 0.0 && -(dt * L0) >= A.gs[base]) fl |= GRACE_FLAG_CFL;
+            if (L0 < 0.0 && fma(dt, L0, A.gs[base]) <= 0.0) fl |= GRACE_FLAG_CFL;
             if (v[0] < 0.0) fl |= GRACE_FLAG_NEGATIVE_MEAN;
             for (int i = 0; i <= k; ++i)
                 if (!isfinite(v[i])) fl |= GRACE_FLAG_NONFINITE;
@@ -259,9 +259,10 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
             const float Fp = j < G.n_if ? F[j] : 0.f;           // F(x_{j+1/2}), 0 at x_max (cons.)
             const double L0 = (f2d_fast(Fm) - f2d_fast(Fp)) * G.inv_h[j];
             if (MODE == MODE_STAGE) {
-                v0 = fma(A.a, n0, A.b * fma(dt, L0, s0));
+                const double euler = fma(dt, L0, s0);
+                v0 = fma(A.a, n0, A.b * euler);
                 // eq. (dt) for this stage's forward-Euler update of the mean
-                if (L0 < 0.0 && -(dt * L0) >= s0) fl |= GRACE_FLAG_CFL;
+                if (negative_bits(L0) && nonpositive_bits(euler)) fl |= GRACE_FLAG_CFL;
             } else {
                 v0 = L0;
             }

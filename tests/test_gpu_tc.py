@@ -130,3 +130,32 @@ def test_forms_agree_with_fp64_gpu_path():
         L = b.rhs(g, precision=form)
         rel = ((L - L64).abs().amax(dim=1) / L64.abs().amax(dim=1)).max().item()
         assert rel <= 50 * TOL_RHS[form], (form, rel)
+
+
+@pytest.mark.parametrize("form", [grace.FP64] + FORMS, ids=["fp64"] + IDS)
+def test_cfl_status_bit_against_oracle(form):
+    """eq. (dt) status bit on 300 cells (two tiles and a ragged tail): cells stepped at a tenth
+    of the first stage's bound keep it clear, cells at ten times the bound set it, as the
+    oracle does.  FP64 compares every status bit; the tensor forms compare the eq. (dt) and
+    negative-mean bits (their limiter decision is FP32)."""
+    n = 300
+    wl = W.batched_additive(n_cells=n)
+    ctx = _ctx(wl.spec)
+    b = ctx.batch(n)
+    g = b.project(wl.ic_kind, wl.ic_params)
+    g0 = g.cpu().numpy()
+    o = oracle.Oracle(wl.spec)
+    L, _ = o.rhs(g0, threads=8)
+    K1 = wl.spec.order_k + 1
+    L0 = L.reshape(n, -1, K1)[:, :, 0]
+    m0 = g0.reshape(n, -1, K1)[:, :, 0]
+    bound = np.where(L0 < 0, m0 / np.where(L0 < 0, -L0, 1.0), np.inf).min(axis=1)
+    dt = np.where(np.arange(n) % 2 == 1, 10.0, 0.1) * bound
+    flags = torch.zeros(n, dtype=torch.uint8, device=DEV)
+    b.step(g, torch.as_tensor(dt, device=DEV), 1, precision=form, flags=flags)
+    assert b.device_error() == 0
+    _, _, fo = o.step(g0, dt, 1, threads=8)
+    f = flags.cpu().numpy()
+    assert np.all(fo[1::2] & grace.FLAG_CFL) and not np.any(fo[::2] & grace.FLAG_CFL)
+    mask = 0xFF if form == grace.FP64 else grace.FLAG_CFL | grace.FLAG_NEGATIVE_MEAN
+    np.testing.assert_array_equal(f & mask, fo & mask)

@@ -65,10 +65,12 @@ __device__ __forceinline__ bool negative_bits(double d)
     return (u >> 63) && mag != 0ull && mag <= 0x7FF0000000000000ull;
 }
 
-// d <= 0 (false for NaN), on the integer pipe
+// d <= 0 (false for NaN), on the integer pipe: as signed integers the encodings of
+// -0 ... -inf lie at or below that of -inf, negative NaNs above it, and +0 is 0
 __device__ __forceinline__ bool nonpositive_bits(double d)
 {
-    return ((unsigned long long)__double_as_longlong(d) << 1) == 0ull || negative_bits(d);
+    const long long b = __double_as_longlong(d);
+    return b <= (long long)0xFFF0000000000000ull || b == 0ll;
 }
 
 // f * 2^s for a binary32 f (s may be large); results below 2^-126 become 0,

@@ -261,8 +261,9 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
             if (MODE == MODE_STAGE) {
                 const double euler = fma(dt, L0, s0);
                 v0 = fma(A.a, n0, A.b * euler);
-                // eq. (dt) for this stage's forward-Euler update of the mean
-                if (negative_bits(L0) && nonpositive_bits(euler)) fl |= GRACE_FLAG_CFL;
+                // eq. (dt) for this stage's forward-Euler update of the mean; L0 < 0
+                // exactly when Fm < Fp (inv_h > 0, and the FP64 difference keeps the sign)
+                if (Fm < Fp && nonpositive_bits(euler)) fl |= GRACE_FLAG_CFL;
             } else {
                 v0 = L0;
             }

@@ -160,6 +160,29 @@ GRACE_API grace_status grace_rhs(grace_batch *batch, const double *g, double *L,
 GRACE_API grace_status grace_step(grace_batch *batch, double *g, const double *dt, int n_steps, int precision,
                         double *mass, unsigned char *flags);
 
+/* grace_step on host buffers: uploads h_g (host, the packed layout of the
+   batch) and h_dt (host [n_cells]), runs n_steps steps exactly as grace_step
+   (same kernels, same results bit for bit), and downloads the new state to
+   h_out (host, may equal h_g), M_1 to h_mass and the status bits to h_flags
+   (host [n_cells] each, or NULL).  The copies run on two streams owned by the
+   batch and the steps on the bound stream; device staging is double-buffered,
+   so with page-locked host buffers successive calls overlap the upload of the
+   next call and the download of the previous one with the steps.  Returns once
+   the work is enqueued: the caller keeps h_g and h_dt unchanged and reads
+   h_out, h_mass and h_flags only after grace_step_host_wait (synchronising the
+   bound stream alone is not enough).  With pageable host memory the CUDA
+   runtime makes the copies synchronous and nothing overlaps.  The first call
+   allocates two staging copies of the batch's state (and synchronises).  With
+   graph replay on (grace_batch_set_graph) every call uses one staging slot so
+   the graph is reused, and calls do not overlap.  Errors: GRACE_ERR_ARG for a
+   NULL h_g, h_out or h_dt or n_steps < 0, otherwise those of grace_step. */
+GRACE_API grace_status grace_step_host(grace_batch *batch, const double *h_g, double *h_out, const double *h_dt,
+                                       int n_steps, int precision, double *h_mass, unsigned char *h_flags);
+
+/* Waits until every grace_step_host call of the batch has finished its copies
+   (and hence its steps); the host outputs are then complete. */
+GRACE_API grace_status grace_step_host_wait(grace_batch *batch);
+
 /* The FP64 L = L[g] of grace_rhs for n_cells cells of one group, for callers
    that cannot allocate device memory: codes whose device memory belongs to
    another framework's pool allocator, and solvers calling the RHS inside a

@@ -169,9 +169,13 @@ struct grace_batch {
     // grouped tensor-form steps of batches with several groups (grace_batch_set_grouped)
     int use_grouped = 1;
     void *grouped = nullptr;       // the grouped plan (grace_batch.cu), built on first use
+    void *host_io = nullptr;       // staging of grace_step_host (grace_host.cu), built on first use
 };
 
 namespace grace {
+
+// frees the staging of grace_step_host (waits for its copies first)
+void free_host_io(grace_batch *b);
 
 // thread-local error detail
 void set_error(const std::string &msg);

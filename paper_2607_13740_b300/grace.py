@@ -48,7 +48,8 @@ def exported_symbols():
             "grace_limit", "grace_profile_enable", "grace_profile_read", "grace_group_stats",
             "grace_batch_error", "grace_rhs_jvp", "grace_rhs_vjp", "grace_param_grad_setup",
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_set_grouped", "grace_batch_destroy",
-            "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc"]
+            "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
+            "grace_step_host", "grace_step_host_wait"]
 
 
 def load(path: str | None = None):
@@ -89,6 +90,8 @@ def load(path: str | None = None):
     L.grace_probe_rates.argtypes = [S, ctypes.POINTER(ctypes.c_double)]
     L.grace_batch_set_graph.argtypes = [_VP, S]
     L.grace_batch_set_grouped.argtypes = [_VP, S]
+    L.grace_step_host.argtypes = [_VP, _VP, _VP, _VP, S, S, _VP, _VP]
+    L.grace_step_host_wait.argtypes = [_VP]
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -215,6 +218,7 @@ class Batch:
     def __init__(self, ctx: Context, n_cells: int, cell_group=None):
         self.ctx = ctx
         self.n_cells = n_cells
+        self._host_pending = []
         h = _VP()
         cg = None
         if cell_group is not None:
@@ -265,6 +269,35 @@ class Batch:
         _check(load().grace_step(self._h, _ptr(g), _ptr(dt), int(n_steps), int(precision),
                                  _ptr(mass), _ptr(flags)), "grace_step")
         return g
+
+    def _check_host(self, t, numel, dtype, what):
+        import torch
+        if t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+            raise GraceError(f"{what} must be a contiguous {dtype} host tensor of {numel} elements")
+
+    def step_host(self, g, dt, n_steps: int, precision: int = FP64, out=None, mass=None, flags=None):
+        """grace_step on host tensors (float64 g [total] and dt [n_cells]; out, mass, flags host
+        tensors or None; out defaults to g).  Returns once the work is enqueued: read the
+        outputs after wait_host().  Page-locked tensors let successive calls overlap."""
+        import torch
+        self._check_host(g, self.total, torch.float64, "g")
+        self._check_host(dt, self.n_cells, torch.float64, "dt")
+        out = g if out is None else out
+        self._check_host(out, self.total, torch.float64, "out")
+        if mass is not None:
+            self._check_host(mass, self.n_cells, torch.float64, "mass")
+        if flags is not None:
+            self._check_host(flags, self.n_cells, torch.uint8, "flags")
+        self.ctx.set_stream()
+        _check(load().grace_step_host(self._h, _ptr(g), _ptr(out), _ptr(dt), int(n_steps), int(precision),
+                                      _ptr(mass), _ptr(flags)), "grace_step_host")
+        self._host_pending.append((g, dt, out, mass, flags))   # alive until wait_host
+        return out
+
+    def wait_host(self):
+        """Waits for every step_host call of this batch; the host outputs are then complete."""
+        _check(load().grace_step_host_wait(self._h), "grace_step_host_wait")
+        self._host_pending.clear()
 
     def mass(self, g):
         import torch

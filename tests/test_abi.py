@@ -85,3 +85,11 @@ def test_null_arguments_are_errors(lib):
 def test_negative_device_is_rejected_on_host(lib):
     d = grace.group_desc(W.additive_spec(8, 2))
     assert _setup(lib, d, device=-1)[0] == 1
+
+
+def test_host_step_rejects_null_batch(lib):
+    """grace_step_host / grace_step_host_wait check their arguments before any CUDA call."""
+    buf = (ctypes.c_double * 4)()
+    assert lib.grace_step_host(None, buf, buf, buf, 1, 0, None, None) == 1
+    assert lib.grace_step_host_wait(None) == 1
+    assert "grace_step_host" in lib.grace_last_error().decode()

@@ -31,6 +31,24 @@ __device__ __forceinline__ unsigned warp_or(unsigned v)
     return v;
 }
 
+// asynchronous global -> shared copies of 4 or 8 bytes (a thread issues all of its copies
+// before waiting, so a block has its whole input in flight at once)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Writes one cell's new coefficients, staged in shared memory, to the FP64 state
 // (coalesced) and, if requested, to the cell's row of the tensor-core A operand
 // as whole 16-byte chunks (TF32: 4 values, BF16: 8 hi + 8 lo values per chunk).
@@ -189,23 +207,48 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
 {
     extern __shared__ double sm[];
     constexpr int CPB = kUpdWarps * 32 / LPC;                     // cells per block (a divisor of 128)
+    // compact stage inputs and compact output: the block's stage inputs are staged in shared
+    // memory (the FP64 row buffer is not needed, so a cell's region holds only its ghat row)
+    constexpr bool STAGED = MODE == MODE_STAGE && IN_MIX && OUT_MIX;
     const int N = G.N, k = G.k, K1 = G.K1, P = G.P, R = G.R;
     const int slot = threadIdx.x / LPC, lane = threadIdx.x % LPC;
     const long long cell0 = block * CPB;
     const long long cell = cell0 + slot;
     const int lda = A.opA_kpad;
-    double *row = sm + (size_t)slot * (P + lda / 2 + 1);          // new coefficients of the cell
-    float *arow = reinterpret_cast<float *>(row + P);             // its ghat row (A operand), kpad floats
+    const size_t cell_dbl = (STAGED ? 0 : P) + lda / 2 + 1;       // doubles per cell region
+    double *row = sm + (size_t)slot * cell_dbl;                   // new coefficients of the cell
+    float *arow = reinterpret_cast<float *>(row + (STAGED ? 0 : P));  // its ghat row (A operand), kpad floats
     // the block's functionals, transposed to [cell][functional]: read from the contraction's
     // [tile][functional][row] layout as CPB-float pieces of each functional's row
-    float *Fs = reinterpret_cast<float *>(sm + (size_t)CPB * (P + lda / 2 + 1));
+    float *Fs = reinterpret_cast<float *>(sm + (size_t)CPB * cell_dbl);
+    // staged inputs: means of g^(s) and g^n [CPB][N] (FP64), higher modes [CPB][N][k] (FP32)
+    double *St_s = sm + (size_t)CPB * cell_dbl + ((size_t)CPB * (R + 1) + 1) / 2;
+    double *St_n = St_s + (size_t)CPB * N;
+    float *St_sh = reinterpret_cast<float *>(St_n + (size_t)CPB * N);
+    float *St_nh = St_sh + (size_t)CPB * N * k;
+    const size_t nN = (size_t)n_cells * N;
     if (MODE != MODE_LIMIT) {
-        const float *Ft = A.F32 + ((size_t)(cell0 >> 7) * R) * kTileM + (cell0 & (kTileM - 1));
         const int nc = (int)min((long long)CPB, (long long)n_cells - cell0);
+        if (STAGED) {
+            // the block's cells are contiguous in both arrays of the compact layout
+            const double *gsm = A.gs + (size_t)cell0 * N, *gnm = A.gn + (size_t)cell0 * N;
+            const float *gsh = reinterpret_cast<const float *>(A.gs + nN) + (size_t)cell0 * N * k;
+            const float *gnh = reinterpret_cast<const float *>(A.gn + nN) + (size_t)cell0 * N * k;
+            for (int i = threadIdx.x; i < nc * N; i += 32 * kUpdWarps) {
+                cp_async8(St_s + i, gsm + i);
+                cp_async8(St_n + i, gnm + i);
+            }
+            for (int i = threadIdx.x; i < nc * N * k; i += 32 * kUpdWarps) {
+                cp_async4(St_sh + i, gsh + i);
+                cp_async4(St_nh + i, gnh + i);
+            }
+        }
+        const float *Ft = A.F32 + ((size_t)(cell0 >> 7) * R) * kTileM + (cell0 & (kTileM - 1));
         for (int idx = threadIdx.x; idx < R * CPB; idx += 32 * kUpdWarps) {
             const int r = idx / CPB, c = idx - r * CPB;
-            if (c < nc) Fs[c * (R + 1) + r] = Ft[(size_t)r * kTileM + c];
+            if (c < nc) cp_async4(Fs + c * (R + 1) + r, Ft + (size_t)r * kTileM + c);
         }
+        cp_async_wait_all();
         __syncthreads();
     }
     if (cell >= n_cells) return;   // whole groups of LPC lanes leave together
@@ -213,7 +256,6 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
     // stage inputs: s = gs (MODE_STAGE), or the state to limit (MODE_LIMIT, FP64 rows in A.gs)
     const double *srcs = MODE == MODE_LIMIT ? A.gs : A.gs;
     const double *srcn = MODE == MODE_STAGE ? A.gn : srcs;
-    const size_t nN = (size_t)n_cells * N;
     const double dt = MODE == MODE_STAGE ? A.dt[cell] : 0.0;
     const float af = (float)A.a, bf = (float)A.b, dtf = MODE == MODE_STAGE ? d2f_fast(dt) : 0.f;
     double msum = 0.0;
@@ -224,7 +266,18 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
         float sf[kB], nf_[kB];
         double vd[kB];     // MODE_LIMIT: the FP64 higher modes
         if (MODE != MODE_RHS) {
-            if (IN_MIX) {
+            if (STAGED) {
+                s0 = St_s[slot * N + j];
+                n0 = St_n[slot * N + j];
+                const float *sh = St_sh + (size_t)(slot * N + j) * k;
+                const float *nh = St_nh + (size_t)(slot * N + j) * k;
+#pragma unroll
+                for (int i = 1; i < kB; ++i) {
+                    sf[i] = i <= k ? sh[i - 1] : 0.f;
+                    nf_[i] = i <= k ? nh[i - 1] : 0.f;
+                    vd[i] = f2d_fast(sf[i]);
+                }
+            } else if (IN_MIX) {
                 s0 = srcs[cell * N + j];
                 n0 = srcn[cell * N + j];
                 const float *sh = reinterpret_cast<const float *>(srcs + nN) + ((size_t)cell * N + j) * k;
@@ -489,12 +542,18 @@ cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, c
     return cudaGetLastError();
 }
 
-// shared memory of update_tc_kernel: one row (P doubles) and one ghat row (kpad floats) per cell,
-// then the block's functionals [cells][R + 1] floats
+// shared memory of update_tc_kernel: one row (P doubles; not with compact stage inputs and
+// output) and one ghat row (kpad floats) per cell, then the block's functionals [cells][R + 1]
+// floats, then (compact stage inputs and output) the staged inputs: 2 x [cells][N] doubles and
+// 2 x [cells][N][k] floats
 static size_t update_tc_smem(const DevGroup &g, const UpdateArgs &a, int lpc)
 {
     const size_t cpb = (size_t)kUpdWarps * 32 / lpc;
-    return cpb * (g.P + a.opA_kpad / 2 + 1) * sizeof(double) + cpb * (g.R + 1) * sizeof(float);
+    const bool staged = a.dt && a.F32 && a.in_mixed && a.out_mixed;
+    const size_t cell_dbl = (staged ? 0 : g.P) + a.opA_kpad / 2 + 1;
+    size_t bytes = (cpb * cell_dbl + (cpb * (g.R + 1) + 1) / 2) * sizeof(double);
+    if (staged) bytes += cpb * g.N * (2 * sizeof(double) + 2 * sizeof(float) * g.k);
+    return bytes;
 }
 
 template <int MODE, int LPC, bool IN_MIX, bool OUT_MIX>

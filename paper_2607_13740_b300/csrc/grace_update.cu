@@ -210,9 +210,6 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
     // compact stage inputs and compact output: the block's stage inputs are staged in shared
     // memory (the FP64 row buffer is not needed, so a cell's region holds only its ghat row)
     constexpr bool STAGED = MODE == MODE_STAGE && IN_MIX && OUT_MIX;
-    // the step-start limiter into the compact layout: the FP64 rows to limit are staged in the
-    // (otherwise unused) FP64 row buffer
-    constexpr bool STAGED_ROWS = MODE == MODE_LIMIT && !IN_MIX && OUT_MIX;
     const int N = G.N, k = G.k, K1 = G.K1, P = G.P, R = G.R;
     const int slot = threadIdx.x / LPC, lane = threadIdx.x % LPC;
     const long long cell0 = block * CPB;
@@ -250,16 +247,6 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
         for (int idx = threadIdx.x; idx < R * CPB; idx += 32 * kUpdWarps) {
             const int r = idx / CPB, c = idx - r * CPB;
             if (c < nc) cp_async4(Fs + c * (R + 1) + r, Ft + (size_t)r * kTileM + c);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-    }
-    if (STAGED_ROWS) {
-        const int nc = (int)min((long long)CPB, (long long)n_cells - cell0);
-        const double *src = A.gs + (size_t)cell0 * P;      // the block's rows are contiguous
-        for (int idx = threadIdx.x; idx < nc * P; idx += 32 * kUpdWarps) {
-            const int c = idx / P;
-            cp_async8(sm + (size_t)c * cell_dbl + (idx - c * P), src + idx);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -302,8 +289,8 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
                     vd[i] = f2d_fast(sf[i]);
                 }
             } else {
-                const double *vs = STAGED_ROWS ? row + (size_t)j * K1 : srcs + (size_t)cell * P + (size_t)j * K1;
-                const double *vn = STAGED_ROWS ? vs : srcn + (size_t)cell * P + (size_t)j * K1;
+                const double *vs = srcs + (size_t)cell * P + (size_t)j * K1;
+                const double *vn = srcn + (size_t)cell * P + (size_t)j * K1;
                 s0 = vs[0];
                 n0 = vn[0];
 #pragma unroll

@@ -177,14 +177,16 @@ __global__ void __launch_bounds__(256) limit_kernel(DevGroup G, double *g, int n
 }
 
 // ---------------------------------------------------------------------------
-// K-c for the tensor path.  One warp per cell, one lane per bin (j = lane,
-// lane + 32, ...).  The stage inputs are read directly (each lane reads its
-// bin's K1 contiguous doubles, so a warp reads one contiguous span); the new row
-// and its A-operand row are assembled in a small per-warp shared-memory buffer and
-// written out coalesced.  The functionals come from the contraction in the
-// [tile][functional][row] layout.  Only the mean row (i = 0: flux difference,
-// stage combination, mass) uses FP64 arithmetic; the higher modes, the limiter
-// and all conversions run on the FP32 and integer pipes.
+// K-c for the tensor path.  LPC lanes per cell (8, 16 or 32), lane l taking bins
+// l, l + LPC, ...  Each block first copies its cells' functionals (from the
+// contraction's [tile][functional][row] layout) into shared memory with cp.async;
+// with compact stage inputs and a compact result it copies the stage inputs too,
+// so every load of the block is in flight at once.  Otherwise the stage inputs
+// are read bin by bin.  A compact result is written by each lane directly; an
+// FP64 row and the A-operand row are assembled in shared memory and written out
+// coalesced.  Only the mean row (i = 0: flux difference, stage combination, the
+// eq. (dt) test, mass) uses FP64 arithmetic; the higher modes, the limiter and
+// all conversions run on the FP32 and integer pipes.
 //   MODE_RHS   : gout = L[g]                            (F32 required)
 //   MODE_STAGE : gout = a gn + b (gs + dt L[gs]), then the limiter when asked
 //   MODE_LIMIT : g = limit(g) (when asked) and the next A operand (no F32)
@@ -254,7 +256,7 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
     if (cell >= n_cells) return;   // whole groups of LPC lanes leave together
     const float *F = Fs + slot * (R + 1);
     // stage inputs: s = gs (MODE_STAGE), or the state to limit (MODE_LIMIT, FP64 rows in A.gs)
-    const double *srcs = MODE == MODE_LIMIT ? A.gs : A.gs;
+    const double *srcs = A.gs;
     const double *srcn = MODE == MODE_STAGE ? A.gn : srcs;
     const double dt = MODE == MODE_STAGE ? A.dt[cell] : 0.0;
     const float af = (float)A.a, bf = (float)A.b, dtf = MODE == MODE_STAGE ? d2f_fast(dt) : 0.f;

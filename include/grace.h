@@ -51,7 +51,9 @@ typedef enum {
     GRACE_ERR_CUDA = 3,         /* a CUDA runtime call failed                          */
     GRACE_ERR_NOMEM = 4,        /* device or host allocation failed                    */
     GRACE_ERR_UNSUPPORTED = 5,  /* valid request the build does not implement          */
-    GRACE_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up                  */
+    GRACE_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                  */
+    GRACE_WARN_CELLS = 100      /* grace_flags_check: some cell has a status bit set;
+                                   every result was written                           */
 } grace_status;
 
 /* arithmetic of the bulk flux contraction (Sec. 3.3 quadrature, folded into a
@@ -84,9 +86,13 @@ enum { GRACE_FLUX_CONSERVATIVE = 0, GRACE_FLUX_NONCONSERVATIVE = 1 };
 enum { GRACE_FLAG_NEGATIVE_MEAN = 1,  /* a cell mean g_j^0 went negative (eq. dt violated) */
        GRACE_FLAG_LIMITED = 2,        /* the scaling limiter changed a bin (eq. gamma < 1)  */
        GRACE_FLAG_NONFINITE = 4,      /* a coefficient became Inf or NaN                    */
-       GRACE_FLAG_CFL = 8 };          /* a stage broke eq. (dt) in a bin losing mass:
+       GRACE_FLAG_CFL = 8,            /* a stage broke eq. (dt) in a bin losing mass:
                                          L_j^0 < 0 and g_j^0 + dt L_j^0 <= 0 (one rounding)
                                          for the stage input g_j^0 */
+       GRACE_FLAG_MASS_DRIFT = 16 };  /* conservative groups: M_1 = sum_j h_j g_j^0 changed
+                                         over the grace_step call by more than 1e-10 of its
+                                         value, or became NaN (eq. g0 conserves it to
+                                         round-off) */
 
 /* One (grid, order, physics) combination shared by the cells of a group. */
 typedef struct {
@@ -156,7 +162,10 @@ GRACE_API grace_status grace_rhs(grace_batch *batch, const double *g, double *L,
    (eqs. recon, gamma) when the group enables it, in place on g (device).
    dt: device [n_cells] per-cell time steps.  mass (device [n_cells] or NULL)
    receives M_1 = sum_j h_j g_j^0 after the last step; flags (device
-   [n_cells] or NULL) receives the OR of GRACE_FLAG_* bits over all stages. */
+   [n_cells] or NULL) receives the OR of GRACE_FLAG_* bits over all stages,
+   and the mass-drift bit from M_1 before and after the call (two extra mass
+   passes; the first call with flags allocates 17 bytes per cell and
+   synchronises). */
 GRACE_API grace_status grace_step(grace_batch *batch, double *g, const double *dt, int n_steps, int precision,
                         double *mass, unsigned char *flags);
 
@@ -295,6 +304,13 @@ GRACE_API grace_status grace_tile_info(const grace_ctx *ctx, int group, int prec
    the batch's cell order (entries of other groups are ignored), copied.
    GRACE_ERR_ORDER from grace_rhs / grace_step on such a batch until this was called. */
 GRACE_API grace_status grace_batch_cell_params(grace_batch *batch, const double *alpha);
+
+/* OR of flags (device [n_cells], as written by grace_step / grace_limit) over
+   the batch's cells, into *any (host, may be NULL).  Synchronises the bound
+   stream (compute calls never do, so they report per-cell problems only
+   through the flags array).  Returns GRACE_WARN_CELLS when some bit is set,
+   GRACE_OK otherwise. */
+GRACE_API grace_status grace_flags_check(grace_batch *batch, const unsigned char *flags, unsigned *any);
 
 /* Reads and clears the batch's device error word: non-zero bits mean a bounded
    device-side wait inside a tensor-core launch gave up (the launch then wrote

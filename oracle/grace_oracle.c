@@ -894,8 +894,13 @@ int orc_step_batch(const orc_params *p, int n_cells, double *g, const double *dt
             for (int cell = 0; cell < n_cells; ++cell) {
                 double *gc = g + (size_t)cell * P;
                 unsigned f = 0;
+                const double m0 = mass_one(&c, gc);
                 for (int s = 0; s < n_steps; ++s) f |= step_one(&c, gc, dt[cell], work);
-                if (mass) mass[cell] = mass_one(&c, gc);
+                const double m1 = mass_one(&c, gc);
+                /* eq. (g0): conservative fluxes keep M_1 to round-off; bit 4 marks a change
+                   above 1e-10 of M_1 over the call (or a NaN) */
+                if (c.p.flux_mode == 0 && !(fabs(m1 - m0) <= 1e-10 * fabs(m0))) f |= 16u;
+                if (mass) mass[cell] = m1;
                 if (flags) flags[cell] = (unsigned char)f;
             }
             free(work);

@@ -186,6 +186,7 @@ const char *grace_status_string(grace_status s)
     case GRACE_ERR_NOMEM: return "out of memory";
     case GRACE_ERR_UNSUPPORTED: return "unsupported";
     case GRACE_ERR_TIMEOUT: return "device wait timed out";
+    case GRACE_WARN_CELLS: return "some cells have status bits set";
     default: return "unknown status";
     }
 }

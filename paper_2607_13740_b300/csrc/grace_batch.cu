@@ -740,6 +740,67 @@ static cudaError_t step_body(grace_batch *b, double *g, const double *dt, int n_
     });
 }
 
+static cudaError_t mass_body(grace_batch *b, const double *g, double *mass)
+{
+    return for_parts(b, [&](Part &p, cudaStream_t st) {
+        const DevGroup &dg = b->ctx->groups[p.group].dg;
+        if (p.direct) return launch_mass(dg, g, p.n, mass, st);
+        cudaError_t r = gather_state(p, dg.P, g, p.d_g, st);
+        if (r == cudaSuccess) r = launch_mass(dg, p.d_g, p.n, p.d_mass, st);
+        if (r == cudaSuccess) {
+            scatter_kernel<double><<<nb(p.n), 256, 0, st>>>(p.n, p.d_idx, p.d_mass, mass);
+            r = cudaGetLastError();
+        }
+        return r;
+    });
+}
+
+// mass-drift bit: M_1 of a cell of a conservative group changed over the call by more than
+// kDriftTol of its value (or became NaN); the scheme conserves it to round-off (eq. g0)
+constexpr double kDriftTol = 1e-10;
+
+__global__ void drift_kernel(int n, const double *__restrict__ m0, const double *__restrict__ m1,
+                             const unsigned char *__restrict__ cons, unsigned char *__restrict__ flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && cons[i] && !(fabs(m1[i] - m0[i]) <= kDriftTol * fabs(m0[i])))
+        flags[i] |= (unsigned char)GRACE_FLAG_MASS_DRIFT;
+}
+
+// the workspaces of the drift bit, allocated outside any graph capture
+static cudaError_t ensure_drift(grace_batch *b)
+{
+    if (b->d_drift) return cudaSuccess;
+    const int n = b->n_cells;
+    std::vector<unsigned char> cons(n);
+    for (int c = 0; c < n; ++c) cons[c] = b->ctx->groups[b->h_group[c]].dg.flux_mode == 0 ? 1 : 0;
+    cudaError_t e = cudaMalloc(&b->d_drift, (size_t)2 * n * sizeof(double) + n);
+    if (e != cudaSuccess) {
+        b->d_drift = nullptr;
+        return e;
+    }
+    return cudaMemcpy(reinterpret_cast<unsigned char *>(b->d_drift + 2 * (size_t)n), cons.data(), n,
+                      cudaMemcpyHostToDevice);
+}
+
+// step_body, plus the mass-drift bit when flags are requested
+static cudaError_t step_flagged(grace_batch *b, double *g, const double *dt, int n_steps, int prec, double *mass,
+                                unsigned char *flags)
+{
+    if (!flags) return step_body(b, g, dt, n_steps, prec, mass, flags);
+    const int n = b->n_cells;
+    double *m0 = b->d_drift, *m1 = b->d_drift + n;
+    const unsigned char *cons = reinterpret_cast<const unsigned char *>(b->d_drift + 2 * (size_t)n);
+    cudaError_t e = mass_body(b, g, m0);
+    if (e == cudaSuccess) e = step_body(b, g, dt, n_steps, prec, mass, flags);
+    if (e == cudaSuccess) e = mass_body(b, g, m1);
+    if (e == cudaSuccess) {
+        drift_kernel<<<(n + 255) / 256, 256, 0, b->ctx->stream>>>(n, m0, m1, cons, flags);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 grace_status grace_step(grace_batch *b, double *g, const double *dt, int n_steps, int prec, double *mass,
                         unsigned char *flags)
 {
@@ -756,8 +817,12 @@ grace_status grace_step(grace_batch *b, double *g, const double *dt, int n_steps
         s = grouped_prepare(b, prec, mass != nullptr, flags != nullptr);
         if (s != GRACE_OK) return s;
     }
+    if (flags) {
+        e = ensure_drift(b);
+        if (e != cudaSuccess) return cuda_fail(e, "grace_step: mass-drift workspace");
+    }
     if (!b->use_graph) {
-        e = step_body(b, g, dt, n_steps, prec, mass, flags);
+        e = step_flagged(b, g, dt, n_steps, prec, mass, flags);
         return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_step");
     }
     // CUDA graph: capture the whole call once per argument set, then replay it
@@ -776,7 +841,7 @@ grace_status grace_step(grace_batch *b, double *g, const double *dt, int n_steps
         e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
             b->ctx->capturing = 1;
-            cudaError_t body = step_body(b, g, dt, n_steps, prec, mass, flags);
+            cudaError_t body = step_flagged(b, g, dt, n_steps, prec, mass, flags);
             b->ctx->capturing = 0;
             e = cudaStreamEndCapture(st, &graph);
             if (body != cudaSuccess) e = body;
@@ -832,17 +897,7 @@ grace_status grace_mass(grace_batch *b, const double *g, double *mass)
         return GRACE_ERR_ARG;
     }
     Guard guard(b->ctx->device);
-    cudaError_t e = for_parts(b, [&](Part &p, cudaStream_t st) {
-        const DevGroup &dg = b->ctx->groups[p.group].dg;
-        if (p.direct) return launch_mass(dg, g, p.n, mass, st);
-        cudaError_t r = gather_state(p, dg.P, g, p.d_g, st);
-        if (r == cudaSuccess) r = launch_mass(dg, p.d_g, p.n, p.d_mass, st);
-        if (r == cudaSuccess) {
-            scatter_kernel<double><<<nb(p.n), 256, 0, st>>>(p.n, p.d_idx, p.d_mass, mass);
-            r = cudaGetLastError();
-        }
-        return r;
-    });
+    const cudaError_t e = mass_body(b, g, mass);
     return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_mass");
 }
 
@@ -908,6 +963,38 @@ grace_status grace_batch_cell_params(grace_batch *b, const double *alpha)
     return GRACE_OK;
 }
 
+__global__ void flags_or_kernel(int n, const unsigned char *__restrict__ flags, unsigned *__restrict__ out)
+{
+    unsigned v = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v |= flags[i];
+    v = __reduce_or_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && v) atomicOr(out, v);
+}
+
+grace_status grace_flags_check(grace_batch *b, const unsigned char *flags, unsigned *any)
+{
+    if (!b || !flags) {
+        set_error("grace_flags_check: null argument");
+        return GRACE_ERR_ARG;
+    }
+    Guard guard(b->ctx->device);
+    cudaStream_t st = b->ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (!b->d_flag_or) e = cudaMalloc(&b->d_flag_or, sizeof(unsigned));
+    unsigned h = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flag_or, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        const int blocks = (int)std::min<long long>(((long long)b->n_cells + 255) / 256, 1184);
+        flags_or_kernel<<<blocks, 256, 0, st>>>(b->n_cells, flags, b->d_flag_or);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, b->d_flag_or, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "grace_flags_check");
+    if (any) *any = h;
+    return h ? GRACE_WARN_CELLS : GRACE_OK;
+}
+
 grace_status grace_batch_error(grace_batch *b, int *code)
 {
     if (!b) {
@@ -938,6 +1025,8 @@ void grace_batch_destroy(grace_batch *b)
     for (Part &p : b->parts) free_part(p);
     cudaFree(b->d_err);
     cudaFree(b->d_adj);
+    cudaFree(b->d_drift);
+    cudaFree(b->d_flag_or);
     if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }

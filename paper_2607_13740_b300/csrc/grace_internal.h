@@ -170,6 +170,9 @@ struct grace_batch {
     int use_grouped = 1;
     void *grouped = nullptr;       // the grouped plan (grace_batch.cu), built on first use
     void *host_io = nullptr;       // staging of grace_step_host (grace_host.cu), built on first use
+    double *d_drift = nullptr;     // M_1 before / after a flagged grace_step [2][n] + per-cell
+                                   // conservative-group bytes [n], built on the first flagged call
+    unsigned *d_flag_or = nullptr; // grace_flags_check's reduction word
 };
 
 namespace grace {

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libgrace.so")
 
 FP64, TF32, BF16X3 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16x3": BF16X3}
-FLAG_NEGATIVE_MEAN, FLAG_LIMITED, FLAG_NONFINITE, FLAG_CFL = 1, 2, 4, 8
+FLAG_NEGATIVE_MEAN, FLAG_LIMITED, FLAG_NONFINITE, FLAG_CFL, FLAG_MASS_DRIFT = 1, 2, 4, 8, 16
+WARN_CELLS = 100
 
 _lib = None
 _VP = ctypes.c_void_p
@@ -49,7 +50,7 @@ def exported_symbols():
             "grace_batch_error", "grace_rhs_jvp", "grace_rhs_vjp", "grace_param_grad_setup",
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_set_grouped", "grace_batch_destroy",
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
-            "grace_step_host", "grace_step_host_wait"]
+            "grace_step_host", "grace_step_host_wait", "grace_flags_check"]
 
 
 def load(path: str | None = None):
@@ -92,6 +93,7 @@ def load(path: str | None = None):
     L.grace_batch_set_grouped.argtypes = [_VP, S]
     L.grace_step_host.argtypes = [_VP, _VP, _VP, _VP, S, S, _VP, _VP]
     L.grace_step_host_wait.argtypes = [_VP]
+    L.grace_flags_check.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_uint)]
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -298,6 +300,18 @@ class Batch:
         """Waits for every step_host call of this batch; the host outputs are then complete."""
         _check(load().grace_step_host_wait(self._h), "grace_step_host_wait")
         self._host_pending.clear()
+
+    def flags_check(self, flags) -> int:
+        """OR of a device flags array over the batch (synchronises the bound stream)."""
+        import torch
+        if not (flags.is_cuda and flags.dtype == torch.uint8 and flags.numel() == self.n_cells):
+            raise GraceError(f"flags must be a uint8 CUDA tensor of {self.n_cells} elements")
+        out = ctypes.c_uint()
+        self.ctx.set_stream()
+        st = load().grace_flags_check(self._h, _ptr(flags), ctypes.byref(out))
+        if st != WARN_CELLS:
+            _check(st, "grace_flags_check")
+        return out.value
 
     def mass(self, g):
         import torch

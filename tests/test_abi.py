@@ -93,3 +93,8 @@ def test_host_step_rejects_null_batch(lib):
     assert lib.grace_step_host(None, buf, buf, buf, 1, 0, None, None) == 1
     assert lib.grace_step_host_wait(None) == 1
     assert "grace_step_host" in lib.grace_last_error().decode()
+
+
+def test_flags_check_rejects_null_and_names_warn_status(lib):
+    assert lib.grace_flags_check(None, None, None) == 1
+    assert lib.grace_status_string(grace.WARN_CELLS).decode() != "unknown status"

@@ -195,3 +195,22 @@ def test_cfl_flag_follows_eq_dt():
         assert np.all((f & 1) == 0) or np.all(f[(f & 1) != 0] & 8)
     _, _, f = o.step(g[:1], 30.0 * bound, 1)
     assert f[0] & 1 and f[0] & 8
+
+
+def test_mass_drift_bit():
+    """eq. (g0): a conservative group keeps M_1 to round-off, so a normal call sets no drift bit
+    (16); a non-conservative group loses mass through x_max by design and is not tested; a call
+    whose state overflows (M_1 becomes inf or NaN) sets it next to the non-finite bit (4)."""
+    spec = SPECS["add"]
+    o = oracle.Oracle(spec)
+    g = o.project(W.IC_EXP, [[1.0, 1.0, 0, 0]] * 2)
+    _, _, f = o.step(g, 1e-3, 5)
+    assert np.all((f & 16) == 0)
+    _, _, f = o.step(g, 1e300, 3)
+    assert np.all(f & 16) and np.all(f & 4)
+    nc = W.additive_spec(8, 2, 1e-3, 1e2).replace(flux_mode=1)
+    onc = oracle.Oracle(nc)
+    gnc = onc.project(W.IC_EXP, [[1.0, 1.0, 0, 0]])
+    m0 = onc.mass(gnc)[0]
+    _, m, f = onc.step(gnc, 0.05, 20)
+    assert abs(m[0] - m0) > 1e-6 * m0 and (f[0] & 16) == 0

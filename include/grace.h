@@ -89,10 +89,11 @@ enum { GRACE_FLAG_NEGATIVE_MEAN = 1,  /* a cell mean g_j^0 went negative (eq. dt
        GRACE_FLAG_CFL = 8,            /* a stage broke eq. (dt) in a bin losing mass:
                                          L_j^0 < 0 and g_j^0 + dt L_j^0 <= 0 (one rounding)
                                          for the stage input g_j^0 */
-       GRACE_FLAG_MASS_DRIFT = 16 };  /* conservative groups: M_1 = sum_j h_j g_j^0 changed
-                                         over the grace_step call by more than 1e-10 of its
-                                         value, or became NaN (eq. g0 conserves it to
-                                         round-off) */
+       GRACE_FLAG_MASS_DRIFT = 16 };  /* conservative groups, cells with none of the bits
+                                         above but LIMITED: M_1 = sum_j h_j g_j^0 changed over
+                                         the grace_step call by more than 1e-9 of its value, or
+                                         became NaN (eq. g0 with eq. dt kept conserves it to
+                                         round-off, so the bit means a conservation failure) */
 
 /* One (grid, order, physics) combination shared by the cells of a group. */
 typedef struct {

@@ -897,9 +897,12 @@ int orc_step_batch(const orc_params *p, int n_cells, double *g, const double *dt
                 const double m0 = mass_one(&c, gc);
                 for (int s = 0; s < n_steps; ++s) f |= step_one(&c, gc, dt[cell], work);
                 const double m1 = mass_one(&c, gc);
-                /* eq. (g0): conservative fluxes keep M_1 to round-off; bit 4 marks a change
-                   above 1e-10 of M_1 over the call (or a NaN) */
-                if (c.p.flux_mode == 0 && !(fabs(m1 - m0) <= 1e-10 * fabs(m0))) f |= 16u;
+                /* eq. (g0): conservative fluxes keep M_1 to round-off while every stage keeps
+                   eq. (dt) (each bin's update below the bin's mass); bit 4 marks a change above
+                   1e-9 of M_1 over the call (or a NaN) in a cell with no negative-mean,
+                   non-finite or eq. (dt) bit */
+                if (c.p.flux_mode == 0 && !(f & (1u | 4u | 8u)) && !(fabs(m1 - m0) <= 1e-9 * fabs(m0)))
+                    f |= 16u;
                 if (mass) mass[cell] = m1;
                 if (flags) flags[cell] = (unsigned char)f;
             }

@@ -756,14 +756,18 @@ static cudaError_t mass_body(grace_batch *b, const double *g, double *mass)
 }
 
 // mass-drift bit: M_1 of a cell of a conservative group changed over the call by more than
-// kDriftTol of its value (or became NaN); the scheme conserves it to round-off (eq. g0)
-constexpr double kDriftTol = 1e-10;
+// kDriftTol of its value (or became NaN) although every stage kept eq. (dt) and left the means
+// non-negative and finite.  Under eq. (dt) each bin's update is smaller than the bin's mass, so
+// the scheme conserves M_1 to round-off (eq. g0); cells with one of those bits set are already
+// flagged, and their M_1 can move by round-off of a much larger state.
+constexpr double kDriftTol = 1e-9;
+constexpr unsigned char kDriftSkip = GRACE_FLAG_NEGATIVE_MEAN | GRACE_FLAG_NONFINITE | GRACE_FLAG_CFL;
 
 __global__ void drift_kernel(int n, const double *__restrict__ m0, const double *__restrict__ m1,
                              const unsigned char *__restrict__ cons, unsigned char *__restrict__ flags)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && cons[i] && !(fabs(m1[i] - m0[i]) <= kDriftTol * fabs(m0[i])))
+    if (i < n && cons[i] && !(flags[i] & kDriftSkip) && !(fabs(m1[i] - m0[i]) <= kDriftTol * fabs(m0[i])))
         flags[i] |= (unsigned char)GRACE_FLAG_MASS_DRIFT;
 }
 

@@ -558,8 +558,13 @@ static void free_grouped(grace_batch *b)
 static bool grouped_applies(grace_batch *b, int prec, int n_steps)
 {
     if (!b->use_grouped || prec == GRACE_FP64 || n_steps < 1 || b->parts.size() < 2) return false;
-    for (const Part &p : b->parts)
-        if (p.direct || b->ctx->groups[p.group].dg.cell_alpha) return false;
+    const size_t limit = update_smem_limit();
+    for (const Part &p : b->parts) {
+        const Group &G = b->ctx->groups[p.group];
+        if (p.direct || G.dg.cell_alpha) return false;
+        // a group whose grouped stage update does not fit a block runs per group
+        if (update_tc_grouped_max_smem(G.dg, G.tc[prec].k_pad) > limit) return false;
+    }
     return true;
 }
 

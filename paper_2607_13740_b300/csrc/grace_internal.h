@@ -254,6 +254,10 @@ struct UpdPart {
 enum { GROUPED_STAGE = 1, GROUPED_LIMIT = 2 };
 int update_tc_grouped_cpb();
 size_t update_tc_grouped_smem(const DevGroup &g, const UpdateArgs &a);
+// the largest shared memory of the grouped stage-update launches for a group (A operand kpad)
+size_t update_tc_grouped_max_smem(const DevGroup &g, int kpad);
+// shared memory a block may opt in to on the current device
+size_t update_smem_limit();
 cudaError_t launch_update_tc_grouped(int mode, bool in_mixed, bool out_mixed, const UpdPart *d_parts, int n_parts,
                                      int n_blocks, size_t smem, cudaStream_t st);
 // the step-start limiter of the tensor path: FP64 rows d_g -> compact stage layout + A operand

@@ -544,6 +544,21 @@ cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, c
     return cudaGetLastError();
 }
 
+// shared memory a block may opt in to on the current device
+size_t update_smem_limit()
+{
+    static int cached[64] = {0};   // per device ordinal, read once
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) cached[dev] = v;
+    }
+    // an attribute that cannot be read leaves the choice to the launch itself
+    return cached[dev] ? (size_t)cached[dev] : ~(size_t)0;
+}
+
 // shared memory of update_tc_kernel: one row (P doubles; not with compact stage inputs and
 // output) and one ghat row (kpad floats) per cell, then the block's functionals [cells][R + 1]
 // floats, then (compact stage inputs and output) the staged inputs: 2 x [cells][N] doubles and
@@ -576,17 +591,38 @@ static cudaError_t launch_update_mode(const DevGroup &g, const UpdateArgs &a, in
 {
     // lanes per cell: the choice that leaves fewer lanes idle over the N bins (8 only when it idles
     // strictly fewer: measured on N = 40, 8 lanes x 5 bins take 75 us per stage vs 97 us for 16 lanes
-    // x 2-3 bins at 65,536 cells)
+    // x 2-3 bins at 65,536 cells); when its block's shared memory does not fit, more lanes per cell
+    // (fewer cells per block)
     const int idle8 = (g.N + 7) / 8 * 8 - g.N, idle16 = (g.N + 15) / 16 * 16 - g.N;
     const int idle32 = (g.N + 31) / 32 * 32 - g.N;
-    if (idle8 < idle16 && idle8 < idle32) return launch_update_lpc<MODE, 8, IN_MIX, OUT_MIX>(g, a, n_cells, st);
-    return idle16 <= idle32 ? launch_update_lpc<MODE, 16, IN_MIX, OUT_MIX>(g, a, n_cells, st)
-                            : launch_update_lpc<MODE, 32, IN_MIX, OUT_MIX>(g, a, n_cells, st);
+    const int pref = idle8 < idle16 && idle8 < idle32 ? 8 : (idle16 <= idle32 ? 16 : 32);
+    const size_t limit = update_smem_limit();
+    for (int lpc = pref; lpc <= 32; lpc *= 2) {
+        if (update_tc_smem(g, a, lpc) > limit) continue;
+        if (lpc == 8) return launch_update_lpc<MODE, 8, IN_MIX, OUT_MIX>(g, a, n_cells, st);
+        if (lpc == 16) return launch_update_lpc<MODE, 16, IN_MIX, OUT_MIX>(g, a, n_cells, st);
+        return launch_update_lpc<MODE, 32, IN_MIX, OUT_MIX>(g, a, n_cells, st);
+    }
+    return cudaErrorInvalidValue;   // even 8 cells per block exceed the shared memory of a block
 }
 
 int update_tc_grouped_cpb() { return kUpdWarps * 32 / kGroupedLpc; }
 
 size_t update_tc_grouped_smem(const DevGroup &g, const UpdateArgs &a) { return update_tc_smem(g, a, kGroupedLpc); }
+
+size_t update_tc_grouped_max_smem(const DevGroup &g, int kpad)
+{
+    // the largest of the grouped launches: a stage with compact inputs and output (staged
+    // inputs), the last stage (FP64 row buffer) and the step-start limiter
+    double one = 0.0;
+    float onef = 0.f;
+    UpdateArgs staged, last;
+    staged.dt = last.dt = &one;
+    staged.F32 = last.F32 = &onef;
+    staged.in_mixed = staged.out_mixed = last.in_mixed = 1;
+    staged.opA_kpad = last.opA_kpad = kpad;
+    return std::max(update_tc_smem(g, staged, kGroupedLpc), update_tc_smem(g, last, kGroupedLpc));
+}
 
 template <int MODE, bool IN_MIX, bool OUT_MIX>
 static cudaError_t launch_grouped(const UpdPart *d_parts, int n_parts, int n_blocks, size_t smem, cudaStream_t st)

@@ -271,6 +271,22 @@ grace_status grace_set_stream(grace_ctx *ctx, void *stream)
     return GRACE_OK;
 }
 
+// A lower bound of the shared memory a contraction launch over tiles t needs: the A tile of 128
+// cells, a 2-deep ring of the smallest B copies (one k-step of the widest tile) and the barrier
+// block.  Tiles that cannot fit it in a block's 227 KB could never launch, so they are refused here.
+static grace_status check_tc_fits(const TcTiles &t, int prec, int group)
+{
+    if (!t.built || t.n_tiles == 0) return GRACE_OK;
+    const size_t planes = prec == GRACE_TF32 ? 1 : 2;
+    const size_t slot = ((size_t)t.max_rows * 32 * planes + 1023) / 1024 * 1024;
+    const size_t need = 1024 + 64 + opA_tile_bytes(prec, t.k_pad) + 2 * slot;
+    if (need <= (size_t)227 * 1024) return GRACE_OK;
+    set_error("grace_precompute: group " + std::to_string(group) + " has " + std::to_string(t.k_pad) +
+              " padded coefficients per cell, too many for a tensor-core A tile in shared memory; "
+              "use GRACE_FP64 for it");
+    return GRACE_ERR_UNSUPPORTED;
+}
+
 grace_status grace_precompute(grace_ctx *ctx, unsigned mask)
 {
     try {
@@ -309,6 +325,7 @@ grace_status grace_precompute(grace_ctx *ctx, unsigned mask)
                     if (!(mask & (1u << prec)) || G.tc[prec].built) continue;
                     grace_status s = build_nc_tc_entries(G, st);
                     if (s == GRACE_OK) s = build_nc_tc_tiles(G, prec, st);
+                    if (s == GRACE_OK) s = check_tc_fits(G.tc[prec], prec, (int)(&G - ctx->groups.data()));
                     if (s != GRACE_OK) return s;
                 }
                 continue;
@@ -344,6 +361,7 @@ grace_status grace_precompute(grace_ctx *ctx, unsigned mask)
             for (int prec = GRACE_TF32; prec <= GRACE_BF16X3; ++prec) {
                 if (!(mask & (1u << prec)) || G.tc[prec].built) continue;
                 grace_status s = build_tc_tiles(G, prec, st);
+                if (s == GRACE_OK) s = check_tc_fits(G.tc[prec], prec, (int)(&G - ctx->groups.data()));
                 if (s != GRACE_OK) return s;
             }
         }

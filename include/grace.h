@@ -177,10 +177,12 @@ GRACE_API grace_status grace_step(grace_batch *batch, double *g, const double *d
    (host [n_cells] each, or NULL).  The copies run on two streams owned by the
    batch and the steps on the bound stream; device staging is double-buffered,
    so with page-locked host buffers successive calls overlap the upload of the
-   next call and the download of the previous one with the steps.  Returns once
-   the work is enqueued: the caller keeps h_g and h_dt unchanged and reads
-   h_out, h_mass and h_flags only after grace_step_host_wait (synchronising the
-   bound stream alone is not enough).  With pageable host memory the CUDA
+   next call and the download of the previous one with the steps.  A call whose
+   h_g or h_dt overlaps the previous call's h_out uploads after that download,
+   so in-place and chained calls (h_out of one call as h_g of the next) need no
+   wait in between.  Returns once the work is enqueued: the caller keeps h_g
+   and h_dt unchanged and reads h_out, h_mass and h_flags only after
+   grace_step_host_wait (synchronising the bound stream alone is not enough).  With pageable host memory the CUDA
    runtime makes the copies synchronous and nothing overlaps.  The first call
    allocates two staging copies of the batch's state (and synchronises).  With
    graph replay on (grace_batch_set_graph) every call uses one staging slot so

@@ -24,7 +24,17 @@ struct HostIo {
     cudaEvent_t uploaded[2] = {nullptr, nullptr}, stepped[2] = {nullptr, nullptr},
                 freed[2] = {nullptr, nullptr};
     int next = 0;
+    // the previous call's output: an input overlapping it must wait for its download
+    const char *last_out = nullptr;
+    size_t last_bytes = 0;
+    int last_slot = -1;
 };
+
+bool overlaps(const void *a, size_t na, const char *b, size_t nb)
+{
+    const char *pa = static_cast<const char *>(a);
+    return b && pa < b + nb && b < pa + na;
+}
 
 void destroy_io(HostIo *io)
 {
@@ -106,8 +116,14 @@ grace_status grace_step_host(grace_batch *b, const double *h_g, double *h_out, c
     const size_t n = (size_t)b->n_cells;
     cudaStream_t st = b->ctx->stream;
 
-    // upload into slot s once its previous result has left the device
+    // upload into slot s once its previous result has left the device, and after the previous
+    // call's download when this call reads what that one writes (in-place or chained calls)
+    const size_t g_bytes = io->n_doubles * sizeof(double);
     cudaError_t e = cudaStreamWaitEvent(io->up, io->freed[s], 0);
+    if (e == cudaSuccess && io->last_slot >= 0 && io->last_slot != s &&
+        (overlaps(h_g, g_bytes, io->last_out, io->last_bytes) ||
+         overlaps(h_dt, n * sizeof(double), io->last_out, io->last_bytes)))
+        e = cudaStreamWaitEvent(io->up, io->freed[io->last_slot], 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(io->d_g[s], h_g, io->n_doubles * sizeof(double), cudaMemcpyHostToDevice, io->up);
     if (e == cudaSuccess) e = cudaMemcpyAsync(io->d_dt[s], h_dt, n * sizeof(double), cudaMemcpyHostToDevice, io->up);
@@ -127,7 +143,11 @@ grace_status grace_step_host(grace_batch *b, const double *h_g, double *h_out, c
         e = cudaMemcpyAsync(h_mass, io->d_mass[s], n * sizeof(double), cudaMemcpyDeviceToHost, io->down);
     if (e == cudaSuccess && h_flags) e = cudaMemcpyAsync(h_flags, io->d_flags[s], n, cudaMemcpyDeviceToHost, io->down);
     if (e == cudaSuccess) e = cudaEventRecord(io->freed[s], io->down);
-    return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_step_host: download");
+    if (e != cudaSuccess) return cuda_fail(e, "grace_step_host: download");
+    io->last_out = reinterpret_cast<const char *>(h_out);
+    io->last_bytes = g_bytes;
+    io->last_slot = s;
+    return GRACE_OK;
 }
 
 grace_status grace_step_host_wait(grace_batch *b)

@@ -98,3 +98,14 @@ def test_host_step_rejects_null_batch(lib):
 def test_flags_check_rejects_null_and_names_warn_status(lib):
     assert lib.grace_flags_check(None, None, None) == 1
     assert lib.grace_status_string(grace.WARN_CELLS).decode() != "unknown status"
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No CPU fallback: without the built CUDA library the binding raises."""
+    import subprocess
+    import sys
+    code = ("from paper_2607_13740_b300 import grace\n"
+            "grace.load('" + os.path.join(ROOT, "_missing", "libgrace.so") + "')\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert out.returncode != 0
+    assert "CUDA library not built" in out.stderr

@@ -91,7 +91,8 @@ enum { GRACE_FLAG_NEGATIVE_MEAN = 1,  /* a cell mean g_j^0 went negative (eq. dt
                                          for the stage input g_j^0 */
        GRACE_FLAG_MASS_DRIFT = 16 };  /* conservative groups, cells with none of the bits
                                          above but LIMITED: M_1 = sum_j h_j g_j^0 changed over
-                                         the grace_step call by more than 1e-9 of its value, or
+                                         the grace_step call by more than
+                                         max(1e-10, 32 n_steps 2^-53) of its value, or
                                          became NaN (eq. g0 with eq. dt kept conserves it to
                                          round-off, so the bit means a conservation failure) */
 

@@ -48,6 +48,11 @@ def lib():
         L.orc_mass_split.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D]
         L.orc_flux_point.argtypes = [P, _D, ctypes.c_int, _D, ctypes.c_int, _D, _D]
         L.orc_vol_frag.argtypes = [P, _D, ctypes.c_int, _D, _D]
+        L.orc_appB_pair.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]
+        L.orc_plant_mass_leak.argtypes = [ctypes.c_double]
+        L.orc_plant_mass_leak.restype = None
+        L.orc_drift_tol.argtypes = [ctypes.c_int]
+        L.orc_drift_tol.restype = ctypes.c_double
         L.orc_rhs_batch.argtypes = [P, ctypes.c_int, _D, _D, _D, ctypes.c_int]
         L.orc_limit_batch.argtypes = [P, ctypes.c_int, _D, _U8]
         L.orc_step_batch.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _U8, ctypes.c_int]
@@ -109,6 +114,17 @@ def bin_min(gj, k: int) -> float:
     return lib().orc_bin_min(_p(gj), int(k))
 
 
+def plant_mass_leak(leak: float) -> None:
+    """Plants a non-conservative update (leak * M_1 added to bin 0 every step) in every later
+    oracle step; 0 removes it.  For tests of the mass-drift bit only."""
+    lib().orc_plant_mass_leak(float(leak))
+
+
+def drift_tol(n_steps: int) -> float:
+    """Relative M_1 change above which a call of n_steps steps sets the mass-drift bit."""
+    return lib().orc_drift_tol(int(n_steps))
+
+
 def max_threads() -> int:
     return lib().orc_max_threads()
 
@@ -155,6 +171,12 @@ class Oracle:
         Va = np.zeros_like(V)
         _check(lib().orc_vol_frag(self._pp, _p(g), int(j), _p(V), _p(Va)), "vol_frag")
         return V, Va
+
+    def appB_pair(self, j: int, u: float, v: float):
+        """App. B sub-interval integrals of one collision pair (u, v) in bin j: J[i], i = 0..k."""
+        J = np.zeros(self.spec.order_k + 1)
+        _check(lib().orc_appB_pair(self._pp, int(j), float(u), float(v), _p(J)), "appB_pair")
+        return J
 
     def rhs(self, g, threads: int = 0):
         g = _f64(g).reshape(-1, self.P)

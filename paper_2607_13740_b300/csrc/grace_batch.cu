@@ -8,6 +8,7 @@
 // scatters results back.  A batch whose cells all belong to one group in the
 // caller's order is a single direct part that works on the caller's arrays.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -761,18 +762,22 @@ static cudaError_t mass_body(grace_batch *b, const double *g, double *mass)
 }
 
 // mass-drift bit: M_1 of a cell of a conservative group changed over the call by more than
-// kDriftTol of its value (or became NaN) although every stage kept eq. (dt) and left the means
-// non-negative and finite.  Under eq. (dt) each bin's update is smaller than the bin's mass, so
-// the scheme conserves M_1 to round-off (eq. g0); cells with one of those bits set are already
-// flagged, and their M_1 can move by round-off of a much larger state.
-constexpr double kDriftTol = 1e-9;
+// drift_tol(n_steps) of its value (or became NaN) although every stage kept eq. (dt) and left the
+// means non-negative and finite.  With conservative fluxes the flux differences of eq. (g0)
+// telescope exactly, so M_1 moves only by the rounding of the stage updates: under eq. (dt)
+// (sum_j h_j dt |L_j^0| <= 2 M_1 per stage) at most 27.1 u M_1 per SSP-RK3 step plus 2 N u for
+// the two mass sums, u = 2^-53.  The tolerance is 32 u per step with a floor of 1e-10.  Cells
+// with one of the skipped bits set are already flagged, and their M_1 can move by round-off of
+// a much larger state.
 constexpr unsigned char kDriftSkip = GRACE_FLAG_NEGATIVE_MEAN | GRACE_FLAG_NONFINITE | GRACE_FLAG_CFL;
 
-__global__ void drift_kernel(int n, const double *__restrict__ m0, const double *__restrict__ m1,
+static double drift_tol(int n_steps) { return std::max(1e-10, 32.0 * std::ldexp(1.0, -53) * n_steps); }
+
+__global__ void drift_kernel(int n, double tol, const double *__restrict__ m0, const double *__restrict__ m1,
                              const unsigned char *__restrict__ cons, unsigned char *__restrict__ flags)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && cons[i] && !(flags[i] & kDriftSkip) && !(fabs(m1[i] - m0[i]) <= kDriftTol * fabs(m0[i])))
+    if (i < n && cons[i] && !(flags[i] & kDriftSkip) && !(fabs(m1[i] - m0[i]) <= tol * fabs(m0[i])))
         flags[i] |= (unsigned char)GRACE_FLAG_MASS_DRIFT;
 }
 
@@ -804,7 +809,7 @@ static cudaError_t step_flagged(grace_batch *b, double *g, const double *dt, int
     if (e == cudaSuccess) e = step_body(b, g, dt, n_steps, prec, mass, flags);
     if (e == cudaSuccess) e = mass_body(b, g, m1);
     if (e == cudaSuccess) {
-        drift_kernel<<<(n + 255) / 256, 256, 0, b->ctx->stream>>>(n, m0, m1, cons, flags);
+        drift_kernel<<<(n + 255) / 256, 256, 0, b->ctx->stream>>>(n, drift_tol(n_steps), m0, m1, cons, flags);
         e = cudaGetLastError();
     }
     return e;

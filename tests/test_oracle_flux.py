@@ -165,11 +165,17 @@ def test_delta_breakage_equals_coagulation_rhs():
     assert np.all(np.abs(Lc - Lf) <= 1e-14 * Sc)
 
 
-def test_appB_volume_term_converges_to_pointwise_flux_integral():
+@pytest.mark.parametrize("spec0", [
+    W.coupled_toy_spec(3, 2, flux_mode=0, x_min=1e-2, x_max=1e2),
+    W.coupled_toy_spec(3, 2, flux_mode=0, x_min=1e-2, x_max=1e2).replace(cutoff_mode=1),
+    W.disk_spec(n_bins=3, order_k=2, a_min=1e-4, a_max=1e-1, cell_alpha=0, alpha=3e-3),
+], ids=["toy_cut_mfrag", "toy_cut_larger", "disk_physics"])
+def test_appB_volume_term_converges_to_pointwise_flux_integral(spec0):
     """App. B reordering: sum over (u, v) of the five sub-interval integrals equals
     int_{I_j} F_frag(x) d_x phi_i dx computed from the pointwise flux; both converge
-    to the same value as the Gauss order grows (R7, R8)."""
-    spec0 = W.coupled_toy_spec(3, 2, flux_mode=0, x_min=1e-2, x_max=1e2)
+    to the same value as the Gauss order grows (R7, R8).  Cases: the paper's cutoff
+    m_cut = m_frag, the cutoff at the larger collider mass, and the disk workload's physics
+    (ballistic-turbulent kernels with the fragmentation ramp, one alpha)."""
     coef = W.random_coefficients(spec0, 1, seed=8, dynamic_range=1.0)[0]
     s8, w8 = npl.leggauss(8)
     diffs = {}
@@ -252,3 +258,112 @@ def test_ballistic_turbulent_fluxes_converge_to_adaptive_quadrature():
         ef.append(abs(oq.flux_point(coef, [x], 2)[0][0] - frag) / abs(frag))
     assert ec[1] < 1e-2 and ec[1] < ec[0] / 50, ec
     assert ef[1] < 1e-3 and ef[1] < ef[0] / 100, ef
+
+
+def _split_by_definition(x, u, v, xmin, cutoff_mode, alpha):
+    """Products of one fragmenting collision from the breakage distribution of eq. (break):
+    m_frag = (u + v) mfrag_ratio(max/min) (eq. mfrag, pinned by its knots) spread as a power
+    law n(w) ~ w^alpha over [x_min, m_cut], plus a remnant of mass m_left = u + v - m_frag at
+    w = m_left.  The power law's mass above / below x is integrated numerically from w n(w);
+    m_cut <= x_min puts the fragment mass at x_min (R10); a remnant below x_min is outside the
+    domain (R10).  Returns (above, below) as in eqs. (inte1), (inte2)."""
+    big, small = max(u, v), min(u, v)
+    mfrag = (u + v) * oracle.mfrag_ratio(big / small)
+    mleft = max(u + v - mfrag, 0.0)
+    mcut = big if cutoff_mode == 1 else mfrag
+    if mcut > xmin:
+        dens = lambda w: w ** (1.0 + alpha)
+        tot = integrate.quad(dens, xmin, mcut, epsabs=0, epsrel=1e-13, limit=200)[0]
+        lo = min(max(x, xmin), mcut)
+        below = mfrag * integrate.quad(dens, xmin, lo, epsabs=0, epsrel=1e-13, limit=200)[0] / tot
+        above = mfrag - below
+    else:
+        below, above = (mfrag, 0.0) if x > xmin else (0.0, mfrag)
+    if mleft > x:
+        above += mleft
+    elif xmin <= mleft:
+        below += mleft
+    return above, below
+
+
+# (u, v) pairs relative to x_min = 1e-2 on a 3-bin grid up to 1e2: equal and very unequal
+# masses, the eq. (mfrag) branches, small colliders whose fragment mass falls below x_min (R10:
+# v < x_min / 0.9 with u / v > 50) and remnants inside and outside the domain
+_PAIRS = [(0.05, 0.04), (0.3, 0.02), (3.0, 0.011), (40.0, 0.0105), (7.0, 0.6), (0.5, 0.45),
+          (20.0, 0.9), (60.0, 30.0), (2.0, 0.15), (0.012, 0.011), (90.0, 0.0102)]
+
+
+@pytest.mark.parametrize("cutoff_mode", [0, 1])
+def test_powerlaw_mass_split_matches_the_breakage_distribution(cutoff_mode):
+    """eqs. (inte1), (inte2): the oracle's mass of products above and below x for power-law
+    fragments plus a remnant equals the numerical w-integral of the breakage distribution, for
+    both cutoffs (m_frag, and the larger collider mass) and the R10 cases."""
+    spec = W.coupled_toy_spec(3, 2, flux_mode=0, x_min=1e-2, x_max=1e2).replace(cutoff_mode=cutoff_mode)
+    o = oracle.Oracle(spec)
+    alpha = spec.break_p[0]
+    xs = [1e-2, 1.05e-2, 0.013, 0.04, 0.3, 2.0, 35.0, 95.0]
+    r10 = 0
+    for u, v in _PAIRS:
+        for x in xs:
+            a, b = o.mass_split([x], [u], [v])
+            ea, eb = _split_by_definition(x, u, v, spec.x_min, cutoff_mode, alpha)
+            assert abs(a[0] - ea) <= 1e-11 * (u + v) and abs(b[0] - eb) <= 1e-11 * (u + v), (u, v, x)
+        r10 += (u + v) * oracle.mfrag_ratio(max(u, v) / min(u, v)) <= spec.x_min
+    assert r10 >= 3        # the R10 branch is exercised
+
+
+def _pair_flux_integral(o, spec, j, u, v):
+    """int_{I_j} f_uv(x) d_x phi_i dx by adaptive quadrature of the pointwise pair flux of
+    eq. (Ffragtrun): the products above x while u < x <= u + v - x_min (positive part, the v range
+    starting at x - u + x_min), minus those in [x_min, x] while x < u (negative part)."""
+    e = o.edges()
+    a, b = e[j], e[j + 1]
+    h, xc = b - a, 0.5 * (a + b)
+    top = u + v - spec.x_min
+
+    def f(x):
+        above, below = o.mass_split([x], [u], [v])
+        val = 0.0
+        if u < x <= top:
+            val += above[0]
+        if x < u:
+            val -= below[0]
+        return val
+
+    big, small = max(u, v), min(u, v)
+    mfrag = (u + v) * oracle.mfrag_ratio(big / small)
+    kinks = [u, top, mfrag, big, u + v - mfrag]
+    pts = sorted(set(p for p in kinks if a < p < b)) or None
+    out, scale = np.zeros(spec.order_k + 1), np.zeros(spec.order_k + 1)
+    for i in range(1, spec.order_k + 1):
+        c = np.zeros(i + 1)
+        c[i] = 1.0
+        dphi = lambda x: (2.0 / h) * npl.legval(2.0 * (x - xc) / h, npl.legder(c))
+        out[i] = integrate.quad(lambda x: f(x) * dphi(x), a, b, points=pts, epsabs=0, epsrel=1e-12,
+                                limit=400)[0]
+        scale[i] = integrate.quad(lambda x: abs(f(x) * dphi(x)), a, b, points=pts, epsabs=0,
+                                  epsrel=1e-10, limit=400)[0]
+    return out, scale
+
+
+@pytest.mark.parametrize("cutoff_mode", [0, 1])
+def test_appB_pair_terms_match_pointwise_flux_integral(cutoff_mode):
+    """App. B per collision pair: the five sub-interval terms (R7: positive terms on
+    I_j cap (u, min(u+v-x_min, m_cut or m_left)), negative terms on I_j cap (x_min, u), R10 for
+    m_cut <= x_min and remnants below x_min) equal the x-integral of the pair's pointwise flux
+    times d_x phi_i over bin j, for every bin and pairs covering each interval end (u, u+v-x_min,
+    m_cut and m_left below, inside and above the bin) and both cutoffs.  A wrong interval end
+    (e.g. a missing min with u+v-x_min or with m_cut) fails this test."""
+    spec = W.coupled_toy_spec(3, 2, flux_mode=0, x_min=1e-2, x_max=1e2).replace(
+        cutoff_mode=cutoff_mode, quad_q=24)
+    o = oracle.Oracle(spec)
+    nonzero = 0
+    for u, v in _PAIRS + [(v_, u_) for u_, v_ in _PAIRS[:4]]:
+        for j in range(spec.n_bins):
+            J = o.appB_pair(j, u, v)
+            ref, scale = _pair_flux_integral(o, spec, j, u, v)
+            assert J[0] == 0.0
+            tol = 1e-10 * max(scale.max(), 1e-300)
+            assert np.all(np.abs(J[1:] - ref[1:]) <= tol), (u, v, j, J, ref)
+            nonzero += int(np.any(ref[1:] != 0.0))
+    assert nonzero >= 20

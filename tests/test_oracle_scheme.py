@@ -201,7 +201,7 @@ def test_mass_drift_bit():
     """eq. (g0): a conservative group keeps M_1 to round-off while eq. (dt) holds, so a normal
     call sets no drift bit (16); a non-conservative group loses mass through x_max by design and
     is not tested; a call whose state overflows is flagged non-finite (4) and not tested for
-    drift.  A correct scheme never sets the bit, so there is no positive case to pin."""
+    drift."""
     spec = SPECS["add"]
     o = oracle.Oracle(spec)
     g = o.project(W.IC_EXP, [[1.0, 1.0, 0, 0]] * 2)
@@ -215,3 +215,48 @@ def test_mass_drift_bit():
     m0 = onc.mass(gnc)[0]
     _, m, f = onc.step(gnc, 0.05, 20)
     assert abs(m[0] - m0) > 1e-6 * m0 and (f[0] & 16) == 0
+
+
+def test_mass_drift_stays_below_the_rounding_bound():
+    """eq. (g0) telescopes exactly, so with eq. (dt) kept the only change of M_1 is the
+    rounding of the stage updates: at most (27.1 n + 2 N) u M_1 for n steps (u = 2^-53; the
+    bound the drift bit's tolerance rests on).  Checked over 60 steps of cells whose mass moves
+    across many bins, against the bound and against the bit's tolerance 32 u n (floor 1e-10)."""
+    wl = W.batched_additive(n_cells=8, n_bins=16, order_k=2, n_steps=60)
+    o = oracle.Oracle(wl.spec)
+    g0 = o.project(wl.ic_kind, wl.ic_params)
+    m0 = o.mass(g0)
+    g, m, f = o.step(g0, wl.dt, wl.n_steps)
+    assert np.all((f & (1 | 4 | 8 | 16)) == 0)
+    u = 2.0 ** -53
+    drift = np.abs(m - m0) / m0
+    assert np.all(drift <= (27.1 * wl.n_steps + 2 * wl.spec.n_bins) * u)
+    assert oracle.drift_tol(1) == 1e-10 and oracle.drift_tol(10 ** 6) == 32 * u * 10 ** 6
+    assert np.all(drift <= oracle.drift_tol(wl.n_steps))
+
+
+def test_mass_drift_bit_positive_case():
+    """A planted non-conservative update (each step adds leak * M_1 to bin 0, a mistake put in
+    the oracle for this test only) sets the drift bit (16) once the change over the call exceeds
+    the tolerance, and not below it; cells that broke eq. (dt) (bit 8) are not tested."""
+    spec = SPECS["add"]
+    o = oracle.Oracle(spec)
+    g = o.project(W.IC_EXP, [[1.0, 1.0, 0, 0], [2.0, 0.3, 0, 0]])
+    try:
+        oracle.plant_mass_leak(1e-9)
+        _, _, f = o.step(g, 1e-3, 3)
+        assert np.all(f & 16)
+        oracle.plant_mass_leak(1e-12)
+        _, _, f = o.step(g, 1e-3, 3)
+        assert np.all((f & 16) == 0)
+        oracle.plant_mass_leak(1e-6)
+        L, _ = o.rhs(g[:1])
+        L0 = L.reshape(spec.n_bins, -1)[:, 0]
+        g0 = g[0].reshape(spec.n_bins, -1)[:, 0]
+        bound = (g0[L0 < 0] / -L0[L0 < 0]).min()
+        _, _, f = o.step(g[:1], 30.0 * bound, 1)
+        assert f[0] & 8 and (f[0] & 16) == 0
+    finally:
+        oracle.plant_mass_leak(0.0)
+    _, _, f = o.step(g, 1e-3, 3)
+    assert np.all((f & 16) == 0)

@@ -205,9 +205,11 @@ GRACE_API grace_status grace_step_host_wait(grace_batch *batch);
    every GPU that loads the library until the process exits, so
    n_cells * n_functionals must not exceed 2^21 (GRACE_ERR_ARG otherwise; C2's
    N = 40, k = 2 group allows 17,620 cells per call).  The context must have
-   been set up and precomputed beforehand (those calls do allocate).  The first
-   call on a device looks up the array's device address on that device; make
-   that first call before any stream capture.  All calls share the one array:
+   been set up and precomputed beforehand (those calls do allocate).  Every
+   call looks up the array's device address on the context's device (a host
+   query); the first lookup on a device may load the library's device code
+   there, so make the first call on a device before any stream capture.  The
+   first call sets up this lookup.  All calls share the one array:
    calls whose executions overlap on the GPU (other streams, other threads)
    race and must be serialised by the caller.  g, L: device, packed layout; runs
    on the context's bound stream.  The paper has no counterpart of this call. */
@@ -321,6 +323,19 @@ GRACE_API grace_status grace_flags_check(grace_batch *batch, const unsigned char
    no results for the affected cells).  Synchronises the bound stream; returns
    GRACE_ERR_TIMEOUT when the word was non-zero. */
 GRACE_API grace_status grace_batch_error(grace_batch *batch, int *code);
+
+/* Failure-detection check: arms a one-shot fault of the next tensor-core
+   contraction launched in this process (any context or batch).  That launch
+   issues none of its operand-table copies, so its MMA issuer waits on a
+   shared-memory barrier that nothing arrives at, and every bounded wait of
+   the launch gives up after wait_cycles SM clock cycles (1 .. 4e9; the
+   default limit of every other launch is 4e9, about 2 s) instead of the
+   default.  The kernel then takes its normal abort path: it records the
+   failure in the batch's device error word, drains its copies in flight,
+   frees its tensor memory and returns without results; grace_batch_error
+   reports GRACE_ERR_TIMEOUT.  Nothing faults or hangs.  The paper has no
+   counterpart of this call. */
+GRACE_API grace_status grace_test_arm_wait_timeout(long long wait_cycles);
 
 /* Measures, on `device`, the CUDA-core throughput used as roofline
    denominators: rates[0] FP64 FMA/s, rates[1] FP32 FMA/s, rates[2] FP64->FP32

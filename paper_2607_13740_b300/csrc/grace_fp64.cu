@@ -79,13 +79,10 @@ cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int
     if (wpb > 4) wpb = 4;
     if (wpb < 1) return cudaErrorInvalidValue;   // P too large for one warp's tile
     const size_t smem = per_warp * wpb;
-    static int configured_max = 0;
-    if ((int)smem > configured_max) {
-        cudaError_t e = cudaFuncSetAttribute(contract_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_max = (int)smem;
-    }
+    // the attribute belongs to the current device, so it is set on every launch
+    cudaError_t e = cudaFuncSetAttribute(contract_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     const int cells_per_block = 32 * wpb;
     const int blocks = (n_cells + cells_per_block - 1) / cells_per_block;
     const dim3 grid(blocks, fp64_functional_chunks(n_cells, g.R));

@@ -7,7 +7,6 @@
 // (which synchronises the device) or a second allocator is not acceptable.
 // For them this entry point keeps the workspace in a fixed array that lives
 // in this file's module for as long as the library stays loaded.
-#include <mutex>
 #include <string>
 
 #include "grace_internal.h"
@@ -19,25 +18,16 @@ namespace {
 constexpr size_t kStaticScratchDoubles = size_t(2) << 20;
 static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-double *g_scratch_dev_ptr[kMaxDevices] = {};
-
-// Device address of the array on the current device, looked up once per device.
-grace_status scratch_on_device(int dev, double **out)
+// Device address of the array on the current device.  It is looked up on every call (a host-side
+// query, no allocation), so a context torn down and re-created (cudaDeviceReset) never leaves a
+// stale address behind.  The first lookup on a device may load the library's device code there,
+// which is why the first call must come before any stream capture.
+grace_status scratch_on_device(double **out)
 {
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("grace_rhs_noalloc: device index out of range");
-        return GRACE_ERR_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_dev_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "grace_rhs_noalloc: cudaGetSymbolAddress");
-        g_scratch_dev_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_dev_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "grace_rhs_noalloc: cudaGetSymbolAddress");
+    *out = static_cast<double *>(p);
     return GRACE_OK;
 }
 
@@ -76,7 +66,7 @@ extern "C" grace_status grace_rhs_noalloc(grace_ctx *ctx, int group, int n_cells
     if (prev != ctx->device && (e = cudaSetDevice(ctx->device)) != cudaSuccess)
         return cuda_fail(e, "grace_rhs_noalloc: cudaSetDevice");
     double *F = nullptr;
-    grace_status s = scratch_on_device(ctx->device, &F);
+    grace_status s = scratch_on_device(&F);
     if (s == GRACE_OK) {
         e = launch_contract_fp64(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, n_cells, F, ctx->stream);
         if (e == cudaSuccess) {

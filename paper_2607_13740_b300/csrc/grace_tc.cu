@@ -43,6 +43,7 @@
 // the device error word, stops issuing work, drains its outstanding copies and
 // releases its tensor memory before returning.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -66,7 +67,7 @@ constexpr int kEpiF = (kMaxF + kEpiSplit - 1) / kEpiSplit;   // functionals per 
 constexpr int kThreads = 32 * (4 + kEpiWarps);
 constexpr int kMaxSplits = 8;
 constexpr int kSmemLimit = 227 * 1024;
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr long long kWaitCycles = 4000000000LL;   // default wait limit, ~2 s at 2 GHz
 
 // cost model (SM cycles), from measurements on this part: one tcgen05.mma with
 // M = 128 issues every ~139 cycles whatever its N; L2 delivers ~45 B/cycle/SM
@@ -120,6 +121,10 @@ struct TcParams {
     // multi-group mode: per-group descriptors and the work items (group, cell tile)
     const struct TcGroupDesc *groups;
     const int2 *items;
+    // failure detection: every mbarrier wait gives up after wait_cycles; withhold_b != 0 (a
+    // test of that path only) issues no B copies, so the MMA issuer's first wait runs out
+    long long wait_cycles;
+    int withhold_b;
 };
 
 // one group of a multi-group launch (all its tiles form one split)
@@ -218,12 +223,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 }
 
 // bounded wait: false on timeout or when another role already aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, long long limit)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -555,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             int ok = 1;
             if (lane == 0) {
                 if (*abort_flag) ok = 0;
-                else if (au > 0 && !mbar_wait(smem_u32(&S->a_empty[ab]), (au - 1) & 1, abort_flag)) {
+                else if (au > 0 && !mbar_wait(smem_u32(&S->a_empty[ab]), (au - 1) & 1, abort_flag, P.wait_cycles)) {
                     fail(P, abort_flag, 1);
                     ok = 0;
                 }
@@ -575,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         // boundaries, limited only by the ring.
         const int me = warp == 0 ? 0 : 1;
         int q = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        for (int it = blockIdx.x; it < n_items && !P.withhold_b; it += gridDim.x) {
             const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
             int ok = *abort_flag ? 0 : 1;
             for (int t = ic.t0; t < ic.t1 && ok; ++t) {
@@ -587,7 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     for (int c = 0; c < n_copies; ++c, ++q) {
                         if ((q & 1) != me) continue;
                         const int slot = q % NS, use = q / NS;
-                        if (use > 0 && !mbar_wait(smem_u32(&S->empty[slot]), (use - 1) & 1, abort_flag)) {
+                        if (use > 0 && !mbar_wait(smem_u32(&S->empty[slot]), (use - 1) & 1, abort_flag, P.wait_cycles)) {
                             fail(P, abort_flag, 2);
                             ok = 0;
                             break;
@@ -610,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         for (int it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x, ++ctl) {
             const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
-            if (!mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag)) {
+            if (!mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles)) {
                 fail(P, abort_flag, 4);
                 break;
             }
@@ -621,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             for (int t = ic.t0; t < ic.t1 && !*abort_flag; ++t) {
                 const TileDesc td = ic.tiles[t];
                 const int buf = acc_use & 1, bu = acc_use >> 1;
-                if (bu > 0 && !mbar_wait(smem_u32(&S->acc_empty[buf]), (bu - 1) & 1, abort_flag)) {
+                if (bu > 0 && !mbar_wait(smem_u32(&S->acc_empty[buf]), (bu - 1) & 1, abort_flag, P.wait_cycles)) {
                     fail(P, abort_flag, 8);
                     break;
                 }
@@ -633,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 uint32_t acc = 0u;
                 for (int c = 0; c < n_copies; ++c) {
                     const int slot = q % NS, use = q / NS;
-                    if (!mbar_wait(smem_u32(&S->full[slot]), use & 1, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&S->full[slot]), use & 1, abort_flag, P.wait_cycles)) {
                         fail(P, abort_flag, 16);
                         break;
                     }
@@ -685,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
             const int ct = ic.ct;
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
-            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles))) {
                 fail(P, abort_flag, 32);
                 break;
             }
@@ -709,7 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 const TileDesc td = ic.tiles[t];
                 const int nf = td.nf_flush & 0xFFFF;
                 const int buf = acc_use & 1, bu = acc_use >> 1;
-                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->acc_full[buf]), bu & 1, abort_flag))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->acc_full[buf]), bu & 1, abort_flag, P.wait_cycles))) {
                     fail(P, abort_flag, 128);
                     aborted = true;
                     break;
@@ -1334,9 +1339,20 @@ static void choose_splits(const TcTiles &t, int n_cell_tiles, int n_sm, TcParams
     P.n_splits = ns;
 }
 
+// One-shot check of failure detection (grace_test_arm_wait_timeout): the next contraction launch
+// of the process waits at most this many cycles and issues no B copies.
+static std::atomic<long long> g_armed_wait_cycles{0};
+
 template <int PREC, int MODE>
 static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
 {
+    P.wait_cycles = kWaitCycles;
+    P.withhold_b = 0;
+    const long long armed = g_armed_wait_cycles.exchange(0);
+    if (armed > 0) {
+        P.wait_cycles = armed;
+        P.withhold_b = 1;
+    }
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
     P.table_bytes = (int)((P.n_tiles * sizeof(TileDesc) + (size_t)P.R * sizeof(int) +
                            (MODE == kModeNC ? (size_t)P.n_d0 * sizeof(float) : 0) + 15) / 16 * 16);
@@ -1500,3 +1516,13 @@ cudaError_t launch_vjp_tc(const DevGroup &g, const TcTiles &t, int prec, const v
 }
 
 }  // namespace grace
+
+extern "C" grace_status grace_test_arm_wait_timeout(long long wait_cycles)
+{
+    if (wait_cycles <= 0 || wait_cycles > grace::kWaitCycles) {
+        grace::set_error("grace_test_arm_wait_timeout: wait_cycles must lie in [1, 4e9]");
+        return GRACE_ERR_ARG;
+    }
+    grace::g_armed_wait_cycles.store(wait_cycles);
+    return GRACE_OK;
+}

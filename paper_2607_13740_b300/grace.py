@@ -50,7 +50,8 @@ def exported_symbols():
             "grace_batch_error", "grace_rhs_jvp", "grace_rhs_vjp", "grace_param_grad_setup",
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_set_grouped", "grace_batch_destroy",
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
-            "grace_step_host", "grace_step_host_wait", "grace_flags_check"]
+            "grace_step_host", "grace_step_host_wait", "grace_flags_check",
+            "grace_test_arm_wait_timeout"]
 
 
 def load(path: str | None = None):
@@ -94,6 +95,7 @@ def load(path: str | None = None):
     L.grace_step_host.argtypes = [_VP, _VP, _VP, _VP, S, S, _VP, _VP]
     L.grace_step_host_wait.argtypes = [_VP]
     L.grace_flags_check.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_uint)]
+    L.grace_test_arm_wait_timeout.argtypes = [ctypes.c_longlong]
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -130,6 +132,12 @@ def _ptr(t):
 def _stream_handle():
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def arm_wait_timeout(wait_cycles: int):
+    """One-shot failure-detection check: the next tensor-core contraction launch issues no
+    operand copies and its bounded waits give up after wait_cycles (grace_test_arm_wait_timeout)."""
+    _check(load().grace_test_arm_wait_timeout(int(wait_cycles)), "grace_test_arm_wait_timeout")
 
 
 def probe_rates(device: int = 0):

@@ -109,3 +109,11 @@ def test_binding_fails_loudly_without_the_library():
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert out.returncode != 0
     assert "CUDA library not built" in out.stderr
+
+
+def test_arm_wait_timeout_rejects_bad_limits():
+    """The failure-detection hook takes limits in [1, 4e9] cycles only (no GPU needed)."""
+    with pytest.raises(grace.GraceError):
+        grace.arm_wait_timeout(0)
+    with pytest.raises(grace.GraceError):
+        grace.arm_wait_timeout(5_000_000_000)

@@ -69,6 +69,35 @@ def test_pipelined_calls_keep_their_own_results():
     assert torch.equal(pageable, ref)
 
 
+@pytest.mark.parametrize("form", [grace.FP64, grace.BF16X3], ids=["fp64", "bf16x3"])
+def test_pinned_chained_and_in_place_calls_need_no_waits(form):
+    """Page-locked buffers, no wait between calls: (a) a chain where each call reads the
+    previous call's output (h_g of call i = h_out of call i-1), (b) five in-place calls on one
+    buffer.  The upload of a call that reads what the previous call writes must follow that
+    call's download; every result equals the device-step chain bit for bit."""
+    wl = W.batched_additive(n_cells=1000)
+    ctx = grace.Context([wl.spec], 0, precisions=(grace.FP64, form))
+    b = ctx.batch(wl.n_cells)
+    g0 = b.project(wl.ic_kind, wl.ic_params).cpu()
+    dt = torch.as_tensor(wl.dt, dtype=torch.float64)
+    refs = [g0]
+    for i in range(5):
+        refs.append(_device_step(b, refs[-1], dt, 2, form)[0])
+    h_dt = dt.pin_memory()
+    bufs = [g0.pin_memory()] + [torch.full_like(g0, float("nan")).pin_memory() for _ in range(5)]
+    for i in range(5):
+        b.step_host(bufs[i], h_dt, 2, form, out=bufs[i + 1])
+    b.wait_host()
+    for i in range(1, 6):
+        assert torch.equal(bufs[i], refs[i]), i
+    inplace = g0.pin_memory()
+    for i in range(5):
+        b.step_host(inplace, h_dt, 2, form)
+    b.wait_host()
+    assert b.device_error() == 0
+    assert torch.equal(inplace, refs[5])
+
+
 def test_mixed_group_batch_and_graph_replay():
     """A batch mixing groups of several N and k (grouped tensor step), then the same batch
     with graph replay on a bound non-default stream (one staging slot)."""

@@ -58,7 +58,11 @@ def test_noalloc_rejects_sizes_beyond_the_fixed_workspace():
     ctx = grace.Context([spec])
     P, R = ctx.group_info(0)
     too_many = (2 ** 21) // R + 1
-    g = torch.zeros(1, dtype=torch.float64, device=DEV)
-    st = _noalloc()(ctx._h, 0, too_many, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(g.data_ptr()))
+    # buffers of the full size, so that a regressed size guard computes wrong values instead of
+    # reading or writing past an allocation
+    g = torch.zeros(too_many * P, dtype=torch.float64, device=DEV)
+    out = torch.zeros_like(g)
+    st = _noalloc()(ctx._h, 0, too_many, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(out.data_ptr()))
+    torch.cuda.synchronize()
     assert st == 1
     assert "exceeds" in grace.load().grace_last_error().decode()

@@ -613,7 +613,7 @@ def main():
     if head not in forms:
         raise SystemExit(f"precision {args.precision} was not precomputed by the library")
     if args.steps is None:
-        args.steps = 3 if head == grace.FP64 else 50
+        args.steps = 3 if head == grace.FP64 else 100
     b = ctx.batch(n)
     g0 = b.project(wl.ic_kind, wl.ic_params)
     dt = torch.as_tensor(wl.dt, device=dev)
@@ -622,7 +622,10 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     names = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}
 
-    def timed(form, steps, warmup, clocks=False):
+    def timed(form, steps, warmup, clocks=False, one_call=False):
+        """K steps timed with CUDA events on the launching stream: one grace_step call of K steps
+        (one_call; the configured workload is one call of 100 steps) or K calls of one step each
+        (every call pays the step-start conversion and the FP64 output of its last stage)."""
         g = g0.clone()
         for _ in range(warmup):
             b.step(g, dt, 1, form)
@@ -637,12 +640,12 @@ def main():
         if sampler:
             sampler.__enter__()
         torch.cuda.synchronize()
-        for s in range(steps):
-            flush.fill_(float(s))            # evict L2 between timed steps (outside the events)
+        for s in range(1 if one_call else steps):
+            flush.fill_(float(s))            # evict L2 before every timed call (outside the events)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            b.step(g, dt, 1, form)
+            b.step(g, dt, steps if one_call else 1, form)
             e1.record()
             evs.append((e0, e1))
         torch.cuda.synchronize()
@@ -656,7 +659,8 @@ def main():
         if world > 1:
             dist.barrier()
         return {"ms": ms_max, "contract_ms": c_ms, "contract_launches": c_n, "update_ms": u_ms,
-                "update_launches": u_n, "g": g, "clocks": sampler.summary() if sampler else None}
+                "update_launches": u_n, "g": g, "clocks": sampler.summary() if sampler else None,
+                "calls": 1 if one_call else steps}
 
     # accuracy of each form against the FP64 GPU path over the same steps
     err_steps = 3
@@ -667,31 +671,70 @@ def main():
                                       for j in range(41)]), device=dev)
     h = (edges[1:] - edges[:-1])
 
-    forms_out = {}
-    for form in forms:
-        steps = args.steps if form == head else min(args.steps, 3 if form == grace.FP64 else 20)
-        r = timed(form, steps, args.warmup if form == head else 1, clocks=(form == head))
-        cell_steps = n * world * steps / (r["ms"] / 1e3)
+    # roofline denominators: the tensor-core forms are timed as sub-ms launches inside sub-ms steps,
+    # so their peak is the burst rate: the measured cuBLAS bf16 burst for BF16x3 (MEASURED_PEAKS.json),
+    # and this project's own tcgen05 kind::tf32 probe (M = 128, N = 256) for TF32; the probe's
+    # single-product bf16 rate is reported beside it
+    mma_peaks = {}
+    for pf, key in ((grace.TF32, "tf32"), (grace.BF16X3, "bf16")):
+        try:
+            mma_peaks[key] = grace.probe_mma(pf, 256, local) / 1e12
+        except Exception as exc:
+            mma_peaks[key + "_error"] = str(exc)[:120]
+    survey_nnz = 410000          # the scope table's estimate of the non-zeros of T for N = 40, k = 2
+
+    def roofline(form, avg_ms, tinfo):
+        """The contraction's achieved rate per launch on three algorithmic bases and its fraction
+        of the form's peak; the primary basis is the exact non-zero count of T (the scope table's
+        per-cell figure, counted by the precompute instead of estimated)."""
         passes = 3 if form == grace.BF16X3 else 1
-        # algorithmic flops per contraction launch: the multiply-adds a cell needs
-        # (FP64 path: every non-zero of T; tensor path: the symmetric-folded tables)
-        tinfo = ctx.tile_info(0, form) if form != grace.FP64 else None
-        nz = tinfo["nnz_fold"] if tinfo else nnz
-        alg_flop = 2.0 * nz * n * passes
-        avg = r["contract_ms"] / max(1, r["contract_launches"])
-        achieved = alg_flop / (avg / 1e3) / 1e12      # TFLOP/s
+        sec = avg_ms / 1e3
+        bases = {"T_nonzeros_exact": nnz, "survey_estimate": survey_nnz}
+        if tinfo:
+            bases["folded_nonzeros"] = tinfo["nnz_fold"]
+        ach = {k: 2.0 * v * n * passes / sec / 1e12 for k, v in bases.items()}
         if form == grace.FP64:
             try:
                 fma64 = grace.probe_rates(local)["fp64_fma_per_s"]   # measured on this GPU
                 peak, psrc = 2.0 * fma64 / 1e12, "measured FP64 FMA rate (grace_probe_rates) x 2 flop"
             except Exception:
                 peak, psrc = NOMINAL_FP64_TFLOPS, "nominal FP64 rate of the part (1.25 TFLOP/s)"
-            bound = "alu"
+            return {"bound": "alu", "achieved": ach["T_nonzeros_exact"], "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach["T_nonzeros_exact"] / peak, "peak_source": psrc,
+                    "bases": {k: {"nonzeros_per_cell": bases[k], "achieved": a, "frac": a / peak}
+                              for k, a in ach.items()}}
+        if form == grace.TF32 and "tf32" in mma_peaks:
+            peak, psust = mma_peaks["tf32"], None
+            psrc = "measured tcgen05 kind::tf32 rate (grace_probe_mma, M = 128, N = 256), burst"
         elif form == grace.TF32:
-            peak = peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16
-            bound, psrc = "tensor", f"{peaks['source']} sustained bf16 x nominal tf32/bf16 ratio"
+            peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
+            psust, psrc = None, f"{peaks['source']} burst bf16 x nominal tf32/bf16 ratio"
         else:
-            peak, bound, psrc = peaks["bf16_tflops_sustained"], "tensor", f"{peaks['source']} sustained bf16"
+            peak, psust = peaks["bf16_tflops"], peaks["bf16_tflops_sustained"]
+            psrc = f"{peaks['source']} burst bf16 (cuBLAS)"
+        out = {"bound": "tensor", "achieved": ach["T_nonzeros_exact"], "peak": peak, "unit": "TFLOP/s",
+               "frac": ach["T_nonzeros_exact"] / peak, "frac_burst": ach["T_nonzeros_exact"] / peak,
+               "peak_source": psrc,
+               "bases": {k: {"nonzeros_per_cell": bases[k], "achieved": a, "frac_burst": a / peak}
+                         for k, a in ach.items()}}
+        if psust:
+            out["frac_sustained"] = ach["T_nonzeros_exact"] / psust
+            out["peak_sustained"] = psust
+            for k, a in ach.items():
+                out["bases"][k]["frac_sustained"] = a / psust
+        return out
+
+    forms_out = {}
+    for form in forms:
+        is_head = form == head
+        steps = args.steps if is_head else min(args.steps, 3 if form == grace.FP64 else 20)
+        # the headline form: one grace_step call of K steps (the configured workload at K = 100),
+        # next to K calls of one step; the other forms: one-step calls
+        r = timed(form, steps, args.warmup if is_head else 1, clocks=is_head, one_call=is_head)
+        r1 = timed(form, min(steps, 20), 1) if is_head else r
+        cell_steps = n * world * steps / (r["ms"] / 1e3)
+        tinfo = ctx.tile_info(0, form) if form != grace.FP64 else None
+        avg = r["contract_ms"] / max(1, r["contract_launches"])
         g = g0.clone()
         b.step(g, dt, err_steps, form)
         d = (g - ref).abs().reshape(n, 40, 3)
@@ -701,12 +744,19 @@ def main():
         drift = ((mass - m0).abs() / m0.abs()).max().item()
         forms_out[names[form]] = {
             "cell_steps_per_s": cell_steps, "ms_per_step": r["ms"] / steps, "steps": steps,
+            "timing": f"one grace_step call of {steps} steps" if is_head else f"{steps} one-step calls",
             "contract_ms_avg": avg, "contract_launches": r["contract_launches"], "tiles": tinfo,
             "update_ms_avg": r["update_ms"] / max(1, r["update_launches"]),
-            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "peak_source": psrc},
+            "update_launches": r["update_launches"],
+            "roofline": roofline(form, avg, tinfo),
             "l1_err_vs_fp64_over_M1": l1, "max_rel_err_vs_fp64": mx, "mass_drift": drift,
             "err_steps": err_steps, "_r": r}
+        if is_head:
+            s1 = min(steps, 20)
+            forms_out[names[form]]["one_step_calls"] = {
+                "cell_steps_per_s": n * world * s1 / (r1["ms"] / 1e3), "ms_per_step": r1["ms"] / s1, "steps": s1,
+                "contract_ms_avg": r1["contract_ms"] / max(1, r1["contract_launches"]),
+                "update_ms_avg": r1["update_ms"] / max(1, r1["update_launches"])}
 
     hd = forms_out[names[head]]
     r = hd.pop("_r")
@@ -766,7 +816,9 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
 
-    launches_per_step = 1 + 3 + 3
+    # kernels of the timed region: the contractions and stage updates counted by the launch
+    # timers, plus the one step-start limiter of each call
+    gpu_launches = r["contract_launches"] + r["update_launches"] + r["calls"]
     line = {
         "metric": METRIC, "value": hd["cell_steps_per_s"], "unit": UNIT, "n_gpus": world,
         "steps": hd["steps"], "warmup": args.warmup, "ms_per_step": hd["ms_per_step"],
@@ -777,22 +829,26 @@ def main():
                    "n_bins": 40, "order_k": 2,
                    "coef_per_cell": wl.spec.n_coef, "kernel": "additive K=x+y", "flux": "conservative",
                    "x_range": [wl.spec.x_min, wl.spec.x_max], "precision": names[head],
-                   "l2": "256 MB buffer written between timed steps (outside the timed events)",
+                   "l2": "256 MB buffer written before every timed call (outside the timed events); inside "
+                         "a multi-step call the working set (state, three compact stage states, functionals, "
+                         "A operand: about 250 MB) exceeds the 126 MB L2",
+                   "timing": f"one grace_step call of {hd['steps']} steps, CUDA events on the launching stream; "
+                             "forms.<precision>.one_step_calls has K calls of one step",
                    "parallelism": f"dp{world} (independent cells, no collective on the data path)"},
-        "roofline": {"bound": hd["roofline"]["bound"], "achieved": hd["roofline"]["achieved"],
-                     "peak": hd["roofline"]["peak"], "unit": "TFLOP/s", "frac": hd["roofline"]["frac"],
+        "roofline": {**{k: v for k, v in hd["roofline"].items() if k != "bases"},
                      "traffic": profiled_traffic(names[head]) if head != grace.FP64 else None,
                      "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch, committed ncu "
                                        "summary (null when the kernel changed since)",
                      "kernel": "flux contraction",
-                     "algorithmic": (f"2 x {hd['tiles']['nnz_fold']} non-zeros of the folded tables"
-                                     if hd.get("tiles") else f"2 x {nnz} non-zeros of T")
-                                    + f" per cell and RHS x {n} cells"
+                     "algorithmic": f"2 x {nnz} non-zeros of T per cell and RHS (exact count of the scope "
+                                    f"table's per-cell figure) x {n} cells"
                                     + (" x 3 bf16 passes" if head == grace.BF16X3 else ""),
-                     "peak_source": hd["roofline"]["peak_source"]},
+                     "bases": hd["roofline"]["bases"],
+                     "tf32_peak_measured": mma_peaks.get("tf32"), "bf16_single_product_peak_measured":
+                         mma_peaks.get("bf16")},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": launches_per_step * hd["steps"],
+        "gpu_launches": gpu_launches,
         "clocks": r["clocks"],
         "forms": forms_out,
         "peaks": peaks,

@@ -342,6 +342,16 @@ GRACE_API grace_status grace_test_arm_wait_timeout(long long wait_cycles);
    conversions/s (3 doubles, host).  Allocates and synchronises. */
 GRACE_API grace_status grace_probe_rates(int device, double *rates);
 
+/* Measures, on `device`, the dense tensor-core rate used as the roofline
+   denominator of a tensor-core form: tcgen05.mma with M = 128 and N = n
+   (a multiple of 16 in [16, 256]) issued back to back by one thread per SM
+   from shared-memory operands, kind::tf32 (precision GRACE_TF32, K = 8) or
+   kind::f16 with bf16 operands (precision GRACE_BF16X3, one product per
+   instruction, K = 16).  *flops_per_s (host) = 2 M N K x instructions / s over
+   the whole GPU.  Allocates and synchronises.  GRACE_ERR_TIMEOUT if the
+   bounded completion wait gave up. */
+GRACE_API grace_status grace_probe_mma(int device, int precision, int n, double *flops_per_s);
+
 GRACE_API void grace_batch_destroy(grace_batch *batch);
 GRACE_API void grace_destroy(grace_ctx *ctx);
 

@@ -51,7 +51,7 @@ def exported_symbols():
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_set_grouped", "grace_batch_destroy",
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
             "grace_step_host", "grace_step_host_wait", "grace_flags_check",
-            "grace_test_arm_wait_timeout"]
+            "grace_test_arm_wait_timeout", "grace_probe_mma"]
 
 
 def load(path: str | None = None):
@@ -90,6 +90,7 @@ def load(path: str | None = None):
     L.grace_param_grad_setup.argtypes = [_VP, S, S, _VP, ctypes.c_double]
     L.grace_adjoint.argtypes = [_VP, _VP, _VP, S, S, _VP, _VP, _VP, S]
     L.grace_probe_rates.argtypes = [S, ctypes.POINTER(ctypes.c_double)]
+    L.grace_probe_mma.argtypes = [S, S, S, ctypes.POINTER(ctypes.c_double)]
     L.grace_batch_set_graph.argtypes = [_VP, S]
     L.grace_batch_set_grouped.argtypes = [_VP, S]
     L.grace_step_host.argtypes = [_VP, _VP, _VP, _VP, S, S, _VP, _VP]
@@ -145,6 +146,14 @@ def probe_rates(device: int = 0):
     out = (ctypes.c_double * 3)()
     _check(load().grace_probe_rates(int(device), out), "grace_probe_rates")
     return {"fp64_fma_per_s": out[0], "fp32_fma_per_s": out[1], "f64_to_f32_cvt_per_s": out[2]}
+
+
+def probe_mma(precision: int, n: int = 256, device: int = 0) -> float:
+    """Measured dense tcgen05.mma rate (FLOP/s) with M = 128 and the given N: kind::tf32 for
+    TF32, kind::f16 with bf16 operands for BF16X3 (one product per instruction)."""
+    out = ctypes.c_double()
+    _check(load().grace_probe_mma(int(device), int(precision), int(n), ctypes.byref(out)), "grace_probe_mma")
+    return out.value
 
 
 class Context:

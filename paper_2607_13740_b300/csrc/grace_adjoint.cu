@@ -282,7 +282,7 @@ __global__ void mu_to_f32_kernel(int R, int n_cells, const double *__restrict__ 
 }
 
 // w[cell][p] = 2^e h_bin(p) (W0 + W1)[p]: the two epilogue planes of the VJP contraction, unscaled
-__global__ void vjp_combine_kernel(DevGroup G, int Pw, int n_cells, const float *__restrict__ W,
+__global__ void vjp_combine_kernel(DevGroup G, int Pw, int n_cells, int planes, const float *__restrict__ W,
                                    const double *__restrict__ inv_scale, double *__restrict__ w)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -291,9 +291,9 @@ __global__ void vjp_combine_kernel(DevGroup G, int Pw, int n_cells, const float 
     const int p = (int)(t - cell * G.P);
     const long long ct = cell / kTileM, tiles = (n_cells + kTileM - 1) / kTileM;
     const int row = (int)(cell - ct * kTileM);
-    const float s0 = W[((size_t)ct * Pw + p) * kTileM + row];
-    const float s1 = W[(((size_t)tiles + ct) * Pw + p) * kTileM + row];
-    w[t] = inv_scale[cell] * G.hbin[p / G.K1] * ((double)s0 + (double)s1);
+    double s = 0.0;
+    for (int q = 0; q < planes; ++q) s += (double)W[(((size_t)q * tiles + ct) * Pw + p) * kTileM + row];
+    w[t] = inv_scale[cell] * G.hbin[p / G.K1] * s;
 }
 
 // a = g + eps v, b = g - eps v with eps = 2^(e_g - e_v) per cell (e: binary exponents of the
@@ -480,7 +480,8 @@ grace_status prepare_tc(grace_batch *b, int prec, bool vjp, const char *who)
         }
     const size_t tiles = ((size_t)p.n + kTileM - 1) / kTileM;
     cudaError_t e = cudaSuccess;
-    if (!p.d_W32) e = cudaMalloc(&p.d_W32, 2 * tiles * vjp_window_cols(G.dg) * kTileM * sizeof(float));
+    if (!p.d_W32)
+        e = cudaMalloc(&p.d_W32, tc_vjp_planes() * tiles * vjp_window_cols(G.dg) * kTileM * sizeof(float));
     if (e == cudaSuccess && !p.d_mu32) e = cudaMalloc(&p.d_mu32, tiles * G.dg.R * kTileM * sizeof(float));
     if (e == cudaSuccess && !p.d_cscale) e = cudaMalloc(&p.d_cscale, (size_t)p.n * sizeof(double));
     if (e != cudaSuccess) {
@@ -502,7 +503,7 @@ cudaError_t jvp_tc(grace_batch *b, int prec, const double *g, const double *v, d
     cudaError_t e = cudaGetLastError();
     const double *src[2] = {p.d_g1, p.d_g2};
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = launch_pack_A(dg, src[k], n, p.d_opA, prec, G.tc[prec].k_pad, st);
+        e = launch_pack_A(dg, src[k], n, p.d_opA, prec, G.tc[prec].k_pad, G.tc[prec].k_ofs, st);
         if (e == cudaSuccess) e = launch_contract_tc(dg, G.tc[prec], prec, p.d_opA, n, p.d_F32, b->d_err, st);
         if (e == cudaSuccess) {
             polar_accumulate_kernel<<<blocks((long long)n * dg.R, 256), 256, 0, st>>>(
@@ -532,12 +533,13 @@ cudaError_t vjp_tc(grace_batch *b, int prec, const double *gs, const double *lam
         mu_to_f32_kernel<<<blocks((long long)n * 32, 256), 256, 0, st>>>(dg.R, n, p.d_F, p.d_mu32, p.d_cscale);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = launch_pack_A(dg, gs, n, p.d_opA, prec, G.tc[prec].k_pad, st);
+    if (e == cudaSuccess) e = launch_pack_A(dg, gs, n, p.d_opA, prec, G.tc[prec].k_pad, G.tc[prec].k_ofs, st);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(p.d_W32, 0, 2 * tiles * vjp_window_cols(dg) * kTileM * sizeof(float), st);
+        e = cudaMemsetAsync(p.d_W32, 0, tc_vjp_planes() * tiles * vjp_window_cols(dg) * kTileM * sizeof(float), st);
     if (e == cudaSuccess) e = launch_vjp_tc(dg, G.tcv[prec], prec, p.d_opA, p.d_mu32, n, p.d_W32, b->d_err, st);
     if (e == cudaSuccess) {
-        vjp_combine_kernel<<<blocks((long long)n * dg.P, 256), 256, 0, st>>>(dg, vjp_window_cols(dg), n, p.d_W32,
+        vjp_combine_kernel<<<blocks((long long)n * dg.P, 256), 256, 0, st>>>(dg, vjp_window_cols(dg), n,
+                                                                              tc_vjp_planes(), p.d_W32,
                                                                               p.d_cscale, w);
         e = cudaGetLastError();
     }
@@ -555,12 +557,12 @@ cudaError_t fwd_step_tc(grace_batch *b, int prec, const double *pre, double *gt,
     const int n = b->n_cells;
     const size_t bytes = (size_t)n * dg.P * sizeof(double);
     cudaError_t e = cudaMemcpyAsync(gt, pre, bytes, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && dg.limiter) e = launch_limit(dg, gt, n, nullptr, nullptr, 0, 0, st);
+    if (e == cudaSuccess && dg.limiter) e = launch_limit(dg, gt, n, nullptr, nullptr, 0, 0, 0, st);
     const double *gin[3] = {gt, g1, g2};
     double *gout[3] = {g1, g2, next};
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
-        e = launch_pack_A(dg, gin[s], n, p.d_opA, prec, G.tc[prec].k_pad, st);
+        e = launch_pack_A(dg, gin[s], n, p.d_opA, prec, G.tc[prec].k_pad, G.tc[prec].k_ofs, st);
         if (e == cudaSuccess) e = launch_contract_tc(dg, G.tc[prec], prec, p.d_opA, n, p.d_F32, b->d_err, st);
         if (e != cudaSuccess) break;
         UpdateArgs u;
@@ -588,7 +590,7 @@ cudaError_t fwd_step(grace_batch *b, const double *pre, double *gt, double *g1, 
     double *dF = b->parts[0].d_F;
     const size_t bytes = (size_t)n * dg.P * sizeof(double);
     cudaError_t e = cudaMemcpyAsync(gt, pre, bytes, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && dg.limiter) e = launch_limit(dg, gt, n, nullptr, nullptr, 0, 0, st);
+    if (e == cudaSuccess && dg.limiter) e = launch_limit(dg, gt, n, nullptr, nullptr, 0, 0, 0, st);
     const double *gin[3] = {gt, g1, g2};
     double *gout[3] = {g1, g2, next};
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};

@@ -191,7 +191,7 @@ cudaError_t part_rhs(grace_batch *b, Part &p, const double *g, double *L, int pr
         if (G.dg.cell_alpha) {
             e = nc_tc_functionals(b, G, p, prec, g, st);
         } else {
-            e = launch_pack_A(G.dg, g, p.n, p.d_opA, prec, G.tc[prec].k_pad, st);
+            e = launch_pack_A(G.dg, g, p.n, p.d_opA, prec, G.tc[prec].k_pad, G.tc[prec].k_ofs, st);
             if (e != cudaSuccess) return e;
             LaunchTimer timer(b->ctx, 0, st);
             e = launch_contract_tc(G.dg, G.tc[prec], prec, p.d_opA, p.n, p.d_F32, b->d_err, st);
@@ -224,7 +224,7 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
     cudaStream_t st = part_stream(b, p);
     const int n = p.n;
     const bool tc = prec != GRACE_FP64;
-    const int kpad = tc ? G.tc[prec].k_pad : 0;
+    const int kpad = tc ? G.tc[prec].k_pad : 0, kofs = tc ? G.tc[prec].k_ofs : 0;
     void *opA = tc ? p.d_opA : nullptr;
     cudaError_t e = cudaSuccess;
     if (flags) e = cudaMemsetAsync(flags, 0, n, st);
@@ -236,7 +236,7 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
         // Per-cell kernels, reduced-precision forms: FP64 stage rows (the contraction dominates,
         // so the compact layout buys nothing here); functionals from nc_tc_functionals, FP32 K-c.
         if (dg.limiter) {
-            e = launch_limit(dg, g, n, flags, nullptr, 0, 0, st);
+            e = launch_limit(dg, g, n, flags, nullptr, 0, 0, 0, st);
             if (e != cudaSuccess) return e;
         }
         for (int step = 0; step < n_steps; ++step) {
@@ -274,7 +274,7 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
         // caller's FP64 rows.
         const size_t xs = (mixed_bytes_for(dg, n) + 15) / 16 * 2;   // doubles per compact state
         double *X[3] = {p.d_mx, p.d_mx + xs, p.d_mx + 2 * xs};
-        e = launch_limit_pack(dg, g, n, flags, X[0], opA, prec, kpad, st);
+        e = launch_limit_pack(dg, g, n, flags, X[0], opA, prec, kpad, kofs, st);
         if (e != cudaSuccess) return e;
         for (int step = 0; step < n_steps; ++step) {
             const bool last = step == n_steps - 1;
@@ -304,6 +304,7 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
                     u.opA = opA;
                     u.opA_prec = prec;
                     u.opA_kpad = kpad;
+                    u.opA_kofs = kofs;
                 }
                 LaunchTimer timer(b->ctx, 1, st);
                 e = launch_update_tc(dg, u, n, st);
@@ -314,7 +315,7 @@ cudaError_t part_step(grace_batch *b, Part &p, double *g, const double *dt, int 
     }
     // reconstruction of the first step (Sec. 3.2.2); later ones are fused into stage 3
     if (dg.limiter) {
-        e = launch_limit(dg, g, n, flags, nullptr, 0, 0, st);
+        e = launch_limit(dg, g, n, flags, nullptr, 0, 0, 0, st);
         if (e != cudaSuccess) return e;
     }
     for (int step = 0; step < n_steps; ++step) {
@@ -591,7 +592,7 @@ static grace_status grouped_prepare(grace_batch *b, int prec, bool with_mass, bo
         Group &G = b->ctx->groups[p.group];
         const DevGroup &dg = G.dg;
         mp.push_back({&G.tc[prec], p.d_opA, p.d_F32, p.n, dg.R});
-        const int kpad = G.tc[prec].k_pad;
+        const int kpad = G.tc[prec].k_pad, kofs = G.tc[prec].k_ofs;
         const size_t xs = (mixed_bytes_for(dg, p.n) + 15) / 16 * 2;
         double *X[3] = {p.d_mx, p.d_mx + xs, p.d_mx + 2 * xs};
         unsigned char *fl = with_flags ? p.d_flags : nullptr;
@@ -604,6 +605,7 @@ static grace_status grouped_prepare(grace_batch *b, int prec, bool with_mass, bo
         u[0].opA = p.d_opA;
         u[0].opA_prec = prec;
         u[0].opA_kpad = kpad;
+        u[0].opA_kofs = kofs;
         u[0].out_mixed = 1;
         // stages 1, 2, 3 (not the call's last step), 3 of the last step
         for (int c = 1; c < 5; ++c) {
@@ -628,6 +630,7 @@ static grace_status grouped_prepare(grace_batch *b, int prec, bool with_mass, bo
                 v.opA = p.d_opA;
                 v.opA_prec = prec;
                 v.opA_kpad = kpad;
+                v.opA_kofs = kofs;
             }
         }
         for (int c = 0; c < 5; ++c) {
@@ -929,7 +932,7 @@ grace_status grace_limit(grace_batch *b, double *g, unsigned char *flags)
         cudaError_t r = cudaSuccess;
         if (!p.direct) r = gather_state(p, dg.P, g, p.d_g, st);
         if (r == cudaSuccess && fl) r = cudaMemsetAsync(fl, 0, p.n, st);
-        if (r == cudaSuccess) r = launch_limit(dg, gs, p.n, fl, nullptr, 0, 0, st);
+        if (r == cudaSuccess) r = launch_limit(dg, gs, p.n, fl, nullptr, 0, 0, 0, st);
         if (r == cudaSuccess && !p.direct) r = scatter_state(p, dg.P, p.d_g, g, st);
         if (r == cudaSuccess && fl && !p.direct) {
             scatter_kernel<unsigned char><<<nb(p.n), 256, 0, st>>>(p.n, p.d_idx, p.d_flags, flags);

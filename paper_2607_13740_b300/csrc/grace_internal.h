@@ -34,6 +34,7 @@ struct TcTiles {
     int built = 0;
     int n_tiles = 0;          // MMA N-tiles (functional group x p-window)
     int k_pad = 0;            // padded K extent of the A operand (elements)
+    int k_ofs = 0;            // A column of coefficient 0 (a_column_offset; 0 for node-space tiles)
     int max_rows = 0;         // largest MMA N over the tiles
     int slot_bytes = 0;       // largest single B copy (bytes)
     void *d_b = nullptr;      // pre-swizzled B k-step blocks (all tiles back to back)
@@ -140,7 +141,7 @@ struct Part {
     double *d_G = nullptr, *d_H = nullptr;   // [n][NQ], [2][n][NQ] nodal values (cell_alpha groups)
     float *d_gh = nullptr;         // [tiles][P][128] scaled coefficients (cell_alpha groups, tensor forms)
     float *d_s = nullptr;          // [n] sqrt(alpha) in FP32 (cell_alpha groups, tensor forms)
-    float *d_W32 = nullptr;        // tensor-form VJP: two output planes [2][tiles][Pw][128]
+    float *d_W32 = nullptr;        // tensor-form VJP: output planes [tc_vjp_planes()][tiles][Pw][128]
     float *d_mu32 = nullptr;       // tensor-form VJP: mu in FP32, [tiles][R][128]
     double *d_cscale = nullptr;    // tensor-form JVP / VJP: per-cell power-of-two scales
     size_t opA_bytes = 0;
@@ -230,6 +231,7 @@ struct UpdateArgs {
     void *opA = nullptr;           // tensor-core A tiles of gout, or null
     int opA_prec = 0;              // GRACE_TF32 / GRACE_BF16X3
     int opA_kpad = 0;
+    int opA_kofs = 0;              // A column of coefficient 0 (TcTiles::k_ofs)
     int in_mixed = 0;              // tensor path: gn / gs in the compact stage layout
     int out_mixed = 0;             // tensor path: gout in the compact stage layout
 };
@@ -262,20 +264,21 @@ cudaError_t launch_update_tc_grouped(int mode, bool in_mixed, bool out_mixed, co
                                      int n_blocks, size_t smem, cudaStream_t st);
 // the step-start limiter of the tensor path: FP64 rows d_g -> compact stage layout + A operand
 cudaError_t launch_limit_pack(const DevGroup &g, const double *d_g, int n_cells, unsigned char *flags,
-                              double *mixed_out, void *opA, int opA_prec, int opA_kpad, cudaStream_t st);
+                              double *mixed_out, void *opA, int opA_prec, int opA_kpad, int opA_kofs,
+                              cudaStream_t st);
 // bytes of one state in the compact stage layout (FP64 means, FP32 higher modes)
 inline size_t mixed_bytes_for(const DevGroup &g, int n_cells)
 {
     return (size_t)n_cells * g.N * (sizeof(double) + (size_t)g.k * sizeof(float));
 }
 cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned char *flags,
-                         void *opA, int opA_prec, int opA_kpad, cudaStream_t st);
+                         void *opA, int opA_prec, int opA_kpad, int opA_kofs, cudaStream_t st);
 cudaError_t launch_mass(const DevGroup &g, const double *d_g, int n_cells, double *mass,
                         cudaStream_t st);
 cudaError_t launch_project(const DevGroup &g, int ic_kind, const double *ic, int n_cells,
                            double *d_g, cudaStream_t st);
 cudaError_t launch_pack_A(const DevGroup &g, const double *d_g, int n_cells, void *opA, int prec,
-                          int kpad, cudaStream_t st);
+                          int kpad, int kofs, cudaStream_t st);
 
 // events recorded around one launch when the context's profiling is on
 struct LaunchTimer {
@@ -354,12 +357,14 @@ struct TcMulti {
 grace_status build_tc_multi(int prec, const std::vector<TcMultiPart> &parts, TcMulti &out);
 cudaError_t launch_contract_tc_multi(const TcMulti &m, int *d_err, cudaStream_t st);
 void free_tc_multi(TcMulti &m);
-// VJP contraction: W[part][tile][Pw][128] (two partial planes, FP32) with
+// VJP contraction: W[part][tile][Pw][128] (tc_vjp_planes() partial planes, FP32) with
 // W = sum_r mu_r (Shat_r ghat) per cell, mu in the [tile][R][128] layout (FP32)
 cudaError_t launch_vjp_tc(const DevGroup &g, const TcTiles &t, int prec, const void *opA, const float *d_mu32,
                           int n_cells, float *d_W32, int *d_err, cudaStream_t st);
 // coefficient columns of the VJP output planes (P rounded up to the 16-wide windows)
 inline int vjp_window_cols(const DevGroup &g) { return (g.P + 15) / 16 * 16; }
+// partial output planes of the VJP contraction (one per epilogue warp of a TMEM lane quadrant)
+int tc_vjp_planes();
 void free_tc_tiles(TcTiles &t);
 size_t opA_bytes_for(const DevGroup &g, int prec, int n_cells, int *kpad);
 

@@ -58,10 +58,10 @@ namespace {
 constexpr int kWin = 16;            // p window width of every N tile
 constexpr int kMaxF = 16;           // functionals per N tile (kMaxF * kWin = 256)
 constexpr int kMaxN = 256;          // MMA N
-constexpr int kMaxSlots = 16;       // B ring depth, sized at launch from free shared memory
+constexpr int kMaxSlots = 8;        // B ring depth, sized at launch from free shared memory
 constexpr int kAccCols = 256;       // TMEM columns per accumulator buffer
 constexpr int kTmemCols = 512;      // two accumulator buffers
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;   // four per TMEM lane quadrant: the epilogue, not the MMA, set the pace with eight
 constexpr int kEpiSplit = kEpiWarps / 4;   // epilogue warps per TMEM lane quadrant
 constexpr int kEpiF = (kMaxF + kEpiSplit - 1) / kEpiSplit;   // functionals per epilogue warp and tile
 constexpr int kThreads = 32 * (4 + kEpiWarps);
@@ -69,8 +69,12 @@ constexpr int kMaxSplits = 8;
 constexpr int kSmemLimit = 227 * 1024;
 constexpr long long kWaitCycles = 4000000000LL;   // default wait limit, ~2 s at 2 GHz
 
-// cost model (SM cycles), from measurements on this part: one tcgen05.mma with
-// M = 128 issues every ~139 cycles whatever its N; L2 delivers ~45 B/cycle/SM
+// cost model (SM cycles), from measurements on this part: in isolation (grace_probe_mma) one
+// tcgen05.mma with M = 128 and N columns (K = 32 bytes) takes ~0.543 N cycles for N >= 128 (139 at
+// N = 256, 69 at N = 128); inside this kernel the time per instruction hardly falls with N (tiles
+// planned for N <= 128 ran 20 % slower than N <= 256 tiles with 13 % more multiply-adds: issue and
+// operand delivery per instruction, not the tensor rate, set the pace), so an instruction is
+// charged its N = 256 time whatever its N; L2 delivers ~45 B/cycle/SM to the B ring
 constexpr double kMmaClk = 139.0;
 constexpr double kL2BytesPerClk = 45.0;
 constexpr double kTileClk = 60.0;        // accumulator hand-off per tile
@@ -80,9 +84,11 @@ constexpr double kItemClk = 2500.0;      // A tile load + pipeline fill per work
 
 struct TileDesc {
     int b_off16;        // offset of the tile's first k-step block in the B images, in 16-byte units
-    int n;              // MMA N = nf * w
-    int nf_flush;       // functionals (ford[f0 .. f0 + nf)) | flush << 16 (last window of its group: write F)
-    int w;              // p window width (kWin)
+    int n;              // MMA N = (nf - fs) * rows per functional
+    int nf_flush;       // nf | fs << 8 | flush << 16: the group's functionals ford[f0 .. f0 + nf), of
+                        // which fs .. nf - 1 have rows in this window (accumulator columns from fs
+                        // on); flush: last window of the group (write F)
+    int acol;           // A-operand column of the window's first coefficient (p0 + the A column offset)
     int p0;             // first p of the window
     int ks_lo, ks_hi;   // MMA k-steps [ks_lo, ks_hi)
     int f0;             // first functional (index into the functional order)
@@ -250,19 +256,13 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
                  : "memory");
 }
 
-// K-major shared-memory matrix descriptors: SWIZZLE_128B (A: 128-byte rows, 8-row
-// groups 1024 B apart) and SWIZZLE_32B (B: 32-byte rows, 8-row groups 256 B apart)
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
-           ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
-}
-
-__device__ __forceinline__ uint64_t desc_sw32(uint32_t addr)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(256u >> 4) << 32) |
-           ((uint64_t)1u << 46) | ((uint64_t)6u << 61);
-}
+// K-major shared-memory matrix descriptors: SWIZZLE_128B (A: 128-byte rows, 8-row groups 1024 B
+// apart) and SWIZZLE_32B (B: 32-byte rows, 8-row groups 256 B apart).  The low 32 bits hold the
+// start address >> 4 (14 bits) and the leading-byte-offset field (1); the high 32 bits the
+// stride-byte offset >> 4, the descriptor version (bit 46) and the swizzle mode (bits 61-63);
+// these high halves are the same for every operand of a kind:
+constexpr uint32_t kDescHi128 = (1024u >> 4) | (1u << 14) | (2u << 29);
+constexpr uint32_t kDescHi32 = (256u >> 4) | (1u << 14) | (6u << 29);
 
 // instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = n
 __device__ __forceinline__ uint32_t instr_desc(int prec, int n)
@@ -271,24 +271,32 @@ __device__ __forceinline__ uint32_t instr_desc(int prec, int n)
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+// tcgen05.mma (kind::tf32, or kind::f16 with bf16 operands) with the operand descriptors given as
+// their two 32-bit halves.  Only the low half (start address >> 4 | leading-byte-offset field)
+// changes from one k-step to the next, so the issuing thread advances it with one 32-bit add per
+// operand: measured on this part, an issue loop that rebuilds 64-bit descriptors per instruction
+// keeps the tensor pipe about half idle (one thread issues every MMA, and its scalar work sits
+// between consecutive instructions).
+template <int PREC>
+__device__ __forceinline__ void mma_lohi(uint32_t d, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi,
+                                         uint32_t idesc, uint32_t acc)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+    if (PREC == GRACE_TF32)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+            "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+            "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc)
+            : "memory");
 }
 
 // TMEM -> registers, 32 lanes x 16 / 32 columns, no wait
@@ -345,9 +353,17 @@ __device__ __forceinline__ void fail(const TcParams &P, volatile int *abort_flag
 template <int PREC, int W>
 __device__ __forceinline__ void load_window(const uint8_t *a_gen, long long a_tile_bytes, int row, int p0, float *gw)
 {
+    // columns of the tile (TF32: 128 rows x 4 bytes, BF16: 128 rows x 2 planes x 2 bytes per column);
+    // 16-byte chunks at or past the last column read as zeros (a window may reach past the padded row
+    // when the A column offset is not zero; its coefficients there are absent)
+    const int kcols = (int)(a_tile_bytes / (kTileM * 4));
     if (PREC == GRACE_TF32) {
 #pragma unroll
         for (int c = 0; c < W / 4; ++c) {
+            if (p0 + 4 * c >= kcols) {
+                gw[4 * c] = gw[4 * c + 1] = gw[4 * c + 2] = gw[4 * c + 3] = 0.f;
+                continue;
+            }
             const float4 v = *reinterpret_cast<const float4 *>(a_gen + swz_offset(kTileM, row, p0 + 4 * c, 4));
             gw[4 * c] = v.x;
             gw[4 * c + 1] = v.y;
@@ -358,6 +374,11 @@ __device__ __forceinline__ void load_window(const uint8_t *a_gen, long long a_ti
         const size_t lo_plane = (size_t)(a_tile_bytes / 2);
 #pragma unroll
         for (int c = 0; c < W / 8; ++c) {
+            if (p0 + 8 * c >= kcols) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) gw[8 * c + e] = 0.f;
+                continue;
+            }
             const size_t off = swz_offset(kTileM, row, p0 + 8 * c, 2);
             const uint4 hi = *reinterpret_cast<const uint4 *>(a_gen + off);
             const uint4 lo = *reinterpret_cast<const uint4 *>(a_gen + lo_plane + off);
@@ -372,28 +393,29 @@ __device__ __forceinline__ void load_window(const uint8_t *a_gen, long long a_ti
 }
 
 template <int PREC, int W, int G>
-__device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_bytes, int row, int p0,
-                                         uint32_t tcol, int nf, int part, float *Facc)
+__device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_bytes, int row, int acol,
+                                         uint32_t tcol, int nf, int fs, int part, float *Facc)
 {
     float gw[W];
-    load_window<PREC, W>(a_gen, a_tile_bytes, row, p0, gw);
+    load_window<PREC, W>(a_gen, a_tile_bytes, row, acol, gw);
 #pragma unroll
     for (int m0 = 0; m0 < kEpiF; m0 += G) {
         if (kEpiSplit * m0 + part >= nf) break;
+        if (kEpiSplit * (m0 + G - 1) + part < fs) continue;
         uint32_t y[G][W];
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
             const int f = kEpiSplit * (m0 + gg) + part;
-            if (f < nf) {
-                if (W == 32) tmem_ld32(tcol + (uint32_t)(f * W), y[gg]);
-                else tmem_ld16(tcol + (uint32_t)(f * W), y[gg]);
+            if (f >= fs && f < nf) {
+                if (W == 32) tmem_ld32(tcol + (uint32_t)((f - fs) * W), y[gg]);
+                else tmem_ld16(tcol + (uint32_t)((f - fs) * W), y[gg]);
             }
         }
         tmem_wait_ld();
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
             const int f = kEpiSplit * (m0 + gg) + part;
-            if (f < nf) {
+            if (f >= fs && f < nf) {
                 float s0 = 0.f, s1 = 0.f;
 #pragma unroll
                 for (int c = 0; c < W; c += 2) {
@@ -415,8 +437,8 @@ constexpr int kEpiFnc = (kMaxN / (2 * kWin) + kEpiSplit - 1) / kEpiSplit;
 
 template <int PREC, int G>
 __device__ __forceinline__ void epi_tile_nc(const uint8_t *a_gen, long long a_tile_bytes, int row, int p0,
-                                            uint32_t tcol, int nf, int part, float s, const float *D0, float ra,
-                                            float rb, float *Facc)
+                                            uint32_t tcol, int nf, int fs, int part, float s, const float *D0,
+                                            float ra, float rb, float *Facc)
 {
     float wc[kWin], wf[kWin];
     load_window<PREC, kWin>(a_gen, a_tile_bytes, row, p0, wc);
@@ -430,17 +452,18 @@ __device__ __forceinline__ void epi_tile_nc(const uint8_t *a_gen, long long a_ti
 #pragma unroll
     for (int m0 = 0; m0 < kEpiFnc; m0 += G) {
         if (kEpiSplit * m0 + part >= nf) break;
+        if (kEpiSplit * (m0 + G - 1) + part < fs) continue;
         uint32_t y[G][2 * kWin];
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
             const int f = kEpiSplit * (m0 + gg) + part;
-            if (f < nf) tmem_ld32(tcol + (uint32_t)(f * 2 * kWin), y[gg]);
+            if (f >= fs && f < nf) tmem_ld32(tcol + (uint32_t)((f - fs) * 2 * kWin), y[gg]);
         }
         tmem_wait_ld();
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
             const int f = kEpiSplit * (m0 + gg) + part;
-            if (f < nf) {
+            if (f >= fs && f < nf) {
                 float s0 = 0.f, s1 = 0.f;
 #pragma unroll
                 for (int t = 0; t < kWin; ++t) {
@@ -457,20 +480,21 @@ __device__ __forceinline__ void epi_tile_nc(const uint8_t *a_gen, long long a_ti
 // [16 f, 16 f + 16) of functional f hold (S_r ghat)_p for the window's 16 coefficients p; the
 // functional's weight mu_r times them is added to the window accumulator Wacc.
 template <int G>
-__device__ __forceinline__ void epi_tile_vjp(uint32_t tcol, int nf, int part, const float *mu_cell, const int *ford,
-                                             int f0, float *Wacc)
+__device__ __forceinline__ void epi_tile_vjp(uint32_t tcol, int nf, int fs, int part, const float *mu_cell,
+                                             const int *ford, int f0, float *Wacc)
 {
 #pragma unroll
     for (int m0 = 0; m0 < kEpiF; m0 += G) {
         if (kEpiSplit * m0 + part >= nf) break;
+        if (kEpiSplit * (m0 + G - 1) + part < fs) continue;
         uint32_t y[G][kWin];
         float mu[G];
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
             const int f = kEpiSplit * (m0 + gg) + part;
             mu[gg] = 0.f;
-            if (f < nf) {
-                tmem_ld16(tcol + (uint32_t)(f * kWin), y[gg]);
+            if (f >= fs && f < nf) {
+                tmem_ld16(tcol + (uint32_t)((f - fs) * kWin), y[gg]);
                 mu[gg] = mu_cell[(size_t)ford[f0 + f] * kTileM];
             }
         }
@@ -478,7 +502,7 @@ __device__ __forceinline__ void epi_tile_vjp(uint32_t tcol, int nf, int part, co
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
             const int f = kEpiSplit * (m0 + gg) + part;
-            if (f < nf) {
+            if (f >= fs && f < nf) {
 #pragma unroll
                 for (int t = 0; t < kWin; ++t) Wacc[t] = fmaf(mu[gg], __uint_as_float(y[gg][t]), Wacc[t]);
             }
@@ -622,7 +646,8 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             S->a_done[ab] = au + 1;
             tc_fence_after();
             const uint32_t a0 = a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes;
-            const uint32_t a_lo = a0 + (uint32_t)(ic.a_bytes / 2);
+            const uint32_t a0_lo = ((a0 >> 4) & 0x3FFFu) | (1u << 16);       // descriptor low half of A
+            const uint32_t alo_delta = (uint32_t)(ic.a_bytes / 2) >> 4;      // to the lo plane (BF16)
             for (int t = ic.t0; t < ic.t1 && !*abort_flag; ++t) {
                 const TileDesc td = ic.tiles[t];
                 const int buf = acc_use & 1, bu = acc_use >> 1;
@@ -646,17 +671,19 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     tc_fence_after();
                     const uint32_t bslot = b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes;
                     const int k0 = c * kps, kn = min(kps, nks - k0);
-                    for (int kk = 0; kk < kn; ++kk) {
-                        const int ks = td.ks_lo + k0 + kk;
-                        const uint32_t a_off = (uint32_t)(ks >> 2) * (kTileM * 128u) + (uint32_t)(ks & 3) * 32u;
-                        const uint32_t bk = bslot + (uint32_t)kk * ks_bytes;
+                    // descriptor low halves in 16-byte units: A k-step ks sits in 128-byte atom ks / 4
+                    // (128 rows x 128 B apart) at 32 B x (ks % 4); B k-step blocks follow each other
+                    uint32_t b_lo = ((bslot >> 4) & 0x3FFFu) | (1u << 16);
+                    const uint32_t b_step = ks_bytes >> 4, b_plane = (uint32_t)td.n * 2u;
+                    int ks = td.ks_lo + k0;
+                    for (int kk = 0; kk < kn; ++kk, ++ks, b_lo += b_step) {
+                        const uint32_t a_lo16 = a0_lo + (uint32_t)(ks >> 2) * (kTileM * 8u) + (uint32_t)(ks & 3) * 2u;
                         if (PREC == GRACE_TF32) {
-                            mma_tf32(d, desc_sw128(a0 + a_off), desc_sw32(bk), idesc, acc);
+                            mma_lohi<PREC>(d, a_lo16, kDescHi128, b_lo, kDescHi32, idesc, acc);
                         } else {
-                            const uint64_t bh = desc_sw32(bk), bl = desc_sw32(bk + (uint32_t)td.n * 32u);
-                            mma_f16(d, desc_sw128(a0 + a_off), bh, idesc, acc);
-                            mma_f16(d, desc_sw128(a0 + a_off), bl, idesc, 1u);
-                            mma_f16(d, desc_sw128(a_lo + a_off), bh, idesc, 1u);
+                            mma_lohi<PREC>(d, a_lo16, kDescHi128, b_lo, kDescHi32, idesc, acc);
+                            mma_lohi<PREC>(d, a_lo16, kDescHi128, b_lo + b_plane, kDescHi32, idesc, 1u);
+                            mma_lohi<PREC>(d, a_lo16 + alo_delta, kDescHi128, b_lo, kDescHi32, idesc, 1u);
                         }
                         acc = 1u;
                     }
@@ -712,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     break;
                 }
                 const TileDesc td = ic.tiles[t];
-                const int nf = td.nf_flush & 0xFFFF;
+                const int nf = td.nf_flush & 0xFF, fs = (td.nf_flush >> 8) & 0xFF;
                 const int buf = acc_use & 1, bu = acc_use >> 1;
                 if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->acc_full[buf]), bu & 1, abort_flag, P.wait_cycles))) {
                     fail(P, abort_flag, 128);
@@ -722,12 +749,12 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 tc_fence_after();
                 const uint32_t tcol = tmem + tlane + (uint32_t)(buf * kAccCols);
                 if (MODE == kModeNC)
-                    epi_tile_nc<PREC, 2>(a_gen, ic.a_bytes, row, td.p0, tcol, nf, part, s_cell, D0s, P.ramp_a,
+                    epi_tile_nc<PREC, 1>(a_gen, ic.a_bytes, row, td.p0, tcol, nf, fs, part, s_cell, D0s, P.ramp_a,
                                          P.ramp_b, Facc);
                 else if (MODE == kModeVJP)
-                    epi_tile_vjp<4>(tcol, nf, part, mu_cell, ford, td.f0, Wacc);
+                    epi_tile_vjp<2>(tcol, nf, fs, part, mu_cell, ford, td.f0, Wacc);
                 else
-                    epi_tile<PREC, kWin, kEpiF>(a_gen, ic.a_bytes, row, td.p0, tcol, nf, part, Facc);
+                    epi_tile<PREC, kWin, 2>(a_gen, ic.a_bytes, row, td.acol, tcol, nf, fs, part, Facc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&S->acc_empty[buf]));
@@ -861,6 +888,7 @@ namespace {
 // w * p0_stride.
 struct Forms {
     int R = 0, rows = 0, kdim = 0, W = 0, p0_stride = 0;
+    int aofs = 0;   // A-operand column of coefficient 0 of the windows (the A column offset)
     std::vector<double> M;
     const double *row(int r, int p) const { return M.data() + ((size_t)r * rows + p) * kdim; }
     int n_win() const { return (rows + W - 1) / W; }
@@ -914,14 +942,17 @@ Plan plan_forms(const Forms &F, const std::vector<int> &ford, int prec)
     for (int x = 0; x < R; ++x) {
         if (best[x] >= inf) continue;
         std::vector<Ext> Un(nw, Ext{F.kdim, 0});
+        std::vector<int> first_live(nw, -1);   // first functional of [x, y) with rows in the window
         for (int y = x + 1; y <= std::min(R, x + maxf); ++y) {
             double c = 0.0;
             for (int w = 0; w < nw; ++w) {
                 const Ext &E = pl.wext[y - 1][w];
+                if (E.hi > E.lo && first_live[w] < 0) first_live[w] = y - 1;
                 Un[w].lo = std::min(Un[w].lo, E.lo);
                 Un[w].hi = std::max(Un[w].hi, E.hi);
                 if (Un[w].hi > Un[w].lo)
-                    c += tile_cost(prec, (y - x) * W, (Un[w].hi + kstep - 1) / kstep - Un[w].lo / kstep);
+                    c += tile_cost(prec, (y - first_live[w]) * W,
+                                   (Un[w].hi + kstep - 1) / kstep - Un[w].lo / kstep);
             }
             if (best[x] + c < best[y]) {
                 best[y] = best[x] + c;
@@ -954,22 +985,26 @@ grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &
     for (size_t gi = 0; gi < pl.first.size(); ++gi) {
         const int x = pl.first[gi];
         const int y = gi + 1 < pl.first.size() ? pl.first[gi + 1] : R;
-        const int nf = y - x, n = nf * W;
+        const int nf = y - x;
         const size_t first = tiles.size();
         double gcost = 0.0;
         for (int w = 0; w < nw; ++w) {
             Ext Un{F.kdim, 0};
+            int fs = -1;   // functionals before the first one with rows in this window take no columns
             for (int f = x; f < y; ++f) {
-                Un.lo = std::min(Un.lo, pl.wext[f][w].lo);
-                Un.hi = std::max(Un.hi, pl.wext[f][w].hi);
+                const Ext &E = pl.wext[f][w];
+                if (E.hi > E.lo && fs < 0) fs = f - x;
+                Un.lo = std::min(Un.lo, E.lo);
+                Un.hi = std::max(Un.hi, E.hi);
             }
             if (Un.hi <= Un.lo) continue;
+            const int n = (nf - fs) * W;
             TileDesc td;
             std::memset(&td, 0, sizeof(td));
             td.n = n;
-            td.nf_flush = nf;
-            td.w = W;
+            td.nf_flush = nf | (fs << 8);
             td.p0 = w * F.p0_stride;
+            td.acol = td.p0 + F.aofs;
             td.ks_lo = Un.lo / kstep;
             td.ks_hi = (Un.hi + kstep - 1) / kstep;
             td.f0 = x;
@@ -980,9 +1015,9 @@ grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &
             uint8_t *img = B.data() + (size_t)td.b_off16 * 16;
             for (int s = 0; s < nks; ++s) {
                 uint8_t *bk = img + (size_t)s * blk * planes;
-                for (int f = 0; f < nf; ++f)
+                for (int f = fs; f < nf; ++f)
                     for (int c = 0; c < W; ++c) {
-                        const int p = w * W + c, rowi = f * W + c;
+                        const int p = w * W + c, rowi = (f - fs) * W + c;
                         if (p >= F.rows) continue;
                         const double *Mr = F.row(ford[x + f], p);
                         for (int xx = 0; xx < kstep; ++xx) {
@@ -1034,7 +1069,7 @@ grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &
         out.group_cost.clear();
         for (size_t i = 0; i < idx.size(); ++i) {
             TileDesc td = tiles[idx[i]];
-            td.nf_flush &= 0xFFFF;
+            td.nf_flush &= 0xFFFF;   // keep nf and fs, clear the flush bit
             const bool first = i == 0 || tile_win[idx[i]] != tile_win[idx[i - 1]];
             const bool last = i + 1 == idx.size() || tile_win[idx[i]] != tile_win[idx[i + 1]];
             if (first) {
@@ -1069,6 +1104,27 @@ grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &
     out.pred_clk = pl.cost;
     out.slot_bytes = (out.slot_bytes + 1023) / 1024 * 1024;
     return GRACE_OK;
+}
+
+// The A operand stores coefficient q at column q + kofs, so that the coefficient range ends close
+// to the padded K extent (every k-step block ends on a k-step boundary there).  Moves the columns
+// of M ([R][P][P], coefficient q in column q) to q + kofs; with shift_rows its rows p to p + kofs
+// as well.  The rows keep their place by default: the p windows stay aligned to the coefficients
+// (fewer padded rows), the window of coefficients [p0, p0 + 16) is read from A columns
+// [p0 + kofs, p0 + kofs + 16), and the epilogue reads zeros past the padded row.
+void shift_forms(Forms &F, int P, int kofs, bool shift_rows)
+{
+    F.aofs = shift_rows ? 0 : kofs;
+    if (kofs == 0) return;
+    const int kd = P + kofs, rows = shift_rows ? P + kofs : P, r0 = shift_rows ? kofs : 0;
+    std::vector<double> M((size_t)F.R * rows * kd, 0.0);
+    for (int r = 0; r < F.R; ++r)
+        for (int p = 0; p < P; ++p)
+            std::memcpy(M.data() + ((size_t)r * rows + p + r0) * kd + kofs, F.M.data() + ((size_t)r * P + p) * P,
+                        (size_t)P * sizeof(double));
+    F.M.swap(M);
+    F.kdim = kd;
+    F.rows = rows;
 }
 
 // functionals in bin order: interface flux of bin j, then its volume terms
@@ -1152,6 +1208,9 @@ grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, Tc
     out = TcTiles();
     const int ae = atom_elems(prec);
     out.k_pad = (P_ + ae - 1) / ae * ae;
+    out.k_ofs = a_column_offset(prec, P_);
+    shift_forms(FT, P_, out.k_ofs, false);
+    shift_forms(FU, P_, out.k_ofs, false);
     if (nnz_T == 0) {
         out.built = 1;
         return GRACE_OK;
@@ -1204,6 +1263,8 @@ grace_status build_vjp_tiles(Group &G, int prec, cudaStream_t st)
                 F.M[i] = (T[i] + T[it]) / (h[p / K1] * h[q / K1]);
             }
     const std::vector<int> ford = functional_order(g);
+    const int kofs = a_column_offset(prec, P_);
+    shift_forms(F, P_, kofs, false);
     const Plan pl = plan_forms(F, ford, prec);
     TcTiles out;
     std::vector<int> written;
@@ -1211,6 +1272,7 @@ grace_status build_vjp_tiles(Group &G, int prec, cudaStream_t st)
     if (s != GRACE_OK) return s;
     const int ae = atom_elems(prec);
     out.k_pad = (P_ + ae - 1) / ae * ae;
+    out.k_ofs = kofs;
     out.vjp = 1;
     out.built = 1;
     free_tc_tiles(G.tcv[prec]);
@@ -1358,18 +1420,19 @@ static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
                            (MODE == kModeNC ? (size_t)P.n_d0 * sizeof(float) : 0) + 15) / 16 * 16);
     const size_t fixed = 1024 + (size_t)P.table_bytes + sizeof(Smem) + 64;
     const size_t a1 = (size_t)P.a_tile_bytes;
-    // Shared-memory plan: 64 KB B copies at N = 256 (fewer k-steps per copy for groups whose A tile
-    // leaves less room); two A tiles (the next work item's A loads during this one) when that still
-    // leaves a 4-deep B ring, else one.  An issuing thread completes about one bulk copy per ~800
-    // cycles whatever its size, so the B stream is bound by the number of copies: measured on the
-    // 65,536-cell workload, 64 KB copies in a 2-deep ring beat 48 KB x 3 and 32 KB x 4 (and 16 KB
-    // copies with two A tiles).
+    // Shared-memory plan: B copies of up to 64 KB (4 BF16 / 8 TF32 k-steps at N = 256) in a ring of at
+    // least two, fewer k-steps per copy for groups whose A tile leaves less room; two A tiles (the
+    // next work item's A loads during this one) only when that still leaves a 4-deep ring.  The MMA
+    // thread pays a fixed cost per copy (barrier wait, fence, commit), so few large copies beat a
+    // deeper ring of small ones: measured on the 65,536-cell workload (BF16x3), two A tiles with a
+    // 3-deep ring of 32 KB copies took 0.217 ms against 0.203 ms for one A tile and 2 x 64 KB (the
+    // A-tile waits fell from 21k to 4k cycles per CTA, the B and per-copy time grew by 50k).
     auto slot_of = [&](int kps) { return (int)(((size_t)kps * max_rows * 32 * planes + 1023) / 1024 * 1024); };
     P.kps = PREC == GRACE_TF32 ? 8 : 4;
     while (P.kps > 1 && fixed + a1 + 2 * (size_t)slot_of(P.kps) > (size_t)kSmemLimit) P.kps /= 2;
+    P.a_bufs = fixed + 2 * a1 + 4 * (size_t)slot_of(P.kps) <= (size_t)kSmemLimit ? 2 : 1;
     P.slot_bytes = slot_of(P.kps);
-    if (fixed + a1 + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
-    P.a_bufs = fixed + 2 * a1 + 4 * (size_t)P.slot_bytes <= (size_t)kSmemLimit ? 2 : 1;
+    if (fixed + P.a_bufs * a1 + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
     P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed - P.a_bufs * a1) / P.slot_bytes);
     const size_t smem = fixed + P.a_bufs * a1 + (size_t)P.n_slots * P.slot_bytes;
     cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1526,3 +1589,7 @@ extern "C" grace_status grace_test_arm_wait_timeout(long long wait_cycles)
     grace::g_armed_wait_cycles.store(wait_cycles);
     return GRACE_OK;
 }
+
+namespace grace {
+int tc_vjp_planes() { return kEpiSplit; }
+}  // namespace grace

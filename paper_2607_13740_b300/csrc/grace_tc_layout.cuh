@@ -37,6 +37,16 @@ __host__ __device__ __forceinline__ size_t swz_offset(int rows, int row, int k, 
     return (size_t)atom * rows * kAtomBytes + (size_t)row * kAtomBytes + (chunk << 4) + (inrow & 15);
 }
 
+// A-operand column of coefficient 0 for P coefficients: the coefficients sit at the end of the
+// padded K extent (columns [kofs, kofs + P)), so that the tables' non-zero column ranges, which
+// mostly run to the last coefficient, end on a k-step boundary.  Kept a multiple of 16 bytes
+// (8 BF16 / 4 TF32 values) so that 16-byte chunks of a row stay aligned.
+__host__ __device__ __forceinline__ int a_column_offset(int prec, int P)
+{
+    const int ae = atom_elems(prec), kpad = (P + ae - 1) / ae * ae, align = 16 / elem_bytes(prec);
+    return (kpad - P) / align * align;
+}
+
 // bytes of one A tile (128 cells, kpad elements, all planes)
 __host__ __device__ __forceinline__ size_t opA_tile_bytes(int prec, int kpad)
 {

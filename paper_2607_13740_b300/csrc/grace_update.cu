@@ -412,7 +412,7 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
         }
         if (A.opA) {
             const float h = G.h32[j];
-            float *ar = arow + j * K1;
+            float *ar = arow + A.opA_kofs + j * K1;
             ar[0] = d2f_fast(v0) * h;
 #pragma unroll
             for (int i = 1; i < kB; ++i)
@@ -421,8 +421,10 @@ __device__ __forceinline__ void update_tc_body(const DevGroup &G, const UpdateAr
         if (A.mass) msum = fma(G.hbin[j], v0, msum);
     }
     const unsigned gmask = LPC == 32 ? 0xffffffffu : (((1u << LPC) - 1u) << (threadIdx.x & (32 - LPC)));
-    if (A.opA)
-        for (int e = P + lane; e < lda; e += LPC) arow[e] = 0.f;
+    if (A.opA) {
+        for (int e = lane; e < A.opA_kofs; e += LPC) arow[e] = 0.f;
+        for (int e = A.opA_kofs + P + lane; e < lda; e += LPC) arow[e] = 0.f;
+    }
     __syncwarp(gmask);
     // coalesced stores of an FP64 result row (the compact layout was written above)
     if (MODE != MODE_LIMIT && !OUT_MIX) {
@@ -659,7 +661,8 @@ cudaError_t launch_update_tc(const DevGroup &g, const UpdateArgs &a, int n_cells
 }
 
 cudaError_t launch_limit_pack(const DevGroup &g, const double *d_g, int n_cells, unsigned char *flags,
-                              double *mixed_out, void *opA, int opA_prec, int opA_kpad, cudaStream_t st)
+                              double *mixed_out, void *opA, int opA_prec, int opA_kpad, int opA_kofs,
+                              cudaStream_t st)
 {
     if (n_cells <= 0) return cudaSuccess;
     UpdateArgs a;
@@ -670,12 +673,13 @@ cudaError_t launch_limit_pack(const DevGroup &g, const double *d_g, int n_cells,
     a.opA = opA;
     a.opA_prec = opA_prec;
     a.opA_kpad = opA_kpad;
+    a.opA_kofs = opA_kofs;
     a.out_mixed = 1;
     return launch_update_mode<MODE_LIMIT, false, true>(g, a, n_cells, st);
 }
 
 cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned char *flags, void *opA,
-                         int opA_prec, int opA_kpad, cudaStream_t st)
+                         int opA_prec, int opA_kpad, int opA_kofs, cudaStream_t st)
 {
     if (n_cells <= 0) return cudaSuccess;
     if (opA) {
@@ -688,6 +692,7 @@ cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned c
         a.opA = opA;
         a.opA_prec = opA_prec;
         a.opA_kpad = opA_kpad;
+        a.opA_kofs = opA_kofs;
         return launch_update_mode<MODE_LIMIT, false, false>(g, a, n_cells, st);
     }
     limit_kernel<<<warp_blocks(n_cells), 256, (size_t)8 * g.P * sizeof(double), st>>>(g, d_g, n_cells, flags, opA,
@@ -712,7 +717,7 @@ cudaError_t launch_project(const DevGroup &g, int ic_kind, const double *ic, int
 }
 
 cudaError_t launch_pack_A(const DevGroup &g, const double *d_g, int n_cells, void *opA, int prec, int kpad,
-                          cudaStream_t st)
+                          int kofs, cudaStream_t st)
 {
     if (n_cells <= 0) return cudaSuccess;
     UpdateArgs a;
@@ -720,6 +725,7 @@ cudaError_t launch_pack_A(const DevGroup &g, const double *d_g, int n_cells, voi
     a.opA = opA;
     a.opA_prec = prec;
     a.opA_kpad = kpad;
+    a.opA_kofs = kofs;
     return launch_update_mode<MODE_LIMIT, false, false>(g, a, n_cells, st);
 }
 

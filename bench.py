@@ -540,6 +540,86 @@ def run_uneven(args):
     print(json.dumps(line), flush=True)
 
 
+def run_eoc(args):
+    """Paper-scale convergence study (Sec. 4.2, eq. eoc) on the GPU in FP64: constant kernel K = 1,
+    non-conservative fluxes on [1e-3, 1e15], f(x, 0) = exp(-x) (g0 = x exp(-x)), to tau = 3e12 against
+    eq. (fcoagsolution), N in {10, 20, 40, 100, 200} and k in {0..4}; time step dt = c (2 + tau), a
+    fixed fraction c of the collision time of the self-similar solution.  Errors e_c (16 Gauss points
+    per bin) and e_d (geometric bin centres) of Sec. 4.1, the relative error of M_1, and the EOC
+    ln(e_N / e_N') / ln(N' / N) between successive N.  One JSON line."""
+    import numpy as np
+    import torch
+    from numpy.polynomial import legendre as npl
+    from paper_2607_13740_b300 import grace, workloads as W
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    tau_end = float(args.tau or 3e12)
+    c = float(args.eoc_c)
+    Ns = [int(x) for x in (args.eoc_n or "10,20,40,100,200").split(",")]
+    ks = [int(x) for x in (args.eoc_k or "0,1,2,3,4").split(",")]
+    s16, w16 = npl.leggauss(16)
+
+    def exact(x, t):
+        return x * 4.0 / (2.0 + t) ** 2 * np.exp(-2.0 * x / (2.0 + t))
+
+    def errors(coef, e, k, t):
+        coef = coef.reshape(len(e) - 1, k + 1)
+        h, xc = np.diff(e), 0.5 * (e[1:] + e[:-1])
+        x = xc[:, None] + 0.5 * h[:, None] * s16[None, :]
+        gh = np.stack([npl.legval(s16, coef[j]) for j in range(len(e) - 1)])
+        ec = float((0.5 * h * (w16[None, :] * np.abs(gh - exact(x, t))).sum(axis=1)).sum())
+        xg = np.sqrt(e[1:] * e[:-1])
+        gd = np.array([npl.legval(2.0 * (xg[j] - xc[j]) / h[j], coef[j]) for j in range(len(e) - 1)])
+        ed = float((h * np.abs(gd - exact(xg, t))).sum())
+        return ec, ed
+
+    res, t0_all = {}, time.time()
+    for k in ks:
+        for N in Ns:
+            spec = W.constant_kernel_spec(N, k, W.FLUX_NONCONSERVATIVE, 1e-3, 1e15)
+            ctx = grace.Context([spec], local)
+            b = ctx.batch(1)
+            g = b.project(W.IC_EXP, [[1.0, 1.0, 0.0, 0.0]])
+            dt = torch.zeros(1, dtype=torch.float64, device=dev)
+            t, n_steps = 0.0, 0
+            torch.cuda.synchronize()
+            tw = time.time()
+            while t < tau_end * (1.0 - 1e-15):
+                step = min(c * (2.0 + t), tau_end - t)
+                dt.fill_(step)
+                b.step(g, dt, 1, grace.FP64)
+                t += step
+                n_steps += 1
+            torch.cuda.synchronize()
+            wall = time.time() - tw
+            e = spec.x_min * (spec.x_max / spec.x_min) ** (np.arange(N + 1) / N)
+            e[0], e[-1] = spec.x_min, spec.x_max
+            coef = g.cpu().numpy().reshape(-1)
+            ec, ed = errors(coef, e, k, t)
+            m1 = float((np.diff(e) * coef.reshape(N, k + 1)[:, 0]).sum())
+            res[(k, N)] = {"e_c": ec, "e_d": ed, "mass_rel_err": abs(m1 - 1.0), "steps": n_steps, "gpu_wall_s": wall,
+                           "finite": bool(np.isfinite(coef).all())}
+    eoc = {}
+    for k in ks:
+        eoc[k] = []
+        for N1, N2 in zip(Ns[:-1], Ns[1:]):
+            a, b_ = res[(k, N1)]["e_c"], res[(k, N2)]["e_c"]
+            eoc[k].append(math.log(a / b_) / math.log(N2 / N1) if a > 0 and b_ > 0 else None)
+    line = {
+        "metric": "EOC of the constant-kernel test (Sec. 4.2) at tau = 3e12, FP64 on the GPU", "unit": "order",
+        "value": {str(k): eoc[k][-1] for k in ks}, "n_gpus": 1, "data": "synthetic (analytic test problem)",
+        "dtype": "f64", "higher_is_better": True,
+        "config": {"workload": "constant_kernel_eoc", "x_range": [1e-3, 1e15], "flux": "non-conservative",
+                   "ic": "f(x,0) = exp(-x)", "tau_end": tau_end, "dt": f"{c} (2 + tau)", "N": Ns, "k": ks},
+        "eoc_per_k": {str(k): eoc[k] for k in ks},
+        "errors": {f"k{k}_N{N}": v for (k, N), v in res.items()},
+        "paper": "EOC = k + 1 for N = 10..200, k = 0..4; e_c < 1% at k = 4 with N = 40",
+        "wall_s": time.time() - t0_all,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,7 +635,11 @@ def main():
     ap.add_argument("--skip-fp64-compare", action="store_true", help="adjoint workload: no FP64 comparison run")
     ap.add_argument("--forms", default=None,
                     help="comma-separated subset of fp64,tf32,bf16x3 to time (default: all built)")
-    ap.add_argument("--workload", default="additive", choices=["additive", "disk", "uneven", "adjoint"],
+    ap.add_argument("--tau", type=float, default=None, help="eoc workload: end time (default 3e12)")
+    ap.add_argument("--eoc-c", type=float, default=0.02, help="eoc workload: dt = c (2 + tau)")
+    ap.add_argument("--eoc-n", default=None, help="eoc workload: comma-separated bin counts")
+    ap.add_argument("--eoc-k", default=None, help="eoc workload: comma-separated degrees")
+    ap.add_argument("--workload", default="additive", choices=["additive", "disk", "uneven", "adjoint", "eoc"],
                     help="additive: the batched additive-kernel headline; disk: coagulation + fragmentation "
                          "with a per-cell turbulence strength (node-space path); uneven: many groups in one batch; "
                          "adjoint: checkpointed adjoint of 200 steps with parameter gradients")
@@ -571,6 +655,9 @@ def main():
         return run_adjoint(args)
     if args.workload == "uneven":
         run_uneven(args)
+        return
+    if args.workload == "eoc":
+        run_eoc(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

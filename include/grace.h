@@ -99,7 +99,7 @@ enum { GRACE_FLAG_NEGATIVE_MEAN = 1,  /* a cell mean g_j^0 went negative (eq. dt
 /* One (grid, order, physics) combination shared by the cells of a group. */
 typedef struct {
     int n_bins;       /* N >= 2: logarithmic bins on [x_min, x_max] (Sec. 3.1)          */
-    int order_k;      /* k in 0..3: Legendre degree (eq. 2.3)                            */
+    int order_k;      /* k in 0..4: Legendre degree (eq. 2.3); 0..3 with cell_alpha      */
     int quad_q;       /* Gauss points per quadrature piece; 0 means k+1 (Sec. 3.3), <= 16 */
     int flux_mode;    /* GRACE_FLUX_*                                                   */
     int coag_kind;    /* GRACE_COAG_*                                                   */

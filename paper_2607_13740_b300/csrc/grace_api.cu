@@ -114,7 +114,7 @@ static grace_status validate(const grace_group_desc &d, int idx)
     if (d.n_bins < 2 || d.n_bins > 4096) return bad("n_bins must be in [2, 4096]");
     if (d.order_k < 0) return bad("order_k must be >= 0");
     if (d.order_k > kKMax) {
-        set_error("group " + std::to_string(idx) + ": order_k > 3 is not supported (the analytic limiter minimum covers k <= 3)");
+        set_error("group " + std::to_string(idx) + ": order_k > 4 is not supported");
         return GRACE_ERR_UNSUPPORTED;
     }
     const int Q = d.quad_q > 0 ? d.quad_q : d.order_k + 1;
@@ -128,6 +128,7 @@ static grace_status validate(const grace_group_desc &d, int idx)
     if (d.cell_alpha != 0 && d.cell_alpha != 1) return bad("cell_alpha must be 0 or 1");
     if (d.cell_alpha) {
         if (d.coag_kind != GRACE_COAG_BALLISTIC) return bad("cell_alpha needs coag_kind BALLISTIC");
+        if (d.order_k > 3) return bad("cell_alpha groups support order_k <= 3");
         if (d.frag_kind != GRACE_FRAG_NONE && d.frag_kind != GRACE_FRAG_BALLISTIC)
             return bad("cell_alpha needs frag_kind NONE or BALLISTIC");
         if (d.frag_kind == GRACE_FRAG_BALLISTIC)

@@ -15,26 +15,32 @@ namespace grace {
 
 namespace {
 
+// CPW cells per warp: 32 (one lane per cell), or 8 for groups whose 32-cell tile would not fit in
+// shared memory (P > 800 coefficients, e.g. N = 200 bins of degree 4): then four lanes share a cell,
+// each summing every fourth q of a row, and the row sums are combined with shuffles.
+template <int CPW>
 __global__ void __launch_bounds__(128) contract_fp64_kernel(
     const double *__restrict__ T, const int *__restrict__ qlo, const int *__restrict__ qhi,
     const int *__restrict__ prange, int R, int P, const double *__restrict__ g, int n_cells,
     double *__restrict__ F)
 {
+    constexpr int SUB = 32 / CPW;    // lanes per cell
     extern __shared__ double gsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const long long cell0 = ((long long)blockIdx.x * nwarps + warp) * 32;
-    double *gw = gsm + (size_t)warp * P * 32;
+    const long long cell0 = ((long long)blockIdx.x * nwarps + warp) * CPW;
+    double *gw = gsm + (size_t)warp * P * CPW;
 
-    // coalesced load of 32 consecutive cells, stored transposed
-    for (int idx = lane; idx < 32 * P; idx += 32) {
+    // coalesced load of CPW consecutive cells, stored transposed
+    for (int idx = lane; idx < CPW * P; idx += 32) {
         const int c = idx / P, q = idx - c * P;
         const long long cell = cell0 + c;
-        gw[q * 32 + c] = cell < n_cells ? g[cell * P + q] : 0.0;
+        gw[q * CPW + c] = cell < n_cells ? g[cell * P + q] : 0.0;
     }
     __syncwarp();
 
-    const long long cell = cell0 + lane;
+    const int c = lane % CPW, sub = lane / CPW;
+    const long long cell = cell0 + c;
     const int r_per = (R + gridDim.y - 1) / gridDim.y;
     const int r_begin = blockIdx.y * r_per, r_end = min(R, r_begin + r_per);
     for (int r = r_begin; r < r_end; ++r) {
@@ -45,15 +51,18 @@ __global__ void __launch_bounds__(128) contract_fp64_kernel(
             if (q0 >= q1) continue;
             const double *Trow = T + ((size_t)r * P + p) * P;
             double y0 = 0.0, y1 = 0.0;
-            int q = q0;
-            for (; q + 1 < q1; q += 2) {
-                y0 = fma(__ldg(Trow + q), gw[q * 32 + lane], y0);
-                y1 = fma(__ldg(Trow + q + 1), gw[(q + 1) * 32 + lane], y1);
+            int q = q0 + sub;
+            for (; q + SUB < q1; q += 2 * SUB) {
+                y0 = fma(__ldg(Trow + q), gw[q * CPW + c], y0);
+                y1 = fma(__ldg(Trow + q + SUB), gw[(q + SUB) * CPW + c], y1);
             }
-            if (q < q1) y0 = fma(__ldg(Trow + q), gw[q * 32 + lane], y0);
-            Fr = fma(gw[p * 32 + lane], y0 + y1, Fr);
+            if (q < q1) y0 = fma(__ldg(Trow + q), gw[q * CPW + c], y0);
+            double y = y0 + y1;
+#pragma unroll
+            for (int o = CPW; o < 32; o <<= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            Fr = fma(gw[p * CPW + c], y, Fr);
         }
-        if (cell < n_cells) F[cell * R + r] = Fr;
+        if (sub == 0 && cell < n_cells) F[cell * R + r] = Fr;
     }
 }
 
@@ -74,19 +83,26 @@ cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int
                                  const int *d_prange, const double *d_g, int n_cells, double *d_F,
                                  cudaStream_t st)
 {
-    const size_t per_warp = (size_t)g.P * 32 * sizeof(double);
+    const bool wide = (size_t)g.P * 32 * sizeof(double) > 200 * 1024;   // 32-cell tile too large
+    const int cpw = wide ? 8 : 32;
+    const size_t per_warp = (size_t)g.P * cpw * sizeof(double);
     int wpb = (int)((200 * 1024) / per_warp);
     if (wpb > 4) wpb = 4;
-    if (wpb < 1) return cudaErrorInvalidValue;   // P too large for one warp's tile
+    if (wpb < 1) return cudaErrorInvalidValue;   // P too large even for 8 cells per warp
     const size_t smem = per_warp * wpb;
     // the attribute belongs to the current device, so it is set on every launch
-    cudaError_t e = cudaFuncSetAttribute(contract_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = wide ? cudaFuncSetAttribute(contract_fp64_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem)
+                         : cudaFuncSetAttribute(contract_fp64_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem);
     if (e != cudaSuccess) return e;
-    const int cells_per_block = 32 * wpb;
+    const int cells_per_block = cpw * wpb;
     const int blocks = (n_cells + cells_per_block - 1) / cells_per_block;
     const dim3 grid(blocks, fp64_functional_chunks(n_cells, g.R));
-    contract_fp64_kernel<<<grid, 32 * wpb, smem, st>>>(d_T, d_qlo, d_qhi, d_prange, g.R, g.P, d_g, n_cells, d_F);
+    if (wide)
+        contract_fp64_kernel<8><<<grid, 32 * wpb, smem, st>>>(d_T, d_qlo, d_qhi, d_prange, g.R, g.P, d_g, n_cells, d_F);
+    else
+        contract_fp64_kernel<32><<<grid, 32 * wpb, smem, st>>>(d_T, d_qlo, d_qhi, d_prange, g.R, g.P, d_g, n_cells, d_F);
     return cudaGetLastError();
 }
 

@@ -11,7 +11,7 @@
 namespace grace {
 
 constexpr int kQMax = 16;   // Gauss points per quadrature piece on the device
-constexpr int kKMax = 3;    // largest Legendre degree with an analytic limiter
+constexpr int kKMax = 4;    // largest Legendre degree (bin minimum: closed form to k = 3, bracketed for k = 4)
 
 // Everything a device kernel needs to know about a group, passed by value.
 struct DevGroup {

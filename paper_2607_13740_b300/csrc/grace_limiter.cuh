@@ -1,5 +1,7 @@
 // Scaling limiter of eqs. (recon) and (gamma): minimum of a bin's polynomial
-// (closed form for k <= 3), an FP32 positivity pre-test and the limiter itself.
+// (closed form for k <= 3; for k = 4 the stationary points are bracketed between the
+// roots of the second derivative and found by bisection), an FP32 positivity
+// pre-test and the limiter itself.
 #pragma once
 
 #include "grace_convert.cuh"
@@ -18,9 +20,68 @@ __device__ __forceinline__ double poly(const double *c, int k, double xi)
     return s;
 }
 
+// Minimum over [-1, 1] of p = sum_{i <= 4} c_i phi_i for degree 4, in the arithmetic of T.  The
+// derivative p' = a0 + a1 x + a2 x^2 + a3 x^3 (a0 = c1 - 3/2 c3, a1 = 3 c2 - 15/2 c4, a2 = 15/2 c3,
+// a3 = 35/2 c4) is monotone between consecutive roots of p'' = a1 + 2 a2 x + 3 a3 x^2, so each such
+// piece of [-1, 1] holds at most one stationary point, located by bisection on the sign of p'
+// (ITERS halvings); the minimum is taken over the end points and those points.
+template <typename T, int ITERS, typename Eval>
+__device__ __forceinline__ T quartic_minimum(const T *c, Eval p)
+{
+    const T a0 = c[1] - T(1.5) * c[3], a1 = T(3) * c[2] - T(7.5) * c[4], a2 = T(7.5) * c[3], a3 = T(17.5) * c[4];
+    auto dp = [&](T x) { return a0 + x * (a1 + x * (a2 + x * a3)); };
+    // roots of p'' (a quadratic, 3 a3 x^2 + 2 a2 x + a1) inside (-1, 1), sorted
+    T br[4];
+    int nb = 0;
+    br[nb++] = T(-1);
+    {
+        const T A = T(3) * a3, B = T(2) * a2, C = a1;
+        T r0 = T(2), r1 = T(2);
+        if (A == T(0)) {
+            if (B != T(0)) r0 = -C / B;
+        } else {
+            const T disc = B * B - T(4) * A * C;
+            if (disc >= T(0)) {
+                const T sq = sqrt(disc);
+                const T qq = T(-0.5) * (B + copysign(sq, B));
+                if (qq != T(0)) {
+                    r0 = qq / A;
+                    r1 = C / qq;
+                } else {
+                    r0 = T(0);
+                }
+            }
+        }
+        if (r1 < r0) {
+            const T t = r0;
+            r0 = r1;
+            r1 = t;
+        }
+        if (r0 > T(-1) && r0 < T(1)) br[nb++] = r0;
+        if (r1 > T(-1) && r1 < T(1)) br[nb++] = r1;
+    }
+    br[nb++] = T(1);
+    T m = p(T(-1)) < p(T(1)) ? p(T(-1)) : p(T(1));
+    for (int s = 0; s + 1 < nb; ++s) {
+        T lo = br[s], hi = br[s + 1];
+        const T dlo = dp(lo), dhi = dp(hi);
+        if (!((dlo < T(0) && dhi > T(0)) || (dlo > T(0) && dhi < T(0)))) continue;
+        const bool rising = dlo < T(0);
+        for (int it = 0; it < ITERS; ++it) {
+            const T mid = T(0.5) * (lo + hi);
+            if ((dp(mid) < T(0)) == rising) lo = mid;
+            else hi = mid;
+        }
+        const T v = p(T(0.5) * (lo + hi));
+        if (v < m) m = v;
+    }
+    return m;
+}
+
 // minimum over [-1, 1] of sum_i c_i phi_i: endpoints and interior stationary points
 __device__ __forceinline__ double bin_minimum(const double *c, int k)
 {
+    if (k == 4) return quartic_minimum<double, 64>(c, [&](double x) { return poly(c, k, x); });
     if (k == 0) return c[0];
     double m = fmin(poly(c, k, -1.0), poly(c, k, 1.0));
     if (k == 2 && c[2] != 0.0) {
@@ -55,6 +116,8 @@ __device__ __forceinline__ double bin_minimum(const double *c, int k)
 // clearly positive on [-1, 1]: then the FP64 scaling limiter would leave it
 // untouched (gamma = 1) and can be skipped.  The margin covers FP32 rounding of
 // the evaluation (coefficients summed in |.|).
+__device__ __forceinline__ float bin_minimum_f(const float *c, int k);
+
 __device__ __forceinline__ bool clearly_positive_f(const float *cf, int k)
 {
     float s = 0.f;
@@ -69,7 +132,9 @@ __device__ __forceinline__ bool clearly_positive_f(const float *cf, int k)
             pm += (i & 1) ? -cf[i] : cf[i];
         }
         m = fminf(p1, pm);
-        if (k == 2 && cf[2] != 0.f) {
+        if (k == 4) {
+            m = bin_minimum_f(cf, k);
+        } else if (k == 2 && cf[2] != 0.f) {
             const float xs = -cf[1] / (3.f * cf[2]);
             if (xs > -1.f && xs < 1.f) m = fminf(m, cf[0] + cf[1] * xs + cf[2] * (1.5f * xs * xs - 0.5f));
         } else if (k == 3) {
@@ -114,19 +179,24 @@ __device__ __forceinline__ bool clearly_positive_mixed(double v0, const float *c
     return clearly_positive_f(cf, k);
 }
 
-// sum_i c_i phi_i(x) in FP32 (Legendre polynomials up to degree 3)
+// sum_i c_i phi_i(x) in FP32 (Legendre polynomials up to degree 4)
 __device__ __forceinline__ float poly_f(const float *c, int k, float x)
 {
     float s = c[0];
     if (k >= 1) s += c[1] * x;
     if (k >= 2) s += c[2] * (1.5f * x * x - 0.5f);
     if (k >= 3) s += c[3] * (2.5f * x * x * x - 1.5f * x);
+    if (k >= 4) {
+        const float x2 = x * x;
+        s += c[4] * (4.375f * x2 * x2 - 3.75f * x2 + 0.375f);
+    }
     return s;
 }
 
 // minimum over [-1, 1] in FP32: end points and interior stationary points
 __device__ __forceinline__ float bin_minimum_f(const float *c, int k)
 {
+    if (k == 4) return quartic_minimum<float, 28>(c, [&](float x) { return poly_f(c, k, x); });
     float m = fminf(poly_f(c, k, 1.f), poly_f(c, k, -1.f));
     if (k == 2 && c[2] != 0.f) {
         const float xs = -c[1] / (3.f * c[2]);

@@ -45,7 +45,8 @@ namespace grace {
 
 namespace {
 
-constexpr int kB = kKMax + 1;
+constexpr int kNcKMax = 3;          // per-cell-kernel groups: k <= 3 (entry layouts below)
+constexpr int kB = kNcKMax + 1;
 
 struct NcEntry {
     int r;              // functional

@@ -1156,7 +1156,7 @@ grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, Tc
 {
     const DevGroup &g = G.dg;
     if (g.k > kKMax) {
-        set_error("tensor-core tiles need k <= 3");
+        set_error("tensor-core tiles need k <= 4");
         return GRACE_ERR_UNSUPPORTED;
     }
     const int P_ = g.P, R = g.R, K1 = g.K1;
@@ -1239,7 +1239,7 @@ grace_status build_vjp_tiles(Group &G, int prec, cudaStream_t st)
 {
     const DevGroup &g = G.dg;
     if (g.k > kKMax) {
-        set_error("tensor-core tiles need k <= 3");
+        set_error("tensor-core tiles need k <= 4");
         return GRACE_ERR_UNSUPPORTED;
     }
     const int P_ = g.P, R = g.R, K1 = g.K1;

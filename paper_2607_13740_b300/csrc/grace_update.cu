@@ -541,7 +541,9 @@ inline int warp_blocks(int n_cells) { return (int)(((long long)n_cells * 32 + 25
 cudaError_t launch_update(const DevGroup &g, const UpdateArgs &a, int n_cells, cudaStream_t st)
 {
     if (!a.F) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)8 * g.P * sizeof(double);
+    const size_t smem = (size_t)8 * g.P * sizeof(double);   // one row per warp (P > 768: above 48 KB)
+    cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     update_kernel<<<warp_blocks(n_cells), 256, smem, st>>>(g, a, n_cells);
     return cudaGetLastError();
 }
@@ -695,8 +697,10 @@ cudaError_t launch_limit(const DevGroup &g, double *d_g, int n_cells, unsigned c
         a.opA_kofs = opA_kofs;
         return launch_update_mode<MODE_LIMIT, false, false>(g, a, n_cells, st);
     }
-    limit_kernel<<<warp_blocks(n_cells), 256, (size_t)8 * g.P * sizeof(double), st>>>(g, d_g, n_cells, flags, opA,
-                                                                                       opA_prec, opA_kpad);
+    const size_t smem = (size_t)8 * g.P * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(limit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    limit_kernel<<<warp_blocks(n_cells), 256, smem, st>>>(g, d_g, n_cells, flags, opA, opA_prec, opA_kpad);
     return cudaGetLastError();
 }
 

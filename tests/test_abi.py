@@ -58,9 +58,14 @@ def test_setup_rejects_invalid_groups(lib, field, value):
 
 
 def test_setup_reports_unsupported_order(lib):
-    d = grace.group_desc(W.additive_spec(8, 4))
+    """k <= 4 (the limiter's bin minimum: closed form to k = 3, bracketed for k = 4); per-cell
+    kernel groups k <= 3 (node-space entry layout)."""
+    d = grace.group_desc(W.additive_spec(8, 5))
     st, _ = _setup(lib, d)
     assert st == 5
+    d = grace.group_desc(W.disk_spec(n_bins=8, order_k=4))
+    st, _ = _setup(lib, d)
+    assert st == 1
 
 
 def test_setup_rejects_missing_kernels_and_bad_power_law(lib):

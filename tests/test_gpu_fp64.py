@@ -33,6 +33,8 @@ RHS_SPECS = {
     "delta_breakage": W.GroupSpec(8, 2, 1e-3, 1e3, 0, W.COAG_NONE, (), W.FRAG_MULT, (0.5,),
                                   W.BREAK_COAG_DELTA),
     "quad_q6": W.additive_spec(8, 2, 1e-3, 1e4).replace(quad_q=6),
+    "const_noncons_k4": W.constant_kernel_spec(12, 4, W.FLUX_NONCONSERVATIVE, 1e-3, 1e15),
+    "toy_remnant_k4": W.coupled_toy_spec(8, 4, flux_mode=0),
 }
 
 
@@ -83,7 +85,7 @@ def test_projection_and_mass_parity():
     np.testing.assert_allclose(m, o.mass(go), rtol=1e-13)
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_limiter_parity(k):
     spec = W.GroupSpec(30, k, 1e-2, 1e2, 0, W.COAG_CONST, (1.0,))
     rng = np.random.default_rng(200 + k)
@@ -201,3 +203,37 @@ def test_errors_surface_as_exceptions():
         b.rhs(g, precision=grace.TF32)      # tensor-core tiles were not requested
     with pytest.raises(grace.GraceError):
         b.rhs(g.float())                    # wrong dtype
+
+
+def test_rhs_parity_large_coefficient_count():
+    """N = 170 bins of degree 4 (P = 850 coefficients per cell): the FP64 contraction stages 8 cells
+    per warp (a 32-cell tile of coefficients would not fit in shared memory) and combines the four
+    lanes of a cell with shuffles; same 1e-12 bar against the oracle."""
+    spec = W.constant_kernel_spec(170, 4, W.FLUX_NONCONSERVATIVE, 1e-3, 1e15)
+    err = _rhs_err(spec, 11, seed=104)
+    assert err.max() <= 1e-12, f"max scaled error {err.max():.3e}"
+
+
+def test_k4_trajectory_with_limiter():
+    """Degree 4 over 20 steps with the limiter (bin minimum bracketed between the roots of the
+    second derivative on the GPU, by a scan and bisection in the oracle): trajectory bars as above,
+    status bits equal."""
+    spec = W.constant_kernel_spec(16, 4, W.FLUX_CONSERVATIVE, 1e-3, 1e6)
+    n = 24
+    rng = np.random.default_rng(105)
+    g = np.zeros((n, 16, 5))
+    g[:, :, 0] = 10.0 ** rng.uniform(-2, 0, (n, 16))
+    g[:, :, 1:] = g[:, :, :1] * rng.uniform(-0.8, 0.8, (n, 16, 4)) / np.arange(1, 5)
+    g = g.reshape(n, -1)
+    ctx = grace.Context([spec])
+    b = ctx.batch(n)
+    gt = torch.as_tensor(g, device=DEV)
+    dt = torch.full((n,), 2e-2, dtype=torch.float64, device=DEV)
+    flags = torch.zeros(n, dtype=torch.uint8, device=DEV)
+    b.step(gt, dt, 20, flags=flags)
+    o = oracle.Oracle(spec)
+    go, _, fo = o.step(g, 2e-2, 20)
+    rel, l1 = _trajectory_check(spec, gt.cpu().numpy(), go, o.edges())
+    assert rel <= 1e-10 and l1 <= 1e-12, (rel, l1)
+    np.testing.assert_array_equal(flags.cpu().numpy(), fo)
+    assert (fo & grace.FLAG_LIMITED).any()

@@ -31,6 +31,7 @@ SPECS = {
     "const_noncons_k1": W.constant_kernel_spec(16, 1, W.FLUX_NONCONSERVATIVE, 1e-4, 1e6),
     "k0": W.additive_spec(20, 0, 1e-3, 1e5),
     "k3": W.GroupSpec(12, 3, 1e-2, 1e4, 0, W.COAG_ADD, (1.0,)),
+    "k4": W.GroupSpec(12, 4, 1e-2, 1e4, 0, W.COAG_ADD, (1.0,)),
     "pure_frag": W.pure_fragmentation_spec(10, 2, 1e-6, 1e3),
     "toy_remnant": W.coupled_toy_spec(10, 2, flux_mode=0),
 }

@@ -362,13 +362,20 @@ def run_disk(args):
 
 
 def run_adjoint(args):
-    """Adjoint workload: 4,096 cells of the coupled coagulation-fragmentation model (N = 40,
-    k = 2, conservative), 200 SSP-RK3 steps with a checkpoint every 10; gradient of the final
-    mass in the top 10 bins with respect to the initial coefficients, v_frag and the fragment
-    exponent.  Times grace_adjoint in the requested form (default bf16x3) next to the FP64
-    adjoint and the forward steps; one JSON line."""
+    """Adjoint workload: 4,096 cells of the disk physics (ballistic-turbulent kernels, fragmentation
+    ramp, power-law fragments up to the larger collider plus the remnant) with one shared
+    alpha_turb = 1e-3 on an N = 40, k = 2 grid of grain radii 1e-4 .. 1e2 cm; per-cell MRN initial
+    states scaled by A ~ lognormal(0, 0.5); 200 SSP-RK3 steps with a checkpoint every 10; loss J =
+    sum over cells of the final mass of grains above a radius (the exact polynomial integral of g
+    above the grain mass of that radius; default 100 um: with alpha_turb = 1e-3 and v_frag = 1 m/s
+    the fragmentation barrier holds the distribution near 30-90 um, and the mass above 1 mm stays
+    ~1e-80 of the total, below the FP32 range of the tensor forms); gradients with respect to the
+    initial coefficients, v_frag and the fragment exponent.
+    Times grace_adjoint in the requested form (default bf16x3) next to the FP64 adjoint and the
+    forward steps; one JSON line."""
     import numpy as np
     import torch
+    from numpy.polynomial import legendre as npl
     from paper_2607_13740_b300 import grace, workloads as W
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -377,20 +384,38 @@ def run_adjoint(args):
     fname = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[form]
     n = args.cells or 4096
     steps, ckpt = args.steps or 200, 10
-    spec = W.coupled_toy_spec(40, 2, flux_mode=W.FLUX_CONSERVATIVE)
+    spec = W.disk_spec(n_bins=40, order_k=2, cell_alpha=0, alpha=1e-3)
+    _, _, ic1 = W.disk_batch(n_cells=1, n_bins=40, order_k=2)
     rng = np.random.default_rng(1005)
-    ic = np.zeros((n, 4))
-    ic[:, 0] = rng.lognormal(0.0, 0.5, n)
-    ic[:, 1] = np.exp(rng.uniform(np.log(1e-3), np.log(1.0), n))
+    ic = np.repeat(ic1, n, axis=0)
+    ic[:, 0] *= rng.lognormal(0.0, 0.5, n)
     ctx = grace.Context([spec], local, precisions=(grace.FP64, form) if form != grace.FP64 else (grace.FP64,))
-    ctx.param_grad_setup([9, 16])                 # frag_p[1] = v_frag, break_p[0] = fragment exponent
+    # v_frag enters both ballistic kernels (coag_p[4], frag_p[4]); break_p[0] is the fragment exponent
+    ctx.param_grad_setup([4, 12, 16])
     b = ctx.batch(n)
-    g0 = b.project(W.IC_EXP, ic)
-    dt = torch.full((n,), 0.2, dtype=torch.float64, device=dev)   # stable over 200 steps (oracle-checked)
+    g0 = b.project(W.IC_POWERLAW, ic)
+    # time step: half the positivity bound at t = 0 per cell (as the disk workload), held fixed
+    L = b.rhs(g0).reshape(n, 40, 3)[:, :, 0]
+    m = g0.reshape(n, 40, 3)[:, :, 0]
+    ratio = torch.where(L < 0, m / (-L), torch.full_like(m, float("inf")))
+    dt = (0.5 * ratio.amin(dim=1)).contiguous()
+    dt = torch.where(torch.isfinite(dt), dt, torch.ones_like(dt))
+    # lambda_T = dJ/dg_T: J = int_{x_cut}^{x_max} g dx, x_cut the mass of a 0.1 cm grain
     edges = spec.x_min * (spec.x_max / spec.x_min) ** (np.arange(41) / 40)
-    lamT = torch.zeros(n, 40, 3, dtype=torch.float64, device=dev)
-    lamT[:, 30:, 0] = torch.as_tensor(np.diff(edges)[30:], device=dev)     # J = mass in bins 30..39
-    lamT = lamT.reshape(n, -1).contiguous()
+    edges[0], edges[-1] = spec.x_min, spec.x_max
+    x_cut = W.grain_mass(args.loss_radius)
+    lam = np.zeros((40, 3))
+    for j in range(40):
+        a_, b_ = edges[j], edges[j + 1]
+        if b_ <= x_cut:
+            continue
+        xi0 = -1.0 if a_ >= x_cut else 2.0 * (x_cut - 0.5 * (a_ + b_)) / (b_ - a_)
+        for i in range(3):
+            c = np.zeros(i + 1)
+            c[i] = 1.0
+            anti = npl.legint(c)
+            lam[j, i] = 0.5 * (b_ - a_) * (npl.legval(1.0, anti) - npl.legval(xi0, anti))
+    lamT = torch.as_tensor(np.tile(lam.reshape(-1), (n, 1)), device=dev).contiguous()
 
     def timed(fn):
         fn()
@@ -430,17 +455,23 @@ def run_adjoint(args):
             "lambda0_max_rel_err_vs_fp64": ((lam_s - lam64).abs().amax(dim=1) /
                                             lam64.abs().amax(dim=1).clamp_min(1e-300)).max().item(),
             "dtheta_max_rel_err_vs_fp64": ((dth_s - dth64).abs().amax(dim=0) /
-                                           dth64.abs().amax(dim=0).clamp_min(1e-300)).max().item()}
+                                           dth64.abs().amax(dim=0).clamp_min(1e-300)).max().item(),
+            "dtheta_sum_fp64": dth64.sum(dim=0).tolist(), "dtheta_sum_form": dth_s.sum(dim=0).tolist()}
     line = {
-        "metric": "adjoint cell-steps/s (4,096 cells, N=40, k=2, coag+frag, 200 steps, ckpt 10)",
+        "metric": "adjoint cell-steps/s (4,096 cells, N=40, k=2, disk physics one alpha, 200 steps, ckpt 10)",
         "value": n * steps / (ms_adj / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 1,
         "ms_per_step": ms_adj / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[fname], "data": "synthetic",
-        "config": {"workload": f"adjoint_{n}cells_N40_k2", "cells": n, "form": fname, "checkpoint_every": ckpt,
-                   "loss": "final mass in bins 30..39", "params": ["v_frag", "fragment exponent"],
-                   "ic": "A x exp(-x/x0), A ~ lognormal(0, 0.5), x0 ~ loguniform[1e-3, 1]",
-                   "dt": "0.2 fixed (stable over 200 steps)"},
+        "config": {"workload": f"adjoint_{n}cells_N40_k2_disk", "cells": n, "form": fname, "checkpoint_every": ckpt,
+                   "physics": "ballistic-turbulent kernels, alpha_turb = 1e-3 shared, ramp over 0.8..1.2 v_frag, "
+                              "power law -11/6 up to the larger collider + remnant",
+                   "loss": f"final mass of grains above radius {args.loss_radius} cm (exact polynomial integral)",
+                   "params": ["v_frag (coag_p[4] + frag_p[4])", "fragment exponent"],
+                   "ic": "MRN g ~ x^(-5/6) over 1..10 um, scaled by A ~ lognormal(0, 0.5)",
+                   "dt": "0.5 x positivity bound at t = 0 per cell"},
         "finite": bool(torch.isfinite(lam0).all().item() and torch.isfinite(dth).all().item()),
+        "J": float((lamT * b.step(g0.clone(), dt, steps, grace.FP64 if form == grace.FP64 else form)).sum()),
+        "dJ_dtheta": {"v_frag": float(dth[:, 0].sum() + dth[:, 1].sum()), "fragment_exponent": float(dth[:, 2].sum())},
         "clocks": sampler.summary(), **res,
     }
     print(json.dumps(line), flush=True)
@@ -636,6 +667,8 @@ def main():
     ap.add_argument("--forms", default=None,
                     help="comma-separated subset of fp64,tf32,bf16x3 to time (default: all built)")
     ap.add_argument("--tau", type=float, default=None, help="eoc workload: end time (default 3e12)")
+    ap.add_argument("--loss-radius", type=float, default=0.01,
+                    help="adjoint workload: the loss is the final mass of grains above this radius (cm)")
     ap.add_argument("--eoc-c", type=float, default=0.02, help="eoc workload: dt = c (2 + tau)")
     ap.add_argument("--eoc-n", default=None, help="eoc workload: comma-separated bin counts")
     ap.add_argument("--eoc-k", default=None, help="eoc workload: comma-separated degrees")

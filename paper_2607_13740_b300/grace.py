@@ -418,29 +418,37 @@ def _make_step_function():
     import torch
 
     class StepFunction(torch.autograd.Function):
-        """g_T = n_steps SSP-RK3 steps (with the limiter) of the batch from g0.
-        backward runs the checkpointed discrete adjoint (FP64)."""
+        """g_T = n_steps SSP-RK3 steps (with the limiter) of the batch from g0 in the given form.
+        backward runs the checkpointed discrete adjoint (grace_adjoint) in the same form: the
+        gradient with respect to g0 and, when theta is given, with respect to the kernel and
+        breakage parameters of param_grad_setup (summed over the cells)."""
 
         @staticmethod
-        def forward(ctx, g0, batch, dt, n_steps, ckpt_every):
+        def forward(ctx, g0, theta, batch, dt, n_steps, ckpt_every, precision):
             g = g0.detach().clone().contiguous()
-            batch.step(g, dt, n_steps, FP64)
-            ctx.batch, ctx.dt, ctx.n_steps, ctx.ckpt = batch, dt, n_steps, ckpt_every
+            batch.step(g, dt, n_steps, precision)
+            ctx.batch, ctx.dt, ctx.n_steps, ctx.ckpt, ctx.prec = batch, dt, n_steps, ckpt_every, precision
+            ctx.want_theta = theta is not None
             ctx.save_for_backward(g0.detach())
             return g
 
         @staticmethod
         def backward(ctx, grad_out):
             (g0,) = ctx.saved_tensors
-            lam0, _ = ctx.batch.adjoint(g0.contiguous(), ctx.dt, ctx.n_steps, grad_out.contiguous(), ctx.ckpt)
-            return lam0, None, None, None, None
+            lam0, dth = ctx.batch.adjoint(g0.contiguous(), ctx.dt, ctx.n_steps, grad_out.contiguous(), ctx.ckpt,
+                                          param_grads=ctx.want_theta, precision=ctx.prec)
+            gtheta = dth.sum(dim=0) if ctx.want_theta else None
+            return lam0, gtheta, None, None, None, None, None
 
     return StepFunction
 
 
-def step_autograd(g0, batch, dt, n_steps: int, ckpt_every: int = 10):
-    """Differentiable wrapper of Batch.step (FP64) for torch.autograd."""
+def step_autograd(g0, batch, dt, n_steps: int, ckpt_every: int = 10, precision: int = FP64, theta=None):
+    """Differentiable wrapper of Batch.step for torch.autograd in any form (FP64, TF32, BF16X3).
+    theta: None, or a tensor with one entry per parameter of Context.param_grad_setup (its values
+    are not read: the parameters are those of the context); its gradient is dJ/dtheta summed over
+    the cells."""
     global StepFunction
     if "StepFunction" not in globals():
         StepFunction = _make_step_function()
-    return StepFunction.apply(g0, batch, dt, n_steps, ckpt_every)
+    return StepFunction.apply(g0, theta, batch, dt, n_steps, ckpt_every, int(precision))

@@ -151,6 +151,68 @@ def test_autograd_function_gradcheck():
     assert torch.autograd.gradcheck(f, (g0,), eps=1e-6, atol=1e-8, rtol=1e-6)
 
 
+def test_autograd_parameter_gradients_in_every_form():
+    """step_autograd with theta: the gradient reaching theta is grace_adjoint's dJ/dtheta summed over
+    the cells (FP64), and the BF16x3 form's gradients (g0 and theta) stay within the trajectory
+    bar of the FP64 ones; J = <lambda_T, g_T> through torch.autograd."""
+    spec = W.coupled_toy_spec(10, 2, flux_mode=0)
+    n, steps, dt = 3, 8, 0.05
+    o, g0, rng = _traj_setup(spec, n, 611)
+    lamT = torch.as_tensor(rng.normal(size=g0.shape), device=DEV)
+    ctx = grace.Context([spec], 0, precisions=(grace.FP64, grace.BF16X3))
+    ctx.param_grad_setup([9, 16])                 # frag_p[1] = v_f, break_p[0] = alpha
+    b = ctx.batch(n)
+    dtt = torch.full((n,), dt, dtype=torch.float64, device=DEV)
+    grads = {}
+    for form in (grace.FP64, grace.BF16X3):
+        gin = torch.as_tensor(g0, device=DEV).clone().requires_grad_(True)
+        theta = torch.zeros(2, dtype=torch.float64, device=DEV, requires_grad=True)
+        gT = grace.step_autograd(gin, b, dtt, steps, 4, precision=form, theta=theta)
+        (gT * lamT).sum().backward()
+        grads[form] = (gin.grad.cpu().numpy(), theta.grad.cpu().numpy())
+    _, dth = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, lamT, 4, param_grads=True)
+    np.testing.assert_allclose(grads[grace.FP64][1], dth.sum(dim=0).cpu().numpy(), rtol=1e-12)
+    for a, r in zip(grads[grace.BF16X3], grads[grace.FP64]):
+        assert np.abs(a - r).max() <= 36 * 5e-5 * np.abs(r).max(), (np.abs(a - r).max(), np.abs(r).max())
+
+
+def test_rosenbrock_step_with_gpu_jvps():
+    """A linearly implicit (Rosenbrock-Euler) step (I - dt J) k = dt L(g), g+ = g + k, solved by GMRES
+    whose matrix-vector products are the GPU's FP64 JVPs, against the dense solve with the oracle's
+    exact Jacobian (polarization of the quadratic L, column by column); dt 20x the explicit
+    positivity bound (a stiff step for the explicit scheme)."""
+    from scipy.sparse.linalg import LinearOperator, gmres
+    spec = W.additive_spec(12, 2, 1e-3, 1e4)
+    o = oracle.Oracle(spec)
+    g = o.project(W.IC_EXP, [[1.0, 0.5, 0, 0]])[0]
+    P = spec.n_coef
+    L0, _ = o.rhs(g[None])
+    L0 = L0[0]
+    means, Lm = g.reshape(-1, 3)[:, 0], L0.reshape(-1, 3)[:, 0]
+    dt = 20.0 * (means[Lm < 0] / -Lm[Lm < 0]).min()
+    J = np.zeros((P, P))
+    for q in range(P):
+        e = np.zeros(P)
+        e[q] = 1.0
+        Lp, _ = o.rhs((g + e)[None])
+        Lm_, _ = o.rhs((g - e)[None])
+        J[:, q] = 0.5 * (Lp[0] - Lm_[0])
+    k_ref = np.linalg.solve(np.eye(P) - dt * J, dt * L0)
+    ctx = grace.Context([spec])
+    b = ctx.batch(1)
+    gd = torch.as_tensor(g[None], device=DEV)
+
+    def matvec(v):
+        Jv = b.jvp(gd, torch.as_tensor(np.asarray(v, dtype=np.float64).reshape(1, P), device=DEV))
+        return np.asarray(v).reshape(P) - dt * Jv.cpu().numpy().reshape(P)
+
+    rhs = dt * b.rhs(gd).cpu().numpy().reshape(P)
+    k_gpu, info = gmres(LinearOperator((P, P), matvec=matvec, dtype=np.float64), rhs, rtol=1e-14, atol=0.0,
+                        restart=P, maxiter=10 * P)
+    assert info == 0
+    assert np.abs(k_gpu - k_ref).max() <= 1e-9 * np.abs(k_ref).max()
+
+
 # ------------------------------------------------------------------ tensor forms
 TOL_RHS = {grace.TF32: 2e-3, grace.BF16X3: 5e-5}
 RANGE_FLOOR = 1e-24

@@ -230,6 +230,22 @@ GRACE_API grace_status grace_batch_set_graph(grace_batch *batch, int enable);
    graph capture).  enable = 0 restores the per-group launches.  Same results bit for bit. */
 GRACE_API grace_status grace_batch_set_grouped(grace_batch *batch, int enable);
 
+/* Operator-split coupling to a hydrodynamics code (Sec. 5.2): advances every cell by its
+   own interval dt_hydro[c] (device [n_cells]) in sub-steps sized by the eq. (dt)
+   positivity bound.  The FP64 RHS at the start gives each cell's bound
+   B_c = min over bins losing mass (L_j^0 < 0) of g_j^0 / |L_j^0| and its count
+   n_c = ceil(dt_hydro_c / (cfl B_c)); the batch then takes N = min(max_c n_c,
+   max_substeps) steps of grace_step in which cell c moves by dt_hydro_c / N (<= cfl B_c
+   unless max_substeps capped N).  *n_sub (host, nullable) receives N.  cfl > 0, e.g. 0.5.
+   Status bit 8 reports cells whose bound tightened below the step during the interval.
+   Allocates a workspace on the first call; synchronises once per call (to read N), so it
+   is not captured in a CUDA graph.  Errors: GRACE_ERR_ARG for a null argument, cfl <= 0 or
+   max_substeps < 1, otherwise those of grace_rhs and grace_step.  The paper gives no
+   algorithm for the coupling; this sub-cycling is the library's. */
+GRACE_API grace_status grace_substep(grace_batch *batch, double *g, const double *dt_hydro, double cfl,
+                                     int max_substeps, int precision, double *mass, unsigned char *flags,
+                                     int *n_sub);
+
 /* M_1 = sum_j h_j g_j^0 per cell (Sec. 4.1).  g, mass: device. */
 GRACE_API grace_status grace_mass(grace_batch *batch, const double *g, double *mass);
 

@@ -52,6 +52,7 @@ def lib():
         L.orc_plant_mass_leak.argtypes = [ctypes.c_double]
         L.orc_plant_mass_leak.restype = None
         L.orc_drift_tol.argtypes = [ctypes.c_int]
+        L.orc_substep_counts.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
         L.orc_drift_tol.restype = ctypes.c_double
         L.orc_rhs_batch.argtypes = [P, ctypes.c_int, _D, _D, _D, ctypes.c_int]
         L.orc_limit_batch.argtypes = [P, ctypes.c_int, _D, _U8]
@@ -177,6 +178,25 @@ class Oracle:
         J = np.zeros(self.spec.order_k + 1)
         _check(lib().orc_appB_pair(self._pp, int(j), float(u), float(v), _p(J)), "appB_pair")
         return J
+
+    def substep_counts(self, g, dt_hydro, cfl: float):
+        """Per-cell sub-step counts ceil(dt_hydro / (cfl B)) of the operator-split coupling, B the eq. (dt)
+        bound of the state (Sec. 5.2)."""
+        g = _f64(g).reshape(-1, self.P)
+        dt = _f64(np.broadcast_to(np.asarray(dt_hydro, dtype=np.float64), (g.shape[0],)))
+        out = np.zeros(g.shape[0], dtype=np.int32)
+        _check(lib().orc_substep_counts(self._pp, g.shape[0], _p(g), _p(dt), float(cfl),
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "substep_counts")
+        return out
+
+    def substep(self, g, dt_hydro, cfl: float, max_substeps: int, threads: int = 0):
+        """The batch's operator-split step: N = min(max counts, max_substeps) SSP-RK3 steps of
+        dt_hydro / N per cell.  Returns (g, mass, flags, N)."""
+        counts = self.substep_counts(g, dt_hydro, cfl)
+        N = int(max(1, min(int(counts.max()), int(max_substeps))))
+        dt = np.broadcast_to(np.asarray(dt_hydro, dtype=np.float64), (counts.size,)) / N
+        g2, m, f = self.step(g, dt, N, threads=threads)
+        return g2, m, f, N
 
     def rhs(self, g, threads: int = 0):
         g = _f64(g).reshape(-1, self.P)

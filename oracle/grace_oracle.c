@@ -956,6 +956,37 @@ int orc_step_batch(const orc_params *p, int n_cells, double *g, const double *dt
     return bad ? -2 : 0;
 }
 
+/* Sub-step counts of the operator-split coupling (Sec. 5.2, the library's sub-cycling): for each
+   cell the eq. (dt) bound B = min over bins losing mass (L_j^0 < 0) of g_j^0 / |L_j^0| of its state,
+   and n = ceil(dt_hydro / (cfl B)), at least 1 (1 when no bin loses mass); counts[cell] = n. */
+int orc_substep_counts(const orc_params *p, int n_cells, const double *g, const double *dt_hydro, double cfl,
+                       int *counts)
+{
+    octx c;
+    if (ctx_init(&c, p)) return -1;
+    const int P = c.P, K1 = c.k + 1;
+    double *L = (double *)malloc(sizeof(double) * (size_t)P);
+    if (!L) { ctx_free(&c); return -2; }
+    for (int cell = 0; cell < n_cells; ++cell) {
+        const double *gc = g + (size_t)cell * P;
+        rhs_one(&c, gc, L, NULL);
+        double B = INFINITY;
+        for (int j = 0; j < c.N; ++j)
+            if (L[(size_t)j * K1] < 0.0) {
+                const double r = gc[(size_t)j * K1] / -L[(size_t)j * K1];
+                if (r < B) B = r;
+            }
+        const double want = dt_hydro[cell] / (cfl * B);
+        int n = 1;
+        if (want > 1.0) n = want < 1073741824.0 ? (int)ceil(want) : 1073741824;
+        else if (!(want >= 0.0)) n = 1073741824;
+        counts[cell] = n;
+    }
+    free(L);
+    ctx_free(&c);
+    return 0;
+}
+
 /* Plants a non-conservative update in every later step (tests of the mass-drift bit only);
    0 removes it. */
 void orc_plant_mass_leak(double leak) { planted_leak = leak; }

@@ -174,12 +174,15 @@ struct grace_batch {
     double *d_drift = nullptr;     // M_1 before / after a flagged grace_step [2][n] + per-cell
                                    // conservative-group bytes [n], built on the first flagged call
     unsigned *d_flag_or = nullptr; // grace_flags_check's reduction word
+    void *hydro = nullptr;         // grace_substep workspace (grace_hydro.cu), built on first use
 };
 
 namespace grace {
 
 // frees the staging of grace_step_host (waits for its copies first)
 void free_host_io(grace_batch *b);
+// frees the workspace of grace_substep
+void free_hydro(grace_batch *b);
 
 // thread-local error detail
 void set_error(const std::string &msg);

@@ -51,7 +51,7 @@ def exported_symbols():
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_set_grouped", "grace_batch_destroy",
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
             "grace_step_host", "grace_step_host_wait", "grace_flags_check",
-            "grace_test_arm_wait_timeout", "grace_probe_mma"]
+            "grace_test_arm_wait_timeout", "grace_probe_mma", "grace_substep"]
 
 
 def load(path: str | None = None):
@@ -91,6 +91,7 @@ def load(path: str | None = None):
     L.grace_adjoint.argtypes = [_VP, _VP, _VP, S, S, _VP, _VP, _VP, S]
     L.grace_probe_rates.argtypes = [S, ctypes.POINTER(ctypes.c_double)]
     L.grace_probe_mma.argtypes = [S, S, S, ctypes.POINTER(ctypes.c_double)]
+    L.grace_substep.argtypes = [_VP, _VP, _VP, ctypes.c_double, S, S, _VP, _VP, ctypes.POINTER(S)]
     L.grace_batch_set_graph.argtypes = [_VP, S]
     L.grace_batch_set_grouped.argtypes = [_VP, S]
     L.grace_step_host.argtypes = [_VP, _VP, _VP, _VP, S, S, _VP, _VP]
@@ -288,6 +289,17 @@ class Batch:
         _check(load().grace_step(self._h, _ptr(g), _ptr(dt), int(n_steps), int(precision),
                                  _ptr(mass), _ptr(flags)), "grace_step")
         return g
+
+    def substep(self, g, dt_hydro, cfl: float = 0.5, max_substeps: int = 1000, precision: int = FP64, mass=None,
+                flags=None) -> int:
+        """Advances every cell by its own dt_hydro (float64 CUDA tensor [n_cells]) in sub-steps sized by
+        the eq. (dt) bound (grace_substep); in place on g; returns the number of sub-steps taken."""
+        self._check_state(g)
+        nsub = ctypes.c_int()
+        self.ctx.set_stream()
+        _check(load().grace_substep(self._h, _ptr(g), _ptr(dt_hydro), float(cfl), int(max_substeps), int(precision),
+                                    _ptr(mass), _ptr(flags), ctypes.byref(nsub)), "grace_substep")
+        return nsub.value
 
     def _check_host(self, t, numel, dtype, what):
         import torch

@@ -260,3 +260,37 @@ def test_mass_drift_bit_positive_case():
         oracle.plant_mass_leak(0.0)
     _, _, f = o.step(g, 1e-3, 3)
     assert np.all((f & 16) == 0)
+
+
+def test_substep_counts_follow_the_positivity_bound():
+    """Sec. 5.2 coupling: the sub-step count of a cell is the smallest n with dt_hydro / n <= cfl B,
+    B the eq. (dt) bound.  Pinned by what the bound means: a forward-Euler update of the state with
+    step B takes the limiting bin's mean exactly to zero and keeps every other mean >= 0, and the
+    count falls by one when dt_hydro shrinks just below (n - 1) cfl B."""
+    spec = SPECS["add"]
+    o = oracle.Oracle(spec)
+    g = o.project(W.IC_EXP, [[1.0, 1.0, 0, 0], [3.0, 0.2, 0, 0]])
+    L, _ = o.rhs(g)
+    K1 = spec.order_k + 1
+    for c in range(2):
+        m, L0 = g[c].reshape(-1, K1)[:, 0], L[c].reshape(-1, K1)[:, 0]
+        # the count for dt_hydro = 1: find B from the counts at growing dt, without retyping the formula
+        n1 = o.substep_counts(g[c:c + 1], 1.0, 0.5)[0]
+        assert n1 >= 1
+        # bracket B: the largest dt with a single sub-step at cfl = 1
+        lo, hi = 0.0, 1.0
+        while o.substep_counts(g[c:c + 1], hi, 1.0)[0] == 1:
+            hi *= 2.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if o.substep_counts(g[c:c + 1], mid, 1.0)[0] == 1:
+                lo = mid
+            else:
+                hi = mid
+        B = lo
+        euler = m + B * L0
+        assert euler.min() >= -1e-12 * m.max()
+        assert np.isclose(np.abs(euler[L0 < 0]).min(), 0.0, atol=1e-12 * m.max())
+        n = o.substep_counts(g[c:c + 1], 7.3 * B, 0.5)[0]
+        assert n == 15
+        assert o.substep_counts(g[c:c + 1], 6.999 * B, 0.5)[0] == 14

@@ -230,7 +230,27 @@ GRACE_API grace_status grace_batch_set_graph(grace_batch *batch, int enable);
    graph capture).  enable = 0 restores the per-group launches.  Same results bit for bit. */
 GRACE_API grace_status grace_batch_set_grouped(grace_batch *batch, int enable);
 
-/* Operator-split coupling to a hydrodynamics code (Sec. 5.2): advances every cell by its
+/* Species of mixed grains (Sec. 5.3): grains are mixtures of n_species (1..4) constituent
+   species whose partial mass densities g_s share the mass grid, g = sum_s g_s.  Every flux
+   integral carries the share of the products of its outer collider, so a species' rate is
+   L_s = L[g_s; g]: the flux integrals of eqs. (Fcoagtrun), (Ffragtrun) and App. B with g_s in the
+   outer collider's slot and g in its partner's (the library's reading; the paper states no
+   equations).  sum_s L_s = L[g], and each species' mass is conserved by conservative fluxes.
+   gs, Ls: device, [n_species][n_cells][P] (species-major, each species a packed state of the
+   batch).  FP64 only; batches of one group in caller order without per-cell kernel parameters
+   (GRACE_ERR_UNSUPPORTED otherwise).  The first call allocates a workspace (synchronises). */
+GRACE_API grace_status grace_rhs_species(grace_batch *batch, int n_species, const double *gs, double *Ls);
+
+/* n_steps SSP-RK3 steps (eq. RK3) of the species, in place on gs ([n_species][n_cells][P],
+   device): every stage forms the total of its input, then each species' rate and stage update;
+   the scaling limiter acts on each species (once per step, as grace_step).  mass (device
+   [n_species][n_cells] or NULL) receives each species' M_1 after the last step; flags (device
+   [n_cells] or NULL) the OR of the status bits of the cell's species, the mass-drift bit from the
+   cell's total M_1.  FP64; the restrictions and workspace of grace_rhs_species. */
+GRACE_API grace_status grace_step_species(grace_batch *batch, int n_species, double *gs, const double *dt,
+                                          int n_steps, double *mass, unsigned char *flags);
+
+/* Operator-split coupling to a hydrodynamics code (Sec. 5.2)/* Operator-split coupling to a hydrodynamics code (Sec. 5.2): advances every cell by its
    own interval dt_hydro[c] (device [n_cells]) in sub-steps sized by the eq. (dt)
    positivity bound.  The FP64 RHS at the start gives each cell's bound
    B_c = min over bins losing mass (L_j^0 < 0) of g_j^0 / |L_j^0| and its count

@@ -52,6 +52,8 @@ def lib():
         L.orc_plant_mass_leak.argtypes = [ctypes.c_double]
         L.orc_plant_mass_leak.restype = None
         L.orc_drift_tol.argtypes = [ctypes.c_int]
+        L.orc_rhs_species_batch.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D, _D]
+        L.orc_step_species_batch.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int, _D, _U8]
         L.orc_substep_counts.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
         L.orc_drift_tol.restype = ctypes.c_double
         L.orc_rhs_batch.argtypes = [P, ctypes.c_int, _D, _D, _D, ctypes.c_int]
@@ -178,6 +180,27 @@ class Oracle:
         J = np.zeros(self.spec.order_k + 1)
         _check(lib().orc_appB_pair(self._pp, int(j), float(u), float(v), _p(J)), "appB_pair")
         return J
+
+    def rhs_species(self, gs):
+        """Species of mixed grains (Sec. 5.3): gs [S, n_cells, P] partial mass densities; returns
+        (L_s, S_s) in the same layout, L_s = L[g_s; sum_s g_s] (the species in the outer slot)."""
+        gs = np.ascontiguousarray(gs, dtype=np.float64)
+        S_, n = gs.shape[0], gs.shape[1]
+        L = np.zeros_like(gs)
+        Sc = np.zeros_like(gs)
+        _check(lib().orc_rhs_species_batch(self._pp, n, S_, _p(gs), _p(L), _p(Sc)), "rhs_species")
+        return L, Sc
+
+    def step_species(self, gs, dt, n_steps: int):
+        """n_steps SSP-RK3 steps of the species [S, n_cells, P]; returns (gs, mass [S, n_cells], flags)."""
+        gs = np.ascontiguousarray(gs, dtype=np.float64).copy()
+        S_, n = gs.shape[0], gs.shape[1]
+        dt = _f64(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        mass = np.zeros((S_, n))
+        f = np.zeros(n, dtype=np.uint8)
+        _check(lib().orc_step_species_batch(self._pp, n, S_, _p(gs), _p(dt), int(n_steps), _p(mass),
+                                            f.ctypes.data_as(_U8)), "step_species")
+        return gs, mass, f
 
     def substep_counts(self, g, dt_hydro, cfl: float):
         """Per-cell sub-step counts ceil(dt_hydro / (cfl B)) of the operator-split coupling, B the eq. (dt)

@@ -372,8 +372,8 @@ static double vmax_of(const octx *c, double u)
    bins A and B reduced to the sub-intervals [a_m, b_m] and Q remapped
    nodes each.                                                         */
 /* ------------------------------------------------------------------ */
-static void flux_point(const octx *c, const double *g, double x, int want_coag, int want_frag,
-                       double *F, double *Fabs)
+static void flux_point(const octx *c, const double *go, const double *g, double x, int want_coag,
+                       int want_frag, double *F, double *Fabs)
 {
     const int Q = c->Q;
     const double xmin = c->p.x_min;
@@ -389,7 +389,7 @@ static void flux_point(const octx *c, const double *g, double x, int want_coag, 
             for (int al = 0; al < Q; ++al) {
                 double u = 0.5 * (a + b) + 0.5 * (b - a) * c->s[al];
                 double Wu = 0.5 * (b - a) * c->w[al];
-                double gua, gu = gval(c, g, l, u, &gua);
+                double gua, gu = gval(c, go, l, u, &gua);
                 double lo = x - u + xmin, hi = vmax_of(c, u);
                 if (!(hi > lo)) continue;
                 for (int m = bin_of(c, lo); m < c->N && c->e[m] < hi; ++m) {
@@ -418,7 +418,7 @@ static void flux_point(const octx *c, const double *g, double x, int want_coag, 
             for (int al = 0; al < Q; ++al) {
                 double u = 0.5 * (a + b) + 0.5 * (b - a) * c->s[al];
                 double Wu = 0.5 * (b - a) * c->w[al];
-                double gua, gu = gval(c, g, l, u, &gua);
+                double gua, gu = gval(c, go, l, u, &gua);
                 double lo = xmin, hi = vmax_of(c, u);
                 if (!(hi > lo)) continue;
                 for (int m = 0; m < c->N && c->e[m] < hi; ++m) {
@@ -511,7 +511,7 @@ static void appB_pair(const octx *c, int j, double u, double v, double *J, doubl
    (u, v) quadrature (appB_pair).  The outer (u, v) quadrature runs over full
    bins in u and over the bins of [x_min, v_max(u)] in v.  V[i], Vabs[i] for
    i = 1..k. */
-static void vol_frag_appB(const octx *c, const double *g, int j, double *V, double *Vabs)
+static void vol_frag_appB(const octx *c, const double *go, const double *g, int j, double *V, double *Vabs)
 {
     const int Q = c->Q, k = c->k;
     const double xmin = c->p.x_min;
@@ -521,7 +521,7 @@ static void vol_frag_appB(const octx *c, const double *g, int j, double *V, doub
         for (int al = 0; al < Q; ++al) {
             double u = 0.5 * (a + b) + 0.5 * (b - a) * c->s[al];
             double Wu = 0.5 * (b - a) * c->w[al];
-            double gua, gu = gval(c, g, l, u, &gua);
+            double gua, gu = gval(c, go, l, u, &gua);
             double hi = vmax_of(c, u);
             for (int m = 0; m < c->N && c->e[m] < hi; ++m) {
                 double va = c->e[m] > xmin ? c->e[m] : xmin;
@@ -548,8 +548,12 @@ static void vol_frag_appB(const octx *c, const double *g, int j, double *V, doub
 /* ------------------------------------------------------------------ */
 /* the operator L[g] (eq. evo)                                         */
 /* ------------------------------------------------------------------ */
-/* Fif[j+1] = F(x_{j+1/2}) for j = -1..N-1 (Fif[0] = F(x_{-1/2}) = 0). */
-static void rhs_one(const octx *c, const double *g, double *L, double *S)
+/* Fif[j+1] = F(x_{j+1/2}) for j = -1..N-1 (Fif[0] = F(x_{-1/2}) = 0).
+   go is the distribution of the outer collider of every flux integral (the particle of mass u
+   whose share of the products crosses x), g that of its partner v: go = g gives L[g]; go = g_s,
+   the partial mass density of a species s of grains that are mixtures of species (Sec. 5.3, with
+   g = sum_s g_s), gives the rate of that species' partial mass (reading R24). */
+static void rhs_one_outer(const octx *c, const double *go, const double *g, double *L, double *S)
 {
     const int N = c->N, k = c->k, Q = c->Q;
     double *Fif = (double *)calloc((size_t)(N + 1) * 2, sizeof(double));
@@ -558,7 +562,7 @@ static void rhs_one(const octx *c, const double *g, double *L, double *S)
        conservative mode (Sec. 3.3), so those two are not evaluated */
     int jmax = c->p.flux_mode == 0 ? N - 2 : N - 1;
     for (int j = 0; j <= jmax; ++j)
-        flux_point(c, g, c->e[j + 1], 1, 1, &Fif[j + 1], &Fab[j + 1]);
+        flux_point(c, go, g, c->e[j + 1], 1, 1, &Fif[j + 1], &Fab[j + 1]);
 
     double P[ORC_KMAX + 1], dP[ORC_KMAX + 1];
     int delta = has_remnant_delta(c);
@@ -571,7 +575,7 @@ static void rhs_one(const octx *c, const double *g, double *L, double *S)
             for (int th = 0; th < Q; ++th) {
                 double xt = xc + 0.5 * h * c->s[th];
                 double Ft, Fta;
-                flux_point(c, g, xt, 1, !delta, &Ft, &Fta);
+                flux_point(c, go, g, xt, 1, !delta, &Ft, &Fta);
                 legendre(k, c->s[th], P, dP);
                 for (int i = 1; i <= k; ++i) {
                     V[i] += c->w[th] * dP[i] * Ft;
@@ -580,7 +584,7 @@ static void rhs_one(const octx *c, const double *g, double *L, double *S)
             }
             if (delta) {
                 double Vf[ORC_KMAX + 1], Vfa[ORC_KMAX + 1];
-                vol_frag_appB(c, g, j, Vf, Vfa);
+                vol_frag_appB(c, go, g, j, Vf, Vfa);
                 for (int i = 1; i <= k; ++i) { V[i] += Vf[i]; Va[i] += Vfa[i]; }
             }
         }
@@ -595,6 +599,9 @@ static void rhs_one(const octx *c, const double *g, double *L, double *S)
     }
     free(Fif);
 }
+
+/* the operator L[g] (eq. evo) */
+static void rhs_one(const octx *c, const double *g, double *L, double *S) { rhs_one_outer(c, g, g, L, S); }
 
 /* ------------------------------------------------------------------ */
 /* scaling limiter (eqs. recon, gamma), minimum computed analytically   */
@@ -863,7 +870,7 @@ int orc_flux_point(const orc_params *p, const double *g, int n, const double *x,
     octx c;
     if (ctx_init(&c, p)) return -1;
     for (int i = 0; i < n; ++i)
-        flux_point(&c, g, x[i], parts & 1, (parts >> 1) & 1, &F[i], Fabs ? &Fabs[i] : NULL);
+        flux_point(&c, g, g, x[i], parts & 1, (parts >> 1) & 1, &F[i], Fabs ? &Fabs[i] : NULL);
     ctx_free(&c);
     return 0;
 }
@@ -874,7 +881,7 @@ int orc_vol_frag(const orc_params *p, const double *g, int j, double *V, double 
     octx c;
     if (ctx_init(&c, p)) return -1;
     if (j < 0 || j >= c.N) { ctx_free(&c); return -1; }
-    vol_frag_appB(&c, g, j, V, Vabs);
+    vol_frag_appB(&c, g, g, j, V, Vabs);
     ctx_free(&c);
     return 0;
 }
@@ -985,6 +992,116 @@ int orc_substep_counts(const orc_params *p, int n_cells, const double *g, const 
     free(L);
     ctx_free(&c);
     return 0;
+}
+
+/* Species of grains that are mixtures (Sec. 5.3, reading R24): gs holds S partial mass densities in
+   the layout [S][n_cells][P]; per cell g = sum_s g_s and L_s = L[g_s; g] (rhs_one_outer), written to
+   Ls in the same layout, Ss the rounding scales (or NULL). */
+int orc_rhs_species_batch(const orc_params *p, int n_cells, int n_species, const double *gs, double *Ls,
+                          double *Ss)
+{
+    octx c;
+    if (ctx_init(&c, p)) return -1;
+    const int P = c.P;
+    int bad = 0;
+    #pragma omp parallel
+    {
+        double *g = (double *)malloc(sizeof(double) * (size_t)P);
+        if (!g) {
+            #pragma omp atomic write
+            bad = 1;
+        } else {
+            #pragma omp for schedule(dynamic, 1)
+            for (int cell = 0; cell < n_cells; ++cell) {
+                for (int i = 0; i < P; ++i) g[i] = 0.0;
+                for (int sp = 0; sp < n_species; ++sp)
+                    for (int i = 0; i < P; ++i) g[i] += gs[((size_t)sp * n_cells + cell) * P + i];
+                for (int sp = 0; sp < n_species; ++sp) {
+                    const size_t o = ((size_t)sp * n_cells + cell) * P;
+                    rhs_one_outer(&c, gs + o, g, Ls + o, Ss ? Ss + o : NULL);
+                }
+            }
+            free(g);
+        }
+    }
+    ctx_free(&c);
+    return bad ? -2 : 0;
+}
+
+/* n_steps SSP-RK3 steps (eq. RK3) of the S species of every cell: each stage forms g = sum_s g_s of
+   the stage input, L_s = L[g_s; g] and the stage combination per species; the scaling limiter
+   (eqs. recon, gamma) acts on each species before each step.  mass[S][n_cells] receives M_1 of each
+   species after the last step, flags[n_cells] the OR of the status bits of the cell's species
+   (as orc_step_batch, the eq. dt bit from each species' forward-Euler mean update; the drift bit
+   from the cell's total M_1). */
+int orc_step_species_batch(const orc_params *p, int n_cells, int n_species, double *gs, const double *dt,
+                           int n_steps, double *mass, unsigned char *flags)
+{
+    octx c;
+    if (ctx_init(&c, p)) return -1;
+    const int P = c.P, S = n_species;
+    int bad = 0;
+    #pragma omp parallel
+    {
+        /* g^n, g^(1), g^(2) of every species, L of every species, the total */
+        double *w = (double *)malloc(sizeof(double) * (size_t)P * (4 * (size_t)S + 1));
+        if (!w) {
+            #pragma omp atomic write
+            bad = 1;
+        } else {
+            #pragma omp for schedule(dynamic, 1)
+            for (int cell = 0; cell < n_cells; ++cell) {
+                double *gn = w, *g1 = w + (size_t)S * P, *g2 = w + 2 * (size_t)S * P, *L = w + 3 * (size_t)S * P;
+                double *gt = w + 4 * (size_t)S * P;
+                unsigned f = 0;
+                double m0 = 0.0;
+                for (int sp = 0; sp < S; ++sp) {
+                    memcpy(gn + (size_t)sp * P, gs + ((size_t)sp * n_cells + cell) * P, sizeof(double) * P);
+                    m0 += mass_one(&c, gn + (size_t)sp * P);
+                }
+                const double d = dt[cell];
+                for (int st = 0; st < n_steps; ++st) {
+                    if (c.p.limiter)
+                        for (int sp = 0; sp < S; ++sp) f |= limit_one(&c, gn + (size_t)sp * P);
+                    for (int stage = 0; stage < 3; ++stage) {
+                        double *in = stage == 0 ? gn : (stage == 1 ? g1 : g2);
+                        double *out = stage == 0 ? g1 : (stage == 1 ? g2 : gn);
+                        for (int i = 0; i < P; ++i) gt[i] = 0.0;
+                        for (int sp = 0; sp < S; ++sp)
+                            for (int i = 0; i < P; ++i) gt[i] += in[(size_t)sp * P + i];
+                        for (int sp = 0; sp < S; ++sp)
+                            rhs_one_outer(&c, in + (size_t)sp * P, gt, L + (size_t)sp * P, NULL);
+                        for (int sp = 0; sp < S; ++sp) {
+                            const double *a = gn + (size_t)sp * P, *b = in + (size_t)sp * P, *l = L + (size_t)sp * P;
+                            double *o = out + (size_t)sp * P;
+                            f |= cfl_flags(&c, b, l, d);
+                            /* the stage combinations written as in step_one */
+                            if (stage == 0)
+                                for (int i = 0; i < P; ++i) o[i] = b[i] + d * l[i];
+                            else if (stage == 1)
+                                for (int i = 0; i < P; ++i) o[i] = 0.75 * a[i] + 0.25 * (b[i] + d * l[i]);
+                            else
+                                for (int i = 0; i < P; ++i) o[i] = a[i] / 3.0 + 2.0 / 3.0 * (b[i] + d * l[i]);
+                            f |= stage_flags(&c, o);
+                        }
+                    }
+                }
+                double m1 = 0.0;
+                for (int sp = 0; sp < S; ++sp) {
+                    const double ms = mass_one(&c, gn + (size_t)sp * P);
+                    m1 += ms;
+                    if (mass) mass[(size_t)sp * n_cells + cell] = ms;
+                    memcpy(gs + ((size_t)sp * n_cells + cell) * P, gn + (size_t)sp * P, sizeof(double) * P);
+                }
+                if (c.p.flux_mode == 0 && !(f & (1u | 4u | 8u)) && !(fabs(m1 - m0) <= drift_tol(n_steps) * fabs(m0)))
+                    f |= 16u;
+                if (flags) flags[cell] = (unsigned char)f;
+            }
+            free(w);
+        }
+    }
+    ctx_free(&c);
+    return bad ? -2 : 0;
 }
 
 /* Plants a non-conservative update in every later step (tests of the mass-drift bit only);

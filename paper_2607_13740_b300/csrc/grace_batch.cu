@@ -1039,6 +1039,7 @@ void grace_batch_destroy(grace_batch *b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     free_host_io(b);
     free_hydro(b);
+    free_species(b);
     free_grouped(b);
     for (Part &p : b->parts) free_part(p);
     cudaFree(b->d_err);

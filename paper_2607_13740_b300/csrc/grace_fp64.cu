@@ -66,7 +66,83 @@ __global__ void __launch_bounds__(128) contract_fp64_kernel(
     }
 }
 
+// Species of mixed grains (Sec. 5.3): F_s[c, r] = sum_p gs_s[c, p] sum_q T_r[p, q] g[c, q] for S <= 4
+// species, g = sum_s gs_s, with T as built (p the outer collider, q its partner).  The row sum over q
+// with g is shared by the species; 32 cells per warp as above, the S outer tiles next to g in shared
+// memory.  F layout [S][cells][R].
+constexpr int kMaxSpecies = 4;
+
+__global__ void __launch_bounds__(128) contract_fp64_species_kernel(
+    const double *__restrict__ T, const int *__restrict__ qlo, const int *__restrict__ qhi,
+    const int *__restrict__ prange, int R, int P, int S, const double *__restrict__ gs,
+    const double *__restrict__ g, int n_cells, double *__restrict__ F)
+{
+    extern __shared__ double gsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const long long cell0 = ((long long)blockIdx.x * nwarps + warp) * 32;
+    double *gw = gsm + (size_t)warp * P * 32 * (1 + S);   // g, then the S outer tiles
+    for (int t = 0; t <= S; ++t) {
+        const double *src = t == 0 ? g : gs + (size_t)(t - 1) * n_cells * P;
+        double *dst = gw + (size_t)t * P * 32;
+        for (int idx = lane; idx < 32 * P; idx += 32) {
+            const int c = idx / P, q = idx - c * P;
+            const long long cell = cell0 + c;
+            dst[q * 32 + c] = cell < n_cells ? src[cell * P + q] : 0.0;
+        }
+    }
+    __syncwarp();
+    const long long cell = cell0 + lane;
+    const int r_per = (R + gridDim.y - 1) / gridDim.y;
+    const int r_begin = blockIdx.y * r_per, r_end = min(R, r_begin + r_per);
+    for (int r = r_begin; r < r_end; ++r) {
+        const int p0 = prange[2 * r], p1 = prange[2 * r + 1];
+        double Fr[kMaxSpecies] = {0.0, 0.0, 0.0, 0.0};
+        for (int p = p0; p < p1; ++p) {
+            const int q0 = qlo[r * P + p], q1 = qhi[r * P + p];
+            if (q0 >= q1) continue;
+            const double *Trow = T + ((size_t)r * P + p) * P;
+            double y0 = 0.0, y1 = 0.0;
+            int q = q0;
+            for (; q + 1 < q1; q += 2) {
+                y0 = fma(__ldg(Trow + q), gw[q * 32 + lane], y0);
+                y1 = fma(__ldg(Trow + q + 1), gw[(q + 1) * 32 + lane], y1);
+            }
+            if (q < q1) y0 = fma(__ldg(Trow + q), gw[q * 32 + lane], y0);
+            const double y = y0 + y1;
+#pragma unroll
+            for (int sp = 0; sp < kMaxSpecies; ++sp)
+                if (sp < S) Fr[sp] = fma(gw[(size_t)(1 + sp) * P * 32 + p * 32 + lane], y, Fr[sp]);
+        }
+        if (cell < n_cells)
+#pragma unroll
+            for (int sp = 0; sp < kMaxSpecies; ++sp)
+                if (sp < S) F[((size_t)sp * n_cells + cell) * R + r] = Fr[sp];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_contract_fp64_species(const DevGroup &g, const double *d_T, const int *d_qlo, const int *d_qhi,
+                                         const int *d_prange, int S, const double *d_gs, const double *d_g,
+                                         int n_cells, double *d_F, cudaStream_t st)
+{
+    if (S < 1 || S > kMaxSpecies) return cudaErrorInvalidValue;
+    const size_t per_warp = (size_t)g.P * 32 * sizeof(double) * (1 + S);
+    int wpb = (int)((200 * 1024) / per_warp);
+    if (wpb > 4) wpb = 4;
+    if (wpb < 1) return cudaErrorInvalidValue;
+    const size_t smem = per_warp * wpb;
+    cudaError_t e = cudaFuncSetAttribute(contract_fp64_species_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int cells_per_block = 32 * wpb;
+    const int blocks = (n_cells + cells_per_block - 1) / cells_per_block;
+    const dim3 grid(blocks, fp64_functional_chunks(n_cells, g.R));
+    contract_fp64_species_kernel<<<grid, 32 * wpb, smem, st>>>(d_T, d_qlo, d_qhi, d_prange, g.R, g.P, S, d_gs, d_g,
+                                                               n_cells, d_F);
+    return cudaGetLastError();
+}
 
 int fp64_functional_chunks(int n_cells, int R)
 {

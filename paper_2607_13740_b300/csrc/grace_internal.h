@@ -175,6 +175,7 @@ struct grace_batch {
                                    // conservative-group bytes [n], built on the first flagged call
     unsigned *d_flag_or = nullptr; // grace_flags_check's reduction word
     void *hydro = nullptr;         // grace_substep workspace (grace_hydro.cu), built on first use
+    void *species = nullptr;       // species workspace (grace_species.cu), built on first use
 };
 
 namespace grace {
@@ -183,6 +184,8 @@ namespace grace {
 void free_host_io(grace_batch *b);
 // frees the workspace of grace_substep
 void free_hydro(grace_batch *b);
+// frees the workspace of the species calls
+void free_species(grace_batch *b);
 
 // thread-local error detail
 void set_error(const std::string &msg);
@@ -215,6 +218,10 @@ cudaError_t launch_row_extents(const DevGroup &g, const double *d_T, int *d_qlo,
                                int *d_prange, cudaStream_t st);
 // functional chunks (grid y) of the FP64 contractions for a batch of n_cells
 int fp64_functional_chunks(int n_cells, int R);
+// species of mixed grains: F_s = sum_p gs_s[p] sum_q T[p, q] g[q], F layout [S][cells][R], S <= 4
+cudaError_t launch_contract_fp64_species(const DevGroup &g, const double *d_T, const int *d_qlo, const int *d_qhi,
+                                         const int *d_prange, int S, const double *d_gs, const double *d_g,
+                                         int n_cells, double *d_F, cudaStream_t st);
 cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int *d_qlo,
                                  const int *d_qhi, const int *d_prange, const double *d_g,
                                  int n_cells, double *d_F, cudaStream_t st);

@@ -291,9 +291,13 @@ GRACE_API grace_status grace_rhs_vjp(grace_batch *batch, const double *g, const 
                                      int precision);
 
 /* Prepares parameter gradients for grace_adjoint: for each id (0..7 coag_p[i],
-   8..15 frag_p[i-8], 16..23 break_p[i-16]) builds dT_r/dtheta by a central
-   difference of the FP64 precompute with relative step rel_step (<= 0 means
-   1e-5).  Replaces any earlier set.  Allocates and synchronises. */
+   8..15 frag_p[i-8], 16..23 break_p[i-16]) builds dT_r/dtheta.  rel_step <= 0: exactly, by
+   forward-mode dual numbers through the FP64 precompute (the derivatives of the kernels, of the
+   breakage mass functions of eqs. (break), (inte1), (inte2) and App. B, and of the Maxwellian
+   probabilities of Sec. 4.5, carried through the same quadrature sums; a clamp such as the
+   fragmentation ramp contributes its one-sided derivative).  rel_step > 0: a central difference
+   of the FP64 precompute with that relative step (kept for cross-checks).  Replaces any earlier
+   set.  Allocates and synchronises. */
 GRACE_API grace_status grace_param_grad_setup(grace_ctx *ctx, int group, int n_params, const int *param_ids,
                                               double rel_step);
 

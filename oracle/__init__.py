@@ -62,6 +62,8 @@ def lib():
         L.orc_mass_batch.argtypes = [P, ctypes.c_int, _D, _D]
         L.orc_project_batch.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D]
         L.orc_max_threads.restype = ctypes.c_int
+        L.orc_tangent_rhs.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D]
+        L.orc_tangent_step.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_int, _D, ctypes.c_int, _D, _D]
         _lib = L
     return _lib
 
@@ -201,6 +203,31 @@ class Oracle:
         _check(lib().orc_step_species_batch(self._pp, n, S_, _p(gs), _p(dt), int(n_steps), _p(mass),
                                             f.ctypes.data_as(_U8)), "step_species")
         return gs, mass, f
+
+    def tangent_rhs(self, g, gdot=None, param_id: int = -1):
+        """Forward-mode derivative build: returns (L[g], dL) with dL the exact derivative of the
+        oracle's L along gdot (None: zero) and parameter param_id (0..7 coag_p, 8..15 frag_p,
+        16..23 break_p; -1 none)."""
+        g = _f64(g).reshape(-1, self.P)
+        gd = None if gdot is None else _f64(gdot).reshape(g.shape)
+        L = np.zeros_like(g)
+        dL = np.zeros_like(g)
+        _check(lib().orc_tangent_rhs(self._pp, g.shape[0], _p(g), None if gd is None else _p(gd), int(param_id),
+                                     _p(L), _p(dL)), "tangent_rhs")
+        return L, dL
+
+    def tangent_step(self, g, dt, n_steps: int, gdot=None, param_id: int = -1):
+        """n_steps oracle steps (limiter + SSP-RK3) on dual numbers: returns (g(T), dg(T)), the
+        exact derivative of the final state along gdot and parameter param_id."""
+        g = _f64(g).reshape(-1, self.P)
+        n = g.shape[0]
+        gd = None if gdot is None else _f64(gdot).reshape(g.shape)
+        dt = _f64(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        out = np.zeros_like(g)
+        dout = np.zeros_like(g)
+        _check(lib().orc_tangent_step(self._pp, n, _p(g), None if gd is None else _p(gd), int(param_id), _p(dt),
+                                      int(n_steps), _p(out), _p(dout)), "tangent_step")
+        return out, dout
 
     def substep_counts(self, g, dt_hydro, cfl: float):
         """Per-cell sub-step counts ceil(dt_hydro / (cfl B)) of the operator-split coupling, B the eq. (dt)

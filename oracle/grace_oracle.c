@@ -54,6 +54,19 @@
 #define ORC_QMAX 40
 #define ORC_KMAX 8
 
+/* Scalar type of every quantity that depends on the state g or on the physics parameters.
+   This file, compiled as C, is the oracle and uses double.  grace_oracle_tangent.cpp compiles
+   the same file as C++ with `real` a forward-mode dual number (value, derivative) to take exact
+   derivatives of this arithmetic with respect to the state or one parameter; RV(x) is the value
+   part (branches, flags and the limiter's minimum location are decided on values).  Grids, Gauss
+   nodes, collision masses u, v and evaluation points x never depend on either and stay double. */
+#ifndef ORC_TANGENT
+typedef double real;
+#define RV(x) (x)
+#define REAL_IS_ZERO(x) ((x) == 0.0)
+#define ORC_API
+#endif
+
 /* ------------------------------------------------------------------ */
 /* public parameter block (mirrored by a ctypes.Structure in Python)   */
 /* ------------------------------------------------------------------ */
@@ -85,8 +98,10 @@ typedef struct {
     int N, k, Q, P;
     double *e;              /* N+1 bin edges x_{j-1/2}                    */
     double s[ORC_QMAX], w[ORC_QMAX];
+    /* the physics parameters as read by the kernels and breakage functions */
+    real coag_p[8], frag_p[8], break_p[8];
     /* Maxwellian collision probabilities (constant when dv_rms is constant) */
-    double beta_coag, beta_frag;
+    real beta_coag, beta_frag;
 } octx;
 
 /* ------------------------------------------------------------------ */
@@ -108,7 +123,7 @@ static void legendre(int k, double xi, double *P, double *dP)
 /* ------------------------------------------------------------------ */
 /* Gauss-Legendre nodes and weights (eq. quad), by Newton on P_Q        */
 /* ------------------------------------------------------------------ */
-int orc_gauss(int Q, double *s, double *w)
+ORC_API int orc_gauss(int Q, double *s, double *w)
 {
     if (Q < 1 || Q > ORC_QMAX) return -1;
     for (int i = 0; i < Q; ++i) {
@@ -141,18 +156,26 @@ int orc_gauss(int Q, double *s, double *w)
 /* ------------------------------------------------------------------ */
 /* context                                                             */
 /* ------------------------------------------------------------------ */
-static double maxwell_below(double vth, double dv)
+static real maxwell_below(real vth, real dv)
 {
     /* beta_coag = int_0^{v_b} f_v dv (Sec. 4.5) */
-    double a = sqrt(3.0 / (2.0 * dv * dv));
+    real a = sqrt(3.0 / (2.0 * dv * dv));
     return erf(a * vth) - vth * sqrt(6.0 / (M_PI * dv * dv)) * exp(-3.0 * vth * vth / (2.0 * dv * dv));
 }
 
-static double maxwell_above(double vth, double dv)
+static real maxwell_above(real vth, real dv)
 {
     /* beta_frag = int_{v_f}^inf f_v dv (Sec. 4.5) */
-    double a = sqrt(3.0 / (2.0 * dv * dv));
+    real a = sqrt(3.0 / (2.0 * dv * dv));
     return 1.0 - erf(a * vth) + vth * sqrt(6.0 / (M_PI * dv * dv)) * exp(-3.0 * vth * vth / (2.0 * dv * dv));
+}
+
+static void ctx_betas(octx *c)
+{
+    if (c->p.coag_kind == ORC_COAG_MAXWELL)
+        c->beta_coag = maxwell_below(c->coag_p[1], c->coag_p[0]);
+    if (c->p.frag_kind == ORC_FRAG_MAXWELL)
+        c->beta_frag = maxwell_above(c->frag_p[1], c->frag_p[0]);
 }
 
 static int ctx_init(octx *c, const orc_params *p)
@@ -173,10 +196,12 @@ static int ctx_init(octx *c, const orc_params *p)
     c->e[0] = p->x_min;
     c->e[c->N] = p->x_max;
     orc_gauss(c->Q, c->s, c->w);
-    if (p->coag_kind == ORC_COAG_MAXWELL)
-        c->beta_coag = maxwell_below(p->coag_p[1], p->coag_p[0]);
-    if (p->frag_kind == ORC_FRAG_MAXWELL)
-        c->beta_frag = maxwell_above(p->frag_p[1], p->frag_p[0]);
+    for (int i = 0; i < 8; ++i) {
+        c->coag_p[i] = p->coag_p[i];
+        c->frag_p[i] = p->frag_p[i];
+        c->break_p[i] = p->break_p[i];
+    }
+    ctx_betas(c);
     return 0;
 }
 
@@ -199,47 +224,47 @@ static double cross_section(double u, double v)
    integration in the tests.  Parameters:
    p[0] = rho_s, p[1] = Sigma_g, p[2] = c_s, p[3] = alpha_turb, p[4] = v_frag,
    p[5] = ramp half-width fraction, p[6] = overall rate scale. */
-static void ballistic(const double *p, double u, double v, double *kc, double *kf)
+static void ballistic(const real *p, double u, double v, real *kc, real *kf)
 {
-    double rho = p[0], sig = p[1], cs = p[2], alpha = p[3], vf = p[4], wr = p[5];
-    double au = cbrt(3.0 * u / (4.0 * M_PI * rho));
-    double av = cbrt(3.0 * v / (4.0 * M_PI * rho));
-    double st = M_PI * rho * fmax(au, av) / (2.0 * sig);
-    double dv = cs * sqrt(3.0 * alpha * st / (1.0 + st * st));
-    double pf = (dv - (1.0 - wr) * vf) / (2.0 * wr * vf);
+    real rho = p[0], sig = p[1], cs = p[2], alpha = p[3], vf = p[4], wr = p[5];
+    real au = cbrt(3.0 * u / (4.0 * M_PI * rho));
+    real av = cbrt(3.0 * v / (4.0 * M_PI * rho));
+    real st = M_PI * rho * fmax(au, av) / (2.0 * sig);
+    real dv = cs * sqrt(3.0 * alpha * st / (1.0 + st * st));
+    real pf = (dv - (1.0 - wr) * vf) / (2.0 * wr * vf);
     if (pf < 0.0) pf = 0.0;
     if (pf > 1.0) pf = 1.0;
-    double rate = p[6] * M_PI * (au + av) * (au + av) * dv;
+    real rate = p[6] * M_PI * (au + av) * (au + av) * dv;
     *kc = rate * (1.0 - pf);
     *kf = rate * pf;
 }
 
-static double kcoag(const octx *c, double u, double v)
+static real kcoag(const octx *c, double u, double v)
 {
-    const double *p = c->p.coag_p;
+    const real *p = c->coag_p;
     switch (c->p.coag_kind) {
     case ORC_COAG_CONST: return p[0];
     case ORC_COAG_ADD: return p[0] * (u + v);
     case ORC_COAG_MULT: return p[0] * u * v;
     case ORC_COAG_MAXWELL: return cross_section(u, v) * p[0] * c->beta_coag;
-    case ORC_COAG_BALLISTIC: { double kc, kf; ballistic(p, u, v, &kc, &kf); return kc; }
+    case ORC_COAG_BALLISTIC: { real kc, kf; ballistic(p, u, v, &kc, &kf); return kc; }
     default: return 0.0;
     }
 }
 
-static double kfrag(const octx *c, double u, double v)
+static real kfrag(const octx *c, double u, double v)
 {
-    const double *p = c->p.frag_p;
+    const real *p = c->frag_p;
     switch (c->p.frag_kind) {
     case ORC_FRAG_MULT: return p[0] * u * v;
     case ORC_FRAG_MAXWELL: return cross_section(u, v) * p[0] * c->beta_frag;
-    case ORC_FRAG_BALLISTIC: { double kc, kf; ballistic(p, u, v, &kc, &kf); return kf; }
+    case ORC_FRAG_BALLISTIC: { real kc, kf; ballistic(p, u, v, &kc, &kf); return kf; }
     default: return 0.0;
     }
 }
 
 /* fragment mass fraction m_frag / (y+z), eq. (mfrag) */
-double orc_mfrag_ratio(double q)
+ORC_API double orc_mfrag_ratio(double q)
 {
     if (q <= 10.0) return 1.0;
     if (q <= 12.0) return (6.5 + 4.5 * cos((q - 10.0) / (12.0 - 10.0) * M_PI)) / (1.0 + q);
@@ -248,14 +273,14 @@ double orc_mfrag_ratio(double q)
     return 0.9 / (1.0 + q);
 }
 
-typedef struct { double mfrag, mleft, mcut, alpha; } frag_out;
+typedef struct { double mfrag, mleft, mcut; real alpha; } frag_out;
 
 static frag_out frag_outcome(const octx *c, double u, double v)
 {
     frag_out o;
     double big = u > v ? u : v, small = u > v ? v : u;
     double tot = u + v;
-    o.alpha = c->p.break_p[0];
+    o.alpha = c->break_p[0];
     o.mfrag = c->p.mfrag_mode == 1 ? tot : tot * orc_mfrag_ratio(big / small);
     o.mleft = tot - o.mfrag;
     if (o.mleft < 0.0) o.mleft = 0.0;
@@ -265,18 +290,18 @@ static frag_out frag_outcome(const octx *c, double u, double v)
 
 /* fraction of power-law fragment mass in [x_min, x] (eq. break with the
    normalisation A of Sec. 4.5); R10 for a cutoff at or below x_min */
-static double pl_fraction(double x, double xmin, double mcut, double alpha)
+static real pl_fraction(double x, double xmin, double mcut, real alpha)
 {
     if (!(mcut > xmin)) return x > xmin ? 1.0 : 0.0;
-    double a2 = 2.0 + alpha;
-    double f = (pow(x, a2) - pow(xmin, a2)) / (pow(mcut, a2) - pow(xmin, a2));
+    real a2 = 2.0 + alpha;
+    real f = (pow(x, a2) - pow(xmin, a2)) / (pow(mcut, a2) - pow(xmin, a2));
     if (f < 0.0) f = 0.0;
     if (f > 1.0) f = 1.0;
     return f;
 }
 
 /* mass of collision products with w > x:  int_x^{u+v} w b(w,u,v) dw  (eq. inte1) */
-static double mass_above(const octx *c, double x, double u, double v)
+static real mass_above(const octx *c, double x, double u, double v)
 {
     switch (c->p.break_kind) {
     case ORC_BREAK_UNIFORM_BINARY: {
@@ -288,7 +313,7 @@ static double mass_above(const octx *c, double x, double u, double v)
     }
     case ORC_BREAK_POWERLAW_REMNANT: {
         frag_out o = frag_outcome(c, u, v);
-        double m = o.mfrag * (1.0 - pl_fraction(x, c->p.x_min, o.mcut, o.alpha));
+        real m = o.mfrag * (1.0 - pl_fraction(x, c->p.x_min, o.mcut, o.alpha));
         if (o.mleft > x) m += o.mleft;
         return m;
     }
@@ -299,7 +324,7 @@ static double mass_above(const octx *c, double x, double u, double v)
 }
 
 /* mass of collision products with x_min <= w <= x:  int_{x_min}^x w b dw  (eq. inte2) */
-static double mass_below(const octx *c, double x, double u, double v)
+static real mass_below(const octx *c, double x, double u, double v)
 {
     double xmin = c->p.x_min;
     switch (c->p.break_kind) {
@@ -312,7 +337,7 @@ static double mass_below(const octx *c, double x, double u, double v)
     }
     case ORC_BREAK_POWERLAW_REMNANT: {
         frag_out o = frag_outcome(c, u, v);
-        double m = o.mfrag * pl_fraction(x, xmin, o.mcut, o.alpha);
+        real m = o.mfrag * pl_fraction(x, xmin, o.mcut, o.alpha);
         if (o.mleft >= xmin && o.mleft <= x) m += o.mleft;
         return m;
     }
@@ -344,15 +369,15 @@ static int bin_of(const octx *c, double y)
 }
 
 /* g_l(u) = sum_i g_l^i phi_i(xi_l(u)) (eq. 2.3); *gabs = sum_i |g_l^i phi_i| */
-static double gval(const octx *c, const double *g, int l, double u, double *gabs)
+static real gval(const octx *c, const real *g, int l, double u, real *gabs)
 {
     double P[ORC_KMAX + 1];
     double h = c->e[l + 1] - c->e[l];
     double xc = 0.5 * (c->e[l] + c->e[l + 1]);
     double xi = 2.0 / h * (u - xc);
     legendre(c->k, xi, P, NULL);
-    const double *gl = g + (size_t)l * (c->k + 1);
-    double s = 0.0, a = 0.0;
+    const real *gl = g + (size_t)l * (c->k + 1);
+    real s = 0.0, a = 0.0;
     for (int i = 0; i <= c->k; ++i) { s += gl[i] * P[i]; a += fabs(gl[i] * P[i]); }
     if (gabs) *gabs = a;
     return s;
@@ -372,14 +397,14 @@ static double vmax_of(const octx *c, double u)
    bins A and B reduced to the sub-intervals [a_m, b_m] and Q remapped
    nodes each.                                                         */
 /* ------------------------------------------------------------------ */
-static void flux_point(const octx *c, const double *go, const double *g, double x, int want_coag,
-                       int want_frag, double *F, double *Fabs)
+static void flux_point(const octx *c, const real *go, const real *g, double x, int want_coag,
+                       int want_frag, real *F, real *Fabs)
 {
     const int Q = c->Q;
     const double xmin = c->p.x_min;
     int do_coag = want_coag && c->p.coag_kind != ORC_COAG_NONE;
     int do_frag = want_frag && c->p.frag_kind != ORC_FRAG_NONE;
-    double Fs = 0.0, Fa = 0.0;
+    real Fs = 0.0, Fa = 0.0;
 
     /* positive flux: u in [x_min, x], v in [x - u + x_min, v_max(u)] */
     if (do_coag || do_frag) {
@@ -389,7 +414,7 @@ static void flux_point(const octx *c, const double *go, const double *g, double 
             for (int al = 0; al < Q; ++al) {
                 double u = 0.5 * (a + b) + 0.5 * (b - a) * c->s[al];
                 double Wu = 0.5 * (b - a) * c->w[al];
-                double gua, gu = gval(c, go, l, u, &gua);
+                real gua, gu = gval(c, go, l, u, &gua);
                 double lo = x - u + xmin, hi = vmax_of(c, u);
                 if (!(hi > lo)) continue;
                 for (int m = bin_of(c, lo); m < c->N && c->e[m] < hi; ++m) {
@@ -399,8 +424,8 @@ static void flux_point(const octx *c, const double *go, const double *g, double 
                     for (int be = 0; be < Q; ++be) {
                         double v = 0.5 * (va + vb) + 0.5 * (vb - va) * c->s[be];
                         double Wv = 0.5 * (vb - va) * c->w[be];
-                        double gva, gv = gval(c, g, m, v, &gva);
-                        double t = 0.0;
+                        real gva, gv = gval(c, g, m, v, &gva);
+                        real t = 0.0;
                         if (do_coag) t += kcoag(c, u, v) / v;
                         if (do_frag) t += kfrag(c, u, v) * mass_above(c, x, u, v) / (v * (u + v));
                         Fs += Wu * Wv * t * gu * gv;
@@ -418,7 +443,7 @@ static void flux_point(const octx *c, const double *go, const double *g, double 
             for (int al = 0; al < Q; ++al) {
                 double u = 0.5 * (a + b) + 0.5 * (b - a) * c->s[al];
                 double Wu = 0.5 * (b - a) * c->w[al];
-                double gua, gu = gval(c, go, l, u, &gua);
+                real gua, gu = gval(c, go, l, u, &gua);
                 double lo = xmin, hi = vmax_of(c, u);
                 if (!(hi > lo)) continue;
                 for (int m = 0; m < c->N && c->e[m] < hi; ++m) {
@@ -428,8 +453,8 @@ static void flux_point(const octx *c, const double *go, const double *g, double 
                     for (int be = 0; be < Q; ++be) {
                         double v = 0.5 * (va + vb) + 0.5 * (vb - va) * c->s[be];
                         double Wv = 0.5 * (vb - va) * c->w[be];
-                        double gva, gv = gval(c, g, m, v, &gva);
-                        double t = kfrag(c, u, v) * mass_below(c, x, u, v) / (v * (u + v));
+                        real gva, gv = gval(c, g, m, v, &gva);
+                        real t = kfrag(c, u, v) * mass_below(c, x, u, v) / (v * (u + v));
                         Fs -= Wu * Wv * t * gu * gv;
                         Fa += fabs(Wu * Wv * t) * gua * gva;
                     }
@@ -444,8 +469,8 @@ static void flux_point(const octx *c, const double *go, const double *g, double 
 /* Gauss integral of f(x) * d/dx phi_i(xi_j(x)), i = 1..k, over [a, b] inside
    bin j, for f = c0 + c1 * x^{2+alpha} (pw = 1) or f = c0 (pw = 0).
    Adds into J[i] and |.| into Jabs[i]. */
-static void sub_integral(const octx *c, int j, double a, double b, double c0, double c1,
-                         double alpha, int pw, double sign, double *J, double *Jabs)
+static void sub_integral(const octx *c, int j, double a, double b, real c0, real c1,
+                         real alpha, int pw, double sign, real *J, real *Jabs)
 {
     if (!(b > a)) return;
     double P[ORC_KMAX + 1], dP[ORC_KMAX + 1];
@@ -454,10 +479,10 @@ static void sub_integral(const octx *c, int j, double a, double b, double c0, do
     for (int t = 0; t < c->Q; ++t) {
         double x = 0.5 * (a + b) + 0.5 * (b - a) * c->s[t];
         double W = 0.5 * (b - a) * c->w[t];
-        double f = c0 + (pw ? c1 * pow(x, 2.0 + alpha) : 0.0);
+        real f = pw ? c0 + c1 * pow(x, 2.0 + alpha) : c0;
         legendre(c->k, 2.0 / h * (x - xc), P, dP);
         for (int i = 1; i <= c->k; ++i) {
-            double d = W * f * (2.0 / h) * dP[i];
+            real d = W * f * (2.0 / h) * dP[i];
             J[i] += sign * d;
             Jabs[i] += fabs(d);
         }
@@ -472,16 +497,16 @@ static double dmin(double a, double b) { return a < b ? a : b; }
    the products heavier than x (eq. inte1) while u < x <= u + v - x_min, minus the products in
    [x_min, x] (eq. inte2) while x_min < x < u.  The x-integral is split into the five
    sub-interval terms of App. B (R7, R8); Ja[i] collects their absolute values. */
-static void appB_pair(const octx *c, int j, double u, double v, double *J, double *Ja)
+static void appB_pair(const octx *c, int j, double u, double v, real *J, real *Ja)
 {
     const double xmin = c->p.x_min;
     const double ja = c->e[j], jb = c->e[j + 1];
     frag_out o = frag_outcome(c, u, v);
     double top = u + v - xmin;  /* x <= u + v - x_min (R7) */
-    double a2 = 2.0 + o.alpha;
+    real a2 = 2.0 + o.alpha;
     if (o.mcut > xmin) {
-        double cA = o.mfrag / (pow(o.mcut, a2) - pow(xmin, a2)); /* A/(2+alpha) */
-        double mc2 = pow(o.mcut, a2), xm2 = pow(xmin, a2);
+        real cA = o.mfrag / (pow(o.mcut, a2) - pow(xmin, a2)); /* A/(2+alpha) */
+        real mc2 = pow(o.mcut, a2), xm2 = pow(xmin, a2);
         /* term 1: +int_{I_j cap (u, min(top, m_cut))} A/(2+a) (m_cut^{2+a} - x^{2+a}) */
         sub_integral(c, j, dmax(ja, u), dmin(jb, dmin(top, o.mcut)),
                      cA * mc2, -cA, o.alpha, 1, +1.0, J, Ja);
@@ -511,7 +536,7 @@ static void appB_pair(const octx *c, int j, double u, double v, double *J, doubl
    (u, v) quadrature (appB_pair).  The outer (u, v) quadrature runs over full
    bins in u and over the bins of [x_min, v_max(u)] in v.  V[i], Vabs[i] for
    i = 1..k. */
-static void vol_frag_appB(const octx *c, const double *go, const double *g, int j, double *V, double *Vabs)
+static void vol_frag_appB(const octx *c, const real *go, const real *g, int j, real *V, real *Vabs)
 {
     const int Q = c->Q, k = c->k;
     const double xmin = c->p.x_min;
@@ -521,7 +546,7 @@ static void vol_frag_appB(const octx *c, const double *go, const double *g, int 
         for (int al = 0; al < Q; ++al) {
             double u = 0.5 * (a + b) + 0.5 * (b - a) * c->s[al];
             double Wu = 0.5 * (b - a) * c->w[al];
-            double gua, gu = gval(c, go, l, u, &gua);
+            real gua, gu = gval(c, go, l, u, &gua);
             double hi = vmax_of(c, u);
             for (int m = 0; m < c->N && c->e[m] < hi; ++m) {
                 double va = c->e[m] > xmin ? c->e[m] : xmin;
@@ -530,11 +555,11 @@ static void vol_frag_appB(const octx *c, const double *go, const double *g, int 
                 for (int be = 0; be < Q; ++be) {
                     double v = 0.5 * (va + vb) + 0.5 * (vb - va) * c->s[be];
                     double Wv = 0.5 * (vb - va) * c->w[be];
-                    double base = Wu * Wv * kfrag(c, u, v) / (v * (u + v));
-                    if (base == 0.0) continue;
-                    double J[ORC_KMAX + 1] = {0}, Ja[ORC_KMAX + 1] = {0};
+                    real base = Wu * Wv * kfrag(c, u, v) / (v * (u + v));
+                    if (REAL_IS_ZERO(base)) continue;
+                    real J[ORC_KMAX + 1] = {0}, Ja[ORC_KMAX + 1] = {0};
                     appB_pair(c, j, u, v, J, Ja);
-                    double gva, gv = gval(c, g, m, v, &gva);
+                    real gva, gv = gval(c, g, m, v, &gva);
                     for (int i = 1; i <= k; ++i) {
                         V[i] += base * gu * gv * J[i];
                         Vabs[i] += fabs(base) * gua * gva * Ja[i];
@@ -553,11 +578,11 @@ static void vol_frag_appB(const octx *c, const double *go, const double *g, int 
    whose share of the products crosses x), g that of its partner v: go = g gives L[g]; go = g_s,
    the partial mass density of a species s of grains that are mixtures of species (Sec. 5.3, with
    g = sum_s g_s), gives the rate of that species' partial mass (reading R24). */
-static void rhs_one_outer(const octx *c, const double *go, const double *g, double *L, double *S)
+static void rhs_one_outer(const octx *c, const real *go, const real *g, real *L, real *S)
 {
     const int N = c->N, k = c->k, Q = c->Q;
-    double *Fif = (double *)calloc((size_t)(N + 1) * 2, sizeof(double));
-    double *Fab = Fif + (N + 1);
+    real *Fif = (real *)calloc((size_t)(N + 1) * 2, sizeof(real));
+    real *Fab = Fif + (N + 1);
     /* interface fluxes; F(x_min) = 0 in both modes and F(x_max) = 0 in the
        conservative mode (Sec. 3.3), so those two are not evaluated */
     int jmax = c->p.flux_mode == 0 ? N - 2 : N - 1;
@@ -569,12 +594,12 @@ static void rhs_one_outer(const octx *c, const double *go, const double *g, doub
     for (int j = 0; j < N; ++j) {
         double h = c->e[j + 1] - c->e[j];
         double xc = 0.5 * (c->e[j] + c->e[j + 1]);
-        double V[ORC_KMAX + 1] = {0}, Va[ORC_KMAX + 1] = {0};
+        real V[ORC_KMAX + 1] = {0}, Va[ORC_KMAX + 1] = {0};
         if (k >= 1) {
             /* volume term int_{I_j} F d_x phi_i = sum_theta w_theta phi_i'(s_theta) F(x_j^theta) */
             for (int th = 0; th < Q; ++th) {
                 double xt = xc + 0.5 * h * c->s[th];
-                double Ft, Fta;
+                real Ft, Fta;
                 flux_point(c, go, g, xt, 1, !delta, &Ft, &Fta);
                 legendre(k, c->s[th], P, dP);
                 for (int i = 1; i <= k; ++i) {
@@ -583,7 +608,7 @@ static void rhs_one_outer(const octx *c, const double *go, const double *g, doub
                 }
             }
             if (delta) {
-                double Vf[ORC_KMAX + 1], Vfa[ORC_KMAX + 1];
+                real Vf[ORC_KMAX + 1], Vfa[ORC_KMAX + 1];
                 vol_frag_appB(c, go, g, j, Vf, Vfa);
                 for (int i = 1; i <= k; ++i) { V[i] += Vf[i]; Va[i] += Vfa[i]; }
             }
@@ -591,8 +616,8 @@ static void rhs_one_outer(const octx *c, const double *go, const double *g, doub
         for (int i = 0; i <= k; ++i) {
             double di = 2.0 / (2.0 * i + 1.0);
             double sgn = (i % 2 == 0) ? 1.0 : -1.0;   /* phi_i(-1) = (-1)^i, phi_i(1) = 1 */
-            double val = V[i] - Fif[j + 1] + sgn * Fif[j];
-            double sc = Va[i] + Fab[j + 1] + Fab[j];
+            real val = V[i] - Fif[j + 1] + sgn * Fif[j];
+            real sc = Va[i] + Fab[j + 1] + Fab[j];
             L[(size_t)j * (k + 1) + i] = 2.0 / h / di * val;
             if (S) S[(size_t)j * (k + 1) + i] = 2.0 / h / di * sc;
         }
@@ -601,7 +626,7 @@ static void rhs_one_outer(const octx *c, const double *go, const double *g, doub
 }
 
 /* the operator L[g] (eq. evo) */
-static void rhs_one(const octx *c, const double *g, double *L, double *S) { rhs_one_outer(c, g, g, L, S); }
+static void rhs_one(const octx *c, const real *g, real *L, real *S) { rhs_one_outer(c, g, g, L, S); }
 
 /* ------------------------------------------------------------------ */
 /* scaling limiter (eqs. recon, gamma), minimum computed analytically   */
@@ -624,20 +649,20 @@ static double dpoly_at(const double *gj, int k, double xi)
     return s;
 }
 
-/* min over [-1, 1] of sum_i g^i phi_i: endpoints plus interior critical
-   points.  k <= 3 in closed form; k >= 4 by bracketing the derivative on a
+/* xi in [-1, 1] where sum_i g^i phi_i takes its minimum: the endpoints and the interior critical
+   points are the candidates.  k <= 3 in closed form; k >= 4 by bracketing the derivative on a
    uniform grid of 256 intervals followed by bisection. */
-double orc_bin_min(const double *gj, int k)
+static double bin_argmin(const double *gj, int k)
 {
-    double m = poly_at(gj, k, -1.0), t = poly_at(gj, k, 1.0);
-    if (t < m) m = t;
-    if (k <= 1) return k == 0 ? gj[0] : m;
+    double xm = -1.0, m = poly_at(gj, k, -1.0), t = poly_at(gj, k, 1.0);
+    if (t < m) { m = t; xm = 1.0; }
+    if (k <= 1) return xm;
     if (k == 2) {
         if (gj[2] != 0.0) {
             double xs = -gj[1] / (3.0 * gj[2]);
-            if (xs > -1.0 && xs < 1.0) { t = poly_at(gj, k, xs); if (t < m) m = t; }
+            if (xs > -1.0 && xs < 1.0) { t = poly_at(gj, k, xs); if (t < m) { m = t; xm = xs; } }
         }
-        return m;
+        return xm;
     }
     if (k == 3) {
         /* p'(xi) = (15/2) g3 xi^2 + 3 g2 xi + (g1 - 3 g3 / 2) */
@@ -655,8 +680,8 @@ double orc_bin_min(const double *gj, int k)
             }
         }
         for (int i = 0; i < nr; ++i)
-            if (r[i] > -1.0 && r[i] < 1.0) { t = poly_at(gj, k, r[i]); if (t < m) m = t; }
-        return m;
+            if (r[i] > -1.0 && r[i] < 1.0) { t = poly_at(gj, k, r[i]); if (t < m) { m = t; xm = r[i]; } }
+        return xm;
     }
     const int M = 256;
     double x0 = -1.0, d0 = dpoly_at(gj, k, x0);
@@ -669,28 +694,41 @@ double orc_bin_min(const double *gj, int k)
                 if ((dlo < 0.0) == (dm < 0.0)) { lo = mid; dlo = dm; } else hi = mid;
             }
             t = poly_at(gj, k, 0.5 * (lo + hi));
-            if (t < m) m = t;
+            if (t < m) { m = t; xm = 0.5 * (lo + hi); }
         }
         x0 = x1; d0 = d1;
     }
-    return m;
+    return xm;
 }
 
-/* applies eq. (recon) with gamma from eq. (gamma) to every bin; returns flag bits */
-static unsigned limit_one(const octx *c, double *g)
+/* min over [-1, 1] of sum_i g^i phi_i (the value at bin_argmin) */
+ORC_API double orc_bin_min(const double *gj, int k)
+{
+    return k == 0 ? gj[0] : poly_at(gj, k, bin_argmin(gj, k));
+}
+
+/* applies eq. (recon) with gamma from eq. (gamma) to every bin; returns flag bits.  The bin
+   minimum is the polynomial at its argmin (found on the values), so in a derivative build the
+   minimum's derivative is the derivative of the polynomial at that fixed point (the envelope
+   theorem: the polynomial's xi-derivative vanishes at an interior minimum). */
+static unsigned limit_one(const octx *c, real *g)
 {
     unsigned flags = 0;
     const int k = c->k;
     if (k == 0) return 0;
     for (int j = 0; j < c->N; ++j) {
-        double *gj = g + (size_t)j * (k + 1);
-        double gbar = gj[0];
-        double gamma;
+        real *gj = g + (size_t)j * (k + 1);
+        real gbar = gj[0];
+        real gamma;
         if (gbar < 0.0) { gamma = 0.0; flags |= 1u; }
         else {
-            double mn = orc_bin_min(gj, k);
-            double den = gbar - mn;
-            gamma = den > 0.0 ? gbar / den : 1.0;
+            double gv[ORC_KMAX + 1], P[ORC_KMAX + 1];
+            for (int i = 0; i <= k; ++i) gv[i] = RV(gj[i]);
+            legendre(k, bin_argmin(gv, k), P, NULL);
+            real mn = 0.0;
+            for (int i = 0; i <= k; ++i) mn += gj[i] * P[i];
+            real den = gbar - mn;
+            gamma = den > 0.0 ? gbar / den : (real)1.0;
             if (gamma > 1.0) gamma = 1.0;
         }
         if (gamma < 1.0) {
@@ -701,21 +739,21 @@ static unsigned limit_one(const octx *c, double *g)
     return flags;
 }
 
-static double mass_one(const octx *c, const double *g)
+static real mass_one(const octx *c, const real *g)
 {
     /* M_1 = sum_j h_j g_j^0 (Sec. 4.1) */
-    double m = 0.0;
+    real m = 0.0;
     for (int j = 0; j < c->N; ++j) m += (c->e[j + 1] - c->e[j]) * g[(size_t)j * (c->k + 1)];
     return m;
 }
 
-static unsigned stage_flags(const octx *c, const double *g)
+static unsigned stage_flags(const octx *c, const real *g)
 {
     unsigned f = 0;
     for (int j = 0; j < c->N; ++j) {
         if (g[(size_t)j * (c->k + 1)] < 0.0) f |= 1u;
         for (int i = 0; i <= c->k; ++i)
-            if (!isfinite(g[(size_t)j * (c->k + 1) + i])) f |= 4u;
+            if (!isfinite(RV(g[(size_t)j * (c->k + 1) + i]))) f |= 4u;
     }
     return f;
 }
@@ -726,12 +764,12 @@ static unsigned stage_flags(const octx *c, const double *g)
    (L_j^0 < 0); a bin with influx or no flux cannot turn negative and is not flagged.
    For L_j^0 < 0 the bound fails exactly when g_j^0 + dt L_j^0 <= 0, evaluated with
    one rounding (fma), which keeps its sign exact.  Flag bit 3. */
-static unsigned cfl_flags(const octx *c, const double *gs, const double *L, double dt)
+static unsigned cfl_flags(const octx *c, const real *gs, const real *L, double dt)
 {
     unsigned f = 0;
     for (int j = 0; j < c->N; ++j) {
-        const double L0 = L[(size_t)j * (c->k + 1)];
-        if (L0 < 0.0 && fma(dt, L0, gs[(size_t)j * (c->k + 1)]) <= 0.0) f |= 8u;
+        const double L0 = RV(L[(size_t)j * (c->k + 1)]);
+        if (L0 < 0.0 && fma(dt, L0, RV(gs[(size_t)j * (c->k + 1)])) <= 0.0) f |= 8u;
     }
     return f;
 }
@@ -741,10 +779,10 @@ static unsigned cfl_flags(const octx *c, const double *gs, const double *L, doub
 static double planted_leak = 0.0;
 
 /* one SSP-RK3 step (eq. RK3) preceded by the reconstruction (Sec. 3.2) */
-static unsigned step_one(const octx *c, double *g, double dt, double *work)
+static unsigned step_one(const octx *c, real *g, double dt, real *work)
 {
     const int P = c->P;
-    double *L = work, *g1 = work + P, *g2 = work + 2 * P;
+    real *L = work, *g1 = work + P, *g2 = work + 2 * P;
     unsigned f = 0;
     if (c->p.limiter) f |= limit_one(c, g);
     rhs_one(c, g, L, NULL);
@@ -809,6 +847,7 @@ static void project_one(const octx *c, int kind, const double *q, double *g)
     }
 }
 
+#ifndef ORC_TANGENT
 /* ------------------------------------------------------------------ */
 /* exported entry points (ctypes)                                      */
 /* ------------------------------------------------------------------ */
@@ -1129,3 +1168,4 @@ int orc_project_batch(const orc_params *p, int n_cells, int kind, const double *
     ctx_free(&c);
     return 0;
 }
+#endif /* ORC_TANGENT */

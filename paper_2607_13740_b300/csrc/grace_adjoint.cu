@@ -677,7 +677,7 @@ grace_status grace_param_grad_setup(grace_ctx *ctx, int group, int n_params, con
         set_error("grace_param_grad_setup: call grace_precompute first");
         return GRACE_ERR_ORDER;
     }
-    if (!(rel_step > 0.0)) rel_step = 1e-5;
+    const bool exact = !(rel_step > 0.0);
     Guard guard(ctx->device);
     Group &G = ctx->groups[group];
     if (G.dg.cell_alpha) {
@@ -687,35 +687,47 @@ grace_status grace_param_grad_setup(grace_ctx *ctx, int group, int n_params, con
     free_param_derivs(G);
     const DevGroup &dg = G.dg;
     const size_t nT = (size_t)dg.R * dg.P * dg.P;
-    double *tp = nullptr, *tm = nullptr;
-    cudaError_t e = cudaMalloc(&tp, nT * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&tm, nT * sizeof(double));
-    for (int i = 0; i < n_params && e == cudaSuccess; ++i) {
-        grace_group_desc dplus = G.desc, dminus = G.desc;
-        double *sp = param_slot(dplus, param_ids[i]), *sm = param_slot(dminus, param_ids[i]);
-        if (!sp) {
-            cudaFree(tp);
-            cudaFree(tm);
+    for (int i = 0; i < n_params; ++i)
+        if (param_ids[i] < 0 || param_ids[i] >= 24) {
             set_error("grace_param_grad_setup: parameter id out of range (0..23)");
             return GRACE_ERR_ARG;
         }
-        const double h = *sp != 0.0 ? rel_step * std::fabs(*sp) : rel_step;
-        *sp += h;
-        *sm -= h;
+    double *tp = nullptr, *tm = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!exact) {
+        e = cudaMalloc(&tp, nT * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&tm, nT * sizeof(double));
+    }
+    for (int i = 0; i < n_params && e == cudaSuccess; ++i) {
         ParamDeriv pd;
         pd.id = param_ids[i];
-        pd.step = h;
+        pd.step = 0.0;
         e = cudaMalloc(&pd.d_dT, nT * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&pd.d_qlo, sizeof(int) * dg.R * dg.P);
         if (e == cudaSuccess) e = cudaMalloc(&pd.d_qhi, sizeof(int) * dg.R * dg.P);
         if (e == cudaSuccess) e = cudaMalloc(&pd.d_prange, sizeof(int) * 2 * dg.R);
         G.dparams.push_back(pd);
         if (e != cudaSuccess) break;
-        e = launch_build_T(make_devgroup(dplus, G.d_edges), tp, ctx->stream);
-        if (e == cudaSuccess) e = launch_build_T(make_devgroup(dminus, G.d_edges), tm, ctx->stream);
-        if (e == cudaSuccess) {
-            central_diff_kernel<<<1024, 256, 0, ctx->stream>>>(nT, tp, tm, 0.5 / h, pd.d_dT);
-            e = cudaGetLastError();
+        if (exact) {
+            // forward mode through the FP64 precompute: the kernels' and breakage functions'
+            // derivatives (eqs. break, inte1, inte2, App. B; the Maxwellian probabilities of
+            // Sec. 4.5) carried through the same quadrature sums
+            double dbc = 0.0, dbf = 0.0;
+            maxwell_beta_derivs(G.desc, pd.id, &dbc, &dbf);
+            e = launch_build_dT(dg, pd.id, dbc, dbf, G.dparams.back().d_dT, ctx->stream);
+        } else {
+            grace_group_desc dplus = G.desc, dminus = G.desc;
+            double *sp = param_slot(dplus, pd.id), *sm = param_slot(dminus, pd.id);
+            const double h = *sp != 0.0 ? rel_step * std::fabs(*sp) : rel_step;
+            *sp += h;
+            *sm -= h;
+            G.dparams.back().step = h;
+            e = launch_build_T(make_devgroup(dplus, G.d_edges), tp, ctx->stream);
+            if (e == cudaSuccess) e = launch_build_T(make_devgroup(dminus, G.d_edges), tm, ctx->stream);
+            if (e == cudaSuccess) {
+                central_diff_kernel<<<1024, 256, 0, ctx->stream>>>(nT, tp, tm, 0.5 / h, G.dparams.back().d_dT);
+                e = cudaGetLastError();
+            }
         }
         if (e == cudaSuccess) e = launch_row_extents(dg, pd.d_dT, pd.d_qlo, pd.d_qhi, pd.d_prange, ctx->stream);
     }

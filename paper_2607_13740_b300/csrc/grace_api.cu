@@ -4,6 +4,7 @@
 #include <new>
 #include <string>
 
+#include "grace_dual.cuh"
 #include "grace_internal.h"
 #include "grace_tc_layout.cuh"
 
@@ -60,10 +61,25 @@ int n_functionals(const grace_group_desc &d)
     return n_if + d.n_bins * d.order_k;
 }
 
-static double maxwell_cdf_below(double vth, double dv)
+// P(v < vth) for the Maxwellian of relative speeds with rms dv (Sec. 4.5); S = double, or Dual
+// for its derivative along one parameter
+template <class S>
+static S maxwell_cdf_below(S vth, S dv)
 {
+    using std::erf;
+    using std::exp;
     const double pi = 3.141592653589793;
-    return std::erf(std::sqrt(1.5) * vth / dv) - vth * std::sqrt(6.0 / pi) / dv * std::exp(-1.5 * vth * vth / (dv * dv));
+    return erf(std::sqrt(1.5) * vth / dv) - vth * std::sqrt(6.0 / pi) / dv * exp(-1.5 * vth * vth / (dv * dv));
+}
+
+void maxwell_beta_derivs(const grace_group_desc &d, int id, double *dbeta_coag, double *dbeta_frag)
+{
+    *dbeta_coag = 0.0;
+    *dbeta_frag = 0.0;
+    if (d.coag_kind == GRACE_COAG_MAXWELL && (id == 0 || id == 1))
+        *dbeta_coag = maxwell_cdf_below(Dual(d.coag_p[1], id == 1 ? 1.0 : 0.0), Dual(d.coag_p[0], id == 0 ? 1.0 : 0.0)).der;
+    if (d.frag_kind == GRACE_FRAG_MAXWELL && (id == 8 || id == 9))
+        *dbeta_frag = -maxwell_cdf_below(Dual(d.frag_p[1], id == 9 ? 1.0 : 0.0), Dual(d.frag_p[0], id == 8 ? 1.0 : 0.0)).der;
 }
 
 DevGroup make_devgroup(const grace_group_desc &d, const double *d_edges)
@@ -94,8 +110,8 @@ DevGroup make_devgroup(const grace_group_desc &d, const double *d_edges)
         g.break_p[i] = d.break_p[i];
     }
     // beta_coag = P(v < v_b), beta_frag = P(v > v_f) for the Maxwellian of Sec. 4.5
-    if (d.coag_kind == GRACE_COAG_MAXWELL) g.beta_coag = maxwell_cdf_below(d.coag_p[1], d.coag_p[0]);
-    if (d.frag_kind == GRACE_FRAG_MAXWELL) g.beta_frag = 1.0 - maxwell_cdf_below(d.frag_p[1], d.frag_p[0]);
+    if (d.coag_kind == GRACE_COAG_MAXWELL) g.beta_coag = maxwell_cdf_below<double>(d.coag_p[1], d.coag_p[0]);
+    if (d.frag_kind == GRACE_FRAG_MAXWELL) g.beta_frag = 1.0 - maxwell_cdf_below<double>(d.frag_p[1], d.frag_p[0]);
     gauss_rule(g.Q, g.gs, g.gw);
     g.edges = d_edges;
     g.hbin = d_edges ? d_edges + g.N + 1 : nullptr;

@@ -214,6 +214,11 @@ int n_functionals(const grace_group_desc &d);
 
 // kernels (launchers)
 cudaError_t launch_build_T(const DevGroup &g, double *d_T, cudaStream_t st);
+// dT_r/dtheta for parameter id (0..7 coag_p, 8..15 frag_p, 16..23 break_p): the same quadrature on
+// dual numbers; dbeta_* the derivatives of the Maxwellian probabilities (maxwell_beta_derivs)
+cudaError_t launch_build_dT(const DevGroup &g, int param_id, double dbeta_coag, double dbeta_frag, double *d_dT,
+                            cudaStream_t st);
+void maxwell_beta_derivs(const grace_group_desc &d, int id, double *dbeta_coag, double *dbeta_frag);
 cudaError_t launch_row_extents(const DevGroup &g, const double *d_T, int *d_qlo, int *d_qhi,
                                int *d_prange, cudaStream_t st);
 // functional chunks (grid y) of the FP64 contractions for a batch of n_cells

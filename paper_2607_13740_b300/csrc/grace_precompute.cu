@@ -25,17 +25,24 @@ namespace {
 
 constexpr int kB = kKMax + 1;   // max coefficients per bin
 
-// Accumulates c * (contribution of outer bin l and inner bin m to F(x)).
-__device__ void point_block(const DevGroup &G, double x, int l, int m, double c, bool coag, bool frag,
-                            double *acc)
+// what a table entry stores: the value of a plain sum, the derivative part of a dual one
+__device__ __forceinline__ double deriv_or_value(double x) { return x; }
+__device__ __forceinline__ double deriv_or_value(const Dual &x) { return x.der; }
+
+// Accumulates c * (contribution of outer bin l and inner bin m to F(x)).  PV: the parameter view
+// (ParPlain for T, ParSeed for the exact dT/dtheta on dual numbers).
+template <class PV>
+__device__ void point_block(const DevGroup &G, const PV &pv, double x, int l, int m, double c, bool coag,
+                            bool frag, par_t<PV> *acc)
 {
+    using S = par_t<PV>;
     const double *e = G.edges;
     const int k = G.k, K1 = G.K1, Q = G.Q;
     const bool do_coag = coag && G.coag_kind != GRACE_COAG_NONE;
     const bool do_frag = frag && G.frag_kind != GRACE_FRAG_NONE;
     const double hl = e[l + 1] - e[l], xl = 0.5 * (e[l] + e[l + 1]);
     const double hm = e[m + 1] - e[m], xm = 0.5 * (e[m] + e[m + 1]);
-    double pu[kB], pv[kB];
+    double pu[kB], pw[kB];
 
     // positive flux: u in [x_min, x] (outer bin l, partial when x is inside it),
     // v in [x - u + x_min, v_max(u)] restricted to bin m (end bins A, B partial)
@@ -53,13 +60,13 @@ __device__ void point_block(const DevGroup &G, double x, int l, int m, double c,
                 for (int be = 0; be < Q; ++be) {
                     const double v = 0.5 * (va + vb) + 0.5 * (vb - va) * G.gs[be];
                     const double Wv = 0.5 * (vb - va) * G.gw[be];
-                    double t = 0.0;
-                    if (do_coag) t += dev_kcoag(G, u, v) / v;
-                    if (do_frag) t += dev_kfrag(G, u, v) * dev_mass_above(G, x, u, v) / (v * (u + v));
-                    const double wt = c * Wu * Wv * t;
-                    dev_legendre(k, 2.0 / hm * (v - xm), pv, nullptr);
+                    S t = 0.0;
+                    if (do_coag) t += kcoag_t(G, pv, u, v) / v;
+                    if (do_frag) t += kfrag_t(G, pv, u, v) * mass_above_t(G, pv, x, u, v) / (v * (u + v));
+                    const S wt = c * Wu * Wv * t;
+                    dev_legendre(k, 2.0 / hm * (v - xm), pw, nullptr);
                     for (int ia = 0; ia < K1; ++ia)
-                        for (int ib = 0; ib < K1; ++ib) acc[ia * K1 + ib] += wt * pu[ia] * pv[ib];
+                        for (int ib = 0; ib < K1; ++ib) acc[ia * K1 + ib] += wt * pu[ia] * pw[ib];
                 }
             }
         }
@@ -78,11 +85,11 @@ __device__ void point_block(const DevGroup &G, double x, int l, int m, double c,
                 for (int be = 0; be < Q; ++be) {
                     const double v = 0.5 * (va + vb) + 0.5 * (vb - va) * G.gs[be];
                     const double Wv = 0.5 * (vb - va) * G.gw[be];
-                    const double t = dev_kfrag(G, u, v) * dev_mass_below(G, x, u, v) / (v * (u + v));
-                    const double wt = c * Wu * Wv * t;
-                    dev_legendre(k, 2.0 / hm * (v - xm), pv, nullptr);
+                    const S t = kfrag_t(G, pv, u, v) * mass_below_t(G, pv, x, u, v) / (v * (u + v));
+                    const S wt = c * Wu * Wv * t;
+                    dev_legendre(k, 2.0 / hm * (v - xm), pw, nullptr);
                     for (int ia = 0; ia < K1; ++ia)
-                        for (int ib = 0; ib < K1; ++ib) acc[ia * K1 + ib] -= wt * pu[ia] * pv[ib];
+                        for (int ib = 0; ib < K1; ++ib) acc[ia * K1 + ib] -= wt * pu[ia] * pw[ib];
                 }
             }
         }
@@ -90,17 +97,18 @@ __device__ void point_block(const DevGroup &G, double x, int l, int m, double c,
 }
 
 // Gauss rule on [a, b] (inside bin j) of (c0 + c1 x^{2+alpha}) d_x phi_i(xi_j(x))
-__device__ double sub_interval(const DevGroup &G, int j, int i, double a, double b, double c0, double c1,
-                               double alpha, bool pw)
+template <class S>
+__device__ S sub_interval(const DevGroup &G, int j, int i, double a, double b, S c0, S c1, S alpha, bool pw)
 {
-    if (!(b > a)) return 0.0;
+    if (!(b > a)) return S(0.0);
     const double *e = G.edges;
     const double h = e[j + 1] - e[j], xc = 0.5 * (e[j] + e[j + 1]);
-    double P[kB], dP[kB], s = 0.0;
+    double P[kB], dP[kB];
+    S s = 0.0;
     for (int t = 0; t < G.Q; ++t) {
         const double x = 0.5 * (a + b) + 0.5 * (b - a) * G.gs[t];
         const double W = 0.5 * (b - a) * G.gw[t];
-        const double f = pw ? c0 + c1 * pow(x, 2.0 + alpha) : c0;
+        const S f = pw ? c0 + c1 * pow(x, 2.0 + alpha) : c0;
         dev_legendre(G.k, 2.0 / h * (x - xc), P, dP);
         s += W * f * (2.0 / h) * dP[i];
     }
@@ -109,37 +117,45 @@ __device__ double sub_interval(const DevGroup &G, int j, int i, double a, double
 
 // App. B: int_{I_j} [above(x) 1{u < x < u+v-x_min} - below(x) 1{x_min < x < u}] d_x phi_i dx
 // for one collision (u, v), as the paper's five sub-interval terms.
-__device__ double appB_J(const DevGroup &G, int j, int i, double u, double v)
+template <class PV>
+__device__ par_t<PV> appB_J(const DevGroup &G, const PV &pv, int j, int i, double u, double v)
 {
+    using S = par_t<PV>;
     const double ja = G.edges[j], jb = G.edges[j + 1], xmin = G.x_min;
-    const FragOutcome o = dev_outcome(G, u, v);
+    const auto o = outcome_t(G, pv, u, v);
     const double top = u + v - xmin;
-    double J = 0.0;
+    const S zero = 0.0;
+    S J = 0.0;
     if (o.mcut > xmin) {
-        const double a2 = 2.0 + o.alpha;
-        const double mc2 = pow(o.mcut, a2), xm2 = pow(xmin, a2);
-        const double cA = o.mfrag / (mc2 - xm2);   // A / (2 + alpha)
-        J += sub_interval(G, j, i, fmax(ja, u), fmin(jb, fmin(top, o.mcut)), cA * mc2, -cA, o.alpha, true);
-        J -= sub_interval(G, j, i, fmax(ja, xmin), fmin(jb, u), -cA * xm2, cA, o.alpha, true);
-        J += sub_interval(G, j, i, fmax(ja, o.mcut), fmin(jb, u), -cA * mc2, cA, o.alpha, true);
+        const S a2 = 2.0 + o.alpha;
+        const S mc2 = pow(o.mcut, a2), xm2 = pow(xmin, a2);
+        const S cA = o.mfrag / (mc2 - xm2);   // A / (2 + alpha)
+        J += sub_interval<S>(G, j, i, fmax(ja, u), fmin(jb, fmin(top, o.mcut)), cA * mc2, -cA, o.alpha, true);
+        J -= sub_interval<S>(G, j, i, fmax(ja, xmin), fmin(jb, u), -cA * xm2, cA, o.alpha, true);
+        J += sub_interval<S>(G, j, i, fmax(ja, o.mcut), fmin(jb, u), -cA * mc2, cA, o.alpha, true);
     } else {
-        J -= sub_interval(G, j, i, fmax(ja, xmin), fmin(jb, u), o.mfrag, 0.0, 0.0, false);
+        J -= sub_interval<S>(G, j, i, fmax(ja, xmin), fmin(jb, u), S(o.mfrag), zero, zero, false);
     }
     if (o.mleft > 0.0) {
-        J += sub_interval(G, j, i, fmax(ja, u), fmin(jb, fmin(top, o.mleft)), o.mleft, 0.0, 0.0, false);
+        J += sub_interval<S>(G, j, i, fmax(ja, u), fmin(jb, fmin(top, o.mleft)), S(o.mleft), zero, zero, false);
         if (o.mleft >= xmin)
-            J -= sub_interval(G, j, i, fmax(ja, o.mleft), fmin(jb, u), o.mleft, 0.0, 0.0, false);
+            J -= sub_interval<S>(G, j, i, fmax(ja, o.mleft), fmin(jb, u), S(o.mleft), zero, zero, false);
     }
     return J;
 }
 
-__device__ void appB_block(const DevGroup &G, int j, int i, int l, int m, double *acc)
+__device__ __forceinline__ bool is_zero(double x) { return x == 0.0; }
+__device__ __forceinline__ bool is_zero(const Dual &x) { return x.val == 0.0 && x.der == 0.0; }
+
+template <class PV>
+__device__ void appB_block(const DevGroup &G, const PV &pv, int j, int i, int l, int m, par_t<PV> *acc)
 {
+    using S = par_t<PV>;
     const double *e = G.edges;
     const int k = G.k, K1 = G.K1, Q = G.Q;
     const double hl = e[l + 1] - e[l], xl = 0.5 * (e[l] + e[l + 1]);
     const double hm = e[m + 1] - e[m], xm = 0.5 * (e[m] + e[m + 1]);
-    double pu[kB], pv[kB];
+    double pu[kB], pw[kB];
     for (int al = 0; al < Q; ++al) {
         const double u = xl + 0.5 * hl * G.gs[al];
         const double Wu = 0.5 * hl * G.gw[al];
@@ -150,28 +166,32 @@ __device__ void appB_block(const DevGroup &G, int j, int i, int l, int m, double
         for (int be = 0; be < Q; ++be) {
             const double v = 0.5 * (va + vb) + 0.5 * (vb - va) * G.gs[be];
             const double Wv = 0.5 * (vb - va) * G.gw[be];
-            const double base = Wu * Wv * dev_kfrag(G, u, v) / (v * (u + v));
-            if (base == 0.0) continue;
-            const double wt = base * appB_J(G, j, i, u, v);
-            dev_legendre(k, 2.0 / hm * (v - xm), pv, nullptr);
+            const S base = Wu * Wv * kfrag_t(G, pv, u, v) / (v * (u + v));
+            if (is_zero(base)) continue;
+            const S wt = base * appB_J(G, pv, j, i, u, v);
+            dev_legendre(k, 2.0 / hm * (v - xm), pw, nullptr);
             for (int ia = 0; ia < K1; ++ia)
-                for (int ib = 0; ib < K1; ++ib) acc[ia * K1 + ib] += wt * pu[ia] * pv[ib];
+                for (int ib = 0; ib < K1; ++ib) acc[ia * K1 + ib] += wt * pu[ia] * pw[ib];
         }
     }
 }
 
-__global__ void __launch_bounds__(128) build_T_kernel(DevGroup G, double *__restrict__ T)
+// one thread per (functional r, outer bin l, inner bin m): the K1 x K1 block of T_r, or with a
+// seeded parameter view the block of dT_r/dtheta (the derivative parts of the same sums)
+template <class PV>
+__device__ void build_block(const DevGroup &G, const PV &pv, double *__restrict__ out)
 {
+    using S = par_t<PV>;
     const int r = blockIdx.y;
     const int lm = blockIdx.x * blockDim.x + threadIdx.x;
     if (lm >= G.N * G.N || r >= G.R) return;
     const int l = lm / G.N, m = lm % G.N;
     const int K1 = G.K1, P = G.P;
-    double acc[kB * kB];
+    S acc[kB * kB];
     for (int t = 0; t < kB * kB; ++t) acc[t] = 0.0;
 
     if (r < G.n_if) {
-        point_block(G, G.edges[r + 1], l, m, 1.0, true, true, acc);
+        point_block(G, pv, G.edges[r + 1], l, m, 1.0, true, true, acc);
     } else {
         const int q = r - G.n_if, j = q / G.k, i = q % G.k + 1;
         const double h = G.edges[j + 1] - G.edges[j], xc = 0.5 * (G.edges[j] + G.edges[j + 1]);
@@ -179,13 +199,24 @@ __global__ void __launch_bounds__(128) build_T_kernel(DevGroup G, double *__rest
         for (int th = 0; th < G.Q; ++th) {
             dev_legendre(G.k, G.gs[th], P_, dP);
             const double c = G.gw[th] * dP[i];
-            point_block(G, xc + 0.5 * h * G.gs[th], l, m, c, true, !G.has_delta, acc);
+            point_block(G, pv, xc + 0.5 * h * G.gs[th], l, m, c, true, !G.has_delta, acc);
         }
-        if (G.has_delta) appB_block(G, j, i, l, m, acc);
+        if (G.has_delta) appB_block(G, pv, j, i, l, m, acc);
     }
     for (int a = 0; a < K1; ++a)
         for (int b = 0; b < K1; ++b)
-            T[((size_t)r * P + l * K1 + a) * P + m * K1 + b] = acc[a * K1 + b];
+            out[((size_t)r * P + l * K1 + a) * P + m * K1 + b] = deriv_or_value(acc[a * K1 + b]);
+}
+
+__global__ void __launch_bounds__(128) build_T_kernel(DevGroup G, double *__restrict__ T)
+{
+    build_block(G, ParPlain{G}, T);
+}
+
+__global__ void __launch_bounds__(128) build_dT_kernel(DevGroup G, int id, double dbeta_coag, double dbeta_frag,
+                                                       double *__restrict__ dT)
+{
+    build_block(G, ParSeed{G, id, dbeta_coag, dbeta_frag}, dT);
 }
 
 // first / one-past-last non-zero q of every row (r, p)
@@ -224,6 +255,14 @@ cudaError_t launch_build_T(const DevGroup &g, double *d_T, cudaStream_t st)
 {
     dim3 grid((g.N * g.N + 127) / 128, g.R);
     build_T_kernel<<<grid, 128, 0, st>>>(g, d_T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_dT(const DevGroup &g, int param_id, double dbeta_coag, double dbeta_frag, double *d_dT,
+                            cudaStream_t st)
+{
+    dim3 grid((g.N * g.N + 127) / 128, g.R);
+    build_dT_kernel<<<grid, 128, 0, st>>>(g, param_id, dbeta_coag, dbeta_frag, d_dT);
     return cudaGetLastError();
 }
 

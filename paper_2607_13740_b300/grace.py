@@ -214,7 +214,7 @@ class Context:
                 "folded")
         return dict(zip(keys, list(a)))
 
-    def param_grad_setup(self, param_ids, group: int = 0, rel_step: float = 1e-5):
+    def param_grad_setup(self, param_ids, group: int = 0, rel_step: float = 0.0):
         """Enables dJ/dtheta in Batch.adjoint for kernel parameters given by id:
         0..7 coag_p[i], 8..15 frag_p[i-8], 16..23 break_p[i-16]."""
         ids = np.ascontiguousarray(param_ids, dtype=np.int32)

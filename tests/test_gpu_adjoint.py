@@ -2,10 +2,10 @@
 
 Pins: L is a quadratic form, so (L(g+v) - L(g-v))/2 = J(g) v exactly; the
 oracle supplies that exact directional derivative.  The VJP is checked by the
-dot-product identity against the JVP; the trajectory adjoint against central
-differences of oracle trajectories (the FP64 reference gradient) and against
-torch.autograd.gradcheck; parameter gradients against central differences of
-oracle trajectories in the parameter.
+dot-product identity against the JVP; the trajectory adjoint and the parameter
+gradients against the oracle's forward-mode derivative build (the oracle on dual
+numbers: the exact derivative of its FP64 trajectory, limiter included), to 1e-10;
+and against torch.autograd.gradcheck.
 
 Tensor forms (TF32, BF16x3), with the forward bars of R15 (TOL = 2e-3 / 5e-5 of the
 oracle's term-magnitude scale S):
@@ -74,53 +74,66 @@ def _traj_setup(spec, n, seed):
 
 
 @pytest.mark.parametrize("ckpt", [1, 4, 20])
-def test_trajectory_adjoint_vs_oracle_directional_derivative(ckpt):
+def test_trajectory_adjoint_vs_oracle_tangent(ckpt):
+    """<lambda_0, v> of the adjoint equals <lambda_T, dg_T> with dg_T the oracle's exact derivative
+    of its trajectory along v (forward mode): two exact FP64 derivatives, equal to rounding."""
     spec = W.additive_spec(12, 2, 1e-3, 1e4).replace(limiter=0)
     n, steps, dt = 4, 12, 0.05
     o, g0, rng = _traj_setup(spec, n, 606)
     lamT = rng.normal(size=g0.shape)
-    # relative perturbation: empty tail bins (where dt times the collision rate is large) stay empty
     v = rng.uniform(-0.1, 0.1, size=g0.shape) * g0
     ctx = grace.Context([spec])
     b = ctx.batch(n)
     dtt = torch.full((n,), dt, dtype=torch.float64, device=DEV)
     lam0, _ = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, torch.as_tensor(lamT, device=DEV), ckpt)
-    lam0 = lam0.cpu().numpy()
-    eps = 1e-4
-    gp, _, _ = o.step(g0 + eps * v, dt, steps)
-    gm, _, _ = o.step(g0 - eps * v, dt, steps)
-    fd = ((gp - gm) / (2 * eps) * lamT).sum(axis=1)
-    ad = (lam0 * v).sum(axis=1)
-    assert np.allclose(ad, fd, rtol=1e-7, atol=1e-9 * np.abs(fd).max()), (ad, fd)
+    _, dg = o.tangent_step(g0, dt, steps, gdot=v)
+    ref = (dg * lamT).sum(axis=1)
+    ad = (lam0.cpu().numpy() * v).sum(axis=1)
+    assert np.allclose(ad, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max()), (ad, ref)
 
 
 def test_trajectory_adjoint_with_active_limiter():
-    """Limiter on (kinks away from the evaluation point): adjoint vs oracle central differences."""
+    """Limiter on (it rescales bins in every step): the adjoint's limiter term (envelope theorem at
+    the bin minimum) against the oracle's forward-mode derivative of the same trajectory."""
     spec = W.coupled_toy_spec(10, 2, flux_mode=0)
     n, steps, dt = 3, 10, 0.05
     o, g0, rng = _traj_setup(spec, n, 607)
     g0 = o.project(W.IC_EXP, [[1.0, 0.3, 0, 0], [2.0, 1.0, 0, 0], [0.5, 3.0, 0, 0]])
+    assert np.all(o.step(g0, dt, steps)[2] & 2)      # the limiter acted in every cell
     lamT = rng.normal(size=g0.shape)
     v = rng.uniform(-0.1, 0.1, size=g0.shape) * g0
     ctx = grace.Context([spec])
     b = ctx.batch(n)
     dtt = torch.full((n,), dt, dtype=torch.float64, device=DEV)
     lam0, _ = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, torch.as_tensor(lamT, device=DEV), 5)
-    eps = 1e-5
-    gp, _, _ = o.step(g0 + eps * v, dt, steps)
-    gm, _, _ = o.step(g0 - eps * v, dt, steps)
-    fd = ((gp - gm) / (2 * eps) * lamT).sum(axis=1)
+    _, dg = o.tangent_step(g0, dt, steps, gdot=v)
+    ref = (dg * lamT).sum(axis=1)
     ad = (lam0.cpu().numpy() * v).sum(axis=1)
-    assert np.allclose(ad, fd, rtol=1e-5, atol=1e-7 * np.abs(fd).max()), (ad, fd)
+    assert np.allclose(ad, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max()), (ad, ref)
 
 
-def test_parameter_gradients_vs_oracle_central_differences():
-    """dJ/dv_frag and dJ/dalpha of the coupled toy model (Sec. 4.5 physics), J = <lambda_T, g_T>."""
-    spec = W.coupled_toy_spec(10, 2, flux_mode=0)
-    n, steps, dt = 3, 8, 0.05
-    o, g0, rng = _traj_setup(spec, n, 608)
+PARAM_CASES = {
+    # Sec. 4.5 physics: dv_rms and v_bounce of the coagulation probability, dv_rms and v_frag of the
+    # fragmentation probability, the fragment index alpha (eqs. break, inte1, inte2, App. B)
+    "toy": (W.coupled_toy_spec(10, 2, flux_mode=0), [0, 1, 8, 9, 16], 0.05),
+    # the disk physics with one alpha_turb (ramp inside the grid): rho_s, alpha_turb, v_frag, alpha
+    "ballistic": (W.disk_spec(n_bins=10, order_k=2, cell_alpha=0, alpha=5e-6), [0, 11, 12, 16], None),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PARAM_CASES))
+def test_parameter_gradients_vs_oracle_tangent(name):
+    """dJ/dtheta, J = <lambda_T, g_T>, from the exact dT/dtheta (forward mode through the FP64
+    precompute) against <lambda_T, dg_T/dtheta> of the oracle's forward-mode trajectory."""
+    spec, ids, dt = PARAM_CASES[name]
+    n, steps = 3, 8
+    o = oracle.Oracle(spec)
+    rng = np.random.default_rng(608)
+    g0 = W.random_coefficients(spec, n, seed=609)
+    if dt is None:
+        # a quarter of the eq. (dt) bound of the initial state
+        dt = 0.25 / o.substep_counts(g0, 1.0, 1.0).max()
     lamT = rng.normal(size=g0.shape)
-    ids = [9, 16]                      # frag_p[1] = v_f, break_p[0] = alpha
     ctx = grace.Context([spec])
     ctx.param_grad_setup(ids)
     b = ctx.batch(n)
@@ -128,17 +141,29 @@ def test_parameter_gradients_vs_oracle_central_differences():
     _, dth = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, torch.as_tensor(lamT, device=DEV), 4,
                        param_grads=True)
     dth = dth.cpu().numpy()
-    for col, (field, idx) in enumerate([("frag_p", 1), ("break_p", 0)]):
-        base = list(getattr(spec, field))
-        h = 1e-5 * abs(base[idx])
-        vals = []
-        for sgn in (+1, -1):
-            p = list(base)
-            p[idx] = base[idx] + sgn * h
-            gT, _, _ = oracle.Oracle(spec.replace(**{field: tuple(p)})).step(g0, dt, steps)
-            vals.append((gT * lamT).sum(axis=1))
-        fd = (vals[0] - vals[1]) / (2 * h)
-        assert np.allclose(dth[:, col], fd, rtol=2e-4, atol=1e-6 * np.abs(fd).max()), (field, dth[:, col], fd)
+    for col, pid in enumerate(ids):
+        _, dg = o.tangent_step(g0, dt, steps, param_id=pid)
+        ref = (dg * lamT).sum(axis=1)
+        assert np.abs(ref).max() > 0.0, pid
+        assert np.allclose(dth[:, col], ref, rtol=1e-10, atol=1e-11 * np.abs(ref).max()), (pid, dth[:, col], ref)
+
+
+def test_finite_difference_tables_agree_with_the_exact_ones():
+    """The central-difference dT/dtheta (rel_step > 0, kept for cross-checks) gives the same
+    gradients as the exact tables to its truncation error."""
+    spec, ids, dt = PARAM_CASES["toy"]
+    n, steps = 3, 6
+    g0 = W.random_coefficients(spec, n, seed=610)
+    lamT = torch.as_tensor(np.random.default_rng(611).normal(size=g0.shape), device=DEV)
+    out = []
+    for rel in (0.0, 1e-6):
+        ctx = grace.Context([spec])
+        ctx.param_grad_setup(ids, rel_step=rel)
+        b = ctx.batch(n)
+        dtt = torch.full((n,), dt, dtype=torch.float64, device=DEV)
+        _, dth = b.adjoint(torch.as_tensor(g0, device=DEV), dtt, steps, lamT, 3, param_grads=True)
+        out.append(dth.cpu().numpy())
+    assert np.allclose(out[1], out[0], rtol=1e-6, atol=1e-8 * np.abs(out[0]).max())
 
 
 def test_autograd_function_gradcheck():

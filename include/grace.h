@@ -250,7 +250,7 @@ GRACE_API grace_status grace_rhs_species(grace_batch *batch, int n_species, cons
 GRACE_API grace_status grace_step_species(grace_batch *batch, int n_species, double *gs, const double *dt,
                                           int n_steps, double *mass, unsigned char *flags);
 
-/* Operator-split coupling to a hydrodynamics code (Sec. 5.2)/* Operator-split coupling to a hydrodynamics code (Sec. 5.2): advances every cell by its
+/* Operator-split coupling to a hydrodynamics code (Sec. 5.2): advances every cell by its
    own interval dt_hydro[c] (device [n_cells]) in sub-steps sized by the eq. (dt)
    positivity bound.  The FP64 RHS at the start gives each cell's bound
    B_c = min over bins losing mass (L_j^0 < 0) of g_j^0 / |L_j^0| and its count

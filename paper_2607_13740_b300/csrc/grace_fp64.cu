@@ -17,7 +17,8 @@ namespace {
 
 // CPW cells per warp: 32 (one lane per cell), or 8 for groups whose 32-cell tile would not fit in
 // shared memory (P > 800 coefficients, e.g. N = 200 bins of degree 4): then four lanes share a cell,
-// each summing every fourth q of a row, and the row sums are combined with shuffles.
+// each summing every fourth q of a row, and the row sums are combined with shuffles.  CPW = 1 for
+// batches of a few cells (single-cell studies): the whole warp shares each row, reading T coalesced.
 template <int CPW>
 __global__ void __launch_bounds__(128) contract_fp64_kernel(
     const double *__restrict__ T, const int *__restrict__ qlo, const int *__restrict__ qhi,
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(128) contract_fp64_kernel(
 // with g is shared by the species; 32 cells per warp as above, the S outer tiles next to g in shared
 // memory.  F layout [S][cells][R].
 constexpr int kMaxSpecies = 4;
+constexpr int kFewCells = 4;   // batches up to this size take one warp per cell
 
 __global__ void __launch_bounds__(128) contract_fp64_species_kernel(
     const double *__restrict__ T, const int *__restrict__ qlo, const int *__restrict__ qhi,
@@ -159,6 +161,20 @@ cudaError_t launch_contract_fp64(const DevGroup &g, const double *d_T, const int
                                  const int *d_prange, const double *d_g, int n_cells, double *d_F,
                                  cudaStream_t st)
 {
+    if (n_cells <= kFewCells) {
+        // one warp per cell and block; functionals spread over blockIdx.y for about 8 warps per SM
+        const size_t smem = (size_t)g.P * sizeof(double);
+        cudaError_t e = cudaFuncSetAttribute(contract_fp64_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, n_sm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        const int chunks = std::max(1, std::min(g.R, (8 * n_sm + n_cells - 1) / std::max(n_cells, 1)));
+        contract_fp64_kernel<1><<<dim3(std::max(n_cells, 1), chunks), 32, smem, st>>>(d_T, d_qlo, d_qhi, d_prange, g.R,
+                                                                                      g.P, d_g, n_cells, d_F);
+        return cudaGetLastError();
+    }
     const bool wide = (size_t)g.P * 32 * sizeof(double) > 200 * 1024;   // 32-cell tile too large
     const int cpw = wide ? 8 : 32;
     const size_t per_warp = (size_t)g.P * cpw * sizeof(double);

@@ -706,8 +706,14 @@ def run_toy(args):
             means = coef[:, 0]
             ok = sel & (means > 0)
             slope = float(np.polyfit(np.log(xc[ok]), np.log(means[ok]), 1)[0]) if ok.sum() >= 2 else None
+            # local slopes between neighbouring bin means over the fit range (is it one power law?)
+            loc = np.diff(np.log(np.where(means > 0, means, np.nan))) / np.diff(np.log(xc))
+            mid = np.sqrt(xc[1:] * xc[:-1])
+            in_fit = (mid >= 1e-5) & (mid <= 1e-2) & np.isfinite(loc)
             rec[f"{tau:g}"] = {"slope": slope, "mass": float((h * means).sum()), "flags": int(flags.item()),
-                               "finite": bool(np.isfinite(coef).all())}
+                               "finite": bool(np.isfinite(coef).all()),
+                               "local_slope_range": [float(loc[in_fit].min()), float(loc[in_fit].max())]
+                               if in_fit.any() else None}
             states[(N, k, tau)] = (e, coef)
         torch.cuda.synchronize()
         out[f"N{N}_k{k}"] = {"tau": rec, "steps": int(round(t / dt_val)), "gpu_wall_s": time.time() - tw}

@@ -235,7 +235,7 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_disk(args):
+def run_disk(args, emit=True):
     """Disk workload (per-cell alpha_turb, coagulation + fragmentation, N = 60): the node-space
     path in FP64 (a bounded 2,048 cells) or in a tensor-core form (262,144 cells by default:
     fixed pairs on tcgen05, partial entries in FP32); one JSON line like the headline's."""
@@ -358,10 +358,12 @@ def run_disk(args):
         "max_rel_err_vs_fp64_rhs": acc, "finite": bool(torch.isfinite(g).all().item()),
         "clocks": sampler.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_adjoint(args):
+def run_adjoint(args, emit=True):
     """Adjoint workload: 4,096 cells of the disk physics (ballistic-turbulent kernels, fragmentation
     ramp, power-law fragments up to the larger collider plus the remnant) with one shared
     alpha_turb = 1e-3 on an N = 40, k = 2 grid of grain radii 1e-4 .. 1e2 cm; per-cell MRN initial
@@ -474,10 +476,12 @@ def run_adjoint(args):
         "dJ_dtheta": {"v_frag": float(dth[:, 0].sum() + dth[:, 1].sum()), "fragment_exponent": float(dth[:, 2].sum())},
         "clocks": sampler.summary(), **res,
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_uneven(args):
+def run_uneven(args, emit=True):
     """Uneven batch: cells of many groups (N ~ U{16..80}, k ~ U{0..3}, constant or additive
     kernel, per-cell rate scale) stepped together in the bf16x3 form: per-group launch sequences
     and the grouped step (one multi-group contraction and one K-c launch per stage), each direct
@@ -581,7 +585,9 @@ def run_uneven(args):
                   "mma_per_tile_max": max(t["mma_per_tile"] for t in tiles),
                   "folded_groups": sum(t["folded"] for t in tiles)},
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_eoc(args):
@@ -748,6 +754,43 @@ def run_toy(args):
     print(json.dumps(line), flush=True)
 
 
+def run_legs(args):
+    """Short runs of the other configurations after the headline (N = 1 only), so that their
+    figures come from the same command: the uneven batch (grouped step, graph-replayed, 3 steps),
+    the adjoint leg (bf16x3, no FP64 comparison) and the disk workload (65,536 cells, k = 2,
+    bf16x3, 3 steps).  Each leg's own JSON line is summarised; a failing leg records its error and
+    never affects the headline."""
+    import copy
+    import torch
+    out = {}
+    base = copy.copy(args)
+    base.steps, base.cells, base.precision, base.variants, base.forms = None, None, None, None, None
+    plans = [
+        ("uneven", run_uneven, {"steps": 3, "variants": "grouped_graph,grouped"}),
+        ("adjoint", run_adjoint, {"skip_fp64_compare": True}),
+        ("disk", run_disk, {"cells": 65536, "steps": 3, "order": 2, "precision": "bf16x3"}),
+    ]
+    for name, fn, over in plans:
+        a = copy.copy(base)
+        for k, v in over.items():
+            setattr(a, k, v)
+        t0 = time.time()
+        try:
+            ln = fn(a, emit=False)
+            keep = {k: ln.get(k) for k in ("metric", "value", "unit", "ms_per_step", "dtype", "roofline", "clocks")}
+            keep["workload"] = (ln.get("config") or {}).get("workload")
+            if name == "adjoint":
+                keep["dJ_dtheta"] = ln.get("dJ_dtheta")
+                keep["adjoint_over_forward"] = ln.get("adjoint_over_forward")
+            out[name] = keep
+        except Exception as exc:          # a leg never takes the headline down
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        out[name]["wall_s"] = time.time() - t0
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -777,6 +820,8 @@ def main():
                          "with a per-cell turbulence strength (node-space path); uneven: many groups in one batch; "
                          "adjoint: checkpointed adjoint of 200 steps with parameter gradients")
     ap.add_argument("--order", type=int, default=2, help="disk workload: Legendre degree k (1..3)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="additive workload: skip the short uneven / adjoint / disk legs reported under 'legs'")
     ap.add_argument("--variants", default=None,
                     help="uneven workload: comma-separated subset of per_group,per_group_graph,grouped,grouped_graph")
     args = ap.parse_args()
@@ -1075,6 +1120,8 @@ def main():
         "forms": forms_out,
         "peaks": peaks,
     }
+    if rank == 0 and world == 1 and not args.no_legs:
+        line["legs"] = run_legs(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

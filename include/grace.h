@@ -98,7 +98,7 @@ enum { GRACE_FLAG_NEGATIVE_MEAN = 1,  /* a cell mean g_j^0 went negative (eq. dt
 
 /* One (grid, order, physics) combination shared by the cells of a group. */
 typedef struct {
-    int n_bins;       /* N >= 2: logarithmic bins on [x_min, x_max] (Sec. 3.1)          */
+    int n_bins;       /* N >= 2 bins on [x_min, x_max]: logarithmic (Sec. 3.1) or edges  */
     int order_k;      /* k in 0..4: Legendre degree (eq. 2.3); 0..3 with cell_alpha      */
     int quad_q;       /* Gauss points per quadrature piece; 0 means k+1 (Sec. 3.3), <= 16 */
     int flux_mode;    /* GRACE_FLUX_*                                                   */
@@ -116,6 +116,9 @@ typedef struct {
                          by grace_batch_cell_params; coag_kind must be BALLISTIC, frag_kind NONE
                          or BALLISTIC with the same p0..p2, p4..p6 as coagulation; 0: per group */
     int reserved_;    /* zero */
+    const double *edges;  /* host, n_bins + 1 strictly increasing finite bin edges with
+                             edges[0] = x_min and edges[n_bins] = x_max, copied by grace_setup
+                             (the pointer is not kept); NULL: the logarithmic grid of Sec. 3.1 */
 } grace_group_desc;
 
 GRACE_API int grace_version(void);

@@ -28,6 +28,7 @@ class OrcParams(ctypes.Structure):
         ("x_min", ctypes.c_double), ("x_max", ctypes.c_double),
         ("coag_p", ctypes.c_double * 8), ("frag_p", ctypes.c_double * 8),
         ("break_p", ctypes.c_double * 8),
+        ("edges", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -88,6 +89,10 @@ def params(spec) -> OrcParams:
         arr = getattr(p, name)
         for i, v in enumerate(vals):
             arr[i] = v
+    if getattr(spec, "edges", None) is not None:
+        buf = (ctypes.c_double * len(spec.edges))(*spec.edges)
+        p.edges = ctypes.cast(buf, _D)
+        p._edges_buf = buf          # alive as long as the parameter block
     return p
 
 

@@ -91,6 +91,7 @@ typedef struct {
     double coag_p[8];
     double frag_p[8];
     double break_p[8];
+    const double *edges;  /* n_bins + 1 bin edges from x_min to x_max, or NULL: the log grid */
 } orc_params;
 
 typedef struct {
@@ -178,6 +179,8 @@ static void ctx_betas(octx *c)
         c->beta_frag = maxwell_above(c->frag_p[1], c->frag_p[0]);
 }
 
+static void ctx_free(octx *c) { free(c->e); c->e = NULL; }
+
 static int ctx_init(octx *c, const orc_params *p)
 {
     memset(c, 0, sizeof(*c));
@@ -190,11 +193,19 @@ static int ctx_init(octx *c, const orc_params *p)
     c->P = c->N * (c->k + 1);
     c->e = (double *)malloc(sizeof(double) * (c->N + 1));
     if (!c->e) return -2;
-    /* logarithmic grid (Sec. 3.1) */
-    for (int j = 0; j <= c->N; ++j)
-        c->e[j] = p->x_min * pow(p->x_max / p->x_min, (double)j / c->N);
-    c->e[0] = p->x_min;
-    c->e[c->N] = p->x_max;
+    if (p->edges) {
+        /* caller's grid: strictly increasing from x_min to x_max */
+        for (int j = 0; j <= c->N; ++j) c->e[j] = p->edges[j];
+        if (c->e[0] != p->x_min || c->e[c->N] != p->x_max) { ctx_free(c); return -1; }
+        for (int j = 0; j < c->N; ++j)
+            if (!(c->e[j + 1] > c->e[j])) { ctx_free(c); return -1; }
+    } else {
+        /* logarithmic grid (Sec. 3.1) */
+        for (int j = 0; j <= c->N; ++j)
+            c->e[j] = p->x_min * pow(p->x_max / p->x_min, (double)j / c->N);
+        c->e[0] = p->x_min;
+        c->e[c->N] = p->x_max;
+    }
     orc_gauss(c->Q, c->s, c->w);
     for (int i = 0; i < 8; ++i) {
         c->coag_p[i] = p->coag_p[i];
@@ -205,7 +216,6 @@ static int ctx_init(octx *c, const orc_params *p)
     return 0;
 }
 
-static void ctx_free(octx *c) { free(c->e); c->e = NULL; }
 
 /* ------------------------------------------------------------------ */
 /* physics: kernels (Secs. 4.2-4.5) and breakage mass functions         */

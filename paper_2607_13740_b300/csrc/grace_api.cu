@@ -158,6 +158,13 @@ static grace_status validate(const grace_group_desc &d, int idx)
     if (d.frag_kind != GRACE_FRAG_NONE && d.break_kind == GRACE_BREAK_POWERLAW_REMNANT && d.break_p[0] == -2.0)
         return bad("power-law index -2 is not supported");
     if (d.limiter != 0 && d.limiter != 1) return bad("limiter must be 0 or 1");
+    if (d.edges) {
+        if (d.edges[0] != d.x_min || d.edges[d.n_bins] != d.x_max)
+            return bad("edges[0] and edges[n_bins] must equal x_min and x_max");
+        for (int j = 0; j < d.n_bins; ++j)
+            if (!(d.edges[j + 1] > d.edges[j]) || !std::isfinite(d.edges[j + 1]))
+                return bad("edges must be finite and strictly increasing");
+    }
     return GRACE_OK;
 }
 
@@ -241,13 +248,18 @@ grace_status grace_setup(grace_ctx **out, int n_groups, const grace_group_desc *
         for (int i = 0; i < n_groups; ++i) {
             Group &G = ctx->groups[i];
             G.desc = groups[i];
+            G.desc.edges = nullptr;   // the caller's array is copied, not kept
             const int N = G.desc.n_bins;
             G.h_edges.resize(N + 1);
-            // logarithmic grid of Sec. 3.1
-            for (int j = 0; j <= N; ++j)
-                G.h_edges[j] = G.desc.x_min * std::pow(G.desc.x_max / G.desc.x_min, (double)j / N);
-            G.h_edges[0] = G.desc.x_min;
-            G.h_edges[N] = G.desc.x_max;
+            if (groups[i].edges) {
+                for (int j = 0; j <= N; ++j) G.h_edges[j] = groups[i].edges[j];
+            } else {
+                // logarithmic grid of Sec. 3.1
+                for (int j = 0; j <= N; ++j)
+                    G.h_edges[j] = G.desc.x_min * std::pow(G.desc.x_max / G.desc.x_min, (double)j / N);
+                G.h_edges[0] = G.desc.x_min;
+                G.h_edges[N] = G.desc.x_max;
+            }
             // one allocation: edges (N+1), h (N), 1/h (N) in FP64, then 1/h (N) and h (N) in FP32
             std::vector<double> tab(3 * (size_t)N + 1 + N, 0.0);
             for (int j = 0; j <= N; ++j) tab[j] = G.h_edges[j];

@@ -39,6 +39,7 @@ class GroupDesc(ctypes.Structure):
         ("coag_p", ctypes.c_double * 8), ("frag_p", ctypes.c_double * 8),
         ("break_p", ctypes.c_double * 8),
         ("cell_alpha", ctypes.c_int), ("reserved_", ctypes.c_int),
+        ("edges", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -127,6 +128,10 @@ def group_desc(spec: W.GroupSpec) -> GroupDesc:
         arr = getattr(d, name)
         for i, v in enumerate(getattr(spec, name)):
             arr[i] = v
+    if spec.edges is not None:
+        buf = (ctypes.c_double * len(spec.edges))(*spec.edges)
+        d.edges = ctypes.cast(buf, ctypes.POINTER(ctypes.c_double))
+        d._edges_buf = buf          # alive as long as the descriptor
     return d
 
 
@@ -170,10 +175,12 @@ class Context:
         L = load()
         self.specs = list(specs) if isinstance(specs, (list, tuple)) else [specs]
         self.device = device
-        arr = (GroupDesc * len(self.specs))(*[group_desc(s) for s in self.specs])
+        descs = [group_desc(s) for s in self.specs]    # hold their edge buffers through the setup call
+        arr = (GroupDesc * len(descs))(*descs)
         h = _VP()
         torch.cuda.set_device(device)
         _check(L.grace_setup(ctypes.byref(h), len(self.specs), arr, device), "grace_setup")
+        del descs
         self._h = h
         self.set_stream()
         mask = 0

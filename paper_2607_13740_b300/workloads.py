@@ -47,6 +47,7 @@ class GroupSpec:
     quad_q: int = 0
     limiter: int = 1
     cell_alpha: int = 0     # 1: the ballistic kernels take alpha_turb per cell (non-separable)
+    edges: tuple = None     # n_bins + 1 bin edges from x_min to x_max, or None: the log grid
 
     @property
     def n_coef(self) -> int:

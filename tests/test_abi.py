@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_2607_13740_b300 import build, grace, workloads as W
@@ -122,3 +124,21 @@ def test_arm_wait_timeout_rejects_bad_limits():
         grace.arm_wait_timeout(0)
     with pytest.raises(grace.GraceError):
         grace.arm_wait_timeout(5_000_000_000)
+
+
+@pytest.mark.parametrize("bad", ["decreasing", "ends", "nan"])
+def test_setup_rejects_invalid_edges(lib, bad):
+    """Caller-supplied bin edges are validated on the host before any CUDA call."""
+    spec = W.additive_spec(6, 1, 1e-2, 1e2)
+    e = list(spec.x_min * (spec.x_max / spec.x_min) ** (np.arange(7) / 6))
+    e[0], e[-1] = spec.x_min, spec.x_max
+    if bad == "decreasing":
+        e[2], e[3] = e[3], e[2]
+    elif bad == "ends":
+        e[-1] = 2e2
+    else:
+        e[4] = float("nan")
+    d = grace.group_desc(spec.replace(edges=tuple(e)))
+    st, h = _setup(lib, d)
+    assert st == 1 and not h.value
+    assert "edges" in lib.grace_last_error().decode()

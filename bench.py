@@ -766,6 +766,55 @@ def run_toy(args):
     print(json.dumps(line), flush=True)
 
 
+def run_species(args, emit=True):
+    """Species of mixed grains (Sec. 5.3): the batched additive workload's 65,536 cells split into
+    S = 2 species (a tracer holding the two smallest bins, and the rest), stepped with
+    grace_step_species in a tensor form (default bf16x3): one tcgen05 pass over T per stage for
+    both species.  CUDA events around one call of K steps; one JSON line (cell-steps/s counts
+    cells, each carrying S distributions)."""
+    import torch
+    from paper_2607_13740_b300 import grace, workloads as W
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    form = {"fp64": grace.FP64, "tf32": grace.TF32, "bf16x3": grace.BF16X3}[args.precision or "bf16x3"]
+    wl = W.batched_additive(n_cells=args.cells or 65536)
+    n, steps = wl.n_cells, args.steps or 10
+    ctx = grace.Context([wl.spec], local, precisions=(grace.FP64, form) if form != grace.FP64 else (grace.FP64,))
+    b = ctx.batch(n)
+    g = b.project(wl.ic_kind, wl.ic_params)
+    tracer = torch.zeros_like(g).reshape(n, wl.spec.n_bins, -1)
+    tracer[:, :2, :] = g.reshape(n, wl.spec.n_bins, -1)[:, :2, :]
+    tracer = tracer.reshape(n, -1)
+    gs0 = torch.stack([tracer, g - tracer]).contiguous()
+    dt = torch.as_tensor(wl.dt, device=dev)
+    gs = gs0.clone()
+    for _ in range(args.warmup):
+        b.step_species(gs, dt, 1, form)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    gs.copy_(gs0)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        b.step_species(gs, dt, steps, form)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fname = {grace.FP64: "fp64", grace.TF32: "tf32", grace.BF16X3: "bf16x3"}[form]
+    line = {
+        "metric": "species cell-steps/s (S = 2 distributions per cell, N=40, k=2)", "value": n * steps / (ms / 1e3),
+        "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "dtype": fname, "data": "synthetic",
+        "config": {"workload": f"species2_{n}cells_N40_k2", "cells": n, "species": 2,
+                   "split": "tracer = the two smallest bins, the rest", "timing": f"one grace_step_species call of {steps} steps"},
+        "finite": bool(torch.isfinite(gs).all().item()), "clocks": clk.summary(),
+    }
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
 def run_legs(args):
     """Short runs of the other configurations after the headline (N = 1 only), so that their
     figures come from the same command: the uneven batch (grouped step, graph-replayed, 3 steps),
@@ -781,6 +830,7 @@ def run_legs(args):
         ("uneven", run_uneven, {"steps": 3, "variants": "grouped_graph,grouped"}),
         ("adjoint", run_adjoint, {"skip_fp64_compare": True}),
         ("disk", run_disk, {"cells": 65536, "steps": 3, "order": 2, "precision": "bf16x3"}),
+        ("species", run_species, {"steps": 10, "precision": "bf16x3"}),
     ]
     for name, fn, over in plans:
         a = copy.copy(base)
@@ -827,7 +877,8 @@ def main():
     ap.add_argument("--toy-tau", default=None, help="toy workload: comma-separated output times (default 1,10,100)")
     ap.add_argument("--toy-dt", type=float, default=0.05, help="toy workload: time step")
     ap.add_argument("--toy-ref-n", type=int, default=300, help="toy workload: bins of the k = 4 reference")
-    ap.add_argument("--workload", default="additive", choices=["additive", "disk", "uneven", "adjoint", "eoc", "toy"],
+    ap.add_argument("--workload", default="additive",
+                    choices=["additive", "disk", "uneven", "adjoint", "eoc", "toy", "species"],
                     help="additive: the batched additive-kernel headline; disk: coagulation + fragmentation "
                          "with a per-cell turbulence strength (node-space path); uneven: many groups in one batch; "
                          "adjoint: checkpointed adjoint of 200 steps with parameter gradients")
@@ -848,6 +899,9 @@ def main():
         return
     if args.workload == "toy":
         return run_toy(args)
+    if args.workload == "species":
+        run_species(args)
+        return
     if args.workload == "eoc":
         run_eoc(args)
         return

@@ -240,18 +240,23 @@ GRACE_API grace_status grace_batch_set_grouped(grace_batch *batch, int enable);
    outer collider's slot and g in its partner's (the library's reading; the paper states no
    equations).  sum_s L_s = L[g], and each species' mass is conserved by conservative fluxes.
    gs, Ls: device, [n_species][n_cells][P] (species-major, each species a packed state of the
-   batch).  FP64 only; batches of one group in caller order without per-cell kernel parameters
-   (GRACE_ERR_UNSUPPORTED otherwise).  The first call allocates a workspace (synchronises). */
-GRACE_API grace_status grace_rhs_species(grace_batch *batch, int n_species, const double *gs, double *Ls);
+   batch).  precision: GRACE_FP64 (one pass over T on the CUDA cores, the partner's row sums shared
+   by the species), or GRACE_TF32 / GRACE_BF16X3 (precomputed for the group): one tcgen05 pass over
+   T as built with the cells' total as the A operand, each species contracting the accumulator in
+   the epilogue; the reduced-precision bars of those forms apply.  Batches of one group in caller
+   order without per-cell kernel parameters (GRACE_ERR_UNSUPPORTED otherwise).  The first call
+   (and the first of each tensor form) allocates a workspace and plans tiles (synchronises). */
+GRACE_API grace_status grace_rhs_species(grace_batch *batch, int n_species, const double *gs, double *Ls,
+                                         int precision);
 
 /* n_steps SSP-RK3 steps (eq. RK3) of the species, in place on gs ([n_species][n_cells][P],
    device): every stage forms the total of its input, then each species' rate and stage update;
    the scaling limiter acts on each species (once per step, as grace_step).  mass (device
    [n_species][n_cells] or NULL) receives each species' M_1 after the last step; flags (device
    [n_cells] or NULL) the OR of the status bits of the cell's species, the mass-drift bit from the
-   cell's total M_1.  FP64; the restrictions and workspace of grace_rhs_species. */
+   cell's total M_1.  precision, restrictions and workspace as grace_rhs_species. */
 GRACE_API grace_status grace_step_species(grace_batch *batch, int n_species, double *gs, const double *dt,
-                                          int n_steps, double *mass, unsigned char *flags);
+                                          int n_steps, int precision, double *mass, unsigned char *flags);
 
 /* Operator-split coupling to a hydrodynamics code (Sec. 5.2): advances every cell by its
    own interval dt_hydro[c] (device [n_cells]) in sub-steps sized by the eq. (dt)

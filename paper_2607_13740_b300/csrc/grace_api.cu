@@ -181,6 +181,7 @@ static void free_group(Group &G)
     G.d_qlo = G.d_qhi = G.d_prange = nullptr;
     for (auto &t : G.tc) free_tc_tiles(t);
     for (auto &t : G.tcv) free_tc_tiles(t);
+    for (auto &t : G.tcs) free_tc_tiles(t);
     free_param_derivs(G);
 }
 

@@ -94,6 +94,7 @@ struct Group {
     long long nnz = 0;            // structural non-zeros of T (all rows)
     TcTiles tc[3];                // indexed by grace_precision
     TcTiles tcv[3];               // VJP tiles (built on the first tensor-form VJP / adjoint call)
+    TcTiles tcs[3];               // species tiles (T unfolded; built on the first tensor-form species call)
     NcTables nc;                  // cell_alpha groups: node-space tables instead of T
     std::vector<ParamDeriv> dparams;
 };
@@ -350,7 +351,15 @@ cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const Tc
 
 // tensor-core path
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);
-grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st);
+grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st,
+                                 bool unfolded_only = false);
+// tiles of T as built (no fold) for the species contraction, into G.tcs[prec]
+grace_status build_species_tiles(Group &G, int prec, cudaStream_t st);
+// species of mixed grains: F_s[c, r] = sum_p ghat_{s,p} sum_q That_r[p, q] ghat_q for every species, the
+// cells' total in opA (the A operand), the species' scaled coefficients in d_gsp
+// ([S][cell tile][k_pad][128] FP32); F_s in the tile layout at d_F32 + s [cell tiles][R][128]
+cudaError_t launch_contract_tc_species(const DevGroup &g, const TcTiles &t, int prec, const void *opA, int n_cells,
+                                       const float *d_gsp, int n_species, float *d_F32, int *d_err, cudaStream_t st);
 grace_status build_nc_tc_tiles(Group &G, int prec, cudaStream_t st);
 grace_status build_vjp_tiles(Group &G, int prec, cudaStream_t st);
 // multi-group contraction (uneven batches): the flux functionals of every part of a batch in one

@@ -127,6 +127,11 @@ struct TcParams {
     // multi-group mode: per-group descriptors and the work items (group, cell tile)
     const struct TcGroupDesc *groups;
     const int2 *items;
+    // species mode: the species' scaled coefficients ghat_s in FP32, [S][cell tile][gsp_kpad][128]
+    // (A columns, one 128-cell column per coefficient), and F_s at F + s f_sstride
+    const float *gsp;
+    long long gsp_sstride, f_sstride;
+    int gsp_kpad, n_species;
     // failure detection: every mbarrier wait gives up after wait_cycles; withhold_b != 0 (a
     // test of that path only) issues no B copies, so the MMA issuer's first wait runs out
     long long wait_cycles;
@@ -146,7 +151,8 @@ struct TcGroupDesc {
 
 // contraction modes: flux functionals, node-space functionals (per-cell kernels), VJP, flux
 // functionals of many groups in one launch (uneven batches)
-constexpr int kModeF = 0, kModeNC = 1, kModeVJP = 2, kModeMulti = 3;
+constexpr int kModeF = 0, kModeNC = 1, kModeVJP = 2, kModeMulti = 3, kModeSpecies = 4;
+constexpr int kMaxSpeciesTc = 4;   // species of mixed grains per launch
 
 // the parameters of one work item: its group's tiles, operands and output, its tile range
 struct ItemCtx {
@@ -424,6 +430,43 @@ __device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_
                 }
                 Facc[m0 + gg] += s0 + s1;
             }
+        }
+    }
+}
+
+// Epilogue of a species tile (mixtures of Sec. 5.3): the accumulator holds, for the cell's total
+// g in the partner slot, Y[c, (r, p)] = sum_q ghat_q That_r[p, q] (T as built, p the outer
+// collider); species s contracts it with its own window ghat_{s, p} (FP32 from global memory,
+// 128 cells per coefficient column, so a warp reads 128 contiguous bytes per coefficient).
+template <int W>
+__device__ __forceinline__ void epi_tile_species(const float *gsp_ct, long long sstride, int n_species, int kpad,
+                                                 int row, int acol, uint32_t tcol, int nf, int fs, int part,
+                                                 float (*FaccS)[kEpiF])
+{
+#pragma unroll
+    for (int sp = 0; sp < kMaxSpeciesTc; ++sp) {
+        if (sp >= n_species) break;
+        float gw[W];
+        const float *src = gsp_ct + (size_t)sp * sstride + (size_t)acol * kTileM + row;
+#pragma unroll
+        for (int c = 0; c < W; ++c) gw[c] = acol + c < kpad ? __ldg(src + (size_t)c * kTileM) : 0.f;   // the last
+        // window of a group may run past the padded K extent (its accumulator columns there are zero)
+#pragma unroll
+        for (int m0 = 0; m0 < kEpiF; ++m0) {
+            const int f = kEpiSplit * m0 + part;
+            if (f >= nf) break;
+            if (f < fs) continue;
+            uint32_t y[W];
+            if (W == 32) tmem_ld32(tcol + (uint32_t)((f - fs) * W), y);
+            else tmem_ld16(tcol + (uint32_t)((f - fs) * W), y);
+            tmem_wait_ld();
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < W; c += 2) {
+                s0 = fmaf(gw[c], __uint_as_float(y[c]), s0);
+                s1 = fmaf(gw[c + 1], __uint_as_float(y[c + 1]), s1);
+            }
+            FaccS[sp][m0] += s0 + s1;
         }
     }
 }
@@ -729,6 +772,11 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             float Facc[kEpiF];
 #pragma unroll
             for (int m = 0; m < kEpiF; ++m) Facc[m] = 0.f;
+            float FaccS[MODE == kModeSpecies ? kMaxSpeciesTc : 1][kEpiF];
+#pragma unroll
+            for (int sp = 0; sp < (MODE == kModeSpecies ? kMaxSpeciesTc : 1); ++sp)
+#pragma unroll
+                for (int m = 0; m < kEpiF; ++m) FaccS[sp][m] = 0.f;
             float Wacc[MODE == kModeVJP ? kWin : 1];
 #pragma unroll
             for (int t = 0; t < (MODE == kModeVJP ? kWin : 1); ++t) Wacc[t] = 0.f;
@@ -753,6 +801,9 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                                          P.ramp_b, Facc);
                 else if (MODE == kModeVJP)
                     epi_tile_vjp<2>(tcol, nf, fs, part, mu_cell, ford, td.f0, Wacc);
+                else if (MODE == kModeSpecies)
+                    epi_tile_species<kWin>(P.gsp + (size_t)ct * P.gsp_kpad * kTileM, P.gsp_sstride, P.n_species,
+                                           P.gsp_kpad, row, td.acol, tcol, nf, fs, part, FaccS);
                 else
                     epi_tile<PREC, kWin, 2>(a_gen, ic.a_bytes, row, td.acol, tcol, nf, fs, part, Facc);
                 tc_fence_before();
@@ -768,6 +819,21 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     }
 #pragma unroll
                     for (int t = 0; t < (MODE == kModeVJP ? kWin : 1); ++t) Wacc[t] = 0.f;
+                } else if (MODE == kModeSpecies && (td.nf_flush >> 16)) {
+#pragma unroll
+                    for (int sp = 0; sp < (MODE == kModeSpecies ? kMaxSpeciesTc : 1); ++sp) {
+                        if (sp >= P.n_species) break;
+                        if (live) {
+                            float *Fo = ic.F + (size_t)sp * P.f_sstride + ((size_t)ct * ic.R) * kTileM + row;
+#pragma unroll
+                            for (int m = 0; m < kEpiF; ++m) {
+                                const int f = kEpiSplit * m + part;
+                                if (f < nf) Fo[(size_t)ic.ford[td.f0 + f] * kTileM] = FaccS[sp][m];
+                            }
+                        }
+#pragma unroll
+                        for (int m = 0; m < kEpiF; ++m) FaccS[sp][m] = 0.f;
+                    }
                 } else if (MODE != kModeVJP && (td.nf_flush >> 16)) {
                     if (live) {
                         float *Fo = ic.F + ((size_t)ct * ic.R) * kTileM + row;
@@ -1143,16 +1209,28 @@ std::vector<int> functional_order(const DevGroup &g)
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
 {
     TcTiles out;
-    grace_status s = build_tc_tiles_from(G, G.d_T, prec, out, st);
+    grace_status s = build_tc_tiles_from(G, G.d_T, prec, out, st, false);
     if (s != GRACE_OK) return s;
     free_tc_tiles(G.tc[prec]);
     G.tc[prec] = out;
     return GRACE_OK;
 }
 
+// tiles of T as built (not folded: the outer and partner slots of a species' form differ)
+grace_status build_species_tiles(Group &G, int prec, cudaStream_t st)
+{
+    TcTiles out;
+    grace_status s = build_tc_tiles_from(G, G.d_T, prec, out, st, true);
+    if (s != GRACE_OK) return s;
+    free_tc_tiles(G.tcs[prec]);
+    G.tcs[prec] = out;
+    return GRACE_OK;
+}
+
 // tiles of the quadratic forms d_T ([R][P][P], FP64, device) of group G; an all-zero d_T gives
 // built tiles with n_tiles = 0 (nothing to contract)
-grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st)
+grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st,
+                                 bool unfolded_only)
 {
     const DevGroup &g = G.dg;
     if (g.k > kKMax) {
@@ -1215,8 +1293,9 @@ grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, Tc
         out.built = 1;
         return GRACE_OK;
     }
-    const Plan pT = plan_forms(FT, ford, prec), pU = plan_forms(FU, ford, prec);
-    const bool use_fold = pU.cost <= pT.cost;
+    const Plan pT = plan_forms(FT, ford, prec);
+    const Plan pU = unfolded_only ? Plan() : plan_forms(FU, ford, prec);
+    const bool use_fold = !unfolded_only && pU.cost <= pT.cost;
     std::vector<int> written;
     grace_status s = emit_tiles(use_fold ? FU : FT, use_fold ? pU : pT, ford, prec, out, written);
     if (s != GRACE_OK) return s;
@@ -1477,6 +1556,36 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
     }
     return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeF>(P, t.max_rows, st)
                               : launch_prec<GRACE_BF16X3, kModeF>(P, t.max_rows, st);
+}
+
+cudaError_t launch_contract_tc_species(const DevGroup &g, const TcTiles &t, int prec, const void *opA, int n_cells,
+                                       const float *d_gsp, int n_species, float *d_F32, int *d_err, cudaStream_t st)
+{
+    if (!t.built || t.nc || t.vjp || n_cells <= 0 || n_species < 1 || n_species > kMaxSpeciesTc)
+        return n_cells == 0 ? cudaSuccess : cudaErrorInvalidValue;
+    TcParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.tiles = (const TileDesc *)t.d_desc;
+    P.ford = t.d_ford;
+    P.n_tiles = t.n_tiles;
+    P.B = (const uint8_t *)t.d_b;
+    P.A = (const uint8_t *)opA;
+    P.a_tile_bytes = (long long)opA_tile_bytes(prec, t.k_pad);
+    P.n_cells = n_cells;
+    P.n_cell_tiles = (n_cells + kTileM - 1) / kTileM;
+    P.R = g.R;
+    P.F = d_F32;
+    P.err = d_err;
+    P.gsp = d_gsp;
+    P.gsp_kpad = t.k_pad;
+    P.gsp_sstride = (long long)P.n_cell_tiles * t.k_pad * kTileM;
+    P.f_sstride = (long long)P.n_cell_tiles * g.R * kTileM;
+    P.n_species = n_species;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
+    return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeSpecies>(P, t.max_rows, st)
+                              : launch_prec<GRACE_BF16X3, kModeSpecies>(P, t.max_rows, st);
 }
 
 void free_tc_multi(TcMulti &m)

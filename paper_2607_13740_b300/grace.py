@@ -93,8 +93,8 @@ def load(path: str | None = None):
     L.grace_adjoint.argtypes = [_VP, _VP, _VP, S, S, _VP, _VP, _VP, S]
     L.grace_probe_rates.argtypes = [S, ctypes.POINTER(ctypes.c_double)]
     L.grace_probe_mma.argtypes = [S, S, S, ctypes.POINTER(ctypes.c_double)]
-    L.grace_rhs_species.argtypes = [_VP, S, _VP, _VP]
-    L.grace_step_species.argtypes = [_VP, S, _VP, _VP, S, _VP, _VP]
+    L.grace_rhs_species.argtypes = [_VP, S, _VP, _VP, S]
+    L.grace_step_species.argtypes = [_VP, S, _VP, _VP, S, S, _VP, _VP]
     L.grace_substep.argtypes = [_VP, _VP, _VP, ctypes.c_double, S, S, _VP, _VP, ctypes.POINTER(S)]
     L.grace_batch_set_graph.argtypes = [_VP, S]
     L.grace_batch_set_grouped.argtypes = [_VP, S]
@@ -300,7 +300,7 @@ class Batch:
                                  _ptr(mass), _ptr(flags)), "grace_step")
         return g
 
-    def rhs_species(self, gs):
+    def rhs_species(self, gs, precision: int = FP64):
         """Species of mixed grains: gs [S, n_cells, P] float64 CUDA tensor of partial mass densities;
         returns L_s = L[g_s; sum_s g_s] in the same layout (grace_rhs_species)."""
         import torch
@@ -308,17 +308,18 @@ class Batch:
             raise GraceError("gs must be a contiguous float64 CUDA tensor [S, n_cells, P]")
         out = torch.empty_like(gs)
         self.ctx.set_stream()
-        _check(load().grace_rhs_species(self._h, gs.shape[0], _ptr(gs), _ptr(out)), "grace_rhs_species")
+        _check(load().grace_rhs_species(self._h, gs.shape[0], _ptr(gs), _ptr(out), int(precision)),
+               "grace_rhs_species")
         return out
 
-    def step_species(self, gs, dt, n_steps: int, mass=None, flags=None):
+    def step_species(self, gs, dt, n_steps: int, precision: int = FP64, mass=None, flags=None):
         """n_steps SSP-RK3 steps of the species, in place on gs [S, n_cells, P] (grace_step_species)."""
         import torch
         if not (gs.is_cuda and gs.dtype == torch.float64 and gs.is_contiguous() and gs.dim() == 3):
             raise GraceError("gs must be a contiguous float64 CUDA tensor [S, n_cells, P]")
         self.ctx.set_stream()
-        _check(load().grace_step_species(self._h, gs.shape[0], _ptr(gs), _ptr(dt), int(n_steps), _ptr(mass),
-                                         _ptr(flags)), "grace_step_species")
+        _check(load().grace_step_species(self._h, gs.shape[0], _ptr(gs), _ptr(dt), int(n_steps), int(precision),
+                                         _ptr(mass), _ptr(flags)), "grace_step_species")
         return gs
 
     def substep(self, g, dt_hydro, cfl: float = 0.5, max_substeps: int = 1000, precision: int = FP64, mass=None,

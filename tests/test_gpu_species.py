@@ -131,3 +131,59 @@ def test_species_rejects_unsupported_batches():
     b2 = grace.Context(specs).batch(len(group), group)
     with pytest.raises(grace.GraceError):
         b2.rhs_species(torch.zeros((2, 64, 1), dtype=torch.float64, device=DEV))
+
+
+TC_FORMS = [grace.TF32, grace.BF16X3]
+TC_IDS = ["tf32", "bf16x3"]
+TC_TOL = {grace.TF32: 2e-3, grace.BF16X3: 5e-5}
+# trajectory bars: the RHS bar accumulated linearly over the 60 stages of 20 steps, each stage
+# moving a species by at most 0.3 of its eq. (dt) bound (dt <= 0.3 B): 60 x 0.3 x TOL = 18 TOL
+TC_TRAJ = {f: 18 * t for f, t in TC_TOL.items()}
+
+
+@pytest.mark.parametrize("form", TC_FORMS, ids=TC_IDS)
+@pytest.mark.parametrize("S", [1, 2, 4])
+@pytest.mark.parametrize("name", ["add", "toy", "k3"])
+def test_species_rhs_tensor_forms(name, S, form):
+    """One tcgen05 pass over T with the cells' total as the A operand, each species contracting
+    the accumulator: within the form's RHS bar of the oracle's species rates (300 cells, three
+    128-cell tiles with a ragged tail)."""
+    spec = SPECS[name]
+    o = oracle.Oracle(spec)
+    g = W.random_coefficients(spec, 300, seed=91)
+    gs = _split(spec, g, S, seed=92 + S)
+    Lo, So = o.rhs_species(gs)
+    b = grace.Context([spec], 0, precisions=(grace.FP64, form)).batch(300)
+    Lg = b.rhs_species(torch.as_tensor(gs, device=DEV), form).cpu().numpy()
+    assert b.device_error() == 0
+    err = np.abs(Lg - Lo) / np.maximum(np.maximum(np.abs(Lo), So), 1e-300)
+    assert err.max() <= TC_TOL[form], err.max()
+
+
+@pytest.mark.parametrize("form", TC_FORMS, ids=TC_IDS)
+def test_species_steps_tensor_forms(form):
+    """20 steps of a tracer and the rest (the additive kernel, limiter on) in a tensor form: the
+    trajectory within the form's bar of the oracle, each species' M_1 conserved to round-off, and
+    the eq. (dt), negative-mean, non-finite and drift bits equal to the oracle's."""
+    spec = SPECS["add"]
+    o = oracle.Oracle(spec)
+    n = 200
+    g = W.random_coefficients(spec, n, seed=86)
+    tracer = np.zeros_like(g)
+    tracer.reshape(n, spec.n_bins, -1)[:, :2, :] = g.reshape(n, spec.n_bins, -1)[:, :2, :]
+    gs = np.stack([tracer, g - tracer])
+    dt = np.random.default_rng(85).uniform(0.1, 0.3, n) * _species_bound(o, spec, gs)
+    go, mo, fo = o.step_species(gs, dt, 20)
+    b = grace.Context([spec], 0, precisions=(grace.FP64, form)).batch(n)
+    gd = torch.as_tensor(gs, device=DEV)
+    mass = torch.zeros((2, n), dtype=torch.float64, device=DEV)
+    flags = torch.zeros(n, dtype=torch.uint8, device=DEV)
+    b.step_species(gd, torch.as_tensor(dt, device=DEV), 20, form, mass=mass, flags=flags)
+    assert b.device_error() == 0
+    err = _traj_err(spec, gd.cpu().numpy(), go)
+    assert err <= TC_TRAJ[form], err
+    h = np.diff(o.edges())
+    m0 = (h[None, None, :] * gs.reshape(2, n, spec.n_bins, -1)[..., 0]).sum(axis=2)
+    assert np.all(np.abs(mass.cpu().numpy() - m0) <= 1e-13 * np.abs(m0).sum(axis=0))
+    keep = np.uint8(~2 & 0xFF)
+    np.testing.assert_array_equal(flags.cpu().numpy() & keep, fo & keep)

@@ -258,6 +258,20 @@ GRACE_API grace_status grace_rhs_species(grace_batch *batch, int n_species, cons
 GRACE_API grace_status grace_step_species(grace_batch *batch, int n_species, double *gs, const double *dt,
                                           int n_steps, int precision, double *mass, unsigned char *flags);
 
+/* Linearly implicit (Rosenbrock-Euler) step for stiff cells, the implicit option of the coupling
+   to a hydrodynamics code (Sec. 5.2): per cell, (I - dt_c J(g)) k = dt_c L[g] with J = dL/dg at g,
+   then g <- g + k (in place; g, dt device [n_cells][P] / [n_cells]).  Each cell's system is solved
+   by restarted GMRES(krylov_dim) (1 .. 64 basis vectors per cycle, at most max_restarts restarts)
+   whose matrix-vector products are grace_rhs_jvp in `precision` over the whole batch (one JVP per
+   Krylov iteration); a cell stops when its residual is below rtol (0 < rtol < 1) of its initial
+   residual ||dt_c L||.  *iterations (host, nullable) receives the Krylov iterations taken.  The
+   paper gives no implicit scheme; this is the library's, on the JVP of the adjoint's tables.
+   Allocates a workspace on first use; synchronises once per cycle and every 4 iterations (to stop
+   when every cell has converged), so it is not captured in a CUDA graph.  Restrictions of
+   grace_rhs_jvp (one group in caller order, no per-cell kernel parameters). */
+GRACE_API grace_status grace_rosenbrock_step(grace_batch *batch, double *g, const double *dt, int precision,
+                                             int krylov_dim, int max_restarts, double rtol, int *iterations);
+
 /* Operator-split coupling to a hydrodynamics code (Sec. 5.2): advances every cell by its
    own interval dt_hydro[c] (device [n_cells]) in sub-steps sized by the eq. (dt)
    positivity bound.  The FP64 RHS at the start gives each cell's bound

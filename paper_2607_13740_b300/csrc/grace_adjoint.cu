@@ -550,7 +550,7 @@ cudaError_t vjp_tc(grace_batch *b, int prec, const double *gs, const double *lam
 cudaError_t fwd_step_tc(grace_batch *b, int prec, const double *pre, double *gt, double *g1, double *g2,
                         double *next, const double *dt)
 {
-    Group &G = b->ctx->groups[0];
+    Group &G = b->ctx->groups[b->parts[0].group];
     const DevGroup &dg = G.dg;
     Part &p = b->parts[0];
     cudaStream_t st = b->ctx->stream;
@@ -583,7 +583,7 @@ cudaError_t fwd_step_tc(grace_batch *b, int prec, const double *pre, double *gt,
 cudaError_t fwd_step(grace_batch *b, const double *pre, double *gt, double *g1, double *g2, double *next,
                      const double *dt)
 {
-    Group &G = b->ctx->groups[0];
+    Group &G = b->ctx->groups[b->parts[0].group];
     const DevGroup &dg = G.dg;
     cudaStream_t st = b->ctx->stream;
     const int n = b->n_cells;
@@ -632,7 +632,7 @@ grace_status grace_rhs_jvp(grace_batch *b, const double *g, const double *v, dou
         cudaError_t e = jvp_tc(b, precision, g, v, Jv, b->ctx->stream);
         return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_jvp");
     }
-    Group &G = b->ctx->groups[0];
+    Group &G = b->ctx->groups[b->parts[0].group];
     cudaStream_t st = b->ctx->stream;
     double *dF = b->parts[0].d_F;
     cudaError_t e = launch_jvp_contract(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, v, b->n_cells, dF, st);
@@ -660,7 +660,7 @@ grace_status grace_rhs_vjp(grace_batch *b, const double *g, const double *lambda
         cudaError_t e = vjp_tc(b, precision, g, lambda, w, b->ctx->stream);
         return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_vjp");
     }
-    Group &G = b->ctx->groups[0];
+    Group &G = b->ctx->groups[b->parts[0].group];
     cudaError_t e = launch_vjp(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, lambda, b->parts[0].d_F, b->n_cells, w,
                                b->ctx->stream);
     return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_vjp");
@@ -756,7 +756,7 @@ grace_status grace_adjoint(grace_batch *b, const double *g0, const double *dt, i
         sp = prepare_tc(b, precision, true, "grace_adjoint");
         if (sp != GRACE_OK) return sp;
     }
-    Group &G = b->ctx->groups[0];
+    Group &G = b->ctx->groups[b->parts[0].group];
     const DevGroup &dg = G.dg;
     cudaStream_t st = b->ctx->stream;
     const int n = b->n_cells, P = dg.P, R = dg.R;

@@ -1040,6 +1040,7 @@ void grace_batch_destroy(grace_batch *b)
     free_host_io(b);
     free_hydro(b);
     free_species(b);
+    free_implicit(b);
     free_grouped(b);
     for (Part &p : b->parts) free_part(p);
     cudaFree(b->d_err);

@@ -177,6 +177,7 @@ struct grace_batch {
     unsigned *d_flag_or = nullptr; // grace_flags_check's reduction word
     void *hydro = nullptr;         // grace_substep workspace (grace_hydro.cu), built on first use
     void *species = nullptr;       // species workspace (grace_species.cu), built on first use
+    void *implicit = nullptr;      // grace_rosenbrock_step workspace (grace_implicit.cu), built on first use
 };
 
 namespace grace {
@@ -187,6 +188,7 @@ void free_host_io(grace_batch *b);
 void free_hydro(grace_batch *b);
 // frees the workspace of the species calls
 void free_species(grace_batch *b);
+void free_implicit(grace_batch *b);
 
 // thread-local error detail
 void set_error(const std::string &msg);

@@ -53,7 +53,7 @@ def exported_symbols():
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
             "grace_step_host", "grace_step_host_wait", "grace_flags_check",
             "grace_test_arm_wait_timeout", "grace_probe_mma", "grace_substep", "grace_rhs_species",
-            "grace_step_species"]
+            "grace_step_species", "grace_rosenbrock_step"]
 
 
 def load(path: str | None = None):
@@ -94,6 +94,7 @@ def load(path: str | None = None):
     L.grace_probe_rates.argtypes = [S, ctypes.POINTER(ctypes.c_double)]
     L.grace_probe_mma.argtypes = [S, S, S, ctypes.POINTER(ctypes.c_double)]
     L.grace_rhs_species.argtypes = [_VP, S, _VP, _VP, S]
+    L.grace_rosenbrock_step.argtypes = [_VP, _VP, _VP, S, S, S, ctypes.c_double, ctypes.POINTER(S)]
     L.grace_step_species.argtypes = [_VP, S, _VP, _VP, S, S, _VP, _VP]
     L.grace_substep.argtypes = [_VP, _VP, _VP, ctypes.c_double, S, S, _VP, _VP, ctypes.POINTER(S)]
     L.grace_batch_set_graph.argtypes = [_VP, S]
@@ -321,6 +322,18 @@ class Batch:
         _check(load().grace_step_species(self._h, gs.shape[0], _ptr(gs), _ptr(dt), int(n_steps), int(precision),
                                          _ptr(mass), _ptr(flags)), "grace_step_species")
         return gs
+
+    def rosenbrock_step(self, g, dt, precision: int = FP64, krylov_dim: int = 30, max_restarts: int = 4,
+                        rtol: float = 1e-10) -> int:
+        """One linearly implicit Euler step per cell, in place on g: (I - dt J) k = dt L[g], g += k,
+        solved by restarted GMRES on the JVPs (grace_rosenbrock_step).  Returns the Krylov
+        iterations taken."""
+        self._check_state(g)
+        self.ctx.set_stream()
+        it = ctypes.c_int(0)
+        _check(load().grace_rosenbrock_step(self._h, _ptr(g), _ptr(dt), int(precision), int(krylov_dim),
+                                            int(max_restarts), float(rtol), ctypes.byref(it)), "grace_rosenbrock_step")
+        return it.value
 
     def substep(self, g, dt_hydro, cfl: float = 0.5, max_substeps: int = 1000, precision: int = FP64, mass=None,
                 flags=None) -> int:

@@ -333,3 +333,33 @@ def test_tensor_form_adjoint_errors():
         b.vjp(g, g, grace.TF32)
     with pytest.raises(grace.GraceError, match="precomputed"):
         b.jvp(g, g, grace.BF16X3)
+
+
+def test_jvp_vjp_adjoint_use_the_batch_group():
+    """A context with two groups and a batch whose cells all belong to the second: the JVP, the
+    VJP (dot-product identity) and the trajectory adjoint use that group's tables (oracle of that
+    group's physics)."""
+    spec0 = W.additive_spec(10, 2, 1e-3, 1e4)
+    spec1 = W.coupled_toy_spec(10, 2, flux_mode=0)
+    n = 5
+    ctx = grace.Context([spec0, spec1])
+    b = ctx.batch(n, np.ones(n, dtype=np.int32))
+    o = oracle.Oracle(spec1)
+    g = W.random_coefficients(spec1, n, seed=621)
+    v = W.random_coefficients(spec1, n, seed=622) * 0.3
+    Jv = b.jvp(torch.as_tensor(g, device=DEV), torch.as_tensor(v, device=DEV)).cpu().numpy()
+    Lp, Sp = o.rhs(g + v)
+    Lm, Sm = o.rhs(g - v)
+    assert np.all(np.abs(Jv - 0.5 * (Lp - Lm)) <= 1e-12 * np.maximum(Sp, Sm))
+    lam = np.random.default_rng(623).normal(size=g.shape)
+    w = b.vjp(torch.as_tensor(g, device=DEV), torch.as_tensor(lam, device=DEV)).cpu().numpy()
+    lhs, rhs = (w * v).sum(axis=1), (Jv * lam).sum(axis=1)
+    assert np.all(np.abs(lhs - rhs) <= 1e-12 * (np.abs(lhs) + np.abs(rhs)))
+    dt, steps = 0.02, 5
+    lamT = np.random.default_rng(624).normal(size=g.shape)
+    lam0, _ = b.adjoint(torch.as_tensor(g, device=DEV), torch.full((n,), dt, dtype=torch.float64, device=DEV), steps,
+                        torch.as_tensor(lamT, device=DEV), 2)
+    _, dg = o.tangent_step(g, dt, steps, gdot=v)
+    ref = (dg * lamT).sum(axis=1)
+    ad = (lam0.cpu().numpy() * v).sum(axis=1)
+    assert np.allclose(ad, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())

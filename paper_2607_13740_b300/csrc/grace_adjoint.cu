@@ -338,6 +338,15 @@ __global__ void polar_accumulate_kernel(int R, int n_cells, const float *__restr
     dF[t] = accumulate ? dF[t] + v : v;
 }
 
+// dF = (Fa - Fb) / (2 eps[cell]) in FP64 (per-cell-kernel JVP by polarization)
+__global__ void polar_combine_kernel(int R, int n_cells, const double *__restrict__ Fa, const double *__restrict__ Fb,
+                                     const double *__restrict__ eps, double *__restrict__ dF)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_cells * R) return;
+    dF[t] = (Fa[t] - Fb[t]) / (2.0 * eps[t / R]);
+}
+
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 size_t warp_tile_smem(int P, int arrays, int *wpb)
@@ -440,18 +449,58 @@ double *param_slot(grace_group_desc &d, int id)
     return &d.break_p[id - 16];
 }
 
-// the adjoint calls work on batches of one group in the caller's order
-grace_status single_part(grace_batch *b, const char *who)
+// the adjoint calls work on batches of one group in the caller's order; groups with a per-cell
+// kernel parameter (no fixed T) in FP64 only, once their parameters are set
+grace_status single_part(grace_batch *b, const char *who, int precision = GRACE_FP64)
 {
     if (b->parts.size() != 1 || !b->parts[0].direct) {
         set_error(std::string(who) + ": batches mixing groups are not supported");
         return GRACE_ERR_UNSUPPORTED;
     }
     if (b->ctx->groups[b->parts[0].group].dg.cell_alpha) {
-        set_error(std::string(who) + ": groups with a per-cell kernel parameter have no fixed T (not supported)");
-        return GRACE_ERR_UNSUPPORTED;
+        if (precision != GRACE_FP64) {
+            set_error(std::string(who) + ": groups with a per-cell kernel parameter: FP64 only");
+            return GRACE_ERR_UNSUPPORTED;
+        }
+        if (!b->alpha_set) {
+            set_error(std::string(who) + ": per-cell kernel parameters not set: call grace_batch_cell_params first");
+            return GRACE_ERR_ORDER;
+        }
     }
     return GRACE_OK;
+}
+
+// per-cell-kernel groups: the adjoint's workspaces of the part (allocated on first use)
+cudaError_t nc_adjoint_ws(grace_batch *b)
+{
+    Part &p = b->parts[0];
+    const Group &G = b->ctx->groups[p.group];
+    if (p.d_gamma) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p.d_gamma, (size_t)p.n * G.nc.NQ * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_F2, (size_t)p.n * G.dg.R * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_eps, (size_t)p.n * sizeof(double));
+    return e;
+}
+
+// FP64 flux functionals of either kind of group into dF
+cudaError_t functionals_fp64(grace_batch *b, const double *g, double *dF, cudaStream_t st)
+{
+    Part &p = b->parts[0];
+    Group &G = b->ctx->groups[p.group];
+    return G.dg.cell_alpha ? launch_nc_functionals(G.dg, G.nc, g, p.d_alpha, b->n_cells, p.d_G, p.d_H, dF, st)
+                           : launch_contract_fp64(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, b->n_cells, dF, st);
+}
+
+// FP64 J(gs)^T lambda into w for either kind of group; leaves mu = D^T lambda in the part's d_F
+cudaError_t vjp_fp64(grace_batch *b, const double *gs, const double *lambda, double *w, cudaStream_t st)
+{
+    Part &p = b->parts[0];
+    Group &G = b->ctx->groups[p.group];
+    if (!G.dg.cell_alpha) return launch_vjp(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gs, lambda, p.d_F, b->n_cells, w, st);
+    cudaError_t e = nc_adjoint_ws(b);
+    if (e == cudaSuccess) e = launch_mu(G.dg, lambda, b->n_cells, p.d_F, st);
+    if (e == cudaSuccess) e = launch_nc_vjp(G.dg, G.nc, gs, p.d_alpha, p.d_F, b->n_cells, p.d_G, p.d_H, p.d_gamma, w, st);
+    return e;
 }
 
 // tensor forms: the precision's tiles (forward, and VJP tiles built on first use) and the
@@ -595,7 +644,7 @@ cudaError_t fwd_step(grace_batch *b, const double *pre, double *gt, double *g1, 
     double *gout[3] = {g1, g2, next};
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
-        e = launch_contract_fp64(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gin[s], n, dF, st);
+        e = functionals_fp64(b, gin[s], dF, st);
         if (e != cudaSuccess) break;
         UpdateArgs u;
         u.F = dF;
@@ -623,7 +672,7 @@ grace_status grace_rhs_jvp(grace_batch *b, const double *g, const double *v, dou
         set_error("grace_rhs_jvp: null argument");
         return GRACE_ERR_ARG;
     }
-    grace_status sp = single_part(b, "grace_rhs_jvp");
+    grace_status sp = single_part(b, "grace_rhs_jvp", precision);
     if (sp != GRACE_OK) return sp;
     Guard guard(b->ctx->device);
     if (precision != GRACE_FP64) {
@@ -634,8 +683,28 @@ grace_status grace_rhs_jvp(grace_batch *b, const double *g, const double *v, dou
     }
     Group &G = b->ctx->groups[b->parts[0].group];
     cudaStream_t st = b->ctx->stream;
-    double *dF = b->parts[0].d_F;
-    cudaError_t e = launch_jvp_contract(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, v, b->n_cells, dF, st);
+    Part &p = b->parts[0];
+    double *dF = p.d_F;
+    cudaError_t e = cudaSuccess;
+    if (G.dg.cell_alpha) {
+        // no fixed T: polarization of the quadratic L, exact up to rounding, with eps = 2^(e_g - e_v)
+        // per cell so that g +- eps v keep the size of g
+        e = nc_adjoint_ws(b);
+        if (e == cudaSuccess) {
+            polar_kernel<<<blocks((long long)b->n_cells * 32, 256), 256, 0, st>>>(G.dg.P, b->n_cells, g, v, p.d_g1,
+                                                                                   p.d_g2, p.d_eps);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = functionals_fp64(b, p.d_g1, dF, st);
+        if (e == cudaSuccess) e = functionals_fp64(b, p.d_g2, p.d_F2, st);
+        if (e == cudaSuccess) {
+            polar_combine_kernel<<<blocks((long long)b->n_cells * G.dg.R, 256), 256, 0, st>>>(G.dg.R, b->n_cells, dF,
+                                                                                               p.d_F2, p.d_eps, dF);
+            e = cudaGetLastError();
+        }
+    } else {
+        e = launch_jvp_contract(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, v, b->n_cells, dF, st);
+    }
     if (e == cudaSuccess) {
         UpdateArgs u;
         u.F = dF;
@@ -651,7 +720,7 @@ grace_status grace_rhs_vjp(grace_batch *b, const double *g, const double *lambda
         set_error("grace_rhs_vjp: null argument");
         return GRACE_ERR_ARG;
     }
-    grace_status sp = single_part(b, "grace_rhs_vjp");
+    grace_status sp = single_part(b, "grace_rhs_vjp", precision);
     if (sp != GRACE_OK) return sp;
     Guard guard(b->ctx->device);
     if (precision != GRACE_FP64) {
@@ -660,9 +729,7 @@ grace_status grace_rhs_vjp(grace_batch *b, const double *g, const double *lambda
         cudaError_t e = vjp_tc(b, precision, g, lambda, w, b->ctx->stream);
         return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_vjp");
     }
-    Group &G = b->ctx->groups[b->parts[0].group];
-    cudaError_t e = launch_vjp(G.dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, g, lambda, b->parts[0].d_F, b->n_cells, w,
-                               b->ctx->stream);
+    cudaError_t e = vjp_fp64(b, g, lambda, w, b->ctx->stream);
     return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_rhs_vjp");
 }
 
@@ -748,7 +815,7 @@ grace_status grace_adjoint(grace_batch *b, const double *g0, const double *dt, i
         set_error("grace_adjoint: null argument, negative step count or ckpt_every < 1");
         return GRACE_ERR_ARG;
     }
-    grace_status sp = single_part(b, "grace_adjoint");
+    grace_status sp = single_part(b, "grace_adjoint", precision);
     if (sp != GRACE_OK) return sp;
     Guard guard(b->ctx->device);
     const bool tc = precision != GRACE_FP64;
@@ -799,8 +866,7 @@ grace_status grace_adjoint(grace_batch *b, const double *g0, const double *dt, i
     if (e == cudaSuccess) e = cudaMemcpyAsync(lam, lambda_T, bytes, cudaMemcpyDeviceToDevice, st);
 
     auto vjp_at = [&](const double *gs, const double *l, double *out) {
-        return tc ? vjp_tc(b, precision, gs, l, out, st)
-                  : launch_vjp(dg, G.d_T, G.d_qlo, G.d_qhi, G.d_prange, gs, l, dF, n, out, st);
+        return tc ? vjp_tc(b, precision, gs, l, out, st) : vjp_fp64(b, gs, l, out, st);
     };
     // dtheta += w dt mu(l) . g^T dT g (mu of the last vjp is in b->d_F).  Tensor forms: the
     // A operand of gs is still packed by the VJP; g^T dT g goes to the FP32 mu buffer, free

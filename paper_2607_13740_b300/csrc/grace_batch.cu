@@ -134,6 +134,9 @@ void free_part(Part &p)
     cudaFree(p.d_W32);
     cudaFree(p.d_mu32);
     cudaFree(p.d_cscale);
+    cudaFree(p.d_gamma);
+    cudaFree(p.d_F2);
+    cudaFree(p.d_eps);
     if (p.stream) cudaStreamDestroy(p.stream);
     if (p.done) cudaEventDestroy(p.done);
     p = Part();

@@ -71,6 +71,9 @@ struct NcTables {
     long long n_entf = 0;
     long long *d_seg = nullptr;   // [R+1] entry ranges per functional
     long long n_entries = 0;
+    // the adjoint (built on the first FP64 VJP): transposed fixed-pair tables and their extents
+    double *d_CcT = nullptr, *d_CfT = nullptr;
+    int *d_qloT = nullptr, *d_qhiT = nullptr;
 };
 
 // d T / d theta for one kernel parameter (central difference of the FP64 precompute)
@@ -145,6 +148,9 @@ struct Part {
     float *d_W32 = nullptr;        // tensor-form VJP: output planes [tc_vjp_planes()][tiles][Pw][128]
     float *d_mu32 = nullptr;       // tensor-form VJP: mu in FP32, [tiles][R][128]
     double *d_cscale = nullptr;    // tensor-form JVP / VJP: per-cell power-of-two scales
+    double *d_gamma = nullptr;     // per-cell-kernel adjoint: [n][NQ] nodal gradient
+    double *d_F2 = nullptr;        // per-cell-kernel JVP: [n][R] the second polarization's functionals
+    double *d_eps = nullptr;       // per-cell-kernel JVP: [n] polarization scales
     size_t opA_bytes = 0;
     cudaStream_t stream = nullptr; // own stream for concurrent parts (null: the context's)
     cudaEvent_t done = nullptr;
@@ -342,6 +348,11 @@ grace_status build_nc_tables(Group &G, cudaStream_t st);
 void free_nc_tables(NcTables &t);
 cudaError_t launch_nc_functionals(const DevGroup &g, const NcTables &t, const double *d_g, const double *d_alpha,
                                   int n_cells, double *d_G, double *d_H, double *d_F, cudaStream_t st);
+// adjoint of the per-cell functionals (FP64): w = sum_r mu_r dF_r/dg for the functional weights mu
+// ([n][R]), with the nodal workspaces of launch_nc_functionals and d_gamma ([n][NQ]); builds the
+// transposed tables on first use (allocates and synchronises)
+cudaError_t launch_nc_vjp(const DevGroup &g, NcTables &t, const double *d_g, const double *d_alpha, const double *d_mu,
+                          int n_cells, double *d_G, double *d_H, double *d_gamma, double *d_w, cudaStream_t st);
 // reduced-precision forms: FP32 partial entries (built once); per RHS the node values -> A
 // operand (+ FP32 scaled coefficients, s per cell), the tcgen05 fixed part (launch_contract_tc
 // with d_cell_s), then the FP32 partial part added into d_F32 ([tile][functional][row])

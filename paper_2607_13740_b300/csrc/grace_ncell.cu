@@ -428,6 +428,133 @@ __global__ void __launch_bounds__(128) nc_partial_kernel(DevGroup G, const NcEnt
     if (live) F[cell * G.R + r] += s * acc;
 }
 
+// ---------------------------------------------------------------- adjoint (FP64)
+// The fixed part of functional r is s G^T M_r G with M_r[i][j] = Cc_r[i][j] (1 - pf_j) + Cf_r[i][j] pf_j
+// (j >= i), G = B g the nodal values; partial entries add s w (pf or 1 - pf) (u . g) (v . g).  So
+//     w = sum_r mu_r dF_r/dg = B^T gamma + (partial entries),
+//     gamma_a = s sum_r mu_r [ sum_j M_r[a][j] G_j + sum_i G_i M_r[i][a] ]
+//             = s sum_r mu_r [ sum_j (Cc_r[a][j] Hc_j + Cf_r[a][j] Hf_j) + (1 - pf_a) (Cc_r^T G)_a + pf_a (Cf_r^T G)_a ].
+
+// transposed copies of both tables, one thread per (r, i, j)
+__global__ void nc_transpose_kernel(int R, int NQ, const double *__restrict__ C, double *__restrict__ CT)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per = (long long)NQ * NQ;
+    if (t >= (long long)R * per) return;
+    const long long r = t / per;
+    const int i = (int)((t - r * per) / NQ), j = (int)(t - r * per - (long long)i * NQ);
+    CT[r * per + (long long)j * NQ + i] = C[t];
+}
+
+// gamma[c][a] for 32 cells per warp: G, Hc, Hf and mu of the warp's cells in shared memory; for
+// every node a, the sum over the functionals of its row of (Cc, Cf) against (Hc, Hf) and of its
+// row of the transposed tables against G
+__global__ void __launch_bounds__(32) nc_vjp_node_kernel(
+    DevGroup G, const double *__restrict__ Cc, const double *__restrict__ Cf, const int *__restrict__ qlo,
+    const int *__restrict__ qhi, const double *__restrict__ CcT, const double *__restrict__ CfT,
+    const int *__restrict__ qloT, const int *__restrict__ qhiT, const double *__restrict__ D0, int R, int NQ,
+    const double *__restrict__ Gv, const double *__restrict__ Hcv, const double *__restrict__ Hfv,
+    const double *__restrict__ mu, const double *__restrict__ alpha, int n_cells, double *__restrict__ gamma)
+{
+    extern __shared__ double vsm[];
+    const int lane = threadIdx.x & 31;
+    const long long cell0 = (long long)blockIdx.x * 32;
+    double *gw = vsm, *hc = gw + (size_t)NQ * 32, *hf = hc + (size_t)NQ * 32, *mw = hf + (size_t)NQ * 32;
+    for (int idx = lane; idx < 32 * NQ; idx += 32) {
+        const int c = idx / NQ, q = idx - c * NQ;
+        const long long cell = cell0 + c;
+        const bool ok = cell < n_cells;
+        gw[q * 32 + c] = ok ? Gv[cell * NQ + q] : 0.0;
+        hc[q * 32 + c] = ok ? Hcv[cell * NQ + q] : 0.0;
+        hf[q * 32 + c] = ok ? Hfv[cell * NQ + q] : 0.0;
+    }
+    for (int idx = lane; idx < 32 * R; idx += 32) {
+        const int c = idx / R, r = idx - c * R;
+        const long long cell = cell0 + c;
+        mw[r * 32 + c] = cell < n_cells ? mu[cell * R + r] : 0.0;
+    }
+    __syncwarp();
+    const long long cell = cell0 + lane;
+    const double s = cell < n_cells ? sqrt(alpha[cell]) : 0.0;
+    for (int a = 0; a < NQ; ++a) {
+        const double pf = dev_pfrag(G.coag_p, s * D0[a]);
+        double acc = 0.0;
+        for (int r = 0; r < R; ++r) {
+            const double m = mw[r * 32 + lane];
+            const size_t row = (size_t)r * NQ + a;
+            double y = 0.0;
+            for (int j = qlo[row]; j < qhi[row]; ++j)
+                y = fma(__ldg(Cc + row * NQ + j), hc[j * 32 + lane], fma(__ldg(Cf + row * NQ + j), hf[j * 32 + lane], y));
+            double zc = 0.0, zf = 0.0;
+            for (int i = qloT[row]; i < qhiT[row]; ++i) {
+                zc = fma(__ldg(CcT + row * NQ + i), gw[i * 32 + lane], zc);
+                zf = fma(__ldg(CfT + row * NQ + i), gw[i * 32 + lane], zf);
+            }
+            acc = fma(m, y + (1.0 - pf) * zc + pf * zf, acc);
+        }
+        if (cell < n_cells) gamma[cell * NQ + a] = s * acc;
+    }
+}
+
+// w[c][l K1 + i] = sum_alpha phi_i(s_alpha) gamma[c][l Q + alpha] (the transpose of the nodal values)
+__global__ void nc_vjp_assemble_kernel(DevGroup G, NodeRule rule, const double *__restrict__ gamma, int NQ,
+                                       int n_cells, double *__restrict__ w)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_cells * G.P) return;
+    const long long cell = t / G.P;
+    const int p = (int)(t - cell * G.P), l = p / G.K1, i = p - l * G.K1;
+    double acc = 0.0;
+    for (int al = 0; al < G.Q; ++al) acc = fma(rule.phi[al * kB + i], gamma[cell * NQ + (long long)l * G.Q + al], acc);
+    w[t] = acc;
+}
+
+// the partial entries' part of w: one thread per cell walks every functional's entries (staged in
+// shared memory for the block's 128 cells) and adds s mu_r w (pf or 1 - pf) [pu (v . g) at bin bu,
+// pv (u . g) at bin bv] into its own row of w
+__global__ void __launch_bounds__(128) nc_vjp_partial_kernel(DevGroup G, const NcEntry *__restrict__ entries,
+                                                             const long long *__restrict__ seg,
+                                                             const double *__restrict__ g,
+                                                             const double *__restrict__ mu,
+                                                             const double *__restrict__ alpha, int n_cells,
+                                                             double *__restrict__ w)
+{
+    __shared__ NcEntry es[64];
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = cell < n_cells;
+    const double s = live ? sqrt(alpha[cell]) : 0.0;
+    const double *gc = g + (size_t)(live ? cell : 0) * G.P;
+    double *wc = w + (size_t)(live ? cell : 0) * G.P;
+    for (int r = 0; r < G.R; ++r) {
+        const double m = live ? s * mu[cell * G.R + r] : 0.0;
+        const long long e0 = seg[r], e1 = seg[r + 1];
+        for (long long c0 = e0; c0 < e1; c0 += 64) {
+            const int n = (int)min((long long)64, e1 - c0);
+            __syncthreads();
+            for (int x = threadIdx.x; x < n * (int)(sizeof(NcEntry) / 8); x += blockDim.x)
+                reinterpret_cast<double *>(es)[x] = reinterpret_cast<const double *>(entries + c0)[x];
+            __syncthreads();
+            if (!live || m == 0.0) continue;
+            for (int t = 0; t < n; ++t) {
+                const NcEntry &e = es[t];
+                const double *gu = gc + (size_t)e.bu * G.K1, *gv = gc + (size_t)e.bv * G.K1;
+                double u = 0.0, v = 0.0;
+                for (int i = 0; i <= G.k; ++i) {
+                    u = fma(gu[i], e.pu[i], u);
+                    v = fma(gv[i], e.pv[i], v);
+                }
+                const double pf = dev_pfrag(G.coag_p, s * e.D0);
+                const double c = m * e.w * (e.kind ? pf : 1.0 - pf);
+                double *wu = wc + (size_t)e.bu * G.K1, *wv = wc + (size_t)e.bv * G.K1;
+                for (int i = 0; i <= G.k; ++i) {
+                    wu[i] = fma(c * v, e.pu[i], wu[i]);
+                    wv[i] = fma(c * u, e.pv[i], wv[i]);
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- reduced-precision forms
 // Per cell tile and bin (block = (tile, bin), thread = row): the scaled coefficients
 // h_l g_{l,i} in FP32 into gh ([tile][P][128]), the node values Ghat_a = sum_i h_l g_{l,i} phi_i(s_alpha)
@@ -721,6 +848,10 @@ void free_nc_tables(NcTables &t)
     cudaFree(t.d_entf);
     cudaFree(t.d_segf);
     cudaFree(t.d_seg);
+    cudaFree(t.d_CcT);
+    cudaFree(t.d_CfT);
+    cudaFree(t.d_qloT);
+    cudaFree(t.d_qhiT);
     t = NcTables();
 }
 
@@ -849,6 +980,74 @@ cudaError_t launch_nc_functionals(const DevGroup &g, const NcTables &t, const do
     if (e != cudaSuccess || t.n_entries == 0) return e;
     const dim3 grid((n_cells + 127) / 128, g.R);
     nc_partial_kernel<<<grid, 128, 0, st>>>(g, (const NcEntry *)t.d_entries, t.d_seg, d_g, d_alpha, n_cells, d_F);
+    return cudaGetLastError();
+}
+
+
+static NodeRule node_rule(const DevGroup &g)
+{
+    NodeRule rule;
+    for (int al = 0; al < g.Q; ++al) {
+        double P[kB];
+        P[0] = 1.0;
+        if (g.k >= 1) P[1] = g.gs[al];
+        for (int n = 1; n < g.k; ++n) P[n + 1] = ((2.0 * n + 1.0) * g.gs[al] * P[n] - n * P[n - 1]) / (n + 1.0);
+        for (int i = 0; i < kB; ++i) rule.phi[al * kB + i] = i <= g.k ? P[i] : 0.0;
+    }
+    return rule;
+}
+
+cudaError_t launch_nc_vjp(const DevGroup &g, NcTables &t, const double *d_g, const double *d_alpha, const double *d_mu,
+                          int n_cells, double *d_G, double *d_H, double *d_gamma, double *d_w, cudaStream_t st)
+{
+    if (n_cells <= 0) return cudaSuccess;
+    if (!t.built) return cudaErrorInvalidValue;
+    const int NQ = t.NQ, R = g.R;
+    cudaError_t e = cudaSuccess;
+    if (!t.d_CcT) {
+        const size_t nt = (size_t)R * NQ * NQ;
+        e = cudaMalloc(&t.d_CcT, nt * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_CfT, nt * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_qloT, (size_t)R * NQ * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_qhiT, (size_t)R * NQ * sizeof(int));
+        if (e == cudaSuccess) {
+            nc_transpose_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(R, NQ, t.d_Cc, t.d_CcT);
+            nc_transpose_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(R, NQ, t.d_Cf, t.d_CfT);
+            nc_extent_kernel<<<(R * NQ + 127) / 128, 128, 0, st>>>(R, NQ, t.d_CcT, t.d_CfT, t.d_qloT, t.d_qhiT);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(t.d_CcT);
+            cudaFree(t.d_CfT);
+            cudaFree(t.d_qloT);
+            cudaFree(t.d_qhiT);
+            t.d_CcT = t.d_CfT = nullptr;
+            t.d_qloT = t.d_qhiT = nullptr;
+            return e;
+        }
+    }
+    const NodeRule rule = node_rule(g);
+    const long long nn = (long long)n_cells * NQ;
+    double *d_Hc = d_H, *d_Hf = d_H + nn;
+    nc_nodal_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(g, rule, t.d_D0, d_g, d_alpha, n_cells, d_G, d_Hc, d_Hf);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = ((size_t)3 * NQ + R) * 32 * sizeof(double);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;   // node count too large for this FP64 kernel
+    e = cudaFuncSetAttribute(nc_vjp_node_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    nc_vjp_node_kernel<<<(n_cells + 31) / 32, 32, smem, st>>>(g, t.d_Cc, t.d_Cf, t.d_qlo, t.d_qhi, t.d_CcT, t.d_CfT,
+                                                              t.d_qloT, t.d_qhiT, t.d_D0, R, NQ, d_G, d_Hc, d_Hf, d_mu,
+                                                              d_alpha, n_cells, d_gamma);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long np = (long long)n_cells * g.P;
+    nc_vjp_assemble_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(g, rule, d_gamma, NQ, n_cells, d_w);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || t.n_entries == 0) return e;
+    nc_vjp_partial_kernel<<<(n_cells + 127) / 128, 128, 0, st>>>(g, (const NcEntry *)t.d_entries, t.d_seg, d_g, d_mu,
+                                                                 d_alpha, n_cells, d_w);
     return cudaGetLastError();
 }
 

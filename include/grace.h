@@ -399,6 +399,18 @@ GRACE_API grace_status grace_batch_error(grace_batch *batch, int *code);
    counterpart of this call. */
 GRACE_API grace_status grace_test_arm_wait_timeout(long long wait_cycles);
 
+/* Selects, for the whole process, where the tensor-form (TF32, BF16X3) forward
+   contractions run on CTA pairs: two SMs of a cluster share every work item,
+   one tcgen05.mma covering 256 cells (cta_group::2), each SM loading half of
+   every table block, so a group's tables stream once per two cell tiles.
+   mode 0 (the default): never; 1: every forward contraction of at least 256
+   cells; 2: multi-group launches only (uneven batches).  Both forms run the
+   same tiles in the same order; on a B300 the pairs measured slower than
+   single CTAs in both places, so they are off unless selected.
+   Returns GRACE_ERR_ARG for other values.  The paper has no counterpart of
+   this call. */
+GRACE_API grace_status grace_set_cta_pairs(int mode);
+
 /* Measures, on `device`, the CUDA-core throughput used as roofline
    denominators: rates[0] FP64 FMA/s, rates[1] FP32 FMA/s, rates[2] FP64->FP32
    conversions/s (3 doubles, host).  Allocates and synchronises. */

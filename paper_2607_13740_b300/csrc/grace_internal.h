@@ -38,6 +38,8 @@ struct TcTiles {
     int max_rows = 0;         // largest MMA N over the tiles
     int slot_bytes = 0;       // largest single B copy (bytes)
     void *d_b = nullptr;      // pre-swizzled B k-step blocks (all tiles back to back)
+    void *d_b_pair = nullptr; // the same images for CTA pairs: per tile [half][k-step][plane][N / 2 rows]
+                              // (forward tiles only; null elsewhere)
     void *d_desc = nullptr;   // per-tile descriptors
     int *d_ford = nullptr;    // functional ids in tile order
     size_t b_bytes = 0;
@@ -365,7 +367,7 @@ cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const Tc
 // tensor-core path
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);
 grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st,
-                                 bool unfolded_only = false);
+                                 bool unfolded_only = false, bool pair_image = false);
 // tiles of T as built (no fold) for the species contraction, into G.tcs[prec]
 grace_status build_species_tiles(Group &G, int prec, cudaStream_t st);
 // species of mixed grains: F_s[c, r] = sum_p ghat_{s,p} sum_q That_r[p, q] ghat_q for every species, the
@@ -387,6 +389,9 @@ struct TcMulti {
     void *d_groups = nullptr;
     void *d_items = nullptr;
     int n_items = 0;
+    void *d_pair_items = nullptr;   // CTA pairs: (group, pair of its cell tiles)
+    int n_pair_items = 0;
+    int pair_ok = 0;                // every group has CTA-pair B images
     long long max_a = 0;
     int max_rows = 0;
     int prec = -1;

@@ -28,7 +28,7 @@
 // Warp roles (persistent, one CTA per SM, work items round-robin):
 //   warps 0, 3    : B bulk-copy producers (lane 0), copies (up to 64 KB) alternating between the two issuers
 //   warp 2 lane 0 : A-tile loader (after allocating TMEM)
-//   warp 1 lane 0 : MMA issuer (kind::tf32, or kind::f16 with bf16 hi/lo x3)
+//   warp 1        : MMA issuer (kind::tf32, or kind::f16 with bf16 hi/lo x3), converged, lane 0 issues
 //   warp 2        : TMEM allocation / release (2 accumulators x 256 columns)
 //   warps 4..19   : epilogue; TMEM lane quadrant = warp % 4, four warps per quadrant
 //                   splitting the functionals of a tile; one cell per thread
@@ -105,6 +105,7 @@ struct TcParams {
     long long a_tile_bytes;
     int n_cells;
     int n_cell_tiles;
+    int n_pair_tiles;     // CTA pairs: pairs of cell tiles (the last one may have no odd tile)
     int R;
     float *F;
     int slot_bytes;       // bytes of one ring slot
@@ -143,6 +144,7 @@ struct TcGroupDesc {
     const TileDesc *tiles;
     const int *ford;
     const uint8_t *B;
+    const uint8_t *Bp;   // CTA-pair images of B (null when the group has none)
     const uint8_t *A;
     float *F;
     long long a_tile_bytes;
@@ -165,31 +167,41 @@ struct ItemCtx {
     int n_cells, R, t0, t1, ct;
 };
 
-template <int MODE>
-__device__ __forceinline__ ItemCtx item_ctx(const TcParams &P, int it, const TileDesc *tiles, const int *ford)
+// Work item `it`: a cell tile (or, for a CTA pair, the pair's cell tiles 2u and 2u + 1, this CTA taking
+// 2u + rank) and a split of the tile list.  A pair without an odd tile loads the even tile's A again
+// (its results are never written: no cell of that tile is live).
+template <int MODE, int PAIR = 0>
+__device__ __forceinline__ ItemCtx item_ctx(const TcParams &P, int it, const TileDesc *tiles, const int *ford,
+                                            uint32_t rank = 0)
 {
     ItemCtx c;
     if (MODE == kModeMulti) {
+        // item (group, cell tile), or for a CTA pair (group, pair of the group's cell tiles)
         const int2 v = P.items[it];
         const TcGroupDesc &g = P.groups[v.x];
+        const int n_ct = (g.n_cells + kTileM - 1) / kTileM;
+        const int ct = PAIR ? 2 * v.y + (int)rank : v.y;
         c.tiles = g.tiles;
         c.ford = g.ford;
-        c.B = g.B;
+        c.B = PAIR ? g.Bp : g.B;
         c.a_bytes = g.a_tile_bytes;
-        c.A = g.A + (size_t)v.y * g.a_tile_bytes;
+        c.A = g.A + (size_t)(ct < n_ct ? ct : ct - 1) * g.a_tile_bytes;
         c.F = g.F;
         c.n_cells = g.n_cells;
         c.R = g.R;
         c.t0 = g.t0;
         c.t1 = g.t1;
-        c.ct = v.y;
+        c.ct = ct;
     } else {
-        const int sp = it / P.n_cell_tiles, ct = it - sp * P.n_cell_tiles;
+        const int nu = PAIR ? P.n_pair_tiles : P.n_cell_tiles;
+        const int sp = it / nu, u = it - sp * nu;
+        const int ct = PAIR ? 2 * u + (int)rank : u;
+        const int ct_a = ct < P.n_cell_tiles ? ct : ct - 1;
         c.tiles = tiles;
         c.ford = ford;
         c.B = P.B;
         c.a_bytes = P.a_tile_bytes;
-        c.A = P.A + (size_t)ct * P.a_tile_bytes;
+        c.A = P.A + (size_t)ct_a * P.a_tile_bytes;
         c.F = P.F;
         c.n_cells = P.n_cells;
         c.R = P.R;
@@ -234,15 +246,60 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait: false on timeout or when another role already aborted
+// acquire at cluster scope: for barriers that the other CTA of a pair arrives on
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false on timeout or when another role (of this CTA or, for CTA pairs, of the
+// peer) already aborted
+template <int CLUSTER = 0>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, long long limit)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!(CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))) {
         if (*abort_flag) return false;
         if (clock64() - t0 > limit) return false;
     }
     return true;
+}
+
+// ---- CTA pairs (cta_group::2): one tcgen05.mma with M = 256 runs on the tensor cores of both SMs of
+// a 2-CTA cluster.  Each CTA holds its own 128 rows (cells) of A and one half of the rows of every B
+// k-step block (the even-ranked CTA the first N / 2), at the same shared-memory offsets; each CTA's
+// TMEM receives its own 128 x N accumulator.  Only the even-ranked CTA issues.
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// shared::cluster address of the same shared-memory variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
@@ -256,10 +313,23 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_commit(uint32_t bar)
+// tcgen05.commit by the lanes with `issue` != 0 (the MMA warp runs converged; one lane issues).  For a
+// CTA pair the commit arrives on the barrier at the same offset in every CTA of `mask`.
+template <int PAIR = 0>
+__device__ __forceinline__ void tc_commit_if(uint32_t bar, uint32_t issue, uint16_t mask = 3)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
+    if (PAIR)
+        asm volatile(
+            "{\n\t.reg .pred e;\n\tsetp.ne.b32 e, %1, 0;\n\t"
+            "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %2;\n\t}" ::"r"(bar),
+            "r"(issue), "h"(mask)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred e;\n\tsetp.ne.b32 e, %1, 0;\n\t"
+            "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar),
+            "r"(issue)
+            : "memory");
 }
 
 // K-major shared-memory matrix descriptors: SWIZZLE_128B (A: 128-byte rows, 8-row groups 1024 B
@@ -270,38 +340,57 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
 constexpr uint32_t kDescHi128 = (1024u >> 4) | (1u << 14) | (2u << 29);
 constexpr uint32_t kDescHi32 = (256u >> 4) | (1u << 14) | (6u << 29);
 
-// instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = n
-__device__ __forceinline__ uint32_t instr_desc(int prec, int n)
+// instruction descriptor: FP32 accumulate, K-major A and B, M = m (128, or 256 for a CTA pair), N = n
+__device__ __forceinline__ uint32_t instr_desc(int prec, int n, int m = 128)
 {
     const uint32_t fmt = prec == GRACE_TF32 ? 2u : 1u;   // TF32 = 2, BF16 = 1
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 // tcgen05.mma (kind::tf32, or kind::f16 with bf16 operands) with the operand descriptors given as
-// their two 32-bit halves.  Only the low half (start address >> 4 | leading-byte-offset field)
-// changes from one k-step to the next, so the issuing thread advances it with one 32-bit add per
-// operand: measured on this part, an issue loop that rebuilds 64-bit descriptors per instruction
-// keeps the tensor pipe about half idle (one thread issues every MMA, and its scalar work sits
-// between consecutive instructions).
-template <int PREC>
+// their two 32-bit halves, issued by the lanes with `issue` != 0.  Only the low half (start
+// address >> 4 | leading-byte-offset field) changes from one k-step to the next, so the issuing
+// warp advances it with one 32-bit add per operand: measured on this part, an issue loop that
+// rebuilds 64-bit descriptors per instruction keeps the tensor pipe about half idle.  The whole
+// warp runs the issue loop (converged) and one lane's instructions are predicated on: a loop run
+// by a lone lane of a diverged warp leaves the tensor pipe idle for ~400 cycles at every exit
+// and re-entry of its inner loop (~200 for a converged warp), measured with groups of 11
+// instructions.
+template <int PREC, int PAIR = 0>
 __device__ __forceinline__ void mma_lohi(uint32_t d, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi,
-                                         uint32_t idesc, uint32_t acc)
+                                         uint32_t idesc, uint32_t acc, uint32_t issue)
 {
-    if (PREC == GRACE_TF32)
+    if (PAIR && PREC == GRACE_TF32)
         asm volatile(
-            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
-            "setp.ne.b32 p, %6, 0;\n\t"
+            "{\n\t.reg .pred p, e;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\tsetp.ne.b32 e, %7, 0;\n\t"
             "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], da, db, %5, p;\n\t}" ::"r"(d),
-            "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc)
+            "@e tcgen05.mma.cta_group::2.kind::tf32 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+            "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc), "r"(issue)
+            : "memory");
+    else if (PAIR)
+        asm volatile(
+            "{\n\t.reg .pred p, e;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\tsetp.ne.b32 e, %7, 0;\n\t"
+            "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+            "@e tcgen05.mma.cta_group::2.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+            "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc), "r"(issue)
+            : "memory");
+    else if (PREC == GRACE_TF32)
+        asm volatile(
+            "{\n\t.reg .pred p, e;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\tsetp.ne.b32 e, %7, 0;\n\t"
+            "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+            "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc), "r"(issue)
             : "memory");
     else
         asm volatile(
-            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
-            "setp.ne.b32 p, %6, 0;\n\t"
+            "{\n\t.reg .pred p, e;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\tsetp.ne.b32 e, %7, 0;\n\t"
             "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d),
-            "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc)
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+            "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc), "r"(issue)
             : "memory");
 }
 
@@ -336,6 +425,7 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 struct Smem {
     uint64_t a_full[2], a_empty[2];
     uint64_t full[kMaxSlots], empty[kMaxSlots];
+    uint64_t peer_a_full[2], peer_full[kMaxSlots];   // CTA pairs: the odd CTA's A / B halves landed
     uint64_t acc_full[2], acc_empty[2];
     uint64_t mma_drain;
     uint32_t tmem_base;
@@ -343,12 +433,19 @@ struct Smem {
     int slot_issued[kMaxSlots];  // copies issued per slot (producer)
     int slot_done[kMaxSlots];    // copies consumed per slot (MMA)
     int a_issued[2], a_done[2];
+    int items_done;              // work items the epilogue finished
 };
 
+// records a failure and stops every role of this CTA (and of the peer CTA of a pair)
+template <int PAIR = 0>
 __device__ __forceinline__ void fail(const TcParams &P, volatile int *abort_flag, int code)
 {
     if (P.err) atomicOr(P.err, code);
     *abort_flag = 1;
+    if (PAIR) {
+        const uint32_t peer = cluster_addr(smem_u32((const void *)abort_flag), cluster_rank() ^ 1u);
+        asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
+    }
 }
 
 // One tile of the epilogue for a p window of width W: loads the cell's ghat
@@ -398,16 +495,31 @@ __device__ __forceinline__ void load_window(const uint8_t *a_gen, long long a_ti
     }
 }
 
-template <int PREC, int W, int G>
-__device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_bytes, int row, int acol,
-                                         uint32_t tcol, int nf, int fs, int part, float *Facc)
+// Releases an accumulator buffer to the MMA warp once this warp's TMEM reads of it are complete (for a
+// CTA pair, on the even CTA's barrier: its MMAs write both CTAs' accumulators).
+template <int PAIR = 0>
+__device__ __forceinline__ void release_acc(uint32_t bar, int lane)
 {
-    float gw[W];
-    load_window<PREC, W>(a_gen, a_tile_bytes, row, acol, gw);
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) {
+        if (PAIR) mbar_arrive_remote(cluster_addr(bar, 0u));
+        else mbar_arrive(bar);
+    }
+}
+
+// The window gw is loaded before the accumulator is ready; the accumulator buffer is released
+// (acc_empty) right after the last TMEM wait, before the last FMAs.
+template <int W, int G, int PAIR>
+__device__ __forceinline__ void epi_tile(const float *gw, uint32_t tcol, int nf, int fs, int part, float *Facc,
+                                         uint32_t acc_empty, int lane)
+{
+    bool released = false;
 #pragma unroll
     for (int m0 = 0; m0 < kEpiF; m0 += G) {
         if (kEpiSplit * m0 + part >= nf) break;
         if (kEpiSplit * (m0 + G - 1) + part < fs) continue;
+        const bool last = m0 + G >= kEpiF || kEpiSplit * (m0 + G) + part >= nf;
         uint32_t y[G][W];
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
@@ -418,6 +530,10 @@ __device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_
             }
         }
         tmem_wait_ld();
+        if (last) {
+            release_acc<PAIR>(acc_empty, lane);
+            released = true;
+        }
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
             const int f = kEpiSplit * (m0 + gg) + part;
@@ -432,6 +548,7 @@ __device__ __forceinline__ void epi_tile(const uint8_t *a_gen, long long a_tile_
             }
         }
     }
+    if (!released) release_acc<PAIR>(acc_empty, lane);
 }
 
 // Epilogue of a species tile (mixtures of Sec. 5.3): the accumulator holds, for the cell's total
@@ -553,7 +670,11 @@ __device__ __forceinline__ void epi_tile_vjp(uint32_t tcol, int nf, int fs, int 
     }
 }
 
-template <int PREC, int MODE>
+// PAIR = 1: launched in clusters of two CTAs that share every work item (cta_group::2, M = 256);
+// the even-ranked CTA issues the MMAs, the odd-ranked CTA's MMA warp relays to it when its own A
+// and B halves have landed (its copies arrive on its own barriers), and both epilogues release the
+// accumulators on the even CTA's barrier.
+template <int PREC, int MODE, int PAIR>
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 {
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
@@ -573,24 +694,32 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NS = P.n_slots;
-    const int n_items = P.n_cell_tiles * P.n_splits;
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const bool lead = rank == 0;
+    const int n_items = (PAIR ? P.n_pair_tiles : P.n_cell_tiles) * P.n_splits;
+    const int item0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;     // a pair shares its items
+    const int item_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
     if (threadIdx.x == 0) {
+        // the even CTA of a pair also counts the odd CTA's epilogue warps
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S->a_full[b]), 1);
+            mbar_init(smem_u32(&S->peer_a_full[b]), 1);
             mbar_init(smem_u32(&S->a_empty[b]), 1 + kEpiWarps);
             mbar_init(smem_u32(&S->acc_full[b]), 1);
-            mbar_init(smem_u32(&S->acc_empty[b]), kEpiWarps);
+            mbar_init(smem_u32(&S->acc_empty[b]), (PAIR ? 2 : 1) * kEpiWarps);
             S->a_issued[b] = S->a_done[b] = 0;
         }
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&S->full[s]), 1);
+            mbar_init(smem_u32(&S->peer_full[s]), 1);
             mbar_init(smem_u32(&S->empty[s]), 1);
             S->slot_issued[s] = 0;
             S->slot_done[s] = 0;
         }
         mbar_init(smem_u32(&S->mma_drain), 1);
         S->abort_flag = 0;
+        S->items_done = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // tile table and functional order into shared memory (read by every role for every tile)
@@ -606,14 +735,24 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         }
     }
     if (warp == 2) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&S->tmem_base)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        // a pair allocates collectively (one warp of each CTA), the same columns in both SMs
+        if (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&S->tmem_base)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&S->tmem_base)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync_all();   // both CTAs' barriers initialised and TMEM allocated
     tc_fence_after();
     const uint32_t tmem = S->tmem_base;
 
@@ -621,14 +760,14 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         // ------------------------------------------------ A loader (after the TMEM allocation): the
         // next work item's A tile as soon as the previous use of that buffer is released
         int ctl = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
-            const ItemCtx c = item_ctx<MODE>(P, it, tiles, ford);
+        for (int it = item0; it < n_items; it += item_step, ++ctl) {
+            const ItemCtx c = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             int ok = 1;
             if (lane == 0) {
                 if (*abort_flag) ok = 0;
-                else if (au > 0 && !mbar_wait(smem_u32(&S->a_empty[ab]), (au - 1) & 1, abort_flag, P.wait_cycles)) {
-                    fail(P, abort_flag, 1);
+                else if (au > 0 && !mbar_wait<PAIR>(smem_u32(&S->a_empty[ab]), (au - 1) & 1, abort_flag, P.wait_cycles)) {
+                    fail<PAIR>(P, abort_flag, 1);
                     ok = 0;
                 }
                 if (ok) {
@@ -647,20 +786,21 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         // boundaries, limited only by the ring.
         const int me = warp == 0 ? 0 : 1;
         int q = 0;
-        for (int it = blockIdx.x; it < n_items && !P.withhold_b; it += gridDim.x) {
-            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
+        for (int it = item0; it < n_items && !P.withhold_b; it += item_step) {
+            const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
             int ok = *abort_flag ? 0 : 1;
             for (int t = ic.t0; t < ic.t1 && ok; ++t) {
                 const TileDesc td = ic.tiles[t];
                 const int nks = td.ks_hi - td.ks_lo, n_copies = (nks + kps - 1) / kps;
-                const uint32_t ks_bytes = (uint32_t)td.n * 32u * planes;
-                const uint8_t *bsrc = ic.B + (size_t)td.b_off16 * 16;
+                // a pair's B images hold each tile as [CTA half][k-step][plane][N / 2 rows x 32 B]
+                const uint32_t ks_bytes = (uint32_t)td.n * (PAIR ? 16u : 32u) * planes;
+                const uint8_t *bsrc = ic.B + (size_t)td.b_off16 * 16 + (PAIR ? (size_t)rank * nks * ks_bytes : 0);
                 if (lane == 0)
                     for (int c = 0; c < n_copies; ++c, ++q) {
                         if ((q & 1) != me) continue;
                         const int slot = q % NS, use = q / NS;
-                        if (use > 0 && !mbar_wait(smem_u32(&S->empty[slot]), (use - 1) & 1, abort_flag, P.wait_cycles)) {
-                            fail(P, abort_flag, 2);
+                        if (use > 0 && !mbar_wait<PAIR>(smem_u32(&S->empty[slot]), (use - 1) & 1, abort_flag, P.wait_cycles)) {
+                            fail<PAIR>(P, abort_flag, 2);
                             ok = 0;
                             break;
                         }
@@ -676,92 +816,150 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             }
             if (!ok) break;
         }
-    } else if (warp == 1 && lane == 0) {
-        // ------------------------------------------------ MMA issuer
-        int q = 0, acc_use = 0, ctl = 0;
-        for (int it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x, ++ctl) {
-            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
+    } else if (warp == 1 && PAIR && !lead) {
+        // ------------------------------------------------ odd CTA of a pair: relays "A landed" and
+        // "B landed" of its own copies to the even CTA's barriers, in the issuer's order
+        int q = 0, ctl = 0;
+        bool stop = __any_sync(0xffffffffu, *abort_flag != 0);
+        const uint32_t lead_cta = 0u;
+        for (int it = item0; it < n_items && !stop; it += item_step, ++ctl) {
+            const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
-            if (!mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles)) {
-                fail(P, abort_flag, 4);
+            if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles))) {
+                if (lane == 0) fail<PAIR>(P, abort_flag, 4);
+                stop = true;
                 break;
             }
-            S->a_done[ab] = au + 1;
+            if (lane == 0) {
+                S->a_done[ab] = au + 1;
+                mbar_arrive_remote(cluster_addr(smem_u32(&S->peer_a_full[ab]), lead_cta));
+            }
+            for (int t = ic.t0; t < ic.t1 && !stop; ++t) {
+                const TileDesc td = ic.tiles[t];
+                const int nks = td.ks_hi - td.ks_lo, n_copies = (nks + kps - 1) / kps;
+                for (int c = 0; c < n_copies; ++c, ++q) {
+                    const int slot = q % NS, use = q / NS;
+                    if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->full[slot]), use & 1, abort_flag, P.wait_cycles))) {
+                        if (lane == 0) fail<PAIR>(P, abort_flag, 16);
+                        stop = true;
+                        break;
+                    }
+                    if (lane == 0) {
+                        S->slot_done[slot] = use + 1;
+                        mbar_arrive_remote(cluster_addr(smem_u32(&S->peer_full[slot]), lead_cta));
+                    }
+                }
+                if (!stop) stop = __any_sync(0xffffffffu, *abort_flag != 0);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer: the warp runs converged, lane 0
+        // issues; every wait and every abort test is made warp-uniform before it steers the loop
+        const uint32_t leader = lane == 0 ? 1u : 0u;
+        constexpr int kM = PAIR ? 2 * kTileM : kTileM;
+        int q = 0, acc_use = 0, ctl = 0;
+        bool stop = __any_sync(0xffffffffu, *abort_flag != 0);
+        for (int it = item0; it < n_items && !stop; it += item_step, ++ctl) {
+            const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
+            const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
+            if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles) &&
+                                             (!PAIR || mbar_wait<PAIR>(smem_u32(&S->peer_a_full[ab]), au & 1, abort_flag,
+                                                                        P.wait_cycles)))) {
+                if (leader) fail<PAIR>(P, abort_flag, 4);
+                stop = true;
+                break;
+            }
+            if (leader) S->a_done[ab] = au + 1;
             tc_fence_after();
             const uint32_t a0 = a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes;
             const uint32_t a0_lo = ((a0 >> 4) & 0x3FFFu) | (1u << 16);       // descriptor low half of A
             const uint32_t alo_delta = (uint32_t)(ic.a_bytes / 2) >> 4;      // to the lo plane (BF16)
-            for (int t = ic.t0; t < ic.t1 && !*abort_flag; ++t) {
+            for (int t = ic.t0; t < ic.t1 && !stop; ++t) {
                 const TileDesc td = ic.tiles[t];
                 const int buf = acc_use & 1, bu = acc_use >> 1;
-                if (bu > 0 && !mbar_wait(smem_u32(&S->acc_empty[buf]), (bu - 1) & 1, abort_flag, P.wait_cycles)) {
-                    fail(P, abort_flag, 8);
+                if (bu > 0 &&
+                    !__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->acc_empty[buf]), (bu - 1) & 1, abort_flag, P.wait_cycles))) {
+                    if (leader) fail<PAIR>(P, abort_flag, 8);
+                    stop = true;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * kAccCols);
-                const uint32_t idesc = instr_desc(PREC, td.n);
-                const uint32_t ks_bytes = (uint32_t)td.n * 32u * planes;
+                const uint32_t idesc = instr_desc(PREC, td.n, kM);
+                // this CTA's rows of a k-step block: N (one CTA) or N / 2 (each CTA of a pair)
+                const uint32_t ks_bytes = (uint32_t)td.n * (PAIR ? 16u : 32u) * planes;
                 const int nks = td.ks_hi - td.ks_lo, n_copies = (nks + kps - 1) / kps;
                 uint32_t acc = 0u;
                 for (int c = 0; c < n_copies; ++c) {
                     const int slot = q % NS, use = q / NS;
-                    if (!mbar_wait(smem_u32(&S->full[slot]), use & 1, abort_flag, P.wait_cycles)) {
-                        fail(P, abort_flag, 16);
+                    if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->full[slot]), use & 1, abort_flag, P.wait_cycles) &&
+                                                     (!PAIR || mbar_wait<PAIR>(smem_u32(&S->peer_full[slot]), use & 1, abort_flag,
+                                                                                P.wait_cycles)))) {
+                        if (leader) fail<PAIR>(P, abort_flag, 16);
+                        stop = true;
                         break;
                     }
-                    S->slot_done[slot] = use + 1;
+                    if (leader) S->slot_done[slot] = use + 1;
                     tc_fence_after();
                     const uint32_t bslot = b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes;
                     const int k0 = c * kps, kn = min(kps, nks - k0);
                     // descriptor low halves in 16-byte units: A k-step ks sits in 128-byte atom ks / 4
                     // (128 rows x 128 B apart) at 32 B x (ks % 4); B k-step blocks follow each other
                     uint32_t b_lo = ((bslot >> 4) & 0x3FFFu) | (1u << 16);
-                    const uint32_t b_step = ks_bytes >> 4, b_plane = (uint32_t)td.n * 2u;
+                    const uint32_t b_step = ks_bytes >> 4, b_plane = (uint32_t)td.n * (PAIR ? 1u : 2u);
                     int ks = td.ks_lo + k0;
                     for (int kk = 0; kk < kn; ++kk, ++ks, b_lo += b_step) {
                         const uint32_t a_lo16 = a0_lo + (uint32_t)(ks >> 2) * (kTileM * 8u) + (uint32_t)(ks & 3) * 2u;
                         if (PREC == GRACE_TF32) {
-                            mma_lohi<PREC>(d, a_lo16, kDescHi128, b_lo, kDescHi32, idesc, acc);
+                            mma_lohi<PREC, PAIR>(d, a_lo16, kDescHi128, b_lo, kDescHi32, idesc, acc, leader);
                         } else {
-                            mma_lohi<PREC>(d, a_lo16, kDescHi128, b_lo, kDescHi32, idesc, acc);
-                            mma_lohi<PREC>(d, a_lo16, kDescHi128, b_lo + b_plane, kDescHi32, idesc, 1u);
-                            mma_lohi<PREC>(d, a_lo16 + alo_delta, kDescHi128, b_lo, kDescHi32, idesc, 1u);
+                            mma_lohi<PREC, PAIR>(d, a_lo16, kDescHi128, b_lo, kDescHi32, idesc, acc, leader);
+                            mma_lohi<PREC, PAIR>(d, a_lo16, kDescHi128, b_lo + b_plane, kDescHi32, idesc, 1u, leader);
+                            mma_lohi<PREC, PAIR>(d, a_lo16 + alo_delta, kDescHi128, b_lo, kDescHi32, idesc, 1u, leader);
                         }
                         acc = 1u;
                     }
-                    tc_commit(smem_u32(&S->empty[slot]));   // frees the slot once these MMAs retire
+                    tc_commit_if<PAIR>(smem_u32(&S->empty[slot]), leader);   // frees the slot once these MMAs retire
                     ++q;
                 }
-                if (*abort_flag) break;
+                if (stop) break;
                 if (!acc) {
-                    fail(P, abort_flag, 64);   // tiles are built with a non-empty K range
+                    if (leader) fail<PAIR>(P, abort_flag, 64);   // tiles are built with a non-empty K range
+                    stop = true;
                     break;
                 }
-                tc_commit(smem_u32(&S->acc_full[buf]));
+                tc_commit_if<PAIR>(smem_u32(&S->acc_full[buf]), leader);
                 ++acc_use;
+                stop = __any_sync(0xffffffffu, *abort_flag != 0);
             }
-            tc_commit(smem_u32(&S->a_empty[ab]));   // the A tile may be overwritten once these MMAs retire
+            if (stop) break;
+            tc_commit_if<PAIR>(smem_u32(&S->a_empty[ab]), leader);   // the A tile may be overwritten once these MMAs retire
+            stop = __any_sync(0xffffffffu, *abort_flag != 0);
         }
-        if (*abort_flag) {
-            tc_commit(smem_u32(&S->mma_drain));
+        __syncwarp();
+        if (leader && *abort_flag) {
+            // every MMA this warp issued has retired before the CTA (and its pair) may leave
+            tc_commit_if<PAIR>(smem_u32(&S->mma_drain), 1u, 1);
             const long long t0 = clock64();
             while (!mbar_try_wait(smem_u32(&S->mma_drain), 0) && clock64() - t0 < kWaitCycles) {
             }
         }
+        __syncwarp();
     } else if (warp >= 4) {
         // ------------------------------------------------ epilogue: one thread per cell
+        constexpr bool kPlainEpi = MODE == kModeF || MODE == kModeMulti;   // epi_tile: window loaded early
         const int part = (warp - 4) >> 2;    // functionals f with f % kEpiSplit == part
         const int qd = warp & 3;             // TMEM lane quadrant (warp % 4)
         const int row = qd * 32 + lane;
         const uint32_t tlane = (uint32_t)(qd * 32) << 16;
         int acc_use = 0, ctl = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++ctl) {
-            const ItemCtx ic = item_ctx<MODE>(P, it, tiles, ford);
+        for (int it = item0; it < n_items; it += item_step, ++ctl) {
+            const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
             const int ct = ic.ct;
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
-            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles))) {
-                fail(P, abort_flag, 32);
+            if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles))) {
+                fail<PAIR>(P, abort_flag, 32);
                 break;
             }
             const uint8_t *a_gen = gbase + (size_t)ab * P.a_tile_bytes;
@@ -789,8 +987,10 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 const TileDesc td = ic.tiles[t];
                 const int nf = td.nf_flush & 0xFF, fs = (td.nf_flush >> 8) & 0xFF;
                 const int buf = acc_use & 1, bu = acc_use >> 1;
-                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->acc_full[buf]), bu & 1, abort_flag, P.wait_cycles))) {
-                    fail(P, abort_flag, 128);
+                float gw[kPlainEpi ? kWin : 1];
+                if (kPlainEpi) load_window<PREC, kWin>(a_gen, ic.a_bytes, row, td.acol, gw);
+                if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->acc_full[buf]), bu & 1, abort_flag, P.wait_cycles))) {
+                    fail<PAIR>(P, abort_flag, 128);
                     aborted = true;
                     break;
                 }
@@ -805,10 +1005,8 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     epi_tile_species<kWin>(P.gsp + (size_t)ct * P.gsp_kpad * kTileM, P.gsp_sstride, P.n_species,
                                            P.gsp_kpad, row, td.acol, tcol, nf, fs, part, FaccS);
                 else
-                    epi_tile<PREC, kWin, 2>(a_gen, ic.a_bytes, row, td.acol, tcol, nf, fs, part, Facc);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&S->acc_empty[buf]));
+                    epi_tile<kWin, 2, PAIR>(gw, tcol, nf, fs, part, Facc, smem_u32(&S->acc_empty[buf]), lane);
+                if (!kPlainEpi) release_acc<PAIR>(smem_u32(&S->acc_empty[buf]), lane);
                 ++acc_use;
                 if (MODE == kModeVJP && (td.nf_flush >> 16)) {
                     // last tile of this coefficient window: this warp's partial sums over its functionals
@@ -850,6 +1048,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             if (aborted) break;
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&S->a_empty[ab]));
+            if (warp == 4 && lane == 0) S->items_done = ctl + 1;
         }
     }
 
@@ -857,6 +1056,14 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
     // every role has stopped issuing; after an abort, drain the copies still in flight
     __syncwarp();
     __syncthreads();
+    if (PAIR && warp == 4 && lane == 0 && !*abort_flag && S->items_done > 0) {
+        // the last item's A release is a commit multicast by the even CTA: it has landed here before
+        // this CTA may leave (bounded)
+        const int last = S->items_done - 1, ab = last % P.a_bufs, au = last / P.a_bufs;
+        const long long t0 = clock64();
+        while (!mbar_try_wait_cluster(smem_u32(&S->a_empty[ab]), au & 1) && clock64() - t0 < kWaitCycles) {
+        }
+    }
     if (warp == 0 && lane == 0 && *abort_flag) {
         // drain copies still in flight into this CTA's shared memory (bounded)
         for (int s = 0; s < NS; ++s)
@@ -874,10 +1081,17 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
     }
     tc_fence_before();
     __syncthreads();
+    // a CTA of a pair leaves only when its peer no longer arrives on its barriers, its MMAs no longer
+    // read the peer's shared memory, and the pair frees its TMEM together
+    if (PAIR) cluster_sync_all();
     tc_fence_after();
     if (warp == 2) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
-                     : "memory");
+        if (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                         : "memory");
     }
 }
 
@@ -887,6 +1101,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 void free_tc_tiles(TcTiles &t)
 {
     cudaFree(t.d_b);
+    cudaFree(t.d_b_pair);
     cudaFree(t.d_desc);
     cudaFree(t.d_ford);
     cudaFree(t.d_D0);
@@ -1035,7 +1250,7 @@ Plan plan_forms(const Forms &F, const std::vector<int> &ford, int prec)
 // B images (SWIZZLE_32B k-step blocks, bf16 hi/lo planes or TF32) and tile descriptors of a
 // plan, uploaded into out; written[r] = 1 for every functional the contraction writes
 grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &ford, int prec, TcTiles &out,
-                        std::vector<int> &written, bool window_major = false)
+                        std::vector<int> &written, bool window_major = false, bool pair_image = false)
 {
     const int R = F.R, W = F.W, nw = F.n_win();
     const int eb = elem_bytes(prec), planes = n_planes(prec);
@@ -1153,7 +1368,27 @@ grace_status emit_tiles(const Forms &F, const Plan &pl, const std::vector<int> &
         return GRACE_ERR_UNSUPPORTED;
     }
     out.group_tile.push_back((int)tiles.size());
+    // CTA-pair images: every tile's k-step blocks split into the halves of their rows (the N / 2
+    // rows of each half start on an 8-row boundary, so the 32-byte swizzle of each row is kept),
+    // each half's blocks contiguous so that a CTA copies only its own
+    std::vector<uint8_t> Bp;
+    if (pair_image) {
+        Bp.assign(B.size(), 0);
+        for (const TileDesc &td : tiles) {
+            const size_t blk = (size_t)td.n * 32, half = blk / 2;
+            const int nks = td.ks_hi - td.ks_lo;
+            const uint8_t *src = B.data() + (size_t)td.b_off16 * 16;
+            uint8_t *dst = Bp.data() + (size_t)td.b_off16 * 16;
+            for (int hh = 0; hh < 2; ++hh)
+                for (int s = 0; s < nks; ++s)
+                    for (int pl = 0; pl < planes; ++pl)
+                        std::memcpy(dst + (((size_t)hh * nks + s) * planes + pl) * half,
+                                    src + ((size_t)s * planes + pl) * blk + (size_t)hh * half, half);
+        }
+    }
     cudaError_t e = cudaMalloc(&out.d_b, B.size());
+    if (e == cudaSuccess && pair_image) e = cudaMalloc(&out.d_b_pair, Bp.size());
+    if (e == cudaSuccess && pair_image) e = cudaMemcpy(out.d_b_pair, Bp.data(), Bp.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&out.d_desc, tiles.size() * sizeof(TileDesc));
     if (e == cudaSuccess) e = cudaMalloc(&out.d_ford, ford.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(out.d_b, B.data(), B.size(), cudaMemcpyHostToDevice);
@@ -1209,7 +1444,7 @@ std::vector<int> functional_order(const DevGroup &g)
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
 {
     TcTiles out;
-    grace_status s = build_tc_tiles_from(G, G.d_T, prec, out, st, false);
+    grace_status s = build_tc_tiles_from(G, G.d_T, prec, out, st, false, true);
     if (s != GRACE_OK) return s;
     free_tc_tiles(G.tc[prec]);
     G.tc[prec] = out;
@@ -1230,7 +1465,7 @@ grace_status build_species_tiles(Group &G, int prec, cudaStream_t st)
 // tiles of the quadratic forms d_T ([R][P][P], FP64, device) of group G; an all-zero d_T gives
 // built tiles with n_tiles = 0 (nothing to contract)
 grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st,
-                                 bool unfolded_only)
+                                 bool unfolded_only, bool pair_image)
 {
     const DevGroup &g = G.dg;
     if (g.k > kKMax) {
@@ -1297,7 +1532,7 @@ grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, Tc
     const Plan pU = unfolded_only ? Plan() : plan_forms(FU, ford, prec);
     const bool use_fold = !unfolded_only && pU.cost <= pT.cost;
     std::vector<int> written;
-    grace_status s = emit_tiles(use_fold ? FU : FT, use_fold ? pU : pT, ford, prec, out, written);
+    grace_status s = emit_tiles(use_fold ? FU : FT, use_fold ? pU : pT, ford, prec, out, written, false, pair_image);
     if (s != GRACE_OK) return s;
     e = cudaMalloc(&out.d_written, R * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(out.d_written, written.data(), R * sizeof(int), cudaMemcpyHostToDevice);
@@ -1484,7 +1719,13 @@ static void choose_splits(const TcTiles &t, int n_cell_tiles, int n_sm, TcParams
 // of the process waits at most this many cycles and issues no B copies.
 static std::atomic<long long> g_armed_wait_cycles{0};
 
-template <int PREC, int MODE>
+// CTA pairs (grace_set_cta_pairs): 0 (default) never, 1 every forward contraction of at least two
+// cell tiles, 2 multi-group launches only.  Measured on this part, pairs were slower in both
+// places (BF16x3, 65,536 cells: 571 against 644 TFLOP/s; uneven batch: 327 against 354): halving
+// each SM's table bytes does not shorten the wait for a tile's table copy.
+static std::atomic<int> g_cta_pairs{0};
+
+template <int PREC, int MODE, int PAIR = 0>
 static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
 {
     P.wait_cycles = kWaitCycles;
@@ -1506,21 +1747,52 @@ static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
     // deeper ring of small ones: measured on the 65,536-cell workload (BF16x3), two A tiles with a
     // 3-deep ring of 32 KB copies took 0.217 ms against 0.203 ms for one A tile and 2 x 64 KB (the
     // A-tile waits fell from 21k to 4k cycles per CTA, the B and per-copy time grew by 50k).
-    auto slot_of = [&](int kps) { return (int)(((size_t)kps * max_rows * 32 * planes + 1023) / 1024 * 1024); };
-    P.kps = PREC == GRACE_TF32 ? 8 : 4;
+    // A CTA of a pair holds half the rows of every k-step block: its copies of up to 64 KB take 8 BF16
+    // / 16 TF32 k-steps at N = 256, a whole tile of the additive workload in one copy (copies of 32 KB
+    // in a 4-deep ring measured slower: the copy engine pays per copy more than per byte).
+    const int rows_cta = PAIR ? max_rows / 2 : max_rows;
+    auto slot_of = [&](int kps) { return (int)(((size_t)kps * rows_cta * 32 * planes + 1023) / 1024 * 1024); };
+    P.kps = (PREC == GRACE_TF32 ? 8 : 4) * (PAIR ? 2 : 1);
     while (P.kps > 1 && fixed + a1 + 2 * (size_t)slot_of(P.kps) > (size_t)kSmemLimit) P.kps /= 2;
     P.a_bufs = fixed + 2 * a1 + 4 * (size_t)slot_of(P.kps) <= (size_t)kSmemLimit ? 2 : 1;
     P.slot_bytes = slot_of(P.kps);
     if (fixed + P.a_bufs * a1 + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
     P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed - P.a_bufs * a1) / P.slot_bytes);
     const size_t smem = fixed + P.a_bufs * a1 + (size_t)P.n_slots * P.slot_bytes;
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = contract_tc_kernel<PREC, MODE, PAIR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int items = P.n_cell_tiles * P.n_splits;
-    const int grid = std::min(items, sm_count(dev));
-    contract_tc_kernel<PREC, MODE><<<grid, kThreads, smem, st>>>(P);
+    if (!PAIR) {
+        const int items = P.n_cell_tiles * P.n_splits;
+        const int grid = std::min(items, sm_count(dev));
+        kern<<<grid, kThreads, smem, st>>>(P);
+        return cudaGetLastError();
+    }
+    // clusters of two CTAs, as many as can be resident at once (a persistent kernel: every cluster
+    // loops over its share of the items)
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * (sm_count(dev) / 2));
+    int max_clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (max_clusters < 1) return cudaErrorInvalidConfiguration;
+    const int items = P.n_pair_tiles * P.n_splits;
+    cfg.gridDim = dim3(2 * std::min(items, max_clusters));
+    e = cudaLaunchKernelEx(&cfg, kern, P);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1544,6 +1816,13 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
     P.err = d_err;
     int dev = 0;
     cudaGetDevice(&dev);
+    if (!t.nc && t.d_b_pair && P.n_cell_tiles >= 2 && g_cta_pairs.load() == 1) {
+        P.B = (const uint8_t *)t.d_b_pair;
+        P.n_pair_tiles = (P.n_cell_tiles + 1) / 2;
+        choose_splits(t, P.n_pair_tiles, sm_count(dev) / 2, P);
+        return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeF, 1>(P, t.max_rows, st)
+                                  : launch_prec<GRACE_BF16X3, kModeF, 1>(P, t.max_rows, st);
+    }
     choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
     if (t.nc) {
         P.D0 = t.d_D0;
@@ -1592,6 +1871,7 @@ void free_tc_multi(TcMulti &m)
 {
     cudaFree(m.d_groups);
     cudaFree(m.d_items);
+    cudaFree(m.d_pair_items);
     m = TcMulti();
 }
 
@@ -1599,7 +1879,8 @@ grace_status build_tc_multi(int prec, const std::vector<TcMultiPart> &parts, TcM
 {
     free_tc_multi(out);
     std::vector<TcGroupDesc> groups;
-    std::vector<std::pair<double, int2>> items;
+    std::vector<std::pair<double, int2>> items, pitems;
+    int pair_ok = 1;
     long long max_a = 0;
     int max_rows = 0;
     for (size_t i = 0; i < parts.size(); ++i) {
@@ -1613,6 +1894,8 @@ grace_status build_tc_multi(int prec, const std::vector<TcMultiPart> &parts, TcM
         g.tiles = (const TileDesc *)p.t->d_desc;
         g.ford = p.t->d_ford;
         g.B = (const uint8_t *)p.t->d_b;
+        g.Bp = (const uint8_t *)p.t->d_b_pair;
+        if (!g.Bp) pair_ok = 0;
         g.A = (const uint8_t *)p.opA;
         g.F = p.F32;
         g.a_tile_bytes = (long long)opA_tile_bytes(prec, p.t->k_pad);
@@ -1624,14 +1907,21 @@ grace_status build_tc_multi(int prec, const std::vector<TcMultiPart> &parts, TcM
         max_rows = std::max(max_rows, p.t->max_rows);
         const int n_ct = (p.n_cells + kTileM - 1) / kTileM;
         for (int ct = 0; ct < n_ct; ++ct) items.push_back({p.t->pred_clk, make_int2((int)i, ct)});
+        for (int u = 0; u < (n_ct + 1) / 2; ++u) pitems.push_back({p.t->pred_clk, make_int2((int)i, u)});
         groups.push_back(g);
     }
     // largest items first: the round-robin assignment then approximates a balanced schedule
-    std::stable_sort(items.begin(), items.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
-    std::vector<int2> it(items.size());
+    auto by_cost = [](const auto &a, const auto &b) { return a.first > b.first; };
+    std::stable_sort(items.begin(), items.end(), by_cost);
+    std::stable_sort(pitems.begin(), pitems.end(), by_cost);
+    std::vector<int2> it(items.size()), pit(pitems.size());
     for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
+    for (size_t i = 0; i < pitems.size(); ++i) pit[i] = pitems[i].second;
     cudaError_t e = cudaMalloc(&out.d_groups, std::max<size_t>(groups.size(), 1) * sizeof(TcGroupDesc));
     if (e == cudaSuccess) e = cudaMalloc(&out.d_items, std::max<size_t>(it.size(), 1) * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&out.d_pair_items, std::max<size_t>(pit.size(), 1) * sizeof(int2));
+    if (e == cudaSuccess && !pit.empty())
+        e = cudaMemcpy(out.d_pair_items, pit.data(), pit.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !groups.empty())
         e = cudaMemcpy(out.d_groups, groups.data(), groups.size() * sizeof(TcGroupDesc), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !it.empty()) e = cudaMemcpy(out.d_items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
@@ -1640,6 +1930,8 @@ grace_status build_tc_multi(int prec, const std::vector<TcMultiPart> &parts, TcM
         return cuda_fail(e, "multi-group contraction: upload");
     }
     out.n_items = (int)it.size();
+    out.n_pair_items = (int)pit.size();
+    out.pair_ok = pair_ok;
     out.max_a = max_a;
     out.max_rows = max_rows;
     out.prec = prec;
@@ -1657,6 +1949,13 @@ cudaError_t launch_contract_tc_multi(const TcMulti &m, int *d_err, cudaStream_t 
     P.n_splits = 1;
     P.a_tile_bytes = m.max_a;     // stride of the A buffers in shared memory
     P.err = d_err;
+    if (m.pair_ok && g_cta_pairs.load() != 0) {
+        // each group's tables stream once per pair of its cell tiles instead of once per tile
+        P.items = (const int2 *)m.d_pair_items;
+        P.n_pair_tiles = m.n_pair_items;
+        return m.prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeMulti, 1>(P, m.max_rows, st)
+                                    : launch_prec<GRACE_BF16X3, kModeMulti, 1>(P, m.max_rows, st);
+    }
     return m.prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeMulti>(P, m.max_rows, st)
                                 : launch_prec<GRACE_BF16X3, kModeMulti>(P, m.max_rows, st);
 }
@@ -1688,6 +1987,16 @@ cudaError_t launch_vjp_tc(const DevGroup &g, const TcTiles &t, int prec, const v
 }
 
 }  // namespace grace
+
+extern "C" grace_status grace_set_cta_pairs(int mode)
+{
+    if (mode < 0 || mode > 2) {
+        grace::set_error("grace_set_cta_pairs: mode must be 0, 1 or 2");
+        return GRACE_ERR_ARG;
+    }
+    grace::g_cta_pairs.store(mode);
+    return GRACE_OK;
+}
 
 extern "C" grace_status grace_test_arm_wait_timeout(long long wait_cycles)
 {

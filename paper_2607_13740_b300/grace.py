@@ -52,7 +52,7 @@ def exported_symbols():
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_set_grouped", "grace_batch_destroy",
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
             "grace_step_host", "grace_step_host_wait", "grace_flags_check",
-            "grace_test_arm_wait_timeout", "grace_probe_mma", "grace_substep", "grace_rhs_species",
+            "grace_test_arm_wait_timeout", "grace_set_cta_pairs", "grace_probe_mma", "grace_substep", "grace_rhs_species",
             "grace_step_species", "grace_rosenbrock_step"]
 
 
@@ -103,6 +103,7 @@ def load(path: str | None = None):
     L.grace_step_host_wait.argtypes = [_VP]
     L.grace_flags_check.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_uint)]
     L.grace_test_arm_wait_timeout.argtypes = [ctypes.c_longlong]
+    L.grace_set_cta_pairs.argtypes = [ctypes.c_int]
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -149,6 +150,16 @@ def arm_wait_timeout(wait_cycles: int):
     """One-shot failure-detection check: the next tensor-core contraction launch issues no
     operand copies and its bounded waits give up after wait_cycles (grace_test_arm_wait_timeout)."""
     _check(load().grace_test_arm_wait_timeout(int(wait_cycles)), "grace_test_arm_wait_timeout")
+
+
+CTA_PAIRS_NEVER, CTA_PAIRS_ALWAYS, CTA_PAIRS_MULTI = 0, 1, 2
+
+
+def set_cta_pairs(mode: int):
+    """Process-wide: where forward contractions in the tensor forms run on CTA pairs
+    (cta_group::2): CTA_PAIRS_NEVER (the default), CTA_PAIRS_ALWAYS or CTA_PAIRS_MULTI
+    (multi-group launches only) (grace_set_cta_pairs)."""
+    _check(load().grace_set_cta_pairs(int(mode)), "grace_set_cta_pairs")
 
 
 def probe_rates(device: int = 0):

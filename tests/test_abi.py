@@ -118,6 +118,15 @@ def test_binding_fails_loudly_without_the_library():
     assert "CUDA library not built" in out.stderr
 
 
+def test_set_cta_pairs_accepts_only_its_three_modes():
+    for v in (0, 1, 2):
+        grace.set_cta_pairs(v)
+    for bad in (-1, 3):
+        with pytest.raises(grace.GraceError):
+            grace.set_cta_pairs(bad)
+    grace.set_cta_pairs(grace.CTA_PAIRS_NEVER)
+
+
 def test_arm_wait_timeout_rejects_bad_limits():
     """The failure-detection hook takes limits in [1, 4e9] cycles only (no GPU needed)."""
     with pytest.raises(grace.GraceError):

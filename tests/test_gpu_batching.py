@@ -118,24 +118,30 @@ def test_graph_replay_is_bitwise_identical(form):
     assert torch.equal(out, ref)
 
 
+@pytest.mark.parametrize("pairs", [grace.CTA_PAIRS_NEVER, grace.CTA_PAIRS_ALWAYS], ids=["single", "pairs"])
 @pytest.mark.parametrize("form", [grace.TF32, grace.BF16X3], ids=["tf32", "bf16x3"])
-def test_grouped_step_equals_per_group_launches(form):
+def test_grouped_step_equals_per_group_launches(form, pairs):
     # groups of very different sizes (N 16..80, k 0..3): several cell tiles for some groups,
-    # ragged last tiles everywhere
+    # ragged last tiles everywhere; the grouped and the per-group launches both on single CTAs or
+    # both on CTA pairs (the same pairs of a group's cell tiles)
     specs, group, ic, dt = W.uneven_batch(900, seed=1107, n_range=(16, 80), orders=(0, 1, 2, 3))
     ctx = grace.Context(specs, 0, precisions=FORMS)
     b = ctx.batch(len(group), group)
     g0 = b.project(W.IC_EXP, ic)
     dtt = torch.as_tensor(dt, device=DEV)
     res = {}
-    for grouped in (True, False):
-        b.set_grouped(grouped)
-        g = g0.clone()
-        mass = torch.zeros(len(group), dtype=torch.float64, device=DEV)
-        flags = torch.zeros(len(group), dtype=torch.uint8, device=DEV)
-        b.step(g, dtt, 3, form, mass=mass, flags=flags)
-        b.step(g, dtt, 2, form)
-        res[grouped] = (g, mass, flags)
+    grace.set_cta_pairs(pairs)
+    try:
+        for grouped in (True, False):
+            b.set_grouped(grouped)
+            g = g0.clone()
+            mass = torch.zeros(len(group), dtype=torch.float64, device=DEV)
+            flags = torch.zeros(len(group), dtype=torch.uint8, device=DEV)
+            b.step(g, dtt, 3, form, mass=mass, flags=flags)
+            b.step(g, dtt, 2, form)
+            res[grouped] = (g, mass, flags)
+    finally:
+        grace.set_cta_pairs(grace.CTA_PAIRS_NEVER)
     assert torch.equal(res[True][0], res[False][0])
     assert torch.equal(res[True][2], res[False][2])
     # the grouped K-c sums a cell's mass over 16 lanes; the per-group launch may use 32

@@ -411,6 +411,16 @@ GRACE_API grace_status grace_test_arm_wait_timeout(long long wait_cycles);
    this call. */
 GRACE_API grace_status grace_set_cta_pairs(int mode);
 
+/* Selects, for the whole process, whether single-group forward contractions in
+   the tensor forms keep the cells' A tile in tensor memory: enable = 1, for
+   groups whose A tile takes at most 128 TMEM columns (TF32 or BF16 hi + lo of
+   at most 128 coefficients), with table tiles of N <= 192 and a three-deep
+   ring of 64 KB table copies in shared memory; enable = 0 (the default) keeps
+   A in shared memory (N <= 256, two ring slots), which measured faster on a
+   B300.  CTA pairs selected with mode 1 take precedence.  Returns
+   GRACE_ERR_ARG for other values.  The paper has no counterpart of this call. */
+GRACE_API grace_status grace_set_tc_a_in_tmem(int enable);
+
 /* Measures, on `device`, the CUDA-core throughput used as roofline
    denominators: rates[0] FP64 FMA/s, rates[1] FP32 FMA/s, rates[2] FP64->FP32
    conversions/s (3 doubles, host).  Allocates and synchronises. */

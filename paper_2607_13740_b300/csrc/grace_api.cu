@@ -469,11 +469,11 @@ grace_status grace_tile_info(const grace_ctx *ctx, int group, int prec, long lon
         set_error("grace_tile_info: bad argument");
         return GRACE_ERR_ARG;
     }
-    const TcTiles &t = ctx->groups[group].tc[prec];
-    if (!t.built) {
+    if (!ctx->groups[group].tc[prec].built) {
         set_error("grace_tile_info: precision not precomputed");
         return GRACE_ERR_ORDER;
     }
+    const TcTiles &t = tc_forward_tiles(ctx->groups[group].tc[prec]);
     info[0] = t.n_tiles;
     info[1] = t.mma_per_tile;
     info[2] = t.mac_per_cell;

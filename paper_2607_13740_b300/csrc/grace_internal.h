@@ -40,6 +40,7 @@ struct TcTiles {
     void *d_b = nullptr;      // pre-swizzled B k-step blocks (all tiles back to back)
     void *d_b_pair = nullptr; // the same images for CTA pairs: per tile [half][k-step][plane][N / 2 rows]
                               // (forward tiles only; null elsewhere)
+    TcTiles *at = nullptr;    // forward tiles of N <= 192 for the A-in-tensor-memory form (owned)
     void *d_desc = nullptr;   // per-tile descriptors
     int *d_ford = nullptr;    // functional ids in tile order
     size_t b_bytes = 0;
@@ -366,8 +367,10 @@ cudaError_t launch_nc_partial_tc(const DevGroup &g, const NcTables &nt, const Tc
 
 // tensor-core path
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st);
+// the tile set a single-group forward contraction of t runs (t, or its A-in-tensor-memory tiles)
+const TcTiles &tc_forward_tiles(const TcTiles &t);
 grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st,
-                                 bool unfolded_only = false, bool pair_image = false);
+                                 bool unfolded_only = false, bool pair_image = false, int max_n = 256);
 // tiles of T as built (no fold) for the species contraction, into G.tcs[prec]
 grace_status build_species_tiles(Group &G, int prec, cudaStream_t st);
 // species of mixed grains: F_s[c, r] = sum_p ghat_{s,p} sum_q That_r[p, q] ghat_q for every species, the

@@ -106,6 +106,9 @@ struct TcParams {
     int n_cells;
     int n_cell_tiles;
     int n_pair_tiles;     // CTA pairs: pairs of cell tiles (the last one may have no odd tile)
+    // TMEM columns of accumulator buffer 0 and the distance to buffer 1; with A in TMEM, the
+    // columns of one A plane (A occupies [0, planes x at_plane_cols))
+    int acc_base, acc_stride, at_plane_cols;
     int R;
     float *F;
     int slot_bytes;       // bytes of one ring slot
@@ -394,6 +397,39 @@ __device__ __forceinline__ void mma_lohi(uint32_t d, uint32_t a_lo, uint32_t a_h
             : "memory");
 }
 
+// A operand in tensor memory: tcgen05.cp of one k-step of A (128 rows x 32 bytes, the same K-major
+// 128-byte-swizzled shared-memory descriptor as the MMA's A operand) into 8 TMEM columns, and
+// tcgen05.mma reading A from TMEM (lane = cell, K packed along the columns), by the lanes with
+// `issue` != 0.
+__device__ __forceinline__ void tc_cp_a(uint32_t taddr, uint32_t desc_lo, uint32_t desc_hi, uint32_t issue)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t.reg .b64 d;\n\tsetp.ne.b32 e, %3, 0;\n\tmov.b64 d, {%1, %2};\n\t"
+        "@e tcgen05.cp.cta_group::1.128x256b [%0], d;\n\t}" ::"r"(taddr),
+        "r"(desc_lo), "r"(desc_hi), "r"(issue)
+        : "memory");
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma_tmem_a(uint32_t d, uint32_t a_t, uint32_t b_lo, uint32_t b_hi, uint32_t idesc,
+                                           uint32_t acc, uint32_t issue)
+{
+    if (PREC == GRACE_TF32)
+        asm volatile(
+            "{\n\t.reg .pred p, e;\n\t.reg .b64 db;\n\t"
+            "setp.ne.b32 p, %5, 0;\n\tsetp.ne.b32 e, %6, 0;\n\tmov.b64 db, {%2, %3};\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], db, %4, p;\n\t}" ::"r"(d),
+            "r"(a_t), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc), "r"(issue)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p, e;\n\t.reg .b64 db;\n\t"
+            "setp.ne.b32 p, %5, 0;\n\tsetp.ne.b32 e, %6, 0;\n\tmov.b64 db, {%2, %3};\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], db, %4, p;\n\t}" ::"r"(d),
+            "r"(a_t), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc), "r"(issue)
+            : "memory");
+}
+
 // TMEM -> registers, 32 lanes x 16 / 32 columns, no wait
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r)
 {
@@ -428,6 +464,7 @@ struct Smem {
     uint64_t peer_a_full[2], peer_full[kMaxSlots];   // CTA pairs: the odd CTA's A / B halves landed
     uint64_t acc_full[2], acc_empty[2];
     uint64_t mma_drain;
+    uint64_t a_free;             // A in TMEM: the MMAs of a work item have retired
     uint32_t tmem_base;
     int abort_flag;
     int slot_issued[kMaxSlots];  // copies issued per slot (producer)
@@ -670,13 +707,22 @@ __device__ __forceinline__ void epi_tile_vjp(uint32_t tcol, int nf, int fs, int 
     }
 }
 
-// PAIR = 1: launched in clusters of two CTAs that share every work item (cta_group::2, M = 256);
-// the even-ranked CTA issues the MMAs, the odd-ranked CTA's MMA warp relays to it when its own A
-// and B halves have landed (its copies arrive on its own barriers), and both epilogues release the
-// accumulators on the even CTA's barrier.
-template <int PREC, int MODE, int PAIR>
+// FORM 0: one CTA per work item, A in shared memory.
+// FORM 1 (CTA pair): launched in clusters of two CTAs that share every work item (cta_group::2,
+// M = 256); the even-ranked CTA issues the MMAs, the odd-ranked CTA's MMA warp relays to it when its
+// own A and B halves have landed (its copies arrive on its own barriers), and both epilogues
+// release the accumulators on the even CTA's barrier.
+// FORM 2 (A in tensor memory): a work item's A tile arrives as the first copy of its stream in a
+// ring slot and the MMA warp moves it into TMEM columns [0, planes x at_plane_cols) with
+// tcgen05.cp once the previous item's MMAs have retired; the MMAs read A from TMEM, so shared
+// memory holds only the ring (three 64 KB slots instead of two beside a 64 KB A tile) and the
+// accumulators shrink to 192 columns (N <= 192).  The epilogue reads its ghat windows from the A
+// operand in global memory.
+template <int PREC, int MODE, int FORM>
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 {
+    constexpr int PAIR = FORM == 1 ? 1 : 0;
+    constexpr bool AT = FORM == 2;
     constexpr int planes = PREC == GRACE_TF32 ? 1 : 2;
     const int kps = P.kps;                             // MMA k-steps per B copy
     extern __shared__ uint8_t smem_raw[];
@@ -718,6 +764,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             S->slot_done[s] = 0;
         }
         mbar_init(smem_u32(&S->mma_drain), 1);
+        mbar_init(smem_u32(&S->a_free), 1);
         S->abort_flag = 0;
         S->items_done = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -760,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         // ------------------------------------------------ A loader (after the TMEM allocation): the
         // next work item's A tile as soon as the previous use of that buffer is released
         int ctl = 0;
-        for (int it = item0; it < n_items; it += item_step, ++ctl) {
+        for (int it = item0; it < n_items && !AT; it += item_step, ++ctl) {
             const ItemCtx c = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
             const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
             int ok = 1;
@@ -789,6 +836,23 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         for (int it = item0; it < n_items && !P.withhold_b; it += item_step) {
             const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
             int ok = *abort_flag ? 0 : 1;
+            if (AT) {
+                // the item's A tile: the first copy of its stream
+                if (lane == 0 && ok && (q & 1) == me) {
+                    const int slot = q % NS, use = q / NS;
+                    if (use > 0 && !mbar_wait(smem_u32(&S->empty[slot]), (use - 1) & 1, abort_flag, P.wait_cycles)) {
+                        fail(P, abort_flag, 2);
+                        ok = 0;
+                    } else {
+                        mbar_expect_tx(smem_u32(&S->full[slot]), (uint32_t)ic.a_bytes);
+                        bulk_g2s(b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes, ic.A, (uint32_t)ic.a_bytes,
+                                 smem_u32(&S->full[slot]));
+                        S->slot_issued[slot] = use + 1;
+                    }
+                }
+                ++q;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+            }
             for (int t = ic.t0; t < ic.t1 && ok; ++t) {
                 const TileDesc td = ic.tiles[t];
                 const int nks = td.ks_hi - td.ks_lo, n_copies = (nks + kps - 1) / kps;
@@ -862,16 +926,41 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         bool stop = __any_sync(0xffffffffu, *abort_flag != 0);
         for (int it = item0; it < n_items && !stop; it += item_step, ++ctl) {
             const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
-            const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
-            if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles) &&
-                                             (!PAIR || mbar_wait<PAIR>(smem_u32(&S->peer_a_full[ab]), au & 1, abort_flag,
+            const int ab = AT ? 0 : ctl % P.a_bufs, au = AT ? 0 : ctl / P.a_bufs;
+            if (AT) {
+                // the item's A tile is the next copy of the ring; it moves into TMEM once the previous
+                // item's MMAs (which read the A columns) have retired
+                const int slot = q % NS, use = q / NS;
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&S->full[slot]), use & 1, abort_flag, P.wait_cycles) &&
+                                                 (ctl == 0 || mbar_wait(smem_u32(&S->a_free), (ctl - 1) & 1, abort_flag,
                                                                         P.wait_cycles)))) {
-                if (leader) fail<PAIR>(P, abort_flag, 4);
-                stop = true;
-                break;
+                    if (leader) fail(P, abort_flag, 4);
+                    stop = true;
+                    break;
+                }
+                if (leader) S->slot_done[slot] = use + 1;
+                tc_fence_after();
+                const uint32_t src_lo = (((b_smem + (uint32_t)slot * (uint32_t)P.slot_bytes) >> 4) & 0x3FFFu) | (1u << 16);
+                const uint32_t plane16 = (uint32_t)(ic.a_bytes / planes) >> 4;            // A plane, 16-byte units
+                const int ksa = (int)(ic.a_bytes / planes / (kTileM * 32));              // k-steps of a plane
+                for (int pl = 0; pl < planes; ++pl)
+                    for (int ks = 0; ks < ksa; ++ks)
+                        tc_cp_a(tmem + (uint32_t)(pl * P.at_plane_cols + ks * 8),
+                                src_lo + (uint32_t)pl * plane16 + (uint32_t)(ks >> 2) * (kTileM * 8u) + (uint32_t)(ks & 3) * 2u,
+                                kDescHi128, leader);
+                tc_commit_if(smem_u32(&S->empty[slot]), leader);   // the slot returns once the copies are done
+                ++q;
+            } else {
+                if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles) &&
+                                                 (!PAIR || mbar_wait<PAIR>(smem_u32(&S->peer_a_full[ab]), au & 1, abort_flag,
+                                                                            P.wait_cycles)))) {
+                    if (leader) fail<PAIR>(P, abort_flag, 4);
+                    stop = true;
+                    break;
+                }
+                if (leader) S->a_done[ab] = au + 1;
+                tc_fence_after();
             }
-            if (leader) S->a_done[ab] = au + 1;
-            tc_fence_after();
             const uint32_t a0 = a_smem + (uint32_t)ab * (uint32_t)P.a_tile_bytes;
             const uint32_t a0_lo = ((a0 >> 4) & 0x3FFFu) | (1u << 16);       // descriptor low half of A
             const uint32_t alo_delta = (uint32_t)(ic.a_bytes / 2) >> 4;      // to the lo plane (BF16)
@@ -885,7 +974,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * kAccCols);
+                const uint32_t d = tmem + (uint32_t)(P.acc_base + buf * P.acc_stride);
                 const uint32_t idesc = instr_desc(PREC, td.n, kM);
                 // this CTA's rows of a k-step block: N (one CTA) or N / 2 (each CTA of a pair)
                 const uint32_t ks_bytes = (uint32_t)td.n * (PAIR ? 16u : 32u) * planes;
@@ -910,6 +999,17 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     const uint32_t b_step = ks_bytes >> 4, b_plane = (uint32_t)td.n * (PAIR ? 1u : 2u);
                     int ks = td.ks_lo + k0;
                     for (int kk = 0; kk < kn; ++kk, ++ks, b_lo += b_step) {
+                        if (AT) {
+                            // A k-step ks: 8 TMEM columns per plane
+                            const uint32_t a_t = tmem + (uint32_t)(ks * 8);
+                            mma_tmem_a<PREC>(d, a_t, b_lo, kDescHi32, idesc, acc, leader);
+                            if (PREC != GRACE_TF32) {
+                                mma_tmem_a<PREC>(d, a_t, b_lo + b_plane, kDescHi32, idesc, 1u, leader);
+                                mma_tmem_a<PREC>(d, a_t + (uint32_t)P.at_plane_cols, b_lo, kDescHi32, idesc, 1u, leader);
+                            }
+                            acc = 1u;
+                            continue;
+                        }
                         const uint32_t a_lo16 = a0_lo + (uint32_t)(ks >> 2) * (kTileM * 8u) + (uint32_t)(ks & 3) * 2u;
                         if (PREC == GRACE_TF32) {
                             mma_lohi<PREC, PAIR>(d, a_lo16, kDescHi128, b_lo, kDescHi32, idesc, acc, leader);
@@ -934,7 +1034,8 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                 stop = __any_sync(0xffffffffu, *abort_flag != 0);
             }
             if (stop) break;
-            tc_commit_if<PAIR>(smem_u32(&S->a_empty[ab]), leader);   // the A tile may be overwritten once these MMAs retire
+            if (AT) tc_commit_if(smem_u32(&S->a_free), leader);      // the A columns may be overwritten once these MMAs retire
+            else tc_commit_if<PAIR>(smem_u32(&S->a_empty[ab]), leader);   // the A tile may be overwritten once these MMAs retire
             stop = __any_sync(0xffffffffu, *abort_flag != 0);
         }
         __syncwarp();
@@ -957,12 +1058,14 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
         for (int it = item0; it < n_items; it += item_step, ++ctl) {
             const ItemCtx ic = item_ctx<MODE, PAIR>(P, it, tiles, ford, rank);
             const int ct = ic.ct;
-            const int ab = ctl % P.a_bufs, au = ctl / P.a_bufs;
-            if (!__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles))) {
+            const int ab = AT ? 0 : ctl % P.a_bufs, au = AT ? 0 : ctl / P.a_bufs;
+            if (!AT && !__all_sync(0xffffffffu, mbar_wait<PAIR>(smem_u32(&S->a_full[ab]), au & 1, abort_flag, P.wait_cycles))) {
                 fail<PAIR>(P, abort_flag, 32);
                 break;
             }
-            const uint8_t *a_gen = gbase + (size_t)ab * P.a_tile_bytes;
+            // the ghat windows: from the A tile in shared memory, or (A in TMEM) from the A operand in
+            // global memory
+            const uint8_t *a_gen = AT ? ic.A : gbase + (size_t)ab * P.a_tile_bytes;
             const long long cell = (long long)ct * kTileM + row;
             const bool live = cell < ic.n_cells;
             const float s_cell = MODE == kModeNC && live ? P.cell_s[cell] : 0.f;
@@ -995,7 +1098,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tcol = tmem + tlane + (uint32_t)(buf * kAccCols);
+                const uint32_t tcol = tmem + tlane + (uint32_t)(P.acc_base + buf * P.acc_stride);
                 if (MODE == kModeNC)
                     epi_tile_nc<PREC, 1>(a_gen, ic.a_bytes, row, td.p0, tcol, nf, fs, part, s_cell, D0s, P.ramp_a,
                                          P.ramp_b, Facc);
@@ -1047,7 +1150,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
             }
             if (aborted) break;
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&S->a_empty[ab]));
+            if (!AT && lane == 0) mbar_arrive(smem_u32(&S->a_empty[ab]));
             if (warp == 4 && lane == 0) S->items_done = ctl + 1;
         }
     }
@@ -1100,6 +1203,10 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams P)
 // ------------------------------------------------------------------ host side
 void free_tc_tiles(TcTiles &t)
 {
+    if (t.at) {
+        free_tc_tiles(*t.at);
+        delete t.at;
+    }
     cudaFree(t.d_b);
     cudaFree(t.d_b_pair);
     cudaFree(t.d_desc);
@@ -1196,7 +1303,7 @@ double tile_cost(int prec, int n, int nks)
 
 // dynamic program over the functional order: best[y] = cheapest cover of ford[0, y) by
 // groups of consecutive functionals, each group one N-tile per non-empty window
-Plan plan_forms(const Forms &F, const std::vector<int> &ford, int prec)
+Plan plan_forms(const Forms &F, const std::vector<int> &ford, int prec, int max_n = kMaxN)
 {
     const int R = F.R, W = F.W, nw = F.n_win(), kstep = 32 / elem_bytes(prec);
     Plan pl;
@@ -1219,7 +1326,7 @@ Plan plan_forms(const Forms &F, const std::vector<int> &ford, int prec)
     std::vector<double> best(R + 1, inf);
     std::vector<int> from(R + 1, -1);
     best[0] = 0.0;
-    const int maxf = std::min(kMaxF, kMaxN / W);
+    const int maxf = std::min(kMaxF, std::min(kMaxN, max_n) / W);
     for (int x = 0; x < R; ++x) {
         if (best[x] >= inf) continue;
         std::vector<Ext> Un(nw, Ext{F.kdim, 0});
@@ -1441,11 +1548,28 @@ std::vector<int> functional_order(const DevGroup &g)
 
 }  // namespace
 
+// TMEM columns of one A plane in the A-in-tensor-memory form, and the accumulator width that leaves
+__host__ __device__ inline int at_plane_cols(int prec, int kpad) { return kpad * elem_bytes(prec) / 4; }
+inline int at_acc_cols(int prec, int kpad)
+{
+    return (kTmemCols - n_planes(prec) * at_plane_cols(prec, kpad)) / 2 / 16 * 16;
+}
+
 grace_status build_tc_tiles(Group &G, int prec, cudaStream_t st)
 {
     TcTiles out;
     grace_status s = build_tc_tiles_from(G, G.d_T, prec, out, st, false, true);
     if (s != GRACE_OK) return s;
+    // the A-in-tensor-memory form for groups whose A tile takes at most 128 TMEM columns (N <= 192)
+    if (n_planes(prec) * at_plane_cols(prec, out.k_pad) <= 128) {
+        TcTiles at;
+        s = build_tc_tiles_from(G, G.d_T, prec, at, st, false, false, at_acc_cols(prec, out.k_pad));
+        if (s != GRACE_OK) {
+            free_tc_tiles(out);
+            return s;
+        }
+        out.at = new TcTiles(at);
+    }
     free_tc_tiles(G.tc[prec]);
     G.tc[prec] = out;
     return GRACE_OK;
@@ -1465,7 +1589,7 @@ grace_status build_species_tiles(Group &G, int prec, cudaStream_t st)
 // tiles of the quadratic forms d_T ([R][P][P], FP64, device) of group G; an all-zero d_T gives
 // built tiles with n_tiles = 0 (nothing to contract)
 grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, TcTiles &out, cudaStream_t st,
-                                 bool unfolded_only, bool pair_image)
+                                 bool unfolded_only, bool pair_image, int max_n)
 {
     const DevGroup &g = G.dg;
     if (g.k > kKMax) {
@@ -1528,8 +1652,8 @@ grace_status build_tc_tiles_from(const Group &G, const double *d_T, int prec, Tc
         out.built = 1;
         return GRACE_OK;
     }
-    const Plan pT = plan_forms(FT, ford, prec);
-    const Plan pU = unfolded_only ? Plan() : plan_forms(FU, ford, prec);
+    const Plan pT = plan_forms(FT, ford, prec, max_n);
+    const Plan pU = unfolded_only ? Plan() : plan_forms(FU, ford, prec, max_n);
     const bool use_fold = !unfolded_only && pU.cost <= pT.cost;
     std::vector<int> written;
     grace_status s = emit_tiles(use_fold ? FU : FT, use_fold ? pU : pT, ford, prec, out, written, false, pair_image);
@@ -1725,9 +1849,17 @@ static std::atomic<long long> g_armed_wait_cycles{0};
 // each SM's table bytes does not shorten the wait for a tile's table copy.
 static std::atomic<int> g_cta_pairs{0};
 
-template <int PREC, int MODE, int PAIR = 0>
+// the A-in-tensor-memory form for single-group forward contractions (grace_set_tc_a_in_tmem), off by
+// default: measured slower on this part (BF16x3, 65,536 cells: 505 against 604 TFLOP/s; TF32 186
+// against 216).  Its tiles are narrower (N <= 192: 45 tiles instead of 36) and each tile still waits
+// ~880 cycles for its table copy with the 3-deep ring, as with the 2-deep one.
+static std::atomic<int> g_a_in_tmem{0};
+
+template <int PREC, int MODE, int FORM = 0>
 static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
 {
+    constexpr int PAIR = FORM == 1 ? 1 : 0;
+    constexpr bool AT = FORM == 2;
     P.wait_cycles = kWaitCycles;
     P.withhold_b = 0;
     const long long armed = g_armed_wait_cycles.exchange(0);
@@ -1752,14 +1884,34 @@ static cudaError_t launch_prec(TcParams P, int max_rows, cudaStream_t st)
     // in a 4-deep ring measured slower: the copy engine pays per copy more than per byte).
     const int rows_cta = PAIR ? max_rows / 2 : max_rows;
     auto slot_of = [&](int kps) { return (int)(((size_t)kps * rows_cta * 32 * planes + 1023) / 1024 * 1024); };
+    P.acc_base = 0;
+    P.acc_stride = kAccCols;
+    P.at_plane_cols = 0;
+    if (AT) {
+        // no A tile in shared memory: ring slots of 64 KB (or the A tile, if larger) hold either the
+        // item's A tile or up to kps k-steps of B; A takes the first TMEM columns, the two
+        // accumulators the rest
+        const int kpad = (int)(a1 / ((size_t)kTileM * elem_bytes(PREC) * planes));
+        P.at_plane_cols = at_plane_cols(PREC, kpad);
+        P.acc_base = planes * P.at_plane_cols;
+        P.acc_stride = at_acc_cols(PREC, kpad);
+        if (max_rows > P.acc_stride) return cudaErrorInvalidValue;
+        P.a_bufs = 0;
+        P.kps = 1;
+        while (slot_of(P.kps + 1) <= std::max<size_t>(65536, a1)) ++P.kps;
+        P.slot_bytes = (int)((std::max<size_t>((size_t)slot_of(P.kps), a1) + 1023) / 1024 * 1024);
+        if (fixed + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
+        P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed) / P.slot_bytes);
+    } else {
     P.kps = (PREC == GRACE_TF32 ? 8 : 4) * (PAIR ? 2 : 1);
     while (P.kps > 1 && fixed + a1 + 2 * (size_t)slot_of(P.kps) > (size_t)kSmemLimit) P.kps /= 2;
     P.a_bufs = fixed + 2 * a1 + 4 * (size_t)slot_of(P.kps) <= (size_t)kSmemLimit ? 2 : 1;
     P.slot_bytes = slot_of(P.kps);
     if (fixed + P.a_bufs * a1 + 2 * (size_t)P.slot_bytes > (size_t)kSmemLimit) return cudaErrorInvalidValue;
     P.n_slots = (int)std::min<size_t>(kMaxSlots, ((size_t)kSmemLimit - fixed - P.a_bufs * a1) / P.slot_bytes);
+    }
     const size_t smem = fixed + P.a_bufs * a1 + (size_t)P.n_slots * P.slot_bytes;
-    auto kern = contract_tc_kernel<PREC, MODE, PAIR>;
+    auto kern = contract_tc_kernel<PREC, MODE, FORM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0;
@@ -1822,6 +1974,16 @@ cudaError_t launch_contract_tc(const DevGroup &g, const TcTiles &t, int prec, co
         choose_splits(t, P.n_pair_tiles, sm_count(dev) / 2, P);
         return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeF, 1>(P, t.max_rows, st)
                                   : launch_prec<GRACE_BF16X3, kModeF, 1>(P, t.max_rows, st);
+    }
+    if (!t.nc && t.at && t.at->built && t.at->n_tiles > 0 && g_a_in_tmem.load()) {
+        const TcTiles &ta = *t.at;
+        P.tiles = (const TileDesc *)ta.d_desc;
+        P.ford = ta.d_ford;
+        P.n_tiles = ta.n_tiles;
+        P.B = (const uint8_t *)ta.d_b;
+        choose_splits(ta, P.n_cell_tiles, sm_count(dev), P);
+        return prec == GRACE_TF32 ? launch_prec<GRACE_TF32, kModeF, 2>(P, ta.max_rows, st)
+                                  : launch_prec<GRACE_BF16X3, kModeF, 2>(P, ta.max_rows, st);
     }
     choose_splits(t, P.n_cell_tiles, sm_count(dev), P);
     if (t.nc) {
@@ -1987,6 +2149,26 @@ cudaError_t launch_vjp_tc(const DevGroup &g, const TcTiles &t, int prec, const v
 }
 
 }  // namespace grace
+
+namespace grace {
+// the tile set a single-group forward contraction of these tiles runs (launch_contract_tc's choice for
+// batches of at least two cell tiles)
+const TcTiles &tc_forward_tiles(const TcTiles &t)
+{
+    if (!t.nc && g_cta_pairs.load() != 1 && t.at && t.at->built && t.at->n_tiles > 0 && g_a_in_tmem.load()) return *t.at;
+    return t;
+}
+}  // namespace grace
+
+extern "C" grace_status grace_set_tc_a_in_tmem(int enable)
+{
+    if (enable != 0 && enable != 1) {
+        grace::set_error("grace_set_tc_a_in_tmem: enable must be 0 or 1");
+        return GRACE_ERR_ARG;
+    }
+    grace::g_a_in_tmem.store(enable);
+    return GRACE_OK;
+}
 
 extern "C" grace_status grace_set_cta_pairs(int mode)
 {

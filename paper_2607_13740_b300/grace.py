@@ -52,7 +52,7 @@ def exported_symbols():
             "grace_adjoint", "grace_probe_rates", "grace_batch_set_graph", "grace_batch_set_grouped", "grace_batch_destroy",
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
             "grace_step_host", "grace_step_host_wait", "grace_flags_check",
-            "grace_test_arm_wait_timeout", "grace_set_cta_pairs", "grace_probe_mma", "grace_substep", "grace_rhs_species",
+            "grace_test_arm_wait_timeout", "grace_set_cta_pairs", "grace_set_tc_a_in_tmem", "grace_probe_mma", "grace_substep", "grace_rhs_species",
             "grace_step_species", "grace_rosenbrock_step"]
 
 
@@ -104,6 +104,7 @@ def load(path: str | None = None):
     L.grace_flags_check.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_uint)]
     L.grace_test_arm_wait_timeout.argtypes = [ctypes.c_longlong]
     L.grace_set_cta_pairs.argtypes = [ctypes.c_int]
+    L.grace_set_tc_a_in_tmem.argtypes = [ctypes.c_int]
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -160,6 +161,12 @@ def set_cta_pairs(mode: int):
     (cta_group::2): CTA_PAIRS_NEVER (the default), CTA_PAIRS_ALWAYS or CTA_PAIRS_MULTI
     (multi-group launches only) (grace_set_cta_pairs)."""
     _check(load().grace_set_cta_pairs(int(mode)), "grace_set_cta_pairs")
+
+
+def set_tc_a_in_tmem(enable: bool):
+    """Process-wide: single-group forward contractions in the tensor forms keep the A tile in
+    tensor memory or in shared memory (the default) (grace_set_tc_a_in_tmem)."""
+    _check(load().grace_set_tc_a_in_tmem(1 if enable else 0), "grace_set_tc_a_in_tmem")
 
 
 def probe_rates(device: int = 0):

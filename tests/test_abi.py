@@ -127,6 +127,14 @@ def test_set_cta_pairs_accepts_only_its_three_modes():
     grace.set_cta_pairs(grace.CTA_PAIRS_NEVER)
 
 
+def test_set_tc_a_in_tmem_accepts_only_zero_and_one():
+    grace.set_tc_a_in_tmem(True)
+    grace.set_tc_a_in_tmem(False)
+    for bad in (-1, 2):
+        with pytest.raises(grace.GraceError):
+            grace._check(grace.load().grace_set_tc_a_in_tmem(bad), "grace_set_tc_a_in_tmem")
+
+
 def test_arm_wait_timeout_rejects_bad_limits():
     """The failure-detection hook takes limits in [1, 4e9] cycles only (no GPU needed)."""
     with pytest.raises(grace.GraceError):

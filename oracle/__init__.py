@@ -289,3 +289,62 @@ class Oracle:
         g = np.zeros((ic.shape[0], self.P))
         _check(lib().orc_project_batch(self._pp, ic.shape[0], int(ic_kind), _p(ic), _p(g)), "project")
         return g
+
+
+# ---------------------------------------------------------------- two dimensions (mass, volume)
+class MVDesc(ctypes.Structure):
+    _fields_ = [
+        ("Nx", ctypes.c_int), ("Nv", ctypes.c_int), ("k", ctypes.c_int), ("Q", ctypes.c_int),
+        ("x_min", ctypes.c_double), ("x_max", ctypes.c_double), ("v_min", ctypes.c_double),
+        ("v_max", ctypes.c_double), ("n_terms", ctypes.c_int),
+        ("coef", ctypes.c_double * 8), ("ax", ctypes.c_double * 8), ("bx", ctypes.c_double * 8),
+        ("av", ctypes.c_double * 8), ("bv", ctypes.c_double * 8),
+    ]
+
+
+def mv_desc(spec) -> MVDesc:
+    d = MVDesc()
+    d.Nx, d.Nv, d.k, d.Q = spec.n_x, spec.n_v, spec.order_k, spec.quad_q
+    d.x_min, d.x_max, d.v_min, d.v_max = spec.x_min, spec.x_max, spec.v_min, spec.v_max
+    d.n_terms = len(spec.terms)
+    for t, (c, ax, bx, av, bv) in enumerate(spec.terms):
+        d.coef[t], d.ax[t], d.bx[t], d.av[t], d.bv[t] = c, ax, bx, av, bv
+    return d
+
+
+class MVOracle:
+    """The two-dimensional (mass, volume) weak form of Sec. 5.3 (grace_oracle_mv.c)."""
+
+    def __init__(self, spec):
+        self.spec = spec
+        self.d = mv_desc(spec)
+        L = lib()
+        P = ctypes.POINTER(MVDesc)
+        L.orc_mv_rhs.argtypes = [P, ctypes.c_int, _D, _D]
+        L.orc_mv_step.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_int]
+        L.orc_mv_mass.argtypes = [P, ctypes.c_int, _D, _D]
+        L.orc_mv_edges.argtypes = [P, _D, _D]
+
+    def rhs(self, g):
+        g = _f64(g).reshape(-1, self.spec.n_coef)
+        L = np.zeros_like(g)
+        _check(lib().orc_mv_rhs(ctypes.byref(self.d), g.shape[0], _p(g), _p(L)), "mv rhs")
+        return L
+
+    def step(self, g, dt, n_steps):
+        g = _f64(g).reshape(-1, self.spec.n_coef).copy()
+        dt = _f64(np.broadcast_to(dt, (g.shape[0],)))
+        _check(lib().orc_mv_step(ctypes.byref(self.d), g.shape[0], _p(g), _p(dt), int(n_steps)), "mv step")
+        return g
+
+    def mass(self, g):
+        g = _f64(g).reshape(-1, self.spec.n_coef)
+        m = np.zeros(g.shape[0])
+        _check(lib().orc_mv_mass(ctypes.byref(self.d), g.shape[0], _p(g), _p(m)), "mv mass")
+        return m
+
+    def edges(self):
+        ex = np.zeros(self.spec.n_x + 1)
+        ev = np.zeros(self.spec.n_v + 1)
+        _check(lib().orc_mv_edges(ctypes.byref(self.d), _p(ex), _p(ev)), "mv edges")
+        return ex, ev

@@ -222,3 +222,65 @@ def disk_batch(n_cells=262144, seed=1003, n_bins=60, order_k=2, rho_dust=1e-12):
     ic[:, 2] = x0
     ic[:, 3] = x1
     return spec, alpha, ic
+
+
+# ---------------------------------------------------------------- two dimensions (mass, volume)
+@dataclasses.dataclass(frozen=True)
+class MVSpec:
+    """A two-dimensional (mass x, volume v) grid of Sec. 5.3: n_x x n_v logarithmic bins, degree k in
+    each coordinate (tensor-product basis), quad_q Gauss nodes per coordinate, and the collision
+    kernel K = sum_t c_t x1^ax_t x2^bx_t v1^av_t v2^bv_t given as terms (c, ax, bx, av, bv)."""
+    n_x: int = 6
+    n_v: int = 6
+    order_k: int = 1
+    x_min: float = 1e-2
+    x_max: float = 1e2
+    v_min: float = 1e-2
+    v_max: float = 1e2
+    quad_q: int = 4
+    terms: tuple = ((1.0, 0.0, 0.0, 0.0, 0.0),)
+
+    @property
+    def n_coef(self) -> int:
+        return self.n_x * self.n_v * (self.order_k + 1) ** 2
+
+
+def mv_additive_spec(n_x=6, n_v=6, order_k=1, quad_q=4, x_min=1e-2, x_max=1e2, v_min=1e-2, v_max=1e2) -> MVSpec:
+    """K = x1 + x2 (independent of the volume)."""
+    return MVSpec(n_x, n_v, order_k, x_min, x_max, v_min, v_max, quad_q,
+                  ((1.0, 1.0, 0.0, 0.0, 0.0), (1.0, 0.0, 1.0, 0.0, 0.0)))
+
+
+def mv_mixed_spec(n_x=6, n_v=6, order_k=1, quad_q=4, x_min=1e-2, x_max=1e2, v_min=1e-2, v_max=1e2) -> MVSpec:
+    """A kernel coupling both coordinates: K = 1 + 0.5 (x1 v2 + x2 v1) + 0.25 (v1^(2/3) + v2^(2/3)),
+    a constant plus cross terms and a cross-section-like volume term."""
+    return MVSpec(n_x, n_v, order_k, x_min, x_max, v_min, v_max, quad_q,
+                  ((1.0, 0.0, 0.0, 0.0, 0.0), (0.5, 1.0, 0.0, 0.0, 1.0), (0.5, 0.0, 1.0, 1.0, 0.0),
+                   (0.25, 0.0, 0.0, 2.0 / 3.0, 0.0), (0.25, 0.0, 0.0, 0.0, 2.0 / 3.0)))
+
+
+def mv_random_coefficients(spec: MVSpec, n_cells: int, seed: int = 11, support=None, rel_modes: float = 0.2):
+    """Seeded positive-mean random coefficients g_{j,m}^{p,q}, layout [cell][(j,p)][(m,q)]; `support`
+    = (jx, jv) keeps only cells j < jx, m < jv (the rest zero)."""
+    rng = np.random.default_rng(seed)
+    K1 = spec.order_k + 1
+    g = np.zeros((n_cells, spec.n_x, K1, spec.n_v, K1))
+    g[:, :, 0, :, 0] = rng.uniform(0.2, 1.0, size=(n_cells, spec.n_x, spec.n_v))
+    if K1 > 1:
+        hi = rng.uniform(-rel_modes, rel_modes, size=(n_cells, spec.n_x, K1, spec.n_v, K1))
+        hi[:, :, 0, :, 0] = 0.0
+        g += hi * g[:, :, 0:1, :, 0:1]
+    if support is not None:
+        jx, jv = support
+        g[:, jx:, :, :, :] = 0.0
+        g[:, :, :, jv:, :] = 0.0
+    return g.reshape(n_cells, spec.n_coef)
+
+
+def mv_batch(n_cells=16384, seed=1005, n_x=12, n_v=12, order_k=1, quad_q=4):
+    """The two-dimensional workload: n_cells independent cells of the mixed kernel on 12 x 12 bins over
+    four decades in mass and volume, degree 1, random positive coefficients in the lower half of
+    both coordinates (their mergers stay inside the grid), dt 1e-3 per cell."""
+    spec = mv_mixed_spec(n_x, n_v, order_k, quad_q)
+    g0 = mv_random_coefficients(spec, n_cells, seed, support=(n_x // 2, n_v // 2))
+    return spec, g0, np.full(n_cells, 1e-3)

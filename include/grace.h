@@ -421,6 +421,49 @@ GRACE_API grace_status grace_set_cta_pairs(int mode);
    GRACE_ERR_ARG for other values.  The paper has no counterpart of this call. */
 GRACE_API grace_status grace_set_tc_a_in_tmem(int enable);
 
+/* ---------------------------------------------------------------------------
+   Two-dimensional (mass x, volume v) DG (Sec. 5.3, "Toward a Multidimensional
+   Treatment").  Cells I_{j,m} = I_j x I_m of logarithmic grids (x_{j-1/2} =
+   x_min (x_max/x_min)^(j/n_x), likewise in v), the tensor-product Legendre basis
+   phi_p(xi_j(x)) phi_q(eta_m(v)) with p, q <= order_k, and the unknown g = x f.
+   The right-hand side is the Galerkin weak form of the multidimensional
+   Smoluchowski equation of Sec. 5.3 tested with x phi_{j,m}^{p,q}, with additive
+   merging (x = x1 + x2, v = v1 + v2), pairs whose merger leaves the grid lost,
+   and the collision kernel
+       K(x1, v1; x2, v2) = sum_t coef[t] x1^ax[t] x2^bx[t] v1^av[t] v2^bv[t]
+   (n_terms <= 8; give a symmetric K, e.g. both orders of an asymmetric term).
+   Every integral uses a Gauss rule of quad_q nodes per coordinate, split
+   exactly where a merger crosses a cell edge.  Coefficient layout per cell:
+   g_{j,m}^{p,q} at ((j (order_k+1) + p) n_v + m)(order_k+1) + q; n_coef =
+   n_x n_v (order_k+1)^2 doubles per cell.  FP64 throughout. */
+typedef struct {
+    int n_x, n_v;              /* bins in mass and in volume (1 .. 256)          */
+    int order_k;               /* degree in each coordinate (0 .. 4)              */
+    int quad_q;                /* Gauss nodes per coordinate and piece (1 .. 24)  */
+    double x_min, x_max, v_min, v_max;
+    int n_terms;               /* 1 .. 8                                          */
+    double coef[8], ax[8], bx[8], av[8], bv[8];
+} grace_mv_desc;
+typedef struct grace_mv grace_mv;
+
+/* Validates the description and builds, on `device`, the 1-D factor forms of
+   every kernel term (the gain forms over pairs of bins in x and in v, the loss
+   factors).  Allocates and synchronises.  GRACE_ERR_UNSUPPORTED when a cell's
+   coefficient matrix (n_x (k+1)) x (n_v (k+1)) does not fit the per-cell stage
+   in shared memory. */
+GRACE_API grace_status grace_mv_setup(grace_mv **mv, const grace_mv_desc *desc, int device);
+/* Stream for the compute calls (the legacy default stream if none). */
+GRACE_API grace_status grace_mv_set_stream(grace_mv *mv, void *cuda_stream);
+/* L = dg/dt for n_cells independent cells; g and L device arrays of n_cells x
+   n_coef doubles (must not overlap).  Asynchronous on the bound stream. */
+GRACE_API grace_status grace_mv_rhs(grace_mv *mv, int n_cells, const double *g, double *L);
+/* n_steps SSP-RK3 steps (eq. (RK3)) in place on g, dt: device array of n_cells
+   step sizes.  No limiter (positivity is the caller's choice of dt).  Allocates
+   a workspace of 3 n_cells n_coef doubles on first use or growth (synchronising
+   then); otherwise asynchronous. */
+GRACE_API grace_status grace_mv_step(grace_mv *mv, int n_cells, double *g, const double *dt, int n_steps);
+GRACE_API void grace_mv_destroy(grace_mv *mv);
+
 /* Measures, on `device`, the CUDA-core throughput used as roofline
    denominators: rates[0] FP64 FMA/s, rates[1] FP32 FMA/s, rates[2] FP64->FP32
    conversions/s (3 doubles, host).  Allocates and synchronises. */

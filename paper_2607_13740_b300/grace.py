@@ -53,7 +53,8 @@ def exported_symbols():
             "grace_destroy", "grace_tile_info", "grace_batch_cell_params", "grace_rhs_noalloc",
             "grace_step_host", "grace_step_host_wait", "grace_flags_check",
             "grace_test_arm_wait_timeout", "grace_set_cta_pairs", "grace_set_tc_a_in_tmem", "grace_probe_mma", "grace_substep", "grace_rhs_species",
-            "grace_step_species", "grace_rosenbrock_step"]
+            "grace_step_species", "grace_rosenbrock_step", "grace_mv_setup", "grace_mv_set_stream", "grace_mv_rhs",
+            "grace_mv_step", "grace_mv_destroy"]
 
 
 def load(path: str | None = None):
@@ -105,6 +106,12 @@ def load(path: str | None = None):
     L.grace_test_arm_wait_timeout.argtypes = [ctypes.c_longlong]
     L.grace_set_cta_pairs.argtypes = [ctypes.c_int]
     L.grace_set_tc_a_in_tmem.argtypes = [ctypes.c_int]
+    L.grace_mv_setup.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.grace_mv_set_stream.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.grace_mv_rhs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    L.grace_mv_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.grace_mv_destroy.argtypes = [ctypes.c_void_p]
+    L.grace_mv_destroy.restype = None
     L.grace_batch_destroy.argtypes = [_VP]
     L.grace_destroy.argtypes = [_VP]
     for name in exported_symbols():
@@ -182,6 +189,74 @@ def probe_mma(precision: int, n: int = 256, device: int = 0) -> float:
     out = ctypes.c_double()
     _check(load().grace_probe_mma(int(device), int(precision), int(n), ctypes.byref(out)), "grace_probe_mma")
     return out.value
+
+
+class MVDesc(ctypes.Structure):
+    """grace_mv_desc: the two-dimensional (mass, volume) grid, degree, rule and kernel terms."""
+    _fields_ = [
+        ("n_x", ctypes.c_int), ("n_v", ctypes.c_int), ("order_k", ctypes.c_int), ("quad_q", ctypes.c_int),
+        ("x_min", ctypes.c_double), ("x_max", ctypes.c_double), ("v_min", ctypes.c_double),
+        ("v_max", ctypes.c_double), ("n_terms", ctypes.c_int),
+        ("coef", ctypes.c_double * 8), ("ax", ctypes.c_double * 8), ("bx", ctypes.c_double * 8),
+        ("av", ctypes.c_double * 8), ("bv", ctypes.c_double * 8),
+    ]
+
+
+def mv_desc(spec) -> MVDesc:
+    d = MVDesc()
+    d.n_x, d.n_v, d.order_k, d.quad_q = spec.n_x, spec.n_v, spec.order_k, spec.quad_q
+    d.x_min, d.x_max, d.v_min, d.v_max = spec.x_min, spec.x_max, spec.v_min, spec.v_max
+    d.n_terms = len(spec.terms)
+    for t, (c, ax, bx, av, bv) in enumerate(spec.terms):
+        d.coef[t], d.ax[t], d.bx[t], d.av[t], d.bv[t] = c, ax, bx, av, bv
+    return d
+
+
+class MV:
+    """Two-dimensional (mass, volume) DG of Sec. 5.3 (grace_mv_*): g and L are float64 CUDA tensors
+    [n_cells, n_coef] in the layout ((j (k+1) + p) n_v + m)(k+1) + q."""
+
+    def __init__(self, spec, device: int = 0):
+        self.spec = spec
+        self.device = device
+        self._h = ctypes.c_void_p()
+        d = mv_desc(spec)
+        _check(load().grace_mv_setup(ctypes.byref(self._h), ctypes.byref(d), int(device)), "grace_mv_setup")
+
+    def _stream(self):
+        _check(load().grace_mv_set_stream(self._h, _stream_handle()), "grace_mv_set_stream")
+
+    def _state(self, g):
+        import torch
+        if not (g.is_cuda and g.dtype == torch.float64 and g.is_contiguous() and g.dim() == 2
+                and g.shape[1] == self.spec.n_coef):
+            raise GraceError("g must be a contiguous float64 CUDA tensor [n_cells, n_coef]")
+
+    def rhs(self, g, out=None):
+        import torch
+        self._state(g)
+        L = out if out is not None else torch.empty_like(g)
+        self._stream()
+        _check(load().grace_mv_rhs(self._h, int(g.shape[0]), _ptr(g), _ptr(L)), "grace_mv_rhs")
+        return L
+
+    def step(self, g, dt, n_steps: int):
+        """n_steps SSP-RK3 steps in place; dt a float64 CUDA tensor [n_cells]."""
+        self._state(g)
+        self._stream()
+        _check(load().grace_mv_step(self._h, int(g.shape[0]), _ptr(g), _ptr(dt), int(n_steps)), "grace_mv_step")
+        return g
+
+    def close(self):
+        if self._h:
+            load().grace_mv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:

@@ -277,10 +277,11 @@ def mv_random_coefficients(spec: MVSpec, n_cells: int, seed: int = 11, support=N
     return g.reshape(n_cells, spec.n_coef)
 
 
-def mv_batch(n_cells=16384, seed=1005, n_x=12, n_v=12, order_k=1, quad_q=4):
+def mv_batch(n_cells=16384, seed=1005, n_x=12, n_v=12, order_k=1, quad_q=8):
     """The two-dimensional workload: n_cells independent cells of the mixed kernel on 12 x 12 bins over
-    four decades in mass and volume, degree 1, random positive coefficients in the lower half of
-    both coordinates (their mergers stay inside the grid), dt 1e-3 per cell."""
+    four decades in mass and volume, degree 1, 8 Gauss nodes per coordinate, random positive
+    coefficients in the lower half of both coordinates (their mergers stay inside the grid), dt 1e-3
+    per cell."""
     spec = mv_mixed_spec(n_x, n_v, order_k, quad_q)
     g0 = mv_random_coefficients(spec, n_cells, seed, support=(n_x // 2, n_v // 2))
     return spec, g0, np.full(n_cells, 1e-3)

@@ -159,3 +159,25 @@ def test_setup_rejects_invalid_edges(lib, bad):
     st, h = _setup(lib, d)
     assert st == 1 and not h.value
     assert "edges" in lib.grace_last_error().decode()
+
+
+@pytest.mark.parametrize("field,value", [("n_x", 0), ("n_v", 0), ("order_k", 5), ("quad_q", 0), ("quad_q", 25),
+                                         ("x_min", 0.0), ("v_max", 1e-3), ("n_terms", 0), ("n_terms", 9)])
+def test_mv_setup_rejects_invalid_descriptions(field, value):
+    """The two-dimensional setup validates its description on the host (no GPU needed)."""
+    from paper_2607_13740_b300 import workloads as W
+    d = grace.mv_desc(W.mv_mixed_spec())
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert grace.load().grace_mv_setup(ctypes.byref(h), ctypes.byref(d), 0) == 1   # GRACE_ERR_ARG
+    assert not h.value
+
+
+def test_mv_setup_rejects_non_finite_kernel_terms():
+    from paper_2607_13740_b300 import workloads as W
+    d = grace.mv_desc(W.mv_mixed_spec())
+    d.coef[0] = float("nan")
+    h = ctypes.c_void_p()
+    assert grace.load().grace_mv_setup(ctypes.byref(h), ctypes.byref(d), 0) == 1
+    assert grace.load().grace_mv_rhs(None, 1, None, None) == 1
+    assert grace.load().grace_mv_step(None, 1, None, None, 1) == 1

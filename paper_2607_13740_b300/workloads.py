@@ -228,7 +228,7 @@ def disk_batch(n_cells=262144, seed=1003, n_bins=60, order_k=2, rho_dust=1e-12):
 @dataclasses.dataclass(frozen=True)
 class MVSpec:
     """A two-dimensional (mass x, volume v) grid of Sec. 5.3: n_x x n_v logarithmic bins, degree k in
-    each coordinate (tensor-product basis), quad_q Gauss nodes per coordinate, and the collision
+    each coordinate (tensor-product basis), quad_q quadrature nodes per coordinate, and the collision
     kernel K = sum_t c_t x1^ax_t x2^bx_t v1^av_t v2^bv_t given as terms (c, ax, bx, av, bv)."""
     n_x: int = 6
     n_v: int = 6
@@ -279,7 +279,7 @@ def mv_random_coefficients(spec: MVSpec, n_cells: int, seed: int = 11, support=N
 
 def mv_batch(n_cells=16384, seed=1005, n_x=12, n_v=12, order_k=1, quad_q=8):
     """The two-dimensional workload: n_cells independent cells of the mixed kernel on 12 x 12 bins over
-    four decades in mass and volume, degree 1, 8 Gauss nodes per coordinate, random positive
+    four decades in mass and volume, degree 1, 8 quadrature nodes per coordinate, random positive
     coefficients in the lower half of both coordinates (their mergers stay inside the grid), dt 1e-3
     per cell."""
     spec = mv_mixed_spec(n_x, n_v, order_k, quad_q)

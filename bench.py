@@ -815,11 +815,98 @@ def run_species(args, emit=True):
     return line
 
 
+def run_mv(args, emit=True):
+    """Two-dimensional (mass, volume) DG of Sec. 5.3: 16,384 independent cells of 12 x 12 bins over four
+    decades in each coordinate, k = 1 (576 coefficients per cell), the mixed five-term kernel, FP64;
+    one grace_mv_step call of `steps` SSP-RK3 steps timed with CUDA events (the state and the step
+    workspace, about 300 MB, exceed the 126 MB L2)."""
+    import torch
+    from paper_2607_13740_b300 import grace, workloads as W
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    n = args.cells or 16384
+    steps = args.steps or 5
+    spec, g0_np, dt_np = W.mv_batch(n_cells=n)
+    t0 = time.time()
+    mv = grace.MV(spec, local)
+    setup_s = time.time() - t0
+    g0 = torch.as_tensor(g0_np, device=dev)
+    dt = torch.as_tensor(dt_np, device=dev)
+    g = g0.clone()
+    for _ in range(max(1, args.warmup)):
+        mv.step(g, dt, 1)
+    torch.cuda.synchronize()
+    g = g0.clone()
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    mv.step(g, dt, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    sampler.__exit__(None, None, None)
+    ms = e0.elapsed_time(e1)
+    # the contraction alone, for its roofline: three RHS launches
+    L = torch.empty_like(g0)
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record()
+    for _ in range(3):
+        mv.rhs(g0, out=L)
+    r1.record()
+    torch.cuda.synchronize()
+    rhs_ms = r0.elapsed_time(r1) / 3
+    # multiply-adds of one RHS and cell as executed: per term the loss (a bilinear scalar and the
+    # cell-local operator) and the gain (per target row a: H = Xg[a] G, W = G^T H, then <Vg[b], W>,
+    # each over the source bins that can land in the target)
+    K1 = spec.order_k + 1
+    Px, Pv = spec.n_x * K1, spec.n_v * K1
+    P = Px * Pv
+    vsum = sum(((b // K1 + 1) * K1) ** 2 for b in range(Pv))
+    gain = sum(((a // K1 + 1) * K1) ** 2 * Pv + Pv * Pv * ((a // K1 + 1) * K1) + vsum for a in range(Px))
+    macs = len(spec.terms) * (P + P * K1 * K1 + gain)
+    achieved = 2.0 * macs * n / (rhs_ms / 1e3) / 1e12
+    try:
+        peak, psrc = 2.0 * grace.probe_rates(local)["fp64_fma_per_s"] / 1e12, "measured FP64 FMA rate x 2"
+    except Exception:
+        peak, psrc = NOMINAL_FP64_TFLOPS, "nominal FP64 rate"
+    # mass sum_{j,m} h_j h_m g^{00}: no merger leaves the grid in these steps, so it changes only by
+    # the quadrature difference of the gain and loss rules
+    ex = spec.x_min * (spec.x_max / spec.x_min) ** (np.arange(spec.n_x + 1) / spec.n_x)
+    ev = spec.v_min * (spec.v_max / spec.v_min) ** (np.arange(spec.n_v + 1) / spec.n_v)
+    w = (np.diff(ex)[:, None] * np.diff(ev)[None, :]).reshape(-1)
+    def mass(t):
+        return (t.cpu().numpy().reshape(n, spec.n_x, K1, spec.n_v, K1)[:, :, 0, :, 0].reshape(n, -1) * w).sum(axis=1)
+    m0, m1 = mass(g0), mass(g)
+    line = {"metric": "2-D (mass, volume) DG cell-steps/s (Sec. 5.3; 12 x 12 bins, k = 1, 5-term kernel, FP64)",
+            "value": n * steps / (ms / 1e3), "unit": "cell-steps/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"mv_{n}cells_{spec.n_x}x{spec.n_v}_k{spec.order_k}", "cells": n,
+                       "n_x": spec.n_x, "n_v": spec.n_v, "order_k": spec.order_k, "quad_q": spec.quad_q,
+                       "coef_per_cell": P, "kernel_terms": len(spec.terms),
+                       "l2": "state + step workspace about 300 MB, larger than the 126 MB L2",
+                       "timing": "one grace_mv_step call, CUDA events on the launching stream"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "kernel": "mv_rhs_kernel (FP64 contraction of the factor forms)",
+                         "algorithmic": f"2 x {macs} multiply-adds per cell and RHS x {n} cells", "peak_source": psrc},
+            "rhs_ms": rhs_ms, "setup_s": setup_s,
+            "mass_drift": float(np.abs(m1 - m0).max() / np.abs(m0).max()),
+            "clocks": sampler.summary()}
+    if emit:
+        print(json.dumps(line))
+    return line
+
+
 def run_legs(args):
     """Short runs of the other configurations after the headline (N = 1 only), so that their
     figures come from the same command: the uneven batch (grouped step, graph-replayed, 3 steps),
-    the adjoint leg (bf16x3, no FP64 comparison) and the disk workload (65,536 cells, k = 2,
-    bf16x3, 3 steps).  Each leg's own JSON line is summarised; a failing leg records its error and
+    the adjoint leg (bf16x3, no FP64 comparison), the disk workload (65,536 cells, k = 2,
+    bf16x3, 3 steps), species (bf16x3, 10 steps) and the two-dimensional (mass, volume) DG (16,384
+    cells, 3 steps).  Each leg's own JSON line is summarised; a failing leg records its error and
     never affects the headline."""
     import copy
     import torch
@@ -831,6 +918,7 @@ def run_legs(args):
         ("adjoint", run_adjoint, {"skip_fp64_compare": True}),
         ("disk", run_disk, {"cells": 65536, "steps": 3, "order": 2, "precision": "bf16x3"}),
         ("species", run_species, {"steps": 10, "precision": "bf16x3"}),
+        ("mv", run_mv, {"steps": 3}),
     ]
     for name, fn, over in plans:
         a = copy.copy(base)
@@ -878,7 +966,7 @@ def main():
     ap.add_argument("--toy-dt", type=float, default=0.05, help="toy workload: time step")
     ap.add_argument("--toy-ref-n", type=int, default=300, help="toy workload: bins of the k = 4 reference")
     ap.add_argument("--workload", default="additive",
-                    choices=["additive", "disk", "uneven", "adjoint", "eoc", "toy", "species"],
+                    choices=["additive", "disk", "uneven", "adjoint", "eoc", "toy", "species", "mv"],
                     help="additive: the batched additive-kernel headline; disk: coagulation + fragmentation "
                          "with a per-cell turbulence strength (node-space path); uneven: many groups in one batch; "
                          "adjoint: checkpointed adjoint of 200 steps with parameter gradients")
@@ -899,6 +987,9 @@ def main():
         return
     if args.workload == "toy":
         return run_toy(args)
+    if args.workload == "mv":
+        run_mv(args)
+        return
     if args.workload == "species":
         run_species(args)
         return

@@ -27,6 +27,7 @@ CASES = {
     "additive_k0": W.mv_additive_spec(4, 4, 0, 6, 0.1, 10.0, 0.1, 10.0),
     "additive_k1": W.mv_additive_spec(4, 4, 1, 6, 0.1, 10.0, 0.1, 10.0),
     "additive_k2": W.mv_additive_spec(3, 3, 2, 6, 0.1, 10.0, 0.1, 10.0),
+    "mixed_k3": W.mv_mixed_spec(2, 3, 3, 5, 0.1, 10.0, 0.1, 10.0),
     "mixed_k1_5x3": W.mv_mixed_spec(5, 3, 1, 6, 0.1, 10.0, 0.1, 100.0),
     "mixed_k1_3x5": W.mv_mixed_spec(3, 5, 1, 5, 0.01, 10.0, 0.1, 10.0),
     "product_k1": W.MVSpec(4, 4, 1, 0.1, 10.0, 0.1, 10.0, 6, ((1.0, 1.0, 1.0, 0.0, 0.0),)),
@@ -89,3 +90,22 @@ def test_workload_grid_sampled_cell():
     rate = (np.diff(ex)[None, :, None] * np.diff(ev)[None, None, :] * Lr).sum(axis=(1, 2))
     m = o.mass(g0)
     assert np.all(np.abs(rate) <= 5e-4 * m), (np.abs(rate) / m).max()
+
+
+def test_full_size_workload_conserves_mass():
+    """The benchmark's workload at its full size (16,384 cells of 12 x 12 bins, Q = 8): no merger
+    leaves the grid in these steps, and with Q = 8 the gain and loss rules agree to round-off, so
+    every cell's mass is kept over three steps (a property that holds at any size)."""
+    spec, g0, dt = W.mv_batch()
+    mv = grace.MV(spec)
+    g = torch.as_tensor(g0, device=DEV)
+    mv.step(g, torch.as_tensor(dt, device=DEV), 3)
+    K1 = spec.order_k + 1
+    o = oracle.MVOracle(spec)
+    ex, ev = o.edges()
+    w = (np.diff(ex)[:, None] * np.diff(ev)[None, :]).reshape(-1)
+    def mass(a):
+        return (a.reshape(a.shape[0], spec.n_x, K1, spec.n_v, K1)[:, :, 0, :, 0].reshape(a.shape[0], -1) * w).sum(axis=1)
+    m0, m1 = mass(g0), mass(g.cpu().numpy())
+    assert np.isfinite(m1).all()
+    assert np.abs(m1 - m0).max() <= 1e-12 * np.abs(m0).max()

@@ -39,6 +39,10 @@
 // Node-space tiles (groups with a per-cell kernel parameter, template NC): A holds the cells'
 // values at the fixed Gauss nodes, the MMA contracts over the smaller node of each pair, and the
 // epilogue weights the accumulator by the fragmentation ramp of the larger node (epi_tile_nc).
+// Launch forms (template FORM): one CTA per work item with A in shared memory (the default); CTA
+// pairs (cta_group::2, M = 256 over the two SMs of a cluster, grace_set_cta_pairs); A in tensor
+// memory (tcgen05.cp of the A tile from a ring slot, grace_set_tc_a_in_tmem).  All three run the
+// same tile schedule; the last two measured slower on this part and are off by default.
 // Every wait on an mbarrier is bounded; on timeout the CTA records an error in
 // the device error word, stops issuing work, drains its outstanding copies and
 // releases its tensor memory before returning.

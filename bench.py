@@ -817,9 +817,10 @@ def run_species(args, emit=True):
 
 def run_mv(args, emit=True):
     """Two-dimensional (mass, volume) DG of Sec. 5.3: 16,384 independent cells of 12 x 12 bins over four
-    decades in each coordinate, k = 1 (576 coefficients per cell), the mixed five-term kernel, FP64;
-    one grace_mv_step call of `steps` SSP-RK3 steps timed with CUDA events (the state and the step
-    workspace, about 300 MB, exceed the 126 MB L2)."""
+    decades in each coordinate, k = 1 (576 coefficients per cell), the mixed five-term kernel, the
+    contraction in FP64 (or FP32 with --mv-arith fp32; the state stays FP64); one grace_mv_step call
+    of `steps` SSP-RK3 steps timed with CUDA events (the state and the step workspace, about 300 MB,
+    exceed the 126 MB L2)."""
     import torch
     from paper_2607_13740_b300 import grace, workloads as W
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -829,7 +830,8 @@ def run_mv(args, emit=True):
     steps = args.steps or 5
     spec, g0_np, dt_np = W.mv_batch(n_cells=n)
     t0 = time.time()
-    mv = grace.MV(spec, local)
+    fp32 = getattr(args, "mv_arith", "fp64") == "fp32"
+    mv = grace.MV(spec, local, fp32=fp32)
     setup_s = time.time() - t0
     g0 = torch.as_tensor(g0_np, device=dev)
     dt = torch.as_tensor(dt_np, device=dev)
@@ -868,10 +870,11 @@ def run_mv(args, emit=True):
     gain = sum(((a // K1 + 1) * K1) ** 2 * Pv + Pv * Pv * ((a // K1 + 1) * K1) + vsum for a in range(Px))
     macs = len(spec.terms) * (P + P * K1 * K1 + gain)
     achieved = 2.0 * macs * n / (rhs_ms / 1e3) / 1e12
+    key, name = ("fp32_fma_per_s", "FP32") if fp32 else ("fp64_fma_per_s", "FP64")
     try:
-        peak, psrc = 2.0 * grace.probe_rates(local)["fp64_fma_per_s"] / 1e12, "measured FP64 FMA rate x 2"
+        peak, psrc = 2.0 * grace.probe_rates(local)[key] / 1e12, f"measured {name} FMA rate x 2"
     except Exception:
-        peak, psrc = NOMINAL_FP64_TFLOPS, "nominal FP64 rate"
+        peak, psrc = (None, "FP32 rate not measured") if fp32 else (NOMINAL_FP64_TFLOPS, "nominal FP64 rate")
     # mass sum_{j,m} h_j h_m g^{00}: no merger leaves the grid in these steps, so it changes only by
     # the quadrature difference of the gain and loss rules
     ex = spec.x_min * (spec.x_max / spec.x_min) ** (np.arange(spec.n_x + 1) / spec.n_x)
@@ -880,18 +883,19 @@ def run_mv(args, emit=True):
     def mass(t):
         return (t.cpu().numpy().reshape(n, spec.n_x, K1, spec.n_v, K1)[:, :, 0, :, 0].reshape(n, -1) * w).sum(axis=1)
     m0, m1 = mass(g0), mass(g)
-    line = {"metric": "2-D (mass, volume) DG cell-steps/s (Sec. 5.3; 12 x 12 bins, k = 1, 5-term kernel, FP64)",
+    line = {"metric": f"2-D (mass, volume) DG cell-steps/s (Sec. 5.3; 12 x 12 bins, k = 1, 5-term kernel, {name})",
             "value": n * steps / (ms / 1e3), "unit": "cell-steps/s", "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"mv_{n}cells_{spec.n_x}x{spec.n_v}_k{spec.order_k}", "cells": n,
+            "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
+            "config": {"workload": f"mv_{n}cells_{spec.n_x}x{spec.n_v}_k{spec.order_k}" + ("_fp32" if fp32 else ""),
+                       "cells": n, "contraction_arithmetic": name.lower(),
                        "n_x": spec.n_x, "n_v": spec.n_v, "order_k": spec.order_k, "quad_q": spec.quad_q,
                        "coef_per_cell": P, "kernel_terms": len(spec.terms),
                        "l2": "state + step workspace about 300 MB, larger than the 126 MB L2",
                        "timing": "one grace_mv_step call, CUDA events on the launching stream"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if peak else None, "traffic": None,
-                         "kernel": "mv_rhs_kernel (FP64 contraction of the factor forms)",
+                         "kernel": f"mv_rhs_kernel ({name} contraction of the factor forms)",
                          "algorithmic": f"2 x {macs} multiply-adds per cell and RHS x {n} cells", "peak_source": psrc},
             "rhs_ms": rhs_ms, "setup_s": setup_s,
             "mass_drift": float(np.abs(m1 - m0).max() / np.abs(m0).max()),
@@ -906,7 +910,7 @@ def run_legs(args):
     figures come from the same command: the uneven batch (grouped step, graph-replayed, 3 steps),
     the adjoint leg (bf16x3, no FP64 comparison), the disk workload (65,536 cells, k = 2,
     bf16x3, 3 steps), species (bf16x3, 10 steps) and the two-dimensional (mass, volume) DG (16,384
-    cells, 3 steps).  Each leg's own JSON line is summarised; a failing leg records its error and
+    cells, 3 steps, FP64 and FP32 contractions).  Each leg's own JSON line is summarised; a failing leg records its error and
     never affects the headline."""
     import copy
     import torch
@@ -918,7 +922,8 @@ def run_legs(args):
         ("adjoint", run_adjoint, {"skip_fp64_compare": True}),
         ("disk", run_disk, {"cells": 65536, "steps": 3, "order": 2, "precision": "bf16x3"}),
         ("species", run_species, {"steps": 10, "precision": "bf16x3"}),
-        ("mv", run_mv, {"steps": 3}),
+        ("mv", run_mv, {"steps": 3, "mv_arith": "fp64"}),
+        ("mv_fp32", run_mv, {"steps": 3, "mv_arith": "fp32"}),
     ]
     for name, fn, over in plans:
         a = copy.copy(base)
@@ -971,6 +976,8 @@ def main():
                          "with a per-cell turbulence strength (node-space path); uneven: many groups in one batch; "
                          "adjoint: checkpointed adjoint of 200 steps with parameter gradients")
     ap.add_argument("--order", type=int, default=2, help="disk workload: Legendre degree k (1..3)")
+    ap.add_argument("--mv-arith", default="fp64", choices=["fp64", "fp32"],
+                    help="mv workload: arithmetic of the contraction (the state stays FP64)")
     ap.add_argument("--no-legs", action="store_true",
                     help="additive workload: skip the short uneven / adjoint / disk legs reported under 'legs'")
     ap.add_argument("--variants", default=None,

@@ -435,7 +435,8 @@ GRACE_API grace_status grace_set_tc_a_in_tmem(int enable);
    Every integral uses a Gauss rule of quad_q nodes per coordinate, split
    exactly where a merger crosses a cell edge.  Coefficient layout per cell:
    g_{j,m}^{p,q} at ((j (order_k+1) + p) n_v + m)(order_k+1) + q; n_coef =
-   n_x n_v (order_k+1)^2 doubles per cell.  FP64 throughout. */
+   n_x n_v (order_k+1)^2 doubles per cell.  The state is FP64; the contraction
+   runs in FP64 or, with arithmetic = 1, in FP32. */
 typedef struct {
     int n_x, n_v;              /* bins in mass and in volume (1 .. 256)          */
     int order_k;               /* degree in each coordinate (0 .. 4)              */
@@ -443,6 +444,9 @@ typedef struct {
     double x_min, x_max, v_min, v_max;
     int n_terms;               /* 1 .. 8                                          */
     double coef[8], ax[8], bx[8], av[8], bv[8];
+    int arithmetic;            /* the RHS contraction: 0 FP64, 1 FP32 (CUDA cores;
+                                  FP32 factor forms and sums; the state, the stage
+                                  combinations of grace_mv_step and L stay FP64)  */
 } grace_mv_desc;
 typedef struct grace_mv grace_mv;
 

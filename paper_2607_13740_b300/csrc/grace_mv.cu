@@ -37,6 +37,7 @@ struct grace_mv {
     int K1 = 1, Px = 0, Pv = 0, P = 0, T = 0;
     double *ex = nullptr, *ev = nullptr, *gz = nullptr, *gw = nullptr;
     double *Xg = nullptr, *Vg = nullptr, *XL1 = nullptr, *XL2 = nullptr, *VL1 = nullptr, *VL2 = nullptr;
+    float *f32 = nullptr;    // FP32 copies of the six factor-form arrays, back to back (arithmetic 1)
     double *ws = nullptr;   // step workspace: g1, g2, L (3 x n_cap x P doubles)
     long long ws_cells = 0;
     size_t smem = 0;
@@ -195,58 +196,63 @@ __global__ void mv_loss_forms_kernel(int dim, int N, int K1, int T, int Q, const
     }
 }
 
+template <class R>
 struct MvArgs {
     int Nx, Nv, K1, Px, Pv, T;
-    const double *Xg, *Vg, *XL1, *XL2, *VL1, *VL2;
+    const R *Xg, *Vg, *XL1, *XL2, *VL1, *VL2;
 };
 
-__device__ __forceinline__ double block_sum(double v, double *red)
+template <class R>
+__device__ __forceinline__ R block_sum(R v, R *red)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double s = 0.0;
+    R s = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
     return s;
 }
 
-// L = dg/dt of one cell per CTA
-__global__ void __launch_bounds__(kMvThreads) mv_rhs_kernel(MvArgs A, int n_cells, const double *__restrict__ g,
+// L = dg/dt of one cell per CTA, in the arithmetic R (double, or float with FP32 factor forms; the
+// state is read and L written in FP64 either way)
+template <class R>
+__global__ void __launch_bounds__(kMvThreads) mv_rhs_kernel(MvArgs<R> A, int n_cells, const double *__restrict__ g,
                                                            double *__restrict__ Lout)
 {
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    R *sm = reinterpret_cast<R *>(sm_raw);
     const int Px = A.Px, Pv = A.Pv, K1 = A.K1, P = Px * Pv;
-    double *G = sm, *Lc = G + P, *H = Lc + P, *Wm = H + P, *Xa = Wm + (size_t)Pv * Pv, *red = Xa + (size_t)Px * Px;
+    R *G = sm, *Lc = G + P, *H = Lc + P, *Wm = H + P, *Xa = Wm + (size_t)Pv * Pv, *red = Xa + (size_t)Px * Px;
     const long long cell = blockIdx.x;
     if (cell >= n_cells) return;
     const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     for (int i = tid; i < P; i += nt) {
-        G[i] = g[cell * P + i];
-        Lc[i] = 0.0;
+        G[i] = (R)g[cell * P + i];
+        Lc[i] = 0;
     }
     __syncthreads();
     for (int t = 0; t < A.T; ++t) {
         // ---- loss: the bilinear scalar, then the cell-local operator
-        const double *XL2 = A.XL2 + (size_t)t * Px, *VL2 = A.VL2 + (size_t)t * Pv;
-        double part = 0.0;
+        const R *XL2 = A.XL2 + (size_t)t * Px, *VL2 = A.VL2 + (size_t)t * Pv;
+        R part = 0;
         for (int i = tid; i < P; i += nt) part += XL2[i / Pv] * VL2[i % Pv] * G[i];
-        const double S = block_sum(part, red);
-        const double *XL1 = A.XL1 + (size_t)t * A.Nx * K1 * K1, *VL1 = A.VL1 + (size_t)t * A.Nv * K1 * K1;
+        const R S = block_sum(part, red);
+        const R *XL1 = A.XL1 + (size_t)t * A.Nx * K1 * K1, *VL1 = A.VL1 + (size_t)t * A.Nv * K1 * K1;
         for (int i = tid; i < P; i += nt) {
             const int a = i / Pv, b = i % Pv, j = a / K1, p = a % K1, m = b / K1, q = b % K1;
-            double s = 0.0;
+            R s = 0;
             for (int p1 = 0; p1 < K1; ++p1) {
-                const double xl = XL1[(j * K1 + p) * K1 + p1];
-                if (xl == 0.0) continue;
+                const R xl = XL1[(j * K1 + p) * K1 + p1];
+                if (xl == (R)0) continue;
                 for (int q1 = 0; q1 < K1; ++q1) s += xl * VL1[(m * K1 + q) * K1 + q1] * G[(j * K1 + p1) * Pv + m * K1 + q1];
             }
             Lc[i] -= S * s;
         }
         __syncthreads();
         // ---- gain, one target row a at a time
-        const double *Xt = A.Xg + (size_t)t * Px * Px * Px, *Vt = A.Vg + (size_t)t * Pv * Pv * Pv;
+        const R *Xt = A.Xg + (size_t)t * Px * Px * Px, *Vt = A.Vg + (size_t)t * Pv * Pv * Pv;
         for (int a = 0; a < Px; ++a) {
             const int amax = (a / K1 + 1) * K1;             // source bins j1, j2 <= j
             for (int i = tid; i < amax * amax; i += nt) Xa[i] = Xt[((size_t)a * Px + i / amax) * Px + i % amax];
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_kernel(MvArgs A, int n_cell
             // H[a1][b2] = sum_{a2} Xa[a1][a2] G[a2][b2]
             for (int i = tid; i < amax * Pv; i += nt) {
                 const int a1 = i / Pv, b2 = i % Pv;
-                double s = 0.0;
+                R s = 0;
                 for (int a2 = 0; a2 < amax; ++a2) s += Xa[a1 * amax + a2] * G[a2 * Pv + b2];
                 H[i] = s;
             }
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_kernel(MvArgs A, int n_cell
             // W[b1][b2] = sum_{a1} G[a1][b1] H[a1][b2]
             for (int i = tid; i < Pv * Pv; i += nt) {
                 const int b1 = i / Pv, b2 = i % Pv;
-                double s = 0.0;
+                R s = 0;
                 for (int a1 = 0; a1 < amax; ++a1) s += G[a1 * Pv + b1] * H[a1 * Pv + b2];
                 Wm[i] = s;
             }
@@ -270,8 +276,8 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_kernel(MvArgs A, int n_cell
             // L[a][b] += sum_{b1, b2 <= (m+1) K1} Vg[b][b1][b2] W[b1][b2], one warp per b
             for (int b = warp; b < Pv; b += nw) {
                 const int bmax = (b / K1 + 1) * K1;
-                const double *Vb = Vt + (size_t)b * Pv * Pv;
-                double s = 0.0;
+                const R *Vb = Vt + (size_t)b * Pv * Pv;
+                R s = 0;
                 for (int i = lane; i < bmax * bmax; i += 32) {
                     const int b1 = i / bmax, b2 = i % bmax;
                     s += Vb[b1 * Pv + b2] * Wm[b1 * Pv + b2];
@@ -282,7 +288,13 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_kernel(MvArgs A, int n_cell
             __syncthreads();
         }
     }
-    for (int i = tid; i < P; i += nt) Lout[cell * P + i] = Lc[i];
+    for (int i = tid; i < P; i += nt) Lout[cell * P + i] = (double)Lc[i];
+}
+
+__global__ void mv_to_f32_kernel(long long n, const double *src, float *dst)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
 }
 
 // out = a gn + b (gs + dt_cell L), elementwise over n_cells x P
@@ -295,9 +307,9 @@ __global__ void mv_combine_kernel(long long n, int P, double a, double b, const 
     out[i] = (a == 0.0 ? 0.0 : a * gn[i]) + b * (gs[i] + h * L[i]);
 }
 
-size_t mv_smem(int Px, int Pv)
+size_t mv_smem(int Px, int Pv, size_t elem)
 {
-    return sizeof(double) * ((size_t)4 * Px * Pv + (size_t)Pv * Pv + (size_t)Px * Px + kMvThreads / 32);
+    return elem * ((size_t)4 * Px * Pv + (size_t)Pv * Pv + (size_t)Px * Px + kMvThreads / 32);
 }
 
 }  // namespace
@@ -317,8 +329,8 @@ grace_status grace_mv_setup(grace_mv **out, const grace_mv_desc *d, int device)
     if (d->n_x < 1 || d->n_v < 1 || d->n_x > 256 || d->n_v > 256 || d->order_k < 0 || d->order_k > kMvKMax ||
         d->quad_q < 1 || d->quad_q > kMvQMax || d->n_terms < 1 || d->n_terms > kMvTMax || !(d->x_min > 0) ||
         !(d->x_max > d->x_min) || !(d->v_min > 0) || !(d->v_max > d->v_min) || !std::isfinite(d->x_max) ||
-        !std::isfinite(d->v_max) || device < 0) {
-        set_error("grace_mv_setup: invalid grid, order, rule, kernel terms or device");
+        !std::isfinite(d->v_max) || device < 0 || (d->arithmetic != 0 && d->arithmetic != 1)) {
+        set_error("grace_mv_setup: invalid grid, order, rule, kernel terms, arithmetic or device");
         return GRACE_ERR_ARG;
     }
     for (int t = 0; t < d->n_terms; ++t)
@@ -328,7 +340,7 @@ grace_status grace_mv_setup(grace_mv **out, const grace_mv_desc *d, int device)
             return GRACE_ERR_ARG;
         }
     const int K1 = d->order_k + 1, Px = d->n_x * K1, Pv = d->n_v * K1;
-    const size_t smem = mv_smem(Px, Pv);
+    const size_t smem = mv_smem(Px, Pv, d->arithmetic ? sizeof(float) : sizeof(double));
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || device >= dev_count) {
         set_error("grace_mv_setup: no such CUDA device");
@@ -388,8 +400,25 @@ grace_status grace_mv_setup(grace_mv **out, const grace_mv_desc *d, int device)
     mv_loss_forms_kernel<<<(nlx + 127) / 128, 128>>>(0, d->n_x, K1, T, Q, m->ex, m->gz, m->gw, tm, m->XL1, m->XL2);
     mv_loss_forms_kernel<<<(nlv + 127) / 128, 128>>>(1, d->n_v, K1, T, Q, m->ev, m->gz, m->gw, tm, m->VL1, m->VL2);
     e = cudaGetLastError();
+    if (e == cudaSuccess && d->arithmetic == 1) {
+        // FP32 copies of the forms, in the order Xg, Vg, XL1, XL2, VL1, VL2
+        const size_t n[6] = {(size_t)nx3, (size_t)nv3, (size_t)T * d->n_x * K1 * K1, (size_t)T * Px,
+                             (size_t)T * d->n_v * K1 * K1, (size_t)T * Pv};
+        const double *src[6] = {m->Xg, m->Vg, m->XL1, m->XL2, m->VL1, m->VL2};
+        size_t tot = 0;
+        for (int i = 0; i < 6; ++i) tot += n[i];
+        e = cudaMalloc(&m->f32, tot * sizeof(float));
+        size_t off = 0;
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
+            mv_to_f32_kernel<<<(unsigned)((n[i] + 255) / 256), 256>>>((long long)n[i], src[i], m->f32 + off);
+            off += n[i];
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mv_rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = d->arithmetic ? cudaFuncSetAttribute(mv_rhs_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaFuncSetAttribute(mv_rhs_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         grace_mv_destroy(m);
         return cuda_fail(e, "grace_mv_setup: factor forms");
@@ -408,23 +437,49 @@ grace_status grace_mv_set_stream(grace_mv *m, void *stream)
     return GRACE_OK;
 }
 
-static MvArgs mv_args(const grace_mv *m)
+}  // extern "C"
+
+template <class R>
+static MvArgs<R> mv_args(const grace_mv *m)
 {
-    MvArgs A;
+    MvArgs<R> A;
     A.Nx = m->d.n_x;
     A.Nv = m->d.n_v;
     A.K1 = m->K1;
     A.Px = m->Px;
     A.Pv = m->Pv;
     A.T = m->T;
-    A.Xg = m->Xg;
-    A.Vg = m->Vg;
-    A.XL1 = m->XL1;
-    A.XL2 = m->XL2;
-    A.VL1 = m->VL1;
-    A.VL2 = m->VL2;
+    if (sizeof(R) == sizeof(double)) {
+        A.Xg = (const R *)m->Xg;
+        A.Vg = (const R *)m->Vg;
+        A.XL1 = (const R *)m->XL1;
+        A.XL2 = (const R *)m->XL2;
+        A.VL1 = (const R *)m->VL1;
+        A.VL2 = (const R *)m->VL2;
+    } else {
+        const size_t nx3 = (size_t)A.T * A.Px * A.Px * A.Px, nv3 = (size_t)A.T * A.Pv * A.Pv * A.Pv;
+        const size_t nl1x = (size_t)A.T * A.Nx * A.K1 * A.K1, nl2x = (size_t)A.T * A.Px;
+        const size_t nl1v = (size_t)A.T * A.Nv * A.K1 * A.K1;
+        const R *f = (const R *)m->f32;
+        A.Xg = f;
+        A.Vg = f + nx3;
+        A.XL1 = f + nx3 + nv3;
+        A.XL2 = f + nx3 + nv3 + nl1x;
+        A.VL1 = f + nx3 + nv3 + nl1x + nl2x;
+        A.VL2 = f + nx3 + nv3 + nl1x + nl2x + nl1v;
+    }
     return A;
 }
+
+static void mv_launch_rhs(const grace_mv *m, int n_cells, const double *g, double *L)
+{
+    if (m->d.arithmetic)
+        mv_rhs_kernel<float><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<float>(m), n_cells, g, L);
+    else
+        mv_rhs_kernel<double><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<double>(m), n_cells, g, L);
+}
+
+extern "C" {
 
 grace_status grace_mv_rhs(grace_mv *m, int n_cells, const double *g, double *L)
 {
@@ -434,7 +489,7 @@ grace_status grace_mv_rhs(grace_mv *m, int n_cells, const double *g, double *L)
     }
     if (n_cells == 0) return GRACE_OK;
     Guard guard(m->device);
-    mv_rhs_kernel<<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args(m), n_cells, g, L);
+    mv_launch_rhs(m, n_cells, g, L);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GRACE_OK : cuda_fail(e, "grace_mv_rhs");
 }
@@ -457,15 +512,14 @@ grace_status grace_mv_step(grace_mv *m, int n_cells, double *g, const double *dt
         m->ws_cells = n_cells;
     }
     double *g1 = m->ws, *g2 = g1 + n, *Lb = g2 + n;
-    const MvArgs A = mv_args(m);
     const unsigned cb = (unsigned)((n + 255) / 256);
     for (int s = 0; s < n_steps; ++s) {
-        // SSP-RK3, eq. (RK3)
-        mv_rhs_kernel<<<n_cells, kMvThreads, m->smem, m->stream>>>(A, n_cells, g, Lb);
+        // SSP-RK3, eq. (RK3); the state and the stage combinations stay FP64
+        mv_launch_rhs(m, n_cells, g, Lb);
         mv_combine_kernel<<<cb, 256, 0, m->stream>>>(n, m->P, 0.0, 1.0, g, g, dt, Lb, g1);
-        mv_rhs_kernel<<<n_cells, kMvThreads, m->smem, m->stream>>>(A, n_cells, g1, Lb);
+        mv_launch_rhs(m, n_cells, g1, Lb);
         mv_combine_kernel<<<cb, 256, 0, m->stream>>>(n, m->P, 0.75, 0.25, g, g1, dt, Lb, g2);
-        mv_rhs_kernel<<<n_cells, kMvThreads, m->smem, m->stream>>>(A, n_cells, g2, Lb);
+        mv_launch_rhs(m, n_cells, g2, Lb);
         mv_combine_kernel<<<cb, 256, 0, m->stream>>>(n, m->P, 1.0 / 3.0, 2.0 / 3.0, g, g2, dt, Lb, g);
     }
     const cudaError_t e = cudaGetLastError();
@@ -486,6 +540,7 @@ void grace_mv_destroy(grace_mv *m)
     cudaFree(m->XL2);
     cudaFree(m->VL1);
     cudaFree(m->VL2);
+    cudaFree(m->f32);
     cudaFree(m->ws);
     delete m;
 }

@@ -198,29 +198,31 @@ class MVDesc(ctypes.Structure):
         ("x_min", ctypes.c_double), ("x_max", ctypes.c_double), ("v_min", ctypes.c_double),
         ("v_max", ctypes.c_double), ("n_terms", ctypes.c_int),
         ("coef", ctypes.c_double * 8), ("ax", ctypes.c_double * 8), ("bx", ctypes.c_double * 8),
-        ("av", ctypes.c_double * 8), ("bv", ctypes.c_double * 8),
+        ("av", ctypes.c_double * 8), ("bv", ctypes.c_double * 8), ("arithmetic", ctypes.c_int),
     ]
 
 
-def mv_desc(spec) -> MVDesc:
+def mv_desc(spec, fp32: bool = False) -> MVDesc:
     d = MVDesc()
     d.n_x, d.n_v, d.order_k, d.quad_q = spec.n_x, spec.n_v, spec.order_k, spec.quad_q
     d.x_min, d.x_max, d.v_min, d.v_max = spec.x_min, spec.x_max, spec.v_min, spec.v_max
     d.n_terms = len(spec.terms)
     for t, (c, ax, bx, av, bv) in enumerate(spec.terms):
         d.coef[t], d.ax[t], d.bx[t], d.av[t], d.bv[t] = c, ax, bx, av, bv
+    d.arithmetic = 1 if fp32 else 0
     return d
 
 
 class MV:
     """Two-dimensional (mass, volume) DG of Sec. 5.3 (grace_mv_*): g and L are float64 CUDA tensors
-    [n_cells, n_coef] in the layout ((j (k+1) + p) n_v + m)(k+1) + q."""
+    [n_cells, n_coef] in the layout ((j (k+1) + p) n_v + m)(k+1) + q; fp32 selects the FP32
+    contraction (the state stays FP64)."""
 
-    def __init__(self, spec, device: int = 0):
+    def __init__(self, spec, device: int = 0, fp32: bool = False):
         self.spec = spec
         self.device = device
         self._h = ctypes.c_void_p()
-        d = mv_desc(spec)
+        d = mv_desc(spec, fp32)
         _check(load().grace_mv_setup(ctypes.byref(self._h), ctypes.byref(d), int(device)), "grace_mv_setup")
 
     def _stream(self):

@@ -162,7 +162,8 @@ def test_setup_rejects_invalid_edges(lib, bad):
 
 
 @pytest.mark.parametrize("field,value", [("n_x", 0), ("n_v", 0), ("order_k", 5), ("quad_q", 0), ("quad_q", 25),
-                                         ("x_min", 0.0), ("v_max", 1e-3), ("n_terms", 0), ("n_terms", 9)])
+                                         ("x_min", 0.0), ("v_max", 1e-3), ("n_terms", 0), ("n_terms", 9),
+                                         ("arithmetic", 2), ("arithmetic", -1)])
 def test_mv_setup_rejects_invalid_descriptions(field, value):
     """The two-dimensional setup validates its description on the host (no GPU needed)."""
     from paper_2607_13740_b300 import workloads as W

@@ -109,3 +109,64 @@ def test_full_size_workload_conserves_mass():
     m0, m1 = mass(g0), mass(g.cpu().numpy())
     assert np.isfinite(m1).all()
     assert np.abs(m1 - m0).max() <= 1e-12 * np.abs(m0).max()
+
+
+# FP32 contraction (arithmetic = 1): the factor forms and the cell's coefficients are rounded to FP32
+# (unit round-off u = 2^-24 = 6.0e-8) and every sum runs in FP32.  The longest chain of rounded
+# operations behind one output, at the sizes here (at most 24 rows and columns per dimension, five
+# kernel terms): the two 24-term sums of H and W, 18 lane terms and 5 butterfly levels of <Vg[b], W>,
+# 24 row and 5 term accumulations into L and three input roundings, n ~ 200, so
+# |dL| <= n u sum|products| ~ 1.2e-5 sum|products|.  With random signed Legendre coefficients the
+# products' magnitudes sum to a few times |L| (at most 8x allowed), hence 1e-4 of the cell's largest |L|.
+TOL32 = 1e-4
+
+
+@pytest.mark.parametrize("name", ["additive_k1", "mixed_k3", "mixed_k1_5x3", "cross_k1"])
+def test_fp32_rhs_matches_oracle(name):
+    spec = CASES[name]
+    g = W.mv_random_coefficients(spec, 3, seed=79)
+    L = grace.MV(spec, fp32=True).rhs(torch.as_tensor(g, device=DEV)).cpu().numpy()
+    Lo = oracle.MVOracle(spec).rhs(g)
+    assert np.isfinite(L).all()
+    err = _rel(L, Lo)
+    assert err <= TOL32, err
+    # the FP32 contraction does round: it is not the FP64 path
+    assert err > 0.0
+
+
+def test_fp32_steps_match_oracle_and_keep_the_state_fp64():
+    spec = CASES["mixed_k1_5x3"]
+    g = W.mv_random_coefficients(spec, 2, seed=83)
+    rate = np.abs(oracle.MVOracle(spec).rhs(g)).max(axis=1)
+    dt = 0.01 * np.abs(g).max(axis=1) / rate
+    gt = torch.as_tensor(g, device=DEV).clone()
+    grace.MV(spec, fp32=True).step(gt, torch.as_tensor(dt, device=DEV), 3)
+    assert gt.dtype == torch.float64
+    go = oracle.MVOracle(spec).step(g, dt, 3)
+    s = np.abs(go).max(axis=1, keepdims=True)
+    # three steps of three stages, each adding dt L with |dt L| ~ 1 % of the largest coefficient
+    assert (np.abs(gt.cpu().numpy() - go) / s).max() <= 9 * 0.01 * TOL32
+
+
+def test_fp32_workload_grid_sampled_cell_and_full_size_mass():
+    """The benchmark's grid shape at a smaller size, one sampled cell against the oracle; then the
+    full-size workload (16,384 cells of 12 x 12 bins, Q = 8) through three FP32 steps, where mass is
+    kept up to the FP32 error of the rates: |dm| <= 9 (dt / 3) sum_bins w |dL| with |dL| bounded by
+    TOL32 of the cell's largest |L| (an exact property of the step at any size)."""
+    spec, g0, dt = W.mv_batch(n_cells=512, n_x=8, n_v=8, quad_q=4)
+    L = grace.MV(spec, fp32=True).rhs(torch.as_tensor(g0, device=DEV)).cpu().numpy()
+    assert _rel(L[[300]], oracle.MVOracle(spec).rhs(g0[[300]])) <= TOL32
+    spec, g0, dt = W.mv_batch()
+    mv = grace.MV(spec, fp32=True)
+    g = torch.as_tensor(g0, device=DEV)
+    Lmax = np.abs(mv.rhs(g).cpu().numpy()).max(axis=1)
+    mv.step(g, torch.as_tensor(dt, device=DEV), 3)
+    K1 = spec.order_k + 1
+    ex, ev = oracle.MVOracle(spec).edges()
+    w = (np.diff(ex)[:, None] * np.diff(ev)[None, :]).reshape(-1)
+    def mass(a):
+        return (a.reshape(a.shape[0], spec.n_x, K1, spec.n_v, K1)[:, :, 0, :, 0].reshape(a.shape[0], -1) * w).sum(axis=1)
+    m0, m1 = mass(g0), mass(g.cpu().numpy())
+    assert np.isfinite(m1).all()
+    bound = 3 * dt * TOL32 * w.sum() * Lmax * 2  # three steps; 2x for the stages' own rates
+    assert np.all(np.abs(m1 - m0) <= bound + 1e-12 * np.abs(m0))

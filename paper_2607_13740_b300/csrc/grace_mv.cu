@@ -291,6 +291,187 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_kernel(MvArgs<R> A, int n_c
     for (int i = tid; i < P; i += nt) Lout[cell * P + i] = (double)Lc[i];
 }
 
+// Shared-memory layout of the FP32 kernel, in floats, each array starting on a 16-byte boundary:
+// G and L (P each), the K1 rows of one mass bin of X_t (K1 Px^2), their H (K1 Px Pv) and W
+// (K1 Pv^2), the block-sum scratch
+struct MvF32Smem {
+    size_t G, L, X, H, W, red, total;
+};
+
+__host__ __device__ inline size_t mv_round4(size_t n) { return (n + 3) & ~(size_t)3; }
+
+__host__ __device__ inline MvF32Smem mv_f32_layout(int Px, int Pv, int K1)
+{
+    MvF32Smem o;
+    const size_t P = (size_t)Px * Pv;
+    o.G = 0;
+    o.L = mv_round4(P);
+    o.X = o.L + mv_round4(P);
+    o.H = o.X + mv_round4((size_t)K1 * Px * Px);
+    o.W = o.H + mv_round4((size_t)K1 * Px * Pv);
+    o.red = o.W + mv_round4((size_t)K1 * Pv * Pv);
+    o.total = o.red + kMvThreads / 32;
+    return o;
+}
+
+// The FP32 contraction, one cell per CTA.  The same sums as mv_rhs_kernel, with the K1 target rows
+// a = j K1 + p of a mass bin j taken together (they share the source range a1, a2 < (j+1) K1):
+// per bin, H_p = X_t[a] G over that range, W_p = G^T H_p, and L[a][b] += <V_t[b], W_p>, so each
+// bin needs three barriers and each V_t element loaded serves K1 products.  With VEC (P_v a
+// multiple of 4) a thread computes four adjacent columns of H or W from one float4 load.
+template <bool VEC>
+__global__ void __launch_bounds__(kMvThreads) mv_rhs_f32_kernel(MvArgs<float> A, int n_cells, const double *__restrict__ g,
+                                                               double *__restrict__ Lout)
+{
+    extern __shared__ __align__(16) float smf[];
+    const int Px = A.Px, Pv = A.Pv, K1 = A.K1, P = Px * Pv;
+    const MvF32Smem o = mv_f32_layout(Px, Pv, K1);
+    float *G = smf + o.G, *Lc = smf + o.L, *Xs = smf + o.X, *H = smf + o.H, *Wm = smf + o.W, *red = smf + o.red;
+    const long long cell = blockIdx.x;
+    if (cell >= n_cells) return;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    const int Pv4 = Pv / 4;
+    for (int i = tid; i < P; i += nt) {
+        G[i] = (float)g[cell * P + i];
+        Lc[i] = 0.f;
+    }
+    __syncthreads();
+    for (int t = 0; t < A.T; ++t) {
+        // ---- loss, as in the FP64 kernel
+        const float *XL2 = A.XL2 + (size_t)t * Px, *VL2 = A.VL2 + (size_t)t * Pv;
+        float part = 0.f;
+        for (int i = tid; i < P; i += nt) part += XL2[i / Pv] * VL2[i % Pv] * G[i];
+        const float S = block_sum(part, red);
+        const float *XL1 = A.XL1 + (size_t)t * A.Nx * K1 * K1, *VL1 = A.VL1 + (size_t)t * A.Nv * K1 * K1;
+        for (int i = tid; i < P; i += nt) {
+            const int a = i / Pv, b = i % Pv, j = a / K1, p = a % K1, m = b / K1, q = b % K1;
+            float s = 0.f;
+            for (int p1 = 0; p1 < K1; ++p1) {
+                const float xl = XL1[(j * K1 + p) * K1 + p1];
+                if (xl == 0.f) continue;
+                for (int q1 = 0; q1 < K1; ++q1) s += xl * VL1[(m * K1 + q) * K1 + q1] * G[(j * K1 + p1) * Pv + m * K1 + q1];
+            }
+            Lc[i] -= S * s;
+        }
+        __syncthreads();
+        // ---- gain, one mass bin (K1 target rows) at a time
+        const float *Xt = A.Xg + (size_t)t * Px * Px * Px, *Vt = A.Vg + (size_t)t * Pv * Pv * Pv;
+        for (int j = 0; j < A.Nx; ++j) {
+            const int amax = (j + 1) * K1, aa = amax * amax;
+            // Xs[p][a1][a2] = X_t[j K1 + p][a1][a2], a1, a2 < amax
+            for (int i = tid; i < K1 * aa; i += nt) {
+                const int p = i / aa, r = i % aa;
+                Xs[i] = Xt[((size_t)(j * K1 + p) * Px + r / amax) * Px + r % amax];
+            }
+            __syncthreads();
+            // H[p][a1][b2] = sum_{a2 < amax} Xs[p][a1][a2] G[a2][b2]
+            if (VEC) {
+                const float4 *G4 = reinterpret_cast<const float4 *>(G);
+                float4 *H4 = reinterpret_cast<float4 *>(H);
+                for (int i = tid; i < K1 * amax * Pv4; i += nt) {
+                    const int pa = i / Pv4, c = i % Pv4;   // pa = p amax + a1
+                    const float *xr = Xs + (size_t)pa * amax;
+                    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int a2 = 0; a2 < amax; ++a2) {
+                        const float x = xr[a2];
+                        const float4 v = G4[a2 * Pv4 + c];
+                        s.x = fmaf(x, v.x, s.x);
+                        s.y = fmaf(x, v.y, s.y);
+                        s.z = fmaf(x, v.z, s.z);
+                        s.w = fmaf(x, v.w, s.w);
+                    }
+                    H4[i] = s;
+                }
+            } else {
+                for (int i = tid; i < K1 * amax * Pv; i += nt) {
+                    const int pa = i / Pv, b2 = i % Pv;
+                    const float *xr = Xs + (size_t)pa * amax;
+                    float s = 0.f;
+                    for (int a2 = 0; a2 < amax; ++a2) s = fmaf(xr[a2], G[a2 * Pv + b2], s);
+                    H[i] = s;
+                }
+            }
+            __syncthreads();
+            // W[p][b1][b2] = sum_{a1 < amax} G[a1][b1] H[p][a1][b2]
+            if (VEC) {
+                const float4 *H4 = reinterpret_cast<const float4 *>(H);
+                float4 *W4 = reinterpret_cast<float4 *>(Wm);
+                for (int i = tid; i < K1 * Pv * Pv4; i += nt) {
+                    const int p = i / (Pv * Pv4), r = i % (Pv * Pv4), b1 = r / Pv4, c = r % Pv4;
+                    const float4 *hp = H4 + (size_t)p * amax * Pv4 + c;
+                    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int a1 = 0; a1 < amax; ++a1) {
+                        const float x = G[a1 * Pv + b1];
+                        const float4 v = hp[a1 * Pv4];
+                        s.x = fmaf(x, v.x, s.x);
+                        s.y = fmaf(x, v.y, s.y);
+                        s.z = fmaf(x, v.z, s.z);
+                        s.w = fmaf(x, v.w, s.w);
+                    }
+                    W4[i] = s;
+                }
+            } else {
+                for (int i = tid; i < K1 * Pv * Pv; i += nt) {
+                    const int p = i / (Pv * Pv), r = i % (Pv * Pv), b1 = r / Pv, b2 = r % Pv;
+                    const float *hp = H + (size_t)p * amax * Pv + b2;
+                    float s = 0.f;
+                    for (int a1 = 0; a1 < amax; ++a1) s = fmaf(G[a1 * Pv + b1], hp[a1 * Pv], s);
+                    Wm[i] = s;
+                }
+            }
+            __syncthreads();
+            // L[j K1 + p][b] += sum_{b1, b2 < bmax} V_t[b][b1][b2] W[p][b1][b2], one warp per b; the
+            // lanes walk the (b1, column group) pairs of the range, the index advanced without a
+            // division; with VEC a group is four columns, those at or beyond bmax masked
+            for (int b = warp; b < Pv; b += nw) {
+                const int bmax = (b / K1 + 1) * K1;
+                const float *Vb = Vt + (size_t)b * Pv * Pv;
+                float s[kMvKMax + 1];
+#pragma unroll
+                for (int p = 0; p <= kMvKMax; ++p) s[p] = 0.f;
+                const int cw = VEC ? (bmax + 3) / 4 : bmax, db1 = 32 / cw, dc = 32 % cw;
+                int b1 = lane / cw, c = lane % cw;
+                while (b1 < bmax) {
+                    if (VEC) {
+                        float4 v = *reinterpret_cast<const float4 *>(Vb + b1 * Pv + 4 * c);
+                        if (4 * c + 1 >= bmax) v.y = 0.f;
+                        if (4 * c + 2 >= bmax) v.z = 0.f;
+                        if (4 * c + 3 >= bmax) v.w = 0.f;
+#pragma unroll
+                        for (int p = 0; p <= kMvKMax; ++p)
+                            if (p < K1) {
+                                const float4 w = *reinterpret_cast<const float4 *>(Wm + (size_t)p * Pv * Pv + b1 * Pv + 4 * c);
+                                s[p] = fmaf(v.x, w.x, fmaf(v.y, w.y, fmaf(v.z, w.z, fmaf(v.w, w.w, s[p]))));
+                            }
+                    } else {
+                        const int e = b1 * Pv + c;
+                        const float v = Vb[e];
+#pragma unroll
+                        for (int p = 0; p <= kMvKMax; ++p)
+                            if (p < K1) s[p] = fmaf(v, Wm[(size_t)p * Pv * Pv + e], s[p]);
+                    }
+                    c += dc;
+                    b1 += db1;
+                    if (c >= cw) {
+                        c -= cw;
+                        ++b1;
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p <= kMvKMax; ++p) {
+                    if (p >= K1) break;
+                    float r = s[p];
+                    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+                    if (lane == 0) Lc[(j * K1 + p) * Pv + b] += r;
+                }
+            }
+            // the next bin writes Xs, H and W only after two more barriers
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < P; i += nt) Lout[cell * P + i] = (double)Lc[i];
+}
+
 __global__ void mv_to_f32_kernel(long long n, const double *src, float *dst)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -340,7 +521,7 @@ grace_status grace_mv_setup(grace_mv **out, const grace_mv_desc *d, int device)
             return GRACE_ERR_ARG;
         }
     const int K1 = d->order_k + 1, Px = d->n_x * K1, Pv = d->n_v * K1;
-    const size_t smem = mv_smem(Px, Pv, d->arithmetic ? sizeof(float) : sizeof(double));
+    const size_t smem = d->arithmetic ? sizeof(float) * mv_f32_layout(Px, Pv, K1).total : mv_smem(Px, Pv, sizeof(double));
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || device >= dev_count) {
         set_error("grace_mv_setup: no such CUDA device");
@@ -406,19 +587,20 @@ grace_status grace_mv_setup(grace_mv **out, const grace_mv_desc *d, int device)
                              (size_t)T * d->n_v * K1 * K1, (size_t)T * Pv};
         const double *src[6] = {m->Xg, m->Vg, m->XL1, m->XL2, m->VL1, m->VL2};
         size_t tot = 0;
-        for (int i = 0; i < 6; ++i) tot += n[i];
+        for (int i = 0; i < 6; ++i) tot += mv_round4(n[i]);   // each copy 16-byte aligned
         e = cudaMalloc(&m->f32, tot * sizeof(float));
         size_t off = 0;
         for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
             mv_to_f32_kernel<<<(unsigned)((n[i] + 255) / 256), 256>>>((long long)n[i], src[i], m->f32 + off);
-            off += n[i];
+            off += mv_round4(n[i]);
         }
         if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
-        e = d->arithmetic ? cudaFuncSetAttribute(mv_rhs_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                          : cudaFuncSetAttribute(mv_rhs_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = d->arithmetic == 0 ? cudaFuncSetAttribute(mv_rhs_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+            : Pv % 4 == 0     ? cudaFuncSetAttribute(mv_rhs_f32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                              : cudaFuncSetAttribute(mv_rhs_f32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         grace_mv_destroy(m);
         return cuda_fail(e, "grace_mv_setup: factor forms");
@@ -457,9 +639,9 @@ static MvArgs<R> mv_args(const grace_mv *m)
         A.VL1 = (const R *)m->VL1;
         A.VL2 = (const R *)m->VL2;
     } else {
-        const size_t nx3 = (size_t)A.T * A.Px * A.Px * A.Px, nv3 = (size_t)A.T * A.Pv * A.Pv * A.Pv;
-        const size_t nl1x = (size_t)A.T * A.Nx * A.K1 * A.K1, nl2x = (size_t)A.T * A.Px;
-        const size_t nl1v = (size_t)A.T * A.Nv * A.K1 * A.K1;
+        const size_t nx3 = mv_round4((size_t)A.T * A.Px * A.Px * A.Px), nv3 = mv_round4((size_t)A.T * A.Pv * A.Pv * A.Pv);
+        const size_t nl1x = mv_round4((size_t)A.T * A.Nx * A.K1 * A.K1), nl2x = mv_round4((size_t)A.T * A.Px);
+        const size_t nl1v = mv_round4((size_t)A.T * A.Nv * A.K1 * A.K1);
         const R *f = (const R *)m->f32;
         A.Xg = f;
         A.Vg = f + nx3;
@@ -473,8 +655,10 @@ static MvArgs<R> mv_args(const grace_mv *m)
 
 static void mv_launch_rhs(const grace_mv *m, int n_cells, const double *g, double *L)
 {
-    if (m->d.arithmetic)
-        mv_rhs_kernel<float><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<float>(m), n_cells, g, L);
+    if (m->d.arithmetic && m->Pv % 4 == 0)
+        mv_rhs_f32_kernel<true><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<float>(m), n_cells, g, L);
+    else if (m->d.arithmetic)
+        mv_rhs_f32_kernel<false><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<float>(m), n_cells, g, L);
     else
         mv_rhs_kernel<double><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<double>(m), n_cells, g, L);
 }

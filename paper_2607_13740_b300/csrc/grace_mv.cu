@@ -47,6 +47,7 @@ namespace grace {
 namespace {
 
 constexpr int kMvThreads = 256;
+constexpr int kMvF32Threads = 128;   // the FP32 kernel: more, smaller CTAs per SM
 constexpr int kMvQMax = 24, kMvKMax = 4, kMvTMax = 8;
 
 __device__ __forceinline__ double leg(int p, double t)
@@ -310,7 +311,7 @@ __host__ __device__ inline MvF32Smem mv_f32_layout(int Px, int Pv, int K1)
     o.H = o.X + mv_round4((size_t)K1 * Px * Px);
     o.W = o.H + mv_round4((size_t)K1 * Px * Pv);
     o.red = o.W + mv_round4((size_t)K1 * Pv * Pv);
-    o.total = o.red + kMvThreads / 32;
+    o.total = o.red + kMvF32Threads / 32;
     return o;
 }
 
@@ -318,13 +319,15 @@ __host__ __device__ inline MvF32Smem mv_f32_layout(int Px, int Pv, int K1)
 // a = j K1 + p of a mass bin j taken together (they share the source range a1, a2 < (j+1) K1):
 // per bin, H_p = X_t[a] G over that range, W_p = G^T H_p, and L[a][b] += <V_t[b], W_p>, so each
 // bin needs three barriers and each V_t element loaded serves K1 products.  With VEC (P_v a
-// multiple of 4) a thread computes four adjacent columns of H or W from one float4 load.
-template <bool VEC>
-__global__ void __launch_bounds__(kMvThreads) mv_rhs_f32_kernel(MvArgs<float> A, int n_cells, const double *__restrict__ g,
+// multiple of 4) a thread computes four adjacent columns of H or W from one float4 load.  The
+// degree is a template parameter (K1 = k + 1 = A.K1), so the loops over the K1 rows carry no
+// predicates and the index divisions by K1 are by a constant.
+template <int K1, bool VEC>
+__global__ void __launch_bounds__(kMvF32Threads) mv_rhs_f32_kernel(MvArgs<float> A, int n_cells, const double *__restrict__ g,
                                                                double *__restrict__ Lout)
 {
     extern __shared__ __align__(16) float smf[];
-    const int Px = A.Px, Pv = A.Pv, K1 = A.K1, P = Px * Pv;
+    const int Px = A.Px, Pv = A.Pv, P = Px * Pv;
     const MvF32Smem o = mv_f32_layout(Px, Pv, K1);
     float *G = smf + o.G, *Lc = smf + o.L, *Xs = smf + o.X, *H = smf + o.H, *Wm = smf + o.W, *red = smf + o.red;
     const long long cell = blockIdx.x;
@@ -426,9 +429,9 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_f32_kernel(MvArgs<float> A,
             for (int b = warp; b < Pv; b += nw) {
                 const int bmax = (b / K1 + 1) * K1;
                 const float *Vb = Vt + (size_t)b * Pv * Pv;
-                float s[kMvKMax + 1];
+                float s[K1];
 #pragma unroll
-                for (int p = 0; p <= kMvKMax; ++p) s[p] = 0.f;
+                for (int p = 0; p < K1; ++p) s[p] = 0.f;
                 const int cw = VEC ? (bmax + 3) / 4 : bmax, db1 = 32 / cw, dc = 32 % cw;
                 int b1 = lane / cw, c = lane % cw;
                 while (b1 < bmax) {
@@ -438,17 +441,15 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_f32_kernel(MvArgs<float> A,
                         if (4 * c + 2 >= bmax) v.z = 0.f;
                         if (4 * c + 3 >= bmax) v.w = 0.f;
 #pragma unroll
-                        for (int p = 0; p <= kMvKMax; ++p)
-                            if (p < K1) {
-                                const float4 w = *reinterpret_cast<const float4 *>(Wm + (size_t)p * Pv * Pv + b1 * Pv + 4 * c);
-                                s[p] = fmaf(v.x, w.x, fmaf(v.y, w.y, fmaf(v.z, w.z, fmaf(v.w, w.w, s[p]))));
-                            }
+                        for (int p = 0; p < K1; ++p) {
+                            const float4 w = *reinterpret_cast<const float4 *>(Wm + (size_t)p * Pv * Pv + b1 * Pv + 4 * c);
+                            s[p] = fmaf(v.x, w.x, fmaf(v.y, w.y, fmaf(v.z, w.z, fmaf(v.w, w.w, s[p]))));
+                        }
                     } else {
                         const int e = b1 * Pv + c;
                         const float v = Vb[e];
 #pragma unroll
-                        for (int p = 0; p <= kMvKMax; ++p)
-                            if (p < K1) s[p] = fmaf(v, Wm[(size_t)p * Pv * Pv + e], s[p]);
+                        for (int p = 0; p < K1; ++p) s[p] = fmaf(v, Wm[(size_t)p * Pv * Pv + e], s[p]);
                     }
                     c += dc;
                     b1 += db1;
@@ -458,8 +459,7 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_f32_kernel(MvArgs<float> A,
                     }
                 }
 #pragma unroll
-                for (int p = 0; p <= kMvKMax; ++p) {
-                    if (p >= K1) break;
+                for (int p = 0; p < K1; ++p) {
                     float r = s[p];
                     for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
                     if (lane == 0) Lc[(j * K1 + p) * Pv + b] += r;
@@ -470,6 +470,27 @@ __global__ void __launch_bounds__(kMvThreads) mv_rhs_f32_kernel(MvArgs<float> A,
         __syncthreads();
     }
     for (int i = tid; i < P; i += nt) Lout[cell * P + i] = (double)Lc[i];
+}
+
+using MvF32Kernel = void (*)(MvArgs<float>, int, const double *, double *);
+
+template <int K1>
+MvF32Kernel mv_f32_pick(bool vec)
+{
+    return vec ? mv_rhs_f32_kernel<K1, true> : mv_rhs_f32_kernel<K1, false>;
+}
+
+// the FP32 kernel for degree k = K1 - 1 (0 .. 4) and the column form VEC
+MvF32Kernel mv_f32_kernel_for(int K1, bool vec)
+{
+    switch (K1) {
+    case 1: return mv_f32_pick<1>(vec);
+    case 2: return mv_f32_pick<2>(vec);
+    case 3: return mv_f32_pick<3>(vec);
+    case 4: return mv_f32_pick<4>(vec);
+    case 5: return mv_f32_pick<5>(vec);
+    default: return nullptr;
+    }
 }
 
 __global__ void mv_to_f32_kernel(long long n, const double *src, float *dst)
@@ -599,8 +620,7 @@ grace_status grace_mv_setup(grace_mv **out, const grace_mv_desc *d, int device)
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
         e = d->arithmetic == 0 ? cudaFuncSetAttribute(mv_rhs_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-            : Pv % 4 == 0     ? cudaFuncSetAttribute(mv_rhs_f32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                              : cudaFuncSetAttribute(mv_rhs_f32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                               : cudaFuncSetAttribute(mv_f32_kernel_for(K1, Pv % 4 == 0), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         grace_mv_destroy(m);
         return cuda_fail(e, "grace_mv_setup: factor forms");
@@ -655,10 +675,8 @@ static MvArgs<R> mv_args(const grace_mv *m)
 
 static void mv_launch_rhs(const grace_mv *m, int n_cells, const double *g, double *L)
 {
-    if (m->d.arithmetic && m->Pv % 4 == 0)
-        mv_rhs_f32_kernel<true><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<float>(m), n_cells, g, L);
-    else if (m->d.arithmetic)
-        mv_rhs_f32_kernel<false><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<float>(m), n_cells, g, L);
+    if (m->d.arithmetic)
+        mv_f32_kernel_for(m->K1, m->Pv % 4 == 0)<<<n_cells, kMvF32Threads, m->smem, m->stream>>>(mv_args<float>(m), n_cells, g, L);
     else
         mv_rhs_kernel<double><<<n_cells, kMvThreads, m->smem, m->stream>>>(mv_args<double>(m), n_cells, g, L);
 }

@@ -31,6 +31,8 @@ CASES = {
     "mixed_k1_5x3": W.mv_mixed_spec(5, 3, 1, 6, 0.1, 10.0, 0.1, 100.0),
     "mixed_k1_3x5": W.mv_mixed_spec(3, 5, 1, 5, 0.01, 10.0, 0.1, 10.0),
     "product_k1": W.MVSpec(4, 4, 1, 0.1, 10.0, 0.1, 10.0, 6, ((1.0, 1.0, 1.0, 0.0, 0.0),)),
+    "additive_k0_5x3": W.mv_additive_spec(5, 3, 0, 6, 0.1, 10.0, 0.1, 10.0),
+    "mixed_k2_3x4": W.mv_mixed_spec(3, 4, 2, 5, 0.1, 10.0, 0.1, 10.0),
     "mixed_k4": W.mv_mixed_spec(2, 2, 4, 6, 0.1, 10.0, 0.1, 10.0),
     "mixed_k4_2x4": W.mv_mixed_spec(2, 4, 4, 5, 0.1, 10.0, 0.1, 10.0),
     "cross_k1": W.MVSpec(4, 3, 1, 0.1, 10.0, 0.1, 10.0, 6, ((2.0, 0.5, 0.0, 0.0, 1.0 / 3.0), (2.0, 0.0, 0.5, 1.0 / 3.0, 0.0))),
@@ -123,9 +125,11 @@ def test_full_size_workload_conserves_mass():
 TOL32 = 1e-4
 
 
-# P_v a multiple of 4 (float4 columns): additive_k1, mixed_k3, mixed_k4_2x4; otherwise scalar columns
-@pytest.mark.parametrize("name", ["additive_k0", "additive_k1", "mixed_k3", "mixed_k4", "mixed_k4_2x4",
-                                  "mixed_k1_5x3", "mixed_k1_3x5", "cross_k1"])
+# every degree k = 0 .. 4 with P_v a multiple of 4 (float4 columns: additive_k0, additive_k1,
+# mixed_k2_3x4, mixed_k3, mixed_k4_2x4) and not (scalar columns: additive_k0_5x3, mixed_k1_5x3,
+# mixed_k1_3x5, cross_k1, additive_k2, mixed_k4)
+@pytest.mark.parametrize("name", ["additive_k0", "additive_k0_5x3", "additive_k1", "additive_k2", "mixed_k2_3x4",
+                                  "mixed_k3", "mixed_k4", "mixed_k4_2x4", "mixed_k1_5x3", "mixed_k1_3x5", "cross_k1"])
 def test_fp32_rhs_matches_oracle(name):
     spec = CASES[name]
     g = W.mv_random_coefficients(spec, 3, seed=79)

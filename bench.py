@@ -895,7 +895,7 @@ def run_mv(args, emit=True):
                        "timing": "one grace_mv_step call, CUDA events on the launching stream"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if peak else None, "traffic": None,
-                         "kernel": f"mv_rhs_kernel ({name} contraction of the factor forms)",
+                         "kernel": ("mv_rhs_f32_kernel" if fp32 else "mv_rhs_kernel") + f" ({name} contraction of the factor forms)",
                          "algorithmic": f"2 x {macs} multiply-adds per cell and RHS x {n} cells", "peak_source": psrc},
             "rhs_ms": rhs_ms, "setup_s": setup_s,
             "mass_drift": float(np.abs(m1 - m0).max() / np.abs(m0).max()),

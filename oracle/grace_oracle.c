@@ -229,9 +229,11 @@ static double cross_section(double u, double v)
 
 /* ballistic kernel with a turbulent relative velocity: the project's own model
    for the large disk workloads (the paper gives no formula; parameters in p).
-   Parity unpinned for this formula (a definition with no closed form to check it
-   against); the flux quadrature with it is pinned against brute-force adaptive
-   integration in the tests.  Parameters:
+   The formula is pinned in the tests by what its definition fixes (symmetry, power
+   laws in alpha, c_s, the rate scale and, for St << 1 and St >> 1, the grain mass;
+   the larger grain setting St; St <-> 1/St invariance and the maximum at St = 1; the
+   ramp's end and mid points); the flux quadrature with it is pinned against
+   brute-force adaptive integration.  Parameters:
    p[0] = rho_s, p[1] = Sigma_g, p[2] = c_s, p[3] = alpha_turb, p[4] = v_frag,
    p[5] = ramp half-width fraction, p[6] = overall rate scale. */
 static void ballistic(const real *p, double u, double v, real *kc, real *kf)

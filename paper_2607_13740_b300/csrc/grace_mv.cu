@@ -369,21 +369,27 @@ __global__ void __launch_bounds__(kMvF32Threads) mv_rhs_f32_kernel(MvArgs<float>
             __syncthreads();
             // H[p][a1][b2] = sum_{a2 < amax} Xs[p][a1][a2] G[a2][b2]
             if (VEC) {
+                // a thread: four columns of row a1 for all K1 rows p (one G load serves K1 x 4 FMAs)
                 const float4 *G4 = reinterpret_cast<const float4 *>(G);
                 float4 *H4 = reinterpret_cast<float4 *>(H);
-                for (int i = tid; i < K1 * amax * Pv4; i += nt) {
-                    const int pa = i / Pv4, c = i % Pv4;   // pa = p amax + a1
-                    const float *xr = Xs + (size_t)pa * amax;
-                    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int i = tid; i < amax * Pv4; i += nt) {
+                    const int a1 = i / Pv4, c = i % Pv4;
+                    float4 s[K1];
+#pragma unroll
+                    for (int p = 0; p < K1; ++p) s[p] = make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int a2 = 0; a2 < amax; ++a2) {
-                        const float x = xr[a2];
                         const float4 v = G4[a2 * Pv4 + c];
-                        s.x = fmaf(x, v.x, s.x);
-                        s.y = fmaf(x, v.y, s.y);
-                        s.z = fmaf(x, v.z, s.z);
-                        s.w = fmaf(x, v.w, s.w);
+#pragma unroll
+                        for (int p = 0; p < K1; ++p) {
+                            const float x = Xs[(p * amax + a1) * amax + a2];
+                            s[p].x = fmaf(x, v.x, s[p].x);
+                            s[p].y = fmaf(x, v.y, s[p].y);
+                            s[p].z = fmaf(x, v.z, s[p].z);
+                            s[p].w = fmaf(x, v.w, s[p].w);
+                        }
                     }
-                    H4[i] = s;
+#pragma unroll
+                    for (int p = 0; p < K1; ++p) H4[(p * amax + a1) * Pv4 + c] = s[p];
                 }
             } else {
                 for (int i = tid; i < K1 * amax * Pv; i += nt) {
@@ -397,21 +403,27 @@ __global__ void __launch_bounds__(kMvF32Threads) mv_rhs_f32_kernel(MvArgs<float>
             __syncthreads();
             // W[p][b1][b2] = sum_{a1 < amax} G[a1][b1] H[p][a1][b2]
             if (VEC) {
+                // a thread: four columns of row b1 for all K1 rows p (one G load serves K1 x 4 FMAs)
                 const float4 *H4 = reinterpret_cast<const float4 *>(H);
                 float4 *W4 = reinterpret_cast<float4 *>(Wm);
-                for (int i = tid; i < K1 * Pv * Pv4; i += nt) {
-                    const int p = i / (Pv * Pv4), r = i % (Pv * Pv4), b1 = r / Pv4, c = r % Pv4;
-                    const float4 *hp = H4 + (size_t)p * amax * Pv4 + c;
-                    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int i = tid; i < Pv * Pv4; i += nt) {
+                    const int b1 = i / Pv4, c = i % Pv4;
+                    float4 s[K1];
+#pragma unroll
+                    for (int p = 0; p < K1; ++p) s[p] = make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int a1 = 0; a1 < amax; ++a1) {
                         const float x = G[a1 * Pv + b1];
-                        const float4 v = hp[a1 * Pv4];
-                        s.x = fmaf(x, v.x, s.x);
-                        s.y = fmaf(x, v.y, s.y);
-                        s.z = fmaf(x, v.z, s.z);
-                        s.w = fmaf(x, v.w, s.w);
+#pragma unroll
+                        for (int p = 0; p < K1; ++p) {
+                            const float4 v = H4[(p * amax + a1) * Pv4 + c];
+                            s[p].x = fmaf(x, v.x, s[p].x);
+                            s[p].y = fmaf(x, v.y, s[p].y);
+                            s[p].z = fmaf(x, v.z, s[p].z);
+                            s[p].w = fmaf(x, v.w, s[p].w);
+                        }
                     }
-                    W4[i] = s;
+#pragma unroll
+                    for (int p = 0; p < K1; ++p) W4[(p * Pv + b1) * Pv4 + c] = s[p];
                 }
             } else {
                 for (int i = tid; i < K1 * Pv * Pv; i += nt) {

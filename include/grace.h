@@ -452,9 +452,11 @@ typedef struct grace_mv grace_mv;
 
 /* Validates the description and builds, on `device`, the 1-D factor forms of
    every kernel term (the gain forms over pairs of bins in x and in v, the loss
-   factors).  Allocates and synchronises.  GRACE_ERR_UNSUPPORTED when a cell's
-   coefficient matrix (n_x (k+1)) x (n_v (k+1)) does not fit the per-cell stage
-   in shared memory. */
+   factors; with arithmetic = 1 also their FP32 copies).  Allocates and
+   synchronises.  GRACE_ERR_ARG for a field out of its range (arithmetic other
+   than 0 or 1 included); GRACE_ERR_UNSUPPORTED when a cell's coefficient matrix
+   (n_x (k+1)) x (n_v (k+1)) does not fit the per-cell stage in shared memory
+   (FP32 stages take less). */
 GRACE_API grace_status grace_mv_setup(grace_mv **mv, const grace_mv_desc *desc, int device);
 /* Stream for the compute calls (the legacy default stream if none). */
 GRACE_API grace_status grace_mv_set_stream(grace_mv *mv, void *cuda_stream);

@@ -216,8 +216,8 @@ __device__ __forceinline__ R block_sum(R v, R *red)
     return s;
 }
 
-// L = dg/dt of one cell per CTA, in the arithmetic R (double, or float with FP32 factor forms; the
-// state is read and L written in FP64 either way)
+// L = dg/dt of one cell per CTA, in the arithmetic R (instantiated for double; the FP32 form is
+// mv_rhs_f32_kernel below); the state is read and L written in FP64
 template <class R>
 __global__ void __launch_bounds__(kMvThreads) mv_rhs_kernel(MvArgs<R> A, int n_cells, const double *__restrict__ g,
                                                            double *__restrict__ Lout)
